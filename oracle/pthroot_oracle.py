@@ -1,0 +1,278 @@
+"""Plain FP64 CPU oracle for the inverse p-th root iteration (Lass, Kuehne, Plessl, arXiv:1703.02283).
+
+TEST INFRASTRUCTURE ONLY. This module is imported by the tests, by ``__graft_entry__.smoke()`` and by
+the benchmark's CPU-baseline leg, and by nothing else. It shares no code with the CUDA path: the only
+common input is the seeded matrix generator in ``paper_1703_02283_gb300.workloads``, which holds none of
+the method's arithmetic.
+
+What it computes. For a symmetric positive definite ``A`` and an integer ``p >= 1`` the method of Sec. 2
+refines an initial guess ``C_0`` by Eq. 1,
+
+    C_{k+1} = ((p + 1) C_k - C_k^{p+1} A) / p,
+
+which converges to ``A^{-1/p}`` when ``||I - C_0^p A||_2 < 1`` (Eq. 2). Eq. 3 gives the initial guess
+``C_0 = A^T / (||A||_1 ||A||_inf)``. For p = 1 the iteration is Newton-Schulz for the inverse (Sec. 2).
+
+Forms. Three evaluation orders are provided; all produce the same iterates in exact arithmetic, because
+every iterate is a polynomial in ``A`` and therefore commutes with it:
+
+* ``literal``: Eq. 1 exactly as printed, ``C^{p+1} A`` formed right to left (``T = A``, then ``p + 1``
+  times ``T = C T``).
+* ``ns`` (p = 1 only): ``C (2I - A C)``, the Newton-Schulz form named in Sec. 2.
+* ``coupled``: ``X_0 = C_0``, ``M_0 = X_0^p A``; ``N_k = ((p+1) I - M_k) / p``, ``X_{k+1} = X_k N_k``,
+  ``M_{k+1} = N_k^p M_k``. Since ``X_{k+1} = X_k ((p+1) I - X_k^p A) / p`` this is Eq. 1 with the product
+  ``X_k^p A`` carried along as ``M_k`` instead of being recomputed. (Reading: the literal order is
+  numerically unstable for ill-conditioned ``A``, so the coupled order is what the library and this
+  oracle run for p >= 2, and ``ns`` for p = 1.)
+
+Readings where the paper is silent. Iterates are kept symmetric, ``(Y + Y^T) / 2``: in the coupled
+form every product (its factors commute exactly in exact arithmetic), in the Newton-Schulz and literal
+forms only the new iterate (their inner products ``A C`` and ``C^j A`` stay unsymmetrised); the stop
+test uses the Frobenius residual ``||I - C^p A||_F`` (the coupled form uses ``||I - M_k||_F``, the same
+quantity in exact arithmetic) against a tolerance, with a stagnation exit once the residual is below
+``stag_below`` and fails to halve; the error metric is the Frobenius distance to the exact root (Sec. 4.3).
+
+Pins (tests/test_oracle_pins.py): the p = 1 limit equals the matrix inverse; the limit equals the closed
+form ``Q diag(lam^{-1/p}) Q^T`` and a LAPACK eigendecomposition root; the per-iteration residual equals
+the scalar recurrence of Eq. 1 in the eigenbasis; hand-computed dyadic iterates of small diagonal cases
+(tests/golden); the Eq. 2 bound for Eq. 3's guess; symmetry and commutation invariants; the three forms
+agree; the quadratic tail.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "norm_1", "norm_inf", "initial_guess_eq3", "initial_guess_scaled_identity", "symmetrize",
+    "sym_product", "power_times", "residual_fro", "step_literal", "step_newton_schulz",
+    "coupled_start", "step_coupled", "solve", "SolveInfo", "closed_form_root", "eig_root",
+    "scalar_recurrence", "scalar_residuals", "forward_error", "default_form",
+]
+
+
+# ---------------------------------------------------------------- norms and initial guess (Eq. 3)
+
+def norm_1(A: np.ndarray) -> float:
+    """||A||_1: the largest absolute column sum, max_j sum_i |a_ij| (the 1-norm of Eq. 3)."""
+    return float(np.max(np.sum(np.abs(A), axis=0)))
+
+
+def norm_inf(A: np.ndarray) -> float:
+    """||A||_inf: the largest absolute row sum, max_i sum_j |a_ij| (the infinity-norm of Eq. 3)."""
+    return float(np.max(np.sum(np.abs(A), axis=1)))
+
+
+def initial_guess_eq3(A: np.ndarray) -> np.ndarray:
+    """Eq. 3: C_0 = (||A||_1 ||A||_inf)^{-1} A^T."""
+    return np.ascontiguousarray(A.T / (norm_1(A) * norm_inf(A)))
+
+
+def initial_guess_scaled_identity(A: np.ndarray, p: int) -> np.ndarray:
+    """The scalar start C_0 = ||A||_1^{-1/p} I, one of the "different possible choices" of Sec. 2.
+
+    Because lambda_max(A) <= ||A||_1, the eigenvalues of C_0^p A lie in (0, 1], so Eq. 2 holds.
+    """
+    n = A.shape[0]
+    return np.eye(n) * norm_1(A) ** (-1.0 / p)
+
+
+# ---------------------------------------------------------------- products
+
+def symmetrize(Y: np.ndarray) -> np.ndarray:
+    """(Y + Y^T) / 2. The paper is silent on symmetrisation; every product here is symmetrised."""
+    return 0.5 * (Y + Y.T)
+
+
+def sym_product(X: np.ndarray, Y: np.ndarray) -> np.ndarray:
+    """Product of two commuting symmetric matrices, symmetrised."""
+    return symmetrize(X @ Y)
+
+
+def power_times(C: np.ndarray, A: np.ndarray, p: int) -> np.ndarray:
+    """C^p A, formed right to left: T = A, then p times T = C T (the order of Eq. 1's C_k^{p+1} A).
+
+    No symmetrisation: for a C that does not commute with A exactly, C^j A is not symmetric.
+    """
+    T = A
+    for _ in range(p):
+        T = C @ T
+    return T
+
+
+def residual_fro(C: np.ndarray, A: np.ndarray, p: int) -> float:
+    """||I - C^p A||_F, the Frobenius version of the quantity bounded in Eq. 2."""
+    n = A.shape[0]
+    return float(np.linalg.norm(np.eye(n) - power_times(C, A, p)))
+
+
+# ---------------------------------------------------------------- one step of each form (Eq. 1)
+
+def step_literal(C: np.ndarray, A: np.ndarray, p: int) -> np.ndarray:
+    """Eq. 1 as printed: C' = ((p + 1) C - C^{p+1} A) / p, the result symmetrised."""
+    T = power_times(C, A, p + 1)
+    return symmetrize(((p + 1) * C - T) / p)
+
+
+def step_newton_schulz(C: np.ndarray, A: np.ndarray) -> np.ndarray:
+    """p = 1 (Sec. 2, Newton-Schulz): C' = 2C - C (A C), equal to Eq. 1 with p = 1 when C commutes with A.
+
+    The inner product T = A C is kept unsymmetrised: its non-symmetric part is what makes the step
+    correct errors that do not commute with A (C A C is symmetric for every symmetric C). Symmetrising T
+    multiplies such errors by -(sqrt(rho) - 1/sqrt(rho))^2 / 4 per step, rho a ratio of eigenvalues of A.
+    """
+    T = A @ C
+    return symmetrize(2.0 * C - C @ T)
+
+
+def coupled_start(X0: np.ndarray, A: np.ndarray, p: int):
+    """Coupled form: (X_0, M_0) with M_0 = X_0^p A; X_0 is a polynomial in A, so each product is symmetric."""
+    M = A
+    for _ in range(p):
+        M = sym_product(X0, M)
+    return X0.copy(), M
+
+
+def step_coupled(X: np.ndarray, M: np.ndarray, p: int):
+    """One coupled step: N = ((p+1) I - M) / p; X' = X N; M' = N^p M (p products, right to left)."""
+    n = X.shape[0]
+    N = ((p + 1) * np.eye(n) - M) / p
+    Xn = sym_product(X, N)
+    Mn = M
+    for _ in range(p):
+        Mn = sym_product(N, Mn)
+    return Xn, Mn
+
+
+# ---------------------------------------------------------------- the solve loop
+
+def default_form(p: int) -> str:
+    """Newton-Schulz for p = 1, the coupled order otherwise."""
+    return "ns" if p == 1 else "coupled"
+
+
+@dataclass
+class SolveInfo:
+    form: str
+    c0: str
+    p: int
+    iterations: int = 0  # number of updates applied to C
+    residuals: list = field(default_factory=list)  # r_0 .. r_k, r_k belongs to the returned iterate
+    stop: str = ""  # "tol", "stagnation", "max_iter" or "diverged"
+    seconds: float = 0.0
+
+
+def solve(A: np.ndarray, p: int, form: str | None = None, c0: str = "eq3", tol: float = 1e-12,
+          max_iter: int = 100, stag_below: float = 1e-3, stag_ratio: float = 0.5,
+          C0: np.ndarray | None = None):
+    """Iterate Eq. 1 from C_0 until the residual meets ``tol``.
+
+    Stop rule (reading; the paper gives none): after computing r_k for the current iterate, stop with
+    "tol" if r_k <= tol; with "diverged" if r_k is not finite; with "stagnation" if r_{k-1} < stag_below
+    and r_k > stag_ratio * r_{k-1}; with "max_iter" if k == max_iter. Otherwise apply one update.
+    The returned iterate is the one whose residual was r_k.
+
+    ``r_k`` is ||I - C_k^p A||_F for the literal and Newton-Schulz forms and ||I - M_k||_F for the
+    coupled form (equal in exact arithmetic).
+    """
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[0]
+    form = form or default_form(p)
+    if form == "ns" and p != 1:
+        raise ValueError("the Newton-Schulz form is the p = 1 case")
+    if C0 is None:
+        C0 = initial_guess_eq3(A) if c0 == "eq3" else initial_guess_scaled_identity(A, p)
+        c0_name = c0
+    else:
+        c0_name = "given"
+    info = SolveInfo(form=form, c0=c0_name, p=p)
+    eye = np.eye(n)
+    t0 = time.perf_counter()
+
+    def decide(r: float, k: int) -> str:
+        info.residuals.append(r)
+        if not np.isfinite(r):
+            return "diverged"
+        if r <= tol:
+            return "tol"
+        if k >= 1 and info.residuals[-2] < stag_below and r > stag_ratio * info.residuals[-2]:
+            return "stagnation"
+        if k >= max_iter:
+            return "max_iter"
+        return ""
+
+    C = np.array(C0, dtype=np.float64, copy=True)
+    k = 0
+    if form == "coupled":
+        X, M = coupled_start(C, A, p)
+        while True:
+            stop = decide(float(np.linalg.norm(eye - M)), k)
+            if stop:
+                break
+            X, M = step_coupled(X, M, p)
+            k += 1
+        C = X
+    elif form == "ns":
+        while True:
+            T = A @ C
+            stop = decide(float(np.linalg.norm(eye - T)), k)
+            if stop:
+                break
+            C = symmetrize(2.0 * C - C @ T)
+            k += 1
+    elif form == "literal":
+        while True:
+            T = power_times(C, A, p)
+            stop = decide(float(np.linalg.norm(eye - T)), k)
+            if stop:
+                break
+            T = C @ T
+            C = symmetrize(((p + 1) * C - T) / p)
+            k += 1
+    else:
+        raise ValueError(f"unknown form {form!r}")
+    info.iterations = k
+    info.stop = stop
+    info.seconds = time.perf_counter() - t0
+    return C, info
+
+
+# ---------------------------------------------------------------- exact roots and the scalar recurrence
+
+def closed_form_root(Q: np.ndarray, lam: np.ndarray, p: int) -> np.ndarray:
+    """A^{-1/p} = Q diag(lam^{-1/p}) Q^T for A = Q diag(lam) Q^T (the limit named in Sec. 2)."""
+    Z = (Q * lam ** (-1.0 / p)) @ Q.T
+    return symmetrize(Z)
+
+
+def eig_root(A: np.ndarray, p: int) -> np.ndarray:
+    """A^{-1/p} from a LAPACK symmetric eigendecomposition (a library routine, used as an independent pin)."""
+    w, V = np.linalg.eigh(A)
+    return symmetrize((V * w ** (-1.0 / p)) @ V.T)
+
+
+def scalar_recurrence(lam: np.ndarray, c0: np.ndarray, p: int, k: int) -> np.ndarray:
+    """Eigenvalues of C_k: Eq. 1 acts on each eigenvalue independently, c' = ((p + 1) c - c^{p+1} lam) / p."""
+    c = np.array(c0, dtype=np.float64)
+    lam = np.asarray(lam, dtype=np.float64)
+    for _ in range(k):
+        c = ((p + 1) * c - c ** (p + 1) * lam) / p
+    return c
+
+
+def scalar_residuals(lam: np.ndarray, c0: np.ndarray, p: int, k_max: int) -> np.ndarray:
+    """||I - C_k^p A||_F = sqrt(sum_i (1 - c_k(lam_i)^p lam_i)^2) for k = 0..k_max (exact-arithmetic model)."""
+    c = np.array(c0, dtype=np.float64)
+    lam = np.asarray(lam, dtype=np.float64)
+    out = []
+    for _ in range(k_max + 1):
+        out.append(float(np.sqrt(np.sum((1.0 - c ** p * lam) ** 2))))
+        c = ((p + 1) * c - c ** (p + 1) * lam) / p
+    return np.asarray(out)
+
+
+def forward_error(C: np.ndarray, Z: np.ndarray) -> float:
+    """||C - Z||_F / ||Z||_F, the Frobenius error of Sec. 4.3 made relative."""
+    return float(np.linalg.norm(C - Z) / np.linalg.norm(Z))
