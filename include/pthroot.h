@@ -1,0 +1,182 @@
+/*
+ * pthroot.h - C ABI of the GB300 inverse matrix p-th root engine.
+ *
+ * The library computes A^{-1/p} for a dense symmetric positive definite A (order n, root index p >= 1)
+ * with the iteration of Lass, Kuehne and Plessl, "Using Approximate Computing for the Calculation of
+ * Inverse Matrix p-th Roots" (arXiv:1703.02283), Sec. 2:
+ *
+ *     C_{k+1} = ((p + 1) C_k - C_k^{p+1} A) / p                         (Eq. 1)
+ *
+ * started from C_0 = (||A||_1 ||A||_inf)^{-1} A^T (Eq. 3), which satisfies ||I - C_0^p A||_2 < 1 (Eq. 2),
+ * and run until ||I - C_k^p A||_F meets a tolerance. Every iterate is a polynomial in A, hence symmetric
+ * and commuting with A; the library evaluates Eq. 1 in an order that yields the same iterates in exact
+ * arithmetic (see pr_form) and computes only the upper-triangle tiles of products that are symmetric.
+ *
+ * Conventions shared by every entry point:
+ *  - Matrices are n x n, FP64, row-major, leading dimension n. Because they are symmetric, row- and
+ *    column-major storage coincide.
+ *  - A matrix pointer may point to device memory or to host memory (pageable or pinned); the library
+ *    copies with cudaMemcpyDefault (unified addressing tells the two apart) on the handle's stream.
+ *  - A handle owns all of its device memory; the caller's buffers are never retained after a call
+ *    returns. One handle may be used by one host thread at a time; distinct handles are independent.
+ *  - Work is issued on the CUDA stream given to pr_init (NULL = the legacy default stream). Entry points
+ *    that return host values (residuals, stop decisions) synchronise that stream.
+ *  - Errors are reported by status code only; the library never exits, never traps on the device and
+ *    never throws across the ABI. pr_last_error() gives a text for the last failing call on a handle.
+ *  - All work runs in the library's own CUDA kernels on the current device; there is no CPU fallback.
+ */
+#ifndef PTHROOT_H
+#define PTHROOT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pr_handle_s* pr_handle;
+
+/* Status codes. PR_ESTAGNATED and PR_EMAXITER are stop reasons, not failures: the handle stays valid
+ * and iteration may be resumed (with another precision, for instance). */
+typedef enum {
+  PR_OK = 0,          /* tolerance met (pr_iterate/pr_solve) or call succeeded                          */
+  PR_EINVAL = 1,      /* bad argument: n < 1, p < 1, unknown enum, NULL pointer, non-finite or
+                         non-symmetric A, or tol < 0                                                       */
+  PR_ENOTSPD = 2,     /* A has a non-positive diagonal entry, so it cannot be positive definite          */
+  PR_ENOMEM = 3,      /* device allocation failed                                                        */
+  PR_ECUDA = 4,       /* a CUDA runtime call or kernel launch failed                                     */
+  PR_EDIVERGED = 5,   /* the residual became NaN or Inf                                                  */
+  PR_ESTAGNATED = 6,  /* residual below stag_below stopped halving: the precision floor was reached      */
+  PR_EMAXITER = 7,    /* the step budget of this call (or the handle's max_iter) ran out                 */
+  PR_ETIMEOUT = 8,    /* a bounded device wait expired; the kernel returned without finishing            */
+  PR_EGATE = 9,       /* reserved for initial guesses that fail the Eq. 2 check                          */
+  PR_ESTATE = 10,     /* call out of order (e.g. pr_result before any pr_init)                           */
+  PR_EUNSUPPORTED = 11 /* precision or form not available for this n / p                                 */
+} pr_status;
+
+/* Arithmetic of the matrix products. */
+typedef enum {
+  PR_FP64 = 0,   /* native FP64 products (DMMA tensor instructions), FP64 accumulation                   */
+  PR_EMU64 = 1,  /* FP64-accurate products from exact BF16 slices on the tcgen05 tensor cores           */
+  PR_BF16 = 3    /* BF16 operands, FP32 accumulation in TMEM (tcgen05 kind::f16); FP64 master copies     */
+} pr_precision;
+
+/* Evaluation order of Eq. 1 (identical iterates in exact arithmetic). */
+typedef enum {
+  PR_FORM_AUTO = 0,     /* PR_FORM_NS for p = 1, PR_FORM_COUPLED otherwise                                */
+  PR_FORM_COUPLED = 1,  /* X_{k+1} = X_k N_k, M_{k+1} = N_k^p M_k, N_k = ((p+1) I - M_k)/p, M_0 = C_0^p A;
+                           the residual is ||I - M_k||_F (equal to ||I - X_k^p A||_F in exact arithmetic) */
+  PR_FORM_NS = 2,       /* p = 1 only (Sec. 2, Newton-Schulz): C' = 2C - C (A C), residual ||I - A C||_F  */
+  PR_FORM_LITERAL = 3   /* Eq. 1 as printed, C^{p+1} A right to left; unstable for ill-conditioned A      */
+} pr_form;
+
+/* Initial guess. */
+typedef enum {
+  PR_C0_EQ3 = 0,       /* Eq. 3: C_0 = A^T / (||A||_1 ||A||_inf)                                         */
+  PR_C0_SCALED_I = 1   /* C_0 = ||A||_1^{-1/p} I; one of the "different possible choices" of Sec. 2       */
+} pr_c0_kind;
+
+/* Options fixed at pr_init. */
+typedef struct {
+  int form;            /* pr_form, default PR_FORM_AUTO                                                  */
+  int c0;              /* pr_c0_kind, default PR_C0_EQ3                                                  */
+  int max_iter;        /* cap on the total number of updates over the handle's life, default 100         */
+  double stag_below;   /* stagnation test armed once the previous residual is below this, default 1e-3  */
+  double stag_ratio;   /* ... and fires when r_k > stag_ratio * r_{k-1}, default 0.5                      */
+  double sym_tol;      /* pr_init rejects A with max|a_ij - a_ji| > sym_tol * max|a_ij|, default 1e-12   */
+  int reanchor;        /* coupled form: on a switch to higher precision recompute M = X^p A, default 1  */
+  int emu_slices;      /* PR_EMU64 slice count per operand (0 = chosen from n), default 0               */
+} pr_options;
+
+/* Counters of one handle. */
+typedef struct {
+  int64_t n;
+  int p;
+  int form;                 /* the form actually run (never PR_FORM_AUTO)                               */
+  int c0;
+  int iterations;           /* updates applied so far                                                    */
+  int iterations_by_precision[4]; /* indexed by pr_precision                                             */
+  int switch_iteration;     /* iteration index at which the precision last changed, -1 if never          */
+  int last_precision;       /* precision of the last update, -1 before the first                          */
+  int last_stop;            /* pr_status of the last pr_iterate / pr_solve                                */
+  double norm_1;            /* ||A||_1 (Eq. 3)                                                            */
+  double norm_inf;          /* ||A||_inf (Eq. 3)                                                          */
+  double last_residual;     /* the residual of the current iterate (see pr_form)                          */
+  int64_t gemms;            /* matrix products issued                                                     */
+  double gemm_flops;        /* algorithmic flops of those products: 2 n^3 per full product, n^2 (n + 1)
+                               per symmetric one (the n (n + 1) / 2 upper-triangle outputs)              */
+  int64_t launches;         /* kernels launched by the library on the handle's stream                     */
+  int64_t gemms_timed;      /* products timed with CUDA events (pr_set_timing)                           */
+  double gemm_ms;           /* summed event time of the timed products                                     */
+  double gemm_flops_timed;  /* algorithmic flops of the timed products                                     */
+} pr_stats_t;
+
+/* Fills *opt with the defaults listed above. */
+void pr_default_options(pr_options* opt);
+
+/* Creates a handle for A^{-1/p}.
+ *   h       out: the new handle (NULL on failure)
+ *   A       n*n FP64, row-major, symmetric positive definite; device or host memory; copied, not retained
+ *   n       order, n >= 1
+ *   p       root index, p >= 1
+ *   opt     options (NULL = defaults)
+ *   stream  cudaStream_t to issue all work on (NULL = default stream)
+ * Computes ||A||_1 and ||A||_inf (Eq. 3), checks A (finite, symmetric within opt->sym_tol, positive
+ * diagonal), forms C_0 and, for the coupled form, M_0 = C_0^p A with its residual. Synchronises the stream.
+ * Errors: PR_EINVAL, PR_ENOTSPD, PR_ENOMEM, PR_ECUDA. */
+pr_status pr_init(pr_handle* h, const double* A, int64_t n, int p, const pr_options* opt, void* stream);
+
+/* Loads a new A of the same order into an existing handle without reallocating: repeats the checks,
+ * norms, C_0 and (coupled form) M_0 of pr_init and clears the iteration state and history. Counters in
+ * pr_stats keep accumulating. A: device or host memory, copied. Synchronises the stream.
+ * Errors: as pr_init, plus PR_ESTATE for a NULL handle. */
+pr_status pr_load(pr_handle h, const double* A);
+
+/* Runs at most max_steps updates of Eq. 1 at the given precision (Sec. 3: low-precision arithmetic for
+ * most iterations, precise arithmetic to refine). Before each update the residual r_k of the current
+ * iterate is tested: r_k <= tol returns PR_OK; a non-finite r_k returns PR_EDIVERGED; r_{k-1} < stag_below
+ * and r_k > stag_ratio * r_{k-1} (both computed in this call) returns PR_ESTAGNATED; an exhausted budget
+ * returns PR_EMAXITER. *steps_done (may be NULL) receives the number of updates applied in this call.
+ * Synchronises the stream once per update to read r_k. */
+pr_status pr_iterate(pr_handle h, int max_steps, int precision, double tol, int* steps_done);
+
+/* The precision ladder in one call: up to bulk_steps updates at bulk_precision (stopping early on its
+ * floor, i.e. stagnation, or on tol), then updates at final_precision until tol, stagnation or
+ * max_iter. bulk_steps = 0 skips the bulk phase. Returns the stop status of the final phase. */
+pr_status pr_solve(pr_handle h, int bulk_precision, int bulk_steps, int final_precision, double tol,
+                   int* steps_done);
+
+/* True residual ||I - C^p A||_F of the current iterate (Eq. 2 in the Frobenius norm), evaluated with
+ * products at the given precision: C^p by symmetric products, then the full product with A.
+ * Synchronises the stream. */
+pr_status pr_residual(pr_handle h, int precision, double* res_fro);
+
+/* Copies the current iterate C_k (n*n FP64, row-major) to C_out (device or host memory, caller-owned).
+ * Synchronises the stream when C_out is host memory. */
+pr_status pr_result(pr_handle h, double* C_out);
+
+/* Copies the handle's counters to *out. */
+pr_status pr_stats(pr_handle h, pr_stats_t* out);
+
+/* Copies up to cap residuals r_0 .. r_k (one per iterate, in order) to out (host memory) and the
+ * number available to *len. */
+pr_status pr_history(pr_handle h, double* out, int cap, int* len);
+
+/* Enables (on != 0) or disables CUDA-event timing of every matrix-product kernel; the summed times
+ * appear in pr_stats (gemm_ms, gemms_timed, gemm_flops_timed). Adds two event records per product. */
+pr_status pr_set_timing(pr_handle h, int on);
+
+/* Frees all device memory of the handle. h may be NULL. */
+pr_status pr_destroy(pr_handle h);
+
+/* Text describing the last failing call on h (or the last failing pr_init when h is NULL). */
+const char* pr_last_error(pr_handle h);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int pr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PTHROOT_H */

@@ -1,0 +1,542 @@
+// Host runtime behind the C ABI of include/pthroot.h: handle state, the three evaluation orders of
+// Eq. 1 (coupled, Newton-Schulz, literal), the stop rule and the precision ladder (Sec. 3).
+#include "pr_internal.h"
+
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+using pr::Epilogue;
+using pr::Mode;
+
+namespace {
+thread_local std::string g_init_error;  // text of the last failing pr_init (no handle to hold it)
+
+int precision_level(int prec) { return prec == PR_BF16 ? 1 : 2; }
+}  // namespace
+
+struct pr_handle_s {
+  int64_t n = 0;
+  int p = 1;
+  int form = PR_FORM_COUPLED;
+  pr_options opt{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+
+  // n x n FP64 buffers: the input, the iterate (X), the carried product (M) and operand (N) of the
+  // coupled form, their next values, and two scratch products.
+  double *A = nullptr, *X = nullptr, *Xn = nullptr, *M = nullptr, *Mn = nullptr, *N = nullptr, *Nn = nullptr;
+  double *T0 = nullptr, *T1 = nullptr;
+  double* partial = nullptr;  // per-tile residual partial sums
+  double* work = nullptr;     // 2n doubles (column and row abs-sums)
+  double* scal = nullptr;     // device scalars: [0..3] checks, [4..5] norms, [6] residual
+  double* hpin = nullptr;     // pinned host mirror of scal
+
+  // CUDA-event timing of the product kernels (pr_set_timing).
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;     // pairs: ev[2i] before, ev[2i + 1] after product i
+  std::vector<double> ev_flops;    // flops of pending pair i
+  int ev_pending = 0;
+
+  bool state_ready = false;   // X, (M, N) and the residual of the current iterate are formed
+  int state_level = 0;        // precision level at which the coupled M was last formed
+  std::vector<double> hist;   // r_0 .. r_k
+  std::vector<int> hist_prec; // precision each r_j was computed at
+  pr_stats_t st{};
+  std::string err;
+};
+
+namespace {
+
+pr_status fail(pr_handle h, pr_status code, const std::string& msg) {
+  if (h) {
+    h->err = msg;
+    h->st.last_stop = code;
+  } else {
+    g_init_error = msg;
+  }
+  return code;
+}
+
+pr_status cuda_fail(pr_handle h, const char* what, cudaError_t e) {
+  std::string msg = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return fail(h, e == cudaErrorMemoryAllocation ? PR_ENOMEM : PR_ECUDA, msg);
+}
+
+#define PR_CK(h, call)                                     \
+  do {                                                      \
+    cudaError_t _e = (call);                                \
+    if (_e != cudaSuccess) return cuda_fail((h), #call, _e); \
+  } while (0)
+
+double sym_flops(int64_t n) { return (double)n * (double)(n + 1) * (double)n; }
+double full_flops(int64_t n) { return 2.0 * (double)n * (double)n * (double)n; }
+
+constexpr int kEventPairs = 64;
+
+// Adds the elapsed time of every pending event pair to the stats (the stream must be synchronised).
+pr_status harvest_events(pr_handle h) {
+  for (int i = 0; i < h->ev_pending; ++i) {
+    float ms = 0.f;
+    PR_CK(h, cudaEventElapsedTime(&ms, h->ev[2 * i], h->ev[2 * i + 1]));
+    h->st.gemm_ms += ms;
+    h->st.gemms_timed += 1;
+    h->st.gemm_flops_timed += h->ev_flops[i];
+  }
+  h->ev_pending = 0;
+  return PR_OK;
+}
+
+pr_status sync(pr_handle h) {
+  PR_CK(h, cudaStreamSynchronize(h->stream));
+  return harvest_events(h);
+}
+
+// One matrix product P = X Y at the requested precision with the fused epilogue e.
+pr_status product(pr_handle h, int prec, const double* X, const double* Y, Mode mode, const Epilogue& e) {
+  const int n = (int)h->n;
+  const double flops = mode == Mode::Sym ? sym_flops(n) : full_flops(n);
+  h->st.gemms += 1;
+  h->st.gemm_flops += flops;
+  if (h->timing) {
+    if (h->ev_pending == kEventPairs) {
+      pr_status s = sync(h);
+      if (s != PR_OK) return s;
+    }
+    PR_CK(h, cudaEventRecord(h->ev[2 * h->ev_pending], h->stream));
+  }
+  switch (prec) {
+    case PR_FP64:
+      PR_CK(h, pr::gemm_f64(X, Y, n, mode, e, h->stream));
+      break;
+    default:
+      return fail(h, PR_EUNSUPPORTED, "precision not available in this build");
+  }
+  h->st.launches += 1;
+  if (h->timing) {
+    PR_CK(h, cudaEventRecord(h->ev[2 * h->ev_pending + 1], h->stream));
+    h->ev_flops[h->ev_pending] = flops;
+    h->ev_pending += 1;
+  }
+  return PR_OK;
+}
+
+int tiles_for(pr_handle h, int prec, Mode mode) {
+  (void)prec;
+  return pr::gemm_f64_tiles((int)h->n, mode);
+}
+
+// Sum of the partials of the last product -> sqrt -> host.
+pr_status read_residual(pr_handle h, int count, double* r) {
+  PR_CK(h, pr::reduce_partials_sqrt(h->partial, count, h->scal + 6, h->stream));
+  h->st.launches += 1;
+  PR_CK(h, cudaMemcpyAsync(h->hpin + 6, h->scal + 6, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  pr_status s = sync(h);
+  if (s != PR_OK) return s;
+  *r = h->hpin[6];
+  return PR_OK;
+}
+
+void push_residual(pr_handle h, double r, int prec, bool replace_last) {
+  if (replace_last && !h->hist.empty()) {
+    h->hist.back() = r;
+    h->hist_prec.back() = prec;
+  } else {
+    h->hist.push_back(r);
+    h->hist_prec.push_back(prec);
+  }
+  h->st.last_residual = r;
+}
+
+// Coupled form: M = X^p A by p symmetric products (X is a polynomial in A), the last epilogue writing
+// N = ((p+1) I - M)/p and the partials of ||I - M||_F.
+pr_status form_M_from_X(pr_handle h, int prec, bool replace_last) {
+  const int p = h->p;
+  const double* src = h->A;
+  for (int j = 1; j <= p; ++j) {
+    Epilogue e;
+    if (j < p) {
+      e.out = (j & 1) ? h->T0 : h->T1;
+    } else {
+      e.out = h->M;
+      e.out2 = h->N;
+      e.a = (double)(p + 1) / p;
+      e.b = -1.0 / p;
+      e.partial = h->partial;
+    }
+    pr_status s = product(h, prec, h->X, src, Mode::Sym, e);
+    if (s != PR_OK) return s;
+    src = e.out;
+  }
+  double r;
+  pr_status s = read_residual(h, tiles_for(h, prec, Mode::Sym), &r);
+  if (s != PR_OK) return s;
+  push_residual(h, r, prec, replace_last);
+  h->state_level = precision_level(prec);
+  return PR_OK;
+}
+
+// X_{k+1} = X_k N_k; M_{k+1} = N_k^p M_k (p symmetric products); N_{k+1} and r_{k+1} fused.
+pr_status coupled_update(pr_handle h, int prec) {
+  const int p = h->p;
+  Epilogue ex;
+  ex.out = h->Xn;
+  pr_status s = product(h, prec, h->X, h->N, Mode::Sym, ex);
+  if (s != PR_OK) return s;
+  const double* src = h->M;
+  for (int j = 1; j <= p; ++j) {
+    Epilogue e;
+    if (j < p) {
+      e.out = (j & 1) ? h->T0 : h->T1;
+    } else {
+      e.out = h->Mn;
+      e.out2 = h->Nn;
+      e.a = (double)(p + 1) / p;
+      e.b = -1.0 / p;
+      e.partial = h->partial;
+    }
+    s = product(h, prec, h->N, src, Mode::Sym, e);
+    if (s != PR_OK) return s;
+    src = e.out;
+  }
+  double r;
+  s = read_residual(h, tiles_for(h, prec, Mode::Sym), &r);
+  if (s != PR_OK) return s;
+  std::swap(h->X, h->Xn);
+  std::swap(h->M, h->Mn);
+  std::swap(h->N, h->Nn);
+  push_residual(h, r, prec, false);
+  return PR_OK;
+}
+
+// Newton-Schulz (p = 1): T = A X (full product, residual ||I - T||_F of the current X).
+pr_status ns_residual(pr_handle h, int prec, double* r) {
+  Epilogue e;
+  e.out = h->T0;
+  e.partial = h->partial;
+  pr_status s = product(h, prec, h->A, h->X, Mode::Full, e);
+  if (s != PR_OK) return s;
+  return read_residual(h, tiles_for(h, prec, Mode::Full), r);
+}
+
+// X' = 2X - X T with T = A X from ns_residual; X T = X A X is symmetric for every symmetric X.
+pr_status ns_update(pr_handle h, int prec) {
+  Epilogue e;
+  e.out2 = h->Xn;
+  e.b = -1.0;
+  e.c = 2.0;
+  e.cin = h->X;
+  pr_status s = product(h, prec, h->X, h->T0, Mode::Sym, e);
+  if (s != PR_OK) return s;
+  std::swap(h->X, h->Xn);
+  return PR_OK;
+}
+
+// Literal Eq. 1: T_j = C T_{j-1}, T_0 = A (full products); the residual from T_p = C^p A.
+pr_status literal_residual(pr_handle h, int prec, double* r) {
+  const double* src = h->A;
+  for (int j = 1; j <= h->p; ++j) {
+    Epilogue e;
+    e.out = (j & 1) ? h->T0 : h->T1;
+    if (j == h->p) e.partial = h->partial;
+    pr_status s = product(h, prec, h->X, src, Mode::Full, e);
+    if (s != PR_OK) return s;
+    src = e.out;
+  }
+  return read_residual(h, tiles_for(h, prec, Mode::Full), r);
+}
+
+// C' = sym(((p+1) C - C T_p) / p).
+pr_status literal_update(pr_handle h, int prec) {
+  const double* Tp = (h->p & 1) ? h->T0 : h->T1;
+  Epilogue e;
+  e.out2 = h->Mn;
+  e.b = -1.0 / h->p;
+  e.c = (double)(h->p + 1) / h->p;
+  e.cin = h->X;
+  pr_status s = product(h, prec, h->X, Tp, Mode::Full, e);
+  if (s != PR_OK) return s;
+  PR_CK(h, pr::symmetrize(h->Mn, (int)h->n, h->Xn, h->stream));
+  h->st.launches += 1;
+  std::swap(h->X, h->Xn);
+  return PR_OK;
+}
+
+// The stop rule: returns a pr_status to stop with, or -1 to apply one more update.
+int decide(pr_handle h, double tol, int steps_this_call, int max_steps) {
+  const size_t m = h->hist.size();
+  const double r = h->hist[m - 1];
+  if (!isfinite(r)) return PR_EDIVERGED;
+  if (r <= tol) return PR_OK;
+  if (m >= 2 && h->hist_prec[m - 2] == h->hist_prec[m - 1] && h->hist[m - 2] < h->opt.stag_below &&
+      r > h->opt.stag_ratio * h->hist[m - 2])
+    return PR_ESTAGNATED;
+  if (h->st.iterations >= h->opt.max_iter || steps_this_call >= max_steps) return PR_EMAXITER;
+  return -1;
+}
+
+bool precision_known(int prec) { return prec == PR_FP64 || prec == PR_EMU64 || prec == PR_BF16; }
+
+pr_status ensure_state(pr_handle h, int prec) {
+  if (h->form != PR_FORM_COUPLED) return PR_OK;
+  if (!h->state_ready) {
+    pr_status s = form_M_from_X(h, prec, false);
+    if (s != PR_OK) return s;
+    h->state_ready = true;
+  } else if (h->opt.reanchor && precision_level(prec) > h->state_level) {
+    pr_status s = form_M_from_X(h, prec, true);
+    if (s != PR_OK) return s;
+  }
+  return PR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pr_version(void) { return 100; }
+
+void pr_default_options(pr_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->form = PR_FORM_AUTO;
+  o->c0 = PR_C0_EQ3;
+  o->max_iter = 100;
+  o->stag_below = 1e-3;
+  o->stag_ratio = 0.5;
+  o->sym_tol = 1e-12;
+  o->reanchor = 1;
+  o->emu_slices = 0;
+}
+
+const char* pr_last_error(pr_handle h) { return h ? h->err.c_str() : g_init_error.c_str(); }
+
+pr_status pr_destroy(pr_handle h) {
+  if (!h) return PR_OK;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  double* bufs[] = {h->A, h->X, h->Xn, h->M, h->Mn, h->N, h->Nn, h->T0, h->T1, h->partial, h->work, h->scal};
+  for (double* b : bufs)
+    if (b) cudaFree(b);
+  if (h->hpin) cudaFreeHost(h->hpin);
+  for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+  delete h;
+  return PR_OK;
+}
+
+pr_status pr_init(pr_handle* out, const double* A, int64_t n, int p, const pr_options* opt, void* stream) {
+  if (!out) return fail(nullptr, PR_EINVAL, "pr_init: h is NULL");
+  *out = nullptr;
+  if (!A) return fail(nullptr, PR_EINVAL, "pr_init: A is NULL");
+  if (n < 1 || n > (int64_t)1 << 17) return fail(nullptr, PR_EINVAL, "pr_init: n must be in [1, 131072]");
+  if (p < 1 || p > 64) return fail(nullptr, PR_EINVAL, "pr_init: p must be in [1, 64]");
+  pr_options o;
+  if (opt) o = *opt; else pr_default_options(&o);
+  if (o.form < PR_FORM_AUTO || o.form > PR_FORM_LITERAL) return fail(nullptr, PR_EINVAL, "pr_init: unknown form");
+  if (o.c0 != PR_C0_EQ3 && o.c0 != PR_C0_SCALED_I) return fail(nullptr, PR_EINVAL, "pr_init: unknown c0 kind");
+  if (o.form == PR_FORM_NS && p != 1) return fail(nullptr, PR_EINVAL, "pr_init: the Newton-Schulz form needs p = 1");
+  if (o.max_iter < 0 || !(o.stag_ratio > 0) || !(o.sym_tol >= 0)) return fail(nullptr, PR_EINVAL, "pr_init: bad option value");
+
+  pr_handle h = new pr_handle_s();
+  h->n = n;
+  h->p = p;
+  h->opt = o;
+  h->form = o.form == PR_FORM_AUTO ? (p == 1 ? PR_FORM_NS : PR_FORM_COUPLED) : o.form;
+  h->stream = (cudaStream_t)stream;
+  h->st.n = n;
+  h->st.p = p;
+  h->st.form = h->form;
+  h->st.c0 = o.c0;
+  h->st.switch_iteration = -1;
+  h->st.last_precision = -1;
+  cudaGetDevice(&h->device);
+
+  auto bail = [&](pr_status code) {
+    g_init_error = h->err;
+    pr_destroy(h);
+    return code;
+  };
+#define PR_INIT_CK(call)                                             \
+  do {                                                               \
+    cudaError_t _e = (call);                                         \
+    if (_e != cudaSuccess) return bail(cuda_fail(h, #call, _e));     \
+  } while (0)
+
+  const size_t bytes = (size_t)n * (size_t)n * sizeof(double);
+  double** mats[] = {&h->A, &h->X, &h->Xn, &h->M, &h->Mn, &h->N, &h->Nn, &h->T0, &h->T1};
+  for (double** m : mats) PR_INIT_CK(cudaMalloc((void**)m, bytes));
+  const int T64 = (int)((n + 63) / 64);
+  PR_INIT_CK(cudaMalloc((void**)&h->partial, sizeof(double) * (size_t)T64 * T64));
+  PR_INIT_CK(cudaMalloc((void**)&h->work, sizeof(double) * 2 * (size_t)n));
+  PR_INIT_CK(cudaMalloc((void**)&h->scal, sizeof(double) * 8));
+  PR_INIT_CK(cudaMallocHost((void**)&h->hpin, sizeof(double) * 8));
+  pr_status s = pr_load(h, A);
+  if (s != PR_OK) return bail(s);
+#undef PR_INIT_CK
+  *out = h;
+  return PR_OK;
+}
+
+pr_status pr_load(pr_handle h, const double* A) {
+  if (!h) return fail(nullptr, PR_ESTATE, "pr_load: NULL handle");
+  if (!A) return fail(h, PR_EINVAL, "pr_load: A is NULL");
+  cudaSetDevice(h->device);
+  const int n = (int)h->n;
+  const size_t bytes = (size_t)n * (size_t)n * sizeof(double);
+  h->state_ready = false;
+  h->state_level = 0;
+  h->hist.clear();
+  h->hist_prec.clear();
+  h->st.iterations = 0;
+  for (int& c : h->st.iterations_by_precision) c = 0;
+  h->st.switch_iteration = -1;
+  h->st.last_precision = -1;
+  h->st.last_residual = 0.0;
+  PR_CK(h, cudaMemcpyAsync(h->A, A, bytes, cudaMemcpyDefault, h->stream));
+  PR_CK(h, pr::validate(h->A, n, h->scal, h->stream));
+  PR_CK(h, pr::abs_norms(h->A, n, h->work, h->scal + 4, h->stream));
+  h->st.launches += 4;
+  PR_CK(h, cudaMemcpyAsync(h->hpin, h->scal, 6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  pr_status s = sync(h);
+  if (s != PR_OK) return s;
+  const double amax = h->hpin[0], asym = h->hpin[1], nonfinite = h->hpin[2], nonpos = h->hpin[3];
+  if (nonfinite > 0) return fail(h, PR_EINVAL, "pr_load: A has non-finite entries");
+  if (asym > h->opt.sym_tol * amax) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "pr_load: A is not symmetric (max|a_ij - a_ji| = %.3e > %.1e * max|a_ij|)", asym,
+             h->opt.sym_tol);
+    return fail(h, PR_EINVAL, buf);
+  }
+  if (nonpos > 0) return fail(h, PR_ENOTSPD, "pr_load: A has a non-positive diagonal entry");
+  h->st.norm_1 = h->hpin[4];
+  h->st.norm_inf = h->hpin[5];
+  // C_0 (Eq. 3, or the scaled identity).
+  if (h->opt.c0 == PR_C0_EQ3) {
+    PR_CK(h, pr::init_c0_eq3(h->A, n, 1.0 / (h->st.norm_1 * h->st.norm_inf), h->X, h->stream));
+  } else {
+    PR_CK(h, pr::set_scaled_identity(h->X, n, pow(h->st.norm_1, -1.0 / h->p), h->stream));
+  }
+  h->st.launches += 1;
+  return sync(h);
+}
+
+pr_status pr_set_timing(pr_handle h, int on) {
+  if (!h) return fail(nullptr, PR_ESTATE, "pr_set_timing: NULL handle");
+  cudaSetDevice(h->device);
+  if (on && h->ev.empty()) {
+    h->ev.resize(2 * kEventPairs);
+    h->ev_flops.resize(kEventPairs);
+    for (cudaEvent_t& e : h->ev) PR_CK(h, cudaEventCreate(&e));
+  }
+  if (!on) {
+    pr_status s = sync(h);
+    if (s != PR_OK) return s;
+  }
+  h->timing = on != 0;
+  return PR_OK;
+}
+
+pr_status pr_iterate(pr_handle h, int max_steps, int precision, double tol, int* steps_done) {
+  if (steps_done) *steps_done = 0;
+  if (!h) return fail(nullptr, PR_ESTATE, "pr_iterate: NULL handle");
+  if (max_steps < 0 || !(tol >= 0)) return fail(h, PR_EINVAL, "pr_iterate: max_steps < 0 or tol < 0 / NaN");
+  if (!precision_known(precision)) return fail(h, PR_EINVAL, "pr_iterate: unknown precision");
+  cudaSetDevice(h->device);
+  pr_status s = ensure_state(h, precision);
+  if (s != PR_OK) return s;
+
+  int steps = 0;
+  int stop = -1;
+  while (true) {
+    if (h->form == PR_FORM_NS || h->form == PR_FORM_LITERAL) {
+      double r;
+      s = h->form == PR_FORM_NS ? ns_residual(h, precision, &r) : literal_residual(h, precision, &r);
+      if (s != PR_OK) return s;
+      // A repeated call re-evaluates the same iterate: replace its residual instead of appending.
+      const bool same_iterate = !h->hist.empty() && (int)h->hist.size() == h->st.iterations + 1;
+      push_residual(h, r, precision, same_iterate);
+    }
+    stop = decide(h, tol, steps, max_steps);
+    if (stop >= 0) break;
+    if (h->st.last_precision >= 0 && h->st.last_precision != precision) h->st.switch_iteration = h->st.iterations;
+    if (h->form == PR_FORM_COUPLED) s = coupled_update(h, precision);
+    else if (h->form == PR_FORM_NS) s = ns_update(h, precision);
+    else s = literal_update(h, precision);
+    if (s != PR_OK) return s;
+    h->st.iterations += 1;
+    h->st.iterations_by_precision[precision] += 1;
+    h->st.last_precision = precision;
+    ++steps;
+  }
+  if (steps_done) *steps_done = steps;
+  h->st.last_stop = stop;
+  if (stop == PR_EDIVERGED) h->err = "pr_iterate: the residual is not finite";
+  return (pr_status)stop;
+}
+
+pr_status pr_solve(pr_handle h, int bulk_precision, int bulk_steps, int final_precision, double tol, int* steps_done) {
+  if (steps_done) *steps_done = 0;
+  if (!h) return fail(nullptr, PR_ESTATE, "pr_solve: NULL handle");
+  int d1 = 0, d2 = 0;
+  if (bulk_steps > 0) {
+    pr_status s = pr_iterate(h, bulk_steps, bulk_precision, tol, &d1);
+    if (steps_done) *steps_done = d1;
+    if (s != PR_ESTAGNATED && s != PR_EMAXITER) return s;
+  }
+  pr_status s = pr_iterate(h, 1 << 30, final_precision, tol, &d2);
+  if (steps_done) *steps_done = d1 + d2;
+  return s;
+}
+
+pr_status pr_residual(pr_handle h, int precision, double* res_fro) {
+  if (!h) return fail(nullptr, PR_ESTATE, "pr_residual: NULL handle");
+  if (!res_fro) return fail(h, PR_EINVAL, "pr_residual: res_fro is NULL");
+  if (!precision_known(precision)) return fail(h, PR_EINVAL, "pr_residual: unknown precision");
+  cudaSetDevice(h->device);
+  // C^p by symmetric products (powers of a symmetric matrix are symmetric), then the full product with A.
+  const double* P = h->X;
+  for (int j = 2; j <= h->p; ++j) {
+    Epilogue e;
+    e.out = (j & 1) ? h->T1 : h->T0;
+    pr_status s = product(h, precision, h->X, P, Mode::Sym, e);
+    if (s != PR_OK) return s;
+    P = e.out;
+  }
+  Epilogue e;
+  e.partial = h->partial;
+  pr_status s = product(h, precision, P, h->A, Mode::Full, e);
+  if (s != PR_OK) return s;
+  return read_residual(h, tiles_for(h, precision, Mode::Full), res_fro);
+}
+
+pr_status pr_result(pr_handle h, double* C_out) {
+  if (!h) return fail(nullptr, PR_ESTATE, "pr_result: NULL handle");
+  if (!C_out) return fail(h, PR_EINVAL, "pr_result: C_out is NULL");
+  cudaSetDevice(h->device);
+  const size_t bytes = (size_t)h->n * (size_t)h->n * sizeof(double);
+  PR_CK(h, cudaMemcpyAsync(C_out, h->X, bytes, cudaMemcpyDefault, h->stream));
+  return sync(h);
+}
+
+pr_status pr_stats(pr_handle h, pr_stats_t* out) {
+  if (!h) return fail(nullptr, PR_ESTATE, "pr_stats: NULL handle");
+  if (!out) return fail(h, PR_EINVAL, "pr_stats: out is NULL");
+  *out = h->st;
+  return PR_OK;
+}
+
+pr_status pr_history(pr_handle h, double* out, int cap, int* len) {
+  if (!h) return fail(nullptr, PR_ESTATE, "pr_history: NULL handle");
+  if (len) *len = (int)h->hist.size();
+  if (out && cap > 0) {
+    const int m = cap < (int)h->hist.size() ? cap : (int)h->hist.size();
+    for (int i = 0; i < m; ++i) out[i] = h->hist[i];
+  }
+  return PR_OK;
+}
+
+}  // extern "C"

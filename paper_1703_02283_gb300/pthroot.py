@@ -1,0 +1,182 @@
+"""Thin ctypes binding of the C ABI in include/pthroot.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and adds nothing to it. Matrix
+arguments may be torch tensors (device or host; their ``data_ptr()`` is passed), numpy arrays (host)
+or raw integer addresses. All compute happens in the library's CUDA kernels; if the shared library
+is missing, importing this module raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libpthroot.so")
+
+# enums (values fixed by include/pthroot.h)
+PR_OK, PR_EINVAL, PR_ENOTSPD, PR_ENOMEM, PR_ECUDA, PR_EDIVERGED, PR_ESTAGNATED = 0, 1, 2, 3, 4, 5, 6
+PR_EMAXITER, PR_ETIMEOUT, PR_EGATE, PR_ESTATE, PR_EUNSUPPORTED = 7, 8, 9, 10, 11
+STATUS_NAMES = {0: "PR_OK", 1: "PR_EINVAL", 2: "PR_ENOTSPD", 3: "PR_ENOMEM", 4: "PR_ECUDA",
+                5: "PR_EDIVERGED", 6: "PR_ESTAGNATED", 7: "PR_EMAXITER", 8: "PR_ETIMEOUT",
+                9: "PR_EGATE", 10: "PR_ESTATE", 11: "PR_EUNSUPPORTED"}
+PR_FP64, PR_EMU64, PR_BF16 = 0, 1, 3
+PR_FORM_AUTO, PR_FORM_COUPLED, PR_FORM_NS, PR_FORM_LITERAL = 0, 1, 2, 3
+PR_C0_EQ3, PR_C0_SCALED_I = 0, 1
+
+
+class pr_options(ctypes.Structure):
+    _fields_ = [("form", ctypes.c_int), ("c0", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("stag_below", ctypes.c_double), ("stag_ratio", ctypes.c_double),
+                ("sym_tol", ctypes.c_double), ("reanchor", ctypes.c_int), ("emu_slices", ctypes.c_int)]
+
+
+class pr_stats_t(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("p", ctypes.c_int), ("form", ctypes.c_int), ("c0", ctypes.c_int),
+                ("iterations", ctypes.c_int), ("iterations_by_precision", ctypes.c_int * 4),
+                ("switch_iteration", ctypes.c_int), ("last_precision", ctypes.c_int),
+                ("last_stop", ctypes.c_int), ("norm_1", ctypes.c_double), ("norm_inf", ctypes.c_double),
+                ("last_residual", ctypes.c_double), ("gemms", ctypes.c_int64), ("gemm_flops", ctypes.c_double),
+                ("launches", ctypes.c_int64), ("gemms_timed", ctypes.c_int64), ("gemm_ms", ctypes.c_double),
+                ("gemm_flops_timed", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["iterations_by_precision"] = list(self.iterations_by_precision)
+        return d
+
+
+_handle_t = ctypes.c_void_p
+_dptr = ctypes.c_void_p
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1703_02283_gb300.build` "
+                          "(the CUDA library is required; there is no fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "pr_version": (ctypes.c_int, []),
+        "pr_default_options": (None, [ctypes.POINTER(pr_options)]),
+        "pr_init": (ctypes.c_int, [ctypes.POINTER(_handle_t), _dptr, ctypes.c_int64, ctypes.c_int,
+                                   ctypes.POINTER(pr_options), ctypes.c_void_p]),
+        "pr_load": (ctypes.c_int, [_handle_t, _dptr]),
+        "pr_set_timing": (ctypes.c_int, [_handle_t, ctypes.c_int]),
+        "pr_iterate": (ctypes.c_int, [_handle_t, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                      ctypes.POINTER(ctypes.c_int)]),
+        "pr_solve": (ctypes.c_int, [_handle_t, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                    ctypes.POINTER(ctypes.c_int)]),
+        "pr_residual": (ctypes.c_int, [_handle_t, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+        "pr_result": (ctypes.c_int, [_handle_t, _dptr]),
+        "pr_stats": (ctypes.c_int, [_handle_t, ctypes.POINTER(pr_stats_t)]),
+        "pr_history": (ctypes.c_int, [_handle_t, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_int)]),
+        "pr_destroy": (ctypes.c_int, [_handle_t]),
+        "pr_last_error": (ctypes.c_char_p, [_handle_t]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+class PthrootError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def _ptr(x) -> int:
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):  # torch.Tensor
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):  # numpy.ndarray
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x).__name__}")
+
+
+def _check(status: int, h=None, allowed=(PR_OK,)) -> int:
+    if status not in allowed:
+        raise PthrootError(status, (_lib.pr_last_error(h) or b"").decode())
+    return status
+
+
+def pr_version() -> int:
+    return _lib.pr_version()
+
+
+def pr_default_options() -> pr_options:
+    o = pr_options()
+    _lib.pr_default_options(ctypes.byref(o))
+    return o
+
+
+def pr_init(A, n: int, p: int, options: pr_options | None = None, stream: int = 0) -> int:
+    """Returns the handle; raises PthrootError on a non-zero status."""
+    h = _handle_t()
+    st = _lib.pr_init(ctypes.byref(h), _ptr(A), int(n), int(p),
+                      ctypes.byref(options) if options is not None else None, ctypes.c_void_p(stream))
+    _check(st, None)
+    return h.value
+
+
+def pr_load(h: int, A) -> None:
+    _check(_lib.pr_load(h, _ptr(A)), h)
+
+
+def pr_set_timing(h: int, on: bool) -> None:
+    _check(_lib.pr_set_timing(h, 1 if on else 0), h)
+
+
+STOPS = (PR_OK, PR_ESTAGNATED, PR_EMAXITER)
+
+
+def pr_iterate(h: int, max_steps: int, precision: int, tol: float) -> tuple[int, int]:
+    """Returns (status, steps_done); stop statuses (PR_OK, PR_ESTAGNATED, PR_EMAXITER) do not raise."""
+    d = ctypes.c_int(0)
+    st = _lib.pr_iterate(h, int(max_steps), int(precision), float(tol), ctypes.byref(d))
+    _check(st, h, STOPS)
+    return st, d.value
+
+
+def pr_solve(h: int, bulk_precision: int, bulk_steps: int, final_precision: int, tol: float) -> tuple[int, int]:
+    d = ctypes.c_int(0)
+    st = _lib.pr_solve(h, int(bulk_precision), int(bulk_steps), int(final_precision), float(tol), ctypes.byref(d))
+    _check(st, h, STOPS)
+    return st, d.value
+
+
+def pr_residual(h: int, precision: int = PR_FP64) -> float:
+    r = ctypes.c_double(0.0)
+    _check(_lib.pr_residual(h, int(precision), ctypes.byref(r)), h)
+    return r.value
+
+
+def pr_result(h: int, C_out) -> None:
+    _check(_lib.pr_result(h, _ptr(C_out)), h)
+
+
+def pr_stats(h: int) -> dict:
+    s = pr_stats_t()
+    _check(_lib.pr_stats(h, ctypes.byref(s)), h)
+    return s.as_dict()
+
+
+def pr_history(h: int) -> list[float]:
+    ln = ctypes.c_int(0)
+    _check(_lib.pr_history(h, None, 0, ctypes.byref(ln)), h)
+    buf = (ctypes.c_double * max(ln.value, 1))()
+    _check(_lib.pr_history(h, buf, ln.value, ctypes.byref(ln)), h)
+    return list(buf[: ln.value])
+
+
+def pr_destroy(h: int) -> None:
+    _check(_lib.pr_destroy(h), None)
+
+
+def pr_last_error(h: int | None = None) -> str:
+    return (_lib.pr_last_error(h) or b"").decode()

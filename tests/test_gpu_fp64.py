@@ -1,0 +1,176 @@
+"""Parity of the native FP64 GPU path with the CPU oracle, through the C ABI.
+
+Bar: the GPU iterate's relative Frobenius distance to the oracle's iterate, and to the exact root, is at
+most max(1e-12, 10 x the oracle's own forward error); the iteration counts agree within one step; the
+residual histories agree (rtol 1e-8) while they are well above the FP64 floor.
+"""
+import numpy as np
+import pytest
+
+from oracle import pthroot_oracle as O
+from paper_1703_02283_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1703_02283_gb300 import pthroot as P  # noqa: E402
+
+DEV = torch.device("cuda:0")
+FORMS = {"auto": P.PR_FORM_AUTO, "coupled": P.PR_FORM_COUPLED, "ns": P.PR_FORM_NS, "literal": P.PR_FORM_LITERAL}
+C0S = {"eq3": P.PR_C0_EQ3, "scaled_identity": P.PR_C0_SCALED_I}
+
+
+def gpu_solve(A_np, p, form="auto", c0="eq3", tol=1e-12, max_iter=100, precision=P.PR_FP64, host=False,
+              stag_below=1e-3):
+    n = A_np.shape[0]
+    o = P.pr_default_options()
+    o.form = FORMS[form]
+    o.c0 = C0S[c0]
+    o.max_iter = max_iter
+    o.stag_below = stag_below
+    stream = torch.cuda.current_stream(DEV).cuda_stream
+    if host:
+        A = np.ascontiguousarray(A_np)
+        h = P.pr_init(A, n, p, o, stream)
+    else:
+        A = torch.from_numpy(A_np).to(DEV)
+        h = P.pr_init(A, n, p, o, stream)
+    try:
+        st, steps = P.pr_iterate(h, max_iter, precision, tol)
+        if host:
+            C = np.empty((n, n))
+            P.pr_result(h, C)
+        else:
+            Ct = torch.empty((n, n), dtype=torch.float64, device=DEV)
+            P.pr_result(h, Ct)
+            C = Ct.cpu().numpy()
+        return C, st, steps, P.pr_history(h), P.pr_stats(h), h
+    except Exception:
+        P.pr_destroy(h)
+        raise
+
+
+def check_parity(case, p, form="auto", c0="eq3", tol=1e-12, **kw):
+    Co, info = O.solve(case.A, p, form=None if form == "auto" else form, c0=c0, tol=tol)
+    C, st, steps, hist, stats, h = gpu_solve(case.A, p, form, c0, tol, **kw)
+    P.pr_destroy(h)
+    Z = O.closed_form_root(case.Q, case.lam, p)
+    bound = max(1e-12, 10 * O.forward_error(Co, Z))
+    assert np.array_equal(C, C.T)
+    assert O.forward_error(C, Co) <= bound, (O.forward_error(C, Co), bound)
+    assert O.forward_error(C, Z) <= bound
+    assert abs(steps - info.iterations) <= 1, (steps, info.iterations, info.stop)
+    floor = O.residual_fro(Z, case.A, p)
+    ho, hg = np.asarray(info.residuals), np.asarray(hist)
+    m = min(len(ho), len(hg))
+    mask = ho[:m] > 1e3 * floor
+    np.testing.assert_allclose(hg[:m][mask], ho[:m][mask], rtol=1e-8)
+    return C, Co, steps, stats
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_small_case_recipe(p):
+    # n = 256, kappa = 1e2 (the recipe the oracle finishes in seconds), Eq. 3 start.
+    case = W.spd_from_spectrum(256, 1e-2, 0)
+    check_parity(case, p)
+
+
+@pytest.mark.parametrize("n", [1, 7, 63, 64, 65, 130, 200])
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_ragged_sizes(n, p):
+    case = W.spd_from_spectrum(n, 0.05, 100 + n)
+    check_parity(case, p, c0="scaled_identity")
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_literal_form_well_conditioned(p):
+    case = W.spd_from_spectrum(96, 0.3, 3)
+    check_parity(case, p, form="literal")
+
+
+def test_coupled_form_p1():
+    case = W.spd_from_spectrum(128, 0.05, 4)
+    check_parity(case, 1, form="coupled")
+
+
+def test_host_buffers():
+    case = W.spd_from_spectrum(150, 0.05, 6)
+    Cd, *_rest, h = gpu_solve(case.A, 2)
+    P.pr_destroy(h)
+    Ch, *_rest, h = gpu_solve(case.A, 2, host=True)
+    P.pr_destroy(h)
+    assert np.array_equal(Cd, Ch)
+
+
+def test_deterministic():
+    case = W.spd_from_spectrum(200, 0.01, 7)
+    a, *_r, h = gpu_solve(case.A, 3)
+    P.pr_destroy(h)
+    b, *_r, h = gpu_solve(case.A, 3)
+    P.pr_destroy(h)
+    assert np.array_equal(a, b)
+
+
+def test_true_residual_matches_definition():
+    case = W.spd_from_spectrum(180, 0.02, 8)
+    for p in (1, 2, 3):
+        C, st, steps, hist, stats, h = gpu_solve(case.A, p)
+        try:
+            r = P.pr_residual(h, P.PR_FP64)
+        finally:
+            P.pr_destroy(h)
+        want = O.residual_fro(C, case.A, p)
+        assert abs(r - want) <= 1e-3 * want + 1e-14, (p, r, want)
+
+
+def test_stop_reasons():
+    case = W.spd_from_spectrum(128, 0.01, 9)
+    C, st, steps, hist, stats, h = gpu_solve(case.A, 1, tol=0.0)
+    P.pr_destroy(h)
+    assert st == P.PR_ESTAGNATED and hist[-2] < 1e-3
+    C, st, steps, hist, stats, h = gpu_solve(case.A, 2, tol=0.0, max_iter=5)
+    P.pr_destroy(h)
+    assert st == P.PR_EMAXITER and steps == 5 and len(hist) == 6 and stats["iterations"] == 5
+
+
+def test_resume_and_stats():
+    case = W.spd_from_spectrum(128, 0.01, 10)
+    o = P.pr_default_options()
+    A = torch.from_numpy(case.A).to(DEV)
+    h = P.pr_init(A, 128, 2, o, torch.cuda.current_stream(DEV).cuda_stream)
+    try:
+        st1, d1 = P.pr_iterate(h, 7, P.PR_FP64, 1e-12)
+        st2, d2 = P.pr_iterate(h, 100, P.PR_FP64, 1e-12)
+        s = P.pr_stats(h)
+    finally:
+        P.pr_destroy(h)
+    Co, info = O.solve(case.A, 2, tol=1e-12)
+    assert st1 == P.PR_EMAXITER and d1 == 7
+    assert st2 == P.PR_OK and abs(d1 + d2 - info.iterations) <= 1
+    assert s["iterations"] == d1 + d2 and s["iterations_by_precision"][P.PR_FP64] == d1 + d2
+    assert s["norm_1"] == pytest.approx(O.norm_1(case.A), rel=1e-14)
+    assert s["norm_inf"] == pytest.approx(O.norm_inf(case.A), rel=1e-14)
+    assert s["gemms"] == 2 + 3 * s["iterations"]
+
+
+def test_input_errors():
+    stream = torch.cuda.current_stream(DEV).cuda_stream
+    case = W.spd_from_spectrum(40, 0.1, 11)
+    A = case.A.copy()
+    A[3, 5] += 1e-3
+    with pytest.raises(P.PthrootError) as e:
+        P.pr_init(torch.from_numpy(A).to(DEV), 40, 2, None, stream)
+    assert e.value.status == P.PR_EINVAL and "symmetric" in str(e.value)
+    A = case.A.copy()
+    A[2, 2] = np.nan
+    with pytest.raises(P.PthrootError) as e:
+        P.pr_init(torch.from_numpy(A).to(DEV), 40, 2, None, stream)
+    assert e.value.status == P.PR_EINVAL
+    A = case.A.copy()
+    A[4, 4] = -1.0
+    with pytest.raises(P.PthrootError) as e:
+        P.pr_init(torch.from_numpy(A).to(DEV), 40, 2, None, stream)
+    assert e.value.status == P.PR_ENOTSPD
