@@ -162,6 +162,14 @@ pr_status pr_stats(pr_handle h, pr_stats_t* out);
  * number available to *len. */
 pr_status pr_history(pr_handle h, double* out, int cap, int* len);
 
+/* One matrix product of the iteration on its own, for testing and timing the product kernels:
+ * P = X Y for symmetric n x n FP64 X and Y (device or host memory) that commute, so that X Y is symmetric.
+ * sym != 0 computes only the upper-triangle tiles and mirrors them (the iteration's symmetric products);
+ * sym == 0 computes every tile. precision PR_FP64 uses FP64 DMMA; PR_BF16 rounds X and Y to BF16 and
+ * accumulates in FP32 on the tcgen05 tensor cores. P: n*n FP64 output (device or host), caller-owned.
+ * Allocates and frees temporary device buffers. Synchronises the stream. */
+pr_status pr_matmul(int precision, const double* X, const double* Y, int64_t n, int sym, double* P, void* stream);
+
 /* Enables (on != 0) or disables CUDA-event timing of every matrix-product kernel; the summed times
  * appear in pr_stats (gemm_ms, gemms_timed, gemm_flops_timed). Adds two event records per product. */
 pr_status pr_set_timing(pr_handle h, int on);

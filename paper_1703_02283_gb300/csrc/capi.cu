@@ -1,5 +1,6 @@
 // Host runtime behind the C ABI of include/pthroot.h: handle state, the three evaluation orders of
-// Eq. 1 (coupled, Newton-Schulz, literal), the stop rule and the precision ladder (Sec. 3).
+// Eq. 1 (coupled, Newton-Schulz, literal), the stop rule and the precision ladder (Sec. 3: low-precision
+// arithmetic for most iterations, then precise refinement).
 #include "pr_internal.h"
 
 #include <math.h>
@@ -16,7 +17,32 @@ using pr::Mode;
 namespace {
 thread_local std::string g_init_error;  // text of the last failing pr_init (no handle to hold it)
 
+// Precision levels: a switch to a higher level re-forms the coupled product M at that level.
 int precision_level(int prec) { return prec == PR_BF16 ? 1 : 2; }
+
+// One matrix in the two representations the products use: FP64 (leading dimension n) and BF16
+// (leading dimension ldl, the operand of the tensor-core products).
+struct Mat {
+  double* f = nullptr;
+  __nv_bfloat16* b = nullptr;
+};
+
+void swap(Mat& a, Mat& b) {
+  std::swap(a.f, b.f);
+  std::swap(a.b, b.b);
+}
+
+// What one product writes; product() maps it onto the kernel epilogue of the chosen precision.
+struct Out {
+  Mat* out = nullptr;        // P
+  bool out_master = true;    // low precision: also keep the FP64 copy of P
+  Mat* out2 = nullptr;       // a I + b P + c cin
+  bool out2_master = true;
+  const double* cin = nullptr;
+  double a = 0.0, b = 0.0, c = 0.0;
+  bool partial = false;      // per-tile sums of the residual ||I - P||_F^2
+  bool transpose = false;    // full-mode products whose result is the B operand of a later product
+};
 }  // namespace
 
 struct pr_handle_s {
@@ -26,28 +52,31 @@ struct pr_handle_s {
   pr_options opt{};
   cudaStream_t stream = nullptr;
   int device = 0;
+  int ldl = 0;  // leading dimension of the BF16 copies
 
-  // n x n FP64 buffers: the input, the iterate (X), the carried product (M) and operand (N) of the
-  // coupled form, their next values, and two scratch products.
-  double *A = nullptr, *X = nullptr, *Xn = nullptr, *M = nullptr, *Mn = nullptr, *N = nullptr, *Nn = nullptr;
-  double *T0 = nullptr, *T1 = nullptr;
+  // The input, the iterate X, the carried product M and operand N of the coupled form, their next
+  // values, and two scratch products.
+  Mat A, X, Xn, M, Mn, N, Nn, T0, T1;
+  bool lp_stale = true;       // BF16 copies of A, X, M, N are out of date
   double* partial = nullptr;  // per-tile residual partial sums
   double* work = nullptr;     // 2n doubles (column and row abs-sums)
-  double* scal = nullptr;     // device scalars: [0..3] checks, [4..5] norms, [6] residual
+  double* scal = nullptr;     // device scalars: [0..3] checks, [4..5] norms, [6] residual, [7] error word
   double* hpin = nullptr;     // pinned host mirror of scal
 
   // CUDA-event timing of the product kernels (pr_set_timing).
   bool timing = false;
-  std::vector<cudaEvent_t> ev;     // pairs: ev[2i] before, ev[2i + 1] after product i
-  std::vector<double> ev_flops;    // flops of pending pair i
+  std::vector<cudaEvent_t> ev;  // pairs: ev[2i] before, ev[2i + 1] after product i
+  std::vector<double> ev_flops;
   int ev_pending = 0;
 
-  bool state_ready = false;   // X, (M, N) and the residual of the current iterate are formed
-  int state_level = 0;        // precision level at which the coupled M was last formed
-  std::vector<double> hist;   // r_0 .. r_k
-  std::vector<int> hist_prec; // precision each r_j was computed at
+  bool state_ready = false;  // (coupled) M, N and the residual of the current iterate are formed
+  int state_level = 0;       // precision level at which M was last formed
+  std::vector<double> hist;  // r_0 .. r_k
+  std::vector<int> hist_prec;
   pr_stats_t st{};
   std::string err;
+
+  int* err_word() { return reinterpret_cast<int*>(scal + 7); }
 };
 
 namespace {
@@ -67,9 +96,9 @@ pr_status cuda_fail(pr_handle h, const char* what, cudaError_t e) {
   return fail(h, e == cudaErrorMemoryAllocation ? PR_ENOMEM : PR_ECUDA, msg);
 }
 
-#define PR_CK(h, call)                                     \
-  do {                                                      \
-    cudaError_t _e = (call);                                \
+#define PR_CK(h, call)                                      \
+  do {                                                       \
+    cudaError_t _e = (call);                                 \
     if (_e != cudaSuccess) return cuda_fail((h), #call, _e); \
   } while (0)
 
@@ -78,7 +107,6 @@ double full_flops(int64_t n) { return 2.0 * (double)n * (double)n * (double)n; }
 
 constexpr int kEventPairs = 64;
 
-// Adds the elapsed time of every pending event pair to the stats (the stream must be synchronised).
 pr_status harvest_events(pr_handle h) {
   for (int i = 0; i < h->ev_pending; ++i) {
     float ms = 0.f;
@@ -91,15 +119,48 @@ pr_status harvest_events(pr_handle h) {
   return PR_OK;
 }
 
+// Synchronises the stream, collects event timings and checks the device error word.
 pr_status sync(pr_handle h) {
   PR_CK(h, cudaStreamSynchronize(h->stream));
-  return harvest_events(h);
+  pr_status s = harvest_events(h);
+  if (s != PR_OK) return s;
+  int word = 0;
+  PR_CK(h, cudaMemcpy(&word, h->err_word(), sizeof(int), cudaMemcpyDeviceToHost));
+  if (word != 0) {
+    char buf[128];
+    snprintf(buf, sizeof buf, "a bounded device wait expired (code %d); the product was abandoned", word);
+    PR_CK(h, cudaMemset(h->err_word(), 0, sizeof(int)));
+    return fail(h, PR_ETIMEOUT, buf);
+  }
+  return PR_OK;
 }
 
-// One matrix product P = X Y at the requested precision with the fused epilogue e.
-pr_status product(pr_handle h, int prec, const double* X, const double* Y, Mode mode, const Epilogue& e) {
+bool lowp(int prec) { return prec == PR_BF16; }
+
+// One matrix product P = X Y (X, Y symmetric, or Y given transposed in its BF16 copy) at the requested
+// precision, with the fused epilogue described by o.
+pr_status product(pr_handle h, int prec, const Mat& X, const Mat& Y, Mode mode, const Out& o) {
   const int n = (int)h->n;
   const double flops = mode == Mode::Sym ? sym_flops(n) : full_flops(n);
+  Epilogue e;
+  e.cin = o.cin;
+  e.a = o.a;
+  e.b = o.b;
+  e.c = o.c;
+  e.partial = o.partial ? h->partial : nullptr;
+  if (lowp(prec)) {
+    if (o.out) {
+      e.out_lp = o.out->b;
+      if (o.out_master) e.out = o.out->f;
+    }
+    if (o.out2) {
+      e.out2_lp = o.out2->b;
+      if (o.out2_master) e.out2 = o.out2->f;
+    }
+  } else {
+    if (o.out) e.out = o.out->f;
+    if (o.out2) e.out2 = o.out2->f;
+  }
   h->st.gemms += 1;
   h->st.gemm_flops += flops;
   if (h->timing) {
@@ -111,7 +172,11 @@ pr_status product(pr_handle h, int prec, const double* X, const double* Y, Mode 
   }
   switch (prec) {
     case PR_FP64:
-      PR_CK(h, pr::gemm_f64(X, Y, n, mode, e, h->stream));
+      PR_CK(h, pr::gemm_f64(X.f, Y.f, n, mode, e, h->stream));
+      h->lp_stale = true;
+      break;
+    case PR_BF16:
+      PR_CK(h, pr::gemm_bf16_tc(X.b, Y.b, n, h->ldl, mode, o.transpose, e, h->err_word(), h->stream));
       break;
     default:
       return fail(h, PR_EUNSUPPORTED, "precision not available in this build");
@@ -126,8 +191,19 @@ pr_status product(pr_handle h, int prec, const double* X, const double* Y, Mode 
 }
 
 int tiles_for(pr_handle h, int prec, Mode mode) {
-  (void)prec;
-  return pr::gemm_f64_tiles((int)h->n, mode);
+  return lowp(prec) ? pr::gemm_tc_tiles((int)h->n, mode) : pr::gemm_f64_tiles((int)h->n, mode);
+}
+
+// Brings the BF16 copies of the state up to date before low-precision products.
+pr_status refresh_lowp(pr_handle h) {
+  if (!h->lp_stale) return PR_OK;
+  const int n = (int)h->n;
+  for (Mat* m : {&h->A, &h->X, &h->M, &h->N}) {
+    PR_CK(h, pr::to_bf16(m->f, n, h->ldl, m->b, h->stream));
+    h->st.launches += 1;
+  }
+  h->lp_stale = false;
+  return PR_OK;
 }
 
 // Sum of the partials of the last product -> sqrt -> host.
@@ -156,21 +232,22 @@ void push_residual(pr_handle h, double r, int prec, bool replace_last) {
 // N = ((p+1) I - M)/p and the partials of ||I - M||_F.
 pr_status form_M_from_X(pr_handle h, int prec, bool replace_last) {
   const int p = h->p;
-  const double* src = h->A;
+  const Mat* src = &h->A;
   for (int j = 1; j <= p; ++j) {
-    Epilogue e;
+    Out o;
     if (j < p) {
-      e.out = (j & 1) ? h->T0 : h->T1;
+      o.out = (j & 1) ? &h->T0 : &h->T1;
+      o.out_master = false;
     } else {
-      e.out = h->M;
-      e.out2 = h->N;
-      e.a = (double)(p + 1) / p;
-      e.b = -1.0 / p;
-      e.partial = h->partial;
+      o.out = &h->M;
+      o.out2 = &h->N;
+      o.a = (double)(p + 1) / p;
+      o.b = -1.0 / p;
+      o.partial = true;
     }
-    pr_status s = product(h, prec, h->X, src, Mode::Sym, e);
+    pr_status s = product(h, prec, h->X, *src, Mode::Sym, o);
     if (s != PR_OK) return s;
-    src = e.out;
+    src = o.out;
   }
   double r;
   pr_status s = read_residual(h, tiles_for(h, prec, Mode::Sym), &r);
@@ -183,86 +260,90 @@ pr_status form_M_from_X(pr_handle h, int prec, bool replace_last) {
 // X_{k+1} = X_k N_k; M_{k+1} = N_k^p M_k (p symmetric products); N_{k+1} and r_{k+1} fused.
 pr_status coupled_update(pr_handle h, int prec) {
   const int p = h->p;
-  Epilogue ex;
-  ex.out = h->Xn;
-  pr_status s = product(h, prec, h->X, h->N, Mode::Sym, ex);
+  Out ox;
+  ox.out = &h->Xn;
+  pr_status s = product(h, prec, h->X, h->N, Mode::Sym, ox);
   if (s != PR_OK) return s;
-  const double* src = h->M;
+  const Mat* src = &h->M;
   for (int j = 1; j <= p; ++j) {
-    Epilogue e;
+    Out o;
     if (j < p) {
-      e.out = (j & 1) ? h->T0 : h->T1;
+      o.out = (j & 1) ? &h->T0 : &h->T1;
+      o.out_master = false;
     } else {
-      e.out = h->Mn;
-      e.out2 = h->Nn;
-      e.a = (double)(p + 1) / p;
-      e.b = -1.0 / p;
-      e.partial = h->partial;
+      o.out = &h->Mn;
+      o.out2 = &h->Nn;
+      o.a = (double)(p + 1) / p;
+      o.b = -1.0 / p;
+      o.partial = true;
     }
-    s = product(h, prec, h->N, src, Mode::Sym, e);
+    s = product(h, prec, h->N, *src, Mode::Sym, o);
     if (s != PR_OK) return s;
-    src = e.out;
+    src = o.out;
   }
   double r;
   s = read_residual(h, tiles_for(h, prec, Mode::Sym), &r);
   if (s != PR_OK) return s;
-  std::swap(h->X, h->Xn);
-  std::swap(h->M, h->Mn);
-  std::swap(h->N, h->Nn);
+  swap(h->X, h->Xn);
+  swap(h->M, h->Mn);
+  swap(h->N, h->Nn);
   push_residual(h, r, prec, false);
   return PR_OK;
 }
 
-// Newton-Schulz (p = 1): T = A X (full product, residual ||I - T||_F of the current X).
+// Newton-Schulz (p = 1): T = A X (full product; its BF16 copy is stored transposed so that it can be
+// the K-major B operand of X T), residual ||I - T||_F of the current X.
 pr_status ns_residual(pr_handle h, int prec, double* r) {
-  Epilogue e;
-  e.out = h->T0;
-  e.partial = h->partial;
-  pr_status s = product(h, prec, h->A, h->X, Mode::Full, e);
+  Out o;
+  o.out = &h->T0;
+  o.out_master = false;
+  o.partial = true;
+  o.transpose = true;
+  pr_status s = product(h, prec, h->A, h->X, Mode::Full, o);
   if (s != PR_OK) return s;
   return read_residual(h, tiles_for(h, prec, Mode::Full), r);
 }
 
 // X' = 2X - X T with T = A X from ns_residual; X T = X A X is symmetric for every symmetric X.
 pr_status ns_update(pr_handle h, int prec) {
-  Epilogue e;
-  e.out2 = h->Xn;
-  e.b = -1.0;
-  e.c = 2.0;
-  e.cin = h->X;
-  pr_status s = product(h, prec, h->X, h->T0, Mode::Sym, e);
+  Out o;
+  o.out2 = &h->Xn;
+  o.b = -1.0;
+  o.c = 2.0;
+  o.cin = h->X.f;
+  pr_status s = product(h, prec, h->X, h->T0, Mode::Sym, o);
   if (s != PR_OK) return s;
-  std::swap(h->X, h->Xn);
+  swap(h->X, h->Xn);
   return PR_OK;
 }
 
-// Literal Eq. 1: T_j = C T_{j-1}, T_0 = A (full products); the residual from T_p = C^p A.
+// Literal Eq. 1 (FP64 only): T_j = C T_{j-1}, T_0 = A (full products); the residual from T_p = C^p A.
 pr_status literal_residual(pr_handle h, int prec, double* r) {
-  const double* src = h->A;
+  const Mat* src = &h->A;
   for (int j = 1; j <= h->p; ++j) {
-    Epilogue e;
-    e.out = (j & 1) ? h->T0 : h->T1;
-    if (j == h->p) e.partial = h->partial;
-    pr_status s = product(h, prec, h->X, src, Mode::Full, e);
+    Out o;
+    o.out = (j & 1) ? &h->T0 : &h->T1;
+    o.partial = j == h->p;
+    pr_status s = product(h, prec, h->X, *src, Mode::Full, o);
     if (s != PR_OK) return s;
-    src = e.out;
+    src = o.out;
   }
   return read_residual(h, tiles_for(h, prec, Mode::Full), r);
 }
 
 // C' = sym(((p+1) C - C T_p) / p).
 pr_status literal_update(pr_handle h, int prec) {
-  const double* Tp = (h->p & 1) ? h->T0 : h->T1;
-  Epilogue e;
-  e.out2 = h->Mn;
-  e.b = -1.0 / h->p;
-  e.c = (double)(h->p + 1) / h->p;
-  e.cin = h->X;
-  pr_status s = product(h, prec, h->X, Tp, Mode::Full, e);
+  const Mat& Tp = (h->p & 1) ? h->T0 : h->T1;
+  Out o;
+  o.out2 = &h->Mn;
+  o.b = -1.0 / h->p;
+  o.c = (double)(h->p + 1) / h->p;
+  o.cin = h->X.f;
+  pr_status s = product(h, prec, h->X, Tp, Mode::Full, o);
   if (s != PR_OK) return s;
-  PR_CK(h, pr::symmetrize(h->Mn, (int)h->n, h->Xn, h->stream));
+  PR_CK(h, pr::symmetrize(h->Mn.f, (int)h->n, h->Xn.f, h->stream));
   h->st.launches += 1;
-  std::swap(h->X, h->Xn);
+  swap(h->X, h->Xn);
   return PR_OK;
 }
 
@@ -281,7 +362,19 @@ int decide(pr_handle h, double tol, int steps_this_call, int max_steps) {
 
 bool precision_known(int prec) { return prec == PR_FP64 || prec == PR_EMU64 || prec == PR_BF16; }
 
+pr_status check_precision(pr_handle h, int prec) {
+  if (!precision_known(prec)) return fail(h, PR_EINVAL, "unknown precision");
+  if (prec == PR_EMU64) return fail(h, PR_EUNSUPPORTED, "PR_EMU64 is not available in this build");
+  if (h->form == PR_FORM_LITERAL && prec != PR_FP64)
+    return fail(h, PR_EUNSUPPORTED, "the literal form runs in PR_FP64 only");
+  return PR_OK;
+}
+
 pr_status ensure_state(pr_handle h, int prec) {
+  if (lowp(prec)) {
+    pr_status s = refresh_lowp(h);
+    if (s != PR_OK) return s;
+  }
   if (h->form != PR_FORM_COUPLED) return PR_OK;
   if (!h->state_ready) {
     pr_status s = form_M_from_X(h, prec, false);
@@ -319,8 +412,11 @@ pr_status pr_destroy(pr_handle h) {
   if (!h) return PR_OK;
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
-  double* bufs[] = {h->A, h->X, h->Xn, h->M, h->Mn, h->N, h->Nn, h->T0, h->T1, h->partial, h->work, h->scal};
-  for (double* b : bufs)
+  for (Mat* m : {&h->A, &h->X, &h->Xn, &h->M, &h->Mn, &h->N, &h->Nn, &h->T0, &h->T1}) {
+    if (m->f) cudaFree(m->f);
+    if (m->b) cudaFree(m->b);
+  }
+  for (double* b : {h->partial, h->work, h->scal})
     if (b) cudaFree(b);
   if (h->hpin) cudaFreeHost(h->hpin);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
@@ -335,11 +431,13 @@ pr_status pr_init(pr_handle* out, const double* A, int64_t n, int p, const pr_op
   if (n < 1 || n > (int64_t)1 << 17) return fail(nullptr, PR_EINVAL, "pr_init: n must be in [1, 131072]");
   if (p < 1 || p > 64) return fail(nullptr, PR_EINVAL, "pr_init: p must be in [1, 64]");
   pr_options o;
-  if (opt) o = *opt; else pr_default_options(&o);
+  if (opt) o = *opt;
+  else pr_default_options(&o);
   if (o.form < PR_FORM_AUTO || o.form > PR_FORM_LITERAL) return fail(nullptr, PR_EINVAL, "pr_init: unknown form");
   if (o.c0 != PR_C0_EQ3 && o.c0 != PR_C0_SCALED_I) return fail(nullptr, PR_EINVAL, "pr_init: unknown c0 kind");
   if (o.form == PR_FORM_NS && p != 1) return fail(nullptr, PR_EINVAL, "pr_init: the Newton-Schulz form needs p = 1");
-  if (o.max_iter < 0 || !(o.stag_ratio > 0) || !(o.sym_tol >= 0)) return fail(nullptr, PR_EINVAL, "pr_init: bad option value");
+  if (o.max_iter < 0 || !(o.stag_ratio > 0) || !(o.sym_tol >= 0))
+    return fail(nullptr, PR_EINVAL, "pr_init: bad option value");
 
   pr_handle h = new pr_handle_s();
   h->n = n;
@@ -347,6 +445,7 @@ pr_status pr_init(pr_handle* out, const double* A, int64_t n, int p, const pr_op
   h->opt = o;
   h->form = o.form == PR_FORM_AUTO ? (p == 1 ? PR_FORM_NS : PR_FORM_COUPLED) : o.form;
   h->stream = (cudaStream_t)stream;
+  h->ldl = pr::bf16_ld((int)n);
   h->st.n = n;
   h->st.p = p;
   h->st.form = h->form;
@@ -360,23 +459,27 @@ pr_status pr_init(pr_handle* out, const double* A, int64_t n, int p, const pr_op
     pr_destroy(h);
     return code;
   };
-#define PR_INIT_CK(call)                                             \
-  do {                                                               \
-    cudaError_t _e = (call);                                         \
-    if (_e != cudaSuccess) return bail(cuda_fail(h, #call, _e));     \
+#define PR_INIT_CK(call)                                         \
+  do {                                                           \
+    cudaError_t _e = (call);                                     \
+    if (_e != cudaSuccess) return bail(cuda_fail(h, #call, _e)); \
   } while (0)
 
   const size_t bytes = (size_t)n * (size_t)n * sizeof(double);
-  double** mats[] = {&h->A, &h->X, &h->Xn, &h->M, &h->Mn, &h->N, &h->Nn, &h->T0, &h->T1};
-  for (double** m : mats) PR_INIT_CK(cudaMalloc((void**)m, bytes));
+  const size_t lbytes = (size_t)n * (size_t)h->ldl * sizeof(__nv_bfloat16);
+  for (Mat* m : {&h->A, &h->X, &h->Xn, &h->M, &h->Mn, &h->N, &h->Nn, &h->T0, &h->T1}) {
+    PR_INIT_CK(cudaMalloc((void**)&m->f, bytes));
+    PR_INIT_CK(cudaMalloc((void**)&m->b, lbytes));
+  }
   const int T64 = (int)((n + 63) / 64);
   PR_INIT_CK(cudaMalloc((void**)&h->partial, sizeof(double) * (size_t)T64 * T64));
   PR_INIT_CK(cudaMalloc((void**)&h->work, sizeof(double) * 2 * (size_t)n));
   PR_INIT_CK(cudaMalloc((void**)&h->scal, sizeof(double) * 8));
+  PR_INIT_CK(cudaMemset(h->scal, 0, sizeof(double) * 8));
   PR_INIT_CK(cudaMallocHost((void**)&h->hpin, sizeof(double) * 8));
+#undef PR_INIT_CK
   pr_status s = pr_load(h, A);
   if (s != PR_OK) return bail(s);
-#undef PR_INIT_CK
   *out = h;
   return PR_OK;
 }
@@ -389,6 +492,7 @@ pr_status pr_load(pr_handle h, const double* A) {
   const size_t bytes = (size_t)n * (size_t)n * sizeof(double);
   h->state_ready = false;
   h->state_level = 0;
+  h->lp_stale = true;
   h->hist.clear();
   h->hist_prec.clear();
   h->st.iterations = 0;
@@ -396,9 +500,9 @@ pr_status pr_load(pr_handle h, const double* A) {
   h->st.switch_iteration = -1;
   h->st.last_precision = -1;
   h->st.last_residual = 0.0;
-  PR_CK(h, cudaMemcpyAsync(h->A, A, bytes, cudaMemcpyDefault, h->stream));
-  PR_CK(h, pr::validate(h->A, n, h->scal, h->stream));
-  PR_CK(h, pr::abs_norms(h->A, n, h->work, h->scal + 4, h->stream));
+  PR_CK(h, cudaMemcpyAsync(h->A.f, A, bytes, cudaMemcpyDefault, h->stream));
+  PR_CK(h, pr::validate(h->A.f, n, h->scal, h->stream));
+  PR_CK(h, pr::abs_norms(h->A.f, n, h->work, h->scal + 4, h->stream));
   h->st.launches += 4;
   PR_CK(h, cudaMemcpyAsync(h->hpin, h->scal, 6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   pr_status s = sync(h);
@@ -416,9 +520,9 @@ pr_status pr_load(pr_handle h, const double* A) {
   h->st.norm_inf = h->hpin[5];
   // C_0 (Eq. 3, or the scaled identity).
   if (h->opt.c0 == PR_C0_EQ3) {
-    PR_CK(h, pr::init_c0_eq3(h->A, n, 1.0 / (h->st.norm_1 * h->st.norm_inf), h->X, h->stream));
+    PR_CK(h, pr::init_c0_eq3(h->A.f, n, 1.0 / (h->st.norm_1 * h->st.norm_inf), h->X.f, h->stream));
   } else {
-    PR_CK(h, pr::set_scaled_identity(h->X, n, pow(h->st.norm_1, -1.0 / h->p), h->stream));
+    PR_CK(h, pr::set_scaled_identity(h->X.f, n, pow(h->st.norm_1, -1.0 / h->p), h->stream));
   }
   h->st.launches += 1;
   return sync(h);
@@ -444,9 +548,10 @@ pr_status pr_iterate(pr_handle h, int max_steps, int precision, double tol, int*
   if (steps_done) *steps_done = 0;
   if (!h) return fail(nullptr, PR_ESTATE, "pr_iterate: NULL handle");
   if (max_steps < 0 || !(tol >= 0)) return fail(h, PR_EINVAL, "pr_iterate: max_steps < 0 or tol < 0 / NaN");
-  if (!precision_known(precision)) return fail(h, PR_EINVAL, "pr_iterate: unknown precision");
+  pr_status s = check_precision(h, precision);
+  if (s != PR_OK) return s;
   cudaSetDevice(h->device);
-  pr_status s = ensure_state(h, precision);
+  s = ensure_state(h, precision);
   if (s != PR_OK) return s;
 
   int steps = 0;
@@ -495,20 +600,26 @@ pr_status pr_solve(pr_handle h, int bulk_precision, int bulk_steps, int final_pr
 pr_status pr_residual(pr_handle h, int precision, double* res_fro) {
   if (!h) return fail(nullptr, PR_ESTATE, "pr_residual: NULL handle");
   if (!res_fro) return fail(h, PR_EINVAL, "pr_residual: res_fro is NULL");
-  if (!precision_known(precision)) return fail(h, PR_EINVAL, "pr_residual: unknown precision");
+  if (!precision_known(precision) || precision == PR_EMU64)
+    return fail(h, precision_known(precision) ? PR_EUNSUPPORTED : PR_EINVAL, "pr_residual: precision not available");
   cudaSetDevice(h->device);
-  // C^p by symmetric products (powers of a symmetric matrix are symmetric), then the full product with A.
-  const double* P = h->X;
-  for (int j = 2; j <= h->p; ++j) {
-    Epilogue e;
-    e.out = (j & 1) ? h->T1 : h->T0;
-    pr_status s = product(h, precision, h->X, P, Mode::Sym, e);
+  if (lowp(precision)) {
+    pr_status s = refresh_lowp(h);
     if (s != PR_OK) return s;
-    P = e.out;
   }
-  Epilogue e;
-  e.partial = h->partial;
-  pr_status s = product(h, precision, P, h->A, Mode::Full, e);
+  // C^p by symmetric products (powers of a symmetric matrix are symmetric), then the full product with A.
+  const Mat* P = &h->X;
+  for (int j = 2; j <= h->p; ++j) {
+    Out o;
+    o.out = (j & 1) ? &h->T1 : &h->T0;
+    o.out_master = false;
+    pr_status s = product(h, precision, h->X, *P, Mode::Sym, o);
+    if (s != PR_OK) return s;
+    P = o.out;
+  }
+  Out o;
+  o.partial = true;
+  pr_status s = product(h, precision, *P, h->A, Mode::Full, o);
   if (s != PR_OK) return s;
   return read_residual(h, tiles_for(h, precision, Mode::Full), res_fro);
 }
@@ -518,8 +629,58 @@ pr_status pr_result(pr_handle h, double* C_out) {
   if (!C_out) return fail(h, PR_EINVAL, "pr_result: C_out is NULL");
   cudaSetDevice(h->device);
   const size_t bytes = (size_t)h->n * (size_t)h->n * sizeof(double);
-  PR_CK(h, cudaMemcpyAsync(C_out, h->X, bytes, cudaMemcpyDefault, h->stream));
+  PR_CK(h, cudaMemcpyAsync(C_out, h->X.f, bytes, cudaMemcpyDefault, h->stream));
   return sync(h);
+}
+
+pr_status pr_matmul(int precision, const double* X, const double* Y, int64_t n, int sym, double* P, void* stream) {
+  if (!X || !Y || !P) return fail(nullptr, PR_EINVAL, "pr_matmul: NULL matrix");
+  if (n < 1 || n > (int64_t)1 << 17) return fail(nullptr, PR_EINVAL, "pr_matmul: n must be in [1, 131072]");
+  if (precision != PR_FP64 && precision != PR_BF16)
+    return fail(nullptr, PR_EUNSUPPORTED, "pr_matmul: precision not available");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int ni = (int)n, ldl = pr::bf16_ld(ni);
+  const size_t bytes = (size_t)n * (size_t)n * sizeof(double);
+  const size_t lbytes = (size_t)n * (size_t)ldl * sizeof(__nv_bfloat16);
+  const Mode mode = sym ? Mode::Sym : Mode::Full;
+  double *dX = nullptr, *dY = nullptr, *dP = nullptr;
+  __nv_bfloat16 *bX = nullptr, *bY = nullptr;
+  int* err = nullptr;
+  cudaError_t e = cudaSuccess;
+  int word = 0;
+  auto step = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+  };
+  step(cudaMalloc((void**)&dX, bytes));
+  step(cudaMalloc((void**)&dY, bytes));
+  step(cudaMalloc((void**)&dP, bytes));
+  step(cudaMalloc((void**)&err, sizeof(int)));
+  if (precision == PR_BF16) {
+    step(cudaMalloc((void**)&bX, lbytes));
+    step(cudaMalloc((void**)&bY, lbytes));
+  }
+  if (e == cudaSuccess) {
+    step(cudaMemsetAsync(err, 0, sizeof(int), s));
+    step(cudaMemcpyAsync(dX, X, bytes, cudaMemcpyDefault, s));
+    step(cudaMemcpyAsync(dY, Y, bytes, cudaMemcpyDefault, s));
+    Epilogue ep;
+    ep.out = dP;
+    if (precision == PR_FP64) {
+      step(pr::gemm_f64(dX, dY, ni, mode, ep, s));
+    } else {
+      step(pr::to_bf16(dX, ni, ldl, bX, s));
+      step(pr::to_bf16(dY, ni, ldl, bY, s));
+      step(pr::gemm_bf16_tc(bX, bY, ni, ldl, mode, false, ep, err, s));
+    }
+    step(cudaMemcpyAsync(P, dP, bytes, cudaMemcpyDefault, s));
+    step(cudaMemcpyAsync(&word, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    step(cudaStreamSynchronize(s));
+  }
+  for (void* q : {(void*)dX, (void*)dY, (void*)dP, (void*)bX, (void*)bY, (void*)err})
+    if (q) cudaFree(q);
+  if (e != cudaSuccess) return cuda_fail(nullptr, "pr_matmul", e);
+  if (word != 0) return fail(nullptr, PR_ETIMEOUT, "pr_matmul: a bounded device wait expired");
+  return PR_OK;
 }
 
 pr_status pr_stats(pr_handle h, pr_stats_t* out) {

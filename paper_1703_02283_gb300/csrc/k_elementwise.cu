@@ -150,9 +150,10 @@ __global__ void k_reduce_sqrt(const double* __restrict__ partial, int count, dou
   if (threadIdx.x == 0) *result = sqrt(sh[0]);
 }
 
-__global__ void k_to_bf16(const double* __restrict__ src, int64_t count, __nv_bfloat16* __restrict__ dst) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
-    dst[e] = __double2bfloat16(src[e]);
+__global__ void k_to_bf16(const double* __restrict__ src, int n, int ldl, __nv_bfloat16* __restrict__ dst) {
+  const int64_t total = (int64_t)n * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    dst[(e / n) * ldl + (e % n)] = __double2bfloat16(src[e]);
 }
 
 int grid_for(int64_t total) {
@@ -207,8 +208,8 @@ cudaError_t reduce_partials_sqrt(const double* partial, int count, double* resul
   return cudaGetLastError();
 }
 
-cudaError_t to_bf16(const double* src, int64_t count, __nv_bfloat16* dst, cudaStream_t s) {
-  k_to_bf16<<<grid_for(count), kThreads, 0, s>>>(src, count, dst);
+cudaError_t to_bf16(const double* src, int n, int ldl, __nv_bfloat16* dst, cudaStream_t s) {
+  k_to_bf16<<<grid_for((int64_t)n * n), kThreads, 0, s>>>(src, n, ldl, dst);
   return cudaGetLastError();
 }
 

@@ -33,6 +33,14 @@ enum class Mode { Sym, Full };
 int gemm_f64_tiles(int n, Mode mode);
 cudaError_t gemm_f64(const double* X, const double* Y, int n, Mode mode, const Epilogue& e, cudaStream_t s);
 
+// ---- BF16 tensor-core products (k_gemm_tc.cu): P = X Y^T for BF16 X, Y (n x n, leading dimension ldl,
+// a multiple of 8, 16-byte aligned), FP32 accumulation; transpose (full mode only) stores P^T.
+// err: device word set to a non-zero code if a bounded wait expired.
+int gemm_tc_tiles(int n, Mode mode);
+int bf16_ld(int n);
+cudaError_t gemm_bf16_tc(const __nv_bfloat16* X, const __nv_bfloat16* Y, int n, int ldl, Mode mode, bool transpose,
+                         const Epilogue& e, int* err, cudaStream_t s);
+
 // ---- elementwise and reductions (k_elementwise.cu)
 // scal[0] = max |a_ij|, scal[1] = max |a_ij - a_ji|, scal[2] = #non-finite, scal[3] = #non-positive diagonal
 cudaError_t validate(const double* A, int n, double* scal4, cudaStream_t s);
@@ -48,7 +56,7 @@ cudaError_t axpby_identity(const double* in, int n, double a, double b, double* 
 cudaError_t symmetrize(const double* in, int n, double* out, cudaStream_t s);
 // *result = sqrt(sum of partial[0..count)) in a fixed order
 cudaError_t reduce_partials_sqrt(const double* partial, int count, double* result, cudaStream_t s);
-// dst = bf16(src)
-cudaError_t to_bf16(const double* src, int64_t count, __nv_bfloat16* dst, cudaStream_t s);
+// dst[i * ldl + j] = bf16(src[i * n + j]) for an n x n matrix
+cudaError_t to_bf16(const double* src, int n, int ldl, __nv_bfloat16* dst, cudaStream_t s);
 
 }  // namespace pr

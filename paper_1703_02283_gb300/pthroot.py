@@ -67,6 +67,8 @@ def _load() -> ctypes.CDLL:
                                     ctypes.POINTER(ctypes.c_int)]),
         "pr_residual": (ctypes.c_int, [_handle_t, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
         "pr_result": (ctypes.c_int, [_handle_t, _dptr]),
+        "pr_matmul": (ctypes.c_int, [ctypes.c_int, _dptr, _dptr, ctypes.c_int64, ctypes.c_int, _dptr,
+                                     ctypes.c_void_p]),
         "pr_stats": (ctypes.c_int, [_handle_t, ctypes.POINTER(pr_stats_t)]),
         "pr_history": (ctypes.c_int, [_handle_t, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                       ctypes.POINTER(ctypes.c_int)]),
@@ -158,6 +160,11 @@ def pr_residual(h: int, precision: int = PR_FP64) -> float:
 
 def pr_result(h: int, C_out) -> None:
     _check(_lib.pr_result(h, _ptr(C_out)), h)
+
+
+def pr_matmul(precision: int, X, Y, n: int, sym: bool, P, stream: int = 0) -> None:
+    _check(_lib.pr_matmul(int(precision), _ptr(X), _ptr(Y), int(n), 1 if sym else 0, _ptr(P),
+                          ctypes.c_void_p(stream)), None)
 
 
 def pr_stats(h: int) -> dict:

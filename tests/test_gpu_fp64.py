@@ -67,7 +67,13 @@ def check_parity(case, p, form="auto", c0="eq3", tol=1e-12, **kw):
     ho, hg = np.asarray(info.residuals), np.asarray(hist)
     m = min(len(ho), len(hg))
     mask = ho[:m] > 1e3 * floor
-    np.testing.assert_allclose(hg[:m][mask], ho[:m][mask], rtol=1e-8)
+    # Two FP64 runs of the iteration differ by roundoff amplified by the spread of M_0 = C_0^p A: its
+    # eigenvalues lam^{p+1}/s^p span kappa^{p+1} from Eq. 3's guess and kappa from the scaled identity.
+    # The residual evaluations themselves differ by roundoff of the order of the FP64 floor.
+    kappa = case.lam.max() / case.lam.min()
+    spread = kappa ** (p + 1) if c0 == "eq3" else kappa
+    rtol = max(1e-8, 10 * 2.2e-16 * spread)
+    np.testing.assert_allclose(hg[:m][mask], ho[:m][mask], rtol=rtol, atol=10 * floor)
     return C, Co, steps, stats
 
 
