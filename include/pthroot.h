@@ -86,6 +86,8 @@ typedef struct {
   double sym_tol;      /* pr_init rejects A with max|a_ij - a_ji| > sym_tol * max|a_ij|, default 1e-12   */
   int reanchor;        /* coupled form: on a switch to higher precision recompute M = X^p A, default 1  */
   int emu_slices;      /* PR_EMU64 slice count per operand (0 = chosen from n), default 0               */
+  double stag_below_lowp; /* stag_below for low-precision (PR_BF16) residuals, whose floor is higher,
+                             default 0.5 (below 0.5 every eigencomponent is in the quadratic phase)      */
 } pr_options;
 
 /* Counters of one handle. */
@@ -139,6 +141,17 @@ pr_status pr_load(pr_handle h, const double* A);
  * returns PR_EMAXITER. *steps_done (may be NULL) receives the number of updates applied in this call.
  * Synchronises the stream once per update to read r_k. */
 pr_status pr_iterate(pr_handle h, int max_steps, int precision, double tol, int* steps_done);
+
+/* The stop rule pr_iterate applies to the residual history, as a pure host function (no device work).
+ * hist[0..len) are residuals r_0 .. r_k (r_k of the current iterate), prec[0..len) the pr_precision each
+ * was computed at; opt NULL = defaults. Returns PR_EDIVERGED if r_k is not finite, PR_OK if r_k <= tol,
+ * PR_ESTAGNATED if r_{k-1} and r_k were computed at the same precision and either
+ *   (a) r_{k-1} < arm and r_k > stag_ratio * r_{k-1}, arm = stag_below (PR_FP64, PR_EMU64) or
+ *       stag_below_lowp (PR_BF16), or
+ *   (b) PR_BF16 only: r_k >= r_{k-1} after some residual of the current run of that precision fell below
+ *       half of the run's first residual (a low-precision floor above stag_below_lowp),
+ * and -1 otherwise (continue). The step budget and max_iter are checked by pr_iterate itself. */
+int pr_stop_rule(const double* hist, const int* prec, int len, double tol, const pr_options* opt);
 
 /* The precision ladder in one call: up to bulk_steps updates at bulk_precision (stopping early on its
  * floor, i.e. stagnation, or on tol), then updates at final_precision until tol, stagnation or

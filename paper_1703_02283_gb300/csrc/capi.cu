@@ -347,15 +347,29 @@ pr_status literal_update(pr_handle h, int prec) {
   return PR_OK;
 }
 
-// The stop rule: returns a pr_status to stop with, or -1 to apply one more update.
-int decide(pr_handle h, double tol, int steps_this_call, int max_steps) {
-  const size_t m = h->hist.size();
-  const double r = h->hist[m - 1];
+// The stop rule (see pr_stop_rule): returns a pr_status to stop with, or -1 to apply one more update.
+int stop_rule(const double* hist, const int* prec, int len, double tol, const pr_options& o) {
+  const double r = hist[len - 1];
   if (!isfinite(r)) return PR_EDIVERGED;
   if (r <= tol) return PR_OK;
-  if (m >= 2 && h->hist_prec[m - 2] == h->hist_prec[m - 1] && h->hist[m - 2] < h->opt.stag_below &&
-      r > h->opt.stag_ratio * h->hist[m - 2])
-    return PR_ESTAGNATED;
+  if (len >= 2 && prec[len - 2] == prec[len - 1]) {
+    const double q = hist[len - 2];
+    const bool low = lowp(prec[len - 1]);
+    const double arm = low ? o.stag_below_lowp : o.stag_below;
+    if (q < arm && r > o.stag_ratio * q) return PR_ESTAGNATED;
+    if (low && r >= q) {
+      int first = len - 1;
+      while (first > 0 && prec[first - 1] == prec[len - 1]) --first;
+      for (int i = first + 1; i < len - 1; ++i)
+        if (hist[i] < 0.5 * hist[first]) return PR_ESTAGNATED;
+    }
+  }
+  return -1;
+}
+
+int decide(pr_handle h, double tol, int steps_this_call, int max_steps) {
+  const int stop = stop_rule(h->hist.data(), h->hist_prec.data(), (int)h->hist.size(), tol, h->opt);
+  if (stop >= 0) return stop;
   if (h->st.iterations >= h->opt.max_iter || steps_this_call >= max_steps) return PR_EMAXITER;
   return -1;
 }
@@ -404,6 +418,7 @@ void pr_default_options(pr_options* o) {
   o->sym_tol = 1e-12;
   o->reanchor = 1;
   o->emu_slices = 0;
+  o->stag_below_lowp = 0.5;
 }
 
 const char* pr_last_error(pr_handle h) { return h ? h->err.c_str() : g_init_error.c_str(); }
@@ -436,7 +451,7 @@ pr_status pr_init(pr_handle* out, const double* A, int64_t n, int p, const pr_op
   if (o.form < PR_FORM_AUTO || o.form > PR_FORM_LITERAL) return fail(nullptr, PR_EINVAL, "pr_init: unknown form");
   if (o.c0 != PR_C0_EQ3 && o.c0 != PR_C0_SCALED_I) return fail(nullptr, PR_EINVAL, "pr_init: unknown c0 kind");
   if (o.form == PR_FORM_NS && p != 1) return fail(nullptr, PR_EINVAL, "pr_init: the Newton-Schulz form needs p = 1");
-  if (o.max_iter < 0 || !(o.stag_ratio > 0) || !(o.sym_tol >= 0))
+  if (o.max_iter < 0 || !(o.stag_ratio > 0) || !(o.sym_tol >= 0) || !(o.stag_below_lowp >= 0))
     return fail(nullptr, PR_EINVAL, "pr_init: bad option value");
 
   pr_handle h = new pr_handle_s();
@@ -581,6 +596,14 @@ pr_status pr_iterate(pr_handle h, int max_steps, int precision, double tol, int*
   h->st.last_stop = stop;
   if (stop == PR_EDIVERGED) h->err = "pr_iterate: the residual is not finite";
   return (pr_status)stop;
+}
+
+int pr_stop_rule(const double* hist, const int* prec, int len, double tol, const pr_options* opt) {
+  if (!hist || !prec || len < 1) return PR_EINVAL;
+  pr_options o;
+  if (opt) o = *opt;
+  else pr_default_options(&o);
+  return stop_rule(hist, prec, len, tol, o);
 }
 
 pr_status pr_solve(pr_handle h, int bulk_precision, int bulk_steps, int final_precision, double tol, int* steps_done) {

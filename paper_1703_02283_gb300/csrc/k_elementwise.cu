@@ -153,7 +153,7 @@ __global__ void k_reduce_sqrt(const double* __restrict__ partial, int count, dou
 __global__ void k_to_bf16(const double* __restrict__ src, int n, int ldl, __nv_bfloat16* __restrict__ dst) {
   const int64_t total = (int64_t)n * n;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
-    dst[(e / n) * ldl + (e % n)] = __double2bfloat16(src[e]);
+    dst[(e / n) * ldl + (e % n)] = bf16_rne(src[e]);
 }
 
 int grid_for(int64_t total) {

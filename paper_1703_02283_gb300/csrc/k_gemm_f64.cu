@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kThreads) k_gemm_f64(const double* __restrict_
           e.out[ij] = P;
           if (mirror) e.out[ji] = P;
           if (e.out_lp) {
-            const __nv_bfloat16 v = __double2bfloat16(P);
+            const __nv_bfloat16 v = bf16_rne(P);
             e.out_lp[ij] = v;
             if (mirror) e.out_lp[ji] = v;
           }
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kThreads) k_gemm_f64(const double* __restrict_
           e.out2[ij] = v;
           if (mirror) e.out2[ji] = v;
           if (e.out2_lp) {
-            const __nv_bfloat16 w = __double2bfloat16(v);
+            const __nv_bfloat16 w = bf16_rne(v);
             e.out2_lp[ij] = w;
             if (mirror) e.out2_lp[ji] = w;
           }

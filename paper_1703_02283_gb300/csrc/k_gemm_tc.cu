@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(TTHREADS, 2)
           if (mirror) e.out[ji] = P;
         }
         if (e.out_lp) {
-          const __nv_bfloat16 b = __double2bfloat16(P);
+          const __nv_bfloat16 b = bf16_rne(P);
           e.out_lp[lij] = b;
           if (mirror) e.out_lp[lji] = b;
         }
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(TTHREADS, 2)
             if (mirror) e.out2[ji] = w;
           }
           if (e.out2_lp) {
-            const __nv_bfloat16 b = __double2bfloat16(w);
+            const __nv_bfloat16 b = bf16_rne(w);
             e.out2_lp[lij] = b;
             if (mirror) e.out2_lp[lji] = b;
           }

@@ -28,6 +28,22 @@ struct Epilogue {
 
 enum class Mode { Sym, Full };
 
+// Round-to-nearest-even conversion of a double to BF16 through round-to-odd FP32 (Boldo and Melquiond,
+// "Emulation of FMA and correctly rounded sums: proved algorithms using rounding to odd", IEEE TC 2008):
+// rounding to odd at 24 bits and then to nearest at 8 bits equals rounding to nearest at 8 bits directly.
+__device__ __forceinline__ __nv_bfloat16 bf16_rne(double x) {
+  float f = __double2float_rz(x);
+  unsigned int u = __float_as_uint(f);
+  if ((double)f != x && (u & 0x7f800000u) != 0x7f800000u) u |= 1u;  // sticky bit: round to odd
+  if ((u & 0x7f800000u) == 0x7f800000u) {                               // Inf / NaN: keep, quiet NaN
+    const unsigned short h = (unsigned short)(u >> 16) | ((u & 0x007fffffu) ? 0x40u : 0u);
+    return __ushort_as_bfloat16(h);
+  }
+  u += 0x7fffu + ((u >> 16) & 1u);  // nearest even at 8 significant bits
+  return __ushort_as_bfloat16((unsigned short)(u >> 16));
+}
+__device__ __forceinline__ __nv_bfloat16 bf16_rne(float x) { return bf16_rne((double)x); }
+
 // ---- FP64 products (k_gemm_f64.cu): P = X Y for n x n row-major X, Y.
 // Returns the number of tiles (= entries written to e.partial).
 int gemm_f64_tiles(int n, Mode mode);

@@ -27,7 +27,8 @@ PR_C0_EQ3, PR_C0_SCALED_I = 0, 1
 class pr_options(ctypes.Structure):
     _fields_ = [("form", ctypes.c_int), ("c0", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("stag_below", ctypes.c_double), ("stag_ratio", ctypes.c_double),
-                ("sym_tol", ctypes.c_double), ("reanchor", ctypes.c_int), ("emu_slices", ctypes.c_int)]
+                ("sym_tol", ctypes.c_double), ("reanchor", ctypes.c_int), ("emu_slices", ctypes.c_int),
+                ("stag_below_lowp", ctypes.c_double)]
 
 
 class pr_stats_t(ctypes.Structure):
@@ -67,6 +68,8 @@ def _load() -> ctypes.CDLL:
                                     ctypes.POINTER(ctypes.c_int)]),
         "pr_residual": (ctypes.c_int, [_handle_t, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
         "pr_result": (ctypes.c_int, [_handle_t, _dptr]),
+        "pr_stop_rule": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                        ctypes.c_double, ctypes.POINTER(pr_options)]),
         "pr_matmul": (ctypes.c_int, [ctypes.c_int, _dptr, _dptr, ctypes.c_int64, ctypes.c_int, _dptr,
                                      ctypes.c_void_p]),
         "pr_stats": (ctypes.c_int, [_handle_t, ctypes.POINTER(pr_stats_t)]),
@@ -160,6 +163,13 @@ def pr_residual(h: int, precision: int = PR_FP64) -> float:
 
 def pr_result(h: int, C_out) -> None:
     _check(_lib.pr_result(h, _ptr(C_out)), h)
+
+
+def pr_stop_rule(hist, prec, tol: float, options: pr_options | None = None) -> int:
+    n = len(hist)
+    h = (ctypes.c_double * max(n, 1))(*hist)
+    q = (ctypes.c_int * max(n, 1))(*prec)
+    return _lib.pr_stop_rule(h, q, n, float(tol), ctypes.byref(options) if options is not None else None)
 
 
 def pr_matmul(precision: int, X, Y, n: int, sym: bool, P, stream: int = 0) -> None:

@@ -37,6 +37,7 @@ def test_host_side_argument_checks():
     from paper_1703_02283_gb300 import pthroot as P
     o = P.pr_default_options()
     assert (o.form, o.c0, o.max_iter, o.stag_below, o.stag_ratio, o.reanchor) == (0, 0, 100, 1e-3, 0.5, 1)
+    assert o.stag_below_lowp == 0.5
     assert P.pr_version() >= 100
     lib = P._lib
     h = ctypes.c_void_p()

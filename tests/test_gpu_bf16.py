@@ -24,8 +24,14 @@ U32 = 2.0 ** -24
 
 
 def bf16(x: np.ndarray) -> np.ndarray:
-    """Round to the nearest BF16 (ties to even) and return as FP64: CPU-side reference rounding."""
-    return torch.from_numpy(np.ascontiguousarray(x)).to(torch.bfloat16).to(torch.float64).numpy()
+    """Round each double to the nearest value with 8 significant bits (ties to even), returned as FP64.
+
+    Written from the definition (x = m 2^e with 0.5 <= |m| < 1, keep rint(m 2^8) / 2^8) so that it rounds
+    once; converting through FP32 first (as a float64 -> bfloat16 cast may) rounds twice and can differ.
+    BF16 range limits do not matter for the values used here.
+    """
+    m, e = np.frexp(np.asarray(x, dtype=np.float64))
+    return np.ldexp(np.rint(m * 256.0) / 256.0, e)
 
 
 def gamma(n):
