@@ -187,10 +187,32 @@ pr_status pr_matmul(int precision, const double* X, const double* Y, int64_t n, 
  * appear in pr_stats (gemm_ms, gemms_timed, gemm_flops_timed). Adds two event records per product. */
 pr_status pr_set_timing(pr_handle h, int on);
 
+/* Largest order accepted by pr_norms_noalloc. */
+#define PR_NORMS_NOALLOC_MAX_N 65536
+
+/* ||A||_1 and ||A||_inf (the norms of Eq. 3's initial guess) for callers that cannot allocate device
+ * memory. The paper has no counterpart: this entry point exists for code that must not call cudaMalloc or
+ * cudaFree, e.g. work issued while a CUDA graph is being captured (allocation calls are not part of a
+ * capture), latency-critical paths that cannot afford the synchronisation cudaFree implies, or programs
+ * whose device memory is already reserved in full by their own allocator.
+ *   A       n*n FP64, row-major, device memory, read only
+ *   n       1 <= n <= PR_NORMS_NOALLOC_MAX_N, else PR_EINVAL (nothing is launched)
+ *   out     device memory, 2 doubles: out[0] = ||A||_1 (largest absolute column sum),
+ *           out[1] = ||A||_inf (largest absolute row sum); written asynchronously on stream
+ *   stream  cudaStream_t (NULL = default stream); the call does not synchronise it
+ * Scratch: a fixed 1 MiB array in the library's device memory (2 * PR_NORMS_NOALLOC_MAX_N doubles) that
+ * every device which loads the library keeps until the process exits. The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress); make that first call before any stream capture
+ * begins. All calls on a device share the array and each call overwrites what it uses, so calls that
+ * overlap on the GPU (on different streams, or from different threads) race and must be serialised.
+ * Allocates nothing: no cudaMalloc, cudaFree or allocating library routine. Errors: PR_EINVAL, PR_ECUDA. */
+pr_status pr_norms_noalloc(const double* A, int64_t n, double* out, void* stream);
+
 /* Frees all device memory of the handle. h may be NULL. */
 pr_status pr_destroy(pr_handle h);
 
-/* Text describing the last failing call on h (or the last failing pr_init when h is NULL). */
+/* Text describing the last failing call on h; with h NULL, the last failing call of this thread that had
+ * no handle (pr_init, pr_matmul, pr_norms_noalloc). */
 const char* pr_last_error(pr_handle h);
 
 /* Library version as major*10000 + minor*100 + patch. */

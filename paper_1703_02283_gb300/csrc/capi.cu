@@ -403,6 +403,10 @@ pr_status ensure_state(pr_handle h, int prec) {
 
 }  // namespace
 
+namespace pr {
+void set_handleless_error(const char* msg) { g_init_error = msg; }
+}  // namespace pr
+
 extern "C" {
 
 int pr_version(void) { return 100; }

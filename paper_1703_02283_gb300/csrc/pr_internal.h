@@ -75,4 +75,7 @@ cudaError_t reduce_partials_sqrt(const double* partial, int count, double* resul
 // dst[i * ldl + j] = bf16(src[i * n + j]) for an n x n matrix
 cudaError_t to_bf16(const double* src, int n, int ldl, __nv_bfloat16* dst, cudaStream_t s);
 
+// Records the text returned by pr_last_error(NULL) for a failing call that has no handle.
+void set_handleless_error(const char* msg);
+
 }  // namespace pr

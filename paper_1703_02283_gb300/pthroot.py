@@ -70,6 +70,7 @@ def _load() -> ctypes.CDLL:
         "pr_result": (ctypes.c_int, [_handle_t, _dptr]),
         "pr_stop_rule": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                         ctypes.c_double, ctypes.POINTER(pr_options)]),
+        "pr_norms_noalloc": (ctypes.c_int, [_dptr, ctypes.c_int64, _dptr, ctypes.c_void_p]),
         "pr_matmul": (ctypes.c_int, [ctypes.c_int, _dptr, _dptr, ctypes.c_int64, ctypes.c_int, _dptr,
                                      ctypes.c_void_p]),
         "pr_stats": (ctypes.c_int, [_handle_t, ctypes.POINTER(pr_stats_t)]),
@@ -170,6 +171,10 @@ def pr_stop_rule(hist, prec, tol: float, options: pr_options | None = None) -> i
     h = (ctypes.c_double * max(n, 1))(*hist)
     q = (ctypes.c_int * max(n, 1))(*prec)
     return _lib.pr_stop_rule(h, q, n, float(tol), ctypes.byref(options) if options is not None else None)
+
+
+def pr_norms_noalloc(A, n: int, out, stream: int = 0) -> None:
+    _check(_lib.pr_norms_noalloc(_ptr(A), int(n), _ptr(out), ctypes.c_void_p(stream)), None)
 
 
 def pr_matmul(precision: int, X, Y, n: int, sym: bool, P, stream: int = 0) -> None:
