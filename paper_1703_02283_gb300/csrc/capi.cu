@@ -276,6 +276,9 @@ pr_status coupled_update(pr_handle h, int prec) {
       o.a = (double)(p + 1) / p;
       o.b = -1.0 / p;
       o.partial = true;
+      // At low precision the FP64 copies of M and N are only needed if a later switch to higher
+      // precision carries them over instead of re-forming M from X.
+      o.out_master = o.out2_master = !(lowp(prec) && h->opt.reanchor);
     }
     s = product(h, prec, h->N, *src, Mode::Sym, o);
     if (s != PR_OK) return s;
@@ -491,7 +494,10 @@ pr_status pr_init(pr_handle* out, const double* A, int64_t n, int p, const pr_op
     PR_INIT_CK(cudaMalloc((void**)&m->b, lbytes));
   }
   const int T64 = (int)((n + 63) / 64);
-  PR_INIT_CK(cudaMalloc((void**)&h->partial, sizeof(double) * (size_t)T64 * T64));
+  size_t nparts = (size_t)T64 * T64;
+  const size_t tc_parts = (size_t)pr::gemm_tc_tiles((int)n, Mode::Full);
+  if (tc_parts > nparts) nparts = tc_parts;
+  PR_INIT_CK(cudaMalloc((void**)&h->partial, sizeof(double) * nparts));
   PR_INIT_CK(cudaMalloc((void**)&h->work, sizeof(double) * 2 * (size_t)n));
   PR_INIT_CK(cudaMalloc((void**)&h->scal, sizeof(double) * 8));
   PR_INIT_CK(cudaMemset(h->scal, 0, sizeof(double) * 8));
