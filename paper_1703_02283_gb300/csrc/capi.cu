@@ -25,12 +25,12 @@ int precision_level(int prec) { return prec == PR_BF16 ? 1 : 2; }
 struct Mat {
   double* f = nullptr;
   __nv_bfloat16* b = nullptr;
+  __nv_bfloat16* sl = nullptr;  // PR_EMU64: S digit planes of f (allocated on first use)
+  int* ex = nullptr;            // PR_EMU64: row exponents of the digit planes
+  bool sl_valid = false;        // the digit planes describe the current f
 };
 
-void swap(Mat& a, Mat& b) {
-  std::swap(a.f, b.f);
-  std::swap(a.b, b.b);
-}
+void swap(Mat& a, Mat& b) { std::swap(a, b); }
 
 // What one product writes; product() maps it onto the kernel epilogue of the chosen precision.
 struct Out {
@@ -53,6 +53,7 @@ struct pr_handle_s {
   cudaStream_t stream = nullptr;
   int device = 0;
   int ldl = 0;  // leading dimension of the BF16 copies
+  int S = 8;    // digit planes per operand for PR_EMU64
 
   // The input, the iterate X, the carried product M and operand N of the coupled form, their next
   // values, and two scratch products.
@@ -137,9 +138,24 @@ pr_status sync(pr_handle h) {
 
 bool lowp(int prec) { return prec == PR_BF16; }
 
+// Digit planes of m for PR_EMU64 products (allocated on first use, recomputed when m changed).
+pr_status ensure_slices(pr_handle h, Mat& m) {
+  const int n = (int)h->n;
+  if (!m.sl) {
+    PR_CK(h, cudaMalloc((void**)&m.sl, (size_t)h->S * (size_t)n * (size_t)h->ldl * sizeof(__nv_bfloat16)));
+    PR_CK(h, cudaMalloc((void**)&m.ex, (size_t)n * sizeof(int)));
+    m.sl_valid = false;
+  }
+  if (m.sl_valid) return PR_OK;
+  PR_CK(h, pr::slice(m.f, n, h->ldl, h->S, m.sl, m.ex, h->stream));
+  h->st.launches += 1;
+  m.sl_valid = true;
+  return PR_OK;
+}
+
 // One matrix product P = X Y (X, Y symmetric, or Y given transposed in its BF16 copy) at the requested
 // precision, with the fused epilogue described by o.
-pr_status product(pr_handle h, int prec, const Mat& X, const Mat& Y, Mode mode, const Out& o) {
+pr_status product(pr_handle h, int prec, Mat& X, Mat& Y, Mode mode, const Out& o) {
   const int n = (int)h->n;
   const double flops = mode == Mode::Sym ? sym_flops(n) : full_flops(n);
   Epilogue e;
@@ -148,7 +164,13 @@ pr_status product(pr_handle h, int prec, const Mat& X, const Mat& Y, Mode mode, 
   e.b = o.b;
   e.c = o.c;
   e.partial = o.partial ? h->partial : nullptr;
-  if (lowp(prec)) {
+  if (prec == PR_EMU64) {
+    pr_status s = ensure_slices(h, X);
+    if (s == PR_OK) s = ensure_slices(h, Y);
+    if (s != PR_OK) return s;
+    if (o.out) e.out = o.out->f;
+    if (o.out2) e.out2 = o.out2->f;
+  } else if (lowp(prec)) {
     if (o.out) {
       e.out_lp = o.out->b;
       if (o.out_master) e.out = o.out->f;
@@ -178,10 +200,16 @@ pr_status product(pr_handle h, int prec, const Mat& X, const Mat& Y, Mode mode, 
     case PR_BF16:
       PR_CK(h, pr::gemm_bf16_tc(X.b, Y.b, n, h->ldl, mode, o.transpose, e, h->err_word(), h->stream));
       break;
+    case PR_EMU64:
+      PR_CK(h, pr::gemm_emu(X.sl, X.ex, Y.sl, Y.ex, n, h->ldl, h->S, mode, o.transpose, e, h->err_word(), h->stream));
+      h->lp_stale = true;
+      break;
     default:
       return fail(h, PR_EUNSUPPORTED, "precision not available in this build");
   }
   h->st.launches += 1;
+  if (o.out) o.out->sl_valid = false;
+  if (o.out2) o.out2->sl_valid = false;
   if (h->timing) {
     PR_CK(h, cudaEventRecord(h->ev[2 * h->ev_pending + 1], h->stream));
     h->ev_flops[h->ev_pending] = flops;
@@ -191,6 +219,7 @@ pr_status product(pr_handle h, int prec, const Mat& X, const Mat& Y, Mode mode, 
 }
 
 int tiles_for(pr_handle h, int prec, Mode mode) {
+  if (prec == PR_EMU64) return pr::emu_tiles((int)h->n, mode);
   return lowp(prec) ? pr::gemm_tc_tiles((int)h->n, mode) : pr::gemm_f64_tiles((int)h->n, mode);
 }
 
@@ -232,7 +261,7 @@ void push_residual(pr_handle h, double r, int prec, bool replace_last) {
 // N = ((p+1) I - M)/p and the partials of ||I - M||_F.
 pr_status form_M_from_X(pr_handle h, int prec, bool replace_last) {
   const int p = h->p;
-  const Mat* src = &h->A;
+  Mat* src = &h->A;
   for (int j = 1; j <= p; ++j) {
     Out o;
     if (j < p) {
@@ -264,7 +293,7 @@ pr_status coupled_update(pr_handle h, int prec) {
   ox.out = &h->Xn;
   pr_status s = product(h, prec, h->X, h->N, Mode::Sym, ox);
   if (s != PR_OK) return s;
-  const Mat* src = &h->M;
+  Mat* src = &h->M;
   for (int j = 1; j <= p; ++j) {
     Out o;
     if (j < p) {
@@ -322,7 +351,7 @@ pr_status ns_update(pr_handle h, int prec) {
 
 // Literal Eq. 1 (FP64 only): T_j = C T_{j-1}, T_0 = A (full products); the residual from T_p = C^p A.
 pr_status literal_residual(pr_handle h, int prec, double* r) {
-  const Mat* src = &h->A;
+  Mat* src = &h->A;
   for (int j = 1; j <= h->p; ++j) {
     Out o;
     o.out = (j & 1) ? &h->T0 : &h->T1;
@@ -336,7 +365,7 @@ pr_status literal_residual(pr_handle h, int prec, double* r) {
 
 // C' = sym(((p+1) C - C T_p) / p).
 pr_status literal_update(pr_handle h, int prec) {
-  const Mat& Tp = (h->p & 1) ? h->T0 : h->T1;
+  Mat& Tp = (h->p & 1) ? h->T0 : h->T1;
   Out o;
   o.out2 = &h->Mn;
   o.b = -1.0 / h->p;
@@ -346,6 +375,7 @@ pr_status literal_update(pr_handle h, int prec) {
   if (s != PR_OK) return s;
   PR_CK(h, pr::symmetrize(h->Mn.f, (int)h->n, h->Xn.f, h->stream));
   h->st.launches += 1;
+  h->Xn.sl_valid = false;
   swap(h->X, h->Xn);
   return PR_OK;
 }
@@ -381,7 +411,6 @@ bool precision_known(int prec) { return prec == PR_FP64 || prec == PR_EMU64 || p
 
 pr_status check_precision(pr_handle h, int prec) {
   if (!precision_known(prec)) return fail(h, PR_EINVAL, "unknown precision");
-  if (prec == PR_EMU64) return fail(h, PR_EUNSUPPORTED, "PR_EMU64 is not available in this build");
   if (h->form == PR_FORM_LITERAL && prec != PR_FP64)
     return fail(h, PR_EUNSUPPORTED, "the literal form runs in PR_FP64 only");
   return PR_OK;
@@ -437,6 +466,8 @@ pr_status pr_destroy(pr_handle h) {
   for (Mat* m : {&h->A, &h->X, &h->Xn, &h->M, &h->Mn, &h->N, &h->Nn, &h->T0, &h->T1}) {
     if (m->f) cudaFree(m->f);
     if (m->b) cudaFree(m->b);
+    if (m->sl) cudaFree(m->sl);
+    if (m->ex) cudaFree(m->ex);
   }
   for (double* b : {h->partial, h->work, h->scal})
     if (b) cudaFree(b);
@@ -458,7 +489,8 @@ pr_status pr_init(pr_handle* out, const double* A, int64_t n, int p, const pr_op
   if (o.form < PR_FORM_AUTO || o.form > PR_FORM_LITERAL) return fail(nullptr, PR_EINVAL, "pr_init: unknown form");
   if (o.c0 != PR_C0_EQ3 && o.c0 != PR_C0_SCALED_I) return fail(nullptr, PR_EINVAL, "pr_init: unknown c0 kind");
   if (o.form == PR_FORM_NS && p != 1) return fail(nullptr, PR_EINVAL, "pr_init: the Newton-Schulz form needs p = 1");
-  if (o.max_iter < 0 || !(o.stag_ratio > 0) || !(o.sym_tol >= 0) || !(o.stag_below_lowp >= 0))
+  if (o.max_iter < 0 || !(o.stag_ratio > 0) || !(o.sym_tol >= 0) || !(o.stag_below_lowp >= 0) ||
+      o.emu_slices < 0 || o.emu_slices > 9)
     return fail(nullptr, PR_EINVAL, "pr_init: bad option value");
 
   pr_handle h = new pr_handle_s();
@@ -468,6 +500,7 @@ pr_status pr_init(pr_handle* out, const double* A, int64_t n, int p, const pr_op
   h->form = o.form == PR_FORM_AUTO ? (p == 1 ? PR_FORM_NS : PR_FORM_COUPLED) : o.form;
   h->stream = (cudaStream_t)stream;
   h->ldl = pr::bf16_ld((int)n);
+  h->S = o.emu_slices > 0 ? o.emu_slices : 8;
   h->st.n = n;
   h->st.p = p;
   h->st.form = h->form;
@@ -496,7 +529,9 @@ pr_status pr_init(pr_handle* out, const double* A, int64_t n, int p, const pr_op
   const int T64 = (int)((n + 63) / 64);
   size_t nparts = (size_t)T64 * T64;
   const size_t tc_parts = (size_t)pr::gemm_tc_tiles((int)n, Mode::Full);
+  const size_t emu_parts = (size_t)pr::emu_tiles((int)n, Mode::Full);
   if (tc_parts > nparts) nparts = tc_parts;
+  if (emu_parts > nparts) nparts = emu_parts;
   PR_INIT_CK(cudaMalloc((void**)&h->partial, sizeof(double) * nparts));
   PR_INIT_CK(cudaMalloc((void**)&h->work, sizeof(double) * 2 * (size_t)n));
   PR_INIT_CK(cudaMalloc((void**)&h->scal, sizeof(double) * 8));
@@ -518,6 +553,7 @@ pr_status pr_load(pr_handle h, const double* A) {
   h->state_ready = false;
   h->state_level = 0;
   h->lp_stale = true;
+  for (Mat* m : {&h->A, &h->X, &h->Xn, &h->M, &h->Mn, &h->N, &h->Nn, &h->T0, &h->T1}) m->sl_valid = false;
   h->hist.clear();
   h->hist_prec.clear();
   h->st.iterations = 0;
@@ -633,15 +669,14 @@ pr_status pr_solve(pr_handle h, int bulk_precision, int bulk_steps, int final_pr
 pr_status pr_residual(pr_handle h, int precision, double* res_fro) {
   if (!h) return fail(nullptr, PR_ESTATE, "pr_residual: NULL handle");
   if (!res_fro) return fail(h, PR_EINVAL, "pr_residual: res_fro is NULL");
-  if (!precision_known(precision) || precision == PR_EMU64)
-    return fail(h, precision_known(precision) ? PR_EUNSUPPORTED : PR_EINVAL, "pr_residual: precision not available");
+  if (!precision_known(precision)) return fail(h, PR_EINVAL, "pr_residual: unknown precision");
   cudaSetDevice(h->device);
   if (lowp(precision)) {
     pr_status s = refresh_lowp(h);
     if (s != PR_OK) return s;
   }
   // C^p by symmetric products (powers of a symmetric matrix are symmetric), then the full product with A.
-  const Mat* P = &h->X;
+  Mat* P = &h->X;
   for (int j = 2; j <= h->p; ++j) {
     Out o;
     o.out = (j & 1) ? &h->T1 : &h->T0;
@@ -669,28 +704,31 @@ pr_status pr_result(pr_handle h, double* C_out) {
 pr_status pr_matmul(int precision, const double* X, const double* Y, int64_t n, int sym, double* P, void* stream) {
   if (!X || !Y || !P) return fail(nullptr, PR_EINVAL, "pr_matmul: NULL matrix");
   if (n < 1 || n > (int64_t)1 << 17) return fail(nullptr, PR_EINVAL, "pr_matmul: n must be in [1, 131072]");
-  if (precision != PR_FP64 && precision != PR_BF16)
-    return fail(nullptr, PR_EUNSUPPORTED, "pr_matmul: precision not available");
+  if (precision != PR_FP64 && precision != PR_BF16 && precision != PR_EMU64)
+    return fail(nullptr, PR_EINVAL, "pr_matmul: unknown precision");
   cudaStream_t s = (cudaStream_t)stream;
-  const int ni = (int)n, ldl = pr::bf16_ld(ni);
+  const int ni = (int)n, ldl = pr::bf16_ld(ni), S = 8;
   const size_t bytes = (size_t)n * (size_t)n * sizeof(double);
   const size_t lbytes = (size_t)n * (size_t)ldl * sizeof(__nv_bfloat16);
   const Mode mode = sym ? Mode::Sym : Mode::Full;
   double *dX = nullptr, *dY = nullptr, *dP = nullptr;
   __nv_bfloat16 *bX = nullptr, *bY = nullptr;
-  int* err = nullptr;
+  int *err = nullptr, *eX = nullptr, *eY = nullptr;
   cudaError_t e = cudaSuccess;
   int word = 0;
   auto step = [&](cudaError_t r) {
     if (e == cudaSuccess) e = r;
   };
+  const size_t planes = precision == PR_EMU64 ? (size_t)S : (size_t)1;
   step(cudaMalloc((void**)&dX, bytes));
   step(cudaMalloc((void**)&dY, bytes));
   step(cudaMalloc((void**)&dP, bytes));
   step(cudaMalloc((void**)&err, sizeof(int)));
-  if (precision == PR_BF16) {
-    step(cudaMalloc((void**)&bX, lbytes));
-    step(cudaMalloc((void**)&bY, lbytes));
+  if (precision != PR_FP64) {
+    step(cudaMalloc((void**)&bX, planes * lbytes));
+    step(cudaMalloc((void**)&bY, planes * lbytes));
+    step(cudaMalloc((void**)&eX, (size_t)n * sizeof(int)));
+    step(cudaMalloc((void**)&eY, (size_t)n * sizeof(int)));
   }
   if (e == cudaSuccess) {
     step(cudaMemsetAsync(err, 0, sizeof(int), s));
@@ -700,16 +738,20 @@ pr_status pr_matmul(int precision, const double* X, const double* Y, int64_t n, 
     ep.out = dP;
     if (precision == PR_FP64) {
       step(pr::gemm_f64(dX, dY, ni, mode, ep, s));
-    } else {
+    } else if (precision == PR_BF16) {
       step(pr::to_bf16(dX, ni, ldl, bX, s));
       step(pr::to_bf16(dY, ni, ldl, bY, s));
       step(pr::gemm_bf16_tc(bX, bY, ni, ldl, mode, false, ep, err, s));
+    } else {
+      step(pr::slice(dX, ni, ldl, S, bX, eX, s));
+      step(pr::slice(dY, ni, ldl, S, bY, eY, s));
+      step(pr::gemm_emu(bX, eX, bY, eY, ni, ldl, S, mode, false, ep, err, s));
     }
     step(cudaMemcpyAsync(P, dP, bytes, cudaMemcpyDefault, s));
     step(cudaMemcpyAsync(&word, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     step(cudaStreamSynchronize(s));
   }
-  for (void* q : {(void*)dX, (void*)dY, (void*)dP, (void*)bX, (void*)bY, (void*)err})
+  for (void* q : {(void*)dX, (void*)dY, (void*)dP, (void*)bX, (void*)bY, (void*)err, (void*)eX, (void*)eY})
     if (q) cudaFree(q);
   if (e != cudaSuccess) return cuda_fail(nullptr, "pr_matmul", e);
   if (word != 0) return fail(nullptr, PR_ETIMEOUT, "pr_matmul: a bounded device wait expired");

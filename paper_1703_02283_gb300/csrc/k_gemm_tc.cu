@@ -59,19 +59,21 @@ __device__ __forceinline__ void tile_coords(int t, int Tm, int Tn, bool sym, int
   bi = bj = 0;
 }
 
+// Writes every requested output at (di, dj) for the product value P. Arithmetic in FP32: the operands
+// carry BF16 precision and the accumulator FP32, and FP64 instructions are scarce on this part.
 struct Emit {
   const Epilogue& e;
   int n, ldl;
-  // Writes every requested output at (di, dj) for the product value P.
-  __device__ __forceinline__ void operator()(int di, int dj, double P) const {
+  float a, b, c;
+  __device__ __forceinline__ void operator()(int di, int dj, float P) const {
     const int64_t ij = (int64_t)di * n + dj, lij = (int64_t)di * ldl + dj;
-    if (e.out) e.out[ij] = P;
+    if (e.out) e.out[ij] = (double)P;
     if (e.out_lp) e.out_lp[lij] = bf16_rne(P);
     if (e.out2 || e.out2_lp) {
-      double w = e.b * P;
-      if (di == dj) w += e.a;
-      if (e.c != 0.0) w += e.c * e.cin[ij];  // cin is symmetric wherever it is used
-      if (e.out2) e.out2[ij] = w;
+      float w = b * P;
+      if (di == dj) w += a;
+      if (c != 0.0f) w = fmaf(c, (float)e.cin[ij], w);  // cin is symmetric wherever it is used
+      if (e.out2) e.out2[ij] = (double)w;
       if (e.out2_lp) e.out2_lp[lij] = bf16_rne(w);
     }
   }
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     // ---------------- epilogue warps
     const int q = warp & 3;
     float* wst = stg + q * STG_FLOATS;
-    const Emit emit{args.e, n, args.ldl};
+    const Emit emit{args.e, n, args.ldl, (float)args.e.a, (float)args.e.b, (float)args.e.c};
     const Epilogue& e = args.e;
     int lt = 0;
     for (int t = blockIdx.x; t < args.ntiles; t += gridDim.x, ++lt) {
@@ -196,7 +198,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       tile_coords(t, args.Tm, args.Tn, SYM, bi, bj);
       const int i0 = bi * BM, j0 = bj * BN;
       const int i = i0 + 32 * q + lane;
-      double part = 0.0;
+      float part = 0.0f;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
         uint32_t v[32];
@@ -208,10 +210,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int c = 0; c < 32; ++c) {
           const int j = j0 + c0 + c;
           if (i >= n || j >= n || (SYM && i > j)) continue;
-          const double P = (double)__uint_as_float(v[c]);
+          const float P = __uint_as_float(v[c]);
           if (e.partial) {
-            const double dd = (i == j ? 1.0 : 0.0) - P;
-            part += ((SYM && i != j) ? 2.0 : 1.0) * dd * dd;
+            const float dd = (i == j ? 1.0f : 0.0f) - P;
+            part = fmaf((SYM && i != j) ? 2.0f * dd : dd, dd, part);
           }
           if (colset && (!SYM || i != j)) emit(j, i, P);
         }
@@ -225,7 +227,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll 4
           for (int rr = 0; rr < 32; ++rr) {
             const int i2 = i0 + 32 * q + rr;
-            if (i2 < n && j2 < n && (!SYM || i2 <= j2)) emit(i2, j2, (double)wst[rr * 33 + lane]);
+            if (i2 < n && j2 < n && (!SYM || i2 <= j2)) emit(i2, j2, wst[rr * 33 + lane]);
           }
           __syncwarp();
         }
@@ -236,7 +238,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (lane == 0) ptx::mbar_arrive(tempty0 + 8 * b);
       if (e.partial) {
         for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        if (lane == 0) e.partial[(int64_t)t * EPI_WARPS + q] = part;
+        if (lane == 0) e.partial[(int64_t)t * EPI_WARPS + q] = (double)part;
       }
     }
   }

@@ -28,21 +28,34 @@ struct Epilogue {
 
 enum class Mode { Sym, Full };
 
-// Round-to-nearest-even conversion of a double to BF16 through round-to-odd FP32 (Boldo and Melquiond,
-// "Emulation of FMA and correctly rounded sums: proved algorithms using rounding to odd", IEEE TC 2008):
-// rounding to odd at 24 bits and then to nearest at 8 bits equals rounding to nearest at 8 bits directly.
-__device__ __forceinline__ __nv_bfloat16 bf16_rne(double x) {
-  float f = __double2float_rz(x);
-  unsigned int u = __float_as_uint(f);
-  if ((double)f != x && (u & 0x7f800000u) != 0x7f800000u) u |= 1u;  // sticky bit: round to odd
-  if ((u & 0x7f800000u) == 0x7f800000u) {                               // Inf / NaN: keep, quiet NaN
-    const unsigned short h = (unsigned short)(u >> 16) | ((u & 0x007fffffu) ? 0x40u : 0u);
-    return __ushort_as_bfloat16(h);
-  }
-  u += 0x7fffu + ((u >> 16) & 1u);  // nearest even at 8 significant bits
+// Round-to-nearest-even conversions to BF16 (8 significant bits), in integer arithmetic: the FP64 units of
+// GB300 are far too slow to sit in an epilogue.
+__device__ __forceinline__ __nv_bfloat16 bf16_rne(float x) {
+  unsigned int u = __float_as_uint(x);
+  if ((u & 0x7f800000u) == 0x7f800000u)  // Inf / NaN (NaN kept quiet)
+    return __ushort_as_bfloat16((unsigned short)((u >> 16) | ((u & 0x007fffffu) ? 0x40u : 0u)));
+  u += 0x7fffu + ((u >> 16) & 1u);  // ties to even on the 16 dropped bits; a carry moves into the exponent
   return __ushort_as_bfloat16((unsigned short)(u >> 16));
 }
-__device__ __forceinline__ __nv_bfloat16 bf16_rne(float x) { return bf16_rne((double)x); }
+
+// From FP64 in one rounding: keep the top 7 of the 52 stored mantissa bits and round on the other 45.
+// Values outside the normal FP32 exponent range (zero, subnormal, huge, Inf, NaN) go through round-to-odd
+// FP32 (Boldo and Melquiond, IEEE TC 2008), which also rounds once.
+__device__ __forceinline__ __nv_bfloat16 bf16_rne(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ffu);
+  if (e >= 1023 - 126 && e <= 1023 + 127) {
+    const unsigned long long m = b & 0xfffffffffffffull;
+    const unsigned long long rest = m & ((1ull << 45) - 1), half = 1ull << 44;
+    unsigned int v = ((unsigned int)(e - 1023 + 127) << 7) | (unsigned int)(m >> 45);
+    if (rest > half || (rest == half && (v & 1u))) v += 1u;  // a carry into the exponent is correct
+    return __ushort_as_bfloat16((unsigned short)(((unsigned int)(b >> 63) << 15) | v));
+  }
+  float f = __double2float_rz(x);
+  unsigned int u = __float_as_uint(f);
+  if ((double)f != x && (u & 0x7f800000u) != 0x7f800000u) u |= 1u;
+  return bf16_rne(__uint_as_float(u));
+}
 
 // ---- FP64 products (k_gemm_f64.cu): P = X Y for n x n row-major X, Y.
 // Returns the number of tiles (= entries written to e.partial).
@@ -56,6 +69,14 @@ int gemm_tc_tiles(int n, Mode mode);
 int bf16_ld(int n);
 cudaError_t gemm_bf16_tc(const __nv_bfloat16* X, const __nv_bfloat16* Y, int n, int ldl, Mode mode, bool transpose,
                          const Epilogue& e, int* err, cudaStream_t s);
+
+// ---- FP64-accurate products from exact BF16 digit slices (k_gemm_emu.cu).
+// slice(): X (n x n FP64) -> S digit planes D (S x n x ldl BF16, most significant first) and row exponents ex.
+// gemm_emu(): P = X Y^T from the slices of X and Y, FP64 epilogue (out / out2 / partial; no BF16 copies).
+int emu_tiles(int n, Mode mode);
+cudaError_t slice(const double* X, int n, int ldl, int S, __nv_bfloat16* D, int* ex, cudaStream_t s);
+cudaError_t gemm_emu(const __nv_bfloat16* DX, const int* ex, const __nv_bfloat16* DY, const int* ey, int n, int ldl,
+                     int S, Mode mode, bool transpose, const Epilogue& e, int* err, cudaStream_t s);
 
 // ---- elementwise and reductions (k_elementwise.cu)
 // scal[0] = max |a_ij|, scal[1] = max |a_ij - a_ji|, scal[2] = #non-finite, scal[3] = #non-positive diagonal

@@ -1,0 +1,156 @@
+"""FP64-accurate products from exact BF16 digit slices (PR_EMU64), through the C ABI.
+
+Product parity: each element is compared with the product evaluated in extended precision (numpy
+longdouble). With S = 8 digits of 7 bits per operand row (row exponent e_i: max_k |x_ik| < 2^(e_i - 1)),
+the representation and the dropped digit pairs (s + t > S + 1) contribute at most (S + 1) 2^(-7S - 2) per
+product term in units of 2^(e_i + f_j); over K = n terms and with a few FP64 roundings of the level sums
+the bound is  n (S + 1) 2^(-7S - 2) 2^(e_i + f_j) + 16 u |P_ij|,  u = 2^-53.
+Solver parity: PR_EMU64 iterations meet the same bar as the native FP64 path against the CPU oracle.
+"""
+import numpy as np
+import pytest
+
+from oracle import pthroot_oracle as O
+from paper_1703_02283_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1703_02283_gb300 import pthroot as P  # noqa: E402
+
+DEV = torch.device("cuda:0")
+S = 8
+U = 2.0 ** -53
+
+
+def row_exponents(X):
+    m = np.abs(X).max(axis=1)
+    _, p = np.frexp(m)  # m = f 2^p, 0.5 <= f < 1
+    return np.where(m > 0, p + 1, 0)
+
+
+def emu_bound(X, Y, ref):
+    n = X.shape[0]
+    ex, ey = row_exponents(X), row_exponents(Y)
+    scale = np.ldexp(1.0, ex[:, None] + ey[None, :])
+    return n * (S + 1) * 2.0 ** (-7 * S - 2) * scale + 16 * U * np.abs(ref)
+
+
+def sym_pair(n, seed):
+    c = W.spd_from_spectrum(n, 0.05, seed)
+    X = c.A / O.norm_1(c.A)
+    Y = 0.5 * np.eye(n) + X @ X
+    return np.ascontiguousarray(X), np.ascontiguousarray(0.5 * (Y + Y.T))
+
+
+def gpu_matmul(prec, X, Y, sym):
+    n = X.shape[0]
+    Xd, Yd = torch.from_numpy(X).to(DEV), torch.from_numpy(Y).to(DEV)
+    Pd = torch.empty_like(Xd)
+    P.pr_matmul(prec, Xd, Yd, n, sym, Pd, torch.cuda.current_stream(DEV).cuda_stream)
+    return Pd.cpu().numpy()
+
+
+@pytest.mark.parametrize("n", [1, 8, 100, 128, 129, 257, 300])
+@pytest.mark.parametrize("sym", [True, False])
+def test_emu_product_elementwise(n, sym):
+    X, Y = sym_pair(n, 60 + n)
+    ref = (X.astype(np.longdouble) @ Y.T.astype(np.longdouble))  # K-major operands: X Y^T (= X Y)
+    Pg = gpu_matmul(P.PR_EMU64, X, Y, sym)
+    err = np.abs(Pg.astype(np.longdouble) - ref).astype(np.float64)
+    bound = emu_bound(X, Y, ref.astype(np.float64))
+    if sym:
+        iu = np.triu_indices(n)
+        assert np.all(err[iu] <= bound[iu])
+        assert np.array_equal(Pg, Pg.T)
+    else:
+        assert np.all(err <= bound)
+    # As accurate as an FP64 product: the Frobenius error is at most that of numpy's FP64 matmul (x 2).
+    e_np = float(np.linalg.norm((X @ Y).astype(np.longdouble) - ref))
+    assert float(np.linalg.norm(err)) <= 2.0 * e_np + 1e-300
+
+
+def test_emu_product_full_size_sampled():
+    n = 4096
+    c = W.spd_from_spectrum(n, 1e-3, 1)
+    X = np.ascontiguousarray(c.A / O.norm_1(c.A))
+    Pg = gpu_matmul(P.PR_EMU64, X, X, True)
+    rng = np.random.default_rng(1)
+    ii, jj = rng.integers(0, n, 1500), rng.integers(0, n, 1500)
+    Xl = X.astype(np.longdouble)
+    ref = np.einsum("ij,ij->i", Xl[ii], Xl[jj])
+    ex = row_exponents(X)
+    bound = n * (S + 1) * 2.0 ** (-7 * S - 2) * np.ldexp(1.0, ex[ii] + ex[jj]) + 16 * U * np.abs(ref.astype(np.float64))
+    err = np.abs(Pg[ii, jj].astype(np.longdouble) - ref).astype(np.float64)
+    assert np.all(err <= bound)
+    assert np.array_equal(Pg, Pg.T)
+
+
+def gpu_solve(case, p, prec, c0=P.PR_C0_EQ3, tol=1e-12, bulk=None, bulk_steps=0):
+    o = P.pr_default_options()
+    o.c0 = c0
+    A = torch.from_numpy(case.A).to(DEV)
+    h = P.pr_init(A, case.n, p, o, torch.cuda.current_stream(DEV).cuda_stream)
+    try:
+        st, steps = P.pr_solve(h, bulk if bulk is not None else prec, bulk_steps, prec, tol)
+        C = torch.empty_like(A)
+        P.pr_result(h, C)
+        return C.cpu().numpy(), st, steps, P.pr_stats(h), P.pr_history(h)
+    finally:
+        P.pr_destroy(h)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_emu_solve_matches_oracle_small_case(p):
+    case = W.spd_from_spectrum(256, 1e-2, 0)
+    C, st, steps, stats, hist = gpu_solve(case, p, P.PR_EMU64)
+    Co, info = O.solve(case.A, p, tol=1e-12)
+    Z = O.closed_form_root(case.Q, case.lam, p)
+    bound = max(1e-12, 10 * O.forward_error(Co, Z))
+    assert O.forward_error(C, Co) <= bound and O.forward_error(C, Z) <= bound
+    assert abs(steps - info.iterations) <= 1
+    assert stats["iterations_by_precision"][P.PR_EMU64] == steps
+
+
+@pytest.mark.parametrize("n", [7, 65, 130, 300])
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_emu_solve_ragged_scaled_identity(n, p):
+    case = W.spd_from_spectrum(n, 0.02, 200 + n)
+    C, st, steps, stats, hist = gpu_solve(case, p, P.PR_EMU64, c0=P.PR_C0_SCALED_I)
+    Co, info = O.solve(case.A, p, c0="scaled_identity", tol=1e-12)
+    Z = O.closed_form_root(case.Q, case.lam, p)
+    bound = max(1e-12, 10 * O.forward_error(Co, Z))
+    assert O.forward_error(C, Z) <= bound
+    assert O.forward_error(C, Co) <= bound
+
+
+def test_ns_ladder_bf16_then_emu64():
+    # p = 1: BF16 bulk iterations, then FP64-accurate emulated ones, reach the FP64 oracle's accuracy.
+    case = W.spd_from_spectrum(512, 1e-3, 14)
+    C, st, steps, stats, hist = gpu_solve(case, 1, P.PR_EMU64, bulk=P.PR_BF16, bulk_steps=100)
+    Co, info = O.solve(case.A, 1, tol=1e-12)
+    Z = O.closed_form_root(case.Q, case.lam, 1)
+    bound = max(1e-12, 10 * O.forward_error(Co, Z))
+    assert O.forward_error(C, Z) <= bound
+    assert stats["iterations_by_precision"][P.PR_BF16] > 0 and stats["iterations_by_precision"][P.PR_EMU64] > 0
+
+
+def test_emu_true_residual():
+    case = W.spd_from_spectrum(200, 0.02, 8)
+    o = P.pr_default_options()
+    A = torch.from_numpy(case.A).to(DEV)
+    h = P.pr_init(A, 200, 2, o, torch.cuda.current_stream(DEV).cuda_stream)
+    try:
+        P.pr_iterate(h, 100, P.PR_FP64, 1e-12)
+        r64 = P.pr_residual(h, P.PR_FP64)
+        remu = P.pr_residual(h, P.PR_EMU64)
+        C = torch.empty_like(A)
+        P.pr_result(h, C)
+    finally:
+        P.pr_destroy(h)
+    want = O.residual_fro(C.cpu().numpy(), case.A, 2)
+    assert abs(remu - want) <= 1e-2 * want + 1e-15
+    assert abs(r64 - want) <= 1e-2 * want + 1e-15
