@@ -1,13 +1,21 @@
 """Benchmark: time to an FP64-accurate A^{-1/p} on one GB300, through the library's C ABI.
 
-One step = the whole hot path on the n = 4096, kappa = 1e3 SPD matrix (Q diag(lam) Q^T, lam log-uniform
-in [1e-3, 1], seed 1) for every root index in --p: load A (checks, ||A||_1, ||A||_inf, C_0 of Eq. 3),
-iterate Eq. 1 to the tolerance (precision ladder per --mode), the true residual ||I - C^p A||_F, and the
-result copy. The value is milliseconds per step (lower is better). Inputs are resident in HBM before
-the timed region; the working set (about 9 x 128 MiB per handle) exceeds the 129 MB L2.
+Workload: the n = 4096, kappa = 1e3 SPD matrix (Q diag(lam) Q^T, lam log-uniform in [1e-3, 1], seed 1),
+roots p = 1, 2, 3, 4, initial guess of Eq. 3, tolerance 1e-12 on the iteration's residual.
 
-`--impl reference` times the CPU oracle (numpy FP64) on the host cores instead, on a bounded sample
-scaled to the same unit.
+One step = the whole hot path for every p in --p: load A (checks, ||A||_1, ||A||_inf, C_0), iterate Eq. 1
+to the tolerance or the precision floor, the true residual ||I - C^p A||_F and the result copy. The value is
+milliseconds per step (lower is better) for --mode:
+  fast   FP64-accurate products from exact BF16 digit slices (PR_EMU64) for every p; for p = 1, whose
+         Newton-Schulz form corrects earlier errors, BF16 iterations first, then PR_EMU64 ones (default);
+  emu64  PR_EMU64 for every iteration;
+  fp64   native FP64 products (the plain FP64 GPU iteration).
+Unless --no-compare, the plain FP64 GPU iteration is also run once per p in the same process and its time
+and accuracy are reported beside the value. Inputs are resident in HBM before the timed region; the
+working set (about 1.5 GiB per handle) exceeds the 129 MB L2.
+
+`--impl reference` times the CPU oracle (numpy FP64) on the host cores instead, on a bounded sample scaled
+to the same unit.
 """
 from __future__ import annotations
 
@@ -30,6 +38,7 @@ from paper_1703_02283_gb300 import workloads as W  # noqa: E402
 METRIC = "time to FP64-accurate A^(-1/p) vs plain FP64 GPU; GEMM TFLOP/s, % of peak"
 NOMINAL_BF16_TFLOPS = 2250.0
 NOMINAL_FP64_TFLOPS = 1.25
+PREC_NAMES = {0: "fp64", 1: "emu64", 3: "bf16"}
 
 
 def parse():
@@ -41,9 +50,10 @@ def parse():
     ap.add_argument("--n", type=int, default=W.SINGLE_CASE["n"])
     ap.add_argument("--lam-min", type=float, default=W.SINGLE_CASE["lam_min"])
     ap.add_argument("--seed", type=int, default=W.SINGLE_CASE["seed"])
-    ap.add_argument("--p", default="2", help="comma-separated root indices solved in one step")
-    ap.add_argument("--mode", default="fp64", choices=["fp64"], help="precision plan of the timed solve")
+    ap.add_argument("--p", default="1,2,3,4", help="comma-separated root indices solved in one step")
+    ap.add_argument("--mode", default="fast", choices=["fast", "emu64", "fp64"])
     ap.add_argument("--tol", type=float, default=1e-12)
+    ap.add_argument("--no-compare", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -128,8 +138,8 @@ def oracle_sample(A: np.ndarray, p: int, iterations: int) -> tuple[float, str]:
     t2 = time.perf_counter()
     per_update = max((t2 - t1) - (t1 - t0), 1e-9)
     setup = max((t1 - t0) - per_update, 0.0)
-    est = setup + per_update * iterations
-    return est * 1e3, f"oracle setup + 1 and + 2 updates at n={A.shape[0]}, p={p}, extrapolated to {iterations} updates"
+    return (setup + per_update * iterations) * 1e3, (f"n={A.shape[0]} p={p}: oracle setup + 1 and + 2 updates, "
+                                                     f"extrapolated to {iterations} updates")
 
 
 def predicted_iterations(case, p: int, tol: float) -> int:
@@ -141,36 +151,34 @@ def predicted_iterations(case, p: int, tol: float) -> int:
     return int(hit[0]) if len(hit) else 200
 
 
+def config_dict(args, ps):
+    return {"workload": f"SPD n={args.n} (Q diag(lam) Q^T), kappa={1 / args.lam_min:g}, p={','.join(map(str, ps))}, "
+                        f"Eq.3 C_0, tol {args.tol:g}", "n": args.n, "kappa": 1 / args.lam_min, "p": ps,
+            "seed": args.seed, "mode": args.mode,
+            "l2": "inputs larger than L2: working set ~1.5 GiB per handle vs 129 MB L2"}
+
+
 def run_reference(args, ps):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    if int(os.environ.get("RANK", "0")) != 0:
         return
     case = W.spd_from_spectrum(args.n, args.lam_min, args.seed)
-    total_ms, samples = [], []
+    totals, samples = [], []
     for _ in range(args.warmup + args.steps):
         ms = 0.0
         for p in ps:
             est, what = oracle_sample(case.A, p, predicted_iterations(case, p, args.tol))
             ms += est
             samples.append(what)
-        total_ms.append(ms)
-    timed = total_ms[args.warmup:]
-    value = float(np.mean(timed))
-    cores = os.cpu_count()
+        totals.append(ms)
+    value = float(np.mean(totals[args.warmup:]))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(args, ps),
-            "cpu_baseline": {"value": value, "unit": "ms", "cores": cores, "kind": "oracle",
-                             "sample": samples[0] + " (each step, per p)"},
+            "cpu_baseline": {"value": value, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "; ".join(samples[:len(ps)]) + " (every step)"},
             "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
-
-
-def config_dict(args, ps):
-    return {"workload": f"SPD n={args.n}, kappa={1 / args.lam_min:g}, p={','.join(map(str, ps))}, "
-                        f"Eq.3 C_0, tol {args.tol:g}", "n": args.n, "kappa": 1 / args.lam_min, "p": ps,
-            "seed": args.seed, "mode": args.mode, "l2": "working set > 129 MB L2 (inputs larger than L2)"}
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -200,20 +208,29 @@ def main():
     case = W.spd_from_spectrum(args.n, args.lam_min, args.seed + 1000 * rank)
     A = torch.from_numpy(case.A).to(dev)
     C = torch.empty_like(A)
-    prec = {"fp64": P.PR_FP64}[args.mode]
-    handles = {}
-    for p in ps:
-        o = P.pr_default_options()
-        handles[p] = P.pr_init(A, args.n, p, o, sptr)
+    handles = {p: P.pr_init(A, args.n, p, P.pr_default_options(), sptr) for p in ps}
 
-    def step():
+    def plan(p, mode):
+        """(bulk precision, bulk steps, final precision) of one solve."""
+        if mode == "fp64":
+            return P.PR_FP64, 0, P.PR_FP64
+        if mode == "emu64" or p != 1:
+            return P.PR_EMU64, 0, P.PR_EMU64
+        return P.PR_BF16, 100, P.PR_EMU64
+
+    def solve_all(mode, Ain, Cout):
         info = {}
         for p, h in handles.items():
-            P.pr_load(h, A)
-            st, steps = P.pr_solve(h, prec, 0, prec, args.tol)
-            res = P.pr_residual(h, prec)
-            P.pr_result(h, C)
-            info[p] = (st, steps, res)
+            bulk, nb, fin = plan(p, mode)
+            P.pr_load(h, Ain)
+            st, steps = P.pr_solve(h, bulk, nb, fin, args.tol)
+            res = P.pr_residual(h, fin)
+            P.pr_result(h, Cout)
+            s = P.pr_stats(h)
+            info[p] = {"status": P.STATUS_NAMES[st], "iterations": steps, "true_residual": res,
+                       "iterations_by_precision": {PREC_NAMES[k]: s["iterations_by_precision"][k] for k in (0, 1, 3)
+                                                   if s["iterations_by_precision"][k]},
+                       "switch_iteration": s["switch_iteration"]}
         return info
 
     def barrier():
@@ -221,8 +238,12 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    def rel_err(Ct, p):
+        Z = (case.Q * case.lam ** (-1.0 / p)) @ case.Q.T
+        return float(np.linalg.norm(Ct.cpu().numpy() - Z) / np.linalg.norm(Z))
+
     for _ in range(args.warmup):
-        step()
+        solve_all(args.mode, A, C)
     barrier()
     s0 = {p: P.pr_stats(h) for p, h in handles.items()}
     for h in handles.values():
@@ -231,7 +252,7 @@ def main():
     with ClockSampler(local) as clk:
         barrier()
         ev0.record(stream)
-        infos = [step() for _ in range(args.steps)]
+        infos = [solve_all(args.mode, A, C) for _ in range(args.steps)]
         ev1.record(stream)
         barrier()
     for h in handles.values():
@@ -242,63 +263,82 @@ def main():
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-
-    # Accuracy of the last step against the exact root (closed form, built on the host).
-    from_closed = {}
     last = infos[-1]
-    Cn = C.cpu().numpy()
-    Zs = {p: (case.Q * case.lam ** (-1.0 / p)) @ case.Q.T for p in ps}
     for p, h in handles.items():
         P.pr_result(h, C)
-        Cn = C.cpu().numpy()
-        Z = Zs[p]
-        from_closed[p] = float(np.linalg.norm(Cn - Z) / np.linalg.norm(Z))
-
-    gemm_ms = sum(s1[p]["gemm_ms"] - s0[p]["gemm_ms"] for p in ps)
-    gemm_fl = sum(s1[p]["gemm_flops_timed"] - s0[p]["gemm_flops_timed"] for p in ps)
-    gemm_n = sum(s1[p]["gemms_timed"] - s0[p]["gemms_timed"] for p in ps)
+        last[p]["rel_error_vs_closed_form"] = rel_err(C, p)
     launches = sum(s1[p]["launches"] - s0[p]["launches"] for p in ps)
-    peaks, peak_src = load_peaks()
-    achieved = gemm_fl / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else None
-    if args.mode == "fp64":
-        peak = peaks["bf16_tflops_sustained"] * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS
-        peak_note = f"{peak_src} bf16 sustained x nominal fp64/bf16 ratio ({NOMINAL_FP64_TFLOPS}/{NOMINAL_BF16_TFLOPS})"
-        dtype = "f64"
-    roofline = {"bound": "tensor", "kernel": "k_gemm_f64 (DMMA)", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
-                "peak_source": peak_note, "launches_timed": gemm_n,
-                "flops_per_launch": gemm_fl / gemm_n if gemm_n else None,
-                "avg_launch_ms": gemm_ms / gemm_n if gemm_n else None}
 
-    # End to end through host buffers (pinned), copies inside the timed region.
+    # Roofline of the dominant product kernel over the timed region (CUDA events around every launch).
+    def delta(key, k):
+        return sum(s1[p][key][k] - s0[p][key][k] for p in ps)
+
+    by_prec = {k: (delta("gemm_ms_by_precision", k), delta("gemm_flops_by_precision", k),
+                   delta("gemms_timed_by_precision", k)) for k in (0, 1, 3)}
+    dom = max(by_prec, key=lambda k: by_prec[k][0])
+    dms, dfl, dn = by_prec[dom]
+    peaks, peak_src = load_peaks()
+    S = s1[ps[0]]["emu_slices"]
+    if dom == P.PR_EMU64:
+        pairs = S * (S + 1) // 2
+        exec_fl = dfl * pairs
+        roofline = {"bound": "tensor", "kernel": "k_gemm_emu (tcgen05 BF16 digit-slice products)",
+                    "achieved": exec_fl / (dms * 1e-3) / 1e12, "peak": peaks["bf16_tflops_sustained"],
+                    "unit": "TFLOP/s", "traffic": None,
+                    "note": f"algorithmic = the {pairs} BF16 digit-pair products per emulated FP64 product "
+                            f"(S={S}), upper-triangle tiles; fp64_equivalent_tflops = FP64 flops / time",
+                    "fp64_equivalent_tflops": dfl / (dms * 1e-3) / 1e12,
+                    "peak_source": f"{peak_src} bf16 sustained (kernel timed inside a long step)"}
+    elif dom == P.PR_BF16:
+        roofline = {"bound": "tensor", "kernel": "k_gemm_bf16_tc", "achieved": dfl / (dms * 1e-3) / 1e12,
+                    "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s", "traffic": None,
+                    "peak_source": f"{peak_src} bf16 sustained"}
+    else:
+        peak = peaks["bf16_tflops_sustained"] * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS
+        roofline = {"bound": "tensor", "kernel": "k_gemm_f64 (DMMA)", "achieved": dfl / (dms * 1e-3) / 1e12,
+                    "peak": peak, "unit": "TFLOP/s", "traffic": None,
+                    "peak_source": f"{peak_src} bf16 sustained x nominal fp64/bf16 ({NOMINAL_FP64_TFLOPS}/"
+                                   f"{NOMINAL_BF16_TFLOPS})"}
+    roofline["frac"] = roofline["achieved"] / roofline["peak"]
+    roofline.update({"launches_timed": dn, "avg_launch_ms": dms / dn if dn else None,
+                     "flops_per_launch_fp64_equivalent": dfl / dn if dn else None})
+    kernel_share = {PREC_NAMES[k]: round(v[0] / (ms * args.steps), 4) for k, v in by_prec.items() if v[2]}
+
+    # End to end through pinned host buffers, copies inside the timed region.
     e2e = None
     if not args.no_e2e:
         Ah = torch.from_numpy(case.A).pin_memory()
         Ch = torch.empty_like(Ah).pin_memory()
-        for _ in range(1):
-            for p, h in handles.items():
-                P.pr_load(h, Ah)
-                P.pr_solve(h, prec, 0, prec, args.tol)
-                P.pr_residual(h, prec)
-                P.pr_result(h, Ch)
+        solve_all(args.mode, Ah, Ch)
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            for p, h in handles.items():
-                P.pr_load(h, Ah)
-                P.pr_solve(h, prec, 0, prec, args.tol)
-                P.pr_residual(h, prec)
-                P.pr_result(h, Ch)
+            solve_all(args.mode, Ah, Ch)
         barrier()
-        e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
         nbytes = args.n * args.n * 8 * len(ps)
-        e2e = {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+        e2e = {"value": (time.perf_counter() - t0) * 1e3 / args.steps, "unit": "ms",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+    # The plain FP64 GPU iteration on the same matrices, once per p (the speed comparison).
+    plain = None
+    if not args.no_compare and args.mode != "fp64":
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        pinfo = solve_all("fp64", A, C)
+        e1.record(stream)
+        barrier()
+        for p, h in handles.items():
+            P.pr_result(h, C)
+            pinfo[p]["rel_error_vs_closed_form"] = rel_err(C, p)
+        pms = e0.elapsed_time(e1)
+        plain = {"ms_per_step": pms, "speedup_of_value": pms / ms, "solves": {str(p): v for p, v in pinfo.items()}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         tot, what = 0.0, []
         for p in ps:
-            est, w = oracle_sample(case.A, p, last[p][1])
+            est, w = oracle_sample(case.A, p, last[p]["iterations"])
             tot += est
             what.append(w)
         cpu = {"value": tot, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle", "sample": "; ".join(what)}
@@ -308,12 +348,11 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-                "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": config_dict(args, ps),
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk.summary(),
-                "solves": {str(p): {"status": P.STATUS_NAMES[last[p][0]], "iterations": last[p][1],
-                                    "true_residual": last[p][2], "rel_error_vs_closed_form": from_closed[p]}
-                           for p in ps}}
+                "vs_baseline": None, "dtype": {"fast": "bf16+emu64(bf16 slices)", "emu64": "emu64(bf16 slices)",
+                                               "fp64": "f64"}[args.mode],
+                "data": "synthetic", "config": config_dict(args, ps), "roofline": roofline,
+                "kernel_time_share": kernel_share, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk.summary(), "solves": {str(p): v for p, v in last.items()}, "plain_fp64_gpu": plain}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -114,6 +114,11 @@ typedef struct {
   int64_t gemms_timed;      /* products timed with CUDA events (pr_set_timing)                           */
   double gemm_ms;           /* summed event time of the timed products                                     */
   double gemm_flops_timed;  /* algorithmic flops of the timed products                                     */
+  int emu_slices;           /* digit planes per operand used by PR_EMU64 (S; S (S + 1) / 2 BF16 products
+                               per emulated product)                                                     */
+  int64_t gemms_timed_by_precision[4];  /* the timed counters above, split by pr_precision            */
+  double gemm_ms_by_precision[4];
+  double gemm_flops_by_precision[4];
 } pr_stats_t;
 
 /* Fills *opt with the defaults listed above. */

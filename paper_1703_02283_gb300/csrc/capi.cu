@@ -68,6 +68,7 @@ struct pr_handle_s {
   bool timing = false;
   std::vector<cudaEvent_t> ev;  // pairs: ev[2i] before, ev[2i + 1] after product i
   std::vector<double> ev_flops;
+  std::vector<int> ev_prec;
   int ev_pending = 0;
 
   bool state_ready = false;  // (coupled) M, N and the residual of the current iterate are formed
@@ -115,6 +116,10 @@ pr_status harvest_events(pr_handle h) {
     h->st.gemm_ms += ms;
     h->st.gemms_timed += 1;
     h->st.gemm_flops_timed += h->ev_flops[i];
+    const int pq = h->ev_prec[i];
+    h->st.gemm_ms_by_precision[pq] += ms;
+    h->st.gemms_timed_by_precision[pq] += 1;
+    h->st.gemm_flops_by_precision[pq] += h->ev_flops[i];
   }
   h->ev_pending = 0;
   return PR_OK;
@@ -213,6 +218,7 @@ pr_status product(pr_handle h, int prec, Mat& X, Mat& Y, Mode mode, const Out& o
   if (h->timing) {
     PR_CK(h, cudaEventRecord(h->ev[2 * h->ev_pending + 1], h->stream));
     h->ev_flops[h->ev_pending] = flops;
+    h->ev_prec[h->ev_pending] = prec;
     h->ev_pending += 1;
   }
   return PR_OK;
@@ -501,6 +507,7 @@ pr_status pr_init(pr_handle* out, const double* A, int64_t n, int p, const pr_op
   h->stream = (cudaStream_t)stream;
   h->ldl = pr::bf16_ld((int)n);
   h->S = o.emu_slices > 0 ? o.emu_slices : 8;
+  h->st.emu_slices = h->S;
   h->st.n = n;
   h->st.p = p;
   h->st.form = h->form;
@@ -595,6 +602,7 @@ pr_status pr_set_timing(pr_handle h, int on) {
   if (on && h->ev.empty()) {
     h->ev.resize(2 * kEventPairs);
     h->ev_flops.resize(kEventPairs);
+    h->ev_prec.resize(kEventPairs);
     for (cudaEvent_t& e : h->ev) PR_CK(h, cudaEventCreate(&e));
   }
   if (!on) {

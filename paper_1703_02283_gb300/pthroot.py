@@ -38,11 +38,15 @@ class pr_stats_t(ctypes.Structure):
                 ("last_stop", ctypes.c_int), ("norm_1", ctypes.c_double), ("norm_inf", ctypes.c_double),
                 ("last_residual", ctypes.c_double), ("gemms", ctypes.c_int64), ("gemm_flops", ctypes.c_double),
                 ("launches", ctypes.c_int64), ("gemms_timed", ctypes.c_int64), ("gemm_ms", ctypes.c_double),
-                ("gemm_flops_timed", ctypes.c_double)]
+                ("gemm_flops_timed", ctypes.c_double), ("emu_slices", ctypes.c_int),
+                ("gemms_timed_by_precision", ctypes.c_int64 * 4), ("gemm_ms_by_precision", ctypes.c_double * 4),
+                ("gemm_flops_by_precision", ctypes.c_double * 4)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
-        d["iterations_by_precision"] = list(self.iterations_by_precision)
+        for k in ("iterations_by_precision", "gemms_timed_by_precision", "gemm_ms_by_precision",
+                  "gemm_flops_by_precision"):
+            d[k] = list(getattr(self, k))
         return d
 
 

@@ -56,3 +56,29 @@ def test_host_side_argument_checks():
     assert h.value is None
     assert lib.pr_iterate(None, 1, P.PR_FP64, 1e-12, None) == P.PR_ESTATE
     assert lib.pr_destroy(None) == P.PR_OK
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structures have the size and field offsets the C compiler gives the header."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    from paper_1703_02283_gb300 import pthroot as P
+    fields = {"pr_options": [f for f, _ in P.pr_options._fields_], "pr_stats_t": [f for f, _ in P.pr_stats_t._fields_]}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pthroot.h"', "int main(void) {"]
+    for st, fs in fields.items():
+        lines.append(f'  printf("{st} %zu\\n", sizeof({st}));')
+        for f in fs:
+            lines.append(f'  printf("{st}.{f} %zu\\n", offsetof({st}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                              check=True).stdout.split("\n") if line)
+    for st, cls in (("pr_options", P.pr_options), ("pr_stats_t", P.pr_stats_t)):
+        assert int(out[st]) == ctypes.sizeof(cls), st
+        for f in fields[st]:
+            assert int(out[f"{st}.{f}"]) == getattr(cls, f).offset, (st, f)
