@@ -147,6 +147,8 @@ pr_status pr_load(pr_handle h, const double* A);
  * iterate is tested: r_k <= tol returns PR_OK; a non-finite r_k returns PR_EDIVERGED; r_{k-1} < stag_below
  * and r_k > stag_ratio * r_{k-1} (both computed in this call) returns PR_ESTAGNATED; an exhausted budget
  * returns PR_EMAXITER. *steps_done (may be NULL) receives the number of updates applied in this call.
+ * When a PR_BF16 run stops because r_k >= r_{k-1}, the last update is undone (the iterate, its residual
+ * and the counters return to step k-1), so that a following precise phase starts from the better iterate.
  * Synchronises the stream once per update to read r_k. */
 pr_status pr_iterate(pr_handle h, int max_steps, int precision, double tol, int* steps_done);
 
@@ -156,8 +158,8 @@ pr_status pr_iterate(pr_handle h, int max_steps, int precision, double tol, int*
  * PR_ESTAGNATED if r_{k-1} and r_k were computed at the same precision and either
  *   (a) r_{k-1} < arm and r_k > stag_ratio * r_{k-1}, arm = stag_below (PR_FP64, PR_EMU64) or
  *       stag_below_lowp (PR_BF16), or
- *   (b) PR_BF16 only: r_k >= r_{k-1} after some residual of the current run of that precision fell below
- *       half of the run's first residual (a low-precision floor above stag_below_lowp),
+ *   (b) PR_BF16 only: r_k >= r_{k-1} (a low-precision floor, or the iteration leaving its region of
+ *       convergence because the rounding of the iterate is too coarse for the conditioning of A),
  * and -1 otherwise (continue). The step budget and max_iter are checked by pr_iterate itself. */
 int pr_stop_rule(const double* hist, const int* prec, int len, double tol, const pr_options* opt);
 

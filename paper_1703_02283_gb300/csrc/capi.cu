@@ -396,12 +396,7 @@ int stop_rule(const double* hist, const int* prec, int len, double tol, const pr
     const bool low = lowp(prec[len - 1]);
     const double arm = low ? o.stag_below_lowp : o.stag_below;
     if (q < arm && r > o.stag_ratio * q) return PR_ESTAGNATED;
-    if (low && r >= q) {
-      int first = len - 1;
-      while (first > 0 && prec[first - 1] == prec[len - 1]) --first;
-      for (int i = first + 1; i < len - 1; ++i)
-        if (hist[i] < 0.5 * hist[first]) return PR_ESTAGNATED;
-    }
+    if (low && r >= q) return PR_ESTAGNATED;  // a low-precision floor, or the iteration leaving its basin
   }
   return -1;
 }
@@ -635,6 +630,22 @@ pr_status pr_iterate(pr_handle h, int max_steps, int precision, double tol, int*
       push_residual(h, r, precision, same_iterate);
     }
     stop = decide(h, tol, steps, max_steps);
+    if (stop == PR_ESTAGNATED && lowp(precision) && steps > 0 && h->hist.size() >= 2 &&
+        h->hist.back() >= h->hist[h->hist.size() - 2] && h->form != PR_FORM_LITERAL) {
+      // The last low-precision update made things worse: return to the previous iterate, which the
+      // double-buffered state still holds, so that a precise phase starts from the better one.
+      swap(h->X, h->Xn);
+      if (h->form == PR_FORM_COUPLED) {
+        swap(h->M, h->Mn);
+        swap(h->N, h->Nn);
+      }
+      h->hist.pop_back();
+      h->hist_prec.pop_back();
+      h->st.last_residual = h->hist.back();
+      h->st.iterations -= 1;
+      h->st.iterations_by_precision[precision] -= 1;
+      steps -= 1;
+    }
     if (stop >= 0) break;
     if (h->st.last_precision >= 0 && h->st.last_precision != precision) h->st.switch_iteration = h->st.iterations;
     if (h->form == PR_FORM_COUPLED) s = coupled_update(h, precision);
