@@ -58,7 +58,7 @@ typedef enum {
 typedef enum {
   PR_FP64 = 0,   /* native FP64 products (DMMA tensor instructions), FP64 accumulation                   */
   PR_EMU64 = 1,  /* FP64-accurate products from exact BF16 digit slices on the tcgen05 tensor cores:
-                    every row of an operand is split into S (default 8) balanced base-128 digits with a
+                    every row of an operand is split into S (default 9) balanced base-128 digits with a
                     row exponent; each digit pair with s + t <= S + 1 is an exact FP32 tensor-core
                     product (K chunks of at most 4096), summed in int32 per level and FP64 overall   */
   PR_BF16 = 3    /* BF16 operands, FP32 accumulation in TMEM (tcgen05 kind::f16); FP64 master copies     */
@@ -88,7 +88,8 @@ typedef struct {
   double stag_ratio;   /* ... and fires when r_k > stag_ratio * r_{k-1}, default 0.5                      */
   double sym_tol;      /* pr_init rejects A with max|a_ij - a_ji| > sym_tol * max|a_ij|, default 1e-12   */
   int reanchor;        /* coupled form: on a switch to higher precision recompute M = X^p A, default 1  */
-  int emu_slices;      /* PR_EMU64 slice count per operand (0 = chosen from n), default 0               */
+  int emu_slices;      /* PR_EMU64 digit planes per operand, 1..9 (0 = the default, 9): S planes keep
+                          7S bits per row and cost S (S + 1) / 2 BF16 products per FP64 product         */
   double stag_below_lowp; /* stag_below for low-precision (PR_BF16) residuals, whose floor is higher,
                              default 0.5 (below 0.5 every eigencomponent is in the quadratic phase)      */
 } pr_options;
@@ -189,7 +190,7 @@ pr_status pr_history(pr_handle h, double* out, int cap, int* len);
  * P = X Y for symmetric n x n FP64 X and Y (device or host memory) that commute, so that X Y is symmetric.
  * sym != 0 computes only the upper-triangle tiles and mirrors them (the iteration's symmetric products);
  * sym == 0 computes every tile. precision PR_FP64 uses FP64 DMMA; PR_BF16 rounds X and Y to BF16 and
- * accumulates in FP32 on the tcgen05 tensor cores; PR_EMU64 forms the product from 8 exact BF16 digit
+ * accumulates in FP32 on the tcgen05 tensor cores; PR_EMU64 forms the product from 9 exact BF16 digit
  * slices per operand (see PR_EMU64). P: n*n FP64 output (device or host), caller-owned.
  * Allocates and frees temporary device buffers. Synchronises the stream. */
 pr_status pr_matmul(int precision, const double* X, const double* Y, int64_t n, int sym, double* P, void* stream);

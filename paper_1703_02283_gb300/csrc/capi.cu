@@ -53,7 +53,7 @@ struct pr_handle_s {
   cudaStream_t stream = nullptr;
   int device = 0;
   int ldl = 0;  // leading dimension of the BF16 copies
-  int S = 8;    // digit planes per operand for PR_EMU64
+  int S = 9;    // digit planes per operand for PR_EMU64
 
   // The input, the iterate X, the carried product M and operand N of the coupled form, their next
   // values, and two scratch products.
@@ -501,7 +501,7 @@ pr_status pr_init(pr_handle* out, const double* A, int64_t n, int p, const pr_op
   h->form = o.form == PR_FORM_AUTO ? (p == 1 ? PR_FORM_NS : PR_FORM_COUPLED) : o.form;
   h->stream = (cudaStream_t)stream;
   h->ldl = pr::bf16_ld((int)n);
-  h->S = o.emu_slices > 0 ? o.emu_slices : 8;
+  h->S = o.emu_slices > 0 ? o.emu_slices : 9;
   h->st.emu_slices = h->S;
   h->st.n = n;
   h->st.p = p;
@@ -726,7 +726,7 @@ pr_status pr_matmul(int precision, const double* X, const double* Y, int64_t n, 
   if (precision != PR_FP64 && precision != PR_BF16 && precision != PR_EMU64)
     return fail(nullptr, PR_EINVAL, "pr_matmul: unknown precision");
   cudaStream_t s = (cudaStream_t)stream;
-  const int ni = (int)n, ldl = pr::bf16_ld(ni), S = 8;
+  const int ni = (int)n, ldl = pr::bf16_ld(ni), S = 9;
   const size_t bytes = (size_t)n * (size_t)n * sizeof(double);
   const size_t lbytes = (size_t)n * (size_t)ldl * sizeof(__nv_bfloat16);
   const Mode mode = sym ? Mode::Sym : Mode::Full;

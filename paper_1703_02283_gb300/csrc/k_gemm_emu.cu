@@ -14,7 +14,8 @@
 //    accumulation of the tensor cores computes it exactly. Pairs are taken level by level (L = s + t); the
 //    exact pair results of a level are summed in int32, and each level is added into an FP64 total.
 //    Dropping the pairs with s + t > S + 1 and the digits beyond S leaves an error of about
-//    (S + 1) 2^(-7S - 1) relative to max|x_i.| max|y_.j| per product term: S = 8 gives 2^-54.
+//    (S + 1) 2^(-7S - 2) in units of 2^(e_i + f_j) per product term: S = 9 (the default) gives 2^-62. F must
+//    fit in 64-bit integers, which limits S to 9.
 //
 // k_gemm_emu is a persistent kernel, one CTA per SM, 128 x 128 output tiles (symmetric mode: upper
 // triangle only, mirrored), 320 threads: warp 0 TMA producer (6-stage ring of 128 x 64 digit boxes), warp 1
@@ -396,6 +397,8 @@ cudaError_t gemm_emu(const __nv_bfloat16* DX, const int* ex, const __nv_bfloat16
   if (S < 1 || S > 9 || ldl % 8 != 0 || ldl < n) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(DX) | reinterpret_cast<uintptr_t>(DY)) & 15) return cudaErrorMisalignedAddress;
   if ((int64_t)S * n > (int64_t)1 << 31) return cudaErrorInvalidValue;
+  // The int32 level sums hold up to S pairs of K-sums of n terms, each term at most 64 * 64.
+  if ((int64_t)S * n * 4096 >= (int64_t)1 << 31) return cudaErrorInvalidValue;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t a = cudaFuncSetAttribute(k_gemm_emu<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);

@@ -1,7 +1,7 @@
 """FP64-accurate products from exact BF16 digit slices (PR_EMU64), through the C ABI.
 
 Product parity: each element is compared with the product evaluated in extended precision (numpy
-longdouble). With S = 8 digits of 7 bits per operand row (row exponent e_i: max_k |x_ik| < 2^(e_i - 1)),
+longdouble). With S = 9 digits of 7 bits per operand row (row exponent e_i: max_k |x_ik| < 2^(e_i - 1)),
 the representation and the dropped digit pairs (s + t > S + 1) contribute at most (S + 1) 2^(-7S - 2) per
 product term in units of 2^(e_i + f_j); over K = n terms and with a few FP64 roundings of the level sums
 the bound is  n (S + 1) 2^(-7S - 2) 2^(e_i + f_j) + 16 u |P_ij|,  u = 2^-53.
@@ -22,7 +22,7 @@ if not torch.cuda.is_available():
 from paper_1703_02283_gb300 import pthroot as P  # noqa: E402
 
 DEV = torch.device("cuda:0")
-S = 8
+S = 9
 U = 2.0 ** -53
 
 
