@@ -38,6 +38,9 @@ constexpr int BOX_BYTES = EBM * EBK * 2, STAGE_BYTES = 2 * BOX_BYTES;
 constexpr int SMEM_BYTES = 1024 + ESTAGES * STAGE_BYTES + 256;
 constexpr int KCHUNK_BLOCKS = 4096 / EBK;  // K blocks per exact pass: 4096 * 64 * 64 = 2^24
 constexpr int TOTAL_COL = 2 * EBN;         // TMEM column of the FP64 totals (2 words per element)
+// Levels summed exactly in int64 before one FP64 addition: a level sum is below S * n * 2^12 <= 2^31, and
+// kGroup levels Horner-combined with 7-bit shifts stay below 2^(31 + 7 (kGroup - 1)) <= 2^59.
+constexpr int kGroup = 5;
 constexpr uint32_t kIdesc = ptx::idesc_bf16_f32(EBM, EBN);
 
 // ------------------------------------------------------------------------------------------ slicing
@@ -50,7 +53,20 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
   return v;
 }
 
+// F = round(x 2^(7S - e)) of one double as an integer (|F| < 2^(7S - 1) for |x| < 2^(e - 1)).
+__device__ __forceinline__ long long fixed_point(unsigned long long u, int e, int S) {
+  const int E = (int)((u >> 52) & 0x7ff);
+  if (E == 0) return 0;  // zero, or a subnormal far below the last digit
+  const unsigned long long M = (u & 0xfffffffffffffull) | (1ull << 52);
+  const int sh = (E - 1023) - e + 7 * S - 52;  // F = M 2^sh, sh <= 7S - 54
+  long long F = 0;
+  if (sh >= 0) F = (long long)(M << sh);
+  else if (sh > -64) F = (long long)((M + (1ull << (-sh - 1))) >> (-sh));
+  return (u >> 63) ? -F : F;
+}
+
 // One warp per row: exponent e_i, then S digit planes D[s][i][k] (s = 0 is the most significant digit).
+// Each lane handles two adjacent columns (ldl is even), so loads are 16 bytes and stores bf16x2.
 __global__ void k_slice(const double* __restrict__ X, int n, int ldl, int S, __nv_bfloat16* __restrict__ D,
                         int* __restrict__ ex) {
   const int lane = threadIdx.x & 31;
@@ -63,30 +79,25 @@ __global__ void k_slice(const double* __restrict__ X, int n, int ldl, int S, __n
       mb = u > mb ? u : mb;
     }
     mb = warp_max_u64(mb);
-    const int emax = (int)(mb >> 52);                 // biased exponent of the row maximum
-    const int e = emax == 0 ? 0 : emax - 1023 + 2;    // zero (or subnormal-only) rows get digits 0
+    const int emax = (int)(mb >> 52);               // biased exponent of the row maximum
+    const int e = emax == 0 ? 0 : emax - 1023 + 2;  // zero (or subnormal-only) rows get digits 0
     if (lane == 0) ex[i] = e;
-    for (int k = lane; k < ldl; k += 32) {
-      long long F = 0;
-      if (k < n && emax != 0) {
-        const unsigned long long u = row[k];
-        const int E = (int)((u >> 52) & 0x7ff);
-        if (E != 0) {  // subnormals are below the last digit
-          const unsigned long long M = (u & 0xfffffffffffffull) | (1ull << 52);
-          const int sh = (E - 1023) - e + 7 * S - 52;  // F = M 2^sh, sh <= 7S - 54
-          if (sh >= 0) F = (long long)(M << sh);
-          else if (sh > -64) F = (long long)((M + (1ull << (-sh - 1))) >> (-sh));
-          if (u >> 63) F = -F;
-        }
+    for (int k = 2 * lane; k < ldl; k += 64) {
+      long long F0 = 0, F1 = 0;
+      if (emax != 0) {
+        if (k < n) F0 = fixed_point(row[k], e, S);
+        if (k + 1 < n) F1 = fixed_point(row[k + 1], e, S);
       }
+      __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(D + (int64_t)i * ldl + k);
       // Balanced base-128 digits, least significant first; the last one takes the remainder (|.| <= 64).
       for (int s = S - 1; s >= 1; --s) {
-        const int r = (int)(F & 127);
-        const int d = r >= 64 ? r - 128 : r;
-        F = (F - d) >> 7;
-        D[(int64_t)s * plane + (int64_t)i * ldl + k] = __float2bfloat16_rn((float)d);
+        const int r0 = (int)(F0 & 127), r1 = (int)(F1 & 127);
+        const int d0 = r0 >= 64 ? r0 - 128 : r0, d1 = r1 >= 64 ? r1 - 128 : r1;
+        F0 = (F0 - d0) >> 7;
+        F1 = (F1 - d1) >> 7;
+        dst[(int64_t)s * (plane / 2)] = __floats2bfloat162_rn((float)d0, (float)d1);
       }
-      D[(int64_t)i * ldl + k] = __float2bfloat16_rn((float)F);
+      dst[0] = __floats2bfloat162_rn((float)F0, (float)F1);
     }
   }
 }
@@ -124,7 +135,7 @@ __device__ __forceinline__ double scale2(double x, int E) {
 }
 
 template <bool SYM>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __maxnreg__(200)
     k_gemm_emu(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, EmuArgs args) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -236,6 +247,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   } else {
     // ---------------- epilogue warps: quadrant q (TMEM lanes 32q..), column half h (64 columns)
+    // Levels are summed exactly in int64, Horner-style over groups of up to kGroup levels (a group's
+    // sum stays below 2^63); only at a group end is the group added into the FP64 total in TMEM.
     const int q = warp & 3, h = (warp - 2) >> 2;
     const Epilogue& e = args.e;
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
@@ -245,58 +258,65 @@ __global__ void __launch_bounds__(THREADS, 1)
       int bi, bj;
       if (SYM) tri_index_emu(t, args.T, bi, bj);
       else { bi = t % args.T; bj = t / args.T; }
-      for (int L = 2; L <= S + 1 && !stop; ++L) {
-        int acc[64];
+      bool first_group = true;
+      for (int g0 = 2; g0 <= S + 1 && !stop; g0 += kGroup) {
+        const int glast = min(g0 + kGroup - 1, S + 1);
+        long long acc[64];
 #pragma unroll
         for (int c = 0; c < 64; ++c) acc[c] = 0;
-        for (int s = 1; s <= L - 1 && !stop; ++s)
-          for (int c = 0; c < args.nchunks; ++c, ++u) {
-            if (__shfl_sync(0xffffffffu, *s_abort, 0)) { stop = true; break; }
-            const int b = u & 1;
-            if (!__all_sync(0xffffffffu, ptx::mbar_wait(tfull0 + 8 * b, (u >> 1) & 1, args.err, 14))) {
-              *s_abort = 1;
-              stop = true;
-              break;
-            }
-            ptx::tc_fence_after();
+        for (int L = g0; L <= glast && !stop; ++L) {
+          const int shift = 7 * (glast - L);
+          for (int s = 1; s <= L - 1 && !stop; ++s)
+            for (int c = 0; c < args.nchunks; ++c, ++u) {
+              if (__shfl_sync(0xffffffffu, *s_abort, 0)) { stop = true; break; }
+              const int b = u & 1;
+              if (!__all_sync(0xffffffffu, ptx::mbar_wait(tfull0 + 8 * b, (u >> 1) & 1, args.err, 14))) {
+                *s_abort = 1;
+                stop = true;
+                break;
+              }
+              ptx::tc_fence_after();
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
-              uint32_t v[32];
-              ptx::tmem_ld_32x32b_x32(tmem + lane_off + (uint32_t)(b * EBN + 64 * h + 32 * half), v);
-              ptx::tmem_ld_wait();
+              for (int half = 0; half < 2; ++half) {
+                uint32_t v[32];
+                ptx::tmem_ld_32x32b_x32(tmem + lane_off + (uint32_t)(b * EBN + 64 * h + 32 * half), v);
+                ptx::tmem_ld_wait();
 #pragma unroll
-              for (int c2 = 0; c2 < 32; ++c2) acc[32 * half + c2] += __float2int_rn(__uint_as_float(v[c2]));
+                for (int c2 = 0; c2 < 32; ++c2)
+                  acc[32 * half + c2] += (long long)__float2int_rn(__uint_as_float(v[c2])) << shift;
+              }
+              ptx::tc_fence_before();
+              __syncwarp();
+              if (lane == 0) ptx::mbar_arrive(tempty0 + 8 * b);
             }
-            ptx::tc_fence_before();
-            __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(tempty0 + 8 * b);
-          }
+        }
         if (stop) break;
-        // Level end: total (+)= acc 2^(-7L), FP64 words in TMEM, 16 elements (32 words) per access.
+        // Group end: total (+)= acc 2^(-7 glast); FP64 words in TMEM, 16 elements (32 words) per access.
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
           const uint32_t ta = tmem + lane_off + (uint32_t)(TOTAL_COL + 128 * h + 32 * g);
           uint32_t w[32];
-          if (L > 2) {
+          if (!first_group) {
             ptx::tmem_ld_32x32b_x32(ta, w);
             ptx::tmem_ld_wait();
           }
 #pragma unroll
           for (int c2 = 0; c2 < 16; ++c2) {
-            double tot = L > 2 ? __hiloint2double((int)w[2 * c2 + 1], (int)w[2 * c2]) : 0.0;
-            tot += scale2((double)acc[16 * g + c2], -7 * L);
+            double tot = scale2((double)acc[16 * g + c2], -7 * glast);
+            if (!first_group) tot += __hiloint2double((int)w[2 * c2 + 1], (int)w[2 * c2]);
             w[2 * c2] = (uint32_t)__double2loint(tot);
             w[2 * c2 + 1] = (uint32_t)__double2hiint(tot);
           }
           ptx::tmem_st_32x32b_x32(ta, w);
           ptx::tmem_st_wait();
         }
+        first_group = false;
       }
       if (stop) break;
-      // Tile end: P = 2^(e_i + f_j) total, then the fused epilogue in FP64.
+      // Tile end: P = 2^(e_i + f_j) total, then the fused epilogue (FP64 values, FP32 residual partials).
       const int i = bi * EBM + 32 * q + lane;
       const int ei = i < n ? args.ex[i] : 0;
-      double part = 0.0;
+      float part = 0.0f;
 #pragma unroll 1
       for (int g = 0; g < 4; ++g) {
         uint32_t w[32];
@@ -309,14 +329,13 @@ __global__ void __launch_bounds__(THREADS, 1)
           if (j >= n || (SYM && i > j)) continue;
           const double P = scale2(__hiloint2double((int)w[2 * c2 + 1], (int)w[2 * c2]), ei + args.ey[j]);
           if (e.partial) {
-            const double dd = (i == j ? 1.0 : 0.0) - P;
-            part += ((SYM && i != j) ? 2.0 : 1.0) * dd * dd;
+            const float dd = (float)((i == j ? 1.0 : 0.0) - P);
+            part = fmaf((SYM && i != j) ? 2.0f * dd : dd, dd, part);
           }
           double w2 = 0.0;
           if (e.out2) {
-            w2 = e.b * P;
-            if (i == j) w2 += e.a;
-            if (e.c != 0.0) w2 += e.c * e.cin[(int64_t)i * n + j];
+            w2 = i == j ? fma(e.b, P, e.a) : e.b * P;
+            if (e.c != 0.0) w2 = fma(e.c, e.cin[(int64_t)i * n + j], w2);
           }
           const bool direct = SYM || !args.transpose, mirrored = SYM ? (i != j) : (bool)args.transpose;
           if (direct) {
@@ -331,7 +350,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       if (e.partial) {
         for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        if (lane == 0) e.partial[(int64_t)t * EPI_WARPS + (warp - 2)] = part;
+        if (lane == 0) e.partial[(int64_t)t * EPI_WARPS + (warp - 2)] = (double)part;
       }
     }
   }
