@@ -135,7 +135,7 @@ __device__ __forceinline__ double scale2(double x, int E) {
 }
 
 template <bool SYM>
-__global__ void __maxnreg__(192)
+__global__ void __launch_bounds__(THREADS, 1)
     k_gemm_emu(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, EmuArgs args) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
