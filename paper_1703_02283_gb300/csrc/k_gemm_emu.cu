@@ -65,16 +65,19 @@ __device__ __forceinline__ long long fixed_point(unsigned long long u, int e, in
   return (u >> 63) ? -F : F;
 }
 
-// One warp per row: exponent e_i, then S digit planes D[s][i][k] (s = 0 is the most significant digit).
-// Each lane handles two adjacent columns (ldl is even), so loads are 16 bytes and stores bf16x2.
-__global__ void k_slice(const double* __restrict__ X, int n, int ldl, int S, __nv_bfloat16* __restrict__ D,
-                        int* __restrict__ ex) {
+// One warp per row r of an R-row FP64 array (leading dimension ldx): exponent e_r, then S digit planes
+// D[s][r][k] (plane s at s R ldl; s = 0 is the most significant digit). Row r has row_n[r] valid columns
+// (all rows n when row_n is null); the rest of the ldl columns get digit 0. Each lane handles two adjacent
+// columns (ldl is even), so loads are 16 bytes and stores bf16x2.
+__global__ void k_slice(const double* __restrict__ X, int R, int n, int ldx, int ldl, int S,
+                        const int* __restrict__ row_n, __nv_bfloat16* __restrict__ D, int* __restrict__ ex) {
   const int lane = threadIdx.x & 31;
-  const int64_t plane = (int64_t)n * ldl;
-  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += (gridDim.x * blockDim.x) >> 5) {
-    const unsigned long long* row = reinterpret_cast<const unsigned long long*>(X + (int64_t)i * n);
+  const int64_t plane = (int64_t)R * ldl;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < R; i += (gridDim.x * blockDim.x) >> 5) {
+    const int nr = row_n ? row_n[i] : n;
+    const unsigned long long* row = reinterpret_cast<const unsigned long long*>(X + (int64_t)i * ldx);
     unsigned long long mb = 0;  // largest |x| as a bit pattern (non-negative doubles order like integers)
-    for (int k = lane; k < n; k += 32) {
+    for (int k = lane; k < nr; k += 32) {
       const unsigned long long u = row[k] & 0x7fffffffffffffffull;
       mb = u > mb ? u : mb;
     }
@@ -85,8 +88,8 @@ __global__ void k_slice(const double* __restrict__ X, int n, int ldl, int S, __n
     for (int k = 2 * lane; k < ldl; k += 64) {
       long long F0 = 0, F1 = 0;
       if (emax != 0) {
-        if (k < n) F0 = fixed_point(row[k], e, S);
-        if (k + 1 < n) F1 = fixed_point(row[k + 1], e, S);
+        if (k < nr) F0 = fixed_point(row[k], e, S);
+        if (k + 1 < nr) F1 = fixed_point(row[k + 1], e, S);
       }
       __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(D + (int64_t)i * ldl + k);
       // Balanced base-128 digits, least significant first; the last one takes the remainder (|.| <= 64).
@@ -104,15 +107,6 @@ __global__ void k_slice(const double* __restrict__ X, int n, int ldl, int S, __n
 
 // ------------------------------------------------------------------------------------------ products
 
-struct EmuArgs {
-  int n, S, T, ntiles, nchunks, KB;
-  int transpose;  // full mode: store P^T
-  Epilogue e;
-  const int* ex;  // row exponents of X
-  const int* ey;  // row exponents of Y
-  int* err;
-};
-
 __device__ __forceinline__ void tri_index_emu(int t, int T, int& bi, int& bj) {
   const double b = 2.0 * T + 1.0;
   int r = (int)floor((b - sqrt(b * b - 8.0 * (double)t)) * 0.5);
@@ -124,6 +118,46 @@ __device__ __forceinline__ void tri_index_emu(int t, int T, int& bi, int& bj) {
   bi = r;
   bj = r + (t - start(r));
 }
+
+// One matrix of a work list: its order, its first row in the packed layout, its epilogue coefficients.
+struct EmuMat {
+  int n, row0;
+  double a, b, c;
+};
+
+struct EmuArgs {
+  int S;                 // digit planes per operand
+  int R;                 // rows of one digit plane (the packed row count)
+  int ld;                // leading dimension of the FP64 outputs and of cin
+  int ntiles;            // work items
+  int T;                 // one matrix: tiles per side (items enumerated implicitly)
+  const int4* items;     // a batch: (matrix, bi, bj, -) per work item; null for one matrix
+  const EmuMat* mats;    // a batch: per-matrix data
+  EmuMat one;            // one matrix: its data
+  int transpose;         // full mode: store P^T
+  Epilogue e;            // output pointers are the bases of the (packed) FP64 buffers
+  const int* ex;         // row exponents of X (indexed by packed row)
+  const int* ey;         // row exponents of Y
+  int* err;
+};
+
+template <bool SYM>
+__device__ __forceinline__ const EmuMat& item_of(const EmuArgs& a, int t, int& bi, int& bj) {
+  if (a.items) {
+    const int4 it = a.items[t];
+    bi = it.y;
+    bj = it.z;
+    return a.mats[it.x];
+  }
+  if (SYM) {
+    tri_index_emu(t, a.T, bi, bj);
+  } else {
+    bi = t % a.T;
+    bj = t / a.T;
+  }
+  return a.one;
+}
+
 
 // x * 2^E for a finite double, by adding to the exponent field when the result stays normal.
 __device__ __forceinline__ double scale2(double x, int E) {
@@ -144,7 +178,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * ESTAGES + 5);
   volatile int* s_abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
-  const int n = args.n, S = args.S, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int S = args.S, R = args.R, ld = args.ld, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t full0 = ptx::smem_u32(bars), empty0 = full0 + 8 * ESTAGES, tfull0 = empty0 + 8 * ESTAGES,
                  tempty0 = tfull0 + 16, drain = tempty0 + 16;
 
@@ -179,12 +213,12 @@ __global__ void __launch_bounds__(THREADS, 1)
       bool stop = false;
       for (int t = blockIdx.x; t < args.ntiles && !stop; t += gridDim.x) {
         int bi, bj;
-        if (SYM) tri_index_emu(t, args.T, bi, bj);
-        else { bi = t % args.T; bj = t / args.T; }
+        const EmuMat& mt = item_of<SYM>(args, t, bi, bj);
+        const int KB = (mt.n + EBK - 1) / EBK;
         for (int L = 2; L <= S + 1 && !stop; ++L)
           for (int s = 1; s <= L - 1 && !stop; ++s) {
-            const int ya = (s - 1) * n + bi * EBM, yb = (L - s - 1) * n + bj * EBN;
-            for (int kb = 0; kb < args.KB; ++kb, ++it) {
+            const int ya = (s - 1) * R + mt.row0 + bi * EBM, yb = (L - s - 1) * R + mt.row0 + bj * EBN;
+            for (int kb = 0; kb < KB; ++kb, ++it) {
               const int st = it % ESTAGES;
               if (*s_abort || !ptx::mbar_wait(empty0 + 8 * st, ((it / ESTAGES) & 1) ^ 1, args.err, 11)) {
                 *s_abort = 1;
@@ -208,10 +242,13 @@ __global__ void __launch_bounds__(THREADS, 1)
       // ---------------- MMA issuer: one "unit" = one pair over one K chunk, into TMEM buffer (unit & 1)
       int it = 0, u = 0;
       bool stop = false;
-      for (int t = blockIdx.x; t < args.ntiles && !stop; t += gridDim.x)
+      for (int t = blockIdx.x; t < args.ntiles && !stop; t += gridDim.x) {
+        int bi, bj;
+        const EmuMat& mt = item_of<SYM>(args, t, bi, bj);
+        const int KB = (mt.n + EBK - 1) / EBK, nchunks = (KB + KCHUNK_BLOCKS - 1) / KCHUNK_BLOCKS;
         for (int L = 2; L <= S + 1 && !stop; ++L)
           for (int s = 1; s <= L - 1 && !stop; ++s)
-            for (int c = 0; c < args.nchunks && !stop; ++c, ++u) {
+            for (int c = 0; c < nchunks && !stop; ++c, ++u) {
               const int b = u & 1;
               if (*s_abort || !ptx::mbar_wait(tempty0 + 8 * b, ((u >> 1) & 1) ^ 1, args.err, 12)) {
                 *s_abort = 1;
@@ -220,8 +257,7 @@ __global__ void __launch_bounds__(THREADS, 1)
               }
               ptx::tc_fence_after();
               const uint32_t d = tmem + (uint32_t)(b * EBN);
-              const int kb0 = c * KCHUNK_BLOCKS, kb1 = min(args.KB, kb0 + KCHUNK_BLOCKS);
-              // The producer streams every K block of the pair in order; skip to this chunk's blocks.
+              const int kb0 = c * KCHUNK_BLOCKS, kb1 = min(KB, kb0 + KCHUNK_BLOCKS);
               for (int kb = kb0; kb < kb1; ++kb) {
                 const int cur = it + (kb - kb0);
                 const int st = cur % ESTAGES;
@@ -242,6 +278,7 @@ __global__ void __launch_bounds__(THREADS, 1)
               if (stop) break;
               ptx::mma_commit(tfull0 + 8 * b);
             }
+      }
       ptx::mma_commit(drain);
       ptx::mbar_wait(drain, 0, nullptr, 0);
     }
@@ -256,8 +293,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     bool stop = false;
     for (int t = blockIdx.x; t < args.ntiles && !stop; t += gridDim.x) {
       int bi, bj;
-      if (SYM) tri_index_emu(t, args.T, bi, bj);
-      else { bi = t % args.T; bj = t / args.T; }
+      const EmuMat& mt = item_of<SYM>(args, t, bi, bj);
+      const int n = mt.n, row0 = mt.row0;
+      const int nchunks = ((n + EBK - 1) / EBK + KCHUNK_BLOCKS - 1) / KCHUNK_BLOCKS;
       bool first_group = true;
       for (int g0 = 2; g0 <= S + 1 && !stop; g0 += kGroup) {
         const int glast = min(g0 + kGroup - 1, S + 1);
@@ -267,7 +305,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int L = g0; L <= glast && !stop; ++L) {
           const int shift = 7 * (glast - L);
           for (int s = 1; s <= L - 1 && !stop; ++s)
-            for (int c = 0; c < args.nchunks; ++c, ++u) {
+            for (int c = 0; c < nchunks; ++c, ++u) {
               if (__shfl_sync(0xffffffffu, *s_abort, 0)) { stop = true; break; }
               const int b = u & 1;
               if (!__all_sync(0xffffffffu, ptx::mbar_wait(tfull0 + 8 * b, (u >> 1) & 1, args.err, 14))) {
@@ -315,7 +353,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (stop) break;
       // Tile end: P = 2^(e_i + f_j) total, then the fused epilogue (FP64 values, FP32 residual partials).
       const int i = bi * EBM + 32 * q + lane;
-      const int ei = i < n ? args.ex[i] : 0;
+      const int ei = i < n ? args.ex[row0 + i] : 0;
       float part = 0.0f;
 #pragma unroll 1
       for (int g = 0; g < 4; ++g) {
@@ -327,24 +365,25 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int c2 = 0; c2 < 16; ++c2) {
           const int j = bj * EBN + 64 * h + 16 * g + c2;
           if (j >= n || (SYM && i > j)) continue;
-          const double P = scale2(__hiloint2double((int)w[2 * c2 + 1], (int)w[2 * c2]), ei + args.ey[j]);
+          const double P = scale2(__hiloint2double((int)w[2 * c2 + 1], (int)w[2 * c2]), ei + args.ey[row0 + j]);
           if (e.partial) {
             const float dd = (float)((i == j ? 1.0 : 0.0) - P);
             part = fmaf((SYM && i != j) ? 2.0f * dd : dd, dd, part);
           }
+          const int64_t ij = (int64_t)(row0 + i) * ld + j, ji = (int64_t)(row0 + j) * ld + i;
           double w2 = 0.0;
           if (e.out2) {
-            w2 = i == j ? fma(e.b, P, e.a) : e.b * P;
-            if (e.c != 0.0) w2 = fma(e.c, e.cin[(int64_t)i * n + j], w2);
+            w2 = i == j ? fma(mt.b, P, mt.a) : mt.b * P;
+            if (mt.c != 0.0) w2 = fma(mt.c, e.cin[ij], w2);
           }
           const bool direct = SYM || !args.transpose, mirrored = SYM ? (i != j) : (bool)args.transpose;
           if (direct) {
-            if (e.out) e.out[(int64_t)i * n + j] = P;
-            if (e.out2) e.out2[(int64_t)i * n + j] = w2;
+            if (e.out) e.out[ij] = P;
+            if (e.out2) e.out2[ij] = w2;
           }
           if (mirrored) {
-            if (e.out) e.out[(int64_t)j * n + i] = P;
-            if (e.out2) e.out2[(int64_t)j * n + i] = w2;
+            if (e.out) e.out[ji] = P;
+            if (e.out2) e.out2[ji] = w2;
           }
         }
       }
@@ -372,12 +411,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn_emu() {
   return fn;
 }
 
-// The S digit planes of an operand stacked as an (S n) x n BF16 matrix (leading dimension ldl); boxes of
-// 64 (K) x 128 rows. Columns k >= n are outside the tensor and read as zero.
-cudaError_t make_slice_map(CUtensorMap* map, const __nv_bfloat16* ptr, int n, int ldl, int S) {
+// The S digit planes of an operand stacked as an (S R) x K BF16 matrix (leading dimension ldl); boxes of
+// 64 (K) x 128 rows. Columns k >= K are outside the tensor and read as zero.
+cudaError_t make_slice_map(CUtensorMap* map, const __nv_bfloat16* ptr, int K, int R, int ldl, int S) {
   auto fn = encode_fn_emu();
   if (!fn) return cudaErrorNotSupported;
-  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)S * (cuuint64_t)n};
+  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)S * (cuuint64_t)R};
   cuuint64_t strides[1] = {(cuuint64_t)ldl * 2};
   cuuint32_t box[2] = {(cuuint32_t)EBK, (cuuint32_t)EBM};
   cuuint32_t estr[2] = {1, 1};
@@ -397,52 +436,27 @@ int sm_count_emu() {
   return count;
 }
 
-}  // namespace
-
-int emu_tiles(int n, Mode mode) {
-  const int T = (n + EBM - 1) / EBM;
-  return (mode == Mode::Sym ? T * (T + 1) / 2 : T * T) * EPI_WARPS;  // one partial per epilogue warp and tile
-}
-
-cudaError_t slice(const double* X, int n, int ldl, int S, __nv_bfloat16* D, int* ex, cudaStream_t s) {
-  int blocks = (n + 7) / 8;  // 8 warps (rows) per block
-  if (blocks > 152 * 8) blocks = 152 * 8;
-  k_slice<<<blocks, 256, 0, s>>>(X, n, ldl, S, D, ex);
-  return cudaGetLastError();
-}
-
-cudaError_t gemm_emu(const __nv_bfloat16* DX, const int* ex, const __nv_bfloat16* DY, const int* ey, int n, int ldl,
-                     int S, Mode mode, bool transpose, const Epilogue& e, int* err, cudaStream_t s) {
-  if (S < 1 || S > 9 || ldl % 8 != 0 || ldl < n) return cudaErrorInvalidValue;
+cudaError_t launch_emu(const __nv_bfloat16* DX, const __nv_bfloat16* DY, int K, int ldl, Mode mode, EmuArgs& a,
+                       cudaStream_t s) {
+  if (a.S < 1 || a.S > 9 || ldl % 8 != 0 || ldl < K) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(DX) | reinterpret_cast<uintptr_t>(DY)) & 15) return cudaErrorMisalignedAddress;
-  if ((int64_t)S * n > (int64_t)1 << 31) return cudaErrorInvalidValue;
-  // The int32 level sums hold up to S pairs of K-sums of n terms, each term at most 64 * 64.
-  if ((int64_t)S * n * 4096 >= (int64_t)1 << 31) return cudaErrorInvalidValue;
+  if ((int64_t)a.S * a.R > (int64_t)1 << 31) return cudaErrorInvalidValue;
+  // The int32 level sums hold up to S pairs of K-sums of K terms, each term at most 64 * 64.
+  if ((int64_t)a.S * K * 4096 >= (int64_t)1 << 31) return cudaErrorInvalidValue;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t a = cudaFuncSetAttribute(k_gemm_emu<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (a != cudaSuccess) return a;
-    a = cudaFuncSetAttribute(k_gemm_emu<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (a != cudaSuccess) return a;
+    cudaError_t r = cudaFuncSetAttribute(k_gemm_emu<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (r != cudaSuccess) return r;
+    r = cudaFuncSetAttribute(k_gemm_emu<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (r != cudaSuccess) return r;
     attr_set = true;
   }
+  if (a.ntiles == 0) return cudaSuccess;
   CUtensorMap mx, my;
-  cudaError_t r = make_slice_map(&mx, DX, n, ldl, S);
+  cudaError_t r = make_slice_map(&mx, DX, K, a.R, ldl, a.S);
   if (r != cudaSuccess) return r;
-  r = make_slice_map(&my, DY, n, ldl, S);
+  r = make_slice_map(&my, DY, K, a.R, ldl, a.S);
   if (r != cudaSuccess) return r;
-  EmuArgs a;
-  a.n = n;
-  a.S = S;
-  a.T = (n + EBM - 1) / EBM;
-  a.ntiles = mode == Mode::Sym ? a.T * (a.T + 1) / 2 : a.T * a.T;
-  a.KB = (n + EBK - 1) / EBK;
-  a.nchunks = (a.KB + KCHUNK_BLOCKS - 1) / KCHUNK_BLOCKS;
-  a.transpose = transpose ? 1 : 0;
-  a.e = e;
-  a.ex = ex;
-  a.ey = ey;
-  a.err = err;
   const int grid = a.ntiles < sm_count_emu() ? a.ntiles : sm_count_emu();
   if (mode == Mode::Sym) {
     k_gemm_emu<true><<<grid, THREADS, SMEM_BYTES, s>>>(mx, my, a);
@@ -450,6 +464,67 @@ cudaError_t gemm_emu(const __nv_bfloat16* DX, const int* ex, const __nv_bfloat16
     k_gemm_emu<false><<<grid, THREADS, SMEM_BYTES, s>>>(mx, my, a);
   }
   return cudaGetLastError();
+}
+
+}  // namespace
+
+int emu_tiles(int n, Mode mode) {
+  const int T = (n + EBM - 1) / EBM;
+  return (mode == Mode::Sym ? T * (T + 1) / 2 : T * T) * EPI_WARPS;  // one partial per epilogue warp and tile
+}
+
+int emu_partials_per_item() { return EPI_WARPS; }
+
+cudaError_t slice(const double* X, int n, int ldl, int S, __nv_bfloat16* D, int* ex, cudaStream_t s) {
+  return slice_rows(X, n, n, n, ldl, S, nullptr, D, ex, s);
+}
+
+cudaError_t slice_rows(const double* X, int R, int n, int ldx, int ldl, int S, const int* row_n, __nv_bfloat16* D,
+                       int* ex, cudaStream_t s) {
+  int blocks = (R + 7) / 8;  // 8 warps (rows) per block
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks < 1) return cudaSuccess;
+  k_slice<<<blocks, 256, 0, s>>>(X, R, n, ldx, ldl, S, row_n, D, ex);
+  return cudaGetLastError();
+}
+
+cudaError_t gemm_emu(const __nv_bfloat16* DX, const int* ex, const __nv_bfloat16* DY, const int* ey, int n, int ldl,
+                     int S, Mode mode, bool transpose, const Epilogue& e, int* err, cudaStream_t s) {
+  EmuArgs a{};
+  a.S = S;
+  a.R = n;
+  a.ld = n;
+  a.T = (n + EBM - 1) / EBM;
+  a.ntiles = mode == Mode::Sym ? a.T * (a.T + 1) / 2 : a.T * a.T;
+  a.items = nullptr;
+  a.mats = nullptr;
+  a.one = EmuMat{n, 0, e.a, e.b, e.c};
+  a.transpose = transpose ? 1 : 0;
+  a.e = e;
+  a.ex = ex;
+  a.ey = ey;
+  a.err = err;
+  return launch_emu(DX, DY, n, ldl, mode, a, s);
+}
+
+cudaError_t gemm_emu_batched(const __nv_bfloat16* DX, const int* ex, const __nv_bfloat16* DY, const int* ey, int R,
+                             int K, int ldl, int ld, int S, Mode mode, bool transpose, const int4* items, int nitems,
+                             const EmuBatchMat* mats, const Epilogue& e, int* err, cudaStream_t s) {
+  static_assert(sizeof(EmuBatchMat) == sizeof(EmuMat), "batch matrix record");
+  EmuArgs a{};
+  a.S = S;
+  a.R = R;
+  a.ld = ld;
+  a.T = 0;
+  a.ntiles = nitems;
+  a.items = items;
+  a.mats = reinterpret_cast<const EmuMat*>(mats);
+  a.transpose = transpose ? 1 : 0;
+  a.e = e;
+  a.ex = ex;
+  a.ey = ey;
+  a.err = err;
+  return launch_emu(DX, DY, K, ldl, mode, a, s);
 }
 
 }  // namespace pr

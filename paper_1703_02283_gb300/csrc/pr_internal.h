@@ -74,9 +74,25 @@ cudaError_t gemm_bf16_tc(const __nv_bfloat16* X, const __nv_bfloat16* Y, int n, 
 // slice(): X (n x n FP64) -> S digit planes D (S x n x ldl BF16, most significant first) and row exponents ex.
 // gemm_emu(): P = X Y^T from the slices of X and Y, FP64 epilogue (out / out2 / partial; no BF16 copies).
 int emu_tiles(int n, Mode mode);
+int emu_partials_per_item();
 cudaError_t slice(const double* X, int n, int ldl, int S, __nv_bfloat16* D, int* ex, cudaStream_t s);
+// Slices R rows of an FP64 array with leading dimension ldx; row r has row_n[r] valid columns (n if null).
+cudaError_t slice_rows(const double* X, int R, int n, int ldx, int ldl, int S, const int* row_n, __nv_bfloat16* D,
+                       int* ex, cudaStream_t s);
 cudaError_t gemm_emu(const __nv_bfloat16* DX, const int* ex, const __nv_bfloat16* DY, const int* ey, int n, int ldl,
                      int S, Mode mode, bool transpose, const Epilogue& e, int* err, cudaStream_t s);
+
+// A batch of matrices packed row-wise in shared buffers (leading dimension ld for FP64, ldl for digit
+// planes; R packed rows per plane; K the largest order). Work item = (matrix, bi, bj, unused), 128 x 128
+// tiles; per-matrix record = {order, first packed row, epilogue a, b, c}. One residual partial per epilogue
+// warp and item (emu_partials_per_item() per item, in item order).
+struct EmuBatchMat {
+  int n, row0;
+  double a, b, c;
+};
+cudaError_t gemm_emu_batched(const __nv_bfloat16* DX, const int* ex, const __nv_bfloat16* DY, const int* ey, int R,
+                             int K, int ldl, int ld, int S, Mode mode, bool transpose, const int4* items, int nitems,
+                             const EmuBatchMat* mats, const Epilogue& e, int* err, cudaStream_t s);
 
 // ---- elementwise and reductions (k_elementwise.cu)
 // scal[0] = max |a_ij|, scal[1] = max |a_ij - a_ji|, scal[2] = #non-finite, scal[3] = #non-positive diagonal
