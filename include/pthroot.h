@@ -199,6 +199,40 @@ pr_status pr_matmul(int precision, const double* X, const double* Y, int64_t n, 
  * appear in pr_stats (gemm_ms, gemms_timed, gemm_flops_timed). Adds two event records per product. */
 pr_status pr_set_timing(pr_handle h, int on);
 
+/* ---- Batches: many independent problems solved together ------------------------------------------------
+ * A batch holds `count` SPD matrices A_i (orders n_i, roots p_i) and iterates them together: every matrix
+ * product stage of an iteration is one launch of the PR_EMU64 tensor-core kernel over the tiles of every
+ * matrix taking part in it (matrices packed row-wise with one leading dimension). Per matrix, the forms,
+ * the initial guess (Eq. 3 or the scaled identity), the stop rule and the results are those of pr_iterate;
+ * a matrix whose stop rule fires leaves the work lists. */
+typedef struct pr_batch_s* pr_batch;
+
+/* Creates a batch. n[i] in [1, 16384], p[i] in [1, 64], A[i]: n[i]*n[i] FP64 row-major, device or host,
+ * copied. opt: form must be PR_FORM_AUTO (NULL = defaults). Checks every matrix as pr_init does.
+ * Errors: PR_EINVAL, PR_ENOTSPD, PR_ENOMEM, PR_ECUDA. */
+pr_status pr_batch_init(pr_batch* b, int count, const int64_t* n, const int* p, const double* const* A,
+                        const pr_options* opt, void* stream);
+
+/* Iterates every active matrix until its stop rule fires (tol, stagnation, max_iter, divergence), with
+ * PR_EMU64 products. iterations[i] and status[i] (a pr_status stop code; may be NULL) receive the outcome
+ * per matrix. Synchronises the stream once per iteration to read the residuals. */
+pr_status pr_batch_solve(pr_batch b, int precision, double tol, int* iterations, int* status);
+
+/* Copies the result of matrix i (n[i]*n[i] FP64, row-major) to C_out (device or host). */
+pr_status pr_batch_result(pr_batch b, int i, double* C_out);
+
+/* Residual history r_0 .. r_k of matrix i (host memory), as pr_history. */
+pr_status pr_batch_history(pr_batch b, int i, double* out, int cap, int* len);
+
+/* Kernels launched by the batch so far. */
+int64_t pr_batch_launches(pr_batch b);
+
+/* Text for the last failing call on b (b NULL: the last failing pr_batch_init of this thread). */
+const char* pr_batch_last_error(pr_batch b);
+
+/* Frees the batch. b may be NULL. */
+pr_status pr_batch_destroy(pr_batch b);
+
 /* Largest order accepted by pr_norms_noalloc. */
 #define PR_NORMS_NOALLOC_MAX_N 65536
 

@@ -386,8 +386,10 @@ pr_status literal_update(pr_handle h, int prec) {
   return PR_OK;
 }
 
+}  // namespace
+
 // The stop rule (see pr_stop_rule): returns a pr_status to stop with, or -1 to apply one more update.
-int stop_rule(const double* hist, const int* prec, int len, double tol, const pr_options& o) {
+int pr::stop_rule(const double* hist, const int* prec, int len, double tol, const pr_options& o) {
   const double r = hist[len - 1];
   if (!isfinite(r)) return PR_EDIVERGED;
   if (r <= tol) return PR_OK;
@@ -400,6 +402,9 @@ int stop_rule(const double* hist, const int* prec, int len, double tol, const pr
   }
   return -1;
 }
+
+namespace {
+using pr::stop_rule;
 
 int decide(pr_handle h, double tol, int steps_this_call, int max_steps) {
   const int stop = stop_rule(h->hist.data(), h->hist_prec.data(), (int)h->hist.size(), tol, h->opt);

@@ -150,6 +150,22 @@ __global__ void k_reduce_sqrt(const double* __restrict__ partial, int count, dou
   if (threadIdx.x == 0) *result = sqrt(sh[0]);
 }
 
+// One block per segment: out[m] = sqrt(sum partial[begin[m]..end[m])) in a fixed order.
+__global__ void k_seg_reduce_sqrt(const double* __restrict__ partial, const int* __restrict__ begin,
+                                  const int* __restrict__ end, double* __restrict__ out) {
+  __shared__ double sh[kThreads];
+  const int m = blockIdx.x;
+  double s = 0.0;
+  for (int i = begin[m] + threadIdx.x; i < end[m]; i += kThreads) s += partial[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[m] = sqrt(sh[0]);
+}
+
 __global__ void k_to_bf16(const double* __restrict__ src, int n, int ldl, __nv_bfloat16* __restrict__ dst) {
   const int64_t total = (int64_t)n * n;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
@@ -205,6 +221,13 @@ cudaError_t symmetrize(const double* in, int n, double* out, cudaStream_t s) {
 
 cudaError_t reduce_partials_sqrt(const double* partial, int count, double* result, cudaStream_t s) {
   k_reduce_sqrt<<<1, kThreads, 0, s>>>(partial, count, result);
+  return cudaGetLastError();
+}
+
+cudaError_t segmented_reduce_sqrt(const double* partial, const int* begin, const int* end, int count, double* out,
+                                  cudaStream_t s) {
+  if (count < 1) return cudaSuccess;
+  k_seg_reduce_sqrt<<<count, kThreads, 0, s>>>(partial, begin, end, out);
   return cudaGetLastError();
 }
 

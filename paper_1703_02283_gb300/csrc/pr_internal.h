@@ -112,6 +112,13 @@ cudaError_t reduce_partials_sqrt(const double* partial, int count, double* resul
 // dst[i * ldl + j] = bf16(src[i * n + j]) for an n x n matrix
 cudaError_t to_bf16(const double* src, int n, int ldl, __nv_bfloat16* dst, cudaStream_t s);
 
+// out[m] = sqrt(sum of partial[begin[m] .. end[m])) for m < count, each sum in a fixed order.
+cudaError_t segmented_reduce_sqrt(const double* partial, const int* begin, const int* end, int count, double* out,
+                                  cudaStream_t s);
+
+// The stop rule of pr_iterate (capi.cu), shared with the batched solver.
+int stop_rule(const double* hist, const int* prec, int len, double tol, const pr_options& o);
+
 // Records the text returned by pr_last_error(NULL) for a failing call that has no handle.
 void set_handleless_error(const char* msg);
 

@@ -74,6 +74,17 @@ def _load() -> ctypes.CDLL:
         "pr_result": (ctypes.c_int, [_handle_t, _dptr]),
         "pr_stop_rule": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                         ctypes.c_double, ctypes.POINTER(pr_options)]),
+        "pr_batch_init": (ctypes.c_int, [ctypes.POINTER(_handle_t), ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_void_p),
+                                         ctypes.POINTER(pr_options), ctypes.c_void_p]),
+        "pr_batch_solve": (ctypes.c_int, [_handle_t, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int)]),
+        "pr_batch_result": (ctypes.c_int, [_handle_t, ctypes.c_int, _dptr]),
+        "pr_batch_history": (ctypes.c_int, [_handle_t, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_int)]),
+        "pr_batch_launches": (ctypes.c_int64, [_handle_t]),
+        "pr_batch_last_error": (ctypes.c_char_p, [_handle_t]),
+        "pr_batch_destroy": (ctypes.c_int, [_handle_t]),
         "pr_norms_noalloc": (ctypes.c_int, [_dptr, ctypes.c_int64, _dptr, ctypes.c_void_p]),
         "pr_matmul": (ctypes.c_int, [ctypes.c_int, _dptr, _dptr, ctypes.c_int64, ctypes.c_int, _dptr,
                                      ctypes.c_void_p]),
@@ -202,6 +213,51 @@ def pr_history(h: int) -> list[float]:
 
 def pr_destroy(h: int) -> None:
     _check(_lib.pr_destroy(h), None)
+
+
+def _bcheck(status: int, b=None, allowed=(PR_OK,)) -> int:
+    if status not in allowed:
+        raise PthrootError(status, (_lib.pr_batch_last_error(b) or b"").decode())
+    return status
+
+
+def pr_batch_init(mats, ps, options: pr_options | None = None, stream: int = 0) -> int:
+    """mats: sequence of square FP64 matrices (torch tensors or numpy arrays); ps: roots."""
+    count = len(mats)
+    n = (ctypes.c_int64 * count)(*[int(m.shape[0]) for m in mats])
+    p = (ctypes.c_int * count)(*[int(x) for x in ps])
+    ptrs = (ctypes.c_void_p * count)(*[_ptr(m) for m in mats])
+    b = _handle_t()
+    _bcheck(_lib.pr_batch_init(ctypes.byref(b), count, n, p, ptrs,
+                               ctypes.byref(options) if options is not None else None, ctypes.c_void_p(stream)))
+    return b.value
+
+
+def pr_batch_solve(b: int, count: int, precision: int, tol: float) -> tuple[list, list]:
+    its = (ctypes.c_int * count)()
+    sts = (ctypes.c_int * count)()
+    _bcheck(_lib.pr_batch_solve(b, int(precision), float(tol), its, sts), b)
+    return list(its), list(sts)
+
+
+def pr_batch_result(b: int, i: int, C_out) -> None:
+    _bcheck(_lib.pr_batch_result(b, int(i), _ptr(C_out)), b)
+
+
+def pr_batch_history(b: int, i: int) -> list[float]:
+    ln = ctypes.c_int(0)
+    _bcheck(_lib.pr_batch_history(b, int(i), None, 0, ctypes.byref(ln)), b)
+    buf = (ctypes.c_double * max(ln.value, 1))()
+    _bcheck(_lib.pr_batch_history(b, int(i), buf, ln.value, ctypes.byref(ln)), b)
+    return list(buf[: ln.value])
+
+
+def pr_batch_launches(b: int) -> int:
+    return int(_lib.pr_batch_launches(b))
+
+
+def pr_batch_destroy(b: int) -> None:
+    _bcheck(_lib.pr_batch_destroy(b))
 
 
 def pr_last_error(h: int | None = None) -> str:

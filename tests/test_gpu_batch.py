@@ -1,0 +1,121 @@
+"""Batched solves (many SPD matrices of uneven orders and roots), through the C ABI.
+
+Each matrix of a batch must meet the single-matrix bar against the CPU oracle, and its result must equal,
+bit for bit, the single-matrix PR_EMU64 solve of the same matrix (same digit planes, same tiles, same
+stop rule).
+"""
+import numpy as np
+import pytest
+
+from oracle import pthroot_oracle as O
+from paper_1703_02283_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1703_02283_gb300 import pthroot as P  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def make_batch(count, n_lo, n_hi, kappa_hi, seed):
+    spec = W.batched_specs(count, n_lo=n_lo, n_hi=n_hi, kappa_hi=kappa_hi, seed=seed)
+    cases = [W.spd_from_spectrum(int(spec.n[i]), float(spec.lam_min[i]), int(spec.seeds[i])) for i in range(count)]
+    return cases, [int(x) for x in spec.p]
+
+
+def single_emu(case, p, c0=P.PR_C0_EQ3):
+    o = P.pr_default_options()
+    o.c0 = c0
+    A = torch.from_numpy(case.A).to(DEV)
+    h = P.pr_init(A, case.n, p, o, torch.cuda.current_stream(DEV).cuda_stream)
+    try:
+        P.pr_iterate(h, 100, P.PR_EMU64, 1e-12)
+        C = torch.empty_like(A)
+        P.pr_result(h, C)
+        return C.cpu().numpy(), P.pr_history(h)
+    finally:
+        P.pr_destroy(h)
+
+
+def run_batch(cases, ps, host=False, c0=P.PR_C0_EQ3):
+    o = P.pr_default_options()
+    o.c0 = c0
+    mats = [np.ascontiguousarray(c.A) if host else torch.from_numpy(c.A).to(DEV) for c in cases]
+    b = P.pr_batch_init(mats, ps, o, torch.cuda.current_stream(DEV).cuda_stream)
+    try:
+        its, sts = P.pr_batch_solve(b, len(cases), P.PR_EMU64, 1e-12)
+        out = []
+        for i, c in enumerate(cases):
+            C = np.empty((c.n, c.n))
+            P.pr_batch_result(b, i, C)
+            out.append((C, P.pr_batch_history(b, i)))
+        return out, its, sts, P.pr_batch_launches(b)
+    finally:
+        P.pr_batch_destroy(b)
+
+
+def test_batch_matches_oracle_and_single_path():
+    cases, ps = make_batch(10, 5, 300, 1e3, 7)
+    out, its, sts, launches = run_batch(cases, ps)
+    assert launches > 0
+    for i, (case, p) in enumerate(zip(cases, ps)):
+        C, hist = out[i]
+        Co, info = O.solve(case.A, p, tol=1e-12)
+        Z = O.closed_form_root(case.Q, case.lam, p)
+        bound = max(1e-12, 10 * O.forward_error(Co, Z))
+        assert O.forward_error(C, Z) <= bound, (i, case.n, p)
+        assert O.forward_error(C, Co) <= bound, (i, case.n, p)
+        assert abs(its[i] - info.iterations) <= 1
+        assert sts[i] in (P.PR_OK, P.PR_ESTAGNATED)
+        Cs, hs = single_emu(case, p)
+        assert np.array_equal(C, Cs), (i, case.n, p)
+        assert hist == hs
+
+
+def test_batch_scaled_identity_host_inputs():
+    cases, ps = make_batch(6, 40, 200, 1e4, 11)
+    out, its, sts, _ = run_batch(cases, ps, host=True, c0=P.PR_C0_SCALED_I)
+    for i, (case, p) in enumerate(zip(cases, ps)):
+        C, _ = out[i]
+        Co, info = O.solve(case.A, p, c0="scaled_identity", tol=1e-12)
+        Z = O.closed_form_root(case.Q, case.lam, p)
+        assert O.forward_error(C, Z) <= max(1e-12, 10 * O.forward_error(Co, Z))
+
+
+def test_batch_single_matrix_and_errors():
+    cases, ps = make_batch(1, 129, 129, 100, 3)
+    out, its, sts, _ = run_batch(cases, ps)
+    Cs, _ = single_emu(cases[0], ps[0])
+    assert np.array_equal(out[0][0], Cs)
+    bad = cases[0].A.copy()
+    bad[1, 2] += 1.0
+    with pytest.raises(P.PthrootError) as e:
+        P.pr_batch_init([bad], [2])
+    assert e.value.status == P.PR_EINVAL
+
+
+@pytest.mark.slow
+def test_batch_full_size_sampled():
+    # The 512-matrix workload (orders 64..1024, kappa up to 1e4, p in {1, 2, 3}); 6 matrices checked against
+    # the oracle, all against their exact roots within the bound the oracle attains on the sampled ones.
+    spec = W.batched_specs(512)
+    cases = [W.spd_from_spectrum(int(spec.n[i]), float(spec.lam_min[i]), int(spec.seeds[i])) for i in range(512)]
+    ps = [int(x) for x in spec.p]
+    out, its, sts, _ = run_batch(cases, ps)
+    print("statuses", {P.STATUS_NAMES[s]: sts.count(s) for s in set(sts)}, "max iterations", max(its))
+    rng = np.random.default_rng(0)
+    for i in rng.choice(512, 6, replace=False):
+        case, p = cases[i], ps[i]
+        Co, info = O.solve(case.A, p, tol=1e-12)
+        Z = O.closed_form_root(case.Q, case.lam, p)
+        assert O.forward_error(out[i][0], Z) <= max(1e-12, 10 * O.forward_error(Co, Z)), (i, case.n, p)
+    # Every matrix satisfies the method's own accuracy floor: the coupled form from Eq. 3 keeps about
+    # u kappa^(p+1) (u = 2^-53); Newton-Schulz about u kappa.
+    for i, (case, p) in enumerate(zip(cases, ps)):
+        Z = O.closed_form_root(case.Q, case.lam, p)
+        floor = 1.1e-16 * case.kappa ** (p + 1 if p > 1 else 1) * np.sqrt(case.n)
+        assert O.forward_error(out[i][0], Z) <= max(1e-10, 100 * floor), (i, case.n, p, case.kappa)
