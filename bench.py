@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="single", choices=["single", "batched"],
+                    help="single: the n=4096 matrix for every p; batched: 512 matrices, n in [64, 1024]")
+    ap.add_argument("--count", type=int, default=512, help="batched: number of matrices")
     return ap.parse_args()
 
 
@@ -183,9 +186,121 @@ def run_reference(args, ps):
 
 # ----------------------------------------------------------------------------- GPU arm
 
+def batched_cases(count):
+    spec = W.batched_specs(count)
+    cases = [W.spd_from_spectrum(int(spec.n[i]), float(spec.lam_min[i]), int(spec.seeds[i])) for i in range(count)]
+    return cases, [int(x) for x in spec.p]
+
+
+def batched_config(args):
+    return {"workload": f"batched: {args.count} SPD matrices, n uniform in [64, 1024], kappa log-uniform in "
+                        f"[10, 1e4], p in {{1, 2, 3}} (seeds 1000+i), Eq.3 C_0, tol {args.tol:g}",
+            "count": args.count, "mode": "emu64",
+            "l2": "inputs larger than L2: packed working set of several GiB"}
+
+
+def oracle_batched_sample(cases, ps, its, k=3):
+    """Oracle time on k matrices (setup + 1, 2 updates each), scaled to the batch by sum(n^3 iterations)."""
+    rng = np.random.default_rng(1)
+    idx = rng.choice(len(cases), k, replace=False)
+    t = 0.0
+    for i in idx:
+        est, _ = oracle_sample(cases[i].A, ps[i], its[i])
+        t += est
+    work = lambda i: cases[i].n ** 3 * max(its[i], 1)  # noqa: E731
+    scale = sum(work(i) for i in range(len(cases))) / sum(work(i) for i in idx)
+    return t * scale, f"oracle on {k} of {len(cases)} matrices (setup + 1 and + 2 updates each), scaled by n^3 x iterations"
+
+
+def run_batched(args):
+    import torch
+
+    from paper_1703_02283_gb300 import pthroot as P
+    if args.impl == "reference":
+        if int(os.environ.get("RANK", "0")) != 0:
+            return
+        cases, ps = batched_cases(args.count)
+        its = [predicted_iterations(c, p, args.tol) for c, p in zip(cases, ps)]
+        vals = []
+        for _ in range(args.warmup + args.steps):
+            v, what = oracle_batched_sample(cases, ps, its)
+            vals.append(v)
+        value = float(np.mean(vals[args.warmup:]))
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": value,
+                          "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic", "config": batched_config(args),
+                          "cpu_baseline": {"value": value, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+                                           "sample": what},
+                          "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    cases, ps = batched_cases(args.count)
+    mats = [torch.from_numpy(c.A).to(dev) for c in cases]
+    nbytes = sum(c.n * c.n * 8 for c in cases)
+
+    def one(inputs):
+        b = P.pr_batch_init(inputs, ps, P.pr_default_options(), stream.cuda_stream)
+        its, sts = P.pr_batch_solve(b, len(cases), P.PR_EMU64, args.tol)
+        outs = []
+        for i, c in enumerate(cases):
+            C = torch.empty((c.n, c.n), dtype=torch.float64, device=dev) if inputs is mats else \
+                torch.empty((c.n, c.n), dtype=torch.float64).pin_memory()
+            P.pr_batch_result(b, i, C)
+            outs.append(C)
+        launches = P.pr_batch_launches(b)
+        P.pr_batch_destroy(b)
+        return its, sts, outs, launches
+
+    for _ in range(args.warmup):
+        one(mats)
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        runs = [one(mats) for _ in range(args.steps)]
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    its, sts, outs, launches = runs[-1]
+    errs = []
+    for i, c in enumerate(cases):
+        Z = (c.Q * c.lam ** (-1.0 / ps[i])) @ c.Q.T
+        errs.append(float(np.linalg.norm(outs[i].cpu().numpy() - Z) / np.linalg.norm(Z)))
+    e2e = None
+    if not args.no_e2e:
+        host = [c.A.copy() for c in cases]
+        host = [torch.from_numpy(h).pin_memory() for h in host]
+        t0 = time.perf_counter()
+        one(host)
+        e2e = {"value": (time.perf_counter() - t0) * 1e3, "unit": "ms", "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes}
+    cpu = None
+    if not args.no_cpu_baseline:
+        v, what = oracle_batched_sample(cases, ps, its)
+        cpu = {"value": v, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle", "sample": what}
+    stat = {}
+    for s_ in sts:
+        stat[P.STATUS_NAMES[s_]] = stat.get(P.STATUS_NAMES[s_], 0) + 1
+    line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "emu64(bf16 slices)", "data": "synthetic", "config": batched_config(args),
+            "roofline": None, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * args.steps,
+            "clocks": clk.summary(),
+            "batch": {"statuses": stat, "iterations_max": max(its), "iterations_mean": float(np.mean(its)),
+                      "rel_error_median": float(np.median(errs)), "rel_error_max": float(np.max(errs)),
+                      "matrices_per_second": len(cases) / (ms * 1e-3)}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ps = [int(x) for x in args.p.split(",")]
+    if args.workload == "batched":
+        return run_batched(args)
     if args.impl == "reference":
         return run_reference(args, ps)
 
