@@ -76,7 +76,12 @@ typedef enum {
 /* Initial guess. */
 typedef enum {
   PR_C0_EQ3 = 0,       /* Eq. 3: C_0 = A^T / (||A||_1 ||A||_inf)                                         */
-  PR_C0_SCALED_I = 1   /* C_0 = ||A||_1^{-1/p} I; one of the "different possible choices" of Sec. 2       */
+  PR_C0_SCALED_I = 1,  /* C_0 = ||A||_1^{-1/p} I; one of the "different possible choices" of Sec. 2       */
+  PR_C0_POLY = 2       /* C_0 = ||A||_1^{-1/p} q(A / ||A||_1), q(x) = c_0 + c_1 x + c_2 x^2 + c_3 x^3 with the
+                          coefficients of pr_options.c0_coef (e.g. predicted by a pr_mlp from pr_features).
+                          A gate checks it: if q <= 0 somewhere on [0, 1] (C_0 not positive definite) or a
+                          power-iteration estimate of ||I - C_0^p A||_2 (Eq. 2) is not below gate_max, the
+                          handle falls back to Eq. 3 (pr_stats.c0 reports the guess used)                  */
 } pr_c0_kind;
 
 /* Options fixed at pr_init. */
@@ -92,6 +97,9 @@ typedef struct {
                           7S bits per row and cost S (S + 1) / 2 BF16 products per FP64 product         */
   double stag_below_lowp; /* stag_below for low-precision (PR_BF16) residuals, whose floor is higher,
                              default 0.5 (below 0.5 every eigencomponent is in the quadratic phase)      */
+  double c0_coef[4];   /* PR_C0_POLY coefficients c_0 .. c_3, default (1, 0, 0, 0) (the scaled identity)  */
+  double gate_max;     /* PR_C0_POLY gate on ||I - C_0^p A||_2, default 0.9                                */
+  int gate_iters;      /* power iterations of the gate, default 30                                         */
 } pr_options;
 
 /* Counters of one handle. */
@@ -120,6 +128,7 @@ typedef struct {
   int64_t gemms_timed_by_precision[4];  /* the timed counters above, split by pr_precision            */
   double gemm_ms_by_precision[4];
   double gemm_flops_by_precision[4];
+  double c0_gate;                   /* PR_C0_POLY: the gate's estimate of ||I - C_0^p A||_2, else 0         */
 } pr_stats_t;
 
 /* Fills *opt with the defaults listed above. */
@@ -232,6 +241,28 @@ const char* pr_batch_last_error(pr_batch b);
 
 /* Frees the batch. b may be NULL. */
 pr_status pr_batch_destroy(pr_batch b);
+
+/* ---- The learned initial guess ---------------------------------------------------------------------------
+ * Spectral features of the handle's A for predicting a polynomial initial guess:
+ * out[k-1] = tr(Ahat^k) / n for k = 1..6 with Ahat = A / ||A||_1, out[6] = ||A||_1, out[7] = ||A||_inf.
+ * The traces come from Ahat, Ahat^2, Ahat^3 (two PR_EMU64 symmetric products) as Frobenius inner products.
+ * out: 8 doubles, host memory. Synchronises the stream. */
+pr_status pr_features(pr_handle h, double* out);
+
+/* A multilayer perceptron 8 -> 64 -> 64 -> 4 (ReLU hidden layers, FP32) on the device, trained with the
+ * mean squared error and Adam (beta1 0.9, beta2 0.999, eps 1e-8). Parameters are a flat FP32 vector of
+ * PR_MLP_PARAMS: W1 (64 x 8, row-major), b1 (64), W2 (64 x 64), b2 (64), W3 (4 x 64), b3 (4). Inputs X are
+ * B x 8, targets T and outputs Y B x 4, row-major, device or host memory, B <= max_batch. */
+#define PR_MLP_PARAMS 4996
+typedef struct pr_mlp_s* pr_mlp;
+pr_status pr_mlp_create(pr_mlp* m, const float* params, int max_batch, void* stream);
+pr_status pr_mlp_forward(pr_mlp m, const float* X, int B, float* Y);
+/* Loss (host) and its gradient (PR_MLP_PARAMS floats, device or host) at the current parameters. */
+pr_status pr_mlp_loss_grad(pr_mlp m, const float* X, const float* T, int B, float* loss, float* grad);
+/* One Adam step with learning rate lr on the batch; *loss (host, may be NULL) gets the loss before it. */
+pr_status pr_mlp_adam_step(pr_mlp m, const float* X, const float* T, int B, float lr, float* loss);
+pr_status pr_mlp_get_params(pr_mlp m, float* params);
+pr_status pr_mlp_destroy(pr_mlp m);
 
 /* Largest order accepted by pr_norms_noalloc. */
 #define PR_NORMS_NOALLOC_MAX_N 65536

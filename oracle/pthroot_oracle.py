@@ -276,3 +276,93 @@ def scalar_residuals(lam: np.ndarray, c0: np.ndarray, p: int, k_max: int) -> np.
 def forward_error(C: np.ndarray, Z: np.ndarray) -> float:
     """||C - Z||_F / ||Z||_F, the Frobenius error of Sec. 4.3 made relative."""
     return float(np.linalg.norm(C - Z) / np.linalg.norm(Z))
+
+
+# ---------------------------------------------------------------- learned polynomial initial guess
+#
+# A generalisation of the scalar start: C_0 = ||A||_1^{-1/p} q(A_hat), q(x) = c_0 + c_1 x + c_2 x^2 + c_3 x^3,
+# A_hat = A / ||A||_1 (eigenvalues in (0, 1] for SPD A). Any such C_0 is a polynomial in A, so it commutes
+# with A and the iterates of Eq. 1 remain polynomials in A; Eq. 2 must still hold, which a gate checks.
+
+def spectral_features(A: np.ndarray) -> np.ndarray:
+    """[tr(A_hat^k)/n for k = 1..6, ||A||_1, ||A||_inf], A_hat = A / ||A||_1 (definitions written out)."""
+    n = A.shape[0]
+    s = norm_1(A)
+    Ah = A / s
+    P = np.eye(n)
+    out = []
+    for _ in range(6):
+        P = P @ Ah
+        out.append(np.trace(P) / n)
+    return np.array(out + [s, norm_inf(A)])
+
+
+def polynomial_initial_guess(A: np.ndarray, p: int, c) -> np.ndarray:
+    """C_0 = ||A||_1^{-1/p} (c_0 I + c_1 A_hat + c_2 A_hat^2 + c_3 A_hat^3)."""
+    n = A.shape[0]
+    s = norm_1(A)
+    Ah = A / s
+    P, C = np.eye(n), np.zeros((n, n))
+    for ci in c:
+        C = C + ci * P
+        P = P @ Ah
+    return symmetrize(C * s ** (-1.0 / p))
+
+
+def gate_value(A: np.ndarray, p: int, C0: np.ndarray) -> float:
+    """||I - C_0^p A||_2 (Eq. 2), from a LAPACK symmetric eigensolver of the symmetrised matrix."""
+    E = np.eye(A.shape[0]) - np.linalg.matrix_power(C0, p) @ A
+    return float(np.abs(np.linalg.eigvalsh(symmetrize(E))).max())
+
+
+def relative_fit(lo: float, hi: float, p: int, degree: int = 3, points: int = 400) -> np.ndarray:
+    """Coefficients c of q minimising sum_x (1 - q(x) x^{1/p})^2 over `points` log-spaced x in [lo, hi]:
+    q(x)^p x close to 1 in the relative sense on the spectrum of A_hat, i.e. C_0^p A close to I."""
+    x = np.exp(np.linspace(np.log(lo), np.log(hi), points))
+    B = np.stack([x ** (i + 1.0 / p) for i in range(degree + 1)], axis=1)
+    c, *_ = np.linalg.lstsq(B, np.ones(points), rcond=None)
+    return c
+
+
+# ---------------------------------------------------------------- the MLP (8 -> 64 -> 64 -> 4, ReLU), FP64
+# Flat parameter layout (shared with the library): W1 (64 x 8), b1 (64), W2 (64 x 64), b2 (64), W3 (4 x 64), b3 (4).
+
+MLP_SHAPES = [(64, 8), (64,), (64, 64), (64,), (4, 64), (4,)]
+MLP_PARAMS = sum(int(np.prod(s)) for s in MLP_SHAPES)
+
+
+def mlp_unpack(theta):
+    out, k = [], 0
+    for s in MLP_SHAPES:
+        m = int(np.prod(s))
+        out.append(np.asarray(theta[k:k + m], dtype=np.float64).reshape(s))
+        k += m
+    return out
+
+
+def mlp_forward(theta, X):
+    """Y = W3 relu(W2 relu(W1 x + b1) + b2) + b3 for each row x of X."""
+    W1, b1, W2, b2, W3, b3 = mlp_unpack(theta)
+    H1 = np.maximum(X @ W1.T + b1, 0.0)
+    H2 = np.maximum(H1 @ W2.T + b2, 0.0)
+    return H2 @ W3.T + b3
+
+
+def mlp_loss_grad(theta, X, T):
+    """Mean squared error over all B x 4 outputs and its gradient (backpropagation written out)."""
+    W1, b1, W2, b2, W3, b3 = mlp_unpack(theta)
+    A1 = X @ W1.T + b1
+    H1 = np.maximum(A1, 0.0)
+    A2 = H1 @ W2.T + b2
+    H2 = np.maximum(A2, 0.0)
+    Y = H2 @ W3.T + b3
+    B = X.shape[0]
+    D = Y - T
+    loss = float(np.sum(D * D) / (B * 4))
+    dY = 2.0 * D / (B * 4)
+    gW3, gb3 = dY.T @ H2, dY.sum(0)
+    dA2 = (dY @ W3) * (A2 > 0)
+    gW2, gb2 = dA2.T @ H1, dA2.sum(0)
+    dA1 = (dA2 @ W2) * (A1 > 0)
+    gW1, gb1 = dA1.T @ X, dA1.sum(0)
+    return loss, np.concatenate([g.ravel() for g in (gW1, gb1, gW2, gb2, gW3, gb3)])

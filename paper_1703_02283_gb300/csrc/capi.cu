@@ -63,6 +63,7 @@ struct pr_handle_s {
   double* work = nullptr;     // 2n doubles (column and row abs-sums)
   double* scal = nullptr;     // device scalars: [0..3] checks, [4..5] norms, [6] residual, [7] error word
   double* hpin = nullptr;     // pinned host mirror of scal
+  double* vec = nullptr;      // PR_C0_POLY gate and features: 4n vectors + reduction partials + scalars
 
   // CUDA-event timing of the product kernels (pr_set_timing).
   bool timing = false;
@@ -441,6 +442,72 @@ pr_status ensure_state(pr_handle h, int prec) {
 
 }  // namespace
 
+namespace {
+
+constexpr int kVecBlocks = 152 * 8;  // upper bound on the reduction blocks of k_learned.cu
+
+pr_status ensure_vec(pr_handle h) {
+  if (!h->vec) PR_CK(h, cudaMalloc((void**)&h->vec, sizeof(double) * (4 * (size_t)h->n + kVecBlocks + 16)));
+  return PR_OK;
+}
+
+// T0 = A A, T1 = A (A A) with FP64-accurate (PR_EMU64) symmetric products.
+pr_status powers_of_A(pr_handle h) {
+  Out o2;
+  o2.out = &h->T0;
+  pr_status s = product(h, PR_EMU64, h->A, h->A, Mode::Sym, o2);
+  if (s != PR_OK) return s;
+  Out o3;
+  o3.out = &h->T1;
+  return product(h, PR_EMU64, h->A, h->T0, Mode::Sym, o3);
+}
+
+// C_0 = ||A||_1^{-1/p} q(A / ||A||_1) with the gate of Eq. 2; falls back to Eq. 3. Sets st.c0, st.c0_gate.
+pr_status poly_initial_guess(pr_handle h) {
+  const int n = (int)h->n, p = h->p;
+  const double* c = h->opt.c0_coef;
+  const double s1 = h->st.norm_1;
+  bool ok = true;
+  for (int k = 0; k <= 1000 && ok; ++k) {  // q > 0 on [0, 1] keeps C_0 positive definite
+    const double x = k / 1000.0;
+    ok = ((c[3] * x + c[2]) * x + c[1]) * x + c[0] > 0.0;
+  }
+  double gate = INFINITY;
+  if (ok) {
+    pr_status s = powers_of_A(h);
+    if (s == PR_OK) s = ensure_vec(h);
+    if (s != PR_OK) return s;
+    const double sc = pow(s1, -1.0 / p);
+    const double a[4] = {sc * c[0], sc * c[1] / s1, sc * c[2] / (s1 * s1), sc * c[3] / (s1 * s1 * s1)};
+    PR_CK(h, pr::poly_combine(h->A.f, h->T0.f, h->T1.f, n, a, h->X.f, h->stream));
+    // Power iteration for ||B||_2, B = I - C_0^p A (symmetric: C_0 is a polynomial in A).
+    double *v = h->vec, *u = v + n, *u2 = u + n, *w = u2 + n, *work = w + n, *sc2 = work + kVecBlocks;
+    PR_CK(h, pr::power_start(n, v, h->stream));
+    for (int it = 0; it < h->opt.gate_iters; ++it) {
+      PR_CK(h, pr::gemv(h->A.f, n, v, u, h->stream));
+      double *src = u, *dst = u2;
+      for (int j = 0; j < p; ++j) {
+        PR_CK(h, pr::gemv(h->X.f, n, src, dst, h->stream));
+        std::swap(src, dst);
+      }
+      PR_CK(h, pr::power_finish_step(v, src, n, w, work, sc2, v, sc2 + 1, h->stream));
+      h->st.launches += p + 4;
+    }
+    PR_CK(h, cudaMemcpyAsync(h->hpin + 6, sc2 + 1, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    pr_status st = sync(h);
+    if (st != PR_OK) return st;
+    gate = h->hpin[6];
+    ok = gate < h->opt.gate_max;
+  }
+  h->st.c0_gate = gate;
+  h->st.c0 = ok ? PR_C0_POLY : PR_C0_EQ3;
+  if (!ok) PR_CK(h, pr::init_c0_eq3(h->A.f, n, 1.0 / (h->st.norm_1 * h->st.norm_inf), h->X.f, h->stream));
+  h->X.sl_valid = false;
+  return PR_OK;
+}
+
+}  // namespace
+
 namespace pr {
 void set_handleless_error(const char* msg) { g_init_error = msg; }
 }  // namespace pr
@@ -461,6 +528,10 @@ void pr_default_options(pr_options* o) {
   o->reanchor = 1;
   o->emu_slices = 0;
   o->stag_below_lowp = 0.5;
+  o->c0_coef[0] = 1.0;
+  o->c0_coef[1] = o->c0_coef[2] = o->c0_coef[3] = 0.0;
+  o->gate_max = 0.9;
+  o->gate_iters = 30;
 }
 
 const char* pr_last_error(pr_handle h) { return h ? h->err.c_str() : g_init_error.c_str(); }
@@ -475,7 +546,7 @@ pr_status pr_destroy(pr_handle h) {
     if (m->sl) cudaFree(m->sl);
     if (m->ex) cudaFree(m->ex);
   }
-  for (double* b : {h->partial, h->work, h->scal})
+  for (double* b : {h->partial, h->work, h->scal, h->vec})
     if (b) cudaFree(b);
   if (h->hpin) cudaFreeHost(h->hpin);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
@@ -493,7 +564,10 @@ pr_status pr_init(pr_handle* out, const double* A, int64_t n, int p, const pr_op
   if (opt) o = *opt;
   else pr_default_options(&o);
   if (o.form < PR_FORM_AUTO || o.form > PR_FORM_LITERAL) return fail(nullptr, PR_EINVAL, "pr_init: unknown form");
-  if (o.c0 != PR_C0_EQ3 && o.c0 != PR_C0_SCALED_I) return fail(nullptr, PR_EINVAL, "pr_init: unknown c0 kind");
+  if (o.c0 != PR_C0_EQ3 && o.c0 != PR_C0_SCALED_I && o.c0 != PR_C0_POLY)
+    return fail(nullptr, PR_EINVAL, "pr_init: unknown c0 kind");
+  if (o.c0 == PR_C0_POLY && (!(o.gate_max > 0) || o.gate_iters < 1))
+    return fail(nullptr, PR_EINVAL, "pr_init: bad gate options");
   if (o.form == PR_FORM_NS && p != 1) return fail(nullptr, PR_EINVAL, "pr_init: the Newton-Schulz form needs p = 1");
   if (o.max_iter < 0 || !(o.stag_ratio > 0) || !(o.sym_tol >= 0) || !(o.stag_below_lowp >= 0) ||
       o.emu_slices < 0 || o.emu_slices > 9)
@@ -586,11 +660,16 @@ pr_status pr_load(pr_handle h, const double* A) {
   if (nonpos > 0) return fail(h, PR_ENOTSPD, "pr_load: A has a non-positive diagonal entry");
   h->st.norm_1 = h->hpin[4];
   h->st.norm_inf = h->hpin[5];
-  // C_0 (Eq. 3, or the scaled identity).
+  // C_0 (Eq. 3, the scaled identity, or the gated polynomial).
+  h->st.c0 = h->opt.c0;
+  h->st.c0_gate = 0.0;
   if (h->opt.c0 == PR_C0_EQ3) {
     PR_CK(h, pr::init_c0_eq3(h->A.f, n, 1.0 / (h->st.norm_1 * h->st.norm_inf), h->X.f, h->stream));
-  } else {
+  } else if (h->opt.c0 == PR_C0_SCALED_I) {
     PR_CK(h, pr::set_scaled_identity(h->X.f, n, pow(h->st.norm_1, -1.0 / h->p), h->stream));
+  } else {
+    pr_status st = poly_initial_guess(h);
+    if (st != PR_OK) return st;
   }
   h->st.launches += 1;
   return sync(h);
@@ -779,6 +858,38 @@ pr_status pr_matmul(int precision, const double* X, const double* Y, int64_t n, 
     if (q) cudaFree(q);
   if (e != cudaSuccess) return cuda_fail(nullptr, "pr_matmul", e);
   if (word != 0) return fail(nullptr, PR_ETIMEOUT, "pr_matmul: a bounded device wait expired");
+  return PR_OK;
+}
+
+pr_status pr_features(pr_handle h, double* out) {
+  if (!h) return fail(nullptr, PR_ESTATE, "pr_features: NULL handle");
+  if (!out) return fail(h, PR_EINVAL, "pr_features: out is NULL");
+  cudaSetDevice(h->device);
+  const int n = (int)h->n;
+  pr_status s = powers_of_A(h);
+  if (s == PR_OK) s = ensure_vec(h);
+  if (s != PR_OK) return s;
+  const int64_t nn = (int64_t)n * n;
+  double *work = h->vec + 4 * (size_t)n, *r = work + kVecBlocks;  // r[0..5]: tr A, <A,A>, <A,P2>, ...
+  PR_CK(h, pr::trace(h->A.f, n, work, r + 0, h->stream));
+  PR_CK(h, pr::frobenius_dot(h->A.f, h->A.f, nn, work, r + 1, h->stream));
+  PR_CK(h, pr::frobenius_dot(h->A.f, h->T0.f, nn, work, r + 2, h->stream));
+  PR_CK(h, pr::frobenius_dot(h->T0.f, h->T0.f, nn, work, r + 3, h->stream));
+  PR_CK(h, pr::frobenius_dot(h->T0.f, h->T1.f, nn, work, r + 4, h->stream));
+  PR_CK(h, pr::frobenius_dot(h->T1.f, h->T1.f, nn, work, r + 5, h->stream));
+  h->st.launches += 12;
+  double t[6];
+  PR_CK(h, cudaMemcpyAsync(t, r, sizeof t, cudaMemcpyDeviceToHost, h->stream));
+  s = sync(h);
+  if (s != PR_OK) return s;
+  const double s1 = h->st.norm_1;
+  double sk = 1.0;
+  for (int k = 0; k < 6; ++k) {
+    sk *= s1;
+    out[k] = t[k] / sk / n;  // tr(A^{k+1}) / s^{k+1} / n
+  }
+  out[6] = h->st.norm_1;
+  out[7] = h->st.norm_inf;
   return PR_OK;
 }
 

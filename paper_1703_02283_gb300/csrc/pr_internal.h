@@ -112,6 +112,23 @@ cudaError_t reduce_partials_sqrt(const double* partial, int count, double* resul
 // dst[i * ldl + j] = bf16(src[i * n + j]) for an n x n matrix
 cudaError_t to_bf16(const double* src, int n, int ldl, __nv_bfloat16* dst, cudaStream_t s);
 
+// ---- learned initial guess (k_learned.cu)
+int mlp_params();
+int mlp_backward_blocks(int B);
+cudaError_t frobenius_dot(const double* X, const double* Y, int64_t total, double* work, double* out, cudaStream_t s);
+cudaError_t trace(const double* X, int n, double* work, double* out, cudaStream_t s);
+cudaError_t poly_combine(const double* A, const double* P2, const double* P3, int n, const double a[4], double* X,
+                         cudaStream_t s);
+cudaError_t gemv(const double* M, int n, const double* x, double* y, cudaStream_t s);
+cudaError_t power_start(int n, double* v, cudaStream_t s);
+// w = v - u, *ss = |w|^2, vout = w / |w|, *est = |w|
+cudaError_t power_finish_step(const double* v, const double* u, int n, double* w, double* work, double* ss, double* vout,
+                              double* est, cudaStream_t s);
+cudaError_t mlp_forward(const float* theta, const float* X, int B, float* Y, float* H1, float* H2, cudaStream_t s);
+cudaError_t mlp_backward(const float* theta, const float* X, const float* T, const float* Y, const float* H1,
+                         const float* H2, int B, float* gpart, float* lpart, float* grad, float* loss, float* m,
+                         float* v, float* theta_rw, float lr, float c1, float c2, bool adam, cudaStream_t s);
+
 // out[m] = sqrt(sum of partial[begin[m] .. end[m])) for m < count, each sum in a fixed order.
 cudaError_t segmented_reduce_sqrt(const double* partial, const int* begin, const int* end, int count, double* out,
                                   cudaStream_t s);

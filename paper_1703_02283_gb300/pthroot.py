@@ -21,14 +21,16 @@ STATUS_NAMES = {0: "PR_OK", 1: "PR_EINVAL", 2: "PR_ENOTSPD", 3: "PR_ENOMEM", 4: 
                 9: "PR_EGATE", 10: "PR_ESTATE", 11: "PR_EUNSUPPORTED"}
 PR_FP64, PR_EMU64, PR_BF16 = 0, 1, 3
 PR_FORM_AUTO, PR_FORM_COUPLED, PR_FORM_NS, PR_FORM_LITERAL = 0, 1, 2, 3
-PR_C0_EQ3, PR_C0_SCALED_I = 0, 1
+PR_C0_EQ3, PR_C0_SCALED_I, PR_C0_POLY = 0, 1, 2
+PR_MLP_PARAMS = 4996
 
 
 class pr_options(ctypes.Structure):
     _fields_ = [("form", ctypes.c_int), ("c0", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("stag_below", ctypes.c_double), ("stag_ratio", ctypes.c_double),
                 ("sym_tol", ctypes.c_double), ("reanchor", ctypes.c_int), ("emu_slices", ctypes.c_int),
-                ("stag_below_lowp", ctypes.c_double)]
+                ("stag_below_lowp", ctypes.c_double), ("c0_coef", ctypes.c_double * 4), ("gate_max", ctypes.c_double),
+                ("gate_iters", ctypes.c_int)]
 
 
 class pr_stats_t(ctypes.Structure):
@@ -40,7 +42,7 @@ class pr_stats_t(ctypes.Structure):
                 ("launches", ctypes.c_int64), ("gemms_timed", ctypes.c_int64), ("gemm_ms", ctypes.c_double),
                 ("gemm_flops_timed", ctypes.c_double), ("emu_slices", ctypes.c_int),
                 ("gemms_timed_by_precision", ctypes.c_int64 * 4), ("gemm_ms_by_precision", ctypes.c_double * 4),
-                ("gemm_flops_by_precision", ctypes.c_double * 4)]
+                ("gemm_flops_by_precision", ctypes.c_double * 4), ("c0_gate", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -85,6 +87,15 @@ def _load() -> ctypes.CDLL:
         "pr_batch_launches": (ctypes.c_int64, [_handle_t]),
         "pr_batch_last_error": (ctypes.c_char_p, [_handle_t]),
         "pr_batch_destroy": (ctypes.c_int, [_handle_t]),
+        "pr_features": (ctypes.c_int, [_handle_t, ctypes.POINTER(ctypes.c_double)]),
+        "pr_mlp_create": (ctypes.c_int, [ctypes.POINTER(_handle_t), _dptr, ctypes.c_int, ctypes.c_void_p]),
+        "pr_mlp_forward": (ctypes.c_int, [_handle_t, _dptr, ctypes.c_int, _dptr]),
+        "pr_mlp_loss_grad": (ctypes.c_int, [_handle_t, _dptr, _dptr, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
+                                            _dptr]),
+        "pr_mlp_adam_step": (ctypes.c_int, [_handle_t, _dptr, _dptr, ctypes.c_int, ctypes.c_float,
+                                            ctypes.POINTER(ctypes.c_float)]),
+        "pr_mlp_get_params": (ctypes.c_int, [_handle_t, _dptr]),
+        "pr_mlp_destroy": (ctypes.c_int, [_handle_t]),
         "pr_norms_noalloc": (ctypes.c_int, [_dptr, ctypes.c_int64, _dptr, ctypes.c_void_p]),
         "pr_matmul": (ctypes.c_int, [ctypes.c_int, _dptr, _dptr, ctypes.c_int64, ctypes.c_int, _dptr,
                                      ctypes.c_void_p]),
@@ -186,6 +197,43 @@ def pr_stop_rule(hist, prec, tol: float, options: pr_options | None = None) -> i
     h = (ctypes.c_double * max(n, 1))(*hist)
     q = (ctypes.c_int * max(n, 1))(*prec)
     return _lib.pr_stop_rule(h, q, n, float(tol), ctypes.byref(options) if options is not None else None)
+
+
+def pr_features(h: int) -> list[float]:
+    out = (ctypes.c_double * 8)()
+    _check(_lib.pr_features(h, out), h)
+    return list(out)
+
+
+def pr_mlp_create(params, max_batch: int, stream: int = 0) -> int:
+    m = _handle_t()
+    _check(_lib.pr_mlp_create(ctypes.byref(m), _ptr(params), int(max_batch), ctypes.c_void_p(stream)))
+    return m.value
+
+
+def pr_mlp_forward(m: int, X, B: int, Y) -> None:
+    _check(_lib.pr_mlp_forward(m, _ptr(X), int(B), _ptr(Y)))
+
+
+def pr_mlp_loss_grad(m: int, X, T, B: int, grad=None) -> float:
+    loss = ctypes.c_float(0.0)
+    _check(_lib.pr_mlp_loss_grad(m, _ptr(X), _ptr(T), int(B), ctypes.byref(loss),
+                                 _ptr(grad) if grad is not None else None))
+    return loss.value
+
+
+def pr_mlp_adam_step(m: int, X, T, B: int, lr: float) -> float:
+    loss = ctypes.c_float(0.0)
+    _check(_lib.pr_mlp_adam_step(m, _ptr(X), _ptr(T), int(B), float(lr), ctypes.byref(loss)))
+    return loss.value
+
+
+def pr_mlp_get_params(m: int, params) -> None:
+    _check(_lib.pr_mlp_get_params(m, _ptr(params)))
+
+
+def pr_mlp_destroy(m: int) -> None:
+    _check(_lib.pr_mlp_destroy(m))
 
 
 def pr_norms_noalloc(A, n: int, out, stream: int = 0) -> None:

@@ -50,6 +50,8 @@ def test_host_side_argument_checks():
     bad.form = P.PR_FORM_NS
     assert lib.pr_init(ctypes.byref(h), dummy, 4, 2, ctypes.byref(bad), None) == P.PR_EINVAL
     assert "Newton-Schulz" in P.pr_last_error(None)
+    o = P.pr_default_options()
+    assert list(o.c0_coef) == [1.0, 0.0, 0.0, 0.0] and o.gate_max == 0.9 and o.gate_iters == 30
     bad = P.pr_default_options()
     bad.c0 = 7
     assert lib.pr_init(ctypes.byref(h), dummy, 4, 2, ctypes.byref(bad), None) == P.PR_EINVAL
