@@ -79,7 +79,8 @@ typedef enum {
   PR_C0_SCALED_I = 1,  /* C_0 = ||A||_1^{-1/p} I; one of the "different possible choices" of Sec. 2       */
   PR_C0_POLY = 2       /* C_0 = ||A||_1^{-1/p} q(A / ||A||_1), q(x) = c_0 + c_1 x + c_2 x^2 + c_3 x^3 with the
                           coefficients of pr_options.c0_coef (e.g. predicted by a pr_mlp from pr_features).
-                          A gate checks it: if q <= 0 somewhere on [0, 1] (C_0 not positive definite) or a
+                          A gate checks it: if q <= 0 somewhere on [0, 1.05 rho] (rho: a power-iteration
+                          estimate of ||A||_2 / ||A||_1, so C_0 might not be positive definite) or a
                           power-iteration estimate of ||I - C_0^p A||_2 (Eq. 2) is not below gate_max, the
                           handle falls back to Eq. 3 (pr_stats.c0 reports the guess used)                  */
 } pr_c0_kind;

@@ -462,20 +462,44 @@ pr_status powers_of_A(pr_handle h) {
   return product(h, PR_EMU64, h->A, h->T0, Mode::Sym, o3);
 }
 
+// Power iteration for ||A||_2 (from below): the spectrum of A / ||A||_1 lies in (0, ||A||_2 / ||A||_1].
+pr_status spectral_radius(pr_handle h, double* out) {
+  const int n = (int)h->n;
+  double *v = h->vec, *u = v + n, *zero = u + n, *w = zero + n, *work = w + n, *sc2 = work + kVecBlocks;
+  PR_CK(h, cudaMemsetAsync(zero, 0, sizeof(double) * n, h->stream));
+  PR_CK(h, pr::power_start(n, v, h->stream));
+  for (int it = 0; it < h->opt.gate_iters; ++it) {
+    PR_CK(h, pr::gemv(h->A.f, n, v, u, h->stream));
+    PR_CK(h, pr::power_finish_step(zero, u, n, w, work, sc2, v, sc2 + 1, h->stream));  // v = -A v / |A v|
+    h->st.launches += 4;
+  }
+  PR_CK(h, cudaMemcpyAsync(h->hpin + 6, sc2 + 1, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  pr_status st = sync(h);
+  if (st == PR_OK) *out = h->hpin[6];
+  return st;
+}
+
 // C_0 = ||A||_1^{-1/p} q(A / ||A||_1) with the gate of Eq. 2; falls back to Eq. 3. Sets st.c0, st.c0_gate.
 pr_status poly_initial_guess(pr_handle h) {
   const int n = (int)h->n, p = h->p;
   const double* c = h->opt.c0_coef;
   const double s1 = h->st.norm_1;
+  pr_status s = ensure_vec(h);
+  if (s != PR_OK) return s;
+  double rho = 0.0;
+  s = spectral_radius(h, &rho);
+  if (s != PR_OK) return s;
+  // q > 0 on [0, 1.05 ||A||_2 / ||A||_1] (a 5 % margin over the estimate from below) keeps C_0 positive
+  // definite; for even p the gate alone would not see a negative q.
+  const double top = fmin(1.0, 1.05 * rho / s1);
   bool ok = true;
-  for (int k = 0; k <= 1000 && ok; ++k) {  // q > 0 on [0, 1] keeps C_0 positive definite
-    const double x = k / 1000.0;
+  for (int k = 0; k <= 1000 && ok; ++k) {
+    const double x = top * k / 1000.0;
     ok = ((c[3] * x + c[2]) * x + c[1]) * x + c[0] > 0.0;
   }
   double gate = INFINITY;
   if (ok) {
-    pr_status s = powers_of_A(h);
-    if (s == PR_OK) s = ensure_vec(h);
+    s = powers_of_A(h);
     if (s != PR_OK) return s;
     const double sc = pow(s1, -1.0 / p);
     const double a[4] = {sc * c[0], sc * c[1] / s1, sc * c[2] / (s1 * s1), sc * c[3] / (s1 * s1 * s1)};

@@ -54,12 +54,13 @@ def _power_norm(apply, n: int, iters: int = 60) -> float:
 
 def target_coefficients(A: np.ndarray, C: np.ndarray, p: int, points: int = 400) -> np.ndarray:
     """Label: the cubic minimising sum_x (1 - q(x) x^{1/p})^2 over log-spaced x on the spectral interval of
-    A/||A||_1, the interval read from the converged root C of the plain method."""
+    A/||A||_1, the interval read from the converged root C of the plain method. The top end is widened by
+    10 % so that q stays positive across the margin the library checks above its estimate of ||A||_2."""
     n = A.shape[0]
     s1 = float(np.abs(A).sum(axis=0).max())
     lam_max = _power_norm(lambda v: A @ v, n)
     lam_min = _power_norm(lambda v: C @ v, n) ** (-p)
-    lo, hi = lam_min / s1, min(lam_max / s1, 1.0)
+    lo, hi = lam_min / s1, min(1.1 * lam_max / s1, 1.0)
     x = np.exp(np.linspace(math.log(lo), math.log(hi), points))
     B = np.stack([x ** (i + 1.0 / p) for i in range(4)], axis=1)
     c, *_ = np.linalg.lstsq(B, np.ones(points), rcond=None)

@@ -42,9 +42,11 @@ def test_features_match_oracle():
 
 @pytest.mark.parametrize("p", [1, 2, 3])
 def test_polynomial_guess_matches_oracle_and_gate(p):
+    # Fit on [lambda_min, 1.1 lambda_max] / ||A||_1: q then stays positive past the 5 % margin the library
+    # checks above its estimate of ||A||_2 (first zero of q at >= 1.11 lambda_max / ||A||_1 for these cases).
     c = W.spd_from_spectrum(200, 1e-2, 30 + p)
     s = O.norm_1(c.A)
-    coef = O.relative_fit(c.lam.min() / s, c.lam.max() / s, p)
+    coef = O.relative_fit(c.lam.min() / s, 1.1 * c.lam.max() / s, p)
     h = handle(c.A, p, c0=P.PR_C0_POLY, c0_coef=coef)
     try:
         st = P.pr_stats(h)
@@ -54,10 +56,30 @@ def test_polynomial_guess_matches_oracle_and_gate(p):
     finally:
         P.pr_destroy(h)
     want = O.polynomial_initial_guess(c.A, p, coef)
+    g = O.gate_value(c.A, p, want)  # exact ||I - C_0^p A||_2, below 0.85 for these cases
+    assert g < 0.85
     assert st["c0"] == P.PR_C0_POLY
     np.testing.assert_allclose(C0.cpu().numpy(), want, rtol=1e-11, atol=1e-14)
-    g = O.gate_value(c.A, p, want)
-    assert st["c0_gate"] <= g * (1 + 1e-9) and st["c0_gate"] >= 0.9 * g  # power iteration: from below
+    # The power iteration approaches ||I - C_0^p A||_2 from below.
+    assert 0.9 * g <= st["c0_gate"] <= g * (1 + 1e-9)
+
+
+def test_polynomial_negative_past_spectrum_falls_back():
+    # The p = 1 fit on exactly [lambda_min, lambda_max] / ||A||_1 has a zero at 1.016 lambda_max / ||A||_1,
+    # inside the checked margin: C_0 would be fine on this spectrum but the guess is refused (gate = inf).
+    c = W.spd_from_spectrum(200, 1e-2, 31)
+    s = O.norm_1(c.A)
+    coef = O.relative_fit(c.lam.min() / s, c.lam.max() / s, 1)
+    h = handle(c.A, 1, c0=P.PR_C0_POLY, c0_coef=coef)
+    try:
+        st = P.pr_stats(h)
+        P.pr_iterate(h, 0, P.PR_FP64, 0.0)
+        C0 = torch.empty((200, 200), dtype=torch.float64, device=DEV)
+        P.pr_result(h, C0)
+    finally:
+        P.pr_destroy(h)
+    assert st["c0"] == P.PR_C0_EQ3 and st["c0_gate"] == float("inf")
+    np.testing.assert_allclose(C0.cpu().numpy(), O.initial_guess_eq3(c.A), rtol=1e-13, atol=1e-18)
 
 
 def test_gate_falls_back_to_eq3():
