@@ -237,6 +237,27 @@ pr_status pr_batch_history(pr_batch b, int i, double* out, int cap, int* len);
 /* Kernels launched by the batch so far. */
 int64_t pr_batch_launches(pr_batch b);
 
+/* Counters of a batch. A "product" is one matrix's share of one stage; its FP64-equivalent algorithmic
+ * flops are n^2 (n + 1) for a symmetric product (upper tiles) and 2 n^3 for a full one. The executed
+ * tensor-core work is emu_slices (emu_slices + 1) / 2 BF16 digit-pair products of each. */
+typedef struct {
+  int64_t launches;          /* kernels launched so far */
+  int64_t stages;            /* product launches */
+  int64_t products;          /* per-matrix products in those launches */
+  double product_flops;      /* their FP64-equivalent algorithmic flops */
+  int64_t stages_timed;      /* product launches timed with CUDA events (pr_batch_set_timing) */
+  double stage_ms;           /* summed event time of the timed launches */
+  double stage_flops_timed;  /* FP64-equivalent algorithmic flops of the timed launches */
+  int emu_slices;            /* digit planes per operand */
+} pr_batch_stats_t;
+
+/* Fills *out. Errors: PR_ESTATE (b NULL), PR_EINVAL (out NULL). */
+pr_status pr_batch_stats(pr_batch b, pr_batch_stats_t* out);
+
+/* on != 0: bracket every product launch with CUDA events on the batch's stream (read back at the
+ * synchronisation that ends each stage). Errors: PR_ESTATE, PR_ECUDA. */
+pr_status pr_batch_set_timing(pr_batch b, int on);
+
 /* Text for the last failing call on b (b NULL: the last failing pr_batch_init of this thread). */
 const char* pr_batch_last_error(pr_batch b);
 
@@ -249,6 +270,14 @@ pr_status pr_batch_destroy(pr_batch b);
  * The traces come from Ahat, Ahat^2, Ahat^3 (two PR_EMU64 symmetric products) as Frobenius inner products.
  * out: 8 doubles, host memory. Synchronises the stream. */
 pr_status pr_features(pr_handle h, double* out);
+
+/* Re-forms C_0 from the loaded A with `kind` (PR_C0_EQ3, PR_C0_SCALED_I or PR_C0_POLY; coef: the 4 cubic
+ * coefficients for PR_C0_POLY, host memory, else may be NULL) and restarts the iteration from it (history
+ * and counts cleared), without re-reading A. PR_C0_POLY is gated exactly as at pr_init; A^2 and A^3
+ * computed by pr_features are reused. The handle's options are not changed: a later pr_load forms C_0
+ * as pr_init's options say. Errors: PR_ESTATE (NULL handle, no matrix loaded), PR_EINVAL
+ * (unknown kind, coef NULL or non-finite for PR_C0_POLY), PR_ECUDA. */
+pr_status pr_set_initial_guess(pr_handle h, int kind, const double* coef);
 
 /* A multilayer perceptron 8 -> 64 -> 64 -> 4 (ReLU hidden layers, FP32) on the device, trained with the
  * mean squared error and Adam (beta1 0.9, beta2 0.999, eps 1e-8). Parameters are a flat FP32 vector of

@@ -64,6 +64,7 @@ struct pr_handle_s {
   double* scal = nullptr;     // device scalars: [0..3] checks, [4..5] norms, [6] residual, [7] error word
   double* hpin = nullptr;     // pinned host mirror of scal
   double* vec = nullptr;      // PR_C0_POLY gate and features: 4n vectors + reduction partials + scalars
+  bool powers_valid = false;  // T0 = A^2 and T1 = A^3 of the loaded A (features, polynomial guess)
 
   // CUDA-event timing of the product kernels (pr_set_timing).
   bool timing = false;
@@ -189,6 +190,8 @@ pr_status product(pr_handle h, int prec, Mat& X, Mat& Y, Mode mode, const Out& o
     if (o.out) e.out = o.out->f;
     if (o.out2) e.out2 = o.out2->f;
   }
+  for (const Mat* t : {o.out, o.out2})
+    if (t == &h->T0 || t == &h->T1) h->powers_valid = false;  // the scratch products are overwritten
   h->st.gemms += 1;
   h->st.gemm_flops += flops;
   if (h->timing) {
@@ -451,15 +454,19 @@ pr_status ensure_vec(pr_handle h) {
   return PR_OK;
 }
 
-// T0 = A A, T1 = A (A A) with FP64-accurate (PR_EMU64) symmetric products.
+// T0 = A A, T1 = A (A A) with FP64-accurate (PR_EMU64) symmetric products; kept until an iteration, a
+// residual or a new A overwrites the scratch products.
 pr_status powers_of_A(pr_handle h) {
+  if (h->powers_valid) return PR_OK;
   Out o2;
   o2.out = &h->T0;
   pr_status s = product(h, PR_EMU64, h->A, h->A, Mode::Sym, o2);
   if (s != PR_OK) return s;
   Out o3;
   o3.out = &h->T1;
-  return product(h, PR_EMU64, h->A, h->T0, Mode::Sym, o3);
+  s = product(h, PR_EMU64, h->A, h->T0, Mode::Sym, o3);
+  h->powers_valid = s == PR_OK;
+  return s;
 }
 
 // Power iteration for ||A||_2 (from below): the spectrum of A / ||A||_1 lies in (0, ||A||_2 / ||A||_1].
@@ -528,6 +535,39 @@ pr_status poly_initial_guess(pr_handle h) {
   if (!ok) PR_CK(h, pr::init_c0_eq3(h->A.f, n, 1.0 / (h->st.norm_1 * h->st.norm_inf), h->X.f, h->stream));
   h->X.sl_valid = false;
   return PR_OK;
+}
+
+// Back to "C_0 formed, no iteration yet" (the loaded A and its norms stay).
+void reset_iteration(pr_handle h) {
+  h->state_ready = false;
+  h->state_level = 0;
+  h->lp_stale = true;
+  for (Mat* m : {&h->X, &h->Xn, &h->M, &h->Mn, &h->N, &h->Nn, &h->T0, &h->T1}) m->sl_valid = false;
+  h->hist.clear();
+  h->hist_prec.clear();
+  h->st.iterations = 0;
+  for (int& c : h->st.iterations_by_precision) c = 0;
+  h->st.switch_iteration = -1;
+  h->st.last_precision = -1;
+  h->st.last_residual = 0.0;
+}
+
+// C_0 of the loaded A (Eq. 3, the scaled identity, or the gated polynomial) into X.
+pr_status form_initial_guess(pr_handle h) {
+  const int n = (int)h->n;
+  h->st.c0 = h->opt.c0;
+  h->st.c0_gate = 0.0;
+  if (h->opt.c0 == PR_C0_EQ3) {
+    PR_CK(h, pr::init_c0_eq3(h->A.f, n, 1.0 / (h->st.norm_1 * h->st.norm_inf), h->X.f, h->stream));
+  } else if (h->opt.c0 == PR_C0_SCALED_I) {
+    PR_CK(h, pr::set_scaled_identity(h->X.f, n, pow(h->st.norm_1, -1.0 / h->p), h->stream));
+  } else {
+    pr_status st = poly_initial_guess(h);
+    if (st != PR_OK) return st;
+  }
+  h->X.sl_valid = false;
+  h->st.launches += 1;
+  return sync(h);
 }
 
 }  // namespace
@@ -655,17 +695,10 @@ pr_status pr_load(pr_handle h, const double* A) {
   cudaSetDevice(h->device);
   const int n = (int)h->n;
   const size_t bytes = (size_t)n * (size_t)n * sizeof(double);
-  h->state_ready = false;
-  h->state_level = 0;
-  h->lp_stale = true;
-  for (Mat* m : {&h->A, &h->X, &h->Xn, &h->M, &h->Mn, &h->N, &h->Nn, &h->T0, &h->T1}) m->sl_valid = false;
-  h->hist.clear();
-  h->hist_prec.clear();
-  h->st.iterations = 0;
-  for (int& c : h->st.iterations_by_precision) c = 0;
-  h->st.switch_iteration = -1;
-  h->st.last_precision = -1;
-  h->st.last_residual = 0.0;
+  reset_iteration(h);
+  h->powers_valid = false;
+  h->A.sl_valid = false;
+  h->st.norm_1 = 0.0;
   PR_CK(h, cudaMemcpyAsync(h->A.f, A, bytes, cudaMemcpyDefault, h->stream));
   PR_CK(h, pr::validate(h->A.f, n, h->scal, h->stream));
   PR_CK(h, pr::abs_norms(h->A.f, n, h->work, h->scal + 4, h->stream));
@@ -684,19 +717,28 @@ pr_status pr_load(pr_handle h, const double* A) {
   if (nonpos > 0) return fail(h, PR_ENOTSPD, "pr_load: A has a non-positive diagonal entry");
   h->st.norm_1 = h->hpin[4];
   h->st.norm_inf = h->hpin[5];
-  // C_0 (Eq. 3, the scaled identity, or the gated polynomial).
-  h->st.c0 = h->opt.c0;
-  h->st.c0_gate = 0.0;
-  if (h->opt.c0 == PR_C0_EQ3) {
-    PR_CK(h, pr::init_c0_eq3(h->A.f, n, 1.0 / (h->st.norm_1 * h->st.norm_inf), h->X.f, h->stream));
-  } else if (h->opt.c0 == PR_C0_SCALED_I) {
-    PR_CK(h, pr::set_scaled_identity(h->X.f, n, pow(h->st.norm_1, -1.0 / h->p), h->stream));
-  } else {
-    pr_status st = poly_initial_guess(h);
-    if (st != PR_OK) return st;
-  }
-  h->st.launches += 1;
-  return sync(h);
+  return form_initial_guess(h);
+}
+
+pr_status pr_set_initial_guess(pr_handle h, int kind, const double* coef) {
+  if (!h) return fail(nullptr, PR_ESTATE, "pr_set_initial_guess: NULL handle");
+  if (kind != PR_C0_EQ3 && kind != PR_C0_SCALED_I && kind != PR_C0_POLY)
+    return fail(h, PR_EINVAL, "pr_set_initial_guess: unknown kind");
+  if (kind == PR_C0_POLY && !coef) return fail(h, PR_EINVAL, "pr_set_initial_guess: PR_C0_POLY needs coef");
+  if (h->st.norm_1 <= 0.0) return fail(h, PR_ESTATE, "pr_set_initial_guess: no matrix loaded");
+  if (kind == PR_C0_POLY)
+    for (int i = 0; i < 4; ++i)
+      if (!std::isfinite(coef[i])) return fail(h, PR_EINVAL, "pr_set_initial_guess: non-finite coefficient");
+  cudaSetDevice(h->device);
+  reset_iteration(h);
+  // A one-off choice: the handle's options (used by later pr_load calls) stay as they are.
+  const pr_options keep = h->opt;
+  h->opt.c0 = kind;
+  if (kind == PR_C0_POLY)
+    for (int i = 0; i < 4; ++i) h->opt.c0_coef[i] = coef[i];
+  pr_status s = form_initial_guess(h);
+  h->opt = keep;
+  return s;
 }
 
 pr_status pr_set_timing(pr_handle h, int on) {

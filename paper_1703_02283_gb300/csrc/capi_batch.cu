@@ -59,6 +59,9 @@ struct pr_batch_s {
   std::vector<std::vector<double>> hist;
   std::vector<int> active, status, iterations;
   int64_t launches = 0;
+  pr_batch_stats_t st{};
+  bool timing = false;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::string errmsg;
 };
 
@@ -123,18 +126,35 @@ pr_status stage(pr_batch b, Buf& Xb, Buf& Yb, Mode mode, const std::vector<int>&
   if ((int)items.size() > b->items_cap) return bfail(b, PR_ECUDA, "pr_batch: work list larger than allocated");
   PB_CK(b, cudaMemcpyAsync(b->items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream));
   PB_CK(b, cudaMemcpyAsync(b->mats, mats.data(), mats.size() * sizeof(EmuBatchMat), cudaMemcpyHostToDevice, b->stream));
+  double flops = 0.0;
+  for (int m : who) {
+    const double nm = b->n[m];
+    flops += mode == Mode::Sym ? nm * nm * (nm + 1.0) : 2.0 * nm * nm * nm;
+  }
   Epilogue e;
   if (so.out) e.out = so.out->f;
   if (so.out2) e.out2 = so.out2->f;
   e.cin = so.cin;
   e.partial = so.partial ? b->partial : nullptr;
+  if (b->timing) PB_CK(b, cudaEventRecord(b->ev0, b->stream));
   PB_CK(b, pr::gemm_emu_batched(Xb.sl, Xb.ex, Yb.sl, Yb.ex, b->R, b->K, b->ld, b->ld, b->S, mode, so.transpose,
                                 b->items, (int)items.size(), b->mats, e, b->err, b->stream));
+  if (b->timing) PB_CK(b, cudaEventRecord(b->ev1, b->stream));
   b->launches += 1;
+  b->st.stages += 1;
+  b->st.products += (int64_t)who.size();
+  b->st.product_flops += flops;
   if (so.out) so.out->sl_valid = false;
   if (so.out2) so.out2->sl_valid = false;
   // The host-side records must outlive the asynchronous copies: wait for this stage's launch inputs.
   PB_CK(b, cudaStreamSynchronize(b->stream));
+  if (b->timing) {
+    float ms = 0.f;
+    PB_CK(b, cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+    b->st.stages_timed += 1;
+    b->st.stage_ms += ms;
+    b->st.stage_flops_timed += flops;
+  }
   return PR_OK;
 }
 
@@ -214,6 +234,8 @@ pr_status pr_batch_destroy(pr_batch b) {
                   (void*)b->res, (void*)b->err})
     if (q) cudaFree(q);
   if (b->hres) cudaFreeHost(b->hres);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
   delete b;
   return PR_OK;
 }
@@ -467,6 +489,26 @@ pr_status pr_batch_history(pr_batch b, int i, double* out, int cap, int* len) {
 }
 
 int64_t pr_batch_launches(pr_batch b) { return b ? b->launches : 0; }
+
+pr_status pr_batch_stats(pr_batch b, pr_batch_stats_t* out) {
+  if (!b) return bfail(nullptr, PR_ESTATE, "pr_batch_stats: NULL batch");
+  if (!out) return bfail(b, PR_EINVAL, "pr_batch_stats: out is NULL");
+  *out = b->st;
+  out->launches = b->launches;
+  out->emu_slices = b->S;
+  return PR_OK;
+}
+
+pr_status pr_batch_set_timing(pr_batch b, int on) {
+  if (!b) return bfail(nullptr, PR_ESTATE, "pr_batch_set_timing: NULL batch");
+  cudaSetDevice(b->device);
+  if (on && !b->ev0) {
+    PB_CK(b, cudaEventCreate(&b->ev0));
+    PB_CK(b, cudaEventCreate(&b->ev1));
+  }
+  b->timing = on != 0;
+  return PR_OK;
+}
 
 const char* pr_batch_last_error(pr_batch b) { return b ? b->errmsg.c_str() : g_batch_error.c_str(); }
 

@@ -143,6 +143,18 @@ def predict(model: Model, features: np.ndarray, stream: int = 0) -> np.ndarray:
     return Y.astype(np.float64)
 
 
+def solve_learned(h: int, mlp: int, precision=P.PR_EMU64, tol: float = 1e-12, max_iter: int = 100):
+    """On a handle with A loaded (pr_init or pr_load): features -> network -> gated polynomial C_0 ->
+    iterations. Returns (status, iterations, guess used, gate estimate)."""
+    f = np.asarray(P.pr_features(h), dtype=np.float32)[None]
+    y = np.empty((1, 4), dtype=np.float32)
+    P.pr_mlp_forward(mlp, f, 1, y)
+    P.pr_set_initial_guess(h, P.PR_C0_POLY, y[0].astype(np.float64))
+    st, its = P.pr_iterate(h, max_iter, precision, tol)
+    s = P.pr_stats(h)
+    return st, its, s["c0"], s["c0_gate"]
+
+
 def solve_with_guess(torch, S: np.ndarray, p: int, coef, precision=P.PR_EMU64, tol: float = 1e-12, stream: int = 0):
     """One solve from the gated polynomial guess; returns (C, iterations, guess used, gate estimate)."""
     dev = torch.device("cuda")

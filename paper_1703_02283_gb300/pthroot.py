@@ -52,6 +52,15 @@ class pr_stats_t(ctypes.Structure):
         return d
 
 
+class pr_batch_stats_t(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("stages", ctypes.c_int64), ("products", ctypes.c_int64),
+                ("product_flops", ctypes.c_double), ("stages_timed", ctypes.c_int64), ("stage_ms", ctypes.c_double),
+                ("stage_flops_timed", ctypes.c_double), ("emu_slices", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _handle_t = ctypes.c_void_p
 _dptr = ctypes.c_void_p
 
@@ -85,9 +94,12 @@ def _load() -> ctypes.CDLL:
         "pr_batch_history": (ctypes.c_int, [_handle_t, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                             ctypes.POINTER(ctypes.c_int)]),
         "pr_batch_launches": (ctypes.c_int64, [_handle_t]),
+        "pr_batch_stats": (ctypes.c_int, [_handle_t, ctypes.POINTER(pr_batch_stats_t)]),
+        "pr_batch_set_timing": (ctypes.c_int, [_handle_t, ctypes.c_int]),
         "pr_batch_last_error": (ctypes.c_char_p, [_handle_t]),
         "pr_batch_destroy": (ctypes.c_int, [_handle_t]),
         "pr_features": (ctypes.c_int, [_handle_t, ctypes.POINTER(ctypes.c_double)]),
+        "pr_set_initial_guess": (ctypes.c_int, [_handle_t, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
         "pr_mlp_create": (ctypes.c_int, [ctypes.POINTER(_handle_t), _dptr, ctypes.c_int, ctypes.c_void_p]),
         "pr_mlp_forward": (ctypes.c_int, [_handle_t, _dptr, ctypes.c_int, _dptr]),
         "pr_mlp_loss_grad": (ctypes.c_int, [_handle_t, _dptr, _dptr, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
@@ -205,6 +217,11 @@ def pr_features(h: int) -> list[float]:
     return list(out)
 
 
+def pr_set_initial_guess(h: int, kind: int, coef=None) -> None:
+    c = None if coef is None else (ctypes.c_double * 4)(*[float(x) for x in coef])
+    _check(_lib.pr_set_initial_guess(h, int(kind), c), h)
+
+
 def pr_mlp_create(params, max_batch: int, stream: int = 0) -> int:
     m = _handle_t()
     _check(_lib.pr_mlp_create(ctypes.byref(m), _ptr(params), int(max_batch), ctypes.c_void_p(stream)))
@@ -302,6 +319,16 @@ def pr_batch_history(b: int, i: int) -> list[float]:
 
 def pr_batch_launches(b: int) -> int:
     return int(_lib.pr_batch_launches(b))
+
+
+def pr_batch_stats(b: int) -> dict:
+    s = pr_batch_stats_t()
+    _bcheck(_lib.pr_batch_stats(b, ctypes.byref(s)), b)
+    return s.as_dict()
+
+
+def pr_batch_set_timing(b: int, on: bool) -> None:
+    _bcheck(_lib.pr_batch_set_timing(b, 1 if on else 0), b)
 
 
 def pr_batch_destroy(b: int) -> None:

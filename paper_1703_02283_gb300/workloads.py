@@ -92,8 +92,10 @@ def jitter_points(r: np.ndarray, sigma: float, rng: np.random.Generator) -> np.n
 
 def overlap_matrix(r: np.ndarray, ell: float = 1.0) -> np.ndarray:
     """S_ij = exp(-|r_i - r_j| / ell): symmetric, unit diagonal, positive definite for distinct points."""
-    d = np.sqrt(((r[:, None, :] - r[None, :, :]) ** 2).sum(-1))
-    S = np.exp(-d / ell)
+    d2 = np.zeros((r.shape[0], r.shape[0]))
+    for k in range(r.shape[1]):  # one coordinate at a time: no n x n x 3 temporary
+        d2 += (r[:, k, None] - r[None, :, k]) ** 2
+    S = np.exp(-np.sqrt(d2) / ell)
     return np.ascontiguousarray(0.5 * (S + S.T))
 
 

@@ -67,7 +67,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     if not shutil.which("gcc"):
         pytest.skip("gcc not available")
     from paper_1703_02283_gb300 import pthroot as P
-    fields = {"pr_options": [f for f, _ in P.pr_options._fields_], "pr_stats_t": [f for f, _ in P.pr_stats_t._fields_]}
+    classes = {"pr_options": P.pr_options, "pr_stats_t": P.pr_stats_t, "pr_batch_stats_t": P.pr_batch_stats_t}
+    fields = {st: [f for f, _ in cls._fields_] for st, cls in classes.items()}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pthroot.h"', "int main(void) {"]
     for st, fs in fields.items():
         lines.append(f'  printf("{st} %zu\\n", sizeof({st}));')
@@ -80,7 +81,7 @@ def test_struct_layouts_match_the_header(tmp_path):
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     out = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], capture_output=True, text=True,
                                                               check=True).stdout.split("\n") if line)
-    for st, cls in (("pr_options", P.pr_options), ("pr_stats_t", P.pr_stats_t)):
+    for st, cls in classes.items():
         assert int(out[st]) == ctypes.sizeof(cls), st
         for f in fields[st]:
             assert int(out[f"{st}.{f}"]) == getattr(cls, f).offset, (st, f)

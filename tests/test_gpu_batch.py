@@ -119,3 +119,32 @@ def test_batch_full_size_sampled():
         Z = O.closed_form_root(case.Q, case.lam, p)
         floor = 1.1e-16 * case.kappa ** (p + 1 if p > 1 else 1) * np.sqrt(case.n)
         assert O.forward_error(out[i][0], Z) <= max(1e-10, 100 * floor), (i, case.n, p, case.kappa)
+
+
+def test_batch_stats_count_every_product():
+    # Per matrix of order n and k iterations: Newton-Schulz (p = 1) runs k + 1 residual products A X (full,
+    # 2 n^3 flops) and k updates X T (symmetric, n^2 (n + 1)); the coupled form runs p products for M_0 and
+    # p + 1 per iteration, all symmetric.
+    cases, ps = make_batch(6, 64, 300, 1e3, 77)
+    mats = [torch.from_numpy(c.A).to(DEV) for c in cases]
+    b = P.pr_batch_init(mats, ps, P.pr_default_options(), torch.cuda.current_stream(DEV).cuda_stream)
+    try:
+        P.pr_batch_set_timing(b, True)
+        its, _ = P.pr_batch_solve(b, len(cases), P.PR_EMU64, 1e-12)
+        st = P.pr_batch_stats(b)
+    finally:
+        P.pr_batch_destroy(b)
+    products, flops = 0, 0.0
+    for c, p, k in zip(cases, ps, its):
+        n = float(c.n)
+        sym, full = n * n * (n + 1), 2 * n ** 3
+        if p == 1:
+            products += 2 * k + 1
+            flops += (k + 1) * full + k * sym
+        else:
+            products += p + k * (p + 1)
+            flops += (p + k * (p + 1)) * sym
+    assert st["products"] == products
+    assert st["product_flops"] == pytest.approx(flops, rel=1e-12)
+    assert st["stages_timed"] == st["stages"] and st["stage_flops_timed"] == st["product_flops"]
+    assert st["stage_ms"] > 0 and st["emu_slices"] == 9 and st["launches"] > st["stages"]

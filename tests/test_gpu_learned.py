@@ -82,6 +82,56 @@ def test_polynomial_negative_past_spectrum_falls_back():
     np.testing.assert_allclose(C0.cpu().numpy(), O.initial_guess_eq3(c.A), rtol=1e-13, atol=1e-18)
 
 
+def test_set_initial_guess_matches_fresh_handles():
+    # Features -> pr_set_initial_guess on one handle must give, bit for bit, what a handle created with the
+    # same polynomial gives (the cached A^2, A^3 are the same products); switching back to Eq. 3 restarts
+    # from Eq. 3's C_0; a later pr_load forms C_0 as pr_init's options say.
+    c = W.spd_from_spectrum(160, 1e-2, 50)
+    s = O.norm_1(c.A)
+    coef = O.relative_fit(c.lam.min() / s, 1.1 * c.lam.max() / s, 2)
+
+    def run(h):
+        P.pr_iterate(h, 100, P.PR_EMU64, 1e-12)
+        C = torch.empty((160, 160), dtype=torch.float64, device=DEV)
+        P.pr_result(h, C)
+        return C.cpu().numpy(), P.pr_history(h), P.pr_stats(h)
+
+    hp = handle(c.A, 2, c0=P.PR_C0_POLY, c0_coef=coef)
+    he = handle(c.A, 2)
+    h = handle(c.A, 2)
+    try:
+        Cp, hist_p, st_p = run(hp)
+        Ce, hist_e, _ = run(he)
+        f = P.pr_features(h)
+        np.testing.assert_allclose(f, O.spectral_features(c.A), rtol=1e-12)
+        P.pr_set_initial_guess(h, P.PR_C0_POLY, coef)
+        C1, hist_1, st_1 = run(h)
+        assert st_1["c0"] == P.PR_C0_POLY and st_1["c0_gate"] == st_p["c0_gate"]
+        assert np.array_equal(C1, Cp) and hist_1 == hist_p and st_1["iterations"] == st_p["iterations"]
+        P.pr_set_initial_guess(h, P.PR_C0_EQ3)
+        C0 = torch.empty((160, 160), dtype=torch.float64, device=DEV)
+        P.pr_result(h, C0)
+        np.testing.assert_allclose(C0.cpu().numpy(), O.initial_guess_eq3(c.A), rtol=1e-13, atol=1e-18)
+        C2, hist_2, _ = run(h)
+        assert np.array_equal(C2, Ce) and hist_2 == hist_e
+        P.pr_set_initial_guess(h, P.PR_C0_POLY, coef)
+        P.pr_load(h, torch.from_numpy(c.A).to(DEV))
+        assert P.pr_stats(h)["c0"] == P.PR_C0_EQ3
+        with pytest.raises(P.PthrootError) as e:
+            P.pr_set_initial_guess(h, 7)
+        assert e.value.status == P.PR_EINVAL
+        with pytest.raises(P.PthrootError) as e:
+            P.pr_set_initial_guess(h, P.PR_C0_POLY, None)
+        assert e.value.status == P.PR_EINVAL
+        with pytest.raises(P.PthrootError) as e:
+            P.pr_set_initial_guess(h, P.PR_C0_POLY, [1.0, float("nan"), 0.0, 0.0])
+        assert e.value.status == P.PR_EINVAL
+    finally:
+        for x in (hp, he, h):
+            P.pr_destroy(x)
+    assert Cp.shape == (160, 160)
+
+
 def test_gate_falls_back_to_eq3():
     c = W.spd_from_spectrum(128, 1e-2, 40)
     for coef in ([1.0, -3.0, 0.0, 0.0],  # q < 0 on [0, 1]
