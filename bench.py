@@ -60,8 +60,8 @@ def parse():
                     help="single: the n=4096 matrix for every p; batched: 512 matrices, n in [64, 1024]")
     ap.add_argument("--count", type=int, default=512, help="batched: number of matrices")
     ap.add_argument("--learned-n", type=int, default=2048, help="learned: matrix order")
-    ap.add_argument("--train-seqs", type=int, default=16, help="learned: training sequences (ids 0..)")
-    ap.add_argument("--test-seqs", type=int, default=4, help="learned: held-out sequences (ids 100..)")
+    ap.add_argument("--train-seqs", type=int, default=40, help="learned: training sequences (ids 0..)")
+    ap.add_argument("--test-seqs", type=int, default=10, help="learned: held-out sequences (ids 40..)")
     ap.add_argument("--every", type=int, default=50, help="learned: sample every this many of 200 steps")
     return ap.parse_args()
 
@@ -336,7 +336,7 @@ def learned_sets(args):
     from paper_1703_02283_gb300 import learned as L
     n = args.learned_n
     train = [S for q in range(args.train_seqs) for S in L.overlap_sequence(q, 200, n, every=args.every)]
-    test = [S for q in range(100, 100 + args.test_seqs) for S in L.overlap_sequence(q, 200, n, every=args.every)]
+    test = [S for q in range(40, 40 + args.test_seqs) for S in L.overlap_sequence(q, 200, n, every=args.every)]
     return train, test
 
 

@@ -37,6 +37,17 @@ form ``Q diag(lam^{-1/p}) Q^T`` and a LAPACK eigendecomposition root; the per-it
 the scalar recurrence of Eq. 1 in the eigenbasis; hand-computed dyadic iterates of small diagonal cases
 (tests/golden); the Eq. 2 bound for Eq. 3's guess; symmetry and commutation invariants; the three forms
 agree; the quadratic tail.
+
+Learned initial guess (the functions after ``forward_error``): spectral features ``tr(Ahat^k)/n``
+(``Ahat = A / ||A||_1``, k = 1..6) with ``||A||_1`` and ``||A||_inf``; the polynomial guess
+``C_0 = ||A||_1^{-1/p} q(Ahat)`` for a cubic q, the degree-0 case being the scaled identity that Sec. 2
+allows; its gate ``||I - C_0^p A||_2`` (Eq. 2) computed exactly by an eigensolver; the relative
+least-squares cubic on a spectral interval that serves as a training label; and the 8-64-64-4 ReLU
+network's forward pass, mean-squared loss and gradient written out layer by layer. Their pins
+(tests/test_oracle_learned.py): traces from the known eigenvalues, C_0's eigenvalues equal q at the
+eigenvalues, Eq. 3 and the scaled identity as special coefficient vectors, the gate against the scalar
+model of Eq. 2, the fit on a vanishing interval, a hand-computed network case and central differences of
+the loss.
 """
 from __future__ import annotations
 
