@@ -6,7 +6,7 @@ roots p = 1, 2, 3, 4, initial guess of Eq. 3, tolerance 1e-12 on the iteration's
 One step = the whole hot path for every p in --p: load A (checks, ||A||_1, ||A||_inf, C_0), iterate Eq. 1
 to the tolerance or the precision floor, the true residual ||I - C^p A||_F and the result copy. The value is
 milliseconds per step (lower is better) for --mode:
-  fast   FP64-accurate products from exact BF16 digit slices (PR_EMU64) for every p; for p = 1, whose
+  fast   FP64-accurate products from exact FP16 digit slices (PR_EMU64) for every p; for p = 1, whose
          Newton-Schulz form corrects earlier errors, BF16 iterations first, then PR_EMU64 ones (default);
   emu64  PR_EMU64 for every iteration;
   fp64   native FP64 products (the plain FP64 GPU iteration).
@@ -279,13 +279,13 @@ def run_batched(args):
     S = bst["emu_slices"]
     pairs = S * (S + 1) // 2
     peaks, peak_src = load_peaks()
-    roofline = {"bound": "tensor", "kernel": "k_gemm_emu (tcgen05 BF16 digit-slice products, batched work lists)",
+    roofline = {"bound": "tensor", "kernel": "k_gemm_emu (tcgen05 FP16 digit-slice products, batched work lists)",
                 "achieved": stage_fl * pairs / (stage_ms * 1e-3) / 1e12, "peak": peaks["bf16_tflops_sustained"],
                 "unit": "TFLOP/s", "traffic": None,
-                "note": f"algorithmic = the {pairs} BF16 digit-pair products per emulated FP64 product (S={S}) of "
+                "note": f"algorithmic = the {pairs} FP16 digit-pair products per emulated FP64 product (S={S}) of "
                         "every matrix's upper-triangle (or full) product; ragged tiles padded to 128 are not counted",
                 "fp64_equivalent_tflops": stage_fl / (stage_ms * 1e-3) / 1e12,
-                "peak_source": f"{peak_src} bf16 sustained (kernel timed inside a long step)",
+                "peak_source": f"{peak_src} bf16 sustained x nominal fp16/bf16 ratio 1 (kernel timed inside a long step)",
                 "launches_timed": stages, "avg_launch_ms": stage_ms / stages if stages else None,
                 "product_kernel_share": stage_ms / (ms * args.steps)}
     roofline["frac"] = roofline["achieved"] / roofline["peak"]
@@ -310,7 +310,7 @@ def run_batched(args):
         stat[P.STATUS_NAMES[s_]] = stat.get(P.STATUS_NAMES[s_], 0) + 1
     line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "emu64(bf16 slices)", "data": "synthetic", "config": batched_config(args),
+            "dtype": "emu64(fp16 slices)", "data": "synthetic", "config": batched_config(args),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(),
             "batch": {"statuses": stat, "iterations_max": max(its), "iterations_mean": float(np.mean(its)),
@@ -438,12 +438,12 @@ def run_learned(args):
     S = s1["emu_slices"]
     pairs = S * (S + 1) // 2
     peaks, peak_src = load_peaks()
-    roofline = {"bound": "tensor", "kernel": "k_gemm_emu (tcgen05 BF16 digit-slice products)",
+    roofline = {"bound": "tensor", "kernel": "k_gemm_emu (tcgen05 FP16 digit-slice products)",
                 "achieved": dfl * pairs / (dms * 1e-3) / 1e12, "peak": peaks["bf16_tflops_sustained"],
                 "unit": "TFLOP/s", "traffic": None,
-                "note": f"algorithmic = the {pairs} BF16 digit-pair products per emulated FP64 product (S={S})",
+                "note": f"algorithmic = the {pairs} FP16 digit-pair products per emulated FP64 product (S={S})",
                 "fp64_equivalent_tflops": dfl / (dms * 1e-3) / 1e12,
-                "peak_source": f"{peak_src} bf16 sustained (kernel timed inside a long step)",
+                "peak_source": f"{peak_src} bf16 sustained x nominal fp16/bf16 ratio 1 (kernel timed inside a long step)",
                 "launches_timed": dn, "avg_launch_ms": dms / dn if dn else None,
                 "product_kernel_share": dms / (ms * args.steps)}
     roofline["frac"] = roofline["achieved"] / roofline["peak"]
@@ -492,7 +492,7 @@ def run_learned(args):
     used = sum(1 for x in info if x[2] == P.PR_C0_POLY)
     line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "emu64(bf16 slices)", "data": "synthetic", "config": learned_config(args),
+            "dtype": "emu64(fp16 slices)", "data": "synthetic", "config": learned_config(args),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(),
             "learned": {"matrices": len(test), "guess_used": used, "gate_values": [round(x[3], 4) for x in info],
@@ -610,13 +610,13 @@ def main():
     if dom == P.PR_EMU64:
         pairs = S * (S + 1) // 2
         exec_fl = dfl * pairs
-        roofline = {"bound": "tensor", "kernel": "k_gemm_emu (tcgen05 BF16 digit-slice products)",
+        roofline = {"bound": "tensor", "kernel": "k_gemm_emu (tcgen05 FP16 digit-slice products)",
                     "achieved": exec_fl / (dms * 1e-3) / 1e12, "peak": peaks["bf16_tflops_sustained"],
                     "unit": "TFLOP/s", "traffic": None,
-                    "note": f"algorithmic = the {pairs} BF16 digit-pair products per emulated FP64 product "
+                    "note": f"algorithmic = the {pairs} FP16 digit-pair products per emulated FP64 product "
                             f"(S={S}), upper-triangle tiles; fp64_equivalent_tflops = FP64 flops / time",
                     "fp64_equivalent_tflops": dfl / (dms * 1e-3) / 1e12,
-                    "peak_source": f"{peak_src} bf16 sustained (kernel timed inside a long step)"}
+                    "peak_source": f"{peak_src} bf16 sustained x nominal fp16/bf16 ratio 1 (kernel timed inside a long step)"}
     elif dom == P.PR_BF16:
         roofline = {"bound": "tensor", "kernel": "k_gemm_bf16_tc", "achieved": dfl / (dms * 1e-3) / 1e12,
                     "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s", "traffic": None,
@@ -676,7 +676,7 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-                "vs_baseline": None, "dtype": {"fast": "bf16+emu64(bf16 slices)", "emu64": "emu64(bf16 slices)",
+                "vs_baseline": None, "dtype": {"fast": "bf16+emu64(fp16 slices)", "emu64": "emu64(fp16 slices)",
                                                "fp64": "f64"}[args.mode],
                 "data": "synthetic", "config": config_dict(args, ps), "roofline": roofline,
                 "kernel_time_share": kernel_share, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

@@ -57,10 +57,11 @@ typedef enum {
 /* Arithmetic of the matrix products. */
 typedef enum {
   PR_FP64 = 0,   /* native FP64 products (DMMA tensor instructions), FP64 accumulation                   */
-  PR_EMU64 = 1,  /* FP64-accurate products from exact BF16 digit slices on the tcgen05 tensor cores:
-                    every row of an operand is split into S (default 9) balanced base-128 digits with a
-                    row exponent; each digit pair with s + t <= S + 1 is an exact FP32 tensor-core
-                    product (K chunks of at most 4096), summed in int32 per level and FP64 overall   */
+  PR_EMU64 = 1,  /* FP64-accurate products from exact FP16 digit slices on the tcgen05 tensor cores:
+                    every row of an operand is split into S (default 8) balanced base-256 digits with a
+                    row exponent; the digit pairs with s + t <= S + 1 are exact FP16 tensor-core
+                    products, summed per level s + t exactly in FP32 (drained every 128 terms) and then
+                    in 128-bit integers, rounded once to FP64                                          */
   PR_BF16 = 3    /* BF16 operands, FP32 accumulation in TMEM (tcgen05 kind::f16); FP64 master copies     */
 } pr_precision;
 
@@ -94,8 +95,8 @@ typedef struct {
   double stag_ratio;   /* ... and fires when r_k > stag_ratio * r_{k-1}, default 0.5                      */
   double sym_tol;      /* pr_init rejects A with max|a_ij - a_ji| > sym_tol * max|a_ij|, default 1e-12   */
   int reanchor;        /* coupled form: on a switch to higher precision recompute M = X^p A, default 1  */
-  int emu_slices;      /* PR_EMU64 digit planes per operand, 1..9 (0 = the default, 9): S planes keep
-                          7S bits per row and cost S (S + 1) / 2 BF16 products per FP64 product         */
+  int emu_slices;      /* PR_EMU64 digit planes per operand, 1..8 (0 = the default, 8): S planes keep
+                          8S bits per row and cost S (S + 1) / 2 FP16 products per FP64 product         */
   double stag_below_lowp; /* stag_below for low-precision (PR_BF16) residuals, whose floor is higher,
                              default 0.5 (below 0.5 every eigencomponent is in the quadratic phase)      */
   double c0_coef[4];   /* PR_C0_POLY coefficients c_0 .. c_3, default (1, 0, 0, 0) (the scaled identity)  */
@@ -124,7 +125,7 @@ typedef struct {
   int64_t gemms_timed;      /* products timed with CUDA events (pr_set_timing)                           */
   double gemm_ms;           /* summed event time of the timed products                                     */
   double gemm_flops_timed;  /* algorithmic flops of the timed products                                     */
-  int emu_slices;           /* digit planes per operand used by PR_EMU64 (S; S (S + 1) / 2 BF16 products
+  int emu_slices;           /* digit planes per operand used by PR_EMU64 (S; S (S + 1) / 2 FP16 products
                                per emulated product)                                                     */
   int64_t gemms_timed_by_precision[4];  /* the timed counters above, split by pr_precision            */
   double gemm_ms_by_precision[4];
@@ -239,7 +240,7 @@ int64_t pr_batch_launches(pr_batch b);
 
 /* Counters of a batch. A "product" is one matrix's share of one stage; its FP64-equivalent algorithmic
  * flops are n^2 (n + 1) for a symmetric product (upper tiles) and 2 n^3 for a full one. The executed
- * tensor-core work is emu_slices (emu_slices + 1) / 2 BF16 digit-pair products of each. */
+ * tensor-core work is emu_slices (emu_slices + 1) / 2 FP16 digit-pair products of each. */
 typedef struct {
   int64_t launches;          /* kernels launched so far */
   int64_t stages;            /* product launches */

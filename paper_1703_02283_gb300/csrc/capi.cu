@@ -25,7 +25,7 @@ int precision_level(int prec) { return prec == PR_BF16 ? 1 : 2; }
 struct Mat {
   double* f = nullptr;
   __nv_bfloat16* b = nullptr;
-  __nv_bfloat16* sl = nullptr;  // PR_EMU64: S digit planes of f (allocated on first use)
+  __half* sl = nullptr;         // PR_EMU64: S FP16 digit planes of f (allocated on first use)
   int* ex = nullptr;            // PR_EMU64: row exponents of the digit planes
   bool sl_valid = false;        // the digit planes describe the current f
 };
@@ -53,7 +53,10 @@ struct pr_handle_s {
   cudaStream_t stream = nullptr;
   int device = 0;
   int ldl = 0;  // leading dimension of the BF16 copies
-  int S = 9;    // digit planes per operand for PR_EMU64
+  int eld = 0;  // K extent of a PR_EMU64 digit-plane row (n rounded up to 16)
+  int S = 8;    // digit planes per operand for PR_EMU64
+  int4* emu_items[2] = {nullptr, nullptr};  // PR_EMU64 work lists: symmetric, full products
+  int emu_nitems[2] = {0, 0};
 
   // The input, the iterate X, the carried product M and operand N of the coupled form, their next
   // values, and two scratch products.
@@ -149,12 +152,12 @@ bool lowp(int prec) { return prec == PR_BF16; }
 pr_status ensure_slices(pr_handle h, Mat& m) {
   const int n = (int)h->n;
   if (!m.sl) {
-    PR_CK(h, cudaMalloc((void**)&m.sl, (size_t)h->S * (size_t)n * (size_t)h->ldl * sizeof(__nv_bfloat16)));
+    PR_CK(h, cudaMalloc((void**)&m.sl, (size_t)8 * (size_t)n * (size_t)h->eld * sizeof(__half)));
     PR_CK(h, cudaMalloc((void**)&m.ex, (size_t)n * sizeof(int)));
     m.sl_valid = false;
   }
   if (m.sl_valid) return PR_OK;
-  PR_CK(h, pr::slice(m.f, n, h->ldl, h->S, m.sl, m.ex, h->stream));
+  PR_CK(h, pr::slice(m.f, n, h->eld, h->S, m.sl, m.ex, h->stream));
   h->st.launches += 1;
   m.sl_valid = true;
   return PR_OK;
@@ -210,7 +213,9 @@ pr_status product(pr_handle h, int prec, Mat& X, Mat& Y, Mode mode, const Out& o
       PR_CK(h, pr::gemm_bf16_tc(X.b, Y.b, n, h->ldl, mode, o.transpose, e, h->err_word(), h->stream));
       break;
     case PR_EMU64:
-      PR_CK(h, pr::gemm_emu(X.sl, X.ex, Y.sl, Y.ex, n, h->ldl, h->S, mode, o.transpose, e, h->err_word(), h->stream));
+      PR_CK(h, pr::gemm_emu(X.sl, X.ex, Y.sl, Y.ex, n, h->eld, h->S, mode, o.transpose,
+                            h->emu_items[mode == Mode::Sym ? 0 : 1], h->emu_nitems[mode == Mode::Sym ? 0 : 1], e,
+                            h->err_word(), h->stream));
       h->lp_stale = true;
       break;
     default:
@@ -612,6 +617,8 @@ pr_status pr_destroy(pr_handle h) {
   }
   for (double* b : {h->partial, h->work, h->scal, h->vec})
     if (b) cudaFree(b);
+  for (int4* it : h->emu_items)
+    if (it) cudaFree(it);
   if (h->hpin) cudaFreeHost(h->hpin);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   delete h;
@@ -634,7 +641,7 @@ pr_status pr_init(pr_handle* out, const double* A, int64_t n, int p, const pr_op
     return fail(nullptr, PR_EINVAL, "pr_init: bad gate options");
   if (o.form == PR_FORM_NS && p != 1) return fail(nullptr, PR_EINVAL, "pr_init: the Newton-Schulz form needs p = 1");
   if (o.max_iter < 0 || !(o.stag_ratio > 0) || !(o.sym_tol >= 0) || !(o.stag_below_lowp >= 0) ||
-      o.emu_slices < 0 || o.emu_slices > 9)
+      o.emu_slices < 0 || o.emu_slices > pr::emu_max_slices())
     return fail(nullptr, PR_EINVAL, "pr_init: bad option value");
 
   pr_handle h = new pr_handle_s();
@@ -644,7 +651,8 @@ pr_status pr_init(pr_handle* out, const double* A, int64_t n, int p, const pr_op
   h->form = o.form == PR_FORM_AUTO ? (p == 1 ? PR_FORM_NS : PR_FORM_COUPLED) : o.form;
   h->stream = (cudaStream_t)stream;
   h->ldl = pr::bf16_ld((int)n);
-  h->S = o.emu_slices > 0 ? o.emu_slices : 9;
+  h->eld = pr::emu_ld((int)n);
+  h->S = o.emu_slices > 0 ? o.emu_slices : pr::emu_max_slices();
   h->st.emu_slices = h->S;
   h->st.n = n;
   h->st.p = p;
@@ -682,6 +690,13 @@ pr_status pr_init(pr_handle* out, const double* A, int64_t n, int p, const pr_op
   PR_INIT_CK(cudaMalloc((void**)&h->scal, sizeof(double) * 8));
   PR_INIT_CK(cudaMemset(h->scal, 0, sizeof(double) * 8));
   PR_INIT_CK(cudaMallocHost((void**)&h->hpin, sizeof(double) * 8));
+  for (int k = 0; k < 2; ++k) {  // the PR_EMU64 work lists of this order (symmetric, full)
+    std::vector<int4> items;
+    pr::emu_tile_list(0, (int)n, k == 0 ? Mode::Sym : Mode::Full, items);
+    h->emu_nitems[k] = (int)items.size();
+    PR_INIT_CK(cudaMalloc((void**)&h->emu_items[k], items.size() * sizeof(int4)));
+    PR_INIT_CK(cudaMemcpy(h->emu_items[k], items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  }
 #undef PR_INIT_CK
   pr_status s = pr_load(h, A);
   if (s != PR_OK) return bail(s);
@@ -876,26 +891,29 @@ pr_status pr_matmul(int precision, const double* X, const double* Y, int64_t n, 
   if (precision != PR_FP64 && precision != PR_BF16 && precision != PR_EMU64)
     return fail(nullptr, PR_EINVAL, "pr_matmul: unknown precision");
   cudaStream_t s = (cudaStream_t)stream;
-  const int ni = (int)n, ldl = pr::bf16_ld(ni), S = 9;
+  const int ni = (int)n, ldl = pr::bf16_ld(ni), S = pr::emu_max_slices();
   const size_t bytes = (size_t)n * (size_t)n * sizeof(double);
-  const size_t lbytes = (size_t)n * (size_t)ldl * sizeof(__nv_bfloat16);
+  const int eld = pr::emu_ld(ni);
+  const size_t lbytes = precision == PR_EMU64 ? (size_t)8 * (size_t)n * (size_t)eld * sizeof(__half)
+                                              : (size_t)n * (size_t)ldl * sizeof(__nv_bfloat16);
   const Mode mode = sym ? Mode::Sym : Mode::Full;
   double *dX = nullptr, *dY = nullptr, *dP = nullptr;
   __nv_bfloat16 *bX = nullptr, *bY = nullptr;
   int *err = nullptr, *eX = nullptr, *eY = nullptr;
+  int4* items = nullptr;
+  std::vector<int4> hitems;
   cudaError_t e = cudaSuccess;
   int word = 0;
   auto step = [&](cudaError_t r) {
     if (e == cudaSuccess) e = r;
   };
-  const size_t planes = precision == PR_EMU64 ? (size_t)S : (size_t)1;
   step(cudaMalloc((void**)&dX, bytes));
   step(cudaMalloc((void**)&dY, bytes));
   step(cudaMalloc((void**)&dP, bytes));
   step(cudaMalloc((void**)&err, sizeof(int)));
   if (precision != PR_FP64) {
-    step(cudaMalloc((void**)&bX, planes * lbytes));
-    step(cudaMalloc((void**)&bY, planes * lbytes));
+    step(cudaMalloc((void**)&bX, lbytes));
+    step(cudaMalloc((void**)&bY, lbytes));
     step(cudaMalloc((void**)&eX, (size_t)n * sizeof(int)));
     step(cudaMalloc((void**)&eY, (size_t)n * sizeof(int)));
   }
@@ -912,15 +930,19 @@ pr_status pr_matmul(int precision, const double* X, const double* Y, int64_t n, 
       step(pr::to_bf16(dY, ni, ldl, bY, s));
       step(pr::gemm_bf16_tc(bX, bY, ni, ldl, mode, false, ep, err, s));
     } else {
-      step(pr::slice(dX, ni, ldl, S, bX, eX, s));
-      step(pr::slice(dY, ni, ldl, S, bY, eY, s));
-      step(pr::gemm_emu(bX, eX, bY, eY, ni, ldl, S, mode, false, ep, err, s));
+      __half *hX = reinterpret_cast<__half*>(bX), *hY = reinterpret_cast<__half*>(bY);
+      pr::emu_tile_list(0, ni, mode, hitems);
+      step(cudaMalloc((void**)&items, hitems.size() * sizeof(int4)));
+      step(cudaMemcpyAsync(items, hitems.data(), hitems.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+      step(pr::slice(dX, ni, eld, S, hX, eX, s));
+      step(pr::slice(dY, ni, eld, S, hY, eY, s));
+      step(pr::gemm_emu(hX, eX, hY, eY, ni, eld, S, mode, false, items, (int)hitems.size(), ep, err, s));
     }
     step(cudaMemcpyAsync(P, dP, bytes, cudaMemcpyDefault, s));
     step(cudaMemcpyAsync(&word, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     step(cudaStreamSynchronize(s));
   }
-  for (void* q : {(void*)dX, (void*)dY, (void*)dP, (void*)bX, (void*)bY, (void*)err, (void*)eX, (void*)eY})
+  for (void* q : {(void*)dX, (void*)dY, (void*)dP, (void*)bX, (void*)bY, (void*)err, (void*)eX, (void*)eY, (void*)items})
     if (q) cudaFree(q);
   if (e != cudaSuccess) return cuda_fail(nullptr, "pr_matmul", e);
   if (word != 0) return fail(nullptr, PR_ETIMEOUT, "pr_matmul: a bounded device wait expired");

@@ -26,7 +26,7 @@ thread_local std::string g_batch_error;
 
 struct Buf {  // a packed FP64 buffer and its digit planes
   double* f = nullptr;
-  __nv_bfloat16* sl = nullptr;
+  __half* sl = nullptr;
   int* ex = nullptr;
   bool sl_valid = false;
 };
@@ -34,7 +34,7 @@ struct Buf {  // a packed FP64 buffer and its digit planes
 
 struct pr_batch_s {
   int count = 0;
-  int S = 9;
+  int S = 8;
   int R = 0;   // packed rows (sum of the orders)
   int K = 0;   // largest order
   int ld = 0;  // leading dimension of the packed buffers (K rounded up to 8)
@@ -84,7 +84,7 @@ pr_status bfail(pr_batch b, pr_status code, const std::string& msg) {
 
 pr_status ensure_slices(pr_batch b, Buf& x) {
   if (x.sl_valid) return PR_OK;
-  PB_CK(b, pr::slice_rows(x.f, b->R, b->K, b->ld, b->ld, b->S, b->row_n, x.sl, x.ex, b->stream));
+  PB_CK(b, pr::slice_rows(x.f, b->R, b->K, b->ld, pr::emu_ld(b->K), b->S, b->row_n, x.sl, x.ex, b->stream));
   b->launches += 1;
   x.sl_valid = true;
   return PR_OK;
@@ -117,10 +117,8 @@ pr_status stage(pr_batch b, Buf& Xb, Buf& Yb, Mode mode, const std::vector<int>&
   for (size_t w = 0; w < who.size(); ++w) mats[who[w]] = EmuBatchMat{b->n[who[w]], b->row0[who[w]], coef[w].x, coef[w].y,
                                                                     coef[w].z};
   for (int m : sorted) {
-    const int T = (b->n[m] + 127) / 128;
     if (seg_begin) (*seg_begin)[m] = (int)items.size() * per;
-    for (int bi = 0; bi < T; ++bi)
-      for (int bj = (mode == Mode::Sym ? bi : 0); bj < T; ++bj) items.push_back(make_int4(m, bi, bj, 0));
+    pr::emu_tile_list(m, b->n[m], mode, items);
     if (seg_end) (*seg_end)[m] = (int)items.size() * per;
   }
   if ((int)items.size() > b->items_cap) return bfail(b, PR_ECUDA, "pr_batch: work list larger than allocated");
@@ -137,7 +135,7 @@ pr_status stage(pr_batch b, Buf& Xb, Buf& Yb, Mode mode, const std::vector<int>&
   e.cin = so.cin;
   e.partial = so.partial ? b->partial : nullptr;
   if (b->timing) PB_CK(b, cudaEventRecord(b->ev0, b->stream));
-  PB_CK(b, pr::gemm_emu_batched(Xb.sl, Xb.ex, Yb.sl, Yb.ex, b->R, b->K, b->ld, b->ld, b->S, mode, so.transpose,
+  PB_CK(b, pr::gemm_emu_batched(Xb.sl, Xb.ex, Yb.sl, Yb.ex, b->R, b->K, pr::emu_ld(b->K), b->ld, b->S, mode, so.transpose,
                                 b->items, (int)items.size(), b->mats, e, b->err, b->stream));
   if (b->timing) PB_CK(b, cudaEventRecord(b->ev1, b->stream));
   b->launches += 1;
@@ -250,7 +248,7 @@ pr_status pr_batch_init(pr_batch* out, int count, const int64_t* n, const int* p
   else pr_default_options(&o);
   if (o.form != PR_FORM_AUTO) return bfail(nullptr, PR_EINVAL, "pr_batch_init: batches run the automatic forms");
   if (o.c0 != PR_C0_EQ3 && o.c0 != PR_C0_SCALED_I) return bfail(nullptr, PR_EINVAL, "pr_batch_init: unknown c0");
-  if (o.emu_slices < 0 || o.emu_slices > 9 || o.max_iter < 0)
+  if (o.emu_slices < 0 || o.emu_slices > pr::emu_max_slices() || o.max_iter < 0)
     return bfail(nullptr, PR_EINVAL, "pr_batch_init: bad option value");
   int64_t R = 0, K = 0;
   for (int m = 0; m < count; ++m) {
@@ -264,7 +262,7 @@ pr_status pr_batch_init(pr_batch* out, int count, const int64_t* n, const int* p
   pr_batch b = new pr_batch_s();
   b->count = count;
   b->opt = o;
-  b->S = o.emu_slices > 0 ? o.emu_slices : 9;
+  b->S = o.emu_slices > 0 ? o.emu_slices : pr::emu_max_slices();
   b->R = (int)R;
   b->K = (int)K;
   b->ld = (int)((K + 7) / 8 * 8);
@@ -300,7 +298,7 @@ pr_status pr_batch_init(pr_batch* out, int count, const int64_t* n, const int* p
     }                                                                                                \
   } while (0)
   const size_t fbytes = (size_t)b->R * b->ld * sizeof(double);
-  const size_t sbytes = (size_t)b->S * b->R * b->ld * sizeof(__nv_bfloat16);
+  const size_t sbytes = (size_t)8 * b->R * pr::emu_ld(b->K) * sizeof(__half);
   for (Buf* x : {&b->A, &b->X, &b->Xn, &b->M, &b->Mn, &b->N, &b->Nn, &b->T0, &b->T1}) {
     PB_INIT_CK(cudaMalloc((void**)&x->f, fbytes));
     PB_INIT_CK(cudaMemsetAsync(x->f, 0, fbytes, b->stream));
@@ -310,10 +308,7 @@ pr_status pr_batch_init(pr_batch* out, int count, const int64_t* n, const int* p
   PB_INIT_CK(cudaMalloc((void**)&b->result, fbytes));
   PB_INIT_CK(cudaMalloc((void**)&b->row_n, (size_t)b->R * sizeof(int)));
   int64_t items = 0;
-  for (int m = 0; m < count; ++m) {
-    const int64_t T = (n[m] + 127) / 128;
-    items += T * T;
-  }
+  for (int m = 0; m < count; ++m) items += pr::emu_tile_count((int)n[m], Mode::Full);
   b->items_cap = (int)items;
   b->partial_cap = (int)(items * pr::emu_partials_per_item());
   PB_INIT_CK(cudaMalloc((void**)&b->items, (size_t)items * sizeof(int4)));

@@ -1,47 +1,62 @@
-// FP64-accurate matrix products from exact BF16 digit slices on the tcgen05 tensor cores (PR_EMU64).
+// FP64-accurate matrix products from exact FP16 digit slices on the tcgen05 tensor cores (PR_EMU64).
 //
-// GB300 executes FP64 at about 1/1800 of its BF16 tensor rate, so the FP64-accurate iterations of Eq. 1
-// (Sec. 3: precise refinement) are built from exact low-precision pieces, following the error-free
-// splitting of Ozaki, Ogita, Oishi and Rump ("Error-free transformations of matrix multiplication by using
-// fast routines of matrix multiplication and its applications", Numer. Algorithms 59, 2012):
+// GB300 executes FP64 at about 1/1800 of its half-precision tensor rate, so the FP64-accurate iterations
+// of Eq. 1 (Sec. 3: precise refinement) are built from exact low-precision pieces, following the
+// error-free splitting of Ozaki, Ogita, Oishi and Rump ("Error-free transformations of matrix
+// multiplication by using fast routines of matrix multiplication and its applications", Numer.
+// Algorithms 59, 2012):
 //
 //  * slicing (k_slice): for row i of X let e_i be the smallest integer with max_k |x_ik| < 2^(e_i - 1). The
-//    integer F_ik = round(x_ik 2^(7S - e_i)) (|F| < 2^(7S - 1)) is written in balanced base 128,
-//    F = sum_{s=1..S} d_s 128^(S-s) with |d_s| <= 64, so x_ik = 2^e_i sum_s d_s 2^(-7s) up to 2^(e_i - 7S - 1).
-//    The digits are small integers, exact in BF16. Integer arithmetic only.
-//  * products (k_gemm_emu): P_ij = 2^(e_i + f_j) sum_{s + t <= S + 1} 2^(-7(s + t)) sum_k dX_s,ik dY_t,jk. Each
-//    inner sum over at most 4096 terms is an integer of magnitude <= 4096 * 64 * 64 = 2^24, so the FP32
-//    accumulation of the tensor cores computes it exactly. Pairs are taken level by level (L = s + t); the
-//    exact pair results of a level are summed in int32, and each level is added into an FP64 total.
-//    Dropping the pairs with s + t > S + 1 and the digits beyond S leaves an error of about
-//    (S + 1) 2^(-7S - 2) in units of 2^(e_i + f_j) per product term: S = 9 (the default) gives 2^-62. F must
-//    fit in 64-bit integers, which limits S to 9.
+//    integer F_ik = round(x_ik 2^(8S - e_i)) (|F| < 2^(8S - 1)) is written in balanced base 256,
+//    F = sum_{s=1..S} d_s 256^(S-s) with |d_s| <= 128, so x_ik = 2^e_i sum_s d_s 2^(-8s) up to 2^(e_i - 8S - 1).
+//    The digits are small integers, exact in FP16. Integer arithmetic only.
+//  * products (k_gemm_emu): P_ij = 2^(e_i + f_j) sum_{L=2..S+1} 2^(-8L) V_L with the level sums
+//    V_L = sum_{s + t = L} sum_k dX_s,ik dY_t,jk. Each digit product is at most 2^14 in magnitude, so a
+//    level (at most 8 pairs) summed over 128 values of k stays within 2^24 and the FP32 accumulation of
+//    the tensor cores is exact. Dropping the pairs with s + t > S + 1 and the digits beyond S leaves an
+//    error of about (S + 2) 2^(-8S - 2) in units of 2^(e_i + f_j) per product term: S = 8 (the default)
+//    gives 2^-63. F must fit in 64-bit integers, which limits S to 8.
 //
-// k_gemm_emu is a persistent kernel, one CTA per SM, 128 x 128 output tiles (symmetric mode: upper
-// triangle only, mirrored), 320 threads: warp 0 TMA producer (6-stage ring of 128 x 64 digit boxes), warp 1
-// MMA issuer (M = N = 128, K = 16, one pass over K per pair into one of two 128-column TMEM accumulators),
-// warps 2-9 epilogue (two warps per TMEM lane quadrant, 64 columns each): per pair they convert the exact
-// FP32 result to int32 and add it to the level sum while the MMA warp fills the other accumulator; at a
-// level end they add the level into an FP64 total kept in TMEM columns 256..511; after the last level
-// they scale by 2^(e_i + f_j) and apply the fused FP64 epilogue. Waits are bounded as in k_gemm_tc.cu.
+// Data movement. All digit planes of both operands for one 16-wide step of k sit in shared memory at
+// once (one TMA box per operand), and every pair (s, t) of the step is issued from them: each plane is
+// fetched once per step instead of once per pair. In memory the 16 digits of a step are stored for 4
+// planes side by side (layout [row][step][plane][16]), so a box row is 128 contiguous bytes (one request)
+// and lands 128-byte swizzled in shared memory, where plane s is the 32-byte K slice s % 4 of group s / 4.
+// The planes of X are copied into tensor memory (tcgen05.cp) and the MMAs read them there, so shared
+// memory serves only the Y planes to the tensor cores.
+//
+// k_gemm_emu is a persistent kernel, one CTA per SM, 128 x 48 output tiles taken from a work list
+// (matrix, tile row, tile column), 448 threads: warp 0 TMA producer (5-stage ring), warp 1 copies the X
+// planes into tensor memory, warps 2-5 issue the MMAs (warp w owns levels 9 - w and 2 + w, 9 pairs per
+// step each: one issuing thread cannot keep the tensor cores busy with 128 x 48 x 16 MMAs, four can),
+// warps 6-13 epilogue (two warps per TMEM lane quadrant, 24 columns each). Tensor memory holds one FP32
+// accumulator per level (8 x 48 columns) and two buffers of X planes (2 x 64 columns). A level's
+// accumulator is drained every 8 steps, the levels staggered so that one drain falls on each step: the
+// epilogue warps convert the exact FP32 values to integers and add them, shifted, into two exact int64
+// totals per element; at the tile's end they round the 128-bit total once to FP64 (integer arithmetic),
+// scale by 2^(e_i + f_j) and apply the fused epilogue. Every wait is bounded as in k_gemm_tc.cu.
 #include "pr_internal.h"
 #include "tc_ptx.h"
 
+#include <cuda_fp16.h>
 #include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <vector>
 
 namespace pr {
 namespace {
 
-constexpr int EBM = 128, EBN = 128, EBK = 64, ESTAGES = 6;
-constexpr int EPI_WARPS = 8, THREADS = 64 + 32 * EPI_WARPS;
-constexpr int BOX_BYTES = EBM * EBK * 2, STAGE_BYTES = 2 * BOX_BYTES;
-constexpr int SMEM_BYTES = 1024 + ESTAGES * STAGE_BYTES + 256;
-constexpr int KCHUNK_BLOCKS = 4096 / EBK;  // K blocks per exact pass: 4096 * 64 * 64 = 2^24
-constexpr int TOTAL_COL = 2 * EBN;         // TMEM column of the FP64 totals (2 words per element)
-// Levels summed exactly in int64 before one FP64 addition: a level sum is below S * n * 2^12 <= 2^31, and
-// kGroup levels Horner-combined with 7-bit shifts stay below 2^(31 + 7 (kGroup - 1)) <= 2^59.
-constexpr int kGroup = 5;
-constexpr uint32_t kIdesc = ptx::idesc_bf16_f32(EBM, EBN);
+constexpr int EBM = 128, EBN = 48, EBK = 16, NSTAGE = 5, SMAX = 8, BAND = 8;
+constexpr int MMA_WARPS = 4, EPI_WARPS = 8, THREADS = 32 * (2 + MMA_WARPS + EPI_WARPS);
+constexpr int A_GROUP = EBM * 128, B_GROUP = EBN * 128;  // bytes of 4 planes (one 128-byte row per row)
+constexpr int A_BYTES = 2 * A_GROUP, STAGE_BYTES = A_BYTES + 2 * B_GROUP;
+constexpr int NBARS = 2 * NSTAGE + 2 * SMAX + 2 + 2 + 1;
+constexpr int SMEM_BYTES = 1024 + NSTAGE * STAGE_BYTES + 8 * NBARS + 16;
+constexpr int ACOL = SMAX * EBN;        // TMEM column of the first X-plane buffer (after the accumulators)
+constexpr uint32_t kIdesc = ptx::idesc_f16_f32(EBM, EBN);
+static_assert(ACOL + 2 * SMAX * 8 <= 512, "tensor memory budget");
+static_assert(STAGE_BYTES % 1024 == 0, "stage alignment");
 
 // ------------------------------------------------------------------------------------------ slicing
 
@@ -53,26 +68,26 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
   return v;
 }
 
-// F = round(x 2^(7S - e)) of one double as an integer (|F| < 2^(7S - 1) for |x| < 2^(e - 1)).
+// F = round(x 2^(8S - e)) of one double as an integer (|F| < 2^(8S - 1) for |x| < 2^(e - 1)).
 __device__ __forceinline__ long long fixed_point(unsigned long long u, int e, int S) {
   const int E = (int)((u >> 52) & 0x7ff);
   if (E == 0) return 0;  // zero, or a subnormal far below the last digit
   const unsigned long long M = (u & 0xfffffffffffffull) | (1ull << 52);
-  const int sh = (E - 1023) - e + 7 * S - 52;  // F = M 2^sh, sh <= 7S - 54
+  const int sh = (E - 1023) - e + 8 * S - 52;  // F = M 2^sh, sh <= 8S - 54
   long long F = 0;
   if (sh >= 0) F = (long long)(M << sh);
   else if (sh > -64) F = (long long)((M + (1ull << (-sh - 1))) >> (-sh));
   return (u >> 63) ? -F : F;
 }
 
-// One warp per row r of an R-row FP64 array (leading dimension ldx): exponent e_r, then S digit planes
-// D[s][r][k] (plane s at s R ldl; s = 0 is the most significant digit). Row r has row_n[r] valid columns
-// (all rows n when row_n is null); the rest of the ldl columns get digit 0. Each lane handles two adjacent
-// columns (ldl is even), so loads are 16 bytes and stores bf16x2.
+// One warp per row r of an R-row FP64 array (leading dimension ldx): exponent e_r, then 8 digit planes in
+// the layout D[r][k / 16][s][k % 16] (row length 8 ldl halves, ldl a multiple of 16; s = 0 is the most
+// significant digit, planes s >= S are zero). Row r has row_n[r] valid columns (all rows n when row_n is
+// null); the rest of the ldl columns get digit 0. Each lane handles two adjacent columns, so loads are 16
+// bytes and stores half2.
 __global__ void k_slice(const double* __restrict__ X, int R, int n, int ldx, int ldl, int S,
-                        const int* __restrict__ row_n, __nv_bfloat16* __restrict__ D, int* __restrict__ ex) {
+                        const int* __restrict__ row_n, __half* __restrict__ D, int* __restrict__ ex) {
   const int lane = threadIdx.x & 31;
-  const int64_t plane = (int64_t)R * ldl;
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < R; i += (gridDim.x * blockDim.x) >> 5) {
     const int nr = row_n ? row_n[i] : n;
     const unsigned long long* row = reinterpret_cast<const unsigned long long*>(X + (int64_t)i * ldx);
@@ -91,33 +106,22 @@ __global__ void k_slice(const double* __restrict__ X, int R, int n, int ldx, int
         if (k < nr) F0 = fixed_point(row[k], e, S);
         if (k + 1 < nr) F1 = fixed_point(row[k + 1], e, S);
       }
-      __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(D + (int64_t)i * ldl + k);
-      // Balanced base-128 digits, least significant first; the last one takes the remainder (|.| <= 64).
+      __half2* dst = reinterpret_cast<__half2*>(D + (int64_t)i * 8 * ldl + (k >> 4) * 128 + (k & 15));
+      for (int s = S; s < SMAX; ++s) dst[8 * s] = __floats2half2_rn(0.0f, 0.0f);
+      // Balanced base-256 digits, least significant first; the last one takes the remainder (|.| <= 128).
       for (int s = S - 1; s >= 1; --s) {
-        const int r0 = (int)(F0 & 127), r1 = (int)(F1 & 127);
-        const int d0 = r0 >= 64 ? r0 - 128 : r0, d1 = r1 >= 64 ? r1 - 128 : r1;
-        F0 = (F0 - d0) >> 7;
-        F1 = (F1 - d1) >> 7;
-        dst[(int64_t)s * (plane / 2)] = __floats2bfloat162_rn((float)d0, (float)d1);
+        const int r0 = (int)(F0 & 255), r1 = (int)(F1 & 255);
+        const int d0 = r0 >= 128 ? r0 - 256 : r0, d1 = r1 >= 128 ? r1 - 256 : r1;
+        F0 = (F0 - d0) >> 8;
+        F1 = (F1 - d1) >> 8;
+        dst[8 * s] = __floats2half2_rn((float)d0, (float)d1);
       }
-      dst[0] = __floats2bfloat162_rn((float)F0, (float)F1);
+      dst[0] = __floats2half2_rn((float)F0, (float)F1);
     }
   }
 }
 
 // ------------------------------------------------------------------------------------------ products
-
-__device__ __forceinline__ void tri_index_emu(int t, int T, int& bi, int& bj) {
-  const double b = 2.0 * T + 1.0;
-  int r = (int)floor((b - sqrt(b * b - 8.0 * (double)t)) * 0.5);
-  if (r < 0) r = 0;
-  if (r > T - 1) r = T - 1;
-  auto start = [T](int q) { return q * T - (q * (q - 1)) / 2; };
-  while (r > 0 && start(r) > t) --r;
-  while (r + 1 < T && start(r + 1) <= t) ++r;
-  bi = r;
-  bj = r + (t - start(r));
-}
 
 // One matrix of a work list: its order, its first row in the packed layout, its epilogue coefficients.
 struct EmuMat {
@@ -127,13 +131,11 @@ struct EmuMat {
 
 struct EmuArgs {
   int S;                 // digit planes per operand
-  int R;                 // rows of one digit plane (the packed row count)
   int ld;                // leading dimension of the FP64 outputs and of cin
   int ntiles;            // work items
-  int T;                 // one matrix: tiles per side (items enumerated implicitly)
-  const int4* items;     // a batch: (matrix, bi, bj, -) per work item; null for one matrix
-  const EmuMat* mats;    // a batch: per-matrix data
-  EmuMat one;            // one matrix: its data
+  const int4* items;     // (matrix, tile row, tile column, -) per work item
+  const EmuMat* mats;    // per-matrix data; null: every item belongs to `one`
+  EmuMat one;
   int transpose;         // full mode: store P^T
   Epilogue e;            // output pointers are the bases of the (packed) FP64 buffers
   const int* ex;         // row exponents of X (indexed by packed row)
@@ -141,57 +143,107 @@ struct EmuArgs {
   int* err;
 };
 
-template <bool SYM>
 __device__ __forceinline__ const EmuMat& item_of(const EmuArgs& a, int t, int& bi, int& bj) {
-  if (a.items) {
-    const int4 it = a.items[t];
-    bi = it.y;
-    bj = it.z;
-    return a.mats[it.x];
-  }
-  if (SYM) {
-    tri_index_emu(t, a.T, bi, bj);
-  } else {
-    bi = t % a.T;
-    bj = t / a.T;
-  }
-  return a.one;
+  const int4 it = a.items[t];
+  bi = it.y;
+  bj = it.z;
+  return a.mats ? a.mats[it.x] : a.one;
 }
 
+// The level whose pairs come r-th in step j: the level drained after step j first (r = 0), the level
+// drained after step j - 1 last (r = 7). Levels 2..9 are the residues 2..7, 0, 1 modulo 8.
+__device__ __forceinline__ int level_at(int j, int r) {
+  const int lam = (7 - (j & 7) - r) & 7;
+  return lam < 2 ? lam + 8 : lam;
+}
 
-// x * 2^E for a finite double, by adding to the exponent field when the result stays normal.
-__device__ __forceinline__ double scale2(double x, int E) {
-  if (x == 0.0) return 0.0;
-  const long long u = __double_as_longlong(x);
-  const int be = (int)((u >> 52) & 0x7ff) + E;
-  if (be > 0 && be < 2047 && ((u >> 52) & 0x7ff) != 0) return __longlong_as_double(u + ((long long)E << 52));
-  return ldexp(x, E);
+// (H 2^64 + Lw) 2^E0 for a two's-complement 128-bit integer H:Lw, rounded once to the nearest double
+// (ties to even), in integer arithmetic.
+__device__ __forceinline__ double wide_to_double(long long H, unsigned long long Lw, int E0) {
+  const unsigned long long sign = (unsigned long long)H & 0x8000000000000000ull;
+  unsigned long long mh = (unsigned long long)H, ml = Lw;
+  if (sign) {
+    ml = ~ml + 1ull;
+    mh = ~mh + (ml == 0ull ? 1ull : 0ull);
+  }
+  if ((mh | ml) == 0ull) return 0.0;
+  const int lz = mh ? __clzll((long long)mh) : 64 + __clzll((long long)ml);
+  if (lz >= 64) {
+    mh = ml << (lz - 64);
+    ml = 0ull;
+  } else if (lz > 0) {
+    mh = (mh << lz) | (ml >> (64 - lz));
+    ml <<= lz;
+  }
+  unsigned long long mant = mh >> 11;  // 53 bits, the leading one at bit 52
+  const unsigned long long rest = mh & 0x7ffull;
+  if (rest > 0x400ull || (rest == 0x400ull && (ml != 0ull || (mant & 1ull)))) ++mant;
+  int ex = 127 - lz + E0;  // exponent of the leading one
+  if (mant >> 53) {
+    mant >>= 1;
+    ++ex;
+  }
+  const int be = ex + 1023;
+  if (be >= 1 && be <= 2046)
+    return __longlong_as_double((long long)(sign | ((unsigned long long)be << 52) | (mant & 0xfffffffffffffull)));
+  const double v = ldexp((double)mant, ex - 52);  // outside the normal range
+  return sign ? -v : v;
+}
+
+// The MMAs of one level L for S = 8 (pairs s = 1 .. L - 1, t = L - s), unrolled: X plane s - 1 from TMEM
+// buffer aT, Y plane t - 1 from the shared-memory slot whose first plane group has descriptor bdesc.
+template <int L>
+__device__ __forceinline__ void mma_level(uint32_t d, uint32_t aT, uint64_t bdesc, bool fresh) {
+#pragma unroll
+  for (int s = 1; s <= L - 1; ++s) {
+    const int t = L - s - 1;
+    ptx::mma_f16_ts(d, aT + 8 * (s - 1), bdesc + (uint64_t)(((t >> 2) * B_GROUP + (t & 3) * 32) >> 4), kIdesc,
+                    (fresh && s == 1) ? 0u : 1u);
+  }
+}
+
+__device__ __forceinline__ void mma_level_s8(int L, uint32_t d, uint32_t aT, uint64_t bdesc, bool fresh) {
+  switch (L) {
+    case 2: mma_level<2>(d, aT, bdesc, fresh); break;
+    case 3: mma_level<3>(d, aT, bdesc, fresh); break;
+    case 4: mma_level<4>(d, aT, bdesc, fresh); break;
+    case 5: mma_level<5>(d, aT, bdesc, fresh); break;
+    case 6: mma_level<6>(d, aT, bdesc, fresh); break;
+    case 7: mma_level<7>(d, aT, bdesc, fresh); break;
+    case 8: mma_level<8>(d, aT, bdesc, fresh); break;
+    default: mma_level<9>(d, aT, bdesc, fresh); break;
+  }
 }
 
 template <bool SYM>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(THREADS, 1)  // 14 warps: at most 128 registers (4 warps on a sub-partition)
     k_gemm_emu(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, EmuArgs args) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* ring = smem;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + ESTAGES * STAGE_BYTES);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * ESTAGES + 5);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NSTAGE * STAGE_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + NBARS);
   volatile int* s_abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
-  const int S = args.S, R = args.R, ld = args.ld, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t full0 = ptx::smem_u32(bars), empty0 = full0 + 8 * ESTAGES, tfull0 = empty0 + 8 * ESTAGES,
-                 tempty0 = tfull0 + 16, drain = tempty0 + 16;
+  const int S = args.S, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t full0 = ptx::smem_u32(bars), empty0 = full0 + 8 * NSTAGE, lfull0 = empty0 + 8 * NSTAGE,
+                 lempty0 = lfull0 + 8 * SMAX, abuf0 = lempty0 + 8 * SMAX, aready0 = abuf0 + 16,
+                 drain = aready0 + 16;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < ESTAGES; ++s) {
+    for (int s = 0; s < NSTAGE; ++s) {
       ptx::mbar_init(full0 + 8 * s, 1);
-      ptx::mbar_init(empty0 + 8 * s, 1);
+      ptx::mbar_init(empty0 + 8 * s, MMA_WARPS + 1);  // the MMA warps and the copy thread read the stage
+    }
+    for (int l = 0; l < SMAX; ++l) {
+      ptx::mbar_init(lfull0 + 8 * l, 1);
+      ptx::mbar_init(lempty0 + 8 * l, EPI_WARPS);
     }
     for (int b = 0; b < 2; ++b) {
-      ptx::mbar_init(tfull0 + 8 * b, 1);
-      ptx::mbar_init(tempty0 + 8 * b, EPI_WARPS);
+      ptx::mbar_init(abuf0 + 8 * b, MMA_WARPS);
+      ptx::mbar_init(aready0 + 8 * b, 1);
     }
-    ptx::mbar_init(drain, 1);
+    ptx::mbar_init(drain, MMA_WARPS + 1);
     *s_abort = 0;
     ptx::fence_barrier_init();
     ptx::prefetch_tmap(&tmX);
@@ -208,195 +260,230 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      // ---------------- TMA producer: for every tile, pair (by level) and K chunk, the K blocks of the chunk
+      // ---------------- TMA producer: per step, the S planes of X (128 rows) and of Y (48 rows)
+      const uint32_t tx = (uint32_t)STAGE_BYTES;
       int it = 0;
       bool stop = false;
       for (int t = blockIdx.x; t < args.ntiles && !stop; t += gridDim.x) {
         int bi, bj;
-        const EmuMat& mt = item_of<SYM>(args, t, bi, bj);
-        const int KB = (mt.n + EBK - 1) / EBK;
-        for (int L = 2; L <= S + 1 && !stop; ++L)
-          for (int s = 1; s <= L - 1 && !stop; ++s) {
-            const int ya = (s - 1) * R + mt.row0 + bi * EBM, yb = (L - s - 1) * R + mt.row0 + bj * EBN;
-            for (int kb = 0; kb < KB; ++kb, ++it) {
-              const int st = it % ESTAGES;
-              if (*s_abort || !ptx::mbar_wait(empty0 + 8 * st, ((it / ESTAGES) & 1) ^ 1, args.err, 11)) {
-                *s_abort = 1;
-                stop = true;
-                break;
-              }
-              uint8_t* sp = ring + st * STAGE_BYTES;
-              ptx::mbar_expect_tx(full0 + 8 * st, STAGE_BYTES);
-              ptx::tma_load_2d(ptx::smem_u32(sp), &tmX, full0 + 8 * st, kb * EBK, ya);
-              ptx::tma_load_2d(ptx::smem_u32(sp + BOX_BYTES), &tmY, full0 + 8 * st, kb * EBK, yb);
-            }
+        const EmuMat& mt = item_of(args, t, bi, bj);
+        const int KS = (mt.n + EBK - 1) / EBK, ya = mt.row0 + bi * EBM, yb = mt.row0 + bj * EBN;
+        for (int j = 0; j < KS; ++j, ++it) {
+          const int st = it % NSTAGE;
+          if (*s_abort || !ptx::mbar_wait(empty0 + 8 * st, ((it / NSTAGE) & 1) ^ 1, args.err, 11)) {
+            *s_abort = 1;
+            stop = true;
+            break;
           }
+          uint8_t* sp = ring + st * STAGE_BYTES;
+          ptx::mbar_expect_tx(full0 + 8 * st, tx);
+          for (int g = 0; g < 2; ++g) {
+            ptx::tma_load_3d(ptx::smem_u32(sp + g * A_GROUP), &tmX, full0 + 8 * st, 0, 2 * j + g, ya);
+            ptx::tma_load_3d(ptx::smem_u32(sp + A_BYTES + g * B_GROUP), &tmY, full0 + 8 * st, 0, 2 * j + g, yb);
+          }
+        }
       }
       if (*s_abort) {
-        for (int k = (it > ESTAGES ? it - ESTAGES : 0); k < it; ++k)
-          ptx::mbar_wait(full0 + 8 * (k % ESTAGES), (k / ESTAGES) & 1, nullptr, 0);
+        for (int k = (it > NSTAGE ? it - NSTAGE : 0); k < it; ++k)
+          ptx::mbar_wait(full0 + 8 * (k % NSTAGE), (k / NSTAGE) & 1, nullptr, 0);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // ---------------- MMA issuer: one "unit" = one pair over one K chunk, into TMEM buffer (unit & 1)
-      int it = 0, u = 0;
+      // ---------------- copy thread: per step, the X planes from shared memory into TMEM buffer (step & 1)
+      int it = 0;
       bool stop = false;
       for (int t = blockIdx.x; t < args.ntiles && !stop; t += gridDim.x) {
         int bi, bj;
-        const EmuMat& mt = item_of<SYM>(args, t, bi, bj);
-        const int KB = (mt.n + EBK - 1) / EBK, nchunks = (KB + KCHUNK_BLOCKS - 1) / KCHUNK_BLOCKS;
-        for (int L = 2; L <= S + 1 && !stop; ++L)
-          for (int s = 1; s <= L - 1 && !stop; ++s)
-            for (int c = 0; c < nchunks && !stop; ++c, ++u) {
-              const int b = u & 1;
-              if (*s_abort || !ptx::mbar_wait(tempty0 + 8 * b, ((u >> 1) & 1) ^ 1, args.err, 12)) {
+        const EmuMat& mt = item_of(args, t, bi, bj);
+        const int KS = (mt.n + EBK - 1) / EBK;
+        for (int j = 0; j < KS; ++j, ++it) {
+          const int st = it % NSTAGE, b = it & 1;
+          if (*s_abort || !ptx::mbar_wait(full0 + 8 * st, (it / NSTAGE) & 1, args.err, 12) ||
+              (it >= 2 && !ptx::mbar_wait(abuf0 + 8 * b, ((it - 2) >> 1) & 1, args.err, 13))) {
+            *s_abort = 1;
+            stop = true;
+            break;
+          }
+          ptx::tc_fence_after();
+          const uint32_t sa = ptx::smem_u32(ring + st * STAGE_BYTES), aT = tmem + (uint32_t)(ACOL + 64 * b);
+          for (int s = 0; s < S; ++s)
+            ptx::tmem_cp_128x256b(aT + 8 * s, ptx::desc_sw128_kmajor(sa + (s >> 2) * A_GROUP + (s & 3) * 32));
+          ptx::mma_commit(aready0 + 8 * b);
+          ptx::mma_commit(empty0 + 8 * st);
+          
+        }
+      }
+      ptx::mma_commit(drain);
+      ptx::mbar_wait(drain, 0, nullptr, 0);
+    }
+  } else if (warp < 2 + MMA_WARPS) {
+    if (lane == 0) {
+      // ---------------- MMA warp w: levels 9 - w and 2 + w (9 pairs in all for S = 8); per step, every pair
+      // (s, t) of its levels into the level's accumulator, the level drained after the previous step last.
+      const int w = warp - 2;
+      uint32_t fresh = 3u, drained = 0u, par = 0u;  // per own level (bit k)
+      int it = 0;
+      bool stop = false;
+      for (int t = blockIdx.x; t < args.ntiles && !stop; t += gridDim.x) {
+        int bi, bj;
+        const EmuMat& mt = item_of(args, t, bi, bj);
+        const int KS = (mt.n + EBK - 1) / EBK;
+        for (int j = 0; j < KS && !stop; ++j, ++it) {
+          const int st = it % NSTAGE, b = it & 1;
+          if (*s_abort || !ptx::mbar_wait(full0 + 8 * st, (it / NSTAGE) & 1, args.err, 14) ||
+              !ptx::mbar_wait(aready0 + 8 * b, (it >> 1) & 1, args.err, 15)) {
+            *s_abort = 1;
+            stop = true;
+            break;
+          }
+          ptx::tc_fence_after();
+          const uint32_t sb = ptx::smem_u32(ring + st * STAGE_BYTES) + A_BYTES;
+          const uint64_t bdesc = ptx::desc_sw128_kmajor(sb);
+          const uint32_t aT = tmem + (uint32_t)(ACOL + 64 * b);
+          const bool last = j == KS - 1;
+          // The level drained after step j - 1 ((j - 1 + L) % 8 == 7) goes second.
+          const int first = ((j - 1 + 9 - w) & 7) == 7 ? 1 : 0;
+          for (int q = 0; q < 2; ++q) {
+            const int k = q == 0 ? first : 1 - first;
+            const int L = k == 0 ? 9 - w : 2 + w;
+            if (L > S + 1) continue;
+            const int li = L - 2;
+            const uint32_t bit = 1u << k;
+            const bool fr = (fresh & bit) != 0;
+            if (fr && (drained & bit)) {
+              if (*s_abort || !ptx::mbar_wait(lempty0 + 8 * li, ((par >> k) & 1u) ^ 1u, args.err, 16)) {
                 *s_abort = 1;
                 stop = true;
                 break;
               }
               ptx::tc_fence_after();
-              const uint32_t d = tmem + (uint32_t)(b * EBN);
-              const int kb0 = c * KCHUNK_BLOCKS, kb1 = min(KB, kb0 + KCHUNK_BLOCKS);
-              for (int kb = kb0; kb < kb1; ++kb) {
-                const int cur = it + (kb - kb0);
-                const int st = cur % ESTAGES;
-                if (*s_abort || !ptx::mbar_wait(full0 + 8 * st, (cur / ESTAGES) & 1, args.err, 13)) {
-                  *s_abort = 1;
-                  stop = true;
-                  break;
-                }
-                ptx::tc_fence_after();
-                const uint32_t sa = ptx::smem_u32(ring + st * STAGE_BYTES);
-                const uint64_t da = ptx::desc_sw128_kmajor(sa), db = ptx::desc_sw128_kmajor(sa + BOX_BYTES);
-#pragma unroll
-                for (int kk = 0; kk < EBK / 16; ++kk)
-                  ptx::mma_f16(d, da + 2 * kk, db + 2 * kk, kIdesc, (kb != kb0 || kk != 0) ? 1u : 0u);
-                ptx::mma_commit(empty0 + 8 * st);
-              }
-              it += kb1 - kb0;
-              if (stop) break;
-              ptx::mma_commit(tfull0 + 8 * b);
             }
+            const uint32_t d = tmem + (uint32_t)(EBN * li);
+            if (S == SMAX) {
+              mma_level_s8(L, d, aT, bdesc, fr);
+            } else {
+              const int s0 = max(1, L - S), s1 = min(S, L - 1);
+              for (int s = s0; s <= s1; ++s) {
+                const int tt = L - s - 1;
+                ptx::mma_f16_ts(d, aT + 8 * (s - 1), bdesc + (uint64_t)(((tt >> 2) * B_GROUP + (tt & 3) * 32) >> 4),
+                                kIdesc, (fr && s == s0) ? 0u : 1u);
+              }
+            }
+            
+            fresh &= ~bit;
+            if (((j + L) & 7) == 7 || last) {
+              ptx::mma_commit(lfull0 + 8 * li);
+              par ^= bit;
+              drained |= bit;
+              fresh |= bit;
+            }
+          }
+          if (stop) break;
+          ptx::mma_commit(empty0 + 8 * st);
+          ptx::mma_commit(abuf0 + 8 * b);
+        }
       }
       ptx::mma_commit(drain);
       ptx::mbar_wait(drain, 0, nullptr, 0);
     }
   } else {
-    // ---------------- epilogue warps: quadrant q (TMEM lanes 32q..), column half h (64 columns)
-    // Levels are summed exactly in int64, Horner-style over groups of up to kGroup levels (a group's
-    // sum stays below 2^63); only at a group end is the group added into the FP64 total in TMEM.
-    const int q = warp & 3, h = (warp - 2) >> 2;
+    // ---------------- epilogue warps: quadrant q (TMEM lanes 32q..), column half h (24 columns)
+    const int q = warp & 3, h = (warp - 2 - MMA_WARPS) >> 2;
     const Epilogue& e = args.e;
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
-    int u = 0;
+    uint32_t epar = 0u;  // per level (bit li): parity of the drains taken so far
     bool stop = false;
     for (int t = blockIdx.x; t < args.ntiles && !stop; t += gridDim.x) {
       int bi, bj;
-      const EmuMat& mt = item_of<SYM>(args, t, bi, bj);
-      const int n = mt.n, row0 = mt.row0;
-      const int nchunks = ((n + EBK - 1) / EBK + KCHUNK_BLOCKS - 1) / KCHUNK_BLOCKS;
-      bool first_group = true;
-      for (int g0 = 2; g0 <= S + 1 && !stop; g0 += kGroup) {
-        const int glast = min(g0 + kGroup - 1, S + 1);
-        long long acc[64];
+      const EmuMat& mt = item_of(args, t, bi, bj);
+      const int n = mt.n, row0 = mt.row0, KS = (n + EBK - 1) / EBK;
+      // Exact totals: hi = sum_{L<=5} V_L 2^(8(5-L)), lo = sum_{L>=6} V_L 2^(8(9-L)); P = hi 2^-40 + lo 2^-72.
+      long long hi[24], lo[24];
 #pragma unroll
-        for (int c = 0; c < 64; ++c) acc[c] = 0;
-        for (int L = g0; L <= glast && !stop; ++L) {
-          const int shift = 7 * (glast - L);
-          for (int s = 1; s <= L - 1 && !stop; ++s)
-            for (int c = 0; c < nchunks; ++c, ++u) {
-              if (__shfl_sync(0xffffffffu, *s_abort, 0)) { stop = true; break; }
-              const int b = u & 1;
-              if (!__all_sync(0xffffffffu, ptx::mbar_wait(tfull0 + 8 * b, (u >> 1) & 1, args.err, 14))) {
-                *s_abort = 1;
-                stop = true;
-                break;
-              }
-              ptx::tc_fence_after();
+      for (int c = 0; c < 24; ++c) hi[c] = lo[c] = 0;
+      for (int j = 0; j < KS && !stop; ++j) {
+        const int nr = j == KS - 1 ? 8 : 1;
+        for (int r = 0; r < nr; ++r) {
+          const int L = level_at(j, r);
+          if (L > S + 1) continue;
+          const int li = L - 2;
+          if (__shfl_sync(0xffffffffu, *s_abort, 0)) {
+            stop = true;
+            break;
+          }
+          if (!__all_sync(0xffffffffu, ptx::mbar_wait(lfull0 + 8 * li, (epar >> li) & 1u, args.err, 18))) {
+            *s_abort = 1;
+            stop = true;
+            break;
+          }
+          ptx::tc_fence_after();
+          // Three loads of 8 columns; the accumulator is released after the last one.
+          const uint32_t ta = tmem + lane_off + (uint32_t)(EBN * li + 24 * h);
+          const bool low = L <= 5;
+          const int sh = low ? 8 * (5 - L) : 8 * (9 - L);
 #pragma unroll
-              for (int half = 0; half < 2; ++half) {
-                uint32_t v[32];
-                ptx::tmem_ld_32x32b_x32(tmem + lane_off + (uint32_t)(b * EBN + 64 * h + 32 * half), v);
-                ptx::tmem_ld_wait();
-#pragma unroll
-                for (int c2 = 0; c2 < 32; ++c2)
-                  acc[32 * half + c2] += (long long)__float2int_rn(__uint_as_float(v[c2])) << shift;
-              }
+          for (int g = 0; g < 3; ++g) {
+            uint32_t v[8];
+            ptx::tmem_ld_32x32b_x8(ta + 8 * g, v);
+            ptx::tmem_ld_wait();
+            if (g == 2) {
               ptx::tc_fence_before();
               __syncwarp();
-              if (lane == 0) ptx::mbar_arrive(tempty0 + 8 * b);
+              if (lane == 0) ptx::mbar_arrive(lempty0 + 8 * li);
             }
-        }
-        if (stop) break;
-        // Group end: total (+)= acc 2^(-7 glast); FP64 words in TMEM, 16 elements (32 words) per access.
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
-          const uint32_t ta = tmem + lane_off + (uint32_t)(TOTAL_COL + 128 * h + 32 * g);
-          uint32_t w[32];
-          if (!first_group) {
-            ptx::tmem_ld_32x32b_x32(ta, w);
-            ptx::tmem_ld_wait();
+            for (int c = 0; c < 8; ++c) {
+              const long long x = (long long)__float2int_rn(__uint_as_float(v[c])) << sh;
+              if (low) hi[8 * g + c] += x;
+              else lo[8 * g + c] += x;
+            }
           }
-#pragma unroll
-          for (int c2 = 0; c2 < 16; ++c2) {
-            double tot = scale2((double)acc[16 * g + c2], -7 * glast);
-            if (!first_group) tot += __hiloint2double((int)w[2 * c2 + 1], (int)w[2 * c2]);
-            w[2 * c2] = (uint32_t)__double2loint(tot);
-            w[2 * c2 + 1] = (uint32_t)__double2hiint(tot);
-          }
-          ptx::tmem_st_32x32b_x32(ta, w);
-          ptx::tmem_st_wait();
-        }
-        first_group = false;
+          epar ^= 1u << li;
+                  }
       }
       if (stop) break;
-      // Tile end: P = 2^(e_i + f_j) total, then the fused epilogue (FP64 values, FP32 residual partials).
+      // Tile end: P = 2^(e_i + f_j - 72) (hi 2^32 + lo), then the fused epilogue (FP64 values, FP32 partials).
       const int i = bi * EBM + 32 * q + lane;
       const int ei = i < n ? args.ex[row0 + i] : 0;
       float part = 0.0f;
-#pragma unroll 1
-      for (int g = 0; g < 4; ++g) {
-        uint32_t w[32];
-        ptx::tmem_ld_32x32b_x32(tmem + lane_off + (uint32_t)(TOTAL_COL + 128 * h + 32 * g), w);
-        ptx::tmem_ld_wait();
-        if (i >= n) continue;
-#pragma unroll 4
-        for (int c2 = 0; c2 < 16; ++c2) {
-          const int j = bj * EBN + 64 * h + 16 * g + c2;
-          if (j >= n || (SYM && i > j)) continue;
-          const double P = scale2(__hiloint2double((int)w[2 * c2 + 1], (int)w[2 * c2]), ei + args.ey[row0 + j]);
-          if (e.partial) {
-            const float dd = (float)((i == j ? 1.0 : 0.0) - P);
-            part = fmaf((SYM && i != j) ? 2.0f * dd : dd, dd, part);
-          }
-          const int64_t ij = (int64_t)(row0 + i) * ld + j, ji = (int64_t)(row0 + j) * ld + i;
-          double w2 = 0.0;
-          if (e.out2) {
-            w2 = i == j ? fma(mt.b, P, mt.a) : mt.b * P;
-            if (mt.c != 0.0) w2 = fma(mt.c, e.cin[ij], w2);
-          }
-          const bool direct = SYM || !args.transpose, mirrored = SYM ? (i != j) : (bool)args.transpose;
-          if (direct) {
-            if (e.out) e.out[ij] = P;
-            if (e.out2) e.out2[ij] = w2;
-          }
-          if (mirrored) {
-            if (e.out) e.out[ji] = P;
-            if (e.out2) e.out2[ji] = w2;
-          }
+#pragma unroll
+      for (int c = 0; c < 24; ++c) {
+        const int jc = bj * EBN + 24 * h + c;
+        if (i >= n || jc >= n || (SYM && i > jc)) continue;
+        const unsigned long long lw0 = (unsigned long long)hi[c] << 32, lw = lw0 + (unsigned long long)lo[c];
+        const long long H = (hi[c] >> 32) + (lo[c] >> 63) + (lw < lw0 ? 1 : 0);
+        const double P = wide_to_double(H, lw, ei + args.ey[row0 + jc] - 72);
+        if (e.partial) {
+          const float dd = i == jc ? (float)(1.0 - P) : -__double2float_rn(P);
+          part = fmaf((SYM && i != jc) ? 2.0f * dd : dd, dd, part);
+        }
+        const int64_t ij = (int64_t)(row0 + i) * args.ld + jc, ji = (int64_t)(row0 + jc) * args.ld + i;
+        double w2 = 0.0;
+        if (e.out2) {
+          w2 = i == jc ? fma(mt.b, P, mt.a) : mt.b * P;
+          if (mt.c != 0.0) w2 = fma(mt.c, e.cin[ij], w2);
+        }
+        const bool direct = SYM || !args.transpose, mirrored = SYM ? (i != jc) : (bool)args.transpose;
+        if (direct) {
+          if (e.out) e.out[ij] = P;
+          if (e.out2) e.out2[ij] = w2;
+        }
+        if (mirrored) {
+          if (e.out) e.out[ji] = P;
+          if (e.out2) e.out2[ji] = w2;
         }
       }
       if (e.partial) {
         for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        if (lane == 0) e.partial[(int64_t)t * EPI_WARPS + (warp - 2)] = (double)part;
+        if (lane == 0) e.partial[(int64_t)t * EPI_WARPS + (warp - 2 - MMA_WARPS)] = (double)part;
       }
-    }
+          }
   }
   ptx::tc_fence_before();
   __syncthreads();
   ptx::tc_fence_after();
-  if (warp == 0) ptx::tmem_dealloc(tmem, 512);
+    if (warp == 0) ptx::tmem_dealloc(tmem, 512);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn_emu() {
@@ -411,16 +498,18 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn_emu() {
   return fn;
 }
 
-// The S digit planes of an operand stacked as an (S R) x K BF16 matrix (leading dimension ldl); boxes of
-// 64 (K) x 128 rows. Columns k >= K are outside the tensor and read as zero.
-cudaError_t make_slice_map(CUtensorMap* map, const __nv_bfloat16* ptr, int K, int R, int ldl, int S) {
+// The digit planes of an operand ([row][step][plane][16], ldl / 16 steps) as a 3-D FP16 tensor
+// (64 halves of one group of 4 planes, group index 2 step + g, row) with byte strides (128, 16 ldl);
+// boxes of 64 x 1 x rows with 128-byte swizzling: one step of 4 planes for `rows` rows. Rows >= R read
+// as zero.
+cudaError_t make_plane_map(CUtensorMap* map, const __half* ptr, int R, int ldl, int rows) {
   auto fn = encode_fn_emu();
   if (!fn) return cudaErrorNotSupported;
-  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)S * (cuuint64_t)R};
-  cuuint64_t strides[1] = {(cuuint64_t)ldl * 2};
-  cuuint32_t box[2] = {(cuuint32_t)EBK, (cuuint32_t)EBM};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(ptr), dims, strides, box, estr,
+  cuuint64_t dims[3] = {64, (cuuint64_t)(ldl / 8), (cuuint64_t)R};
+  cuuint64_t strides[2] = {128, (cuuint64_t)ldl * 16};
+  cuuint32_t box[3] = {64, 1, (cuuint32_t)rows};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<__half*>(ptr), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
@@ -436,13 +525,10 @@ int sm_count_emu() {
   return count;
 }
 
-cudaError_t launch_emu(const __nv_bfloat16* DX, const __nv_bfloat16* DY, int K, int ldl, Mode mode, EmuArgs& a,
+cudaError_t launch_emu(const __half* DX, const __half* DY, int R, int K, int ldl, Mode mode, EmuArgs& a,
                        cudaStream_t s) {
-  if (a.S < 1 || a.S > 9 || ldl % 8 != 0 || ldl < K) return cudaErrorInvalidValue;
+  if (a.S < 1 || a.S > SMAX || ldl % 16 != 0 || ldl < K || K < 1 || !a.items) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(DX) | reinterpret_cast<uintptr_t>(DY)) & 15) return cudaErrorMisalignedAddress;
-  if ((int64_t)a.S * a.R > (int64_t)1 << 31) return cudaErrorInvalidValue;
-  // The int32 level sums hold up to S pairs of K-sums of K terms, each term at most 64 * 64.
-  if ((int64_t)a.S * K * 4096 >= (int64_t)1 << 31) return cudaErrorInvalidValue;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t r = cudaFuncSetAttribute(k_gemm_emu<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
@@ -453,9 +539,9 @@ cudaError_t launch_emu(const __nv_bfloat16* DX, const __nv_bfloat16* DY, int K, 
   }
   if (a.ntiles == 0) return cudaSuccess;
   CUtensorMap mx, my;
-  cudaError_t r = make_slice_map(&mx, DX, K, a.R, ldl, a.S);
+  cudaError_t r = make_plane_map(&mx, DX, R, ldl, EBM);
   if (r != cudaSuccess) return r;
-  r = make_slice_map(&my, DY, K, a.R, ldl, a.S);
+  r = make_plane_map(&my, DY, R, ldl, EBN);
   if (r != cudaSuccess) return r;
   const int grid = a.ntiles < sm_count_emu() ? a.ntiles : sm_count_emu();
   if (mode == Mode::Sym) {
@@ -468,19 +554,35 @@ cudaError_t launch_emu(const __nv_bfloat16* DX, const __nv_bfloat16* DY, int K, 
 
 }  // namespace
 
-int emu_tiles(int n, Mode mode) {
-  const int T = (n + EBM - 1) / EBM;
-  return (mode == Mode::Sym ? T * (T + 1) / 2 : T * T) * EPI_WARPS;  // one partial per epilogue warp and tile
+void emu_tile_list(int m, int n, Mode mode, std::vector<int4>& out) {
+  const int TM = (n + EBM - 1) / EBM, TN = (n + EBN - 1) / EBN;
+  for (int g = 0; g < TM; g += BAND)
+    for (int bj = 0; bj < TN; ++bj)
+      for (int bi = g; bi < std::min(g + BAND, TM); ++bi)
+        if (mode != Mode::Sym || EBN * bj + EBN - 1 >= EBM * bi) out.push_back(make_int4(m, bi, bj, 0));
 }
+
+int emu_tile_count(int n, Mode mode) {
+  std::vector<int4> v;
+  emu_tile_list(0, n, mode, v);
+  return (int)v.size();
+}
+
+int emu_tiles(int n, Mode mode) { return emu_tile_count(n, mode) * EPI_WARPS; }
 
 int emu_partials_per_item() { return EPI_WARPS; }
 
-cudaError_t slice(const double* X, int n, int ldl, int S, __nv_bfloat16* D, int* ex, cudaStream_t s) {
+int emu_max_slices() { return SMAX; }
+
+int emu_ld(int K) { return (K + 15) / 16 * 16; }
+
+cudaError_t slice(const double* X, int n, int ldl, int S, __half* D, int* ex, cudaStream_t s) {
   return slice_rows(X, n, n, n, ldl, S, nullptr, D, ex, s);
 }
 
-cudaError_t slice_rows(const double* X, int R, int n, int ldx, int ldl, int S, const int* row_n, __nv_bfloat16* D,
-                       int* ex, cudaStream_t s) {
+cudaError_t slice_rows(const double* X, int R, int n, int ldx, int ldl, int S, const int* row_n, __half* D, int* ex,
+                       cudaStream_t s) {
+  if (S < 1 || S > SMAX || ldl % 16 != 0) return cudaErrorInvalidValue;
   int blocks = (R + 7) / 8;  // 8 warps (rows) per block
   if (blocks > 152 * 8) blocks = 152 * 8;
   if (blocks < 1) return cudaSuccess;
@@ -488,15 +590,13 @@ cudaError_t slice_rows(const double* X, int R, int n, int ldx, int ldl, int S, c
   return cudaGetLastError();
 }
 
-cudaError_t gemm_emu(const __nv_bfloat16* DX, const int* ex, const __nv_bfloat16* DY, const int* ey, int n, int ldl,
-                     int S, Mode mode, bool transpose, const Epilogue& e, int* err, cudaStream_t s) {
+cudaError_t gemm_emu(const __half* DX, const int* ex, const __half* DY, const int* ey, int n, int ldl, int S, Mode mode,
+                     bool transpose, const int4* items, int nitems, const Epilogue& e, int* err, cudaStream_t s) {
   EmuArgs a{};
   a.S = S;
-  a.R = n;
   a.ld = n;
-  a.T = (n + EBM - 1) / EBM;
-  a.ntiles = mode == Mode::Sym ? a.T * (a.T + 1) / 2 : a.T * a.T;
-  a.items = nullptr;
+  a.ntiles = nitems;
+  a.items = items;
   a.mats = nullptr;
   a.one = EmuMat{n, 0, e.a, e.b, e.c};
   a.transpose = transpose ? 1 : 0;
@@ -504,18 +604,16 @@ cudaError_t gemm_emu(const __nv_bfloat16* DX, const int* ex, const __nv_bfloat16
   a.ex = ex;
   a.ey = ey;
   a.err = err;
-  return launch_emu(DX, DY, n, ldl, mode, a, s);
+  return launch_emu(DX, DY, n, n, ldl, mode, a, s);
 }
 
-cudaError_t gemm_emu_batched(const __nv_bfloat16* DX, const int* ex, const __nv_bfloat16* DY, const int* ey, int R,
-                             int K, int ldl, int ld, int S, Mode mode, bool transpose, const int4* items, int nitems,
+cudaError_t gemm_emu_batched(const __half* DX, const int* ex, const __half* DY, const int* ey, int R, int K, int ldl,
+                             int ld, int S, Mode mode, bool transpose, const int4* items, int nitems,
                              const EmuBatchMat* mats, const Epilogue& e, int* err, cudaStream_t s) {
   static_assert(sizeof(EmuBatchMat) == sizeof(EmuMat), "batch matrix record");
   EmuArgs a{};
   a.S = S;
-  a.R = R;
   a.ld = ld;
-  a.T = 0;
   a.ntiles = nitems;
   a.items = items;
   a.mats = reinterpret_cast<const EmuMat*>(mats);
@@ -524,7 +622,7 @@ cudaError_t gemm_emu_batched(const __nv_bfloat16* DX, const int* ex, const __nv_
   a.ex = ex;
   a.ey = ey;
   a.err = err;
-  return launch_emu(DX, DY, K, ldl, mode, a, s);
+  return launch_emu(DX, DY, R, K, ldl, mode, a, s);
 }
 
 }  // namespace pr

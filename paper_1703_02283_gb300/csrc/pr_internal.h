@@ -3,7 +3,10 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
+
+#include <vector>
 
 #include "../../include/pthroot.h"
 
@@ -70,28 +73,36 @@ int bf16_ld(int n);
 cudaError_t gemm_bf16_tc(const __nv_bfloat16* X, const __nv_bfloat16* Y, int n, int ldl, Mode mode, bool transpose,
                          const Epilogue& e, int* err, cudaStream_t s);
 
-// ---- FP64-accurate products from exact BF16 digit slices (k_gemm_emu.cu).
-// slice(): X (n x n FP64) -> S digit planes D (S x n x ldl BF16, most significant first) and row exponents ex.
-// gemm_emu(): P = X Y^T from the slices of X and Y, FP64 epilogue (out / out2 / partial; no BF16 copies).
-int emu_tiles(int n, Mode mode);
+// ---- FP64-accurate products from exact FP16 digit slices (k_gemm_emu.cu).
+// slice(): X (n x n FP64) -> 8 digit planes D (layout [row][k / 16][plane][k % 16], n x 8 ldl FP16 with
+// ldl = emu_ld(n); planes >= S zero) and row exponents ex.
+// gemm_emu(): P = X Y^T from the slices of X and Y over the work items (tile lists of emu_tile_list), FP64
+// epilogue (out / out2 / partial; no BF16 copies). One residual partial per epilogue warp and item
+// (emu_partials_per_item() per item, in item order).
+// emu_tile_list(): appends the work items (m, tile row, tile column, 0) of matrix m (order n) in the
+// kernel's order; tiles are 128 rows x 48 columns, symmetric mode keeps those reaching the upper triangle.
+void emu_tile_list(int m, int n, Mode mode, std::vector<int4>& out);
+int emu_tile_count(int n, Mode mode);
+int emu_tiles(int n, Mode mode);  // residual partials of one product: emu_tile_count * emu_partials_per_item
 int emu_partials_per_item();
-cudaError_t slice(const double* X, int n, int ldl, int S, __nv_bfloat16* D, int* ex, cudaStream_t s);
+int emu_max_slices();
+int emu_ld(int K);  // the K extent of a digit-plane row: K rounded up to 16
+cudaError_t slice(const double* X, int n, int ldl, int S, __half* D, int* ex, cudaStream_t s);
 // Slices R rows of an FP64 array with leading dimension ldx; row r has row_n[r] valid columns (n if null).
-cudaError_t slice_rows(const double* X, int R, int n, int ldx, int ldl, int S, const int* row_n, __nv_bfloat16* D,
-                       int* ex, cudaStream_t s);
-cudaError_t gemm_emu(const __nv_bfloat16* DX, const int* ex, const __nv_bfloat16* DY, const int* ey, int n, int ldl,
-                     int S, Mode mode, bool transpose, const Epilogue& e, int* err, cudaStream_t s);
+cudaError_t slice_rows(const double* X, int R, int n, int ldx, int ldl, int S, const int* row_n, __half* D, int* ex,
+                       cudaStream_t s);
+cudaError_t gemm_emu(const __half* DX, const int* ex, const __half* DY, const int* ey, int n, int ldl, int S, Mode mode,
+                     bool transpose, const int4* items, int nitems, const Epilogue& e, int* err, cudaStream_t s);
 
 // A batch of matrices packed row-wise in shared buffers (leading dimension ld for FP64, ldl for digit
-// planes; R packed rows per plane; K the largest order). Work item = (matrix, bi, bj, unused), 128 x 128
-// tiles; per-matrix record = {order, first packed row, epilogue a, b, c}. One residual partial per epilogue
-// warp and item (emu_partials_per_item() per item, in item order).
+// planes; R packed rows per plane; K the largest order). Work items from emu_tile_list per matrix;
+// per-matrix record = {order, first packed row, epilogue a, b, c}.
 struct EmuBatchMat {
   int n, row0;
   double a, b, c;
 };
-cudaError_t gemm_emu_batched(const __nv_bfloat16* DX, const int* ex, const __nv_bfloat16* DY, const int* ey, int R,
-                             int K, int ldl, int ld, int S, Mode mode, bool transpose, const int4* items, int nitems,
+cudaError_t gemm_emu_batched(const __half* DX, const int* ex, const __half* DY, const int* ey, int R, int K, int ldl,
+                             int ld, int S, Mode mode, bool transpose, const int4* items, int nitems,
                              const EmuBatchMat* mats, const Epilogue& e, int* err, cudaStream_t s);
 
 // ---- elementwise and reductions (k_elementwise.cu)
