@@ -301,32 +301,47 @@ pr_status form_M_from_X(pr_handle h, int prec, bool replace_last) {
   return PR_OK;
 }
 
-// X_{k+1} = X_k N_k; M_{k+1} = N_k^p M_k (p symmetric products); N_{k+1} and r_{k+1} fused.
+// X_{k+1} = X_k N_k; M_{k+1} = N_k^p M_k (p symmetric products, 3 for p = 4); N_{k+1} and r_{k+1} fused.
 pr_status coupled_update(pr_handle h, int prec) {
   const int p = h->p;
   Out ox;
   ox.out = &h->Xn;
   pr_status s = product(h, prec, h->X, h->N, Mode::Sym, ox);
   if (s != PR_OK) return s;
-  Mat* src = &h->M;
-  for (int j = 1; j <= p; ++j) {
+  Out last;
+  last.out = &h->Mn;
+  last.out2 = &h->Nn;
+  last.a = (double)(p + 1) / p;
+  last.b = -1.0 / p;
+  last.partial = true;
+  // At low precision the FP64 copies of M and N are only needed if a later switch to higher precision
+  // carries them over instead of re-forming M from X.
+  last.out_master = last.out2_master = !(lowp(prec) && h->opt.reanchor);
+  if (p == 4) {
+    // N^4 M = (N^2)^2 M: three products instead of four (every factor is a polynomial in A).
     Out o;
-    if (j < p) {
-      o.out = (j & 1) ? &h->T0 : &h->T1;
-      o.out_master = false;
-    } else {
-      o.out = &h->Mn;
-      o.out2 = &h->Nn;
-      o.a = (double)(p + 1) / p;
-      o.b = -1.0 / p;
-      o.partial = true;
-      // At low precision the FP64 copies of M and N are only needed if a later switch to higher
-      // precision carries them over instead of re-forming M from X.
-      o.out_master = o.out2_master = !(lowp(prec) && h->opt.reanchor);
-    }
-    s = product(h, prec, h->N, *src, Mode::Sym, o);
+    o.out = &h->T0;
+    o.out_master = false;
+    s = product(h, prec, h->N, h->N, Mode::Sym, o);
     if (s != PR_OK) return s;
-    src = o.out;
+    o.out = &h->T1;
+    s = product(h, prec, h->T0, h->T0, Mode::Sym, o);
+    if (s == PR_OK) s = product(h, prec, h->T1, h->M, Mode::Sym, last);
+    if (s != PR_OK) return s;
+  } else {
+    Mat* src = &h->M;
+    for (int j = 1; j <= p; ++j) {
+      Out o;
+      if (j < p) {
+        o.out = (j & 1) ? &h->T0 : &h->T1;
+        o.out_master = false;
+      } else {
+        o = last;
+      }
+      s = product(h, prec, h->N, *src, Mode::Sym, o);
+      if (s != PR_OK) return s;
+      src = o.out;
+    }
   }
   double r;
   s = read_residual(h, tiles_for(h, prec, Mode::Sym), &r);

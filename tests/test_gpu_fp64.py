@@ -180,3 +180,24 @@ def test_input_errors():
     with pytest.raises(P.PthrootError) as e:
         P.pr_init(torch.from_numpy(A).to(DEV), 40, 2, None, stream)
     assert e.value.status == P.PR_ENOTSPD
+
+
+def test_p4_chain_uses_squares():
+    # p = 4: M' = N^4 M is formed as (N^2)^2 M, three products per update (plus X N); M_0 = X^4 A keeps the
+    # plain chain of four. Same iterates as the oracle's N (N (N (N M))) up to rounding.
+    case = W.spd_from_spectrum(130, 0.05, 12)
+    stream = torch.cuda.current_stream(DEV).cuda_stream
+    h = P.pr_init(torch.from_numpy(case.A).to(DEV), 130, 4, P.pr_default_options(), stream)
+    try:
+        st, d = P.pr_iterate(h, 100, P.PR_FP64, 1e-12)
+        s = P.pr_stats(h)
+        C = torch.empty((130, 130), dtype=torch.float64, device=DEV)
+        P.pr_result(h, C)
+    finally:
+        P.pr_destroy(h)
+    assert s["gemms"] == 4 + 4 * s["iterations"]
+    Co, info = O.solve(case.A, 4, tol=1e-12)
+    Z = O.closed_form_root(case.Q, case.lam, 4)
+    bound = max(1e-12, 10 * O.forward_error(Co, Z))
+    assert O.forward_error(C.cpu().numpy(), Z) <= bound and O.forward_error(C.cpu().numpy(), Co) <= bound
+    assert abs(d - info.iterations) <= 1
