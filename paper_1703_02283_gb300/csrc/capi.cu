@@ -57,6 +57,7 @@ struct pr_handle_s {
   int S = 8;    // digit planes per operand for PR_EMU64
   int4* emu_items[2] = {nullptr, nullptr};  // PR_EMU64 work lists: symmetric, full products
   int emu_nitems[2] = {0, 0};
+  long long* emu_scratch = nullptr;          // PR_EMU64 first-pass totals (pr::emu_scratch_bytes())
 
   // The input, the iterate X, the carried product M and operand N of the coupled form, their next
   // values, and two scratch products.
@@ -215,7 +216,7 @@ pr_status product(pr_handle h, int prec, Mat& X, Mat& Y, Mode mode, const Out& o
     case PR_EMU64:
       PR_CK(h, pr::gemm_emu(X.sl, X.ex, Y.sl, Y.ex, n, h->eld, h->S, mode, o.transpose,
                             h->emu_items[mode == Mode::Sym ? 0 : 1], h->emu_nitems[mode == Mode::Sym ? 0 : 1], e,
-                            h->err_word(), h->stream));
+                            h->emu_scratch, h->err_word(), h->stream));
       h->lp_stale = true;
       break;
     default:
@@ -634,6 +635,7 @@ pr_status pr_destroy(pr_handle h) {
     if (b) cudaFree(b);
   for (int4* it : h->emu_items)
     if (it) cudaFree(it);
+  if (h->emu_scratch) cudaFree(h->emu_scratch);
   if (h->hpin) cudaFreeHost(h->hpin);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   delete h;
@@ -712,6 +714,7 @@ pr_status pr_init(pr_handle* out, const double* A, int64_t n, int p, const pr_op
     PR_INIT_CK(cudaMalloc((void**)&h->emu_items[k], items.size() * sizeof(int4)));
     PR_INIT_CK(cudaMemcpy(h->emu_items[k], items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
   }
+  PR_INIT_CK(cudaMalloc((void**)&h->emu_scratch, pr::emu_scratch_bytes()));
 #undef PR_INIT_CK
   pr_status s = pr_load(h, A);
   if (s != PR_OK) return bail(s);
@@ -916,6 +919,7 @@ pr_status pr_matmul(int precision, const double* X, const double* Y, int64_t n, 
   __nv_bfloat16 *bX = nullptr, *bY = nullptr;
   int *err = nullptr, *eX = nullptr, *eY = nullptr;
   int4* items = nullptr;
+  long long* scratch = nullptr;
   std::vector<int4> hitems;
   cudaError_t e = cudaSuccess;
   int word = 0;
@@ -948,16 +952,17 @@ pr_status pr_matmul(int precision, const double* X, const double* Y, int64_t n, 
       __half *hX = reinterpret_cast<__half*>(bX), *hY = reinterpret_cast<__half*>(bY);
       pr::emu_tile_list(0, ni, mode, hitems);
       step(cudaMalloc((void**)&items, hitems.size() * sizeof(int4)));
+      step(cudaMalloc((void**)&scratch, pr::emu_scratch_bytes()));
       step(cudaMemcpyAsync(items, hitems.data(), hitems.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
       step(pr::slice(dX, ni, eld, S, hX, eX, s));
       step(pr::slice(dY, ni, eld, S, hY, eY, s));
-      step(pr::gemm_emu(hX, eX, hY, eY, ni, eld, S, mode, false, items, (int)hitems.size(), ep, err, s));
+      step(pr::gemm_emu(hX, eX, hY, eY, ni, eld, S, mode, false, items, (int)hitems.size(), ep, scratch, err, s));
     }
     step(cudaMemcpyAsync(P, dP, bytes, cudaMemcpyDefault, s));
     step(cudaMemcpyAsync(&word, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     step(cudaStreamSynchronize(s));
   }
-  for (void* q : {(void*)dX, (void*)dY, (void*)dP, (void*)bX, (void*)bY, (void*)err, (void*)eX, (void*)eY, (void*)items})
+  for (void* q : {(void*)dX, (void*)dY, (void*)dP, (void*)bX, (void*)bY, (void*)err, (void*)eX, (void*)eY, (void*)items, (void*)scratch})
     if (q) cudaFree(q);
   if (e != cudaSuccess) return cuda_fail(nullptr, "pr_matmul", e);
   if (word != 0) return fail(nullptr, PR_ETIMEOUT, "pr_matmul: a bounded device wait expired");

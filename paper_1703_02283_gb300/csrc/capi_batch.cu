@@ -55,6 +55,7 @@ struct pr_batch_s {
   double* res = nullptr;
   double* hres = nullptr;  // pinned
   int* err = nullptr;
+  long long* scratch = nullptr;  // PR_EMU64 first-pass totals
   // per matrix
   std::vector<std::vector<double>> hist;
   std::vector<int> active, status, iterations;
@@ -136,7 +137,7 @@ pr_status stage(pr_batch b, Buf& Xb, Buf& Yb, Mode mode, const std::vector<int>&
   e.partial = so.partial ? b->partial : nullptr;
   if (b->timing) PB_CK(b, cudaEventRecord(b->ev0, b->stream));
   PB_CK(b, pr::gemm_emu_batched(Xb.sl, Xb.ex, Yb.sl, Yb.ex, b->R, b->K, pr::emu_ld(b->K), b->ld, b->S, mode, so.transpose,
-                                b->items, (int)items.size(), b->mats, e, b->err, b->stream));
+                                b->items, (int)items.size(), b->mats, e, b->scratch, b->err, b->stream));
   if (b->timing) PB_CK(b, cudaEventRecord(b->ev1, b->stream));
   b->launches += 1;
   b->st.stages += 1;
@@ -229,7 +230,7 @@ pr_status pr_batch_destroy(pr_batch b) {
     if (x->ex) cudaFree(x->ex);
   }
   for (void* q : {(void*)b->result, (void*)b->row_n, (void*)b->partial, (void*)b->items, (void*)b->mats, (void*)b->seg,
-                  (void*)b->res, (void*)b->err})
+                  (void*)b->res, (void*)b->err, (void*)b->scratch})
     if (q) cudaFree(q);
   if (b->hres) cudaFreeHost(b->hres);
   if (b->ev0) cudaEventDestroy(b->ev0);
@@ -317,6 +318,7 @@ pr_status pr_batch_init(pr_batch* out, int count, const int64_t* n, const int* p
   PB_INIT_CK(cudaMalloc((void**)&b->seg, (size_t)2 * count * sizeof(int)));
   PB_INIT_CK(cudaMalloc((void**)&b->res, (size_t)count * sizeof(double)));
   PB_INIT_CK(cudaMalloc((void**)&b->err, sizeof(int)));
+  PB_INIT_CK(cudaMalloc((void**)&b->scratch, pr::emu_scratch_bytes()));
   PB_INIT_CK(cudaMemsetAsync(b->err, 0, sizeof(int), b->stream));
   PB_INIT_CK(cudaMallocHost((void**)&b->hres, (size_t)count * sizeof(double)));
   {

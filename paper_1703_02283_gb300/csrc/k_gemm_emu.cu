@@ -18,23 +18,25 @@
 //    gives 2^-63. F must fit in 64-bit integers, which limits S to 8.
 //
 // Data movement. All digit planes of both operands for one 16-wide step of k sit in shared memory at
-// once (one TMA box per operand), and every pair (s, t) of the step is issued from them: each plane is
-// fetched once per step instead of once per pair. In memory the 16 digits of a step are stored for 4
-// planes side by side (layout [row][step][plane][16]), so a box row is 128 contiguous bytes (one request)
-// and lands 128-byte swizzled in shared memory, where plane s is the 32-byte K slice s % 4 of group s / 4.
-// The planes of X are copied into tensor memory (tcgen05.cp) and the MMAs read them there, so shared
-// memory serves only the Y planes to the tensor cores.
+// once (one TMA box per operand and plane group), and every pair (s, t) of the step is issued from them:
+// each plane is fetched once per step instead of once per pair. In memory the 16 digits of a step are
+// stored for 4 planes side by side (layout [row][step][plane][16]), so a box row is 128 contiguous bytes
+// (one request) and lands 128-byte swizzled in shared memory, where plane s is the 32-byte K slice s % 4
+// of group s / 4. The planes of X are copied into tensor memory (tcgen05.cp) and the MMAs read them there;
+// shared memory serves only the Y planes to the tensor cores (both operands from shared memory would cap
+// the tensor cores at the 128 bytes per clock that shared memory delivers).
 //
-// k_gemm_emu is a persistent kernel, one CTA per SM, 128 x 48 output tiles taken from a work list
-// (matrix, tile row, tile column), 448 threads: warp 0 TMA producer (5-stage ring), warp 1 copies the X
-// planes into tensor memory, warps 2-5 issue the MMAs (warp w owns levels 9 - w and 2 + w, 9 pairs per
-// step each: one issuing thread cannot keep the tensor cores busy with 128 x 48 x 16 MMAs, four can),
-// warps 6-13 epilogue (two warps per TMEM lane quadrant, 24 columns each). Tensor memory holds one FP32
-// accumulator per level (8 x 48 columns) and two buffers of X planes (2 x 64 columns). A level's
-// accumulator is drained every 8 steps, the levels staggered so that one drain falls on each step: the
-// epilogue warps convert the exact FP32 values to integers and add them, shifted, into two exact int64
-// totals per element; at the tile's end they round the 128-bit total once to FP64 (integer arithmetic),
-// scale by 2^(e_i + f_j) and apply the fused epilogue. Every wait is bounded as in k_gemm_tc.cu.
+// k_gemm_emu is a persistent kernel, one CTA per SM, 128 x 96 output tiles taken from a work list
+// (matrix, tile row, tile column). Tensor memory holds four FP32 level accumulators of 96 columns and two
+// 64-column buffers of X planes, so a tile takes two passes over k: levels 2..5 (digits 1..4 only) and
+// levels 6..9. 640 threads: warp 0 TMA producer (4-stage ring), warp 1 copies the X planes into TMEM,
+// warps 2-3 issue the MMAs (warp w owns accumulators 3 - w and w: 5 and 13 pairs per step), warps 4-19
+// epilogue (four warps per TMEM lane quadrant, 24 columns each). An accumulator is drained every 8
+// steps, staggered one every second step: the epilogue warps load its columns, release it, convert the
+// exact FP32 values to integers and add them, shifted, into an exact int64 total per element. The
+// first pass's totals wait in a scratch buffer; at the tile's end the 128-bit total hi 2^32 + lo is
+// rounded once to FP64 (integer arithmetic), scaled by 2^(e_i + f_j) and the fused epilogue applied.
+// Every wait is bounded as in k_gemm_tc.cu.
 #include "pr_internal.h"
 #include "tc_ptx.h"
 
@@ -47,16 +49,19 @@
 namespace pr {
 namespace {
 
-constexpr int EBM = 128, EBN = 48, EBK = 16, NSTAGE = 5, SMAX = 8, BAND = 8;
-constexpr int MMA_WARPS = 4, EPI_WARPS = 8, THREADS = 32 * (2 + MMA_WARPS + EPI_WARPS);
+constexpr int EBM = 128, EBN = 96, EBK = 16, SMAX = 8, BAND = 8, NSTAGE = 4;
+constexpr int NACC = 4;                  // level accumulators in TMEM: levels 2..5 (pass 0), 6..9 (pass 1)
+constexpr int MMA_WARPS = 2, EPI_WARPS = 16, THREADS = 32 * (2 + MMA_WARPS + EPI_WARPS);
+constexpr int EPI_COLS = EBN / 4;        // columns per epilogue warp (four warps per TMEM lane quadrant)
 constexpr int A_GROUP = EBM * 128, B_GROUP = EBN * 128;  // bytes of 4 planes (one 128-byte row per row)
 constexpr int A_BYTES = 2 * A_GROUP, STAGE_BYTES = A_BYTES + 2 * B_GROUP;
-constexpr int NBARS = 2 * NSTAGE + 2 * SMAX + 2 + 2 + 1;
+constexpr int NBARS = 2 * NSTAGE + 2 * NACC + 2 + 1;
 constexpr int SMEM_BYTES = 1024 + NSTAGE * STAGE_BYTES + 8 * NBARS + 16;
-constexpr int ACOL = SMAX * EBN;        // TMEM column of the first X-plane buffer (after the accumulators)
+constexpr int ACOL = NACC * EBN;         // TMEM column of the first X-plane buffer (after the accumulators)
+constexpr int SCRATCH_PER_CTA = EPI_WARPS * 32 * EPI_COLS;  // int64 totals of the first pass
 constexpr uint32_t kIdesc = ptx::idesc_f16_f32(EBM, EBN);
 static_assert(ACOL + 2 * SMAX * 8 <= 512, "tensor memory budget");
-static_assert(STAGE_BYTES % 1024 == 0, "stage alignment");
+static_assert(STAGE_BYTES % 1024 == 0 && SMEM_BYTES <= 232448, "shared memory");
 
 // ------------------------------------------------------------------------------------------ slicing
 
@@ -140,6 +145,7 @@ struct EmuArgs {
   Epilogue e;            // output pointers are the bases of the (packed) FP64 buffers
   const int* ex;         // row exponents of X (indexed by packed row)
   const int* ey;         // row exponents of Y
+  long long* scratch;    // SCRATCH_PER_CTA int64 per CTA: the first pass's exact totals
   int* err;
 };
 
@@ -150,16 +156,9 @@ __device__ __forceinline__ const EmuMat& item_of(const EmuArgs& a, int t, int& b
   return a.mats ? a.mats[it.x] : a.one;
 }
 
-// The level whose pairs come r-th in step j: the level drained after step j first (r = 0), the level
-// drained after step j - 1 last (r = 7). Levels 2..9 are the residues 2..7, 0, 1 modulo 8.
-__device__ __forceinline__ int level_at(int j, int r) {
-  const int lam = (7 - (j & 7) - r) & 7;
-  return lam < 2 ? lam + 8 : lam;
-}
-
 // (H 2^64 + Lw) 2^E0 for a two's-complement 128-bit integer H:Lw, rounded once to the nearest double
 // (ties to even), in integer arithmetic.
-__device__ __forceinline__ double wide_to_double(long long H, unsigned long long Lw, int E0) {
+__device__ __noinline__ double wide_to_double(long long H, unsigned long long Lw, int E0) {
   const unsigned long long sign = (unsigned long long)H & 0x8000000000000000ull;
   unsigned long long mh = (unsigned long long)H, ml = Lw;
   if (sign) {
@@ -191,7 +190,7 @@ __device__ __forceinline__ double wide_to_double(long long H, unsigned long long
 }
 
 // The MMAs of one level L for S = 8 (pairs s = 1 .. L - 1, t = L - s), unrolled: X plane s - 1 from TMEM
-// buffer aT, Y plane t - 1 from the shared-memory slot whose first plane group has descriptor bdesc.
+// buffer aT, Y plane t - 1 from the shared-memory stage whose first plane group has descriptor bdesc.
 template <int L>
 __device__ __forceinline__ void mma_level(uint32_t d, uint32_t aT, uint64_t bdesc, bool fresh) {
 #pragma unroll
@@ -215,8 +214,12 @@ __device__ __forceinline__ void mma_level_s8(int L, uint32_t d, uint32_t aT, uin
   }
 }
 
+// Accumulator a of a pass is drained after step j when (j + 2a) % 8 == 7 (staggered: one drain every
+// second step; 8 pairs x 8 steps x 16 x 2^14 = 2^24 keeps every level exact) and after the pass's last step.
+__device__ __forceinline__ bool drains_after(int a, int j) { return ((j + 2 * a) & 7) == 7; }
+
 template <bool SYM>
-__global__ void __launch_bounds__(THREADS, 1)  // 14 warps: at most 128 registers (4 warps on a sub-partition)
+__global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (5 warps per sub-partition)
     k_gemm_emu(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, EmuArgs args) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -227,22 +230,18 @@ __global__ void __launch_bounds__(THREADS, 1)  // 14 warps: at most 128 register
 
   const int S = args.S, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t full0 = ptx::smem_u32(bars), empty0 = full0 + 8 * NSTAGE, lfull0 = empty0 + 8 * NSTAGE,
-                 lempty0 = lfull0 + 8 * SMAX, abuf0 = lempty0 + 8 * SMAX, aready0 = abuf0 + 16,
-                 drain = aready0 + 16;
+                 lempty0 = lfull0 + 8 * NACC, aready0 = lempty0 + 8 * NACC, drain = aready0 + 16;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
       ptx::mbar_init(full0 + 8 * s, 1);
       ptx::mbar_init(empty0 + 8 * s, MMA_WARPS + 1);  // the MMA warps and the copy thread read the stage
     }
-    for (int l = 0; l < SMAX; ++l) {
-      ptx::mbar_init(lfull0 + 8 * l, 1);
-      ptx::mbar_init(lempty0 + 8 * l, EPI_WARPS);
+    for (int a = 0; a < NACC; ++a) {
+      ptx::mbar_init(lfull0 + 8 * a, 1);
+      ptx::mbar_init(lempty0 + 8 * a, EPI_WARPS);
     }
-    for (int b = 0; b < 2; ++b) {
-      ptx::mbar_init(abuf0 + 8 * b, MMA_WARPS);
-      ptx::mbar_init(aready0 + 8 * b, 1);
-    }
+    for (int b = 0; b < 2; ++b) ptx::mbar_init(aready0 + 8 * b, 1);
     ptx::mbar_init(drain, MMA_WARPS + 1);
     *s_abort = 0;
     ptx::fence_barrier_init();
@@ -257,29 +256,33 @@ __global__ void __launch_bounds__(THREADS, 1)  // 14 warps: at most 128 register
   __syncthreads();
   ptx::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // Planes used by a pass: levels 2..5 need digits 1..4 only (one plane group), levels 6..9 all 8.
+  const int groups1 = S > 4 ? 2 : 1;
 
   if (warp == 0) {
     if (lane == 0) {
-      // ---------------- TMA producer: per step, the S planes of X (128 rows) and of Y (48 rows)
-      const uint32_t tx = (uint32_t)STAGE_BYTES;
+      // ---------------- TMA producer: per step, the plane groups of X (128 rows) and of Y (96 rows)
       int it = 0;
       bool stop = false;
       for (int t = blockIdx.x; t < args.ntiles && !stop; t += gridDim.x) {
         int bi, bj;
         const EmuMat& mt = item_of(args, t, bi, bj);
         const int KS = (mt.n + EBK - 1) / EBK, ya = mt.row0 + bi * EBM, yb = mt.row0 + bj * EBN;
-        for (int j = 0; j < KS; ++j, ++it) {
-          const int st = it % NSTAGE;
-          if (*s_abort || !ptx::mbar_wait(empty0 + 8 * st, ((it / NSTAGE) & 1) ^ 1, args.err, 11)) {
-            *s_abort = 1;
-            stop = true;
-            break;
-          }
-          uint8_t* sp = ring + st * STAGE_BYTES;
-          ptx::mbar_expect_tx(full0 + 8 * st, tx);
-          for (int g = 0; g < 2; ++g) {
-            ptx::tma_load_3d(ptx::smem_u32(sp + g * A_GROUP), &tmX, full0 + 8 * st, 0, 2 * j + g, ya);
-            ptx::tma_load_3d(ptx::smem_u32(sp + A_BYTES + g * B_GROUP), &tmY, full0 + 8 * st, 0, 2 * j + g, yb);
+        for (int pass = 0; pass < 2 && !stop; ++pass) {
+          const int ng = pass == 0 ? 1 : groups1;
+          for (int j = 0; j < KS; ++j, ++it) {
+            const int st = it % NSTAGE;
+            if (*s_abort || !ptx::mbar_wait(empty0 + 8 * st, ((it / NSTAGE) & 1) ^ 1, args.err, 11)) {
+              *s_abort = 1;
+              stop = true;
+              break;
+            }
+            uint8_t* sp = ring + st * STAGE_BYTES;
+            ptx::mbar_expect_tx(full0 + 8 * st, (uint32_t)ng * (A_GROUP + B_GROUP));
+            for (int g = 0; g < ng; ++g) {
+              ptx::tma_load_3d(ptx::smem_u32(sp + g * A_GROUP), &tmX, full0 + 8 * st, 0, 2 * j + g, ya);
+              ptx::tma_load_3d(ptx::smem_u32(sp + A_BYTES + g * B_GROUP), &tmY, full0 + 8 * st, 0, 2 * j + g, yb);
+            }
           }
         }
       }
@@ -290,28 +293,31 @@ __global__ void __launch_bounds__(THREADS, 1)  // 14 warps: at most 128 register
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // ---------------- copy thread: per step, the X planes from shared memory into TMEM buffer (step & 1)
+      // ---------------- copy thread: per step, the X planes of the pass into TMEM buffer (step & 1), once
+      // the MMAs of two steps back (the last readers of that buffer) have finished.
       int it = 0;
       bool stop = false;
       for (int t = blockIdx.x; t < args.ntiles && !stop; t += gridDim.x) {
         int bi, bj;
         const EmuMat& mt = item_of(args, t, bi, bj);
         const int KS = (mt.n + EBK - 1) / EBK;
-        for (int j = 0; j < KS; ++j, ++it) {
-          const int st = it % NSTAGE, b = it & 1;
-          if (*s_abort || !ptx::mbar_wait(full0 + 8 * st, (it / NSTAGE) & 1, args.err, 12) ||
-              (it >= 2 && !ptx::mbar_wait(abuf0 + 8 * b, ((it - 2) >> 1) & 1, args.err, 13))) {
-            *s_abort = 1;
-            stop = true;
-            break;
+        for (int pass = 0; pass < 2 && !stop; ++pass) {
+          const int np = pass == 0 ? min(S, 4) : S;
+          for (int j = 0; j < KS; ++j, ++it) {
+            const int st = it % NSTAGE, b = it & 1;
+            if (*s_abort || !ptx::mbar_wait(full0 + 8 * st, (it / NSTAGE) & 1, args.err, 12) ||
+                (it >= 2 && !ptx::mbar_wait(empty0 + 8 * ((it - 2) % NSTAGE), ((it - 2) / NSTAGE) & 1, args.err, 13))) {
+              *s_abort = 1;
+              stop = true;
+              break;
+            }
+            ptx::tc_fence_after();
+            const uint32_t sa = ptx::smem_u32(ring + st * STAGE_BYTES), aT = tmem + (uint32_t)(ACOL + 64 * b);
+            for (int s = 0; s < np; ++s)
+              ptx::tmem_cp_128x256b(aT + 8 * s, ptx::desc_sw128_kmajor(sa + (s >> 2) * A_GROUP + (s & 3) * 32));
+            ptx::mma_commit(aready0 + 8 * b);
+            ptx::mma_commit(empty0 + 8 * st);
           }
-          ptx::tc_fence_after();
-          const uint32_t sa = ptx::smem_u32(ring + st * STAGE_BYTES), aT = tmem + (uint32_t)(ACOL + 64 * b);
-          for (int s = 0; s < S; ++s)
-            ptx::tmem_cp_128x256b(aT + 8 * s, ptx::desc_sw128_kmajor(sa + (s >> 2) * A_GROUP + (s & 3) * 32));
-          ptx::mma_commit(aready0 + 8 * b);
-          ptx::mma_commit(empty0 + 8 * st);
-          
         }
       }
       ptx::mma_commit(drain);
@@ -319,128 +325,135 @@ __global__ void __launch_bounds__(THREADS, 1)  // 14 warps: at most 128 register
     }
   } else if (warp < 2 + MMA_WARPS) {
     if (lane == 0) {
-      // ---------------- MMA warp w: levels 9 - w and 2 + w (9 pairs in all for S = 8); per step, every pair
-      // (s, t) of its levels into the level's accumulator, the level drained after the previous step last.
+      // ---------------- MMA warp w: accumulators a = 3 - w and w of each pass (levels 5 - w, 2 + w in the first
+      // pass, 9 - w, 6 + w in the second: 5 and 13 pairs per step for S = 8, the same for both warps).
       const int w = warp - 2;
-      uint32_t fresh = 3u, drained = 0u, par = 0u;  // per own level (bit k)
+      uint32_t fresh = 3u, drained = 0u, par = 0u;  // per own accumulator k (a = k == 0 ? 3 - w : w)
       int it = 0;
       bool stop = false;
       for (int t = blockIdx.x; t < args.ntiles && !stop; t += gridDim.x) {
         int bi, bj;
         const EmuMat& mt = item_of(args, t, bi, bj);
         const int KS = (mt.n + EBK - 1) / EBK;
-        for (int j = 0; j < KS && !stop; ++j, ++it) {
-          const int st = it % NSTAGE, b = it & 1;
-          if (*s_abort || !ptx::mbar_wait(full0 + 8 * st, (it / NSTAGE) & 1, args.err, 14) ||
-              !ptx::mbar_wait(aready0 + 8 * b, (it >> 1) & 1, args.err, 15)) {
-            *s_abort = 1;
-            stop = true;
-            break;
-          }
-          ptx::tc_fence_after();
-          const uint32_t sb = ptx::smem_u32(ring + st * STAGE_BYTES) + A_BYTES;
-          const uint64_t bdesc = ptx::desc_sw128_kmajor(sb);
-          const uint32_t aT = tmem + (uint32_t)(ACOL + 64 * b);
-          const bool last = j == KS - 1;
-          // The level drained after step j - 1 ((j - 1 + L) % 8 == 7) goes second.
-          const int first = ((j - 1 + 9 - w) & 7) == 7 ? 1 : 0;
-          for (int q = 0; q < 2; ++q) {
-            const int k = q == 0 ? first : 1 - first;
-            const int L = k == 0 ? 9 - w : 2 + w;
-            if (L > S + 1) continue;
-            const int li = L - 2;
-            const uint32_t bit = 1u << k;
-            const bool fr = (fresh & bit) != 0;
-            if (fr && (drained & bit)) {
-              if (*s_abort || !ptx::mbar_wait(lempty0 + 8 * li, ((par >> k) & 1u) ^ 1u, args.err, 16)) {
-                *s_abort = 1;
-                stop = true;
-                break;
+        for (int pass = 0; pass < 2 && !stop; ++pass) {
+          for (int j = 0; j < KS && !stop; ++j, ++it) {
+            const int st = it % NSTAGE, b = it & 1;
+            if (*s_abort || !ptx::mbar_wait(full0 + 8 * st, (it / NSTAGE) & 1, args.err, 14) ||
+                !ptx::mbar_wait(aready0 + 8 * b, (it >> 1) & 1, args.err, 15)) {
+              *s_abort = 1;
+              stop = true;
+              break;
+            }
+            ptx::tc_fence_after();
+            const uint64_t bdesc = ptx::desc_sw128_kmajor(ptx::smem_u32(ring + st * STAGE_BYTES) + A_BYTES);
+            const uint32_t aT = tmem + (uint32_t)(ACOL + 64 * b);
+            const bool last = j == KS - 1;
+            // An accumulator being drained (fresh after a drain) goes second.
+            const int first = ((fresh & 1u) && (drained & 1u)) ? 1 : 0;
+            for (int q = 0; q < 2; ++q) {
+              const int k = q == 0 ? first : 1 - first;
+              const int a = k == 0 ? 3 - w : w;
+              const int L = 2 + 4 * pass + a;
+              if (L > S + 1) continue;
+              const uint32_t bit = 1u << k;
+              const bool fr = (fresh & bit) != 0;
+              if (fr && (drained & bit)) {
+                if (*s_abort || !ptx::mbar_wait(lempty0 + 8 * a, ((par >> k) & 1u) ^ 1u, args.err, 16)) {
+                  *s_abort = 1;
+                  stop = true;
+                  break;
+                }
+                ptx::tc_fence_after();
               }
-              ptx::tc_fence_after();
-            }
-            const uint32_t d = tmem + (uint32_t)(EBN * li);
-            if (S == SMAX) {
-              mma_level_s8(L, d, aT, bdesc, fr);
-            } else {
-              const int s0 = max(1, L - S), s1 = min(S, L - 1);
-              for (int s = s0; s <= s1; ++s) {
-                const int tt = L - s - 1;
-                ptx::mma_f16_ts(d, aT + 8 * (s - 1), bdesc + (uint64_t)(((tt >> 2) * B_GROUP + (tt & 3) * 32) >> 4),
-                                kIdesc, (fr && s == s0) ? 0u : 1u);
+              const uint32_t d = tmem + (uint32_t)(EBN * a);
+              if (S == SMAX) {
+                mma_level_s8(L, d, aT, bdesc, fr);
+              } else {
+                const int s0 = max(1, L - S), s1 = min(S, L - 1);
+                for (int s = s0; s <= s1; ++s) {
+                  const int tt = L - s - 1;
+                  ptx::mma_f16_ts(d, aT + 8 * (s - 1), bdesc + (uint64_t)(((tt >> 2) * B_GROUP + (tt & 3) * 32) >> 4),
+                                  kIdesc, (fr && s == s0) ? 0u : 1u);
+                }
+              }
+              fresh &= ~bit;
+              if (drains_after(a, j) || last) {
+                ptx::mma_commit(lfull0 + 8 * a);
+                par ^= bit;
+                drained |= bit;
+                fresh |= bit;
               }
             }
-            
-            fresh &= ~bit;
-            if (((j + L) & 7) == 7 || last) {
-              ptx::mma_commit(lfull0 + 8 * li);
-              par ^= bit;
-              drained |= bit;
-              fresh |= bit;
-            }
+            if (stop) break;
+            ptx::mma_commit(empty0 + 8 * st);
           }
-          if (stop) break;
-          ptx::mma_commit(empty0 + 8 * st);
-          ptx::mma_commit(abuf0 + 8 * b);
         }
       }
       ptx::mma_commit(drain);
       ptx::mbar_wait(drain, 0, nullptr, 0);
     }
   } else {
-    // ---------------- epilogue warps: quadrant q (TMEM lanes 32q..), column half h (24 columns)
-    const int q = warp & 3, h = (warp - 2 - MMA_WARPS) >> 2;
+    // ---------------- epilogue warps: quadrant q (TMEM lanes 32q..), column quarter h (24 columns)
+    const int ew = warp - 2 - MMA_WARPS, q = warp & 3, h = ew >> 2;
     const Epilogue& e = args.e;
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
-    uint32_t epar = 0u;  // per level (bit li): parity of the drains taken so far
+    long long* scr = args.scratch + (size_t)blockIdx.x * SCRATCH_PER_CTA + (size_t)(ew * 32 + lane);
+    uint32_t epar = 0u;  // per accumulator: parity of the drains taken so far
     bool stop = false;
     for (int t = blockIdx.x; t < args.ntiles && !stop; t += gridDim.x) {
       int bi, bj;
       const EmuMat& mt = item_of(args, t, bi, bj);
       const int n = mt.n, row0 = mt.row0, KS = (n + EBK - 1) / EBK;
-      // Exact totals: hi = sum_{L<=5} V_L 2^(8(5-L)), lo = sum_{L>=6} V_L 2^(8(9-L)); P = hi 2^-40 + lo 2^-72.
-      long long hi[24], lo[24];
+      // Exact totals: the first pass gives hi = sum_{L<=5} V_L 2^(8(5-L)) (kept in scratch), the second
+      // lo = sum_{L>=6} V_L 2^(8(9-L)); P = hi 2^-40 + lo 2^-72.
+      long long acc[EPI_COLS];
 #pragma unroll
-      for (int c = 0; c < 24; ++c) hi[c] = lo[c] = 0;
-      for (int j = 0; j < KS && !stop; ++j) {
-        const int nr = j == KS - 1 ? 8 : 1;
-        for (int r = 0; r < nr; ++r) {
-          const int L = level_at(j, r);
-          if (L > S + 1) continue;
-          const int li = L - 2;
-          if (__shfl_sync(0xffffffffu, *s_abort, 0)) {
-            stop = true;
-            break;
-          }
-          if (!__all_sync(0xffffffffu, ptx::mbar_wait(lfull0 + 8 * li, (epar >> li) & 1u, args.err, 18))) {
-            *s_abort = 1;
-            stop = true;
-            break;
-          }
-          ptx::tc_fence_after();
-          // Three loads of 8 columns; the accumulator is released after the last one.
-          const uint32_t ta = tmem + lane_off + (uint32_t)(EBN * li + 24 * h);
-          const bool low = L <= 5;
-          const int sh = low ? 8 * (5 - L) : 8 * (9 - L);
-#pragma unroll
-          for (int g = 0; g < 3; ++g) {
-            uint32_t v[8];
-            ptx::tmem_ld_32x32b_x8(ta + 8 * g, v);
+      for (int c = 0; c < EPI_COLS; ++c) acc[c] = 0;
+      for (int pass = 0; pass < 2 && !stop; ++pass) {
+        for (int j = 0; j < KS && !stop; ++j) {
+          const bool lastj = j == KS - 1;
+          for (int a = 0; a < NACC; ++a) {
+            const int L = 2 + 4 * pass + a;
+            if (L > S + 1 || !(lastj || drains_after(a, j))) continue;
+            if (__shfl_sync(0xffffffffu, *s_abort, 0)) {
+              stop = true;
+              break;
+            }
+            if (!__all_sync(0xffffffffu, ptx::mbar_wait(lfull0 + 8 * a, (epar >> a) & 1u, args.err, 17))) {
+              *s_abort = 1;
+              stop = true;
+              break;
+            }
+            ptx::tc_fence_after();
+            const int sh = 8 * (3 - a);  // 8 (5 - L) in the first pass, 8 (9 - L) in the second
+            const uint32_t ta = tmem + lane_off + (uint32_t)(EBN * a + EPI_COLS * h);
+            // 24 columns as 16 + 8 (h even) or 8 + 16 (h odd): every load starts on a multiple of its width.
+            // Both loads, one wait, and the accumulator is released before any integer work.
+            uint32_t v[EPI_COLS];
+            if ((h & 1) == 0) {
+              ptx::tmem_ld_32x32b_x16(ta, v);
+              ptx::tmem_ld_32x32b_x8(ta + 16, v + 16);
+            } else {
+              ptx::tmem_ld_32x32b_x8(ta, v);
+              ptx::tmem_ld_32x32b_x16(ta + 8, v + 8);
+            }
             ptx::tmem_ld_wait();
-            if (g == 2) {
-              ptx::tc_fence_before();
-              __syncwarp();
-              if (lane == 0) ptx::mbar_arrive(lempty0 + 8 * li);
-            }
+            ptx::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(lempty0 + 8 * a);
+            epar ^= 1u << a;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-              const long long x = (long long)__float2int_rn(__uint_as_float(v[c])) << sh;
-              if (low) hi[8 * g + c] += x;
-              else lo[8 * g + c] += x;
-            }
+            for (int c = 0; c < EPI_COLS; ++c) acc[c] += (long long)__float2int_rn(__uint_as_float(v[c])) << sh;
           }
-          epar ^= 1u << li;
-                  }
+        }
+        if (stop) break;
+        if (pass == 0) {
+#pragma unroll
+          for (int c = 0; c < EPI_COLS; ++c) {
+            scr[(size_t)c * (EPI_WARPS * 32)] = acc[c];
+            acc[c] = 0;
+          }
+        }
       }
       if (stop) break;
       // Tile end: P = 2^(e_i + f_j - 72) (hi 2^32 + lo), then the fused epilogue (FP64 values, FP32 partials).
@@ -448,11 +461,12 @@ __global__ void __launch_bounds__(THREADS, 1)  // 14 warps: at most 128 register
       const int ei = i < n ? args.ex[row0 + i] : 0;
       float part = 0.0f;
 #pragma unroll
-      for (int c = 0; c < 24; ++c) {
-        const int jc = bj * EBN + 24 * h + c;
+      for (int c = 0; c < EPI_COLS; ++c) {
+        const int jc = bj * EBN + EPI_COLS * h + c;
+        const long long hi = scr[(size_t)c * (EPI_WARPS * 32)], lo = acc[c];
         if (i >= n || jc >= n || (SYM && i > jc)) continue;
-        const unsigned long long lw0 = (unsigned long long)hi[c] << 32, lw = lw0 + (unsigned long long)lo[c];
-        const long long H = (hi[c] >> 32) + (lo[c] >> 63) + (lw < lw0 ? 1 : 0);
+        const unsigned long long lw0 = (unsigned long long)hi << 32, lw = lw0 + (unsigned long long)lo;
+        const long long H = (hi >> 32) + (lo >> 63) + (lw < lw0 ? 1 : 0);
         const double P = wide_to_double(H, lw, ei + args.ey[row0 + jc] - 72);
         if (e.partial) {
           const float dd = i == jc ? (float)(1.0 - P) : -__double2float_rn(P);
@@ -476,14 +490,14 @@ __global__ void __launch_bounds__(THREADS, 1)  // 14 warps: at most 128 register
       }
       if (e.partial) {
         for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        if (lane == 0) e.partial[(int64_t)t * EPI_WARPS + (warp - 2 - MMA_WARPS)] = (double)part;
+        if (lane == 0) e.partial[(int64_t)t * EPI_WARPS + ew] = (double)part;
       }
-          }
+    }
   }
   ptx::tc_fence_before();
   __syncthreads();
   ptx::tc_fence_after();
-    if (warp == 0) ptx::tmem_dealloc(tmem, 512);
+  if (warp == 0) ptx::tmem_dealloc(tmem, 512);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn_emu() {
@@ -527,7 +541,7 @@ int sm_count_emu() {
 
 cudaError_t launch_emu(const __half* DX, const __half* DY, int R, int K, int ldl, Mode mode, EmuArgs& a,
                        cudaStream_t s) {
-  if (a.S < 1 || a.S > SMAX || ldl % 16 != 0 || ldl < K || K < 1 || !a.items) return cudaErrorInvalidValue;
+  if (a.S < 1 || a.S > SMAX || ldl % 16 != 0 || ldl < K || K < 1 || !a.items || !a.scratch) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(DX) | reinterpret_cast<uintptr_t>(DY)) & 15) return cudaErrorMisalignedAddress;
   static bool attr_set = false;
   if (!attr_set) {
@@ -590,9 +604,13 @@ cudaError_t slice_rows(const double* X, int R, int n, int ldx, int ldl, int S, c
   return cudaGetLastError();
 }
 
+size_t emu_scratch_bytes() { return (size_t)sm_count_emu() * SCRATCH_PER_CTA * sizeof(long long); }
+
 cudaError_t gemm_emu(const __half* DX, const int* ex, const __half* DY, const int* ey, int n, int ldl, int S, Mode mode,
-                     bool transpose, const int4* items, int nitems, const Epilogue& e, int* err, cudaStream_t s) {
+                     bool transpose, const int4* items, int nitems, const Epilogue& e, long long* scratch, int* err,
+                     cudaStream_t s) {
   EmuArgs a{};
+  a.scratch = scratch;
   a.S = S;
   a.ld = n;
   a.ntiles = nitems;
@@ -609,9 +627,10 @@ cudaError_t gemm_emu(const __half* DX, const int* ex, const __half* DY, const in
 
 cudaError_t gemm_emu_batched(const __half* DX, const int* ex, const __half* DY, const int* ey, int R, int K, int ldl,
                              int ld, int S, Mode mode, bool transpose, const int4* items, int nitems,
-                             const EmuBatchMat* mats, const Epilogue& e, int* err, cudaStream_t s) {
+                             const EmuBatchMat* mats, const Epilogue& e, long long* scratch, int* err, cudaStream_t s) {
   static_assert(sizeof(EmuBatchMat) == sizeof(EmuMat), "batch matrix record");
   EmuArgs a{};
+  a.scratch = scratch;
   a.S = S;
   a.ld = ld;
   a.ntiles = nitems;

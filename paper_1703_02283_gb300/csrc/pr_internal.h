@@ -80,19 +80,21 @@ cudaError_t gemm_bf16_tc(const __nv_bfloat16* X, const __nv_bfloat16* Y, int n, 
 // epilogue (out / out2 / partial; no BF16 copies). One residual partial per epilogue warp and item
 // (emu_partials_per_item() per item, in item order).
 // emu_tile_list(): appends the work items (m, tile row, tile column, 0) of matrix m (order n) in the
-// kernel's order; tiles are 128 rows x 48 columns, symmetric mode keeps those reaching the upper triangle.
+// kernel's order; tiles are 128 rows x 96 columns, symmetric mode keeps those reaching the upper triangle.
 void emu_tile_list(int m, int n, Mode mode, std::vector<int4>& out);
 int emu_tile_count(int n, Mode mode);
 int emu_tiles(int n, Mode mode);  // residual partials of one product: emu_tile_count * emu_partials_per_item
 int emu_partials_per_item();
 int emu_max_slices();
 int emu_ld(int K);  // the K extent of a digit-plane row: K rounded up to 16
+size_t emu_scratch_bytes();  // device scratch each gemm_emu / gemm_emu_batched call needs (per stream)
 cudaError_t slice(const double* X, int n, int ldl, int S, __half* D, int* ex, cudaStream_t s);
 // Slices R rows of an FP64 array with leading dimension ldx; row r has row_n[r] valid columns (n if null).
 cudaError_t slice_rows(const double* X, int R, int n, int ldx, int ldl, int S, const int* row_n, __half* D, int* ex,
                        cudaStream_t s);
 cudaError_t gemm_emu(const __half* DX, const int* ex, const __half* DY, const int* ey, int n, int ldl, int S, Mode mode,
-                     bool transpose, const int4* items, int nitems, const Epilogue& e, int* err, cudaStream_t s);
+                     bool transpose, const int4* items, int nitems, const Epilogue& e, long long* scratch, int* err,
+                     cudaStream_t s);
 
 // A batch of matrices packed row-wise in shared buffers (leading dimension ld for FP64, ldl for digit
 // planes; R packed rows per plane; K the largest order). Work items from emu_tile_list per matrix;
@@ -103,7 +105,7 @@ struct EmuBatchMat {
 };
 cudaError_t gemm_emu_batched(const __half* DX, const int* ex, const __half* DY, const int* ey, int R, int K, int ldl,
                              int ld, int S, Mode mode, bool transpose, const int4* items, int nitems,
-                             const EmuBatchMat* mats, const Epilogue& e, int* err, cudaStream_t s);
+                             const EmuBatchMat* mats, const Epilogue& e, long long* scratch, int* err, cudaStream_t s);
 
 // ---- elementwise and reductions (k_elementwise.cu)
 // scal[0] = max |a_ij|, scal[1] = max |a_ij - a_ji|, scal[2] = #non-finite, scal[3] = #non-positive diagonal
