@@ -50,6 +50,7 @@ struct pr_batch_s {
   int partial_cap = 0;
   int4* items = nullptr;
   int items_cap = 0;
+  std::vector<int4> items_host;
   EmuBatchMat* mats = nullptr;
   int* seg = nullptr;  // segment begin[count], end[count]
   double* res = nullptr;
@@ -62,7 +63,18 @@ struct pr_batch_s {
   int64_t launches = 0;
   pr_batch_stats_t st{};
   bool timing = false;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // Pinned staging of the per-stage work lists, a ring of slots: a slot is rewritten only after the copy
+  // that read it has completed (its event), so stages need no stream synchronisation.
+  static constexpr int kSlots = 4;
+  int4* h_items[kSlots] = {};
+  EmuBatchMat* h_mats[kSlots] = {};
+  cudaEvent_t slot_ev[kSlots] = {};
+  bool slot_used[kSlots] = {};
+  int slot = 0;
+  // Event pairs around product launches, read at the next synchronisation.
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+  std::vector<double> ev_flops;
+  size_t ev_pending = 0;
   std::string errmsg;
 };
 
@@ -82,6 +94,19 @@ pr_status bfail(pr_batch b, pr_status code, const std::string& msg) {
       return bfail((b), _e == cudaErrorMemoryAllocation ? PR_ENOMEM : PR_ECUDA,                          \
                    std::string(#call) + ": " + cudaGetErrorName(_e) + " (" + cudaGetErrorString(_e) + ")"); \
   } while (0)
+
+// Adds the times of the product launches bracketed since the last call (the stream has been synchronised).
+pr_status harvest_timing(pr_batch b) {
+  for (size_t k = 0; k < b->ev_pending; ++k) {
+    float ms = 0.f;
+    PB_CK(b, cudaEventElapsedTime(&ms, b->ev_pool[k].first, b->ev_pool[k].second));
+    b->st.stages_timed += 1;
+    b->st.stage_ms += ms;
+    b->st.stage_flops_timed += b->ev_flops[k];
+  }
+  b->ev_pending = 0;
+  return PR_OK;
+}
 
 pr_status ensure_slices(pr_batch b, Buf& x) {
   if (x.sl_valid) return PR_OK;
@@ -111,20 +136,28 @@ pr_status stage(pr_batch b, Buf& Xb, Buf& Yb, Mode mode, const std::vector<int>&
   if (s != PR_OK) return s;
   std::vector<int> sorted = who;
   std::sort(sorted.begin(), sorted.end(), [&](int x, int y) { return b->n[x] > b->n[y]; });
-  std::vector<int4> items;
-  std::vector<EmuBatchMat> mats(b->count);
+  // The host staging slot: wait until the copy that last read it has completed.
+  const int sl = b->slot;
+  b->slot = (b->slot + 1) % pr_batch_s::kSlots;
+  if (b->slot_used[sl]) PB_CK(b, cudaEventSynchronize(b->slot_ev[sl]));
+  EmuBatchMat* mats = b->h_mats[sl];
   for (int m = 0; m < b->count; ++m) mats[m] = EmuBatchMat{b->n[m], b->row0[m], 0.0, 0.0, 0.0};
   const int per = pr::emu_partials_per_item();
   for (size_t w = 0; w < who.size(); ++w) mats[who[w]] = EmuBatchMat{b->n[who[w]], b->row0[who[w]], coef[w].x, coef[w].y,
                                                                     coef[w].z};
+  std::vector<int4>& items = b->items_host;
+  items.clear();
   for (int m : sorted) {
     if (seg_begin) (*seg_begin)[m] = (int)items.size() * per;
     pr::emu_tile_list(m, b->n[m], mode, items);
     if (seg_end) (*seg_end)[m] = (int)items.size() * per;
   }
   if ((int)items.size() > b->items_cap) return bfail(b, PR_ECUDA, "pr_batch: work list larger than allocated");
-  PB_CK(b, cudaMemcpyAsync(b->items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream));
-  PB_CK(b, cudaMemcpyAsync(b->mats, mats.data(), mats.size() * sizeof(EmuBatchMat), cudaMemcpyHostToDevice, b->stream));
+  std::copy(items.begin(), items.end(), b->h_items[sl]);
+  PB_CK(b, cudaMemcpyAsync(b->items, b->h_items[sl], items.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream));
+  PB_CK(b, cudaMemcpyAsync(b->mats, mats, (size_t)b->count * sizeof(EmuBatchMat), cudaMemcpyHostToDevice, b->stream));
+  PB_CK(b, cudaEventRecord(b->slot_ev[sl], b->stream));
+  b->slot_used[sl] = true;
   double flops = 0.0;
   for (int m : who) {
     const double nm = b->n[m];
@@ -135,25 +168,29 @@ pr_status stage(pr_batch b, Buf& Xb, Buf& Yb, Mode mode, const std::vector<int>&
   if (so.out2) e.out2 = so.out2->f;
   e.cin = so.cin;
   e.partial = so.partial ? b->partial : nullptr;
-  if (b->timing) PB_CK(b, cudaEventRecord(b->ev0, b->stream));
+  if (b->timing) {
+    if (b->ev_pending == b->ev_pool.size()) {
+      cudaEvent_t e0, e1;
+      PB_CK(b, cudaEventCreate(&e0));
+      PB_CK(b, cudaEventCreate(&e1));
+      b->ev_pool.emplace_back(e0, e1);
+      b->ev_flops.push_back(0.0);
+    }
+    PB_CK(b, cudaEventRecord(b->ev_pool[b->ev_pending].first, b->stream));
+  }
   PB_CK(b, pr::gemm_emu_batched(Xb.sl, Xb.ex, Yb.sl, Yb.ex, b->R, b->K, pr::emu_ld(b->K), b->ld, b->S, mode, so.transpose,
                                 b->items, (int)items.size(), b->mats, e, b->scratch, b->err, b->stream));
-  if (b->timing) PB_CK(b, cudaEventRecord(b->ev1, b->stream));
+  if (b->timing) {
+    PB_CK(b, cudaEventRecord(b->ev_pool[b->ev_pending].second, b->stream));
+    b->ev_flops[b->ev_pending] = flops;
+    b->ev_pending += 1;
+  }
   b->launches += 1;
   b->st.stages += 1;
   b->st.products += (int64_t)who.size();
   b->st.product_flops += flops;
   if (so.out) so.out->sl_valid = false;
   if (so.out2) so.out2->sl_valid = false;
-  // The host-side records must outlive the asynchronous copies: wait for this stage's launch inputs.
-  PB_CK(b, cudaStreamSynchronize(b->stream));
-  if (b->timing) {
-    float ms = 0.f;
-    PB_CK(b, cudaEventElapsedTime(&ms, b->ev0, b->ev1));
-    b->st.stages_timed += 1;
-    b->st.stage_ms += ms;
-    b->st.stage_flops_timed += flops;
-  }
   return PR_OK;
 }
 
@@ -177,6 +214,8 @@ pr_status read_residuals(pr_batch b, const std::vector<int>& who, const std::vec
     cudaMemsetAsync(b->err, 0, sizeof(int), b->stream);
     return bfail(b, PR_ETIMEOUT, "pr_batch: a bounded device wait expired");
   }
+  pr_status hs = harvest_timing(b);
+  if (hs != PR_OK) return hs;
   for (size_t w = 0; w < who.size(); ++w) b->hist[who[w]].push_back(b->hres[w]);
   return PR_OK;
 }
@@ -233,8 +272,15 @@ pr_status pr_batch_destroy(pr_batch b) {
                   (void*)b->res, (void*)b->err, (void*)b->scratch})
     if (q) cudaFree(q);
   if (b->hres) cudaFreeHost(b->hres);
-  if (b->ev0) cudaEventDestroy(b->ev0);
-  if (b->ev1) cudaEventDestroy(b->ev1);
+  for (int k = 0; k < pr_batch_s::kSlots; ++k) {
+    if (b->h_items[k]) cudaFreeHost(b->h_items[k]);
+    if (b->h_mats[k]) cudaFreeHost(b->h_mats[k]);
+    if (b->slot_ev[k]) cudaEventDestroy(b->slot_ev[k]);
+  }
+  for (auto& pr_ : b->ev_pool) {
+    cudaEventDestroy(pr_.first);
+    cudaEventDestroy(pr_.second);
+  }
   delete b;
   return PR_OK;
 }
@@ -313,6 +359,11 @@ pr_status pr_batch_init(pr_batch* out, int count, const int64_t* n, const int* p
   b->items_cap = (int)items;
   b->partial_cap = (int)(items * pr::emu_partials_per_item());
   PB_INIT_CK(cudaMalloc((void**)&b->items, (size_t)items * sizeof(int4)));
+  for (int k = 0; k < pr_batch_s::kSlots; ++k) {
+    PB_INIT_CK(cudaMallocHost((void**)&b->h_items[k], (size_t)items * sizeof(int4)));
+    PB_INIT_CK(cudaMallocHost((void**)&b->h_mats[k], (size_t)count * sizeof(EmuBatchMat)));
+    PB_INIT_CK(cudaEventCreateWithFlags(&b->slot_ev[k], cudaEventDisableTiming));
+  }
   PB_INIT_CK(cudaMalloc((void**)&b->partial, (size_t)b->partial_cap * sizeof(double)));
   PB_INIT_CK(cudaMalloc((void**)&b->mats, (size_t)count * sizeof(EmuBatchMat)));
   PB_INIT_CK(cudaMalloc((void**)&b->seg, (size_t)2 * count * sizeof(int)));
@@ -424,6 +475,8 @@ pr_status pr_batch_solve(pr_batch b, int precision, double tol, int* iterations,
           const size_t off = (size_t)b->row0[m] * b->ld;
           PB_CK(b, cudaMemcpyAsync(b->result + off, b->X.f + off, (size_t)b->n[m] * b->ld * sizeof(double),
                                    cudaMemcpyDeviceToDevice, b->stream));
+          // Its rows are no longer sliced (row order -1).
+          PB_CK(b, cudaMemsetAsync(b->row_n + b->row0[m], 0xFF, (size_t)b->n[m] * sizeof(int), b->stream));
         } else {
           (pass == 0 ? ns2 : cp2).push_back(m);
         }
@@ -457,6 +510,8 @@ pr_status pr_batch_solve(pr_batch b, int precision, double tol, int* iterations,
     for (int m : cp) b->iterations[m] += 1;
   }
   PB_CK(b, cudaStreamSynchronize(b->stream));
+  s = harvest_timing(b);
+  if (s != PR_OK) return s;
   for (int m = 0; m < count; ++m) {
     if (iterations) iterations[m] = b->iterations[m];
     if (status) status[m] = b->status[m];
@@ -499,10 +554,6 @@ pr_status pr_batch_stats(pr_batch b, pr_batch_stats_t* out) {
 pr_status pr_batch_set_timing(pr_batch b, int on) {
   if (!b) return bfail(nullptr, PR_ESTATE, "pr_batch_set_timing: NULL batch");
   cudaSetDevice(b->device);
-  if (on && !b->ev0) {
-    PB_CK(b, cudaEventCreate(&b->ev0));
-    PB_CK(b, cudaEventCreate(&b->ev1));
-  }
   b->timing = on != 0;
   return PR_OK;
 }

@@ -88,13 +88,14 @@ __device__ __forceinline__ long long fixed_point(unsigned long long u, int e, in
 // One warp per row r of an R-row FP64 array (leading dimension ldx): exponent e_r, then 8 digit planes in
 // the layout D[r][k / 16][s][k % 16] (row length 8 ldl halves, ldl a multiple of 16; s = 0 is the most
 // significant digit, planes s >= S are zero). Row r has row_n[r] valid columns (all rows n when row_n is
-// null); the rest of the ldl columns get digit 0. Each lane handles two adjacent columns, so loads are 16
-// bytes and stores half2.
+// null); the rest of the ldl columns get digit 0; rows with row_n[r] < 0 are skipped (left as they are).
+// Each lane handles two adjacent columns, so loads are 16 bytes and stores half2.
 __global__ void k_slice(const double* __restrict__ X, int R, int n, int ldx, int ldl, int S,
                         const int* __restrict__ row_n, __half* __restrict__ D, int* __restrict__ ex) {
   const int lane = threadIdx.x & 31;
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < R; i += (gridDim.x * blockDim.x) >> 5) {
     const int nr = row_n ? row_n[i] : n;
+    if (nr < 0) continue;
     const unsigned long long* row = reinterpret_cast<const unsigned long long*>(X + (int64_t)i * ldx);
     unsigned long long mb = 0;  // largest |x| as a bit pattern (non-negative doubles order like integers)
     for (int k = lane; k < nr; k += 32) {
