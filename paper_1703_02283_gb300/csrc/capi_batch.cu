@@ -379,46 +379,56 @@ pr_status pr_batch_init(pr_batch* out, int count, const int64_t* n, const int* p
     PB_INIT_CK(cudaMemcpyAsync(b->row_n, rn.data(), rn.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
     PB_INIT_CK(cudaStreamSynchronize(b->stream));
   }
-  // Per matrix: checks, the norms of Eq. 3 and C_0, staged through an n x n work area.
+  // Per matrix: checks and the norms of Eq. 3 (all matrices queued, one read-back), then C_0; staged
+  // through an n x n work area on the batch's stream, without waiting between matrices.
   double *tA = nullptr, *tC = nullptr, *scal = nullptr, *work = nullptr, *hs = nullptr;
   PB_INIT_CK(cudaMalloc((void**)&tA, (size_t)K * K * sizeof(double)));
   PB_INIT_CK(cudaMalloc((void**)&tC, (size_t)K * K * sizeof(double)));
-  PB_INIT_CK(cudaMalloc((void**)&scal, 8 * sizeof(double)));
+  PB_INIT_CK(cudaMalloc((void**)&scal, 8 * (size_t)count * sizeof(double)));
   PB_INIT_CK(cudaMalloc((void**)&work, 2 * (size_t)K * sizeof(double)));
-  PB_INIT_CK(cudaMallocHost((void**)&hs, 8 * sizeof(double)));
+  PB_INIT_CK(cudaMallocHost((void**)&hs, 8 * (size_t)count * sizeof(double)));
   pr_status st = PR_OK;
-  for (int m = 0; m < count && st == PR_OK; ++m) {
+  cudaError_t e = cudaSuccess;
+  for (int m = 0; m < count && e == cudaSuccess; ++m) {
     const int nm = b->n[m];
     const size_t pitch = (size_t)b->ld * sizeof(double), w = (size_t)nm * sizeof(double);
-    cudaError_t e = cudaMemcpyAsync(tA, A[m], (size_t)nm * nm * sizeof(double), cudaMemcpyDefault, b->stream);
-    if (e == cudaSuccess) e = pr::validate(tA, nm, scal, b->stream);
-    if (e == cudaSuccess) e = pr::abs_norms(tA, nm, work, scal + 4, b->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hs, scal, 6 * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    if (e != cudaSuccess) {
-      st = bfail(b, PR_ECUDA, std::string("pr_batch_init: ") + cudaGetErrorName(e));
-      break;
-    }
-    if (hs[2] > 0 || hs[1] > o.sym_tol * hs[0]) {
-      st = bfail(b, PR_EINVAL, "pr_batch_init: matrix " + std::to_string(m) + " is not finite and symmetric");
-      break;
-    }
-    if (hs[3] > 0) {
-      st = bfail(b, PR_ENOTSPD, "pr_batch_init: matrix " + std::to_string(m) + " has a non-positive diagonal");
-      break;
-    }
-    if (o.c0 == PR_C0_EQ3) e = pr::init_c0_eq3(tA, nm, 1.0 / (hs[4] * hs[5]), tC, b->stream);
-    else e = pr::set_scaled_identity(tC, nm, pow(hs[4], -1.0 / p[m]), b->stream);
+    e = cudaMemcpyAsync(tA, A[m], (size_t)nm * nm * sizeof(double), cudaMemcpyDefault, b->stream);
+    if (e == cudaSuccess) e = pr::validate(tA, nm, scal + 8 * m, b->stream);
+    if (e == cudaSuccess) e = pr::abs_norms(tA, nm, work, scal + 8 * m + 4, b->stream);
     if (e == cudaSuccess)
       e = cudaMemcpy2DAsync(b->A.f + (size_t)b->row0[m] * b->ld, pitch, tA, w, w, nm, cudaMemcpyDeviceToDevice,
                             b->stream);
+    b->launches += 4;
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hs, scal, 8 * (size_t)count * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) st = bfail(b, PR_ECUDA, std::string("pr_batch_init: ") + cudaGetErrorName(e));
+  for (int m = 0; m < count && st == PR_OK; ++m) {
+    const double* h = hs + 8 * m;
+    if (h[2] > 0 || h[1] > o.sym_tol * h[0])
+      st = bfail(b, PR_EINVAL, "pr_batch_init: matrix " + std::to_string(m) + " is not finite and symmetric");
+    else if (h[3] > 0)
+      st = bfail(b, PR_ENOTSPD, "pr_batch_init: matrix " + std::to_string(m) + " has a non-positive diagonal");
+  }
+  for (int m = 0; m < count && st == PR_OK && e == cudaSuccess; ++m) {
+    const int nm = b->n[m];
+    const double* h = hs + 8 * m;
+    const size_t pitch = (size_t)b->ld * sizeof(double), w = (size_t)nm * sizeof(double);
+    if (o.c0 == PR_C0_EQ3) {
+      e = cudaMemcpy2DAsync(tA, w, b->A.f + (size_t)b->row0[m] * b->ld, pitch, w, nm, cudaMemcpyDeviceToDevice,
+                            b->stream);
+      if (e == cudaSuccess) e = pr::init_c0_eq3(tA, nm, 1.0 / (h[4] * h[5]), tC, b->stream);
+    } else {
+      e = pr::set_scaled_identity(tC, nm, pow(h[4], -1.0 / p[m]), b->stream);
+    }
     if (e == cudaSuccess)
       e = cudaMemcpy2DAsync(b->X.f + (size_t)b->row0[m] * b->ld, pitch, tC, w, w, nm, cudaMemcpyDeviceToDevice,
                             b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    if (e != cudaSuccess) st = bfail(b, PR_ECUDA, std::string("pr_batch_init: ") + cudaGetErrorName(e));
-    b->launches += 5;
+    b->launches += 1;
   }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (st == PR_OK && e != cudaSuccess) st = bfail(b, PR_ECUDA, std::string("pr_batch_init: ") + cudaGetErrorName(e));
   cudaFree(tA);
   cudaFree(tC);
   cudaFree(scal);

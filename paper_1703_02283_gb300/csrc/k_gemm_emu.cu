@@ -88,7 +88,8 @@ __device__ __forceinline__ long long fixed_point(unsigned long long u, int e, in
 // One warp per row r of an R-row FP64 array (leading dimension ldx): exponent e_r, then 8 digit planes in
 // the layout D[r][k / 16][s][k % 16] (row length 8 ldl halves, ldl a multiple of 16; s = 0 is the most
 // significant digit, planes s >= S are zero). Row r has row_n[r] valid columns (all rows n when row_n is
-// null); the rest of the ldl columns get digit 0; rows with row_n[r] < 0 are skipped (left as they are).
+// null); columns from there up to the next multiple of 16 (the last step the products read for that
+// row's matrix) get digit 0, later columns are left as they are; rows with row_n[r] < 0 are skipped.
 // Each lane handles two adjacent columns, so loads are 16 bytes and stores half2.
 __global__ void k_slice(const double* __restrict__ X, int R, int n, int ldx, int ldl, int S,
                         const int* __restrict__ row_n, __half* __restrict__ D, int* __restrict__ ex) {
@@ -106,7 +107,8 @@ __global__ void k_slice(const double* __restrict__ X, int R, int n, int ldx, int
     const int emax = (int)(mb >> 52);               // biased exponent of the row maximum
     const int e = emax == 0 ? 0 : emax - 1023 + 2;  // zero (or subnormal-only) rows get digits 0
     if (lane == 0) ex[i] = e;
-    for (int k = 2 * lane; k < ldl; k += 64) {
+    const int kend = min(ldl, (nr + 15) & ~15);
+    for (int k = 2 * lane; k < kend; k += 64) {
       long long F0 = 0, F1 = 0;
       if (emax != 0) {
         if (k < nr) F0 = fixed_point(row[k], e, S);
