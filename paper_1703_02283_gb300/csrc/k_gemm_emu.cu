@@ -115,16 +115,34 @@ __global__ void k_slice(const double* __restrict__ X, int R, int n, int ldx, int
         if (k + 1 < nr) F1 = fixed_point(row[k + 1], e, S);
       }
       __half2* dst = reinterpret_cast<__half2*>(D + (int64_t)i * 8 * ldl + (k >> 4) * 128 + (k & 15));
-      for (int s = S; s < SMAX; ++s) dst[8 * s] = __floats2half2_rn(0.0f, 0.0f);
-      // Balanced base-256 digits, least significant first; the last one takes the remainder (|.| <= 128).
-      for (int s = S - 1; s >= 1; --s) {
-        const int r0 = (int)(F0 & 255), r1 = (int)(F1 & 255);
-        const int d0 = r0 >= 128 ? r0 - 256 : r0, d1 = r1 >= 128 ? r1 - 256 : r1;
-        F0 = (F0 - d0) >> 8;
-        F1 = (F1 - d1) >> 8;
-        dst[8 * s] = __floats2half2_rn((float)d0, (float)d1);
+      if (S == SMAX) {
+        // Balanced base-256 digits in 32-bit arithmetic: digit k (least significant first) is
+        // v = byte_k(F) + c minus 256 c' with carry c' = (v >= 128); the top digit is (F >> 56) + c.
+        // (The same digits as the 64-bit recurrence F <- (F - d) >> 8 below.)
+        const unsigned lo0 = (unsigned)F0, lo1 = (unsigned)F1;
+        const unsigned hu0 = (unsigned)(F0 >> 32), hu1 = (unsigned)(F1 >> 32);
+        int c0 = 0, c1 = 0;
+#pragma unroll
+        for (int k = 0; k < SMAX - 1; ++k) {
+          const int v0 = (int)(((k < 4 ? lo0 >> (8 * k) : hu0 >> (8 * (k - 4)))) & 255u) + c0;
+          const int v1 = (int)(((k < 4 ? lo1 >> (8 * k) : hu1 >> (8 * (k - 4)))) & 255u) + c1;
+          c0 = v0 >= 128 ? 1 : 0;
+          c1 = v1 >= 128 ? 1 : 0;
+          dst[8 * (SMAX - 1 - k)] = __floats2half2_rn((float)(v0 - 256 * c0), (float)(v1 - 256 * c1));
+        }
+        dst[0] = __floats2half2_rn((float)(((int)hu0 >> 24) + c0), (float)(((int)hu1 >> 24) + c1));
+      } else {
+        for (int s = S; s < SMAX; ++s) dst[8 * s] = __floats2half2_rn(0.0f, 0.0f);
+        // Balanced base-256 digits, least significant first; the last one takes the remainder (|.| <= 128).
+        for (int s = S - 1; s >= 1; --s) {
+          const int r0 = (int)(F0 & 255), r1 = (int)(F1 & 255);
+          const int d0 = r0 >= 128 ? r0 - 256 : r0, d1 = r1 >= 128 ? r1 - 256 : r1;
+          F0 = (F0 - d0) >> 8;
+          F1 = (F1 - d1) >> 8;
+          dst[8 * s] = __floats2half2_rn((float)d0, (float)d1);
+        }
+        dst[0] = __floats2half2_rn((float)F0, (float)F1);
       }
-      dst[0] = __floats2half2_rn((float)F0, (float)F1);
     }
   }
 }
