@@ -201,8 +201,9 @@ pr_status pr_history(pr_handle h, double* out, int cap, int* len);
  * P = X Y for symmetric n x n FP64 X and Y (device or host memory) that commute, so that X Y is symmetric.
  * sym != 0 computes only the upper-triangle tiles and mirrors them (the iteration's symmetric products);
  * sym == 0 computes every tile. precision PR_FP64 uses FP64 DMMA; PR_BF16 rounds X and Y to BF16 and
- * accumulates in FP32 on the tcgen05 tensor cores; PR_EMU64 forms the product from 9 exact BF16 digit
- * slices per operand (see PR_EMU64). P: n*n FP64 output (device or host), caller-owned.
+ * accumulates in FP32 on the tcgen05 tensor cores; PR_EMU64 forms the product from 8 balanced base-256
+ * digit planes per operand, exact in FP16, and the 36 digit-plane pairs that reach FP64 accuracy (see
+ * PR_EMU64). P: n*n FP64 output (device or host), caller-owned.
  * Allocates and frees temporary device buffers. Synchronises the stream. */
 pr_status pr_matmul(int precision, const double* X, const double* Y, int64_t n, int sym, double* P, void* stream);
 

@@ -58,11 +58,6 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// Named barrier among `threads` threads (a multiple of 32) of the CTA; id 0 is __syncthreads'.
-__device__ __forceinline__ void named_bar_sync(int id, int threads) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
-}
-
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
@@ -81,16 +76,6 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::
           "r"(dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "r"(z)
-      : "memory");
-}
-
-// 4-D tiled TMA load of the box at (x, y, z, w) into shared memory, completing on bar.
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y, int z,
-                                            int w) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], [%2];" ::
-          "r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "r"(z), "r"(w)
       : "memory");
 }
 
@@ -171,20 +156,6 @@ __device__ __forceinline__ void tmem_ld_32x32b_x16(uint32_t taddr, uint32_t* r) 
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Warp-collective store of 32 consecutive 32-bit columns per lane (the inverse of tmem_ld_32x32b_x32).
-__device__ __forceinline__ void tmem_st_32x32b_x32(uint32_t taddr, const uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
-      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
-      "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
-      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
-      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
-      "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
-      "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
-      : "memory");
-}
-__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
 // Shared-memory matrix descriptor of a K-major operand tile written by TMA with 128-byte swizzling:
 // rows of 128 bytes (64 BF16 along K), 8-row swizzle atoms 1024 bytes apart (stride byte offset).
 __device__ __forceinline__ uint64_t desc_sw128_kmajor(uint32_t saddr) {
@@ -194,18 +165,6 @@ __device__ __forceinline__ uint64_t desc_sw128_kmajor(uint32_t saddr) {
   d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;    // stride byte offset >> 4
   d |= (uint64_t)1u << 46;                          // descriptor version for tcgen05
   d |= (uint64_t)2u << 61;                          // layout: 128-byte swizzle
-  return d;
-}
-
-// Shared-memory matrix descriptor of a K-major operand tile written by TMA with 32-byte swizzling: rows of
-// 32 bytes (16 halves along K, one MMA's K), 8-row swizzle atoms 256 bytes apart (stride byte offset).
-__device__ __forceinline__ uint64_t desc_sw32_kmajor(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);        // start address >> 4
-  d |= (uint64_t)1u << 16;                        // leading byte offset (unused: K fits one swizzle row)
-  d |= (uint64_t)((256u >> 4) & 0x3FFFu) << 32;   // stride byte offset >> 4
-  d |= (uint64_t)1u << 46;                        // descriptor version for tcgen05
-  d |= (uint64_t)6u << 61;                        // layout: 32-byte swizzle
   return d;
 }
 
