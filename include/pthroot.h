@@ -216,7 +216,8 @@ pr_status pr_set_timing(pr_handle h, int on);
  * product stage of an iteration is one launch of the PR_EMU64 tensor-core kernel over the tiles of every
  * matrix taking part in it (matrices packed row-wise with one leading dimension). Per matrix, the forms,
  * the initial guess (Eq. 3 or the scaled identity), the stop rule and the results are those of pr_iterate;
- * a matrix whose stop rule fires leaves the work lists. */
+ * a matrix whose stop rule fires leaves the work lists. A solve is one CUDA graph with a device-side loop:
+ * work lists, residuals, stop rules and the loop condition are computed on the GPU. */
 typedef struct pr_batch_s* pr_batch;
 
 /* Creates a batch. n[i] in [1, 16384], p[i] in [1, 64], A[i]: n[i]*n[i] FP64 row-major, device or host,
@@ -227,7 +228,10 @@ pr_status pr_batch_init(pr_batch* b, int count, const int64_t* n, const int* p, 
 
 /* Iterates every active matrix until its stop rule fires (tol, stagnation, max_iter, divergence), with
  * PR_EMU64 products. iterations[i] and status[i] (a pr_status stop code; may be NULL) receive the outcome
- * per matrix. Synchronises the stream once per iteration to read the residuals. */
+ * per matrix. The first call captures the solve graph (on a private stream); every call launches it once
+ * on the batch's stream and synchronises that stream once, at the end. A call after every matrix has
+ * stopped changes nothing. Errors: PR_ESTATE, PR_EINVAL (tol < 0), PR_EUNSUPPORTED (precision other than
+ * PR_EMU64), PR_ECUDA, PR_ETIMEOUT (a bounded device wait expired). */
 pr_status pr_batch_solve(pr_batch b, int precision, double tol, int* iterations, int* status);
 
 /* Copies the result of matrix i (n[i]*n[i] FP64, row-major) to C_out (device or host). */
@@ -247,8 +251,8 @@ typedef struct {
   int64_t stages;            /* product launches */
   int64_t products;          /* per-matrix products in those launches */
   double product_flops;      /* their FP64-equivalent algorithmic flops */
-  int64_t stages_timed;      /* product launches timed with CUDA events (pr_batch_set_timing) */
-  double stage_ms;           /* summed event time of the timed launches */
+  int64_t stages_timed;      /* product launches timed (pr_batch_set_timing) */
+  double stage_ms;           /* summed time of the timed launches: first CTA start to last CTA end */
   double stage_flops_timed;  /* FP64-equivalent algorithmic flops of the timed launches */
   int emu_slices;            /* digit planes per operand */
 } pr_batch_stats_t;
@@ -256,8 +260,9 @@ typedef struct {
 /* Fills *out. Errors: PR_ESTATE (b NULL), PR_EINVAL (out NULL). */
 pr_status pr_batch_stats(pr_batch b, pr_batch_stats_t* out);
 
-/* on != 0: bracket every product launch with CUDA events on the batch's stream (read back at the
- * synchronisation that ends each stage). Errors: PR_ESTATE, PR_ECUDA. */
+/* on != 0: add the product launches of the following solves to stages_timed / stage_ms /
+ * stage_flops_timed. Each launch folds the device clock (%globaltimer, ns) at the start of its first CTA
+ * and at the end of its last into a slot that the solve graph reads back itself. Errors: PR_ESTATE. */
 pr_status pr_batch_set_timing(pr_batch b, int on);
 
 /* Text for the last failing call on b (b NULL: the last failing pr_batch_init of this thread). */

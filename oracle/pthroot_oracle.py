@@ -60,7 +60,8 @@ __all__ = [
     "norm_1", "norm_inf", "initial_guess_eq3", "initial_guess_scaled_identity", "symmetrize",
     "sym_product", "power_times", "residual_fro", "step_literal", "step_newton_schulz",
     "coupled_start", "step_coupled", "solve", "SolveInfo", "closed_form_root", "eig_root",
-    "scalar_recurrence", "scalar_residuals", "forward_error", "default_form",
+    "scalar_recurrence", "scalar_residuals", "forward_error", "default_form", "closed_form_block",
+    "residual_rows",
 ]
 
 
@@ -256,6 +257,24 @@ def closed_form_root(Q: np.ndarray, lam: np.ndarray, p: int) -> np.ndarray:
     """A^{-1/p} = Q diag(lam^{-1/p}) Q^T for A = Q diag(lam) Q^T (the limit named in Sec. 2)."""
     Z = (Q * lam ** (-1.0 / p)) @ Q.T
     return symmetrize(Z)
+
+
+def closed_form_block(Q_rows: np.ndarray, Q_cols: np.ndarray, lam: np.ndarray, p: int) -> np.ndarray:
+    """Entries Z[I, J] of Z = Q diag(lam^{-1/p}) Q^T from rows I and J of Q: the closed form of Sec. 2's limit
+    evaluated one entry at a time, Z_ij = sum_k Q_ik lam_k^{-1/p} Q_jk (for orders too large to form Z)."""
+    return (np.asarray(Q_rows) * lam ** (-1.0 / p)) @ np.asarray(Q_cols).T
+
+
+def residual_rows(C: np.ndarray, A: np.ndarray, p: int, rows) -> np.ndarray:
+    """Rows I of I - C^p A, formed as e_I^T - (((C[I] C) C) ... C) A with p - 1 factors C: the residual of
+    Eq. 2 on a subset of rows, for orders where the full product is too large for the CPU."""
+    rows = np.asarray(rows)
+    T = np.array(C[rows], dtype=np.float64)
+    for _ in range(p - 1):
+        T = T @ C
+    R = -(T @ A)
+    R[np.arange(len(rows)), rows] += 1.0
+    return R
 
 
 def eig_root(A: np.ndarray, p: int) -> np.ndarray:

@@ -415,17 +415,8 @@ pr_status literal_update(pr_handle h, int prec) {
 
 // The stop rule (see pr_stop_rule): returns a pr_status to stop with, or -1 to apply one more update.
 int pr::stop_rule(const double* hist, const int* prec, int len, double tol, const pr_options& o) {
-  const double r = hist[len - 1];
-  if (!isfinite(r)) return PR_EDIVERGED;
-  if (r <= tol) return PR_OK;
-  if (len >= 2 && prec[len - 2] == prec[len - 1]) {
-    const double q = hist[len - 2];
-    const bool low = lowp(prec[len - 1]);
-    const double arm = low ? o.stag_below_lowp : o.stag_below;
-    if (q < arm && r > o.stag_ratio * q) return PR_ESTAGNATED;
-    if (low && r >= q) return PR_ESTAGNATED;  // a low-precision floor, or the iteration leaving its basin
-  }
-  return -1;
+  const bool prev = len >= 2 && prec[len - 2] == prec[len - 1];
+  return stop_rule_last(hist[len - 1], prev, prev ? hist[len - 2] : 0.0, lowp(prec[len - 1]), tol, o);
 }
 
 namespace {

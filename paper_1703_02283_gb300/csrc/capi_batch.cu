@@ -1,11 +1,18 @@
 // Batched solves: many independent problems A_i^{-1/p_i} (SPD matrices of uneven orders and roots) iterated
 // together. Every matrix product stage of an iteration is one launch of the digit-slice tensor-core kernel
-// over the 128 x 128 tiles of all matrices taking part in that stage; the matrices are packed row-wise
-// in shared device buffers with one leading dimension, so one TMA descriptor serves the whole batch.
+// over the 128 x 96 tiles of all matrices taking part in that stage; the matrices are packed row-wise in
+// shared device buffers with one leading dimension, so one TMA descriptor serves the whole batch.
 //
 // Per matrix the iteration, the forms (Newton-Schulz for p = 1, coupled for p >= 2, as in capi.cu), the
-// initial guess of Eq. 3 and the stop rule are those of the single-matrix path. A matrix whose stop rule
-// fires is copied to the result buffer and leaves the work lists.
+// initial guess (Eq. 3 or the scaled identity) and the stop rule are those of the single-matrix path. A
+// matrix whose stop rule fires is copied to the result buffer and leaves the work lists.
+//
+// The whole solve is one CUDA graph, launched once per pr_batch_solve: a prologue (the coupled start
+// M_0 = X_0^p A), then a device-side while loop whose body is two iterations (the FP64 buffers alternate,
+// so two iterations bring them back), then the timing harvest. Every decision between launches (which
+// matrices take part in a stage, their residuals, their stop rules, the loop condition) is taken by the
+// control kernels of k_batch.cu from state kept on the device, so the host neither waits nor builds work
+// lists during the solve. The graph is captured on the first pr_batch_solve and reused.
 #include "pr_internal.h"
 
 #include <math.h>
@@ -13,10 +20,14 @@
 #include <string.h>
 
 #include <algorithm>
+#include <climits>
+#include <numeric>
 #include <string>
 #include <utility>
 #include <vector>
 
+using pr::BatchCtl;
+using pr::BatchStage;
 using pr::EmuBatchMat;
 using pr::Epilogue;
 using pr::Mode;
@@ -30,6 +41,8 @@ struct Buf {  // a packed FP64 buffer and its digit planes
   int* ex = nullptr;
   bool sl_valid = false;
 };
+
+constexpr int kMaxSlots = 64;  // timing slots: product launches per captured graph
 }  // namespace
 
 struct pr_batch_s {
@@ -38,43 +51,49 @@ struct pr_batch_s {
   int R = 0;   // packed rows (sum of the orders)
   int K = 0;   // largest order
   int ld = 0;  // leading dimension of the packed buffers (K rounded up to 8)
+  int pmax = 0;  // largest root of a coupled-form matrix
+  int hcap = 0;  // history entries per matrix (max_iter + 2)
   cudaStream_t stream = nullptr;
   int device = 0;
   pr_options opt{};
   std::vector<int> n, p, row0, form;
-  std::vector<int> order;  // matrices by decreasing order (load balance of the work lists)
   Buf A, X, Xn, M, Mn, N, Nn, T0, T1;
   double* result = nullptr;  // packed results
-  int* row_n = nullptr;      // order of the matrix owning each packed row
+  int* row_n = nullptr;      // order of the matrix owning each packed row (-1 once it stopped)
   double* partial = nullptr;
-  int partial_cap = 0;
-  int4* items = nullptr;
-  int items_cap = 0;
-  std::vector<int4> items_host;
-  EmuBatchMat* mats = nullptr;
-  int* seg = nullptr;  // segment begin[count], end[count]
-  double* res = nullptr;
-  double* hres = nullptr;  // pinned
+  int4* items = nullptr;     // the current stage's work list
   int* err = nullptr;
   long long* scratch = nullptr;  // PR_EMU64 first-pass totals
-  // per matrix
+  // device-side control (k_batch.cu); one allocation per kind
+  int* d_static = nullptr;   // order, n, p, form, row0, off_sym, cnt_sym, off_full, cnt_full
+  int4* d_items_all = nullptr;  // every matrix's symmetric items, then every matrix's full items
+  int* d_state = nullptr;    // active, status, iters, hlen, loops
+  double* d_dstate = nullptr;  // hist (count x hcap), tally[8], params[8]
+  int* d_stage = nullptr;    // nitems, member, ofs, seg_b, seg_e
+  EmuBatchMat* mats = nullptr;
+  unsigned long long* tstamp = nullptr;
+  double* flops_pending = nullptr;
+  BatchCtl ctl{};
+  // host mirrors (pinned) of the state
+  int* h_state = nullptr;
+  double* h_dstate = nullptr;
+  int h_err = 0;
+  // the solve graph
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphConditionalHandle cond = 0;
+  int nslots = 0;
+  int64_t cnt = 0;  // launches recorded by the capture in progress
+  int64_t launches_pro = 0, launches_body = 0, launches_epi = 0;
+  int loops_seen = 0;
+  double tally_seen[3] = {0.0, 0.0, 0.0};
+  // per matrix (host)
   std::vector<std::vector<double>> hist;
-  std::vector<int> active, status, iterations;
+  std::vector<int> status, iterations;
   int64_t launches = 0;
   pr_batch_stats_t st{};
   bool timing = false;
-  // Pinned staging of the per-stage work lists, a ring of slots: a slot is rewritten only after the copy
-  // that read it has completed (its event), so stages need no stream synchronisation.
-  static constexpr int kSlots = 4;
-  int4* h_items[kSlots] = {};
-  EmuBatchMat* h_mats[kSlots] = {};
-  cudaEvent_t slot_ev[kSlots] = {};
-  bool slot_used[kSlots] = {};
-  int slot = 0;
-  // Event pairs around product launches, read at the next synchronisation.
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
-  std::vector<double> ev_flops;
-  size_t ev_pending = 0;
   std::string errmsg;
 };
 
@@ -95,30 +114,15 @@ pr_status bfail(pr_batch b, pr_status code, const std::string& msg) {
                    std::string(#call) + ": " + cudaGetErrorName(_e) + " (" + cudaGetErrorString(_e) + ")"); \
   } while (0)
 
-// Adds the times of the product launches bracketed since the last call (the stream has been synchronised).
-pr_status harvest_timing(pr_batch b) {
-  for (size_t k = 0; k < b->ev_pending; ++k) {
-    float ms = 0.f;
-    PB_CK(b, cudaEventElapsedTime(&ms, b->ev_pool[k].first, b->ev_pool[k].second));
-    b->st.stages_timed += 1;
-    b->st.stage_ms += ms;
-    b->st.stage_flops_timed += b->ev_flops[k];
-  }
-  b->ev_pending = 0;
-  return PR_OK;
-}
-
 pr_status ensure_slices(pr_batch b, Buf& x) {
   if (x.sl_valid) return PR_OK;
   PB_CK(b, pr::slice_rows(x.f, b->R, b->K, b->ld, pr::emu_ld(b->K), b->S, b->row_n, x.sl, x.ex, b->stream));
-  b->launches += 1;
+  b->cnt += 1;
   x.sl_valid = true;
   return PR_OK;
 }
 
-// One stage: P = X Y for every matrix in `who` (indices), with per-matrix epilogue coefficients `coef`
-// (a, b, c). Writes out / out2 (packed), residual partials (if `partial_base` >= 0) and returns, through
-// seg_begin / seg_end (host), the partial range of each matrix.
+// What one stage writes.
 struct StageOut {
   Buf* out = nullptr;
   Buf* out2 = nullptr;
@@ -127,132 +131,185 @@ struct StageOut {
   bool transpose = false;
 };
 
-pr_status stage(pr_batch b, Buf& Xb, Buf& Yb, Mode mode, const std::vector<int>& who,
-                const std::vector<double3>& coef, const StageOut& so, std::vector<int>* seg_begin,
-                std::vector<int>* seg_end) {
-  if (who.empty()) return PR_OK;
+// One stage: P = X Y for every member of `sp` (decided on the device when the stage runs), with the
+// members' epilogue coefficients; residual partials are reduced and appended to the members' histories.
+pr_status stage(pr_batch b, Buf& Xb, Buf& Yb, const BatchStage& sp, const StageOut& so) {
   pr_status s = ensure_slices(b, Xb);
   if (s == PR_OK) s = ensure_slices(b, Yb);
   if (s != PR_OK) return s;
-  std::vector<int> sorted = who;
-  std::sort(sorted.begin(), sorted.end(), [&](int x, int y) { return b->n[x] > b->n[y]; });
-  // The host staging slot: wait until the copy that last read it has completed.
-  const int sl = b->slot;
-  b->slot = (b->slot + 1) % pr_batch_s::kSlots;
-  if (b->slot_used[sl]) PB_CK(b, cudaEventSynchronize(b->slot_ev[sl]));
-  EmuBatchMat* mats = b->h_mats[sl];
-  for (int m = 0; m < b->count; ++m) mats[m] = EmuBatchMat{b->n[m], b->row0[m], 0.0, 0.0, 0.0};
-  const int per = pr::emu_partials_per_item();
-  for (size_t w = 0; w < who.size(); ++w) mats[who[w]] = EmuBatchMat{b->n[who[w]], b->row0[who[w]], coef[w].x, coef[w].y,
-                                                                    coef[w].z};
-  std::vector<int4>& items = b->items_host;
-  items.clear();
-  for (int m : sorted) {
-    if (seg_begin) (*seg_begin)[m] = (int)items.size() * per;
-    pr::emu_tile_list(m, b->n[m], mode, items);
-    if (seg_end) (*seg_end)[m] = (int)items.size() * per;
-  }
-  if ((int)items.size() > b->items_cap) return bfail(b, PR_ECUDA, "pr_batch: work list larger than allocated");
-  std::copy(items.begin(), items.end(), b->h_items[sl]);
-  PB_CK(b, cudaMemcpyAsync(b->items, b->h_items[sl], items.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream));
-  PB_CK(b, cudaMemcpyAsync(b->mats, mats, (size_t)b->count * sizeof(EmuBatchMat), cudaMemcpyHostToDevice, b->stream));
-  PB_CK(b, cudaEventRecord(b->slot_ev[sl], b->stream));
-  b->slot_used[sl] = true;
-  double flops = 0.0;
-  for (int m : who) {
-    const double nm = b->n[m];
-    flops += mode == Mode::Sym ? nm * nm * (nm + 1.0) : 2.0 * nm * nm * nm;
-  }
+  if (b->nslots >= kMaxSlots) return bfail(b, PR_ECUDA, "pr_batch: too many product stages in one graph");
+  BatchStage st = sp;
+  st.slot = b->nslots++;
+  PB_CK(b, pr::batch_stage_list(b->ctl, st, b->stream));
   Epilogue e;
   if (so.out) e.out = so.out->f;
   if (so.out2) e.out2 = so.out2->f;
   e.cin = so.cin;
   e.partial = so.partial ? b->partial : nullptr;
-  if (b->timing) {
-    if (b->ev_pending == b->ev_pool.size()) {
-      cudaEvent_t e0, e1;
-      PB_CK(b, cudaEventCreate(&e0));
-      PB_CK(b, cudaEventCreate(&e1));
-      b->ev_pool.emplace_back(e0, e1);
-      b->ev_flops.push_back(0.0);
-    }
-    PB_CK(b, cudaEventRecord(b->ev_pool[b->ev_pending].first, b->stream));
+  PB_CK(b, pr::gemm_emu_batched(Xb.sl, Xb.ex, Yb.sl, Yb.ex, b->R, b->K, pr::emu_ld(b->K), b->ld, b->S,
+                                st.full ? Mode::Full : Mode::Sym, so.transpose, b->items, 0, b->ctl.nitems, b->mats, e,
+                                b->scratch, b->err, b->tstamp + 2 * st.slot, b->stream));
+  b->cnt += 2;
+  if (so.partial) {
+    PB_CK(b, pr::batch_residuals(b->ctl, b->partial, b->stream));
+    b->cnt += 1;
   }
-  PB_CK(b, pr::gemm_emu_batched(Xb.sl, Xb.ex, Yb.sl, Yb.ex, b->R, b->K, pr::emu_ld(b->K), b->ld, b->S, mode, so.transpose,
-                                b->items, (int)items.size(), b->mats, e, b->scratch, b->err, b->stream));
-  if (b->timing) {
-    PB_CK(b, cudaEventRecord(b->ev_pool[b->ev_pending].second, b->stream));
-    b->ev_flops[b->ev_pending] = flops;
-    b->ev_pending += 1;
-  }
-  b->launches += 1;
-  b->st.stages += 1;
-  b->st.products += (int64_t)who.size();
-  b->st.product_flops += flops;
   if (so.out) so.out->sl_valid = false;
   if (so.out2) so.out2->sl_valid = false;
   return PR_OK;
 }
 
-// Residuals of the matrices in `who` from the partial ranges of the last stage; appended to histories.
-pr_status read_residuals(pr_batch b, const std::vector<int>& who, const std::vector<int>& sb,
-                         const std::vector<int>& se) {
-  if (who.empty()) return PR_OK;
-  std::vector<int> seg(2 * who.size());
-  for (size_t w = 0; w < who.size(); ++w) {
-    seg[w] = sb[who[w]];
-    seg[who.size() + w] = se[who[w]];
-  }
-  PB_CK(b, cudaMemcpyAsync(b->seg, seg.data(), seg.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
-  PB_CK(b, pr::segmented_reduce_sqrt(b->partial, b->seg, b->seg + who.size(), (int)who.size(), b->res, b->stream));
-  b->launches += 1;
-  PB_CK(b, cudaMemcpyAsync(b->hres, b->res, who.size() * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
-  int word = 0;
-  PB_CK(b, cudaMemcpyAsync(&word, b->err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
-  PB_CK(b, cudaStreamSynchronize(b->stream));
-  if (word != 0) {
-    cudaMemsetAsync(b->err, 0, sizeof(int), b->stream);
-    return bfail(b, PR_ETIMEOUT, "pr_batch: a bounded device wait expired");
-  }
-  pr_status hs = harvest_timing(b);
-  if (hs != PR_OK) return hs;
-  for (size_t w = 0; w < who.size(); ++w) b->hist[who[w]].push_back(b->hres[w]);
-  return PR_OK;
+BatchStage spec(int full, int form, int pcmp, int pj, int fresh, double a = 0.0, double bb = 0.0, double c = 0.0) {
+  BatchStage st{};
+  st.full = full;
+  st.form = form;
+  st.pcmp = pcmp;
+  st.pj = pj;
+  st.fresh_only = fresh;
+  st.a = a;
+  st.b = bb;
+  st.c = c;
+  return st;
 }
 
-// Coupled chain for the matrices in `who`: Y_1 = F src0, Y_j = F Y_{j-1}, the p-th product written as
-// (out, out2 = ((p+1) I - out)/p) with residual partials; intermediate products go to T0 / T1.
-pr_status chain(pr_batch b, Buf& F, Buf& src0, Buf& outM, Buf& outN, const std::vector<int>& who,
-                std::vector<int>& sb, std::vector<int>& se) {
-  int pmax = 0;
-  for (int m : who) pmax = std::max(pmax, b->p[m]);
-  for (int j = 1; j <= pmax; ++j) {
+// Coupled chain of the coupled-form members: Y_1 = F src0, Y_j = F Y_{j-1}; the p-th product is written as
+// (out, out2 = ((p+1) I - out)/p) with its residual; intermediate products go to T0 / T1.
+pr_status chain(pr_batch b, Buf& F, Buf& src0, Buf& outM, Buf& outN, int fresh) {
+  for (int j = 1; j <= b->pmax; ++j) {
     Buf& src = j == 1 ? src0 : ((j - 1) & 1 ? b->T0 : b->T1);
-    std::vector<int> fin, mid;
-    std::vector<double3> cf, cm;
-    for (int m : who) {
-      if (b->p[m] == j) {
-        fin.push_back(m);
-        cf.push_back(make_double3((double)(j + 1) / j, -1.0 / j, 0.0));
-      } else if (b->p[m] > j) {
-        mid.push_back(m);
-        cm.push_back(make_double3(0.0, 0.0, 0.0));
-      }
-    }
     StageOut om;
     om.out = (j & 1) ? &b->T0 : &b->T1;
-    pr_status s = stage(b, F, src, Mode::Sym, mid, cm, om, nullptr, nullptr);
+    pr_status s = stage(b, F, src, spec(0, PR_FORM_COUPLED, 2, j, fresh), om);
     if (s != PR_OK) return s;
     StageOut of;
     of.out = &outM;
     of.out2 = &outN;
     of.partial = true;
-    s = stage(b, F, src, Mode::Sym, fin, cf, of, &sb, &se);
-    if (s != PR_OK) return s;
-    s = read_residuals(b, fin, sb, se);
+    s = stage(b, F, src, spec(0, PR_FORM_COUPLED, 1, j, fresh, (double)(j + 1) / j, -1.0 / j, 0.0), of);
     if (s != PR_OK) return s;
   }
   return PR_OK;
+}
+
+// One iteration of every iterating matrix: the Newton-Schulz residuals, the stop rules, the updates
+// (Newton-Schulz X' = 2X - X T; coupled X' = X N, M' = N^p M with N' and r'), then the buffer swap.
+pr_status iteration(pr_batch b, bool last) {
+  StageOut o;
+  o.out = &b->T0;
+  o.partial = true;
+  o.transpose = true;
+  pr_status s = stage(b, b->A, b->X, spec(1, PR_FORM_NS, 0, 0, 0), o);
+  if (s != PR_OK) return s;
+  PB_CK(b, pr::batch_decide(b->ctl, b->X.f, b->opt, b->stream));
+  b->cnt += 1;
+  StageOut u;
+  u.out2 = &b->Xn;
+  u.cin = b->X.f;
+  s = stage(b, b->X, b->T0, spec(0, PR_FORM_NS, 0, 0, 0, 0.0, -1.0, 2.0), u);
+  if (s != PR_OK) return s;
+  StageOut x;
+  x.out = &b->Xn;
+  s = stage(b, b->X, b->N, spec(0, PR_FORM_COUPLED, 0, 0, 0), x);
+  if (s == PR_OK) s = chain(b, b->N, b->M, b->Mn, b->Nn, 0);
+  if (s != PR_OK) return s;
+  std::swap(b->X, b->Xn);
+  std::swap(b->M, b->Mn);
+  std::swap(b->N, b->Nn);
+  PB_CK(b, pr::batch_advance(b->ctl, b->cond, last ? 1 : 0, b->opt.max_iter + 4, b->stream));
+  b->cnt += 1;
+  return PR_OK;
+}
+
+void invalidate_slices(pr_batch b) {
+  for (Buf* x : {&b->A, &b->X, &b->Xn, &b->M, &b->Mn, &b->N, &b->Nn, &b->T0, &b->T1}) x->sl_valid = false;
+}
+
+// Captures the solve graph (prologue, while loop of two iterations, harvest) on a private stream.
+pr_status build_graph(pr_batch b) {
+  PB_CK(b, pr::emu_prepare());
+  if (!b->cap) PB_CK(b, cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+  PB_CK(b, cudaGraphCreate(&b->graph, 0));
+  PB_CK(b, cudaGraphConditionalHandleCreate(&b->cond, b->graph, 1, cudaGraphCondAssignDefault));
+  cudaStream_t user = b->stream;
+  b->stream = b->cap;
+  b->nslots = 0;
+  auto capture = [&](cudaGraph_t g, const cudaGraphNode_t* dep, size_t ndep, auto&& body) -> pr_status {
+    cudaError_t e = cudaStreamBeginCaptureToGraph(b->cap, g, dep, nullptr, ndep, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return bfail(b, PR_ECUDA, std::string("pr_batch: capture: ") + cudaGetErrorName(e));
+    b->cnt = 0;
+    pr_status s = body();
+    cudaGraph_t out = nullptr;
+    e = cudaStreamEndCapture(b->cap, &out);
+    if (s == PR_OK && e != cudaSuccess) s = bfail(b, PR_ECUDA, std::string("pr_batch: capture: ") + cudaGetErrorName(e));
+    return s;
+  };
+  // Prologue: the coupled start M_0 = X_0^p A, N_0, r_0 of every matrix without a residual yet.
+  invalidate_slices(b);
+  pr_status s = capture(b->graph, nullptr, 0, [&]() {
+    pr_status r = ensure_slices(b, b->A);
+    return r == PR_OK ? chain(b, b->X, b->A, b->M, b->N, 1) : r;
+  });
+  b->launches_pro = b->cnt;
+  // The prologue is one chain of nodes: the while loop follows its last node.
+  cudaGraphNode_t sink = nullptr;
+  if (s == PR_OK) {
+    size_t nn = 0;
+    cudaError_t e = cudaGraphGetNodes(b->graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (e == cudaSuccess) e = cudaGraphGetNodes(b->graph, nodes.data(), &nn);
+    for (size_t i = 0; e == cudaSuccess && i < nn; ++i) {
+      size_t nd = 0;
+      e = cudaGraphNodeGetDependentNodes(nodes[i], nullptr, nullptr, &nd);
+      if (e == cudaSuccess && nd == 0) {
+        if (sink) e = cudaErrorInvalidValue;  // more than one last node
+        sink = nodes[i];
+      }
+    }
+    if (e != cudaSuccess || !sink) s = bfail(b, PR_ECUDA, "pr_batch: prologue graph has no single last node");
+  }
+  cudaGraphNode_t loop = nullptr;
+  cudaGraph_t body = nullptr;
+  if (s == PR_OK) {
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = b->cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaError_t e = cudaGraphAddNode(&loop, b->graph, &sink, nullptr, 1, &cp);
+    if (e != cudaSuccess) s = bfail(b, PR_ECUDA, std::string("pr_batch: loop node: ") + cudaGetErrorName(e));
+    else body = cp.conditional.phGraph_out[0];
+  }
+  // Loop body: two iterations. At its entry only A's digit planes are known to be current.
+  if (s == PR_OK) {
+    invalidate_slices(b);
+    b->A.sl_valid = true;
+    s = capture(body, nullptr, 0, [&]() {
+      pr_status r = iteration(b, false);
+      return r == PR_OK ? iteration(b, true) : r;
+    });
+    b->launches_body = b->cnt;
+  }
+  if (s == PR_OK) {
+    s = capture(b->graph, &loop, 1, [&]() -> pr_status {
+      PB_CK(b, pr::batch_harvest(b->ctl, b->nslots, b->stream));
+      b->cnt += 1;
+      return PR_OK;
+    });
+    b->launches_epi = b->cnt;
+  }
+  if (s == PR_OK) {
+    cudaError_t e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) s = bfail(b, PR_ECUDA, std::string("pr_batch: instantiate: ") + cudaGetErrorName(e));
+  }
+  b->stream = user;
+  invalidate_slices(b);
+  if (s != PR_OK) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+  }
+  return s;
 }
 
 }  // namespace
@@ -263,24 +320,20 @@ pr_status pr_batch_destroy(pr_batch b) {
   if (!b) return PR_OK;
   cudaSetDevice(b->device);
   if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->cap) cudaStreamDestroy(b->cap);
   for (Buf* x : {&b->A, &b->X, &b->Xn, &b->M, &b->Mn, &b->N, &b->Nn, &b->T0, &b->T1}) {
     if (x->f) cudaFree(x->f);
     if (x->sl) cudaFree(x->sl);
     if (x->ex) cudaFree(x->ex);
   }
-  for (void* q : {(void*)b->result, (void*)b->row_n, (void*)b->partial, (void*)b->items, (void*)b->mats, (void*)b->seg,
-                  (void*)b->res, (void*)b->err, (void*)b->scratch})
+  for (void* q : {(void*)b->result, (void*)b->row_n, (void*)b->partial, (void*)b->items, (void*)b->err,
+                  (void*)b->scratch, (void*)b->d_static, (void*)b->d_items_all, (void*)b->d_state, (void*)b->d_dstate,
+                  (void*)b->d_stage, (void*)b->mats, (void*)b->tstamp, (void*)b->flops_pending})
     if (q) cudaFree(q);
-  if (b->hres) cudaFreeHost(b->hres);
-  for (int k = 0; k < pr_batch_s::kSlots; ++k) {
-    if (b->h_items[k]) cudaFreeHost(b->h_items[k]);
-    if (b->h_mats[k]) cudaFreeHost(b->h_mats[k]);
-    if (b->slot_ev[k]) cudaEventDestroy(b->slot_ev[k]);
-  }
-  for (auto& pr_ : b->ev_pool) {
-    cudaEventDestroy(pr_.first);
-    cudaEventDestroy(pr_.second);
-  }
+  if (b->h_state) cudaFreeHost(b->h_state);
+  if (b->h_dstate) cudaFreeHost(b->h_dstate);
   delete b;
   return PR_OK;
 }
@@ -320,15 +373,16 @@ pr_status pr_batch_init(pr_batch* out, int count, const int64_t* n, const int* p
   b->row0.resize(count);
   b->form.resize(count);
   b->hist.resize(count);
-  b->active.assign(count, 1);
   b->status.assign(count, -1);
   b->iterations.assign(count, 0);
+  b->hcap = o.max_iter + 2;
   int row = 0;
   for (int m = 0; m < count; ++m) {
     b->n[m] = (int)n[m];
     b->p[m] = p[m];
     b->row0[m] = row;
     b->form[m] = p[m] == 1 ? PR_FORM_NS : PR_FORM_COUPLED;
+    if (p[m] > 1) b->pmax = std::max(b->pmax, p[m]);
     row += (int)n[m];
   }
   auto bail = [&](pr_status code) {
@@ -354,24 +408,98 @@ pr_status pr_batch_init(pr_batch* out, int count, const int64_t* n, const int* p
   }
   PB_INIT_CK(cudaMalloc((void**)&b->result, fbytes));
   PB_INIT_CK(cudaMalloc((void**)&b->row_n, (size_t)b->R * sizeof(int)));
-  int64_t items = 0;
-  for (int m = 0; m < count; ++m) items += pr::emu_tile_count((int)n[m], Mode::Full);
-  b->items_cap = (int)items;
-  b->partial_cap = (int)(items * pr::emu_partials_per_item());
-  PB_INIT_CK(cudaMalloc((void**)&b->items, (size_t)items * sizeof(int4)));
-  for (int k = 0; k < pr_batch_s::kSlots; ++k) {
-    PB_INIT_CK(cudaMallocHost((void**)&b->h_items[k], (size_t)items * sizeof(int4)));
-    PB_INIT_CK(cudaMallocHost((void**)&b->h_mats[k], (size_t)count * sizeof(EmuBatchMat)));
-    PB_INIT_CK(cudaEventCreateWithFlags(&b->slot_ev[k], cudaEventDisableTiming));
+  // Every matrix's work items (symmetric and full) and the device-side control state.
+  std::vector<int4> isym, ifull;
+  std::vector<int> stat(9 * (size_t)count);
+  int* s_order = stat.data();
+  std::iota(s_order, s_order + count, 0);
+  std::stable_sort(s_order, s_order + count, [&](int x, int y) { return b->n[x] > b->n[y]; });
+  for (int m = 0; m < count; ++m) {
+    stat[count + m] = b->n[m];
+    stat[2 * count + m] = b->p[m];
+    stat[3 * count + m] = b->form[m];
+    stat[4 * count + m] = b->row0[m];
+    stat[5 * count + m] = (int)isym.size();
+    pr::emu_tile_list(m, b->n[m], Mode::Sym, isym);
+    stat[6 * count + m] = (int)isym.size() - stat[5 * count + m];
+    stat[7 * count + m] = (int)ifull.size();
+    pr::emu_tile_list(m, b->n[m], Mode::Full, ifull);
+    stat[8 * count + m] = (int)ifull.size() - stat[7 * count + m];
   }
-  PB_INIT_CK(cudaMalloc((void**)&b->partial, (size_t)b->partial_cap * sizeof(double)));
+  const size_t items = ifull.size();  // no stage has more items than every matrix's full product
+  const size_t hist_len = (size_t)count * b->hcap;
+  PB_INIT_CK(cudaMalloc((void**)&b->items, items * sizeof(int4)));
+  PB_INIT_CK(cudaMalloc((void**)&b->partial, items * pr::emu_partials_per_item() * sizeof(double)));
   PB_INIT_CK(cudaMalloc((void**)&b->mats, (size_t)count * sizeof(EmuBatchMat)));
-  PB_INIT_CK(cudaMalloc((void**)&b->seg, (size_t)2 * count * sizeof(int)));
-  PB_INIT_CK(cudaMalloc((void**)&b->res, (size_t)count * sizeof(double)));
   PB_INIT_CK(cudaMalloc((void**)&b->err, sizeof(int)));
   PB_INIT_CK(cudaMalloc((void**)&b->scratch, pr::emu_scratch_bytes()));
   PB_INIT_CK(cudaMemsetAsync(b->err, 0, sizeof(int), b->stream));
-  PB_INIT_CK(cudaMallocHost((void**)&b->hres, (size_t)count * sizeof(double)));
+  PB_INIT_CK(cudaMalloc((void**)&b->d_static, stat.size() * sizeof(int)));
+  PB_INIT_CK(cudaMalloc((void**)&b->d_items_all, (isym.size() + ifull.size()) * sizeof(int4)));
+  PB_INIT_CK(cudaMalloc((void**)&b->d_state, (4 * (size_t)count + 1) * sizeof(int)));
+  PB_INIT_CK(cudaMalloc((void**)&b->d_dstate, (hist_len + 16) * sizeof(double)));
+  PB_INIT_CK(cudaMalloc((void**)&b->d_stage, (1 + 4 * (size_t)count) * sizeof(int)));
+  PB_INIT_CK(cudaMalloc((void**)&b->tstamp, 2 * kMaxSlots * sizeof(unsigned long long)));
+  PB_INIT_CK(cudaMalloc((void**)&b->flops_pending, kMaxSlots * sizeof(double)));
+  PB_INIT_CK(cudaMallocHost((void**)&b->h_state, (4 * (size_t)count + 1) * sizeof(int)));
+  PB_INIT_CK(cudaMallocHost((void**)&b->h_dstate, (hist_len + 16) * sizeof(double)));
+  {
+    std::vector<int> st0(4 * (size_t)count + 1, 0);
+    std::fill(st0.begin(), st0.begin() + count, 1);               // active
+    std::fill(st0.begin() + count, st0.begin() + 2 * count, -1);  // status
+    std::vector<unsigned long long> ts(2 * kMaxSlots);
+    for (int k = 0; k < kMaxSlots; ++k) {
+      ts[2 * k] = ULLONG_MAX;
+      ts[2 * k + 1] = 0ull;
+    }
+    PB_INIT_CK(cudaMemcpy(b->d_static, stat.data(), stat.size() * sizeof(int), cudaMemcpyHostToDevice));
+    PB_INIT_CK(cudaMemcpy(b->d_items_all, isym.data(), isym.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    PB_INIT_CK(cudaMemcpy(b->d_items_all + isym.size(), ifull.data(), ifull.size() * sizeof(int4),
+                          cudaMemcpyHostToDevice));
+    PB_INIT_CK(cudaMemcpy(b->d_state, st0.data(), st0.size() * sizeof(int), cudaMemcpyHostToDevice));
+    PB_INIT_CK(cudaMemset(b->d_dstate, 0, (hist_len + 16) * sizeof(double)));
+    PB_INIT_CK(cudaMemcpy(b->tstamp, ts.data(), ts.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice));
+    PB_INIT_CK(cudaMemset(b->flops_pending, 0, kMaxSlots * sizeof(double)));
+  }
+  {
+    BatchCtl& c = b->ctl;
+    const int* d = b->d_static;
+    c.count = count;
+    c.hcap = b->hcap;
+    c.per = pr::emu_partials_per_item();
+    c.ld = b->ld;
+    c.order = d;
+    c.n = d + count;
+    c.p = d + 2 * count;
+    c.form = d + 3 * count;
+    c.row0 = d + 4 * count;
+    c.off_sym = d + 5 * count;
+    c.cnt_sym = d + 6 * count;
+    c.off_full = d + 7 * count;
+    c.cnt_full = d + 8 * count;
+    c.items_sym = b->d_items_all;
+    c.items_full = b->d_items_all + isym.size();
+    c.active = b->d_state;
+    c.status = b->d_state + count;
+    c.iters = b->d_state + 2 * count;
+    c.hlen = b->d_state + 3 * count;
+    c.loops = b->d_state + 4 * count;
+    c.hist = b->d_dstate;
+    c.tally = b->d_dstate + hist_len;
+    c.params = b->d_dstate + hist_len + 8;
+    c.items = b->items;
+    c.nitems = b->d_stage;
+    c.mats = b->mats;
+    c.member = b->d_stage + 1;
+    c.ofs = b->d_stage + 1 + count;
+    c.seg_b = b->d_stage + 1 + 2 * count;
+    c.seg_e = b->d_stage + 1 + 3 * count;
+    c.tstamp = b->tstamp;
+    c.flops_pending = b->flops_pending;
+    c.result = b->result;
+    c.row_n = b->row_n;
+    c.err = b->err;
+  }
   {
     std::vector<int> rn(b->R);
     for (int m = 0; m < count; ++m)
@@ -445,86 +573,47 @@ pr_status pr_batch_solve(pr_batch b, int precision, double tol, int* iterations,
   if (precision != PR_EMU64) return bfail(b, PR_EUNSUPPORTED, "pr_batch_solve: batches run PR_EMU64 products");
   if (!(tol >= 0)) return bfail(b, PR_EINVAL, "pr_batch_solve: tol < 0");
   cudaSetDevice(b->device);
-  const int count = b->count;
-  std::vector<int> sb(count, 0), se(count, 0);
-  std::vector<int> ns, cp;  // active Newton-Schulz and coupled matrices
-  for (int m = 0; m < count; ++m)
-    if (b->active[m]) (b->form[m] == PR_FORM_NS ? ns : cp).push_back(m);
-  // Coupled start: M_0 = X_0^p A, N_0 and r_0 (once).
-  pr_status s = PR_OK;
-  bool fresh = true;
-  for (int m : cp) fresh = fresh && b->hist[m].empty();
-  if (!cp.empty() && fresh) {
-    s = chain(b, b->X, b->A, b->M, b->N, cp, sb, se);
+  if (!b->exec) {
+    pr_status s = build_graph(b);
     if (s != PR_OK) return s;
   }
-  std::vector<int> prec_hist;
-  while (!ns.empty() || !cp.empty()) {
-    // Newton-Schulz residual of the current iterate: T = A X (stored transposed), ||I - T||_F.
-    if (!ns.empty()) {
-      StageOut o;
-      o.out = &b->T0;
-      o.partial = true;
-      o.transpose = true;
-      s = stage(b, b->A, b->X, Mode::Full, ns, std::vector<double3>(ns.size(), make_double3(0, 0, 0)), o, &sb, &se);
-      if (s == PR_OK) s = read_residuals(b, ns, sb, se);
-      if (s != PR_OK) return s;
-    }
-    // Stop decisions; stopped matrices are copied out and leave the lists.
-    std::vector<int> ns2, cp2;
-    for (int pass = 0; pass < 2; ++pass) {
-      const std::vector<int>& lst = pass == 0 ? ns : cp;
-      for (int m : lst) {
-        const std::vector<double>& h = b->hist[m];
-        prec_hist.assign(h.size(), PR_EMU64);
-        int stop = pr::stop_rule(h.data(), prec_hist.data(), (int)h.size(), tol, b->opt);
-        if (stop < 0 && b->iterations[m] >= b->opt.max_iter) stop = PR_EMAXITER;
-        if (stop >= 0) {
-          b->status[m] = stop;
-          b->active[m] = 0;
-          const size_t off = (size_t)b->row0[m] * b->ld;
-          PB_CK(b, cudaMemcpyAsync(b->result + off, b->X.f + off, (size_t)b->n[m] * b->ld * sizeof(double),
-                                   cudaMemcpyDeviceToDevice, b->stream));
-          // Its rows are no longer sliced (row order -1).
-          PB_CK(b, cudaMemsetAsync(b->row_n + b->row0[m], 0xFF, (size_t)b->n[m] * sizeof(int), b->stream));
-        } else {
-          (pass == 0 ? ns2 : cp2).push_back(m);
-        }
-      }
-    }
-    ns.swap(ns2);
-    cp.swap(cp2);
-    if (ns.empty() && cp.empty()) break;
-    // Updates. Newton-Schulz: X' = 2X - X T. Coupled: X' = X N; M' = N^p M with N' and r'.
-    {
-      StageOut o;
-      o.out2 = &b->Xn;
-      o.cin = b->X.f;
-      s = stage(b, b->X, b->T0, Mode::Sym, ns, std::vector<double3>(ns.size(), make_double3(0.0, -1.0, 2.0)), o,
-                nullptr, nullptr);
-      if (s != PR_OK) return s;
-    }
-    {
-      StageOut o;
-      o.out = &b->Xn;
-      s = stage(b, b->X, b->N, Mode::Sym, cp, std::vector<double3>(cp.size(), make_double3(0, 0, 0)), o, nullptr,
-                nullptr);
-      if (s == PR_OK && !cp.empty()) s = chain(b, b->N, b->M, b->Mn, b->Nn, cp, sb, se);
-      if (s != PR_OK) return s;
-    }
-    // Every matrix still active advanced; buffers of stopped matrices are no longer read.
-    std::swap(b->X, b->Xn);
-    std::swap(b->M, b->Mn);
-    std::swap(b->N, b->Nn);
-    for (int m : ns) b->iterations[m] += 1;
-    for (int m : cp) b->iterations[m] += 1;
-  }
+  const int count = b->count;
+  const size_t hist_len = (size_t)count * b->hcap;
+  b->h_dstate[hist_len + 8] = tol;
+  PB_CK(b, cudaMemcpyAsync(b->d_dstate + hist_len + 8, b->h_dstate + hist_len + 8, sizeof(double),
+                           cudaMemcpyHostToDevice, b->stream));
+  PB_CK(b, cudaGraphLaunch(b->exec, b->stream));
+  PB_CK(b, cudaMemcpyAsync(b->h_state, b->d_state, (4 * (size_t)count + 1) * sizeof(int), cudaMemcpyDeviceToHost,
+                           b->stream));
+  PB_CK(b, cudaMemcpyAsync(b->h_dstate, b->d_dstate, (hist_len + 8) * sizeof(double), cudaMemcpyDeviceToHost,
+                           b->stream));
+  PB_CK(b, cudaMemcpyAsync(&b->h_err, b->err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
   PB_CK(b, cudaStreamSynchronize(b->stream));
-  s = harvest_timing(b);
-  if (s != PR_OK) return s;
+  // Launches: the prologue and the harvest once, the loop body once per pass.
+  const int loops = b->h_state[4 * count];
+  b->launches += b->launches_pro + (int64_t)(loops - b->loops_seen) * b->launches_body + b->launches_epi;
+  b->loops_seen = loops;
+  const double* tally = b->h_dstate + hist_len;
+  b->st.stages = (int64_t)tally[3];
+  b->st.products = (int64_t)tally[4];
+  b->st.product_flops = tally[5];
+  if (b->timing) {
+    b->st.stage_ms += (tally[0] - b->tally_seen[0]) * 1e-6;
+    b->st.stage_flops_timed += tally[1] - b->tally_seen[1];
+    b->st.stages_timed += (int64_t)(tally[2] - b->tally_seen[2]);
+  }
+  for (int k = 0; k < 3; ++k) b->tally_seen[k] = tally[k];
   for (int m = 0; m < count; ++m) {
+    b->status[m] = b->h_state[count + m];
+    b->iterations[m] = b->h_state[2 * count + m];
+    const int len = b->h_state[3 * count + m];
+    b->hist[m].assign(b->h_dstate + (size_t)m * b->hcap, b->h_dstate + (size_t)m * b->hcap + len);
     if (iterations) iterations[m] = b->iterations[m];
     if (status) status[m] = b->status[m];
+  }
+  if (b->h_err != 0) {
+    cudaMemsetAsync(b->err, 0, sizeof(int), b->stream);
+    return bfail(b, PR_ETIMEOUT, "pr_batch: a bounded device wait expired");
   }
   return PR_OK;
 }
@@ -563,7 +652,6 @@ pr_status pr_batch_stats(pr_batch b, pr_batch_stats_t* out) {
 
 pr_status pr_batch_set_timing(pr_batch b, int on) {
   if (!b) return bfail(nullptr, PR_ESTATE, "pr_batch_set_timing: NULL batch");
-  cudaSetDevice(b->device);
   b->timing = on != 0;
   return PR_OK;
 }

@@ -138,32 +138,18 @@ __global__ void k_symmetrize(const double* __restrict__ in, int n, double* __res
 }
 
 __global__ void k_reduce_sqrt(const double* __restrict__ partial, int count, double* __restrict__ result) {
-  __shared__ double sh[kThreads];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < count; i += kThreads) s += partial[i];
-  sh[threadIdx.x] = s;
-  __syncthreads();
-  for (int w = kThreads / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *result = sqrt(sh[0]);
+  __shared__ double sh[kReduceThreads];
+  const double r = block_sum_sqrt(partial, count, sh);
+  if (threadIdx.x == 0) *result = r;
 }
 
 // One block per segment: out[m] = sqrt(sum partial[begin[m]..end[m])) in a fixed order.
 __global__ void k_seg_reduce_sqrt(const double* __restrict__ partial, const int* __restrict__ begin,
                                   const int* __restrict__ end, double* __restrict__ out) {
-  __shared__ double sh[kThreads];
+  __shared__ double sh[kReduceThreads];
   const int m = blockIdx.x;
-  double s = 0.0;
-  for (int i = begin[m] + threadIdx.x; i < end[m]; i += kThreads) s += partial[i];
-  sh[threadIdx.x] = s;
-  __syncthreads();
-  for (int w = kThreads / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) out[m] = sqrt(sh[0]);
+  const double r = block_sum_sqrt(partial + begin[m], end[m] - begin[m], sh);
+  if (threadIdx.x == 0) out[m] = r;
 }
 
 __global__ void k_to_bf16(const double* __restrict__ src, int n, int ldl, __nv_bfloat16* __restrict__ dst) {
@@ -220,14 +206,14 @@ cudaError_t symmetrize(const double* in, int n, double* out, cudaStream_t s) {
 }
 
 cudaError_t reduce_partials_sqrt(const double* partial, int count, double* result, cudaStream_t s) {
-  k_reduce_sqrt<<<1, kThreads, 0, s>>>(partial, count, result);
+  k_reduce_sqrt<<<1, kReduceThreads, 0, s>>>(partial, count, result);
   return cudaGetLastError();
 }
 
 cudaError_t segmented_reduce_sqrt(const double* partial, const int* begin, const int* end, int count, double* out,
                                   cudaStream_t s) {
   if (count < 1) return cudaSuccess;
-  k_seg_reduce_sqrt<<<count, kThreads, 0, s>>>(partial, begin, end, out);
+  k_seg_reduce_sqrt<<<count, kReduceThreads, 0, s>>>(partial, begin, end, out);
   return cudaGetLastError();
 }
 

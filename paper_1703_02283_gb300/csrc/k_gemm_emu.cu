@@ -159,6 +159,7 @@ struct EmuArgs {
   int S;                 // digit planes per operand
   int ld;                // leading dimension of the FP64 outputs and of cin
   int ntiles;            // work items
+  const int* ntiles_dev; // if set, the number of work items is read here (written by an earlier kernel)
   const int4* items;     // (matrix, tile row, tile column, -) per work item
   const EmuMat* mats;    // per-matrix data; null: every item belongs to `one`
   EmuMat one;
@@ -168,6 +169,7 @@ struct EmuArgs {
   const int* ey;         // row exponents of Y
   long long* scratch;    // SCRATCH_PER_CTA int64 per CTA: the first pass's exact totals
   int* err;
+  unsigned long long* tstamp;  // if set: [0] min over CTAs of the start time, [1] max of the end time (ns)
 };
 
 __device__ __forceinline__ const EmuMat& item_of(const EmuArgs& a, int t, int& bi, int& bj) {
@@ -242,6 +244,9 @@ __device__ __forceinline__ bool drains_after(int a, int j) { return ((j + 2 * a)
 template <bool SYM>
 __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (5 warps per sub-partition)
     k_gemm_emu(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, EmuArgs args) {
+  const int ntiles = args.ntiles_dev ? *args.ntiles_dev : args.ntiles;
+  if ((int)blockIdx.x >= ntiles) return;  // no work for this CTA (uniform over the block)
+  if (args.tstamp && threadIdx.x == 0) atomicMin(&args.tstamp[0], (unsigned long long)ptx::globaltimer());
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* ring = smem;
@@ -285,7 +290,7 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
       // ---------------- TMA producer: per step, the plane groups of X (128 rows) and of Y (96 rows)
       int it = 0;
       bool stop = false;
-      for (int t = blockIdx.x; t < args.ntiles && !stop; t += gridDim.x) {
+      for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
         int bi, bj;
         const EmuMat& mt = item_of(args, t, bi, bj);
         const int KS = (mt.n + EBK - 1) / EBK, ya = mt.row0 + bi * EBM, yb = mt.row0 + bj * EBN;
@@ -318,7 +323,7 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
       // the MMAs of two steps back (the last readers of that buffer) have finished.
       int it = 0;
       bool stop = false;
-      for (int t = blockIdx.x; t < args.ntiles && !stop; t += gridDim.x) {
+      for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
         int bi, bj;
         const EmuMat& mt = item_of(args, t, bi, bj);
         const int KS = (mt.n + EBK - 1) / EBK;
@@ -352,7 +357,7 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
       uint32_t fresh = 3u, drained = 0u, par = 0u;  // per own accumulator k (a = k == 0 ? 3 - w : w)
       int it = 0;
       bool stop = false;
-      for (int t = blockIdx.x; t < args.ntiles && !stop; t += gridDim.x) {
+      for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
         int bi, bj;
         const EmuMat& mt = item_of(args, t, bi, bj);
         const int KS = (mt.n + EBK - 1) / EBK;
@@ -421,7 +426,7 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
     long long* scr = args.scratch + (size_t)blockIdx.x * SCRATCH_PER_CTA + (size_t)(ew * 32 + lane);
     uint32_t epar = 0u;  // per accumulator: parity of the drains taken so far
     bool stop = false;
-    for (int t = blockIdx.x; t < args.ntiles && !stop; t += gridDim.x) {
+    for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
       int bi, bj;
       const EmuMat& mt = item_of(args, t, bi, bj);
       const int n = mt.n, row0 = mt.row0, KS = (n + EBK - 1) / EBK;
@@ -519,6 +524,7 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
   __syncthreads();
   ptx::tc_fence_after();
   if (warp == 0) ptx::tmem_dealloc(tmem, 512);
+  if (args.tstamp && threadIdx.x == 0) atomicMax(&args.tstamp[1], (unsigned long long)ptx::globaltimer());
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn_emu() {
@@ -560,10 +566,7 @@ int sm_count_emu() {
   return count;
 }
 
-cudaError_t launch_emu(const __half* DX, const __half* DY, int R, int K, int ldl, Mode mode, EmuArgs& a,
-                       cudaStream_t s) {
-  if (a.S < 1 || a.S > SMAX || ldl % 16 != 0 || ldl < K || K < 1 || !a.items || !a.scratch) return cudaErrorInvalidValue;
-  if ((reinterpret_cast<uintptr_t>(DX) | reinterpret_cast<uintptr_t>(DY)) & 15) return cudaErrorMisalignedAddress;
+cudaError_t prepare_emu() {
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t r = cudaFuncSetAttribute(k_gemm_emu<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
@@ -572,13 +575,24 @@ cudaError_t launch_emu(const __half* DX, const __half* DY, int R, int K, int ldl
     if (r != cudaSuccess) return r;
     attr_set = true;
   }
-  if (a.ntiles == 0) return cudaSuccess;
+  if (!encode_fn_emu()) return cudaErrorNotSupported;
+  sm_count_emu();
+  return cudaSuccess;
+}
+
+cudaError_t launch_emu(const __half* DX, const __half* DY, int R, int K, int ldl, Mode mode, EmuArgs& a,
+                       cudaStream_t s) {
+  if (a.S < 1 || a.S > SMAX || ldl % 16 != 0 || ldl < K || K < 1 || !a.items || !a.scratch) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(DX) | reinterpret_cast<uintptr_t>(DY)) & 15) return cudaErrorMisalignedAddress;
+  cudaError_t pr_ = prepare_emu();
+  if (pr_ != cudaSuccess) return pr_;
+  if (a.ntiles == 0 && !a.ntiles_dev) return cudaSuccess;
   CUtensorMap mx, my;
   cudaError_t r = make_plane_map(&mx, DX, R, ldl, EBM);
   if (r != cudaSuccess) return r;
   r = make_plane_map(&my, DY, R, ldl, EBN);
   if (r != cudaSuccess) return r;
-  const int grid = a.ntiles < sm_count_emu() ? a.ntiles : sm_count_emu();
+  const int grid = a.ntiles_dev || a.ntiles >= sm_count_emu() ? sm_count_emu() : a.ntiles;
   if (mode == Mode::Sym) {
     k_gemm_emu<true><<<grid, THREADS, SMEM_BYTES, s>>>(mx, my, a);
   } else {
@@ -625,6 +639,8 @@ cudaError_t slice_rows(const double* X, int R, int n, int ldx, int ldl, int S, c
   return cudaGetLastError();
 }
 
+cudaError_t emu_prepare() { return prepare_emu(); }
+
 size_t emu_scratch_bytes() { return (size_t)sm_count_emu() * SCRATCH_PER_CTA * sizeof(long long); }
 
 cudaError_t gemm_emu(const __half* DX, const int* ex, const __half* DY, const int* ey, int n, int ldl, int S, Mode mode,
@@ -648,13 +664,16 @@ cudaError_t gemm_emu(const __half* DX, const int* ex, const __half* DY, const in
 
 cudaError_t gemm_emu_batched(const __half* DX, const int* ex, const __half* DY, const int* ey, int R, int K, int ldl,
                              int ld, int S, Mode mode, bool transpose, const int4* items, int nitems,
-                             const EmuBatchMat* mats, const Epilogue& e, long long* scratch, int* err, cudaStream_t s) {
+                             const int* nitems_dev, const EmuBatchMat* mats, const Epilogue& e, long long* scratch,
+                             int* err, unsigned long long* tstamp, cudaStream_t s) {
   static_assert(sizeof(EmuBatchMat) == sizeof(EmuMat), "batch matrix record");
   EmuArgs a{};
   a.scratch = scratch;
   a.S = S;
   a.ld = ld;
   a.ntiles = nitems;
+  a.ntiles_dev = nitems_dev;
+  a.tstamp = tstamp;
   a.items = items;
   a.mats = reinterpret_cast<const EmuMat*>(mats);
   a.transpose = transpose ? 1 : 0;

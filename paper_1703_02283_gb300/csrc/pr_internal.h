@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <math.h>
 #include <stdint.h>
 
 #include <vector>
@@ -88,6 +89,7 @@ int emu_partials_per_item();
 int emu_max_slices();
 int emu_ld(int K);  // the K extent of a digit-plane row: K rounded up to 16
 size_t emu_scratch_bytes();  // device scratch each gemm_emu / gemm_emu_batched call needs (per stream)
+cudaError_t emu_prepare();   // one-time kernel attributes and driver entry points (before a graph capture)
 cudaError_t slice(const double* X, int n, int ldl, int S, __half* D, int* ex, cudaStream_t s);
 // Slices R rows of an FP64 array with leading dimension ldx; row r has row_n[r] valid columns (n if null).
 cudaError_t slice_rows(const double* X, int R, int n, int ldx, int ldl, int S, const int* row_n, __half* D, int* ex,
@@ -98,14 +100,17 @@ cudaError_t gemm_emu(const __half* DX, const int* ex, const __half* DY, const in
 
 // A batch of matrices packed row-wise in shared buffers (leading dimension ld for FP64, ldl for digit
 // planes; R packed rows per plane; K the largest order). Work items from emu_tile_list per matrix;
-// per-matrix record = {order, first packed row, epilogue a, b, c}.
+// per-matrix record = {order, first packed row, epilogue a, b, c}. nitems_dev (if set): the number of
+// items is read on the device (the launch is one persistent CTA per SM). tstamp (if set): the kernel
+// folds its start and end times (ns, %globaltimer) into tstamp[0] (min) and tstamp[1] (max).
 struct EmuBatchMat {
   int n, row0;
   double a, b, c;
 };
 cudaError_t gemm_emu_batched(const __half* DX, const int* ex, const __half* DY, const int* ey, int R, int K, int ldl,
                              int ld, int S, Mode mode, bool transpose, const int4* items, int nitems,
-                             const EmuBatchMat* mats, const Epilogue& e, long long* scratch, int* err, cudaStream_t s);
+                             const int* nitems_dev, const EmuBatchMat* mats, const Epilogue& e, long long* scratch,
+                             int* err, unsigned long long* tstamp, cudaStream_t s);
 
 // ---- elementwise and reductions (k_elementwise.cu)
 // scal[0] = max |a_ij|, scal[1] = max |a_ij - a_ji|, scal[2] = #non-finite, scal[3] = #non-positive diagonal
@@ -142,12 +147,98 @@ cudaError_t mlp_backward(const float* theta, const float* X, const float* T, con
                          const float* H2, int B, float* gpart, float* lpart, float* grad, float* loss, float* m,
                          float* v, float* theta_rw, float lr, float c1, float c2, bool adam, cudaStream_t s);
 
+// sqrt(sum of v[0 .. count)) on a block of kReduceThreads threads, in one fixed order: thread t adds v[t],
+// v[t + T], ... and the T partial sums meet in a pairwise tree. Every reduction of residual partials uses
+// it, so that a batched solve reproduces the single-matrix path bit for bit. sh: T doubles of shared memory.
+constexpr int kReduceThreads = 256;
+__device__ inline double block_sum_sqrt(const double* v, int count, double* sh) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < count; i += kReduceThreads) s += v[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kReduceThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  return sqrt(sh[0]);
+}
+
 // out[m] = sqrt(sum of partial[begin[m] .. end[m])) for m < count, each sum in a fixed order.
 cudaError_t segmented_reduce_sqrt(const double* partial, const int* begin, const int* end, int count, double* out,
                                   cudaStream_t s);
 
-// The stop rule of pr_iterate (capi.cu), shared with the batched solver.
+// The stop rule of pr_iterate on the newest residual r of a history: prev says that the residual before it,
+// q, was taken at the same precision; low that the precision is a low one (PR_BF16). Returns a pr_status
+// to stop with, or -1 to apply one more update. (Host and device: the batched solver decides on the GPU.)
+__host__ __device__ inline int stop_rule_last(double r, bool prev, double q, bool low, double tol,
+                                              const pr_options& o) {
+  if (!isfinite(r)) return PR_EDIVERGED;
+  if (r <= tol) return PR_OK;
+  if (prev) {
+    const double arm = low ? o.stag_below_lowp : o.stag_below;
+    if (q < arm && r > o.stag_ratio * q) return PR_ESTAGNATED;
+    if (low && r >= q) return PR_ESTAGNATED;  // a low-precision floor, or the iteration leaving its basin
+  }
+  return -1;
+}
+// The same rule on a whole history with its per-entry precisions (capi.cu).
 int stop_rule(const double* hist, const int* prec, int len, double tol, const pr_options& o);
+
+// ---- device-side control of batched solves (k_batch.cu)
+// All state of a batch that the solve loop reads or changes lives on the device, so that the whole loop
+// runs as one graph: the kernels below build each product stage's work list from the matrices' states,
+// append residuals to the histories, apply every matrix's stop rule and set the loop condition.
+struct BatchCtl {
+  int count;  // matrices
+  int hcap;   // history entries per matrix
+  int per;    // residual partials per work item
+  int ld;     // leading dimension of the packed FP64 buffers
+  // static description
+  const int* order;                      // matrices by decreasing order
+  const int *n, *p, *form, *row0;        // per matrix
+  const int *off_sym, *cnt_sym, *off_full, *cnt_full;  // per matrix: its items in items_sym / items_full
+  const int4 *items_sym, *items_full;    // every matrix's work items (emu_tile_list), symmetric and full
+  // state
+  int *active, *status, *iters, *hlen;   // per matrix (status -1: running)
+  int* loops;                            // solve-loop passes so far
+  double* hist;                          // count x hcap residual histories
+  double* tally;                         // [0] timed ns, [1] timed flops, [2] timed launches,
+                                         // [3] non-empty product launches, [4] products, [5] product flops
+  const double* params;                  // [0] tolerance
+  // the current stage
+  int4* items;                           // its work list
+  int* nitems;
+  EmuBatchMat* mats;                     // its per-matrix records
+  int *seg_b, *seg_e, *member, *ofs;     // per matrix: residual partial range, membership, first item
+  // timing slots of the product launches (2 timestamps and the flops of the last launch per slot)
+  unsigned long long* tstamp;
+  double* flops_pending;
+  // results
+  double* result;
+  int* row_n;
+  const int* err;
+};
+// Membership of a product stage: matrices of one form that are still iterating, optionally with p == pj
+// (pcmp 1) or p > pj (pcmp 2), optionally only those without a residual yet (fresh_only).
+struct BatchStage {
+  int full;         // 0: symmetric-mode work items, 1: full
+  int form;         // PR_FORM_NS or PR_FORM_COUPLED
+  int pcmp, pj;
+  int fresh_only;
+  int slot;         // timing slot of the product launch
+  double a, b, c;   // epilogue coefficients of the members
+};
+cudaError_t batch_stage_list(const BatchCtl& c, const BatchStage& st, cudaStream_t s);
+// Residual of every member of the last stage from its partials, appended to its history.
+cudaError_t batch_residuals(const BatchCtl& c, const double* partial, cudaStream_t s);
+// The stop rule for every iterating matrix; a stopping matrix's rows of X go to the results and leave
+// the digit slicing (row order -1).
+cudaError_t batch_decide(const BatchCtl& c, const double* X, const pr_options& o, cudaStream_t s);
+// Counts one update for every iterating matrix; with set_cond, sets the loop condition of the solve graph:
+// some matrix still iterating, no device wait expired and fewer than `limit` passes.
+cudaError_t batch_advance(const BatchCtl& c, cudaGraphConditionalHandle h, int set_cond, int limit, cudaStream_t s);
+// Adds the last launch of every timing slot to the tally.
+cudaError_t batch_harvest(const BatchCtl& c, int nslots, cudaStream_t s);
 
 // Records the text returned by pr_last_error(NULL) for a failing call that has no handle.
 void set_handleless_error(const char* msg);

@@ -15,6 +15,7 @@ Recipes (all seeded with ``numpy.random.default_rng``):
 * ``overlap_points`` / ``overlap_matrix``: an overlap-type SPD matrix ``S_ij = exp(-|r_i - r_j| / ell)``
   for points uniform in a cube, standing in for the H2O overlap matrices of Sec. 4.1 (unit diagonal,
   entries in (0, 1], decaying with distance), which are not available.
+* ``spd_from_spectrum_device``: the same recipe built on the GPU by torch, for the order-16384 case.
 * ``batched_specs``: sizes, condition numbers and roots of a batch of independent problems.
 """
 from __future__ import annotations
@@ -70,6 +71,39 @@ def spd_from_spectrum(n: int, lam_min: float, seed: int) -> SpdCase:
     A = (Q * lam) @ Q.T
     A = 0.5 * (A + A.T)
     return SpdCase(A=np.ascontiguousarray(A), Q=Q, lam=lam, seed=seed)
+
+
+@dataclass
+class DeviceSpdCase:
+    """An SPD matrix built on the device, for orders where the host QR takes minutes."""
+
+    A: object  # (n, n) torch.float64 CUDA tensor, symmetric positive definite
+    Q: object  # (n, n) torch.float64 CUDA tensor, orthogonal
+    lam: np.ndarray  # (n,) float64 eigenvalues (host)
+    seed: int
+
+
+def spd_from_spectrum_device(n: int, lam_min: float, seed: int, device) -> DeviceSpdCase:
+    """The ``spd_from_spectrum`` recipe with the normal matrix, its QR factorisation and the product
+    ``Q diag(lam) Q^T`` taken on the device by torch (its normal generator seeded with ``seed``,
+    cuSOLVER, cuBLAS). The spectrum is the host recipe's, from ``numpy.random.default_rng(seed)``.
+    Same distributions as ``spd_from_spectrum``; not the same matrix."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    G = torch.randn((n, n), dtype=torch.float64, device=device, generator=g)
+    Q, R = torch.linalg.qr(G)
+    d = torch.sign(torch.diagonal(R))
+    d[d == 0] = 1.0
+    del G, R
+    Q.mul_(d)
+    lam = log_uniform_spectrum(np.random.default_rng(seed), n, lam_min)
+    A = (Q * torch.from_numpy(lam).to(device)) @ Q.T
+    At = A.T.contiguous()
+    A.add_(At).mul_(0.5)
+    del At
+    return DeviceSpdCase(A=A, Q=Q, lam=lam, seed=seed)
 
 
 # The fixed workloads. Sizes and spectra follow the benchmark recipes: a small plain-FP64 case that the

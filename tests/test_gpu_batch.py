@@ -2,7 +2,8 @@
 
 Each matrix of a batch must meet the single-matrix bar against the CPU oracle, and its result must equal,
 bit for bit, the single-matrix PR_EMU64 solve of the same matrix (same digit planes, same tiles, same
-stop rule).
+stop rule): the batch's work lists, residuals and stop decisions, taken on the device inside one graph,
+must reproduce what the single-matrix path decides on the host.
 """
 import numpy as np
 import pytest
@@ -27,9 +28,11 @@ def make_batch(count, n_lo, n_hi, kappa_hi, seed):
     return cases, [int(x) for x in spec.p]
 
 
-def single_emu(case, p, c0=P.PR_C0_EQ3):
+def single_emu(case, p, c0=P.PR_C0_EQ3, max_iter=None):
     o = P.pr_default_options()
     o.c0 = c0
+    if max_iter is not None:
+        o.max_iter = max_iter
     A = torch.from_numpy(case.A).to(DEV)
     h = P.pr_init(A, case.n, p, o, torch.cuda.current_stream(DEV).cuda_stream)
     try:
@@ -41,18 +44,32 @@ def single_emu(case, p, c0=P.PR_C0_EQ3):
         P.pr_destroy(h)
 
 
-def run_batch(cases, ps, host=False, c0=P.PR_C0_EQ3):
+def run_batch(cases, ps, host=False, c0=P.PR_C0_EQ3, max_iter=None, repeat=False):
     o = P.pr_default_options()
     o.c0 = c0
+    if max_iter is not None:
+        o.max_iter = max_iter
     mats = [np.ascontiguousarray(c.A) if host else torch.from_numpy(c.A).to(DEV) for c in cases]
     b = P.pr_batch_init(mats, ps, o, torch.cuda.current_stream(DEV).cuda_stream)
     try:
         its, sts = P.pr_batch_solve(b, len(cases), P.PR_EMU64, 1e-12)
-        out = []
-        for i, c in enumerate(cases):
-            C = np.empty((c.n, c.n))
-            P.pr_batch_result(b, i, C)
-            out.append((C, P.pr_batch_history(b, i)))
+
+        def results():
+            out = []
+            for i, c in enumerate(cases):
+                C = np.empty((c.n, c.n))
+                P.pr_batch_result(b, i, C)
+                out.append((C, P.pr_batch_history(b, i)))
+            return out
+
+        out = results()
+        if repeat:
+            # A second solve after every matrix stopped runs the graph once more and changes nothing.
+            launches = P.pr_batch_launches(b)
+            assert P.pr_batch_solve(b, len(cases), P.PR_EMU64, 1e-12) == (its, sts)
+            assert P.pr_batch_launches(b) > launches
+            for (C, h), (C2, h2) in zip(out, results()):
+                assert np.array_equal(C, C2) and h == h2
         return out, its, sts, P.pr_batch_launches(b)
     finally:
         P.pr_batch_destroy(b)
@@ -96,6 +113,30 @@ def test_batch_single_matrix_and_errors():
     with pytest.raises(P.PthrootError) as e:
         P.pr_batch_init([bad], [2])
     assert e.value.status == P.PR_EINVAL
+
+
+def test_batch_more_matrices_than_one_control_block():
+    # 1100 matrices of orders 1..24: the work-list scan runs over two chunks of 1024 matrices. Sampled
+    # results equal the single-matrix path bit for bit, and a repeated solve changes nothing.
+    cases, ps = make_batch(1100, 1, 24, 1e2, 5)
+    out, its, sts, _ = run_batch(cases, ps, repeat=True)
+    assert all(s in (P.PR_OK, P.PR_ESTAGNATED) for s in sts)
+    for i in list(range(0, 1100, 97)) + [1099]:
+        Cs, hs = single_emu(cases[i], ps[i])
+        assert np.array_equal(out[i][0], Cs), (i, cases[i].n, ps[i])
+        assert out[i][1] == hs
+
+
+def test_batch_max_iter_stops_every_matrix():
+    # A cap of 3 updates: every matrix stops with PR_EMAXITER after 3 iterations (4 residuals), at the
+    # iterate the single-matrix path with the same cap returns.
+    cases, ps = make_batch(8, 50, 260, 1e3, 21)
+    out, its, sts, _ = run_batch(cases, ps, max_iter=3)
+    assert its == [3] * 8 and sts == [P.PR_EMAXITER] * 8
+    for i, (case, p) in enumerate(zip(cases, ps)):
+        assert len(out[i][1]) == 4
+        Cs, hs = single_emu(case, p, max_iter=3)
+        assert np.array_equal(out[i][0], Cs) and out[i][1] == hs
 
 
 @pytest.mark.slow

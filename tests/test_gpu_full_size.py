@@ -1,0 +1,156 @@
+"""Solves at the full workload sizes, through the C ABI.
+
+* The order-4096 single-matrix recipe (kappa = 1e3, p = 1..4, Eq. 3's C_0) in the launch configuration
+  the benchmark times: BF16 Newton-Schulz then EMU64 for p = 1, EMU64 for p >= 2.
+* Order-4096 instances of the large recipe (kappa = 1e4, p = 2) from the scaled identity.
+* The order-16384 large case itself, built on the device.
+
+The order-4096 results are compared with the oracle's own solves of the same recipes
+(tests/golden/oracle_n4096.json, written by tests/golden/make_oracle_n4096.py from oracle/ only) and with
+the closed form. The order-16384 result is checked on a sampled block of the closed form, sampled rows of
+its residual and its whole residual history against the scalar model of Eq. 1.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import pthroot_oracle as O
+from paper_1703_02283_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1703_02283_gb300 import pthroot as P  # noqa: E402
+
+DEV = torch.device("cuda:0")
+with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_n4096.json")) as _f:
+    GOLD = json.load(_f)
+
+
+def gold(lam_min, seed, p, c0):
+    for g in GOLD["cases"]:
+        if g["lam_min"] == lam_min and g["seed"] == seed and g["p"] == p and g["c0"] == c0:
+            return g
+    raise KeyError((lam_min, seed, p, c0))
+
+
+def stream():
+    return torch.cuda.current_stream(DEV).cuda_stream
+
+
+def solve(A, n, p, bulk, bulk_steps, final, tol, c0=P.PR_C0_EQ3):
+    o = P.pr_default_options()
+    o.c0 = c0
+    h = P.pr_init(A, n, p, o, stream())
+    try:
+        st, steps = P.pr_solve(h, bulk, bulk_steps, final, tol)
+        res = P.pr_residual(h, final)
+        C = torch.empty((n, n), dtype=torch.float64, device=DEV)
+        P.pr_result(h, C)
+        info = dict(status=st, steps=steps, residual=res, history=P.pr_history(h), stats=P.pr_stats(h))
+    finally:
+        P.pr_destroy(h)
+    return C, info
+
+
+def check_against_gold(C, info, g, Z):
+    # Forward error within max(1e-12, 10 x the oracle's own) (the parity bar for FP64 ends), and the
+    # sampled block of the oracle's result within the same bar.
+    bar = max(1e-12, 10 * g["forward_error"])
+    fe = O.forward_error(C, Z)
+    assert fe <= bar, (fe, g["forward_error"])
+    idx = np.asarray(g["block_indices"])
+    blk, want = C[np.ix_(idx, idx)], np.asarray(g["block"])
+    assert np.linalg.norm(blk - want) <= 2 * bar * np.linalg.norm(want)
+    return fe
+
+
+@pytest.fixture(scope="module")
+def single_case():
+    c = W.spd_from_spectrum(4096, 1e-3, 1)
+    return c, torch.from_numpy(c.A).to(DEV)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_single_recipe_n4096_against_oracle(single_case, p):
+    c, A = single_case
+    g = gold(1e-3, 1, p, "eq3")
+    if p == 1:
+        C, info = solve(A, 4096, 1, P.PR_BF16, 100, P.PR_EMU64, g["tol"])
+    else:
+        C, info = solve(A, 4096, p, P.PR_EMU64, 0, P.PR_EMU64, g["tol"])
+    C = C.cpu().numpy()
+    assert info["status"] == P.PR_OK
+    check_against_gold(C, info, g, O.closed_form_root(c.Q, c.lam, p))
+    if p == 1:
+        # The BF16 phase hands over to EMU64 Newton-Schulz, which corrects it (X' - Z = -E A E).
+        by = info["stats"]["iterations_by_precision"]
+        assert by[P.PR_BF16] > 0 and by[P.PR_EMU64] > 0
+        assert info["steps"] <= g["iterations"] + 3
+    else:
+        # Same form, start and stop rule as the oracle: about the same iteration count, and the same
+        # residual history while nearly every eigenvalue of M is still far from 1. (Later the two differ by
+        # more than rounding: Eq. 3's M_0 spans kappa^(p+1), so its smallest eigenvalues carry relative
+        # errors up to u kappa^(p+1) that decide when each of them converges.)
+        assert abs(info["steps"] - g["iterations"]) <= 3
+        hg = np.asarray(g["residuals"])
+        k = np.nonzero(hg > 0.5 * np.sqrt(4096))[0]
+        assert len(k) >= 3
+        np.testing.assert_allclose(np.asarray(info["history"])[k], hg[k], rtol=1e-8)
+    # The true residual of the result, with EMU64 products: at most what the oracle's result has.
+    assert info["residual"] <= max(g["tol"], 10 * g["true_residual"])
+
+
+@pytest.mark.parametrize("seed", [20, 21])
+def test_large_recipe_n4096_instances_against_oracle(seed):
+    c = W.spd_from_spectrum(4096, 1e-4, seed)
+    g = gold(1e-4, seed, 2, "scaled_identity")
+    A = torch.from_numpy(c.A).to(DEV)
+    C, info = solve(A, 4096, 2, P.PR_EMU64, 0, P.PR_EMU64, g["tol"], c0=P.PR_C0_SCALED_I)
+    assert info["status"] == P.PR_OK and info["stats"]["c0"] == P.PR_C0_SCALED_I
+    fe = check_against_gold(C.cpu().numpy(), info, g, O.closed_form_root(c.Q, c.lam, 2))
+    assert fe <= 1e-10  # the large recipe's accuracy bar
+    assert abs(info["steps"] - g["iterations"]) <= 2
+    # The scaled identity's M_0 spans only kappa: the histories agree down to far below 1.
+    hg = np.asarray(g["residuals"])
+    k = np.nonzero(hg > 1e-4)[0]
+    np.testing.assert_allclose(np.asarray(info["history"])[k], hg[k], rtol=1e-6)
+
+
+@pytest.mark.slow
+def test_large_case_n16384():
+    n, p, tol = 16384, 2, 1e-12
+    case = W.spd_from_spectrum_device(n, 1e-4, 2, DEV)
+    C, info = solve(case.A, n, p, P.PR_EMU64, 0, P.PR_EMU64, tol, c0=P.PR_C0_SCALED_I)
+    assert info["status"] == P.PR_OK
+    rng = np.random.default_rng(16384)
+    I = np.sort(rng.choice(n, 64, replace=False))
+    J = np.sort(rng.choice(n, 64, replace=False))
+    QI, QJ, lam = case.Q[I].cpu().numpy(), case.Q[J].cpu().numpy(), case.lam
+    Ah = case.A.cpu().numpy()
+    del case
+    Ch = C.cpu().numpy()
+    del C
+    # Closed form, entry by entry, on a block around the diagonal and an off-diagonal block.
+    for cols, Qc in ((I, QI), (J, QJ)):
+        Z = O.closed_form_block(QI, Qc, lam, p)
+        assert np.linalg.norm(Ch[np.ix_(I, cols)] - Z) <= 1e-10 * np.linalg.norm(Z)
+    # Every residual of the history against the scalar model of Eq. 1 from the same C_0, while far above
+    # rounding, and the iteration count the model needs to reach the rounding level.
+    c0 = np.full(n, O.norm_1(Ah) ** (-1.0 / p))
+    model = O.scalar_residuals(lam, c0, p, info["steps"] + 5)
+    hist = np.asarray(info["history"])
+    k = np.nonzero(model[: len(hist)] > 1e-4)[0]
+    np.testing.assert_allclose(hist[k], model[k], rtol=1e-6)
+    k_conv = int(np.nonzero(model <= 1e-10)[0][0])
+    assert k_conv - 1 <= info["steps"] <= k_conv + 3
+    # Sampled rows of I - C^2 A on the host, scaled to a Frobenius estimate, and the library's true
+    # residual: both at the rounding level of an FP64 result (far below the 1e-4 the model tracks above).
+    rows = O.residual_rows(Ch, Ah, p, I)
+    est = np.sqrt(np.sum(rows ** 2) * n / len(I))
+    assert 0 < est <= 1e-8 and 0 < info["residual"] <= 1e-8

@@ -103,6 +103,26 @@ def test_limit_matches_closed_form_and_lapack(p):
         assert O.residual_fro(Z, c.A, p) < 1e-12
 
 
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_closed_form_block_and_residual_rows(p):
+    # Entry-wise closed form: on every row pair it is an inverse p-th root (Z^p A = I, Z symmetric) and
+    # the inverse itself for p = 1; a block of it is the same block of the full root.
+    c = _case(40, 5e-2, 13)
+    Z = O.closed_form_block(c.Q, c.Q, c.lam, p)
+    assert np.linalg.norm(np.linalg.matrix_power(Z, p) @ c.A - np.eye(40)) < 1e-11
+    assert np.array_equal(Z, Z.T) or np.abs(Z - Z.T).max() < 1e-13
+    if p == 1:
+        np.testing.assert_allclose(Z, np.linalg.inv(c.A), rtol=1e-11, atol=1e-12)
+    rows, cols = np.array([3, 17, 39]), np.array([0, 17, 22, 5])
+    np.testing.assert_allclose(O.closed_form_block(c.Q[rows], c.Q[cols], c.lam, p), Z[np.ix_(rows, cols)],
+                               rtol=1e-13, atol=1e-15)
+    # Residual rows: zero (to rounding) at the root, e_i - (row i of C^p) A in general, here for C = A
+    # (rows of I - A^{p+1}, formed independently by matrix_power).
+    assert np.abs(O.residual_rows(Z, c.A, p, rows)).max() < 1e-12
+    want = (np.eye(40) - np.linalg.matrix_power(c.A, p + 1))[rows]
+    np.testing.assert_allclose(O.residual_rows(c.A, c.A, p, rows), want, rtol=1e-12, atol=1e-14)
+
+
 def test_p1_is_the_inverse():
     c = _case(64, 1e-2, 5)
     C, info = O.solve(c.A, 1, tol=1e-13)
