@@ -28,6 +28,10 @@ if not torch.cuda.is_available():
 from paper_1703_02283_gb300 import pthroot as P  # noqa: E402
 
 DEV = torch.device("cuda:0")
+# The library's residuals come from FP32 partial sums of the squared FP64 residual entries (per lane 24
+# terms, then a 32-lane tree per partial; the partials are added in FP64): relative error below
+# (24 + 5) 2^-24 / 2 < 2e-6 in r.
+RES_RTOL = 2e-6
 with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_n4096.json")) as _f:
     GOLD = json.load(_f)
 
@@ -101,7 +105,7 @@ def test_single_recipe_n4096_against_oracle(single_case, p):
         hg = np.asarray(g["residuals"])
         k = np.nonzero(hg > 0.5 * np.sqrt(4096))[0]
         assert len(k) >= 3
-        np.testing.assert_allclose(np.asarray(info["history"])[k], hg[k], rtol=1e-8)
+        np.testing.assert_allclose(np.asarray(info["history"])[k], hg[k], rtol=RES_RTOL)
     # The true residual of the result, with EMU64 products: at most what the oracle's result has.
     assert info["residual"] <= max(GOLD["tol"], 10 * g["true_residual"])
 
@@ -119,7 +123,7 @@ def test_large_recipe_n4096_instances_against_oracle(seed):
     # The scaled identity's M_0 spans only kappa: the histories agree down to far below 1.
     hg = np.asarray(g["residuals"])
     k = np.nonzero(hg > 1e-4)[0]
-    np.testing.assert_allclose(np.asarray(info["history"])[k], hg[k], rtol=1e-6)
+    np.testing.assert_allclose(np.asarray(info["history"])[k], hg[k], rtol=RES_RTOL)
 
 
 @pytest.mark.slow
@@ -146,7 +150,7 @@ def test_large_case_n16384():
     model = O.scalar_residuals(lam, c0, p, info["steps"] + 5)
     hist = np.asarray(info["history"])
     k = np.nonzero(model[: len(hist)] > 1e-4)[0]
-    np.testing.assert_allclose(hist[k], model[k], rtol=1e-6)
+    np.testing.assert_allclose(hist[k], model[k], rtol=RES_RTOL)
     k_conv = int(np.nonzero(model <= 1e-10)[0][0])
     assert k_conv - 1 <= info["steps"] <= k_conv + 3
     # Sampled rows of I - C^2 A on the host, scaled to a Frobenius estimate, and the library's true
