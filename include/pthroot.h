@@ -226,6 +226,11 @@ typedef struct pr_batch_s* pr_batch;
 pr_status pr_batch_init(pr_batch* b, int count, const int64_t* n, const int* p, const double* const* A,
                         const pr_options* opt, void* stream);
 
+/* Replaces the batch's matrices by A[0..count) of the same orders (device or host, copied; checked as
+ * pr_batch_init checks them) and restarts every matrix from its initial guess. Keeps the device memory and
+ * the captured solve graph. Errors: PR_ESTATE (b NULL), PR_EINVAL, PR_ENOTSPD, PR_ECUDA. */
+pr_status pr_batch_load(pr_batch b, const double* const* A);
+
 /* Iterates every active matrix until its stop rule fires (tol, stagnation, max_iter, divergence), with
  * PR_EMU64 products. iterations[i] and status[i] (a pr_status stop code; may be NULL) receive the outcome
  * per matrix. The first call captures the solve graph (on a private stream); every call launches it once

@@ -74,6 +74,8 @@ struct pr_batch_s {
   unsigned long long* tstamp = nullptr;
   double* flops_pending = nullptr;
   BatchCtl ctl{};
+  // loading: an n x n work area, per-matrix checks and norms (device and pinned host)
+  double *tA = nullptr, *tC = nullptr, *scal = nullptr, *work = nullptr, *hs = nullptr;
   // host mirrors (pinned) of the state
   int* h_state = nullptr;
   double* h_dstate = nullptr;
@@ -312,6 +314,74 @@ pr_status build_graph(pr_batch b) {
   return s;
 }
 
+// Copies the matrices in (device or host), checks them as pr_init does, forms the norms of Eq. 3 and C_0,
+// and resets every matrix to "iterating, no residual yet". The solve graph (if captured) stays valid.
+pr_status load(pr_batch b, const double* const* A, const char* who) {
+  const int count = b->count;
+  for (int m = 0; m < count; ++m)
+    if (!A[m]) return bfail(b, PR_EINVAL, std::string(who) + ": NULL matrix");
+  {
+    std::vector<int> rn(b->R);
+    for (int m = 0; m < count; ++m)
+      for (int r = 0; r < b->n[m]; ++r) rn[b->row0[m] + r] = b->n[m];
+    std::vector<int> st0(4 * (size_t)count, 0);
+    std::fill(st0.begin(), st0.begin() + count, 1);               // active
+    std::fill(st0.begin() + count, st0.begin() + 2 * count, -1);  // status
+    PB_CK(b, cudaMemcpyAsync(b->row_n, rn.data(), rn.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    PB_CK(b, cudaMemcpyAsync(b->d_state, st0.data(), st0.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    PB_CK(b, cudaStreamSynchronize(b->stream));
+  }
+  for (int m = 0; m < count; ++m) {
+    b->status[m] = -1;
+    b->iterations[m] = 0;
+    b->hist[m].clear();
+  }
+  // Per matrix: checks and the norms of Eq. 3 (all matrices queued, one read-back), then C_0; staged
+  // through an n x n work area on the batch's stream, without waiting between matrices.
+  cudaError_t e = cudaSuccess;
+  for (int m = 0; m < count && e == cudaSuccess; ++m) {
+    const int nm = b->n[m];
+    const size_t pitch = (size_t)b->ld * sizeof(double), w = (size_t)nm * sizeof(double);
+    e = cudaMemcpyAsync(b->tA, A[m], (size_t)nm * nm * sizeof(double), cudaMemcpyDefault, b->stream);
+    if (e == cudaSuccess) e = pr::validate(b->tA, nm, b->scal + 8 * m, b->stream);
+    if (e == cudaSuccess) e = pr::abs_norms(b->tA, nm, b->work, b->scal + 8 * m + 4, b->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(b->A.f + (size_t)b->row0[m] * b->ld, pitch, b->tA, w, w, nm, cudaMemcpyDeviceToDevice,
+                            b->stream);
+    b->launches += 4;
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->hs, b->scal, 8 * (size_t)count * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bfail(b, PR_ECUDA, std::string(who) + ": " + cudaGetErrorName(e));
+  for (int m = 0; m < count; ++m) {
+    const double* h = b->hs + 8 * m;
+    if (h[2] > 0 || h[1] > b->opt.sym_tol * h[0])
+      return bfail(b, PR_EINVAL, std::string(who) + ": matrix " + std::to_string(m) + " is not finite and symmetric");
+    if (h[3] > 0)
+      return bfail(b, PR_ENOTSPD, std::string(who) + ": matrix " + std::to_string(m) + " has a non-positive diagonal");
+  }
+  for (int m = 0; m < count && e == cudaSuccess; ++m) {
+    const int nm = b->n[m];
+    const double* h = b->hs + 8 * m;
+    const size_t pitch = (size_t)b->ld * sizeof(double), w = (size_t)nm * sizeof(double);
+    if (b->opt.c0 == PR_C0_EQ3) {
+      e = cudaMemcpy2DAsync(b->tA, w, b->A.f + (size_t)b->row0[m] * b->ld, pitch, w, nm, cudaMemcpyDeviceToDevice,
+                            b->stream);
+      if (e == cudaSuccess) e = pr::init_c0_eq3(b->tA, nm, 1.0 / (h[4] * h[5]), b->tC, b->stream);
+    } else {
+      e = pr::set_scaled_identity(b->tC, nm, pow(h[4], -1.0 / b->p[m]), b->stream);
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(b->X.f + (size_t)b->row0[m] * b->ld, pitch, b->tC, w, w, nm, cudaMemcpyDeviceToDevice,
+                            b->stream);
+    b->launches += 1;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bfail(b, PR_ECUDA, std::string(who) + ": " + cudaGetErrorName(e));
+  return PR_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -330,8 +400,10 @@ pr_status pr_batch_destroy(pr_batch b) {
   }
   for (void* q : {(void*)b->result, (void*)b->row_n, (void*)b->partial, (void*)b->items, (void*)b->err,
                   (void*)b->scratch, (void*)b->d_static, (void*)b->d_items_all, (void*)b->d_state, (void*)b->d_dstate,
-                  (void*)b->d_stage, (void*)b->mats, (void*)b->tstamp, (void*)b->flops_pending})
+                  (void*)b->d_stage, (void*)b->mats, (void*)b->tstamp, (void*)b->flops_pending, (void*)b->tA,
+                  (void*)b->tC, (void*)b->scal, (void*)b->work})
     if (q) cudaFree(q);
+  if (b->hs) cudaFreeHost(b->hs);
   if (b->h_state) cudaFreeHost(b->h_state);
   if (b->h_dstate) cudaFreeHost(b->h_dstate);
   delete b;
@@ -500,72 +572,23 @@ pr_status pr_batch_init(pr_batch* out, int count, const int64_t* n, const int* p
     c.row_n = b->row_n;
     c.err = b->err;
   }
-  {
-    std::vector<int> rn(b->R);
-    for (int m = 0; m < count; ++m)
-      for (int r = 0; r < b->n[m]; ++r) rn[b->row0[m] + r] = b->n[m];
-    PB_INIT_CK(cudaMemcpyAsync(b->row_n, rn.data(), rn.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
-    PB_INIT_CK(cudaStreamSynchronize(b->stream));
-  }
-  // Per matrix: checks and the norms of Eq. 3 (all matrices queued, one read-back), then C_0; staged
-  // through an n x n work area on the batch's stream, without waiting between matrices.
-  double *tA = nullptr, *tC = nullptr, *scal = nullptr, *work = nullptr, *hs = nullptr;
-  PB_INIT_CK(cudaMalloc((void**)&tA, (size_t)K * K * sizeof(double)));
-  PB_INIT_CK(cudaMalloc((void**)&tC, (size_t)K * K * sizeof(double)));
-  PB_INIT_CK(cudaMalloc((void**)&scal, 8 * (size_t)count * sizeof(double)));
-  PB_INIT_CK(cudaMalloc((void**)&work, 2 * (size_t)K * sizeof(double)));
-  PB_INIT_CK(cudaMallocHost((void**)&hs, 8 * (size_t)count * sizeof(double)));
-  pr_status st = PR_OK;
-  cudaError_t e = cudaSuccess;
-  for (int m = 0; m < count && e == cudaSuccess; ++m) {
-    const int nm = b->n[m];
-    const size_t pitch = (size_t)b->ld * sizeof(double), w = (size_t)nm * sizeof(double);
-    e = cudaMemcpyAsync(tA, A[m], (size_t)nm * nm * sizeof(double), cudaMemcpyDefault, b->stream);
-    if (e == cudaSuccess) e = pr::validate(tA, nm, scal + 8 * m, b->stream);
-    if (e == cudaSuccess) e = pr::abs_norms(tA, nm, work, scal + 8 * m + 4, b->stream);
-    if (e == cudaSuccess)
-      e = cudaMemcpy2DAsync(b->A.f + (size_t)b->row0[m] * b->ld, pitch, tA, w, w, nm, cudaMemcpyDeviceToDevice,
-                            b->stream);
-    b->launches += 4;
-  }
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(hs, scal, 8 * (size_t)count * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-  if (e != cudaSuccess) st = bfail(b, PR_ECUDA, std::string("pr_batch_init: ") + cudaGetErrorName(e));
-  for (int m = 0; m < count && st == PR_OK; ++m) {
-    const double* h = hs + 8 * m;
-    if (h[2] > 0 || h[1] > o.sym_tol * h[0])
-      st = bfail(b, PR_EINVAL, "pr_batch_init: matrix " + std::to_string(m) + " is not finite and symmetric");
-    else if (h[3] > 0)
-      st = bfail(b, PR_ENOTSPD, "pr_batch_init: matrix " + std::to_string(m) + " has a non-positive diagonal");
-  }
-  for (int m = 0; m < count && st == PR_OK && e == cudaSuccess; ++m) {
-    const int nm = b->n[m];
-    const double* h = hs + 8 * m;
-    const size_t pitch = (size_t)b->ld * sizeof(double), w = (size_t)nm * sizeof(double);
-    if (o.c0 == PR_C0_EQ3) {
-      e = cudaMemcpy2DAsync(tA, w, b->A.f + (size_t)b->row0[m] * b->ld, pitch, w, nm, cudaMemcpyDeviceToDevice,
-                            b->stream);
-      if (e == cudaSuccess) e = pr::init_c0_eq3(tA, nm, 1.0 / (h[4] * h[5]), tC, b->stream);
-    } else {
-      e = pr::set_scaled_identity(tC, nm, pow(h[4], -1.0 / p[m]), b->stream);
-    }
-    if (e == cudaSuccess)
-      e = cudaMemcpy2DAsync(b->X.f + (size_t)b->row0[m] * b->ld, pitch, tC, w, w, nm, cudaMemcpyDeviceToDevice,
-                            b->stream);
-    b->launches += 1;
-  }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-  if (st == PR_OK && e != cudaSuccess) st = bfail(b, PR_ECUDA, std::string("pr_batch_init: ") + cudaGetErrorName(e));
-  cudaFree(tA);
-  cudaFree(tC);
-  cudaFree(scal);
-  cudaFree(work);
-  cudaFreeHost(hs);
+  PB_INIT_CK(cudaMalloc((void**)&b->tA, (size_t)K * K * sizeof(double)));
+  PB_INIT_CK(cudaMalloc((void**)&b->tC, (size_t)K * K * sizeof(double)));
+  PB_INIT_CK(cudaMalloc((void**)&b->scal, 8 * (size_t)count * sizeof(double)));
+  PB_INIT_CK(cudaMalloc((void**)&b->work, 2 * (size_t)K * sizeof(double)));
+  PB_INIT_CK(cudaMallocHost((void**)&b->hs, 8 * (size_t)count * sizeof(double)));
+  const pr_status st = load(b, A, "pr_batch_init");
 #undef PB_INIT_CK
   if (st != PR_OK) return bail(st);
   *out = b;
   return PR_OK;
+}
+
+pr_status pr_batch_load(pr_batch b, const double* const* A) {
+  if (!b) return bfail(nullptr, PR_ESTATE, "pr_batch_load: NULL batch");
+  if (!A) return bfail(b, PR_EINVAL, "pr_batch_load: A is NULL");
+  cudaSetDevice(b->device);
+  return load(b, A, "pr_batch_load");
 }
 
 pr_status pr_batch_solve(pr_batch b, int precision, double tol, int* iterations, int* status) {

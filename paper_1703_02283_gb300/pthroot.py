@@ -88,6 +88,7 @@ def _load() -> ctypes.CDLL:
         "pr_batch_init": (ctypes.c_int, [ctypes.POINTER(_handle_t), ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_void_p),
                                          ctypes.POINTER(pr_options), ctypes.c_void_p]),
+        "pr_batch_load": (ctypes.c_int, [_handle_t, ctypes.POINTER(ctypes.c_void_p)]),
         "pr_batch_solve": (ctypes.c_int, [_handle_t, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_int)]),
         "pr_batch_result": (ctypes.c_int, [_handle_t, ctypes.c_int, _dptr]),
@@ -296,6 +297,12 @@ def pr_batch_init(mats, ps, options: pr_options | None = None, stream: int = 0) 
     _bcheck(_lib.pr_batch_init(ctypes.byref(b), count, n, p, ptrs,
                                ctypes.byref(options) if options is not None else None, ctypes.c_void_p(stream)))
     return b.value
+
+
+def pr_batch_load(b: int, mats) -> None:
+    """Replaces the matrices of a batch (same orders) and restarts every solve."""
+    ptrs = (ctypes.c_void_p * len(mats))(*[_ptr(m) for m in mats])
+    _bcheck(_lib.pr_batch_load(b, ptrs), b)
 
 
 def pr_batch_solve(b: int, count: int, precision: int, tol: float) -> tuple[list, list]:

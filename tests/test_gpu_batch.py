@@ -127,6 +127,36 @@ def test_batch_more_matrices_than_one_control_block():
         assert out[i][1] == hs
 
 
+def test_batch_load_reuses_the_batch():
+    # A batch solved once, then loaded with other matrices of the same orders and roots (from host memory):
+    # its results, histories and iteration counts equal those of a fresh batch of the new matrices, bit for
+    # bit (same captured graph, state reset on the device).
+    cases, ps = make_batch(7, 30, 260, 1e3, 41)
+    other = [W.spd_from_spectrum(c.n, 1e-2, 5000 + i) for i, c in enumerate(cases)]
+    b = P.pr_batch_init([torch.from_numpy(c.A).to(DEV) for c in cases], ps, P.pr_default_options(),
+                        torch.cuda.current_stream(DEV).cuda_stream)
+    try:
+        P.pr_batch_solve(b, len(cases), P.PR_EMU64, 1e-12)
+        P.pr_batch_load(b, [np.ascontiguousarray(c.A) for c in other])
+        its, sts = P.pr_batch_solve(b, len(cases), P.PR_EMU64, 1e-12)
+        got = []
+        for i, c in enumerate(other):
+            C = np.empty((c.n, c.n))
+            P.pr_batch_result(b, i, C)
+            got.append((C, P.pr_batch_history(b, i)))
+        bad = other[0].A.copy()
+        bad[0, 1] += 1.0
+        with pytest.raises(P.PthrootError) as e:
+            P.pr_batch_load(b, [bad] + [c.A for c in other[1:]])
+        assert e.value.status == P.PR_EINVAL
+    finally:
+        P.pr_batch_destroy(b)
+    fresh, fits, fsts, _ = run_batch(other, ps)
+    assert its == fits and sts == fsts
+    for (C, h), (C2, h2) in zip(got, fresh):
+        assert np.array_equal(C, C2) and h == h2
+
+
 def test_batch_max_iter_stops_every_matrix():
     # A cap of 3 updates: every matrix stops with PR_EMAXITER after 3 iterations (4 residuals), at the
     # iterate the single-matrix path with the same cap returns.
