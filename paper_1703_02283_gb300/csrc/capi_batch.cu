@@ -88,7 +88,6 @@ struct pr_batch_s {
   int nslots = 0;
   int64_t cnt = 0;  // launches recorded by the capture in progress
   int64_t launches_pro = 0, launches_body = 0, launches_epi = 0;
-  int loops_seen = 0;
   double tally_seen[3] = {0.0, 0.0, 0.0};
   // per matrix (host)
   std::vector<std::vector<double>> hist;
@@ -605,6 +604,7 @@ pr_status pr_batch_solve(pr_batch b, int precision, double tol, int* iterations,
   b->h_dstate[hist_len + 8] = tol;
   PB_CK(b, cudaMemcpyAsync(b->d_dstate + hist_len + 8, b->h_dstate + hist_len + 8, sizeof(double),
                            cudaMemcpyHostToDevice, b->stream));
+  PB_CK(b, cudaMemsetAsync(b->ctl.loops, 0, sizeof(int), b->stream));  // the pass limit is per solve
   PB_CK(b, cudaGraphLaunch(b->exec, b->stream));
   PB_CK(b, cudaMemcpyAsync(b->h_state, b->d_state, (4 * (size_t)count + 1) * sizeof(int), cudaMemcpyDeviceToHost,
                            b->stream));
@@ -614,8 +614,7 @@ pr_status pr_batch_solve(pr_batch b, int precision, double tol, int* iterations,
   PB_CK(b, cudaStreamSynchronize(b->stream));
   // Launches: the prologue and the harvest once, the loop body once per pass.
   const int loops = b->h_state[4 * count];
-  b->launches += b->launches_pro + (int64_t)(loops - b->loops_seen) * b->launches_body + b->launches_epi;
-  b->loops_seen = loops;
+  b->launches += b->launches_pro + (int64_t)loops * b->launches_body + b->launches_epi;
   const double* tally = b->h_dstate + hist_len;
   b->st.stages = (int64_t)tally[3];
   b->st.products = (int64_t)tally[4];
@@ -638,6 +637,9 @@ pr_status pr_batch_solve(pr_batch b, int precision, double tol, int* iterations,
     cudaMemsetAsync(b->err, 0, sizeof(int), b->stream);
     return bfail(b, PR_ETIMEOUT, "pr_batch: a bounded device wait expired");
   }
+  for (int m = 0; m < count; ++m)
+    if (b->status[m] < 0)
+      return bfail(b, PR_ECUDA, "pr_batch_solve: the solve loop ended with matrix " + std::to_string(m) + " iterating");
   return PR_OK;
 }
 

@@ -200,7 +200,7 @@ struct BatchCtl {
   const int4 *items_sym, *items_full;    // every matrix's work items (emu_tile_list), symmetric and full
   // state
   int *active, *status, *iters, *hlen;   // per matrix (status -1: running)
-  int* loops;                            // solve-loop passes so far
+  int* loops;                            // passes of the solve loop in the current solve
   double* hist;                          // count x hcap residual histories
   double* tally;                         // [0] timed ns, [1] timed flops, [2] timed launches,
                                          // [3] non-empty product launches, [4] products, [5] product flops

@@ -137,8 +137,9 @@ def test_batch_load_reuses_the_batch():
                         torch.cuda.current_stream(DEV).cuda_stream)
     try:
         P.pr_batch_solve(b, len(cases), P.PR_EMU64, 1e-12)
-        P.pr_batch_load(b, [np.ascontiguousarray(c.A) for c in other])
-        its, sts = P.pr_batch_solve(b, len(cases), P.PR_EMU64, 1e-12)
+        for _ in range(8):  # together more loop passes than the limit of one solve
+            P.pr_batch_load(b, [np.ascontiguousarray(c.A) for c in other])
+            its, sts = P.pr_batch_solve(b, len(cases), P.PR_EMU64, 1e-12)
         got = []
         for i, c in enumerate(other):
             C = np.empty((c.n, c.n))
