@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--mode", default="fast", choices=["fast", "emu64", "fp64"])
     ap.add_argument("--tol", type=float, default=1e-12)
     ap.add_argument("--no-compare", action="store_true", help="skip the plain FP64 comparison run")
+    ap.add_argument("--emu-slices", type=int, default=0, help="PR_EMU64 digit planes per operand (0: the default, 8)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="single", choices=["single", "batched", "learned"],
@@ -543,7 +544,9 @@ def main():
     case = W.spd_from_spectrum(args.n, args.lam_min, args.seed + 1000 * rank)
     A = torch.from_numpy(case.A).to(dev)
     C = torch.empty_like(A)
-    handles = {p: P.pr_init(A, args.n, p, P.pr_default_options(), sptr) for p in ps}
+    opts = P.pr_default_options()
+    opts.emu_slices = args.emu_slices
+    handles = {p: P.pr_init(A, args.n, p, opts, sptr) for p in ps}
 
     def plan(p, mode):
         """(bulk precision, bulk steps, final precision) of one solve."""

@@ -207,6 +207,11 @@ pr_status pr_history(pr_handle h, double* out, int cap, int* len);
  * Allocates and frees temporary device buffers. Synchronises the stream. */
 pr_status pr_matmul(int precision, const double* X, const double* Y, int64_t n, int sym, double* P, void* stream);
 
+/* pr_matmul with PR_EMU64 products of `slices` digit planes per operand (1..8; pr_matmul uses 8), for
+ * testing every slice count the options allow (pr_options.emu_slices). Errors: as pr_matmul, and
+ * PR_EINVAL for slices outside [1, 8]. */
+pr_status pr_matmul_emu(int slices, const double* X, const double* Y, int64_t n, int sym, double* P, void* stream);
+
 /* Enables (on != 0) or disables CUDA-event timing of every matrix-product kernel; the summed times
  * appear in pr_stats (gemm_ms, gemms_timed, gemm_flops_timed). Adds two event records per product. */
 pr_status pr_set_timing(pr_handle h, int on);

@@ -588,6 +588,77 @@ namespace pr {
 void set_handleless_error(const char* msg) { g_init_error = msg; }
 }  // namespace pr
 
+namespace {
+
+pr_status matmul(int precision, int S, const double* X, const double* Y, int64_t n, int sym, double* P,
+                 void* stream) {
+  if (!X || !Y || !P) return fail(nullptr, PR_EINVAL, "pr_matmul: NULL matrix");
+  if (n < 1 || n > (int64_t)1 << 17) return fail(nullptr, PR_EINVAL, "pr_matmul: n must be in [1, 131072]");
+  if (precision != PR_FP64 && precision != PR_BF16 && precision != PR_EMU64)
+    return fail(nullptr, PR_EINVAL, "pr_matmul: unknown precision");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int ni = (int)n, ldl = pr::bf16_ld(ni);
+  const size_t bytes = (size_t)n * (size_t)n * sizeof(double);
+  const int eld = pr::emu_ld(ni);
+  const size_t lbytes = precision == PR_EMU64 ? (size_t)8 * (size_t)n * (size_t)eld * sizeof(__half)
+                                              : (size_t)n * (size_t)ldl * sizeof(__nv_bfloat16);
+  const Mode mode = sym ? Mode::Sym : Mode::Full;
+  double *dX = nullptr, *dY = nullptr, *dP = nullptr;
+  __nv_bfloat16 *bX = nullptr, *bY = nullptr;
+  int *err = nullptr, *eX = nullptr, *eY = nullptr;
+  int4* items = nullptr;
+  long long* scratch = nullptr;
+  std::vector<int4> hitems;
+  cudaError_t e = cudaSuccess;
+  int word = 0;
+  auto step = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+  };
+  step(cudaMalloc((void**)&dX, bytes));
+  step(cudaMalloc((void**)&dY, bytes));
+  step(cudaMalloc((void**)&dP, bytes));
+  step(cudaMalloc((void**)&err, sizeof(int)));
+  if (precision != PR_FP64) {
+    step(cudaMalloc((void**)&bX, lbytes));
+    step(cudaMalloc((void**)&bY, lbytes));
+    step(cudaMalloc((void**)&eX, (size_t)n * sizeof(int)));
+    step(cudaMalloc((void**)&eY, (size_t)n * sizeof(int)));
+  }
+  if (e == cudaSuccess) {
+    step(cudaMemsetAsync(err, 0, sizeof(int), s));
+    step(cudaMemcpyAsync(dX, X, bytes, cudaMemcpyDefault, s));
+    step(cudaMemcpyAsync(dY, Y, bytes, cudaMemcpyDefault, s));
+    Epilogue ep;
+    ep.out = dP;
+    if (precision == PR_FP64) {
+      step(pr::gemm_f64(dX, dY, ni, mode, ep, s));
+    } else if (precision == PR_BF16) {
+      step(pr::to_bf16(dX, ni, ldl, bX, s));
+      step(pr::to_bf16(dY, ni, ldl, bY, s));
+      step(pr::gemm_bf16_tc(bX, bY, ni, ldl, mode, false, ep, err, s));
+    } else {
+      __half *hX = reinterpret_cast<__half*>(bX), *hY = reinterpret_cast<__half*>(bY);
+      pr::emu_tile_list(0, ni, mode, hitems);
+      step(cudaMalloc((void**)&items, hitems.size() * sizeof(int4)));
+      step(cudaMalloc((void**)&scratch, pr::emu_scratch_bytes()));
+      step(cudaMemcpyAsync(items, hitems.data(), hitems.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+      step(pr::slice(dX, ni, eld, S, hX, eX, s));
+      step(pr::slice(dY, ni, eld, S, hY, eY, s));
+      step(pr::gemm_emu(hX, eX, hY, eY, ni, eld, S, mode, false, items, (int)hitems.size(), ep, scratch, err, s));
+    }
+    step(cudaMemcpyAsync(P, dP, bytes, cudaMemcpyDefault, s));
+    step(cudaMemcpyAsync(&word, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    step(cudaStreamSynchronize(s));
+  }
+  for (void* q : {(void*)dX, (void*)dY, (void*)dP, (void*)bX, (void*)bY, (void*)err, (void*)eX, (void*)eY, (void*)items, (void*)scratch})
+    if (q) cudaFree(q);
+  if (e != cudaSuccess) return cuda_fail(nullptr, "pr_matmul", e);
+  if (word != 0) return fail(nullptr, PR_ETIMEOUT, "pr_matmul: a bounded device wait expired");
+  return PR_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int pr_version(void) { return 100; }
@@ -894,71 +965,16 @@ pr_status pr_result(pr_handle h, double* C_out) {
   return sync(h);
 }
 
-pr_status pr_matmul(int precision, const double* X, const double* Y, int64_t n, int sym, double* P, void* stream) {
-  if (!X || !Y || !P) return fail(nullptr, PR_EINVAL, "pr_matmul: NULL matrix");
-  if (n < 1 || n > (int64_t)1 << 17) return fail(nullptr, PR_EINVAL, "pr_matmul: n must be in [1, 131072]");
-  if (precision != PR_FP64 && precision != PR_BF16 && precision != PR_EMU64)
-    return fail(nullptr, PR_EINVAL, "pr_matmul: unknown precision");
-  cudaStream_t s = (cudaStream_t)stream;
-  const int ni = (int)n, ldl = pr::bf16_ld(ni), S = pr::emu_max_slices();
-  const size_t bytes = (size_t)n * (size_t)n * sizeof(double);
-  const int eld = pr::emu_ld(ni);
-  const size_t lbytes = precision == PR_EMU64 ? (size_t)8 * (size_t)n * (size_t)eld * sizeof(__half)
-                                              : (size_t)n * (size_t)ldl * sizeof(__nv_bfloat16);
-  const Mode mode = sym ? Mode::Sym : Mode::Full;
-  double *dX = nullptr, *dY = nullptr, *dP = nullptr;
-  __nv_bfloat16 *bX = nullptr, *bY = nullptr;
-  int *err = nullptr, *eX = nullptr, *eY = nullptr;
-  int4* items = nullptr;
-  long long* scratch = nullptr;
-  std::vector<int4> hitems;
-  cudaError_t e = cudaSuccess;
-  int word = 0;
-  auto step = [&](cudaError_t r) {
-    if (e == cudaSuccess) e = r;
-  };
-  step(cudaMalloc((void**)&dX, bytes));
-  step(cudaMalloc((void**)&dY, bytes));
-  step(cudaMalloc((void**)&dP, bytes));
-  step(cudaMalloc((void**)&err, sizeof(int)));
-  if (precision != PR_FP64) {
-    step(cudaMalloc((void**)&bX, lbytes));
-    step(cudaMalloc((void**)&bY, lbytes));
-    step(cudaMalloc((void**)&eX, (size_t)n * sizeof(int)));
-    step(cudaMalloc((void**)&eY, (size_t)n * sizeof(int)));
-  }
-  if (e == cudaSuccess) {
-    step(cudaMemsetAsync(err, 0, sizeof(int), s));
-    step(cudaMemcpyAsync(dX, X, bytes, cudaMemcpyDefault, s));
-    step(cudaMemcpyAsync(dY, Y, bytes, cudaMemcpyDefault, s));
-    Epilogue ep;
-    ep.out = dP;
-    if (precision == PR_FP64) {
-      step(pr::gemm_f64(dX, dY, ni, mode, ep, s));
-    } else if (precision == PR_BF16) {
-      step(pr::to_bf16(dX, ni, ldl, bX, s));
-      step(pr::to_bf16(dY, ni, ldl, bY, s));
-      step(pr::gemm_bf16_tc(bX, bY, ni, ldl, mode, false, ep, err, s));
-    } else {
-      __half *hX = reinterpret_cast<__half*>(bX), *hY = reinterpret_cast<__half*>(bY);
-      pr::emu_tile_list(0, ni, mode, hitems);
-      step(cudaMalloc((void**)&items, hitems.size() * sizeof(int4)));
-      step(cudaMalloc((void**)&scratch, pr::emu_scratch_bytes()));
-      step(cudaMemcpyAsync(items, hitems.data(), hitems.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
-      step(pr::slice(dX, ni, eld, S, hX, eX, s));
-      step(pr::slice(dY, ni, eld, S, hY, eY, s));
-      step(pr::gemm_emu(hX, eX, hY, eY, ni, eld, S, mode, false, items, (int)hitems.size(), ep, scratch, err, s));
-    }
-    step(cudaMemcpyAsync(P, dP, bytes, cudaMemcpyDefault, s));
-    step(cudaMemcpyAsync(&word, err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    step(cudaStreamSynchronize(s));
-  }
-  for (void* q : {(void*)dX, (void*)dY, (void*)dP, (void*)bX, (void*)bY, (void*)err, (void*)eX, (void*)eY, (void*)items, (void*)scratch})
-    if (q) cudaFree(q);
-  if (e != cudaSuccess) return cuda_fail(nullptr, "pr_matmul", e);
-  if (word != 0) return fail(nullptr, PR_ETIMEOUT, "pr_matmul: a bounded device wait expired");
-  return PR_OK;
+pr_status pr_matmul_emu(int slices, const double* X, const double* Y, int64_t n, int sym, double* P, void* stream) {
+  if (slices < 1 || slices > pr::emu_max_slices())
+    return fail(nullptr, PR_EINVAL, "pr_matmul_emu: slices must be in [1, 8]");
+  return matmul(PR_EMU64, slices, X, Y, n, sym, P, stream);
 }
+
+pr_status pr_matmul(int precision, const double* X, const double* Y, int64_t n, int sym, double* P, void* stream) {
+  return matmul(precision, pr::emu_max_slices(), X, Y, n, sym, P, stream);
+}
+
 
 pr_status pr_features(pr_handle h, double* out) {
   if (!h) return fail(nullptr, PR_ESTATE, "pr_features: NULL handle");

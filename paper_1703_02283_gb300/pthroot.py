@@ -112,6 +112,8 @@ def _load() -> ctypes.CDLL:
         "pr_norms_noalloc": (ctypes.c_int, [_dptr, ctypes.c_int64, _dptr, ctypes.c_void_p]),
         "pr_matmul": (ctypes.c_int, [ctypes.c_int, _dptr, _dptr, ctypes.c_int64, ctypes.c_int, _dptr,
                                      ctypes.c_void_p]),
+        "pr_matmul_emu": (ctypes.c_int, [ctypes.c_int, _dptr, _dptr, ctypes.c_int64, ctypes.c_int, _dptr,
+                                     ctypes.c_void_p]),
         "pr_stats": (ctypes.c_int, [_handle_t, ctypes.POINTER(pr_stats_t)]),
         "pr_history": (ctypes.c_int, [_handle_t, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                       ctypes.POINTER(ctypes.c_int)]),
@@ -261,6 +263,11 @@ def pr_norms_noalloc(A, n: int, out, stream: int = 0) -> None:
 def pr_matmul(precision: int, X, Y, n: int, sym: bool, P, stream: int = 0) -> None:
     _check(_lib.pr_matmul(int(precision), _ptr(X), _ptr(Y), int(n), 1 if sym else 0, _ptr(P),
                           ctypes.c_void_p(stream)), None)
+
+
+def pr_matmul_emu(slices: int, X, Y, n: int, sym: bool, P, stream: int = 0) -> None:
+    _check(_lib.pr_matmul_emu(int(slices), _ptr(X), _ptr(Y), int(n), 1 if sym else 0, _ptr(P),
+                              ctypes.c_void_p(stream)), None)
 
 
 def pr_stats(h: int) -> dict:

@@ -33,11 +33,11 @@ def row_exponents(X):
     return np.where(m > 0, p + 1, 0)
 
 
-def emu_bound(X, Y, ref):
+def emu_bound(X, Y, ref, slices=S):
     n = X.shape[0]
     ex, ey = row_exponents(X), row_exponents(Y)
     scale = np.ldexp(1.0, ex[:, None] + ey[None, :])
-    return n * (S + 2) * 2.0 ** (-8 * S - 2) * scale + 16 * U * np.abs(ref)
+    return n * (slices + 2) * 2.0 ** (-8 * slices - 2) * scale + 16 * U * np.abs(ref)
 
 
 def sym_pair(n, seed):
@@ -71,6 +71,23 @@ def test_emu_product_elementwise(n, sym):
         assert np.all(err <= bound)
 
 
+@pytest.mark.parametrize("slices", [1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("n,sym", [(129, True), (300, False)])
+def test_emu_product_every_slice_count(slices, n, sym):
+    # Every slice count the options allow: element-wise within the truncation bound of `slices` planes.
+    X, Y = sym_pair(n, 90 + n)
+    ref = (X.astype(np.longdouble) @ Y.T.astype(np.longdouble))
+    Xd, Yd = torch.from_numpy(X).to(DEV), torch.from_numpy(Y).to(DEV)
+    Pd = torch.empty_like(Xd)
+    P.pr_matmul_emu(slices, Xd, Yd, n, sym, Pd, torch.cuda.current_stream(DEV).cuda_stream)
+    Pg = Pd.cpu().numpy()
+    err = np.abs(Pg.astype(np.longdouble) - ref).astype(np.float64)
+    bound = emu_bound(X, Y, ref.astype(np.float64), slices)
+    sel = np.triu_indices(n) if sym else np.indices((n, n)).reshape(2, -1)
+    assert np.all(np.isfinite(Pg[sel]))
+    assert np.all(err[sel] <= bound[sel]), (slices, float(np.max(err[sel] / bound[sel])))
+
+
 def test_emu_product_full_size_sampled():
     n = 4096
     c = W.spd_from_spectrum(n, 1e-3, 1)
@@ -87,9 +104,10 @@ def test_emu_product_full_size_sampled():
     assert np.array_equal(Pg, Pg.T)
 
 
-def gpu_solve(case, p, prec, c0=P.PR_C0_EQ3, tol=1e-12, bulk=None, bulk_steps=0):
+def gpu_solve(case, p, prec, c0=P.PR_C0_EQ3, tol=1e-12, bulk=None, bulk_steps=0, slices=0):
     o = P.pr_default_options()
     o.c0 = c0
+    o.emu_slices = slices
     A = torch.from_numpy(case.A).to(DEV)
     h = P.pr_init(A, case.n, p, o, torch.cuda.current_stream(DEV).cuda_stream)
     try:
@@ -111,6 +129,20 @@ def test_emu_solve_matches_oracle_small_case(p):
     assert O.forward_error(C, Co) <= bound and O.forward_error(C, Z) <= bound
     assert abs(steps - info.iterations) <= 1
     assert stats["iterations_by_precision"][P.PR_EMU64] == steps
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_emu_solve_seven_slices(p):
+    # 7 planes keep 56 bits per row: a per-term error of 9 2^-58 of the row/column scale, still below
+    # FP64 rounding; the solve meets the same bar against the oracle.
+    case = W.spd_from_spectrum(256, 1e-2, 0)
+    C, st, steps, stats, hist = gpu_solve(case, p, P.PR_EMU64, slices=7)
+    assert stats["emu_slices"] == 7 and st in (P.PR_OK, P.PR_ESTAGNATED)
+    Co, info = O.solve(case.A, p, tol=1e-12)
+    Z = O.closed_form_root(case.Q, case.lam, p)
+    bound = max(1e-12, 10 * O.forward_error(Co, Z))
+    assert O.forward_error(C, Co) <= bound and O.forward_error(C, Z) <= bound
+    assert abs(steps - info.iterations) <= 1
 
 
 @pytest.mark.parametrize("n", [7, 65, 130, 300])
