@@ -212,6 +212,13 @@ pr_status pr_matmul(int precision, const double* X, const double* Y, int64_t n, 
  * PR_EINVAL for slices outside [1, 8]. */
 pr_status pr_matmul_emu(int slices, const double* X, const double* Y, int64_t n, int sym, double* P, void* stream);
 
+/* Exercises the failure path of the library's bounded device waits: launches one kernel that waits on an
+ * mbarrier that nothing completes, through the same bounded-wait helper every tcgen05 kernel uses. The
+ * wait gives up after its limit (2 s), records its code in a device error word and the kernel returns; the
+ * CUDA context stays usable. Returns PR_ETIMEOUT (the expected outcome; *waited_s, if not NULL, receives
+ * the device-clock time the wait took), PR_ECUDA if the wait did not run out or a CUDA call failed. */
+pr_status pr_selftest_wait(void* stream, double* waited_s);
+
 /* Enables (on != 0) or disables CUDA-event timing of every matrix-product kernel; the summed times
  * appear in pr_stats (gemm_ms, gemms_timed, gemm_flops_timed). Adds two event records per product. */
 pr_status pr_set_timing(pr_handle h, int on);

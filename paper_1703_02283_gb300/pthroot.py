@@ -114,6 +114,7 @@ def _load() -> ctypes.CDLL:
                                      ctypes.c_void_p]),
         "pr_matmul_emu": (ctypes.c_int, [ctypes.c_int, _dptr, _dptr, ctypes.c_int64, ctypes.c_int, _dptr,
                                      ctypes.c_void_p]),
+        "pr_selftest_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
         "pr_stats": (ctypes.c_int, [_handle_t, ctypes.POINTER(pr_stats_t)]),
         "pr_history": (ctypes.c_int, [_handle_t, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                       ctypes.POINTER(ctypes.c_int)]),
@@ -263,6 +264,13 @@ def pr_norms_noalloc(A, n: int, out, stream: int = 0) -> None:
 def pr_matmul(precision: int, X, Y, n: int, sym: bool, P, stream: int = 0) -> None:
     _check(_lib.pr_matmul(int(precision), _ptr(X), _ptr(Y), int(n), 1 if sym else 0, _ptr(P),
                           ctypes.c_void_p(stream)), None)
+
+
+def pr_selftest_wait(stream: int = 0) -> tuple[int, float]:
+    """(status, seconds waited): PR_ETIMEOUT is the expected status."""
+    w = ctypes.c_double(0.0)
+    st = _lib.pr_selftest_wait(ctypes.c_void_p(stream), ctypes.byref(w))
+    return st, w.value
 
 
 def pr_matmul_emu(slices: int, X, Y, n: int, sym: bool, P, stream: int = 0) -> None:

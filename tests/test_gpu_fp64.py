@@ -201,3 +201,16 @@ def test_p4_chain_uses_squares():
     bound = max(1e-12, 10 * O.forward_error(Co, Z))
     assert O.forward_error(C.cpu().numpy(), Z) <= bound and O.forward_error(C.cpu().numpy(), Co) <= bound
     assert abs(d - info.iterations) <= 1
+
+
+def test_bounded_wait_expires_and_context_survives():
+    # A device wait that nothing completes runs out after its limit and is reported as PR_ETIMEOUT; the
+    # next products on the same context are still correct.
+    st, waited = P.pr_selftest_wait(torch.cuda.current_stream(DEV).cuda_stream)
+    assert st == P.PR_ETIMEOUT and 1.9 < waited < 3.0
+    assert "expected" in P.pr_last_error()
+    case = W.spd_from_spectrum(130, 0.05, 12)
+    X = torch.from_numpy(case.A).to(DEV)
+    Pd = torch.empty_like(X)
+    P.pr_matmul(P.PR_EMU64, X, X, 130, True, Pd, torch.cuda.current_stream(DEV).cuda_stream)
+    np.testing.assert_allclose(Pd.cpu().numpy(), case.A @ case.A, rtol=1e-12, atol=1e-14)
