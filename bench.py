@@ -39,7 +39,7 @@ METRIC = "time to FP64-accurate A^(-1/p) vs plain FP64 GPU; GEMM TFLOP/s, % of p
 NOMINAL_BF16_TFLOPS = 2250.0
 NOMINAL_FP64_TFLOPS = 1.25
 PREC_NAMES = {0: "fp64", 1: "emu64", 3: "bf16"}
-EMU_TRAFFIC_BYTES = {4096: 2.363865e9 + 0.198035e9}  # ncu dram__bytes_read.sum + dram__bytes_write.sum, by n
+EMU_TRAFFIC_BYTES = {4096: 2.371166e9 + 0.200156e9}  # ncu dram__bytes_read.sum + dram__bytes_write.sum, by n
 
 
 def parse():
