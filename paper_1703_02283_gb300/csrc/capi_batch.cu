@@ -635,7 +635,8 @@ pr_status pr_batch_solve(pr_batch b, int precision, double tol, int* iterations,
   }
   if (b->h_err != 0) {
     cudaMemsetAsync(b->err, 0, sizeof(int), b->stream);
-    return bfail(b, PR_ETIMEOUT, "pr_batch: a bounded device wait expired");
+    return bfail(b, PR_ETIMEOUT,
+                 "pr_batch: a bounded device wait expired (code " + std::to_string(b->h_err) + ")");
   }
   for (int m = 0; m < count; ++m)
     if (b->status[m] < 0)
