@@ -42,6 +42,31 @@ PREC_NAMES = {0: "fp64", 1: "emu64", 3: "bf16"}
 EMU_TRAFFIC_BYTES = {4096: 2.371166e9 + 0.200156e9}  # ncu dram__bytes_read.sum + dram__bytes_write.sum, by n
 
 
+# ----------------------------------------------------------------------------- replicas (N > 1 under torchrun)
+# Every workload runs one independent replica per rank (its own inputs, same recipe, seeds offset by rank):
+# the problems do not share data, so no collective enters the data path. The ranks meet only at barriers
+# around the timed region and in one MAX reduction of the timings; rank 0 prints.
+
+def replica_env() -> tuple[int, int, int]:
+    """(world size, rank, local rank) from the launcher's environment."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def replica_seed(seed: int, rank: int) -> int:
+    return seed + 1000 * rank
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over all ranks of the default process group (x itself when there is none)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -192,9 +217,12 @@ def run_reference(args, ps):
 
 # ----------------------------------------------------------------------------- GPU arm
 
-def batched_cases(count):
-    spec = W.batched_specs(count)
-    cases = [W.spd_from_spectrum(int(spec.n[i]), float(spec.lam_min[i]), int(spec.seeds[i])) for i in range(count)]
+def batched_cases(count, rank=0):
+    """The batch of one replica: rank 0 the benchmark's batch (specs seed 999, matrix seeds 1000 + i), other
+    ranks the same recipe with their own seeds."""
+    spec = W.batched_specs(count, seed=999 + rank)
+    seeds = [int(x) + 100000 * rank for x in spec.seeds]
+    cases = [W.spd_from_spectrum(int(spec.n[i]), float(spec.lam_min[i]), seeds[i]) for i in range(count)]
     return cases, [int(x) for x in spec.p]
 
 
@@ -241,11 +269,14 @@ def run_batched(args):
                                            "sample": what},
                           "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import torch.distributed as dist
+    world, rank, local = replica_env()
+    if world > 1:
+        dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
-    cases, ps = batched_cases(args.count)
+    cases, ps = batched_cases(args.count, rank)
     mats = [torch.from_numpy(c.A).to(dev) for c in cases]
     nbytes = sum(c.n * c.n * 8 for c in cases)
 
@@ -267,16 +298,21 @@ def run_batched(args):
         bst = {k: (s1[k] - s0[k] if k != "emu_slices" else s1[k]) for k in s1}
         return its, sts, outs, bst
 
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
     for _ in range(args.warmup):
         one(mats)
-    torch.cuda.synchronize(dev)
+    barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         ev0.record(stream)
         runs = [one(mats) for _ in range(args.steps)]
         ev1.record(stream)
-        torch.cuda.synchronize(dev)
-    ms = ev0.elapsed_time(ev1) / args.steps
+        barrier()
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, dev)
     its, sts, outs, bst = runs[-1]
     launches = sum(r[3]["launches"] for r in runs)
     # Roofline of the product kernel over the timed steps (CUDA events around every product launch).
@@ -304,27 +340,32 @@ def run_batched(args):
     if not args.no_e2e:
         host = [c.A.copy() for c in cases]
         host = [torch.from_numpy(h).pin_memory() for h in host]
+        barrier()
         t0 = time.perf_counter()
         one(host)
-        e2e = {"value": (time.perf_counter() - t0) * 1e3, "unit": "ms", "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": nbytes}
+        barrier()
+        e2e = {"value": max_over_ranks((time.perf_counter() - t0) * 1e3, dist, dev), "unit": "ms",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
     P.pr_batch_destroy(b)
     cpu = None
-    if not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, what = oracle_batched_sample(cases, ps, its)
         cpu = {"value": v, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle", "sample": what}
     stat = {}
     for s_ in sts:
         stat[P.STATUS_NAMES[s_]] = stat.get(P.STATUS_NAMES[s_], 0) + 1
-    line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "emu64(fp16 slices)", "data": "synthetic", "config": batched_config(args),
+    line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "emu64(fp16 slices)", "data": "synthetic", "config": batched_config(args),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(),
             "batch": {"statuses": stat, "iterations_max": max(its), "iterations_mean": float(np.mean(its)),
                       "rel_error_median": float(np.median(errs)), "rel_error_max": float(np.max(errs)),
-                      "matrices_per_second": len(cases) / (ms * 1e-3)}}
-    print(json.dumps(line), flush=True)
+                      "matrices_per_second": world * len(cases) / (ms * 1e-3)}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 
 
 # ----------------------------------------------------------------------------- learned initial guess
@@ -391,7 +432,10 @@ def run_learned(args):
 
     from paper_1703_02283_gb300 import learned as L
     from paper_1703_02283_gb300 import pthroot as P
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import torch.distributed as dist
+    world, rank, local = replica_env()
+    if world > 1:
+        dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
@@ -426,9 +470,14 @@ def run_learned(args):
             info.append((st, its, P.PR_C0_EQ3, 0.0))
         return info
 
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
     for _ in range(args.warmup):
         learned_step(Ad, Cd)
-    torch.cuda.synchronize(dev)
+    barrier()
     s0 = P.pr_stats(h)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
@@ -436,8 +485,8 @@ def run_learned(args):
         for _ in range(args.steps):
             info = learned_step(Ad, Cd)
         ev1.record(stream)
-        torch.cuda.synchronize(dev)
-    ms = ev0.elapsed_time(ev1) / args.steps
+        barrier()
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, dev)
     s1 = P.pr_stats(h)
     launches = (s1["launches"] - s0["launches"]) + args.steps * len(test)  # + one MLP forward per matrix
     dms = s1["gemm_ms_by_precision"][P.PR_EMU64] - s0["gemm_ms_by_precision"][P.PR_EMU64]
@@ -480,15 +529,15 @@ def run_learned(args):
         Ah = [torch.from_numpy(S).pin_memory() for S in test]
         Ch = [torch.empty((n, n), dtype=torch.float64).pin_memory() for _ in test]
         learned_step(Ah, Ch)
-        torch.cuda.synchronize(dev)
+        barrier()
         t0 = time.perf_counter()
         learned_step(Ah, Ch)
-        torch.cuda.synchronize(dev)
+        barrier()
         nbytes = n * n * 8 * len(test)
-        e2e = {"value": (time.perf_counter() - t0) * 1e3, "unit": "ms", "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": nbytes}
+        e2e = {"value": max_over_ranks((time.perf_counter() - t0) * 1e3, dist, dev), "unit": "ms",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
     cpu = None
-    if not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         its_plain = [x[1] for x in pinfo]
         est, what = oracle_sample(test[0], p, int(np.mean(its_plain)))
         cpu = {"value": est * len(test), "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
@@ -498,9 +547,9 @@ def run_learned(args):
     its_l = [x[1] for x in info]
     its_p = [x[1] for x in pinfo]
     used = sum(1 for x in info if x[2] == P.PR_C0_POLY)
-    line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "emu64(fp16 slices)", "data": "synthetic", "config": learned_config(args),
+    line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "emu64(fp16 slices)", "data": "synthetic", "config": learned_config(args),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(),
             "learned": {"matrices": len(test), "guess_used": used, "gate_values": [round(x[3], 4) for x in info],
@@ -512,7 +561,10 @@ def run_learned(args):
             "plain_eq3": {"ms_per_step": pms, "speedup_of_value": pms / ms, "iterations_mean": float(np.mean(its_p)),
                           "iterations": its_p, "statuses": [P.STATUS_NAMES[x[0]] for x in pinfo],
                           "rel_error_vs_eigh": errs_p}}
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def main():
@@ -530,9 +582,7 @@ def main():
 
     from paper_1703_02283_gb300 import pthroot as P
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = replica_env()
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -541,7 +591,7 @@ def main():
     sptr = stream.cuda_stream
 
     # Replicas: every rank solves its own matrix of the same recipe (seed offset by rank).
-    case = W.spd_from_spectrum(args.n, args.lam_min, args.seed + 1000 * rank)
+    case = W.spd_from_spectrum(args.n, args.lam_min, replica_seed(args.seed, rank))
     A = torch.from_numpy(case.A).to(dev)
     C = torch.empty_like(A)
     opts = P.pr_default_options()
@@ -597,10 +647,7 @@ def main():
         P.pr_set_timing(h, False)
     ms = ev0.elapsed_time(ev1) / args.steps
     s1 = {p: P.pr_stats(h) for p, h in handles.items()}
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     last = infos[-1]
     for p, h in handles.items():
         P.pr_result(h, C)
@@ -657,7 +704,7 @@ def main():
             solve_all(args.mode, Ah, Ch)
         barrier()
         nbytes = args.n * args.n * 8 * len(ps)
-        e2e = {"value": (time.perf_counter() - t0) * 1e3 / args.steps, "unit": "ms",
+        e2e = {"value": max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, dist, dev), "unit": "ms",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
     # The plain FP64 GPU iteration on the same matrices, once per p (the speed comparison).
