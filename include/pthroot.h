@@ -212,6 +212,49 @@ pr_status pr_matmul(int precision, const double* X, const double* Y, int64_t n, 
  * PR_EINVAL for slices outside [1, 8]. */
 pr_status pr_matmul_emu(int slices, const double* X, const double* Y, int64_t n, int sym, double* P, void* stream);
 
+/* ---- Checkpoint and resume ----------------------------------------------------------------------------
+ * The state of an iteration as one host byte buffer: the iterate X and, for the coupled form with its
+ * product formed, M and N (FP64, and their BF16 copies), the residual history with the precision of each
+ * entry, and the counters the stop rule reads. Importing it into a handle that holds the same A (same
+ * order, root and form, and the same ||A||_1, ||A||_inf; from pr_init or pr_load) resumes the iteration
+ * where the export left it: the iterates that follow are bit-identical to those of the exporting handle.
+ * Layout: pr_state_header; hist_len doubles (r_0 ..); hist_len int32 precisions, padded to a multiple of
+ * 8 bytes; n_mats FP64 matrices n x n (X, then M, N); n_mats BF16 matrices n x ldl (same order). */
+#define PR_STATE_MAGIC 0x5052535441544531ull /* "PRSTATE1" */
+typedef struct {
+  uint64_t magic;
+  int64_t n;
+  int32_t version;         /* 1 */
+  int32_t p;
+  int32_t form;
+  int32_t c0;
+  double norm_1;           /* of the A the state belongs to */
+  double norm_inf;
+  int32_t state_ready;     /* coupled form: M, N and the residual of X are formed */
+  int32_t state_level;     /* precision level at which M was formed */
+  int32_t lp_stale;        /* the BF16 copies are out of date */
+  int32_t iterations;
+  int32_t iterations_by_precision[4];
+  int32_t switch_iteration;
+  int32_t last_precision;
+  int32_t hist_len;
+  int32_t n_mats;          /* 1 (X) or 3 (X, M, N) */
+  int32_t ldl;             /* leading dimension of the BF16 copies */
+  int32_t reserved;
+  double last_residual;
+} pr_state_header;
+
+/* *bytes = the size of the state buffer pr_export_state writes now. Errors: PR_ESTATE, PR_EINVAL. */
+pr_status pr_state_size(pr_handle h, size_t* bytes);
+
+/* Writes the state into buf (host memory, `bytes` >= pr_state_size). Synchronises the stream.
+ * Errors: PR_ESTATE, PR_EINVAL (NULL or short buffer), PR_ECUDA. */
+pr_status pr_export_state(pr_handle h, void* buf, size_t bytes);
+
+/* Replaces the handle's iteration state by an exported one. Errors: PR_ESTATE, PR_EINVAL (bad magic or
+ * version, short buffer, or a state of another order, root, form or matrix), PR_ECUDA. */
+pr_status pr_import_state(pr_handle h, const void* buf, size_t bytes);
+
 /* Exercises the failure path of the library's bounded device waits: launches one kernel that waits on an
  * mbarrier that nothing completes, through the same bounded-wait helper every tcgen05 kernel uses. The
  * wait gives up after its limit (2 s), records its code in a device error word and the kernel returns; the

@@ -816,6 +816,134 @@ pr_status pr_load(pr_handle h, const double* A) {
   return form_initial_guess(h);
 }
 
+namespace {
+
+// Byte layout of an exported state (see pr_state_header).
+struct StateLayout {
+  size_t hist, prec, f, b, total;
+  int n_mats;
+};
+
+StateLayout state_layout(pr_handle h, int hist_len, int n_mats) {
+  const size_t nn = (size_t)h->n * (size_t)h->n, nb = (size_t)h->n * (size_t)h->ldl;
+  StateLayout L;
+  L.n_mats = n_mats;
+  L.hist = sizeof(pr_state_header);
+  L.prec = L.hist + (size_t)hist_len * sizeof(double);
+  L.f = L.prec + ((size_t)hist_len * sizeof(int32_t) + 7) / 8 * 8;
+  L.b = L.f + (size_t)n_mats * nn * sizeof(double);
+  L.total = L.b + (size_t)n_mats * nb * sizeof(__nv_bfloat16);
+  return L;
+}
+
+int state_mats(pr_handle h) { return h->form == PR_FORM_COUPLED && h->state_ready ? 3 : 1; }
+
+}  // namespace
+
+pr_status pr_state_size(pr_handle h, size_t* bytes) {
+  if (!h) return fail(nullptr, PR_ESTATE, "pr_state_size: NULL handle");
+  if (!bytes) return fail(h, PR_EINVAL, "pr_state_size: bytes is NULL");
+  *bytes = state_layout(h, (int)h->hist.size(), state_mats(h)).total;
+  return PR_OK;
+}
+
+pr_status pr_export_state(pr_handle h, void* buf, size_t bytes) {
+  if (!h) return fail(nullptr, PR_ESTATE, "pr_export_state: NULL handle");
+  const StateLayout L = state_layout(h, (int)h->hist.size(), state_mats(h));
+  if (!buf || bytes < L.total) return fail(h, PR_EINVAL, "pr_export_state: buffer NULL or too small");
+  cudaSetDevice(h->device);
+  pr_state_header hd{};
+  hd.magic = PR_STATE_MAGIC;
+  hd.version = 1;
+  hd.n = h->n;
+  hd.p = h->p;
+  hd.form = h->form;
+  hd.c0 = h->st.c0;
+  hd.norm_1 = h->st.norm_1;
+  hd.norm_inf = h->st.norm_inf;
+  hd.state_ready = h->state_ready ? 1 : 0;
+  hd.state_level = h->state_level;
+  hd.lp_stale = h->lp_stale ? 1 : 0;
+  hd.iterations = h->st.iterations;
+  for (int k = 0; k < 4; ++k) hd.iterations_by_precision[k] = h->st.iterations_by_precision[k];
+  hd.switch_iteration = h->st.switch_iteration;
+  hd.last_precision = h->st.last_precision;
+  hd.hist_len = (int32_t)h->hist.size();
+  hd.n_mats = L.n_mats;
+  hd.ldl = h->ldl;
+  hd.last_residual = h->st.last_residual;
+  char* out = static_cast<char*>(buf);
+  memcpy(out, &hd, sizeof hd);
+  if (!h->hist.empty()) {
+    memcpy(out + L.hist, h->hist.data(), h->hist.size() * sizeof(double));
+    for (size_t k = 0; k < h->hist_prec.size(); ++k) {
+      const int32_t v = h->hist_prec[k];
+      memcpy(out + L.prec + k * sizeof(int32_t), &v, sizeof v);
+    }
+  }
+  const size_t nn = (size_t)h->n * (size_t)h->n, nb = (size_t)h->n * (size_t)h->ldl;
+  const Mat* mats[3] = {&h->X, &h->M, &h->N};
+  for (int k = 0; k < L.n_mats; ++k) {
+    PR_CK(h, cudaMemcpyAsync(out + L.f + k * nn * sizeof(double), mats[k]->f, nn * sizeof(double),
+                             cudaMemcpyDeviceToHost, h->stream));
+    PR_CK(h, cudaMemcpyAsync(out + L.b + k * nb * sizeof(__nv_bfloat16), mats[k]->b, nb * sizeof(__nv_bfloat16),
+                             cudaMemcpyDeviceToHost, h->stream));
+  }
+  return sync(h);
+}
+
+pr_status pr_import_state(pr_handle h, const void* buf, size_t bytes) {
+  if (!h) return fail(nullptr, PR_ESTATE, "pr_import_state: NULL handle");
+  if (!buf || bytes < sizeof(pr_state_header)) return fail(h, PR_EINVAL, "pr_import_state: buffer NULL or too small");
+  pr_state_header hd;
+  memcpy(&hd, buf, sizeof hd);
+  if (hd.magic != PR_STATE_MAGIC || hd.version != 1) return fail(h, PR_EINVAL, "pr_import_state: not a state buffer");
+  if (hd.n != h->n || hd.p != h->p || hd.form != h->form || hd.ldl != h->ldl)
+    return fail(h, PR_EINVAL, "pr_import_state: the state belongs to another order, root or form");
+  if (hd.norm_1 != h->st.norm_1 || hd.norm_inf != h->st.norm_inf)
+    return fail(h, PR_EINVAL, "pr_import_state: the state belongs to another matrix (its norms differ)");
+  if (hd.hist_len < 0 || hd.hist_len > h->opt.max_iter + 2 || (hd.n_mats != 1 && hd.n_mats != 3) ||
+      (hd.n_mats == 3) != (hd.form == PR_FORM_COUPLED && hd.state_ready != 0))
+    return fail(h, PR_EINVAL, "pr_import_state: inconsistent header");
+  const StateLayout L = state_layout(h, hd.hist_len, hd.n_mats);
+  if (bytes < L.total) return fail(h, PR_EINVAL, "pr_import_state: buffer shorter than its header says");
+  cudaSetDevice(h->device);
+  const char* in = static_cast<const char*>(buf);
+  const size_t nn = (size_t)h->n * (size_t)h->n, nb = (size_t)h->n * (size_t)h->ldl;
+  Mat* mats[3] = {&h->X, &h->M, &h->N};
+  for (int k = 0; k < L.n_mats; ++k) {
+    PR_CK(h, cudaMemcpyAsync(mats[k]->f, in + L.f + k * nn * sizeof(double), nn * sizeof(double),
+                             cudaMemcpyHostToDevice, h->stream));
+    PR_CK(h, cudaMemcpyAsync(mats[k]->b, in + L.b + k * nb * sizeof(__nv_bfloat16), nb * sizeof(__nv_bfloat16),
+                             cudaMemcpyHostToDevice, h->stream));
+  }
+  if (hd.lp_stale == 0) {  // the BF16 copies are current: A's (not in the state) must be too
+    PR_CK(h, pr::to_bf16(h->A.f, (int)h->n, h->ldl, h->A.b, h->stream));
+    h->st.launches += 1;
+  }
+  pr_status s = sync(h);
+  if (s != PR_OK) return s;
+  reset_iteration(h);
+  h->state_ready = hd.state_ready != 0;
+  h->state_level = hd.state_level;
+  h->lp_stale = hd.lp_stale != 0;
+  h->st.c0 = hd.c0;
+  h->st.iterations = hd.iterations;
+  for (int k = 0; k < 4; ++k) h->st.iterations_by_precision[k] = hd.iterations_by_precision[k];
+  h->st.switch_iteration = hd.switch_iteration;
+  h->st.last_precision = hd.last_precision;
+  h->st.last_residual = hd.last_residual;
+  h->hist.resize(hd.hist_len);
+  h->hist_prec.resize(hd.hist_len);
+  if (hd.hist_len > 0) memcpy(h->hist.data(), in + L.hist, (size_t)hd.hist_len * sizeof(double));
+  for (int k = 0; k < hd.hist_len; ++k) {
+    int32_t v;
+    memcpy(&v, in + L.prec + (size_t)k * sizeof(int32_t), sizeof v);
+    h->hist_prec[k] = v;
+  }
+  return PR_OK;
+}
+
 pr_status pr_set_initial_guess(pr_handle h, int kind, const double* coef) {
   if (!h) return fail(nullptr, PR_ESTATE, "pr_set_initial_guess: NULL handle");
   if (kind != PR_C0_EQ3 && kind != PR_C0_SCALED_I && kind != PR_C0_POLY)

@@ -52,6 +52,16 @@ class pr_stats_t(ctypes.Structure):
         return d
 
 
+class pr_state_header(ctypes.Structure):
+    _fields_ = [("magic", ctypes.c_uint64), ("n", ctypes.c_int64), ("version", ctypes.c_int32),
+                ("p", ctypes.c_int32), ("form", ctypes.c_int32), ("c0", ctypes.c_int32),
+                ("norm_1", ctypes.c_double), ("norm_inf", ctypes.c_double), ("state_ready", ctypes.c_int32),
+                ("state_level", ctypes.c_int32), ("lp_stale", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("iterations_by_precision", ctypes.c_int32 * 4), ("switch_iteration", ctypes.c_int32),
+                ("last_precision", ctypes.c_int32), ("hist_len", ctypes.c_int32), ("n_mats", ctypes.c_int32),
+                ("ldl", ctypes.c_int32), ("reserved", ctypes.c_int32), ("last_residual", ctypes.c_double)]
+
+
 class pr_batch_stats_t(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("stages", ctypes.c_int64), ("products", ctypes.c_int64),
                 ("product_flops", ctypes.c_double), ("stages_timed", ctypes.c_int64), ("stage_ms", ctypes.c_double),
@@ -114,6 +124,9 @@ def _load() -> ctypes.CDLL:
                                      ctypes.c_void_p]),
         "pr_matmul_emu": (ctypes.c_int, [ctypes.c_int, _dptr, _dptr, ctypes.c_int64, ctypes.c_int, _dptr,
                                      ctypes.c_void_p]),
+        "pr_state_size": (ctypes.c_int, [_handle_t, ctypes.POINTER(ctypes.c_size_t)]),
+        "pr_export_state": (ctypes.c_int, [_handle_t, ctypes.c_void_p, ctypes.c_size_t]),
+        "pr_import_state": (ctypes.c_int, [_handle_t, ctypes.c_void_p, ctypes.c_size_t]),
         "pr_selftest_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
         "pr_stats": (ctypes.c_int, [_handle_t, ctypes.POINTER(pr_stats_t)]),
         "pr_history": (ctypes.c_int, [_handle_t, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
@@ -264,6 +277,24 @@ def pr_norms_noalloc(A, n: int, out, stream: int = 0) -> None:
 def pr_matmul(precision: int, X, Y, n: int, sym: bool, P, stream: int = 0) -> None:
     _check(_lib.pr_matmul(int(precision), _ptr(X), _ptr(Y), int(n), 1 if sym else 0, _ptr(P),
                           ctypes.c_void_p(stream)), None)
+
+
+def pr_export_state(h: int):
+    """The handle's iteration state as a numpy uint8 array (layout: pr_state_header, then the payload)."""
+    import numpy as np
+    size = ctypes.c_size_t(0)
+    _check(_lib.pr_state_size(h, ctypes.byref(size)), h)
+    buf = np.zeros(size.value, dtype=np.uint8)
+    _check(_lib.pr_export_state(h, buf.ctypes.data, buf.nbytes), h)
+    return buf
+
+
+def pr_import_state(h: int, buf) -> None:
+    _check(_lib.pr_import_state(h, buf.ctypes.data, buf.nbytes), h)
+
+
+def pr_state_header_of(buf) -> pr_state_header:
+    return pr_state_header.from_buffer_copy(bytes(buf[:ctypes.sizeof(pr_state_header)]))
 
 
 def pr_selftest_wait(stream: int = 0) -> tuple[int, float]:

@@ -67,7 +67,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     if not shutil.which("gcc"):
         pytest.skip("gcc not available")
     from paper_1703_02283_gb300 import pthroot as P
-    classes = {"pr_options": P.pr_options, "pr_stats_t": P.pr_stats_t, "pr_batch_stats_t": P.pr_batch_stats_t}
+    classes = {"pr_options": P.pr_options, "pr_stats_t": P.pr_stats_t, "pr_batch_stats_t": P.pr_batch_stats_t,
+               "pr_state_header": P.pr_state_header}
     fields = {st: [f for f, _ in cls._fields_] for st, cls in classes.items()}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pthroot.h"', "int main(void) {"]
     for st, fs in fields.items():
