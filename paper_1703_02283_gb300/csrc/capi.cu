@@ -167,6 +167,9 @@ pr_status ensure_slices(pr_handle h, Mat& m) {
 // One matrix product P = X Y (X, Y symmetric, or Y given transposed in its BF16 copy) at the requested
 // precision, with the fused epilogue described by o.
 pr_status product(pr_handle h, int prec, Mat& X, Mat& Y, Mode mode, const Out& o) {
+  const pr::NvtxRange trace(prec == PR_EMU64 ? (mode == Mode::Sym ? "product EMU64 sym" : "product EMU64 full")
+                            : prec == PR_BF16 ? (mode == Mode::Sym ? "product BF16 sym" : "product BF16 full")
+                                              : (mode == Mode::Sym ? "product FP64 sym" : "product FP64 full"));
   const int n = (int)h->n;
   const double flops = mode == Mode::Sym ? sym_flops(n) : full_flops(n);
   Epilogue e;
@@ -992,9 +995,12 @@ pr_status pr_iterate(pr_handle h, int max_steps, int precision, double tol, int*
   s = ensure_state(h, precision);
   if (s != PR_OK) return s;
 
+  const pr::NvtxRange trace_call("pr_iterate");
   int steps = 0;
   int stop = -1;
   while (true) {
+    const pr::NvtxRange trace_it(precision == PR_EMU64 ? "iteration EMU64"
+                                 : precision == PR_BF16 ? "iteration BF16" : "iteration FP64");
     if (h->form == PR_FORM_NS || h->form == PR_FORM_LITERAL) {
       double r;
       s = h->form == PR_FORM_NS ? ns_residual(h, precision, &r) : literal_residual(h, precision, &r);

@@ -605,6 +605,7 @@ pr_status pr_batch_solve(pr_batch b, int precision, double tol, int* iterations,
   PB_CK(b, cudaMemcpyAsync(b->d_dstate + hist_len + 8, b->h_dstate + hist_len + 8, sizeof(double),
                            cudaMemcpyHostToDevice, b->stream));
   PB_CK(b, cudaMemsetAsync(b->ctl.loops, 0, sizeof(int), b->stream));  // the pass limit is per solve
+  const pr::NvtxRange trace("pr_batch_solve graph");
   PB_CK(b, cudaGraphLaunch(b->exec, b->stream));
   PB_CK(b, cudaMemcpyAsync(b->h_state, b->d_state, (4 * (size_t)count + 1) * sizeof(int), cudaMemcpyDeviceToHost,
                            b->stream));

@@ -11,7 +11,18 @@
 
 #include "../../include/pthroot.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace pr {
+
+// An NVTX range for the scope of the object (tracing tools show the library's iterations, products and
+// batch solves on the host timeline; without a tool attached a push/pop costs a few nanoseconds).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Fused epilogue of one matrix product P = X Y, applied to every computed element (i, j). In symmetric
 // mode only elements with i <= j are computed and each is also stored at (j, i).
