@@ -52,6 +52,7 @@ struct pr_batch_s {
   int K = 0;   // largest order
   int ld = 0;  // leading dimension of the packed buffers (K rounded up to 8)
   int pmax = 0;  // largest root of a coupled-form matrix
+  bool has_p3 = false;  // some matrix has p = 3 (its update takes two products, update_p3)
   int hcap = 0;  // history entries per matrix (max_iter + 2)
   cudaStream_t stream = nullptr;
   int device = 0;
@@ -160,36 +161,61 @@ pr_status stage(pr_batch b, Buf& Xb, Buf& Yb, const BatchStage& sp, const StageO
   return PR_OK;
 }
 
-BatchStage spec(int full, int form, int pcmp, int pj, int fresh, double a = 0.0, double bb = 0.0, double c = 0.0) {
+BatchStage spec(int full, int form, int pcmp, int pj, int fresh, double a = 0.0, double bb = 0.0, double c = 0.0,
+                int pskip = 0) {
   BatchStage st{};
   st.full = full;
   st.form = form;
   st.pcmp = pcmp;
   st.pj = pj;
   st.fresh_only = fresh;
+  st.pskip = pskip;
   st.a = a;
   st.b = bb;
   st.c = c;
   return st;
 }
 
-// Coupled chain of the coupled-form members: Y_1 = F src0, Y_j = F Y_{j-1}; the p-th product is written as
-// (out, out2 = ((p+1) I - out)/p) with its residual; intermediate products go to T0 / T1.
-pr_status chain(pr_batch b, Buf& F, Buf& src0, Buf& outM, Buf& outN, int fresh) {
+// Coupled chain of the coupled-form members (except those with p == pskip): Y_1 = F src0, Y_j = F Y_{j-1};
+// the p-th product is written as (out, out2 = ((p+1) I - out)/p) with its residual; intermediate products
+// go to T0 / T1.
+pr_status chain(pr_batch b, Buf& F, Buf& src0, Buf& outM, Buf& outN, int fresh, int pskip) {
   for (int j = 1; j <= b->pmax; ++j) {
+    if (j == pskip && j == b->pmax) break;
     Buf& src = j == 1 ? src0 : ((j - 1) & 1 ? b->T0 : b->T1);
     StageOut om;
     om.out = (j & 1) ? &b->T0 : &b->T1;
-    pr_status s = stage(b, F, src, spec(0, PR_FORM_COUPLED, 2, j, fresh), om);
+    pr_status s = stage(b, F, src, spec(0, PR_FORM_COUPLED, 2, j, fresh, 0.0, 0.0, 0.0, pskip), om);
     if (s != PR_OK) return s;
+    if (j == pskip) continue;
     StageOut of;
     of.out = &outM;
     of.out2 = &outN;
     of.partial = true;
-    s = stage(b, F, src, spec(0, PR_FORM_COUPLED, 1, j, fresh, (double)(j + 1) / j, -1.0 / j, 0.0), of);
+    s = stage(b, F, src, spec(0, PR_FORM_COUPLED, 1, j, fresh, (double)(j + 1) / j, -1.0 / j, 0.0, pskip), of);
     if (s != PR_OK) return s;
   }
   return PR_OK;
+}
+
+// p = 3 members: M' = N^3 M = L R with L = (4M - M^2) / 27 and R = 16I - 8M + M^2, two products (as the
+// single-matrix path does). The element-wise step runs over every packed row: rows of other matrices in
+// T0 hold nothing live at this point of the iteration.
+pr_status update_p3(pr_batch b, Buf& outM, Buf& outN) {
+  StageOut s1;
+  s1.out = &b->T0;
+  s1.out2 = &b->T1;
+  s1.cin = b->M.f;
+  pr_status s = stage(b, b->M, b->M, spec(0, PR_FORM_COUPLED, 1, 3, 0, 16.0, 1.0, -8.0), s1);
+  if (s != PR_OK) return s;
+  PB_CK(b, pr::lincomb(b->M.f, b->T0.f, (int64_t)b->R * b->ld, 4.0, -1.0, 27.0, b->T0.f, b->stream));
+  b->cnt += 1;
+  b->T0.sl_valid = false;
+  StageOut s2;
+  s2.out = &outM;
+  s2.out2 = &outN;
+  s2.partial = true;
+  return stage(b, b->T0, b->T1, spec(0, PR_FORM_COUPLED, 1, 3, 0, 4.0 / 3.0, -1.0 / 3.0, 0.0), s2);
 }
 
 // One iteration of every iterating matrix: the Newton-Schulz residuals, the stop rules, the updates
@@ -211,7 +237,8 @@ pr_status iteration(pr_batch b, bool last) {
   StageOut x;
   x.out = &b->Xn;
   s = stage(b, b->X, b->N, spec(0, PR_FORM_COUPLED, 0, 0, 0), x);
-  if (s == PR_OK) s = chain(b, b->N, b->M, b->Mn, b->Nn, 0);
+  if (s == PR_OK && b->has_p3) s = update_p3(b, b->Mn, b->Nn);
+  if (s == PR_OK) s = chain(b, b->N, b->M, b->Mn, b->Nn, 0, b->has_p3 ? 3 : 0);
   if (s != PR_OK) return s;
   std::swap(b->X, b->Xn);
   std::swap(b->M, b->Mn);
@@ -248,7 +275,7 @@ pr_status build_graph(pr_batch b) {
   invalidate_slices(b);
   pr_status s = capture(b->graph, nullptr, 0, [&]() {
     pr_status r = ensure_slices(b, b->A);
-    return r == PR_OK ? chain(b, b->X, b->A, b->M, b->N, 1) : r;
+    return r == PR_OK ? chain(b, b->X, b->A, b->M, b->N, 1, 0) : r;
   });
   b->launches_pro = b->cnt;
   // The prologue is one chain of nodes: the while loop follows its last node.
@@ -454,6 +481,7 @@ pr_status pr_batch_init(pr_batch* out, int count, const int64_t* n, const int* p
     b->row0[m] = row;
     b->form[m] = p[m] == 1 ? PR_FORM_NS : PR_FORM_COUPLED;
     if (p[m] > 1) b->pmax = std::max(b->pmax, p[m]);
+    if (p[m] == 3) b->has_p3 = true;
     row += (int)n[m];
   }
   auto bail = [&](pr_status code) {

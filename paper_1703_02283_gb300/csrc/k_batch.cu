@@ -24,6 +24,7 @@ __device__ __forceinline__ bool stage_member(const BatchCtl& c, const BatchStage
   if (st.pcmp == 1 && p != st.pj) return false;
   if (st.pcmp == 2 && p <= st.pj) return false;
   if (st.fresh_only && c.hlen[m] != 0) return false;
+  if (st.pskip != 0 && p == st.pskip) return false;
   return true;
 }
 

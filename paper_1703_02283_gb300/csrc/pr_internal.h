@@ -134,6 +134,9 @@ cudaError_t init_c0_eq3(const double* A, int n, double inv_s, double* X, cudaStr
 cudaError_t set_scaled_identity(double* X, int n, double c, cudaStream_t s);
 // out = a * I + b * in
 cudaError_t axpby_identity(const double* in, int n, double a, double b, double* out, cudaStream_t s);
+// out[e] = (a x[e] + b y[e]) / d for e < total (out may alias x or y)
+cudaError_t lincomb(const double* x, const double* y, int64_t total, double a, double b, double d, double* out,
+                    cudaStream_t s);
 // out = (in + in^T) / 2 (out != in)
 cudaError_t symmetrize(const double* in, int n, double* out, cudaStream_t s);
 // *result = sqrt(sum of partial[0..count)) in a fixed order
@@ -230,12 +233,14 @@ struct BatchCtl {
   const int* err;
 };
 // Membership of a product stage: matrices of one form that are still iterating, optionally with p == pj
-// (pcmp 1) or p > pj (pcmp 2), optionally only those without a residual yet (fresh_only).
+// (pcmp 1) or p > pj (pcmp 2), optionally only those without a residual yet (fresh_only), and never those
+// with p == pskip (0: none).
 struct BatchStage {
   int full;         // 0: symmetric-mode work items, 1: full
   int form;         // PR_FORM_NS or PR_FORM_COUPLED
   int pcmp, pj;
   int fresh_only;
+  int pskip;
   int slot;         // timing slot of the product launch
   double a, b, c;   // epilogue coefficients of the members
 };

@@ -196,7 +196,7 @@ def test_batch_full_size_sampled():
 def test_batch_stats_count_every_product():
     # Per matrix of order n and k iterations: Newton-Schulz (p = 1) runs k + 1 residual products A X (full,
     # 2 n^3 flops) and k updates X T (symmetric, n^2 (n + 1)); the coupled form runs p products for M_0 and
-    # p + 1 per iteration, all symmetric.
+    # p + 1 per iteration (3 for p = 3: X N, M^2, L R), all symmetric.
     cases, ps = make_batch(6, 64, 300, 1e3, 77)
     mats = [torch.from_numpy(c.A).to(DEV) for c in cases]
     b = P.pr_batch_init(mats, ps, P.pr_default_options(), torch.cuda.current_stream(DEV).cuda_stream)
@@ -214,8 +214,9 @@ def test_batch_stats_count_every_product():
             products += 2 * k + 1
             flops += (k + 1) * full + k * sym
         else:
-            products += p + k * (p + 1)
-            flops += (p + k * (p + 1)) * sym
+            per = 3 if p == 3 else p + 1
+            products += p + k * per
+            flops += (p + k * per) * sym
     assert st["products"] == products
     assert st["product_flops"] == pytest.approx(flops, rel=1e-12)
     assert st["stages_timed"] == st["stages"] and st["stage_flops_timed"] == st["product_flops"]

@@ -203,6 +203,28 @@ def test_p4_chain_uses_squares():
     assert abs(d - info.iterations) <= 1
 
 
+@pytest.mark.parametrize("prec", [P.PR_FP64, P.PR_EMU64])
+def test_p3_update_takes_two_products(prec):
+    # p = 3: M' = N^3 M is formed as L R, L = (4M - M^2)/27, R = 16I - 8M + M^2 (two products, plus X N);
+    # M_0 = X^3 A keeps the plain chain of three. Same iterates as the oracle's N (N (N M)) up to rounding.
+    case = W.spd_from_spectrum(140, 0.02, 13)
+    stream = torch.cuda.current_stream(DEV).cuda_stream
+    h = P.pr_init(torch.from_numpy(case.A).to(DEV), 140, 3, P.pr_default_options(), stream)
+    try:
+        st, d = P.pr_iterate(h, 100, prec, 1e-12)
+        s = P.pr_stats(h)
+        C = torch.empty((140, 140), dtype=torch.float64, device=DEV)
+        P.pr_result(h, C)
+    finally:
+        P.pr_destroy(h)
+    assert s["gemms"] == 3 + 3 * s["iterations"]
+    Co, info = O.solve(case.A, 3, tol=1e-12)
+    Z = O.closed_form_root(case.Q, case.lam, 3)
+    bound = max(1e-12, 10 * O.forward_error(Co, Z))
+    assert O.forward_error(C.cpu().numpy(), Z) <= bound and O.forward_error(C.cpu().numpy(), Co) <= bound
+    assert abs(d - info.iterations) <= 1
+
+
 def test_bounded_wait_expires_and_context_survives():
     # A device wait that nothing completes runs out after its limit and is reported as PR_ETIMEOUT; the
     # next products on the same context are still correct.
