@@ -322,7 +322,7 @@ pr_status coupled_update(pr_handle h, int prec) {
   // carries them over instead of re-forming M from X.
   last.out_master = last.out2_master = !(lowp(prec) && h->opt.reanchor);
   if (p == 3 && !lowp(prec)) {
-    // N^3 M = M (4I - M)^3 / 27 = L R with L = (4M - M^2) / 27 and R = 16I - 8M + M^2: two products
+    // N^3 M = M (4I - M)^3 / 27 = L R with L = 4M - M^2 and R = (16I - 8M + M^2) / 27: two products
     // instead of three (every factor is a polynomial in M, hence in A). The first product gives M^2 and, in
     // its epilogue, R; L follows element by element. (Low precision keeps the plain chain: its FP64 copy of
     // M, which L needs, is not kept.)
@@ -330,12 +330,12 @@ pr_status coupled_update(pr_handle h, int prec) {
     o.out = &h->T0;
     o.out2 = &h->T1;
     o.cin = h->M.f;
-    o.a = 16.0;
-    o.b = 1.0;
-    o.c = -8.0;
+    o.a = 16.0 / 27.0;
+    o.b = 1.0 / 27.0;
+    o.c = -8.0 / 27.0;
     s = product(h, prec, h->M, h->M, Mode::Sym, o);
     if (s != PR_OK) return s;
-    PR_CK(h, pr::lincomb(h->M.f, h->T0.f, h->n * h->n, 4.0, -1.0, 27.0, h->T0.f, h->stream));
+    PR_CK(h, pr::lincomb(h->M.f, h->T0.f, h->n * h->n, 4.0, -1.0, h->T0.f, h->stream));
     h->st.launches += 1;
     h->T0.sl_valid = false;
     s = product(h, prec, h->T0, h->T1, Mode::Sym, last);

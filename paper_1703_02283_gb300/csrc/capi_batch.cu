@@ -61,6 +61,7 @@ struct pr_batch_s {
   Buf A, X, Xn, M, Mn, N, Nn, T0, T1;
   double* result = nullptr;  // packed results
   int* row_n = nullptr;      // order of the matrix owning each packed row (-1 once it stopped)
+  int* row_n_p3 = nullptr;   // the same for rows of p = 3 matrices, -1 on every other row
   double* partial = nullptr;
   int4* items = nullptr;     // the current stage's work list
   int* err = nullptr;
@@ -119,6 +120,14 @@ pr_status bfail(pr_batch b, pr_status code, const std::string& msg) {
 pr_status ensure_slices(pr_batch b, Buf& x) {
   if (x.sl_valid) return PR_OK;
   PB_CK(b, pr::slice_rows(x.f, b->R, b->K, b->ld, pr::emu_ld(b->K), b->S, b->row_n, x.sl, x.ex, b->stream));
+  b->cnt += 1;
+  x.sl_valid = true;
+  return PR_OK;
+}
+
+// Digit planes of the rows of p = 3 matrices only; x counts as sliced until the caller says otherwise.
+pr_status slice_p3_rows(pr_batch b, Buf& x) {
+  PB_CK(b, pr::slice_rows(x.f, b->R, b->K, b->ld, pr::emu_ld(b->K), b->S, b->row_n_p3, x.sl, x.ex, b->stream));
   b->cnt += 1;
   x.sl_valid = true;
   return PR_OK;
@@ -198,24 +207,27 @@ pr_status chain(pr_batch b, Buf& F, Buf& src0, Buf& outM, Buf& outN, int fresh, 
   return PR_OK;
 }
 
-// p = 3 members: M' = N^3 M = L R with L = (4M - M^2) / 27 and R = 16I - 8M + M^2, two products (as the
-// single-matrix path does). The element-wise step runs over every packed row: rows of other matrices in
-// T0 hold nothing live at this point of the iteration.
+// p = 3 members: M' = N^3 M = L R with L = 4M - M^2 and R = (16I - 8M + M^2) / 27, two products (as the
+// single-matrix path does). L is formed, and L and R are sliced, on the rows of p = 3 matrices only.
 pr_status update_p3(pr_batch b, Buf& outM, Buf& outN) {
   StageOut s1;
   s1.out = &b->T0;
   s1.out2 = &b->T1;
   s1.cin = b->M.f;
-  pr_status s = stage(b, b->M, b->M, spec(0, PR_FORM_COUPLED, 1, 3, 0, 16.0, 1.0, -8.0), s1);
+  pr_status s = stage(b, b->M, b->M, spec(0, PR_FORM_COUPLED, 1, 3, 0, 16.0 / 27.0, 1.0 / 27.0, -8.0 / 27.0), s1);
   if (s != PR_OK) return s;
-  PB_CK(b, pr::lincomb(b->M.f, b->T0.f, (int64_t)b->R * b->ld, 4.0, -1.0, 27.0, b->T0.f, b->stream));
+  PB_CK(b, pr::batch_lincomb(b->ctl, 3, b->M.f, b->T0.f, 4.0, -1.0, b->T0.f, b->stream));
   b->cnt += 1;
-  b->T0.sl_valid = false;
+  s = slice_p3_rows(b, b->T0);
+  if (s == PR_OK) s = slice_p3_rows(b, b->T1);
+  if (s != PR_OK) return s;
   StageOut s2;
   s2.out = &outM;
   s2.out2 = &outN;
   s2.partial = true;
-  return stage(b, b->T0, b->T1, spec(0, PR_FORM_COUPLED, 1, 3, 0, 4.0 / 3.0, -1.0 / 3.0, 0.0), s2);
+  s = stage(b, b->T0, b->T1, spec(0, PR_FORM_COUPLED, 1, 3, 0, 4.0 / 3.0, -1.0 / 3.0, 0.0), s2);
+  b->T0.sl_valid = b->T1.sl_valid = false;  // their planes cover p = 3 rows only
+  return s;
 }
 
 // One iteration of every iterating matrix: the Newton-Schulz residuals, the stop rules, the updates
@@ -347,13 +359,17 @@ pr_status load(pr_batch b, const double* const* A, const char* who) {
   for (int m = 0; m < count; ++m)
     if (!A[m]) return bfail(b, PR_EINVAL, std::string(who) + ": NULL matrix");
   {
-    std::vector<int> rn(b->R);
+    std::vector<int> rn(b->R), rn3(b->R);
     for (int m = 0; m < count; ++m)
-      for (int r = 0; r < b->n[m]; ++r) rn[b->row0[m] + r] = b->n[m];
+      for (int r = 0; r < b->n[m]; ++r) {
+        rn[b->row0[m] + r] = b->n[m];
+        rn3[b->row0[m] + r] = b->p[m] == 3 ? b->n[m] : -1;
+      }
     std::vector<int> st0(4 * (size_t)count, 0);
     std::fill(st0.begin(), st0.begin() + count, 1);               // active
     std::fill(st0.begin() + count, st0.begin() + 2 * count, -1);  // status
     PB_CK(b, cudaMemcpyAsync(b->row_n, rn.data(), rn.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    PB_CK(b, cudaMemcpyAsync(b->row_n_p3, rn3.data(), rn3.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
     PB_CK(b, cudaMemcpyAsync(b->d_state, st0.data(), st0.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
     PB_CK(b, cudaStreamSynchronize(b->stream));
   }
@@ -424,7 +440,7 @@ pr_status pr_batch_destroy(pr_batch b) {
     if (x->sl) cudaFree(x->sl);
     if (x->ex) cudaFree(x->ex);
   }
-  for (void* q : {(void*)b->result, (void*)b->row_n, (void*)b->partial, (void*)b->items, (void*)b->err,
+  for (void* q : {(void*)b->result, (void*)b->row_n, (void*)b->row_n_p3, (void*)b->partial, (void*)b->items, (void*)b->err,
                   (void*)b->scratch, (void*)b->d_static, (void*)b->d_items_all, (void*)b->d_state, (void*)b->d_dstate,
                   (void*)b->d_stage, (void*)b->mats, (void*)b->tstamp, (void*)b->flops_pending, (void*)b->tA,
                   (void*)b->tC, (void*)b->scal, (void*)b->work})
@@ -507,6 +523,7 @@ pr_status pr_batch_init(pr_batch* out, int count, const int64_t* n, const int* p
   }
   PB_INIT_CK(cudaMalloc((void**)&b->result, fbytes));
   PB_INIT_CK(cudaMalloc((void**)&b->row_n, (size_t)b->R * sizeof(int)));
+  PB_INIT_CK(cudaMalloc((void**)&b->row_n_p3, (size_t)b->R * sizeof(int)));
   // Every matrix's work items (symmetric and full) and the device-side control state.
   std::vector<int4> isym, ifull;
   std::vector<int> stat(9 * (size_t)count);
@@ -597,6 +614,7 @@ pr_status pr_batch_init(pr_batch* out, int count, const int64_t* n, const int* p
     c.flops_pending = b->flops_pending;
     c.result = b->result;
     c.row_n = b->row_n;
+    c.row_n2 = b->row_n_p3;
     c.err = b->err;
   }
   PB_INIT_CK(cudaMalloc((void**)&b->tA, (size_t)K * K * sizeof(double)));

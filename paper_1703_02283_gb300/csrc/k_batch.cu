@@ -167,7 +167,10 @@ __global__ void k_batch_decide(BatchCtl c, const double* __restrict__ X, pr_opti
   const int n = c.n[m], r0 = c.row0[m];
   const size_t base = (size_t)r0 * c.ld, total = (size_t)n * c.ld;
   for (size_t e = threadIdx.x; e < total; e += blockDim.x) c.result[base + e] = X[base + e];
-  for (int r = threadIdx.x; r < n; r += blockDim.x) c.row_n[r0 + r] = -1;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    c.row_n[r0 + r] = -1;
+    if (c.row_n2) c.row_n2[r0 + r] = -1;
+  }
   if (threadIdx.x == 0) {
     c.status[m] = stop;
     c.active[m] = 0;
@@ -195,6 +198,19 @@ __global__ void __launch_bounds__(kCtlThreads) k_batch_advance(BatchCtl c, cudaG
   }
 }
 
+__global__ void k_batch_lincomb(BatchCtl c, int pj, const double* x, const double* y, double a, double b,
+                                double* out) {
+  const int m = blockIdx.x;
+  if (!c.active[m] || c.p[m] != pj) return;  // uniform over the block
+  const int n = c.n[m];
+  const size_t base = (size_t)c.row0[m] * c.ld;
+  for (int r = 0; r < n; ++r)
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      const size_t e = base + (size_t)r * c.ld + k;
+      out[e] = fma(a, x[e], b * y[e]);
+    }
+}
+
 __global__ void k_batch_harvest(BatchCtl c, int nslots) {
   if (threadIdx.x == 0)
     for (int k = 0; k < nslots; ++k) harvest_slot(c, k);
@@ -219,6 +235,12 @@ cudaError_t batch_decide(const BatchCtl& c, const double* X, const pr_options& o
 
 cudaError_t batch_advance(const BatchCtl& c, cudaGraphConditionalHandle h, int set_cond, int limit, cudaStream_t s) {
   k_batch_advance<<<1, kCtlThreads, 0, s>>>(c, h, set_cond, limit);
+  return cudaGetLastError();
+}
+
+cudaError_t batch_lincomb(const BatchCtl& c, int pj, const double* x, const double* y, double a, double b,
+                          double* out, cudaStream_t s) {
+  k_batch_lincomb<<<c.count, 256, 0, s>>>(c, pj, x, y, a, b, out);
   return cudaGetLastError();
 }
 

@@ -122,11 +122,10 @@ __global__ void k_axpby_identity(const double* __restrict__ in, int n, double a,
     out[e] = ((e / n == e % n) ? a : 0.0) + b * in[e];
 }
 
-// out = (a x + b y) / d element by element: one rounding for a x + b y when a x is exact (a a power of
-// two), one for the division. out may be x or y.
-__global__ void k_lincomb(const double* x, const double* y, int64_t total, double a, double b, double d, double* out) {
+// out = a x + b y element by element, as fma(a, x, b y) (one rounding when b y is exact). out may be x or y.
+__global__ void k_lincomb(const double* x, const double* y, int64_t total, double a, double b, double* out) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
-    out[e] = fma(a, x[e], b * y[e]) / d;
+    out[e] = fma(a, x[e], b * y[e]);
 }
 
 __global__ void k_symmetrize(const double* __restrict__ in, int n, double* __restrict__ out) {
@@ -206,9 +205,8 @@ cudaError_t axpby_identity(const double* in, int n, double a, double b, double* 
   return cudaGetLastError();
 }
 
-cudaError_t lincomb(const double* x, const double* y, int64_t total, double a, double b, double d, double* out,
-                    cudaStream_t s) {
-  k_lincomb<<<grid_for(total), kThreads, 0, s>>>(x, y, total, a, b, d, out);
+cudaError_t lincomb(const double* x, const double* y, int64_t total, double a, double b, double* out, cudaStream_t s) {
+  k_lincomb<<<grid_for(total), kThreads, 0, s>>>(x, y, total, a, b, out);
   return cudaGetLastError();
 }
 

@@ -134,9 +134,8 @@ cudaError_t init_c0_eq3(const double* A, int n, double inv_s, double* X, cudaStr
 cudaError_t set_scaled_identity(double* X, int n, double c, cudaStream_t s);
 // out = a * I + b * in
 cudaError_t axpby_identity(const double* in, int n, double a, double b, double* out, cudaStream_t s);
-// out[e] = (a x[e] + b y[e]) / d for e < total (out may alias x or y)
-cudaError_t lincomb(const double* x, const double* y, int64_t total, double a, double b, double d, double* out,
-                    cudaStream_t s);
+// out[e] = fma(a, x[e], b y[e]) for e < total (out may alias x or y)
+cudaError_t lincomb(const double* x, const double* y, int64_t total, double a, double b, double* out, cudaStream_t s);
 // out = (in + in^T) / 2 (out != in)
 cudaError_t symmetrize(const double* in, int n, double* out, cudaStream_t s);
 // *result = sqrt(sum of partial[0..count)) in a fixed order
@@ -230,6 +229,7 @@ struct BatchCtl {
   // results
   double* result;
   int* row_n;
+  int* row_n2;     // if set: a second per-row order array (-1 for rows not sliced) that stops also clear
   const int* err;
 };
 // Membership of a product stage: matrices of one form that are still iterating, optionally with p == pj
@@ -255,6 +255,10 @@ cudaError_t batch_decide(const BatchCtl& c, const double* X, const pr_options& o
 cudaError_t batch_advance(const BatchCtl& c, cudaGraphConditionalHandle h, int set_cond, int limit, cudaStream_t s);
 // Adds the last launch of every timing slot to the tally.
 cudaError_t batch_harvest(const BatchCtl& c, int nslots, cudaStream_t s);
+// out = fma(a, x, b y) (as lincomb) on the rows and columns of every iterating matrix with root pj, in the
+// packed layout (leading dimension c.ld); other elements are left as they are.
+cudaError_t batch_lincomb(const BatchCtl& c, int pj, const double* x, const double* y, double a, double b,
+                          double* out, cudaStream_t s);
 
 // Records the text returned by pr_last_error(NULL) for a failing call that has no handle.
 void set_handleless_error(const char* msg);
