@@ -198,14 +198,18 @@ __global__ void __launch_bounds__(kCtlThreads) k_batch_advance(BatchCtl c, cudaG
   }
 }
 
-__global__ void k_batch_lincomb(BatchCtl c, int pj, const double* x, const double* y, double a, double b,
-                                double* out) {
+// Block (m, g): warps take the rows r = 8 g + w, 8 g + w + 8 G, ... of matrix m (G row groups), lanes the
+// columns.
+constexpr int kLincombGroups = 16;
+
+__global__ void __launch_bounds__(256) k_batch_lincomb(BatchCtl c, int pj, const double* x, const double* y,
+                                                       double a, double b, double* out) {
   const int m = blockIdx.x;
   if (!c.active[m] || c.p[m] != pj) return;  // uniform over the block
-  const int n = c.n[m];
+  const int n = c.n[m], lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const size_t base = (size_t)c.row0[m] * c.ld;
-  for (int r = 0; r < n; ++r)
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+  for (int r = 8 * blockIdx.y + w; r < n; r += 8 * kLincombGroups)
+    for (int k = lane; k < n; k += 32) {
       const size_t e = base + (size_t)r * c.ld + k;
       out[e] = fma(a, x[e], b * y[e]);
     }
@@ -240,7 +244,7 @@ cudaError_t batch_advance(const BatchCtl& c, cudaGraphConditionalHandle h, int s
 
 cudaError_t batch_lincomb(const BatchCtl& c, int pj, const double* x, const double* y, double a, double b,
                           double* out, cudaStream_t s) {
-  k_batch_lincomb<<<c.count, 256, 0, s>>>(c, pj, x, y, a, b, out);
+  k_batch_lincomb<<<dim3(c.count, kLincombGroups), 256, 0, s>>>(c, pj, x, y, a, b, out);
   return cudaGetLastError();
 }
 
