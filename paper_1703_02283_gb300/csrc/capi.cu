@@ -58,6 +58,8 @@ struct pr_handle_s {
   int4* emu_items[2] = {nullptr, nullptr};  // PR_EMU64 work lists: symmetric, full products
   int emu_nitems[2] = {0, 0};
   long long* emu_scratch = nullptr;          // PR_EMU64 first-pass totals (pr::emu_scratch_bytes())
+  long long* emu_split = nullptr;            // PR_EMU64 half totals of tiles split over K (pr::emu_launch_list)
+  int* emu_split_cnt = nullptr;
 
   // The input, the iterate X, the carried product M and operand N of the coupled form, their next
   // values, and two scratch products.
@@ -219,7 +221,7 @@ pr_status product(pr_handle h, int prec, Mat& X, Mat& Y, Mode mode, const Out& o
     case PR_EMU64:
       PR_CK(h, pr::gemm_emu(X.sl, X.ex, Y.sl, Y.ex, n, h->eld, h->S, mode, o.transpose,
                             h->emu_items[mode == Mode::Sym ? 0 : 1], h->emu_nitems[mode == Mode::Sym ? 0 : 1], e,
-                            h->emu_scratch, h->err_word(), h->stream));
+                            h->emu_scratch, h->emu_split, h->emu_split_cnt, h->err_word(), h->stream));
       h->lp_stale = true;
       break;
     default:
@@ -630,6 +632,8 @@ pr_status matmul(int precision, int S, const double* X, const double* Y, int64_t
   int *err = nullptr, *eX = nullptr, *eY = nullptr;
   int4* items = nullptr;
   long long* scratch = nullptr;
+  long long* split = nullptr;
+  int* split_cnt = nullptr;
   std::vector<int4> hitems;
   cudaError_t e = cudaSuccess;
   int word = 0;
@@ -660,19 +664,27 @@ pr_status matmul(int precision, int S, const double* X, const double* Y, int64_t
       step(pr::gemm_bf16_tc(bX, bY, ni, ldl, mode, false, ep, err, s));
     } else {
       __half *hX = reinterpret_cast<__half*>(bX), *hY = reinterpret_cast<__half*>(bY);
-      pr::emu_tile_list(0, ni, mode, hitems);
+      pr::emu_launch_list(ni, mode, hitems);
+      const int slots = pr::emu_split_slots(ni, mode);
       step(cudaMalloc((void**)&items, hitems.size() * sizeof(int4)));
       step(cudaMalloc((void**)&scratch, pr::emu_scratch_bytes()));
+      if (slots > 0) {
+        step(cudaMalloc((void**)&split, pr::emu_split_bytes(slots)));
+        step(cudaMalloc((void**)&split_cnt, pr::emu_split_counters(slots) * sizeof(int)));
+        step(cudaMemsetAsync(split_cnt, 0, pr::emu_split_counters(slots) * sizeof(int), s));
+      }
       step(cudaMemcpyAsync(items, hitems.data(), hitems.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
       step(pr::slice(dX, ni, eld, S, hX, eX, s));
       step(pr::slice(dY, ni, eld, S, hY, eY, s));
-      step(pr::gemm_emu(hX, eX, hY, eY, ni, eld, S, mode, false, items, (int)hitems.size(), ep, scratch, err, s));
+      step(pr::gemm_emu(hX, eX, hY, eY, ni, eld, S, mode, false, items, (int)hitems.size(), ep, scratch, split,
+                        split_cnt, err, s));
     }
     step(cudaMemcpyAsync(P, dP, bytes, cudaMemcpyDefault, s));
     step(cudaMemcpyAsync(&word, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     step(cudaStreamSynchronize(s));
   }
-  for (void* q : {(void*)dX, (void*)dY, (void*)dP, (void*)bX, (void*)bY, (void*)err, (void*)eX, (void*)eY, (void*)items, (void*)scratch})
+  for (void* q : {(void*)dX, (void*)dY, (void*)dP, (void*)bX, (void*)bY, (void*)err, (void*)eX, (void*)eY, (void*)items,
+                  (void*)scratch, (void*)split, (void*)split_cnt})
     if (q) cudaFree(q);
   if (e != cudaSuccess) return cuda_fail(nullptr, "pr_matmul", e);
   if (word != 0)
@@ -721,6 +733,8 @@ pr_status pr_destroy(pr_handle h) {
   for (int4* it : h->emu_items)
     if (it) cudaFree(it);
   if (h->emu_scratch) cudaFree(h->emu_scratch);
+  if (h->emu_split) cudaFree(h->emu_split);
+  if (h->emu_split_cnt) cudaFree(h->emu_split_cnt);
   if (h->hpin) cudaFreeHost(h->hpin);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   delete h;
@@ -792,14 +806,21 @@ pr_status pr_init(pr_handle* out, const double* A, int64_t n, int p, const pr_op
   PR_INIT_CK(cudaMalloc((void**)&h->scal, sizeof(double) * 8));
   PR_INIT_CK(cudaMemset(h->scal, 0, sizeof(double) * 8));
   PR_INIT_CK(cudaMallocHost((void**)&h->hpin, sizeof(double) * 8));
+  int slots = 0;
   for (int k = 0; k < 2; ++k) {  // the PR_EMU64 work lists of this order (symmetric, full)
     std::vector<int4> items;
-    pr::emu_tile_list(0, (int)n, k == 0 ? Mode::Sym : Mode::Full, items);
+    pr::emu_launch_list((int)n, k == 0 ? Mode::Sym : Mode::Full, items);
+    slots = std::max(slots, pr::emu_split_slots((int)n, k == 0 ? Mode::Sym : Mode::Full));
     h->emu_nitems[k] = (int)items.size();
     PR_INIT_CK(cudaMalloc((void**)&h->emu_items[k], items.size() * sizeof(int4)));
     PR_INIT_CK(cudaMemcpy(h->emu_items[k], items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
   }
   PR_INIT_CK(cudaMalloc((void**)&h->emu_scratch, pr::emu_scratch_bytes()));
+  if (slots > 0) {
+    PR_INIT_CK(cudaMalloc((void**)&h->emu_split, pr::emu_split_bytes(slots)));
+    PR_INIT_CK(cudaMalloc((void**)&h->emu_split_cnt, pr::emu_split_counters(slots) * sizeof(int)));
+    PR_INIT_CK(cudaMemset(h->emu_split_cnt, 0, pr::emu_split_counters(slots) * sizeof(int)));
+  }
 #undef PR_INIT_CK
   pr_status s = pr_load(h, A);
   if (s != PR_OK) return bail(s);

@@ -58,7 +58,8 @@ constexpr int A_BYTES = 2 * A_GROUP, STAGE_BYTES = A_BYTES + 2 * B_GROUP;
 constexpr int NBARS = 2 * NSTAGE + 2 * NACC + 2 + 1;
 constexpr int SMEM_BYTES = 1024 + NSTAGE * STAGE_BYTES + 8 * NBARS + 16;
 constexpr int ACOL = NACC * EBN;         // TMEM column of the first X-plane buffer (after the accumulators)
-constexpr int SCRATCH_PER_CTA = EPI_WARPS * 32 * EPI_COLS;  // int64 totals of the first pass
+constexpr int SCRATCH_PER_CTA = 2 * EPI_WARPS * 32 * EPI_COLS;  // int64 totals: first pass (hi), then lo
+constexpr int SPLIT_PER_PART = 2 * EPI_WARPS * 32 * EPI_COLS;  // int64: (hi, lo) per element of a tile
 constexpr uint32_t kIdesc = ptx::idesc_f16_f32(EBM, EBN);
 static_assert(ACOL + 2 * SMAX * 8 <= 512, "tensor memory budget");
 static_assert(STAGE_BYTES % 1024 == 0 && SMEM_BYTES <= 232448, "shared memory");
@@ -160,7 +161,7 @@ struct EmuArgs {
   int ld;                // leading dimension of the FP64 outputs and of cin
   int ntiles;            // work items
   const int* ntiles_dev; // if set, the number of work items is read here (written by an earlier kernel)
-  const int4* items;     // (matrix, tile row, tile column, -) per work item
+  const int4* items;     // (matrix, tile row, tile column, part) per work item (part 0: the whole tile)
   const EmuMat* mats;    // per-matrix data; null: every item belongs to `one`
   EmuMat one;
   int transpose;         // full mode: store P^T
@@ -170,13 +171,23 @@ struct EmuArgs {
   long long* scratch;    // SCRATCH_PER_CTA int64 per CTA: the first pass's exact totals
   int* err;
   unsigned long long* tstamp;  // if set: [0] min over CTAs of the start time, [1] max of the end time (ns)
+  long long* split;      // split tiles: per slot, 2 parts x SPLIT_PER_PART exact totals (hi, lo pairs)
+  int* split_cnt;        // split tiles: per slot and epilogue warp, the parts finished so far (reset to 0)
 };
 
-__device__ __forceinline__ const EmuMat& item_of(const EmuArgs& a, int t, int& bi, int& bj) {
+// Item t: its matrix, tile, and the K steps [j0, j1) it covers. kpart = 0 is the whole tile; a tile split in
+// two has items with kpart = 1 + 2 slot + half, half 0 taking the first KS / 2 steps and half 1 the rest.
+__device__ __forceinline__ const EmuMat& item_of(const EmuArgs& a, int t, int& bi, int& bj, int& kpart, int& j0,
+                                                 int& j1) {
   const int4 it = a.items[t];
   bi = it.y;
   bj = it.z;
-  return a.mats ? a.mats[it.x] : a.one;
+  kpart = it.w;
+  const EmuMat& mt = a.mats ? a.mats[it.x] : a.one;
+  const int KS = (mt.n + EBK - 1) / EBK, h = KS >> 1;
+  j0 = kpart == 0 || ((kpart - 1) & 1) == 0 ? 0 : h;
+  j1 = kpart == 0 || ((kpart - 1) & 1) == 1 ? KS : h;
+  return mt;
 }
 
 // (H 2^64 + Lw) 2^E0 for a two's-complement 128-bit integer H:Lw, rounded once to the nearest double
@@ -291,12 +302,12 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
       int it = 0;
       bool stop = false;
       for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
-        int bi, bj;
-        const EmuMat& mt = item_of(args, t, bi, bj);
-        const int KS = (mt.n + EBK - 1) / EBK, ya = mt.row0 + bi * EBM, yb = mt.row0 + bj * EBN;
+        int bi, bj, kpart, j0, j1;
+        const EmuMat& mt = item_of(args, t, bi, bj, kpart, j0, j1);
+        const int ya = mt.row0 + bi * EBM, yb = mt.row0 + bj * EBN;
         for (int pass = 0; pass < 2 && !stop; ++pass) {
           const int ng = pass == 0 ? 1 : groups1;
-          for (int j = 0; j < KS; ++j, ++it) {
+          for (int j = j0; j < j1; ++j, ++it) {
             const int st = it % NSTAGE;
             if (*s_abort || !ptx::mbar_wait(empty0 + 8 * st, ((it / NSTAGE) & 1) ^ 1, args.err, 11)) {
               *s_abort = 1;
@@ -324,12 +335,11 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
       int it = 0;
       bool stop = false;
       for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
-        int bi, bj;
-        const EmuMat& mt = item_of(args, t, bi, bj);
-        const int KS = (mt.n + EBK - 1) / EBK;
+        int bi, bj, kpart, j0, j1;
+        item_of(args, t, bi, bj, kpart, j0, j1);
         for (int pass = 0; pass < 2 && !stop; ++pass) {
           const int np = pass == 0 ? min(S, 4) : S;
-          for (int j = 0; j < KS; ++j, ++it) {
+          for (int j = j0; j < j1; ++j, ++it) {
             const int st = it % NSTAGE, b = it & 1;
             if (*s_abort || !ptx::mbar_wait(full0 + 8 * st, (it / NSTAGE) & 1, args.err, 12) ||
                 (it >= 2 && !ptx::mbar_wait(empty0 + 8 * ((it - 2) % NSTAGE), ((it - 2) / NSTAGE) & 1, args.err, 13))) {
@@ -358,9 +368,9 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
       int it = 0;
       bool stop = false;
       for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
-        int bi, bj;
-        const EmuMat& mt = item_of(args, t, bi, bj);
-        const int KS = (mt.n + EBK - 1) / EBK;
+        int bi, bj, kpart, j0, j1;
+        item_of(args, t, bi, bj, kpart, j0, j1);
+        const int KS = j1 - j0;
         for (int pass = 0; pass < 2 && !stop; ++pass) {
           for (int j = 0; j < KS && !stop; ++j, ++it) {
             const int st = it % NSTAGE, b = it & 1;
@@ -427,9 +437,9 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
     uint32_t epar = 0u;  // per accumulator: parity of the drains taken so far
     bool stop = false;
     for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
-      int bi, bj;
-      const EmuMat& mt = item_of(args, t, bi, bj);
-      const int n = mt.n, row0 = mt.row0, KS = (n + EBK - 1) / EBK;
+      int bi, bj, kpart, j0, j1;
+      const EmuMat& mt = item_of(args, t, bi, bj, kpart, j0, j1);
+      const int n = mt.n, row0 = mt.row0, KS = j1 - j0;
       // Exact totals: the first pass gives hi = sum_{L<=5} V_L 2^(8(5-L)) (kept in scratch), the second
       // lo = sum_{L>=6} V_L 2^(8(9-L)); P = hi 2^-40 + lo 2^-72.
       long long acc[EPI_COLS];
@@ -482,6 +492,39 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
         }
       }
       if (stop) break;
+      const int tile = kpart == 0 ? t : (kpart - 1) >> 1;  // residual partials are indexed by tile, not by item
+      // The second pass's totals join the first's in the scratch, so that nothing of the step loop stays
+      // live through the tile end.
+      long long* scr_lo = scr + (size_t)EPI_COLS * (EPI_WARPS * 32);
+#pragma unroll
+      for (int c = 0; c < EPI_COLS; ++c) scr_lo[(size_t)c * (EPI_WARPS * 32)] = acc[c];
+      if (kpart != 0) {
+        // A tile split over K: this warp publishes its half's exact totals. The same warp of the other half
+        // covers the same elements; whichever of the two finishes second adds the other's totals to its own
+        // (integers, so the sum is exact and independent of the order) and applies the epilogue. Nobody
+        // waits: the first to finish just moves on.
+        const int half = (kpart - 1) & 1;
+        longlong2* pub = reinterpret_cast<longlong2*>(args.split) + ((size_t)tile * 2 + half) * (SPLIT_PER_PART / 2) +
+                         (ew * 32 + lane);
+        for (int c = 0; c < EPI_COLS; ++c)
+          pub[c * (EPI_WARPS * 32)] = make_longlong2(scr[(size_t)c * (EPI_WARPS * 32)], scr_lo[(size_t)c * (EPI_WARPS * 32)]);
+        __threadfence();
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) {
+          int* cnt = args.split_cnt + (size_t)tile * EPI_WARPS + ew;
+          last = atomicAdd(cnt, 1) == 1;
+          if (last) *cnt = 0;  // ready for the next launch
+        }
+        if (!__shfl_sync(0xffffffffu, last, 0)) continue;
+        __threadfence();
+        const longlong2* oth = pub + (half ? -1 : 1) * (ptrdiff_t)(SPLIT_PER_PART / 2);
+        for (int c = 0; c < EPI_COLS; ++c) {
+          const longlong2 o = __ldcg(oth + c * (EPI_WARPS * 32));
+          scr[(size_t)c * (EPI_WARPS * 32)] += o.x;
+          scr_lo[(size_t)c * (EPI_WARPS * 32)] += o.y;
+        }
+      }
       // Tile end: P = 2^(e_i + f_j - 72) (hi 2^32 + lo), then the fused epilogue (FP64 values, FP32 partials).
       const int i = bi * EBM + 32 * q + lane;
       const int ei = i < n ? args.ex[row0 + i] : 0;
@@ -489,7 +532,7 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
 #pragma unroll
       for (int c = 0; c < EPI_COLS; ++c) {
         const int jc = bj * EBN + EPI_COLS * h + c;
-        const long long hi = scr[(size_t)c * (EPI_WARPS * 32)], lo = acc[c];
+        const long long hi = scr[(size_t)c * (EPI_WARPS * 32)], lo = scr_lo[(size_t)c * (EPI_WARPS * 32)];
         if (i >= n || jc >= n || (SYM && i > jc)) continue;
         const unsigned long long lw0 = (unsigned long long)hi << 32, lw = lw0 + (unsigned long long)lo;
         const long long H = (hi >> 32) + (lo >> 63) + (lw < lw0 ? 1 : 0);
@@ -516,7 +559,7 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
       }
       if (e.partial) {
         for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        if (lane == 0) e.partial[(int64_t)t * EPI_WARPS + ew] = (double)part;
+        if (lane == 0) e.partial[(int64_t)tile * EPI_WARPS + ew] = (double)part;
       }
     }
   }
@@ -611,6 +654,33 @@ void emu_tile_list(int m, int n, Mode mode, std::vector<int4>& out) {
         if (mode != Mode::Sym || EBN * bj + EBN - 1 >= EBM * bi) out.push_back(make_int4(m, bi, bj, 0));
 }
 
+// One product of a single matrix: its tiles, each split over K into two halves when that shortens the
+// launch. A launch of T tiles on G CTAs lasts ceil(T / G) tile times; split, ceil(2T / G) half-tile times.
+// Halves of tile k are items (0, bi, bj, 1 + 2k) and (0, bi, bj, 2 + 2k), next to each other.
+int emu_split_slots(int n, Mode mode) {
+  const int T = emu_tile_count(n, mode), G = sm_count_emu(), KS = (n + EBK - 1) / EBK;
+  const bool split = KS >= 2 && T < 4 * G && (2 * T + G - 1) / G < 2 * ((T + G - 1) / G);
+  return split ? T : 0;
+}
+
+void emu_launch_list(int n, Mode mode, std::vector<int4>& out) {
+  std::vector<int4> tiles;
+  emu_tile_list(0, n, mode, tiles);
+  if (emu_split_slots(n, mode) == 0) {
+    out.insert(out.end(), tiles.begin(), tiles.end());
+    return;
+  }
+  for (size_t k = 0; k < tiles.size(); ++k) {
+    const int4 t = tiles[k];
+    out.push_back(make_int4(t.x, t.y, t.z, 1 + 2 * (int)k));
+    out.push_back(make_int4(t.x, t.y, t.z, 2 + 2 * (int)k));
+  }
+}
+
+size_t emu_split_bytes(int slots) { return (size_t)slots * 2 * SPLIT_PER_PART * sizeof(long long); }
+
+size_t emu_split_counters(int slots) { return (size_t)slots * EPI_WARPS; }
+
 int emu_tile_count(int n, Mode mode) {
   std::vector<int4> v;
   emu_tile_list(0, n, mode, v);
@@ -644,10 +714,12 @@ cudaError_t emu_prepare() { return prepare_emu(); }
 size_t emu_scratch_bytes() { return (size_t)sm_count_emu() * SCRATCH_PER_CTA * sizeof(long long); }
 
 cudaError_t gemm_emu(const __half* DX, const int* ex, const __half* DY, const int* ey, int n, int ldl, int S, Mode mode,
-                     bool transpose, const int4* items, int nitems, const Epilogue& e, long long* scratch, int* err,
-                     cudaStream_t s) {
+                     bool transpose, const int4* items, int nitems, const Epilogue& e, long long* scratch,
+                     long long* split, int* split_cnt, int* err, cudaStream_t s) {
   EmuArgs a{};
   a.scratch = scratch;
+  a.split = split;
+  a.split_cnt = split_cnt;
   a.S = S;
   a.ld = n;
   a.ntiles = nitems;

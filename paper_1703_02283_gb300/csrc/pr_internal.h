@@ -88,13 +88,21 @@ cudaError_t gemm_bf16_tc(const __nv_bfloat16* X, const __nv_bfloat16* Y, int n, 
 // ---- FP64-accurate products from exact FP16 digit slices (k_gemm_emu.cu).
 // slice(): X (n x n FP64) -> 8 digit planes D (layout [row][k / 16][plane][k % 16], n x 8 ldl FP16 with
 // ldl = emu_ld(n); planes >= S zero) and row exponents ex.
-// gemm_emu(): P = X Y^T from the slices of X and Y over the work items (tile lists of emu_tile_list), FP64
-// epilogue (out / out2 / partial; no BF16 copies). One residual partial per epilogue warp and item
-// (emu_partials_per_item() per item, in item order).
+// gemm_emu(): P = X Y^T from the slices of X and Y over the work items (emu_launch_list), FP64 epilogue
+// (out / out2 / partial; no BF16 copies). One residual partial per epilogue warp and tile
+// (emu_partials_per_item() per tile, in tile order, also when tiles are split).
 // emu_tile_list(): appends the work items (m, tile row, tile column, 0) of matrix m (order n) in the
 // kernel's order; tiles are 128 rows x 96 columns, symmetric mode keeps those reaching the upper triangle.
 void emu_tile_list(int m, int n, Mode mode, std::vector<int4>& out);
 int emu_tile_count(int n, Mode mode);
+// The work list of one single-matrix product: emu_tile_list, with every tile split over K into two items
+// when that shortens the launch (emu_split_slots tiles; 0: not split). A split launch needs
+// emu_split_bytes(slots) bytes of exact half totals and emu_split_counters(slots) ints, zero before the
+// first launch (the kernel leaves them zero).
+void emu_launch_list(int n, Mode mode, std::vector<int4>& out);
+int emu_split_slots(int n, Mode mode);
+size_t emu_split_bytes(int slots);
+size_t emu_split_counters(int slots);
 int emu_tiles(int n, Mode mode);  // residual partials of one product: emu_tile_count * emu_partials_per_item
 int emu_partials_per_item();
 int emu_max_slices();
@@ -106,8 +114,8 @@ cudaError_t slice(const double* X, int n, int ldl, int S, __half* D, int* ex, cu
 cudaError_t slice_rows(const double* X, int R, int n, int ldx, int ldl, int S, const int* row_n, __half* D, int* ex,
                        cudaStream_t s);
 cudaError_t gemm_emu(const __half* DX, const int* ex, const __half* DY, const int* ey, int n, int ldl, int S, Mode mode,
-                     bool transpose, const int4* items, int nitems, const Epilogue& e, long long* scratch, int* err,
-                     cudaStream_t s);
+                     bool transpose, const int4* items, int nitems, const Epilogue& e, long long* scratch,
+                     long long* split, int* split_cnt, int* err, cudaStream_t s);
 
 // A batch of matrices packed row-wise in shared buffers (leading dimension ld for FP64, ldl for digit
 // planes; R packed rows per plane; K the largest order). Work items from emu_tile_list per matrix;
