@@ -60,6 +60,7 @@ struct pr_handle_s {
   long long* emu_scratch = nullptr;          // PR_EMU64 first-pass totals (pr::emu_scratch_bytes())
   long long* emu_split = nullptr;            // PR_EMU64 half totals of tiles split over K (pr::emu_launch_list)
   int* emu_split_cnt = nullptr;
+  int emu_nsplit[2] = {0, 0};                // split tiles of the symmetric and the full work list
 
   // The input, the iterate X, the carried product M and operand N of the coupled form, their next
   // values, and two scratch products.
@@ -221,7 +222,8 @@ pr_status product(pr_handle h, int prec, Mat& X, Mat& Y, Mode mode, const Out& o
     case PR_EMU64:
       PR_CK(h, pr::gemm_emu(X.sl, X.ex, Y.sl, Y.ex, n, h->eld, h->S, mode, o.transpose,
                             h->emu_items[mode == Mode::Sym ? 0 : 1], h->emu_nitems[mode == Mode::Sym ? 0 : 1], e,
-                            h->emu_scratch, h->emu_split, h->emu_split_cnt, h->err_word(), h->stream));
+                            h->emu_scratch, h->emu_nsplit[mode == Mode::Sym ? 0 : 1] ? h->emu_split : nullptr,
+                            h->emu_split_cnt, h->err_word(), h->stream));
       h->lp_stale = true;
       break;
     default:
@@ -810,7 +812,8 @@ pr_status pr_init(pr_handle* out, const double* A, int64_t n, int p, const pr_op
   for (int k = 0; k < 2; ++k) {  // the PR_EMU64 work lists of this order (symmetric, full)
     std::vector<int4> items;
     pr::emu_launch_list((int)n, k == 0 ? Mode::Sym : Mode::Full, items);
-    slots = std::max(slots, pr::emu_split_slots((int)n, k == 0 ? Mode::Sym : Mode::Full));
+    h->emu_nsplit[k] = pr::emu_split_slots((int)n, k == 0 ? Mode::Sym : Mode::Full);
+    slots = std::max(slots, h->emu_nsplit[k]);
     h->emu_nitems[k] = (int)items.size();
     PR_INIT_CK(cudaMalloc((void**)&h->emu_items[k], items.size() * sizeof(int4)));
     PR_INIT_CK(cudaMemcpy(h->emu_items[k], items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));

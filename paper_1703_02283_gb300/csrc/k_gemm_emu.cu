@@ -177,16 +177,24 @@ struct EmuArgs {
 
 // Item t: its matrix, tile, and the K steps [j0, j1) it covers. kpart = 0 is the whole tile; a tile split in
 // two has items with kpart = 1 + 2 slot + half, half 0 taking the first KS / 2 steps and half 1 the rest.
+template <bool SPLIT>
 __device__ __forceinline__ const EmuMat& item_of(const EmuArgs& a, int t, int& bi, int& bj, int& kpart, int& j0,
                                                  int& j1) {
   const int4 it = a.items[t];
   bi = it.y;
   bj = it.z;
-  kpart = it.w;
   const EmuMat& mt = a.mats ? a.mats[it.x] : a.one;
-  const int KS = (mt.n + EBK - 1) / EBK, h = KS >> 1;
-  j0 = kpart == 0 || ((kpart - 1) & 1) == 0 ? 0 : h;
-  j1 = kpart == 0 || ((kpart - 1) & 1) == 1 ? KS : h;
+  const int KS = (mt.n + EBK - 1) / EBK;
+  if constexpr (SPLIT) {
+    const int h = KS >> 1;
+    kpart = it.w;
+    j0 = kpart == 0 || ((kpart - 1) & 1) == 0 ? 0 : h;
+    j1 = kpart == 0 || ((kpart - 1) & 1) == 1 ? KS : h;
+  } else {
+    kpart = 0;
+    j0 = 0;
+    j1 = KS;
+  }
   return mt;
 }
 
@@ -252,7 +260,7 @@ __device__ __forceinline__ void mma_level_s8(int L, uint32_t d, uint32_t aT, uin
 // second step; 8 pairs x 8 steps x 16 x 2^14 = 2^24 keeps every level exact) and after the pass's last step.
 __device__ __forceinline__ bool drains_after(int a, int j) { return ((j + 2 * a) & 7) == 7; }
 
-template <bool SYM>
+template <bool SYM, bool SPLIT>
 __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (5 warps per sub-partition)
     k_gemm_emu(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, EmuArgs args) {
   const int ntiles = args.ntiles_dev ? *args.ntiles_dev : args.ntiles;
@@ -303,7 +311,7 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
       bool stop = false;
       for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
         int bi, bj, kpart, j0, j1;
-        const EmuMat& mt = item_of(args, t, bi, bj, kpart, j0, j1);
+        const EmuMat& mt = item_of<SPLIT>(args, t, bi, bj, kpart, j0, j1);
         const int ya = mt.row0 + bi * EBM, yb = mt.row0 + bj * EBN;
         for (int pass = 0; pass < 2 && !stop; ++pass) {
           const int ng = pass == 0 ? 1 : groups1;
@@ -336,7 +344,7 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
       bool stop = false;
       for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
         int bi, bj, kpart, j0, j1;
-        item_of(args, t, bi, bj, kpart, j0, j1);
+        item_of<SPLIT>(args, t, bi, bj, kpart, j0, j1);
         for (int pass = 0; pass < 2 && !stop; ++pass) {
           const int np = pass == 0 ? min(S, 4) : S;
           for (int j = j0; j < j1; ++j, ++it) {
@@ -369,7 +377,7 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
       bool stop = false;
       for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
         int bi, bj, kpart, j0, j1;
-        item_of(args, t, bi, bj, kpart, j0, j1);
+        item_of<SPLIT>(args, t, bi, bj, kpart, j0, j1);
         const int KS = j1 - j0;
         for (int pass = 0; pass < 2 && !stop; ++pass) {
           for (int j = 0; j < KS && !stop; ++j, ++it) {
@@ -438,7 +446,7 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
     bool stop = false;
     for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
       int bi, bj, kpart, j0, j1;
-      const EmuMat& mt = item_of(args, t, bi, bj, kpart, j0, j1);
+      const EmuMat& mt = item_of<SPLIT>(args, t, bi, bj, kpart, j0, j1);
       const int n = mt.n, row0 = mt.row0, KS = j1 - j0;
       // Exact totals: the first pass gives hi = sum_{L<=5} V_L 2^(8(5-L)) (kept in scratch), the second
       // lo = sum_{L>=6} V_L 2^(8(9-L)); P = hi 2^-40 + lo 2^-72.
@@ -492,37 +500,40 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
         }
       }
       if (stop) break;
-      const int tile = kpart == 0 ? t : (kpart - 1) >> 1;  // residual partials are indexed by tile, not by item
-      // The second pass's totals join the first's in the scratch, so that nothing of the step loop stays
-      // live through the tile end.
+      const int tile = SPLIT && kpart != 0 ? (kpart - 1) >> 1 : t;  // residual partials are indexed by tile
       long long* scr_lo = scr + (size_t)EPI_COLS * (EPI_WARPS * 32);
+      if constexpr (SPLIT) {
+        // The second pass's totals join the first's in the scratch, so that nothing of the step loop stays
+        // live through the tile end.
 #pragma unroll
-      for (int c = 0; c < EPI_COLS; ++c) scr_lo[(size_t)c * (EPI_WARPS * 32)] = acc[c];
-      if (kpart != 0) {
-        // A tile split over K: this warp publishes its half's exact totals. The same warp of the other half
-        // covers the same elements; whichever of the two finishes second adds the other's totals to its own
-        // (integers, so the sum is exact and independent of the order) and applies the epilogue. Nobody
-        // waits: the first to finish just moves on.
-        const int half = (kpart - 1) & 1;
-        longlong2* pub = reinterpret_cast<longlong2*>(args.split) + ((size_t)tile * 2 + half) * (SPLIT_PER_PART / 2) +
-                         (ew * 32 + lane);
-        for (int c = 0; c < EPI_COLS; ++c)
-          pub[c * (EPI_WARPS * 32)] = make_longlong2(scr[(size_t)c * (EPI_WARPS * 32)], scr_lo[(size_t)c * (EPI_WARPS * 32)]);
-        __threadfence();
-        __syncwarp();
-        int last = 0;
-        if (lane == 0) {
-          int* cnt = args.split_cnt + (size_t)tile * EPI_WARPS + ew;
-          last = atomicAdd(cnt, 1) == 1;
-          if (last) *cnt = 0;  // ready for the next launch
-        }
-        if (!__shfl_sync(0xffffffffu, last, 0)) continue;
-        __threadfence();
-        const longlong2* oth = pub + (half ? -1 : 1) * (ptrdiff_t)(SPLIT_PER_PART / 2);
-        for (int c = 0; c < EPI_COLS; ++c) {
-          const longlong2 o = __ldcg(oth + c * (EPI_WARPS * 32));
-          scr[(size_t)c * (EPI_WARPS * 32)] += o.x;
-          scr_lo[(size_t)c * (EPI_WARPS * 32)] += o.y;
+        for (int c = 0; c < EPI_COLS; ++c) scr_lo[(size_t)c * (EPI_WARPS * 32)] = acc[c];
+        if (kpart != 0) {
+          // A tile split over K: this warp publishes its half's exact totals. The same warp of the other
+          // half covers the same elements; whichever of the two finishes second adds the other's totals to
+          // its own (integers, so the sum is exact and independent of the order) and applies the epilogue.
+          // Nobody waits: the first to finish just moves on.
+          const int half = (kpart - 1) & 1;
+          longlong2* pub = reinterpret_cast<longlong2*>(args.split) + ((size_t)tile * 2 + half) * (SPLIT_PER_PART / 2) +
+                           (ew * 32 + lane);
+          for (int c = 0; c < EPI_COLS; ++c)
+            pub[c * (EPI_WARPS * 32)] =
+                make_longlong2(scr[(size_t)c * (EPI_WARPS * 32)], scr_lo[(size_t)c * (EPI_WARPS * 32)]);
+          __threadfence();
+          __syncwarp();
+          int last = 0;
+          if (lane == 0) {
+            int* cnt = args.split_cnt + (size_t)tile * EPI_WARPS + ew;
+            last = atomicAdd(cnt, 1) == 1;
+            if (last) *cnt = 0;  // ready for the next launch
+          }
+          if (!__shfl_sync(0xffffffffu, last, 0)) continue;
+          __threadfence();
+          const longlong2* oth = pub + (half ? -1 : 1) * (ptrdiff_t)(SPLIT_PER_PART / 2);
+          for (int c = 0; c < EPI_COLS; ++c) {
+            const longlong2 o = __ldcg(oth + c * (EPI_WARPS * 32));
+            scr[(size_t)c * (EPI_WARPS * 32)] += o.x;
+            scr_lo[(size_t)c * (EPI_WARPS * 32)] += o.y;
+          }
         }
       }
       // Tile end: P = 2^(e_i + f_j - 72) (hi 2^32 + lo), then the fused epilogue (FP64 values, FP32 partials).
@@ -532,7 +543,8 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
 #pragma unroll
       for (int c = 0; c < EPI_COLS; ++c) {
         const int jc = bj * EBN + EPI_COLS * h + c;
-        const long long hi = scr[(size_t)c * (EPI_WARPS * 32)], lo = scr_lo[(size_t)c * (EPI_WARPS * 32)];
+        const long long hi = scr[(size_t)c * (EPI_WARPS * 32)];
+        const long long lo = SPLIT ? scr_lo[(size_t)c * (EPI_WARPS * 32)] : acc[c];
         if (i >= n || jc >= n || (SYM && i > jc)) continue;
         const unsigned long long lw0 = (unsigned long long)hi << 32, lw = lw0 + (unsigned long long)lo;
         const long long H = (hi >> 32) + (lo >> 63) + (lw < lw0 ? 1 : 0);
@@ -612,9 +624,13 @@ int sm_count_emu() {
 cudaError_t prepare_emu() {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t r = cudaFuncSetAttribute(k_gemm_emu<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaError_t r = cudaFuncSetAttribute(k_gemm_emu<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (r != cudaSuccess) return r;
-    r = cudaFuncSetAttribute(k_gemm_emu<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    r = cudaFuncSetAttribute(k_gemm_emu<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (r != cudaSuccess) return r;
+    r = cudaFuncSetAttribute(k_gemm_emu<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (r != cudaSuccess) return r;
+    r = cudaFuncSetAttribute(k_gemm_emu<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (r != cudaSuccess) return r;
     attr_set = true;
   }
@@ -637,9 +653,11 @@ cudaError_t launch_emu(const __half* DX, const __half* DY, int R, int K, int ldl
   if (r != cudaSuccess) return r;
   const int grid = a.ntiles_dev || a.ntiles >= sm_count_emu() ? sm_count_emu() : a.ntiles;
   if (mode == Mode::Sym) {
-    k_gemm_emu<true><<<grid, THREADS, SMEM_BYTES, s>>>(mx, my, a);
+    if (a.split) k_gemm_emu<true, true><<<grid, THREADS, SMEM_BYTES, s>>>(mx, my, a);
+    else k_gemm_emu<true, false><<<grid, THREADS, SMEM_BYTES, s>>>(mx, my, a);
   } else {
-    k_gemm_emu<false><<<grid, THREADS, SMEM_BYTES, s>>>(mx, my, a);
+    if (a.split) k_gemm_emu<false, true><<<grid, THREADS, SMEM_BYTES, s>>>(mx, my, a);
+    else k_gemm_emu<false, false><<<grid, THREADS, SMEM_BYTES, s>>>(mx, my, a);
   }
   return cudaGetLastError();
 }
