@@ -672,10 +672,10 @@ def main():
         exec_fl = dfl * pairs
         # DRAM bytes (read + write) per symmetric n = 4096 product from one ncu capture; other sizes were not
         # captured.
-        last = EMU_TRAFFIC_BYTES.get(args.n) if S == 8 else None
+        traffic_seen = EMU_TRAFFIC_BYTES.get(args.n) if S == 8 else None
         roofline = {"bound": "tensor", "kernel": "k_gemm_emu (tcgen05 FP16 digit-slice products)",
                     "achieved": exec_fl / (dms * 1e-3) / 1e12, "peak": peaks["bf16_tflops_sustained"],
-                    "unit": "TFLOP/s", "traffic": None, "traffic_last_capture": last,
+                    "unit": "TFLOP/s", "traffic": None, "traffic_last_capture": traffic_seen,
                     "note": f"algorithmic = the {pairs} FP16 digit-pair products per emulated FP64 product "
                             f"(S={S}), upper-triangle tiles; fp64_equivalent_tflops = FP64 flops / time",
                     "fp64_equivalent_tflops": dfl / (dms * 1e-3) / 1e12,
