@@ -188,11 +188,26 @@ def predicted_iterations(case, p: int, tol: float) -> int:
     return int(hit[0]) if len(hit) else 200
 
 
+L2_BYTES = 129e6
+
+
+def handle_bytes(n: int) -> float:
+    """Device bytes a handle of order n works on: nine FP64 matrices, their BF16 copies and the digit
+    planes (8 FP16 planes) of the six matrices the products slice."""
+    ld = (n + 15) // 16 * 16
+    return 9 * 8.0 * n * n + 9 * 2.0 * n * ld + 6 * 16.0 * n * ld
+
+
+def l2_note(nbytes: float) -> str:
+    side = "larger" if nbytes > L2_BYTES else "smaller"
+    return f"inputs {side} than L2: working set {nbytes / 2**30:.3g} GiB vs 129 MB L2"
+
+
 def config_dict(args, ps):
     return {"workload": f"SPD n={args.n} (Q diag(lam) Q^T), kappa={1 / args.lam_min:g}, p={','.join(map(str, ps))}, "
                         f"Eq.3 C_0, tol {args.tol:g}", "n": args.n, "kappa": 1 / args.lam_min, "p": ps,
             "seed": args.seed, "mode": args.mode,
-            "l2": "inputs larger than L2: working set ~1.5 GiB per handle vs 129 MB L2"}
+            "l2": l2_note(handle_bytes(args.n)) + " per handle"}
 
 
 def run_reference(args, ps):
@@ -229,12 +244,20 @@ def batched_cases(count, rank=0):
     return cases, [int(x) for x in spec.p]
 
 
+def batch_bytes(count: int) -> float:
+    """Device bytes of the packed batch: nine FP64 buffers and their digit planes, R rows x the largest order."""
+    spec = W.batched_specs(count)
+    R, K = int(spec.n.sum()), int(spec.n.max())
+    ld = (K + 15) // 16 * 16
+    return 9 * 8.0 * R * ld + 9 * 16.0 * R * ld
+
+
 def batched_config(args):
     return {"workload": f"batched: {args.count} SPD matrices, n uniform in [64, 1024], kappa log-uniform in "
                         f"[10, 1e4], p in {{1, 2, 3}} (seeds 1000+i), Eq.3 C_0, tol {args.tol:g}",
             "count": args.count, "mode": "emu64",
             "step": "pr_batch_load of every matrix + pr_batch_solve (one graph launch) + every pr_batch_result",
-            "l2": "inputs larger than L2: packed working set of several GiB"}
+            "l2": l2_note(batch_bytes(args.count)) + " (packed batch)"}
 
 
 def oracle_batched_sample(cases, ps, its, k=3):
@@ -381,7 +404,7 @@ def learned_config(args):
                         f"every {args.every} steps; timed on {args.test_seqs} held-out sequences sampled the same way; "
                         f"p=2, tol {args.tol:g}, gated polynomial C_0 (fallback Eq.3), PR_EMU64 products",
             "n": n, "p": 2, "train_sequences": args.train_seqs, "test_sequences": args.test_seqs, "every": args.every,
-            "mode": "emu64", "l2": "inputs larger than L2: ~0.6 GiB working set per handle vs 129 MB L2"}
+            "mode": "emu64", "l2": l2_note(handle_bytes(n)) + " per handle"}
 
 
 def learned_sets(args):
