@@ -37,6 +37,12 @@
 // first pass's totals wait in a scratch buffer; at the tile's end the 128-bit total hi 2^32 + lo is
 // rounded once to FP64 (integer arithmetic), scaled by 2^(e_i + f_j) and the fused epilogue applied.
 // Every wait is bounded as in k_gemm_tc.cu.
+//
+// Split tiles (the SPLIT variant). A short single-matrix launch whose tiles fill the SMs for a fraction of
+// a wave is given every tile as two items over halves of k (emu_launch_list). Each half ends with exact
+// int64 totals; the epilogue warp of the half that finishes second (one atomic counter per tile and warp)
+// adds the other half's totals to its own, which is exact and independent of the order, and applies the
+// epilogue. No warp waits for another CTA. Residual partials are indexed by tile, as without splitting.
 #include "pr_internal.h"
 #include "tc_ptx.h"
 
