@@ -307,8 +307,9 @@ int64_t pr_batch_launches(pr_batch b);
  * flops are n^2 (n + 1) for a symmetric product (upper tiles) and 2 n^3 for a full one. The executed
  * tensor-core work is emu_slices (emu_slices + 1) / 2 FP16 digit-pair products of each. */
 typedef struct {
-  int64_t launches;          /* kernels launched so far */
-  int64_t stages;            /* product launches */
+  int64_t launches;          /* kernels launched so far (in the solve graph: its prologue, epilogue and every
+                                pass of its loop body, whether or not a launch found work) */
+  int64_t stages;            /* product launches with work (a graph stage whose list is empty does not count) */
   int64_t products;          /* per-matrix products in those launches */
   double product_flops;      /* their FP64-equivalent algorithmic flops */
   int64_t stages_timed;      /* product launches timed (pr_batch_set_timing) */
