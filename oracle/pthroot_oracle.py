@@ -61,7 +61,7 @@ __all__ = [
     "sym_product", "power_times", "residual_fro", "step_literal", "step_newton_schulz",
     "coupled_start", "step_coupled", "solve", "SolveInfo", "closed_form_root", "eig_root",
     "scalar_recurrence", "scalar_residuals", "forward_error", "default_form", "closed_form_block",
-    "residual_rows",
+    "residual_rows", "eq2_prescale",
 ]
 
 
@@ -80,6 +80,22 @@ def norm_inf(A: np.ndarray) -> float:
 def initial_guess_eq3(A: np.ndarray) -> np.ndarray:
     """Eq. 3: C_0 = (||A||_1 ||A||_inf)^{-1} A^T."""
     return np.ascontiguousarray(A.T / (norm_1(A) * norm_inf(A)))
+
+
+def eq2_prescale(A: np.ndarray, p: int):
+    """Reading of Eq. 2's scale caveat for Eq. 3's C_0 (the paper says Eq. 3 always satisfies Eq. 2).
+
+    The eigenvalues of C_0^p A are lam^(p+1) / (||A||_1 ||A||_inf)^p <= ||A||_1^(1-p), so for p > 1 and
+    ||A||_1 ||A||_inf < 1 Eq. 2 can fail (A = 0.1 I, p = 2: ||I - C_0^2 A||_2 = 9). Such an A is replaced by
+    2^k A with ||2^k A||_1 = 2 f in [1, 2), where ||A||_1 = f 2^e, f in [0.5, 1), k = 1 - e; a power of two
+    scales exactly, and A^{-1/p} = 2^(k/p) (2^k A)^{-1/p}. Returns (the matrix to iterate on, k); k = 0 leaves
+    A as it is (p = 1, or ||A||_1 ||A||_inf >= 1).
+    """
+    if p <= 1 or norm_1(A) * norm_inf(A) >= 1.0:
+        return A, 0
+    _, e = np.frexp(norm_1(A))
+    k = 1 - int(e)
+    return np.ldexp(A, k), k
 
 
 def initial_guess_scaled_identity(A: np.ndarray, p: int) -> np.ndarray:
@@ -172,13 +188,14 @@ class SolveInfo:
     p: int
     iterations: int = 0  # number of updates applied to C
     residuals: list = field(default_factory=list)  # r_0 .. r_k, r_k belongs to the returned iterate
-    stop: str = ""  # "tol", "stagnation", "max_iter" or "diverged"
+    stop: str = ""  # "tol", "stagnation", "max_iter", "diverged" or (coupled form) "inaccurate"
     seconds: float = 0.0
+    true_residual: float = -1.0  # ||I - C^p A||_F of the returned iterate (coupled form with verify)
 
 
 def solve(A: np.ndarray, p: int, form: str | None = None, c0: str = "eq3", tol: float = 1e-12,
           max_iter: int = 100, stag_below: float = 1e-3, stag_ratio: float = 0.5,
-          C0: np.ndarray | None = None):
+          C0: np.ndarray | None = None, verify: bool = True):
     """Iterate Eq. 1 from C_0 until the residual meets ``tol``.
 
     Stop rule (reading; the paper gives none): after computing r_k for the current iterate, stop with
@@ -187,7 +204,10 @@ def solve(A: np.ndarray, p: int, form: str | None = None, c0: str = "eq3", tol: 
     The returned iterate is the one whose residual was r_k.
 
     ``r_k`` is ||I - C_k^p A||_F for the literal and Newton-Schulz forms and ||I - M_k||_F for the
-    coupled form (equal in exact arithmetic).
+    coupled form (equal in exact arithmetic). With ``verify`` the coupled form then evaluates the true
+    residual ||I - C^p A||_F of the returned iterate (reading: the residual Sec. 2 defines is the true one;
+    rounding errors carried in M can separate the two), and a "tol" stop whose true residual exceeds
+    ``tol`` becomes "inaccurate".
     """
     A = np.asarray(A, dtype=np.float64)
     n = A.shape[0]
@@ -246,6 +266,12 @@ def solve(A: np.ndarray, p: int, form: str | None = None, c0: str = "eq3", tol: 
     else:
         raise ValueError(f"unknown form {form!r}")
     info.iterations = k
+    if form == "coupled" and verify and stop != "diverged":
+        info.true_residual = residual_fro(C, A, p)
+        if stop == "tol" and not info.true_residual <= tol:
+            stop = "inaccurate"
+    elif form != "coupled" and stop != "diverged":
+        info.true_residual = info.residuals[-1]  # the Newton-Schulz and literal forms test the true residual
     info.stop = stop
     info.seconds = time.perf_counter() - t0
     return C, info

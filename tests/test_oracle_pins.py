@@ -60,6 +60,36 @@ def test_eq2_scaling_caveat_small_norm():
     assert np.linalg.norm(np.eye(3) - C0 @ C0 @ A, 2) == pytest.approx(9.0, rel=1e-12)
 
 
+def test_eq2_prescale_restores_convergence():
+    # A = 0.1 I, p = 2: Eq. 3 on A itself diverges; on 2^k A (||2^k A||_1 = 1.6) Eq. 2 holds exactly
+    # (from the spectrum) and 2^(k/2) times the limit is 0.1^(-1/2) I.
+    A = 0.1 * np.eye(4)
+    _, info = O.solve(A, 2, tol=1e-14, max_iter=40)
+    assert info.stop == "diverged" or info.residuals[-1] > 1.0
+    As, k = O.eq2_prescale(A, 2)
+    assert k == 4 and np.array_equal(As, 1.6 * np.eye(4)) and 1.0 <= O.norm_1(As) < 2.0
+    mu = 1.6 ** 3 / (O.norm_1(As) * O.norm_inf(As)) ** 2  # eigenvalue of C_0^2 As
+    assert abs(1.0 - mu) < 1.0
+    C, info = O.solve(As, 2, tol=1e-14)
+    assert info.stop in ("tol", "stagnation")
+    np.testing.assert_allclose(2.0 ** (k / 2) * C, 0.1 ** -0.5 * np.eye(4), rtol=1e-14)
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_eq2_prescale_matches_closed_form(p):
+    # A random SPD matrix shrunk below ||A||_1 = 1: the scaled solve, scaled back, is the closed-form root of
+    # the shrunk matrix; k = 0 when nothing needs scaling (p = 1, or ||A||_1 >= 1).
+    c = _case(40, 0.05, 21)
+    A = 0.01 * c.A
+    As, k = O.eq2_prescale(A, p)
+    assert k > 0 and 1.0 <= O.norm_1(As) < 2.0 and np.array_equal(As, A * 2.0 ** k)
+    C, info = O.solve(As, p, tol=1e-13)
+    Z = O.closed_form_root(c.Q, 0.01 * c.lam, p)
+    # Eq. 3's M_0 spans kappa^(p+1) = 20^4: about u kappa^(p+1) = 3.6e-11 of relative error is carried.
+    assert O.forward_error(2.0 ** (k / p) * C, Z) < 1e-11
+    assert O.eq2_prescale(A, 1)[1] == 0 and O.eq2_prescale(c.A, p)[1] == 0
+
+
 # ------------------------------------------------------------------------- hand-derived iterates
 
 def _golden_cases():
@@ -97,7 +127,7 @@ def test_limit_matches_closed_form_and_lapack(p):
     assert O.forward_error(Ze, Z) < 1e-13
     for c0 in ("eq3", "scaled_identity"):
         C, info = O.solve(c.A, p, c0=c0, tol=1e-13)
-        assert info.stop in ("tol", "stagnation")
+        assert info.stop in ("tol", "stagnation", "inaccurate")
         assert O.forward_error(C, Z) < 1e-12, (c0, info)
         # Z^p A = I (definition of the inverse p-th root)
         assert O.residual_fro(Z, c.A, p) < 1e-12
@@ -207,8 +237,9 @@ def test_forms_agree_well_conditioned():
 
 def test_stop_rule_outcomes():
     c = _case(32, 0.1, 1)
-    _, info = O.solve(c.A, 2, tol=1e-8)
+    C, info = O.solve(c.A, 2, tol=1e-8)
     assert info.stop == "tol" and info.residuals[-1] <= 1e-8 and info.residuals[-2] > 1e-8
+    assert info.true_residual == O.residual_fro(C, c.A, 2) <= 1e-8
     _, info = O.solve(c.A, 2, tol=0.0, max_iter=3, stag_below=0.0)
     assert info.stop == "max_iter" and info.iterations == 3 and len(info.residuals) == 4
     _, info = O.solve(c.A, 1, tol=0.0)  # the floor cannot be passed: stagnation
@@ -217,6 +248,24 @@ def test_stop_rule_outcomes():
     bad[0, 0] = np.nan
     _, info = O.solve(bad, 2, tol=1e-8)
     assert info.stop == "diverged"
+
+
+def test_verified_stop_of_the_coupled_form():
+    # Eq. 3's M_0 spans kappa^(p+1): at kappa = 1e3, p = 3 the carried ||I - M||_F reaches 1e-12 while the
+    # true residual of X stays far above it (rounding carried in M), so the verified stop is "inaccurate";
+    # without verification it is "tol". The scaled identity (M_0 spans kappa) meets the same tolerance for
+    # real. The Newton-Schulz form tests the true residual itself.
+    c = W.spd_from_spectrum(128, 1e-3, 5)
+    C, info = O.solve(c.A, 3, tol=1e-12)
+    assert info.stop == "inaccurate" and info.residuals[-1] <= 1e-12
+    assert info.true_residual == O.residual_fro(C, c.A, 3) > 1e-9
+    _, info2 = O.solve(c.A, 3, tol=1e-12, verify=False)
+    assert info2.stop == "tol" and info2.true_residual == -1.0
+    c = _case(64, 0.1, 5)
+    C, info = O.solve(c.A, 3, c0="scaled_identity", tol=1e-12)
+    assert info.stop == "tol" and info.true_residual == O.residual_fro(C, c.A, 3) <= 1e-12
+    C, info = O.solve(c.A, 1, tol=1e-12)
+    assert info.true_residual == info.residuals[-1]
 
 
 # ------------------------------------------------------------------------- the pins catch mistakes

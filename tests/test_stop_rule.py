@@ -57,7 +57,10 @@ def test_agrees_with_oracle_on_fp64_histories():
         h = info.residuals
         for k in range(1, len(h) + 1):
             got = rule(h[:k], [F64] * k, tol=tol)
-            want = {"tol": P.PR_OK, "stagnation": P.PR_ESTAGNATED, "diverged": P.PR_EDIVERGED}.get(info.stop)
+            # The pure rule tests the carried residual only: a verified "inaccurate" stop is a PR_OK of the rule
+            # (pr_iterate turns it into PR_EINACCURATE after evaluating the true residual).
+            want = {"tol": P.PR_OK, "inaccurate": P.PR_OK, "stagnation": P.PR_ESTAGNATED,
+                    "diverged": P.PR_EDIVERGED}.get(info.stop)
             if k < len(h):
                 assert got == CONTINUE, (p, k)
             elif info.stop != "max_iter":
