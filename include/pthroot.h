@@ -36,22 +36,29 @@ extern "C" {
 
 typedef struct pr_handle_s* pr_handle;
 
-/* Status codes. PR_ESTAGNATED and PR_EMAXITER are stop reasons, not failures: the handle stays valid
- * and iteration may be resumed (with another precision, for instance). */
+/* Status codes. PR_ESTAGNATED, PR_EMAXITER and PR_EINACCURATE are stop reasons, not failures: the handle
+ * stays valid and iteration may be resumed (with another precision, for instance). */
 typedef enum {
   PR_OK = 0,          /* tolerance met (pr_iterate/pr_solve) or call succeeded                          */
   PR_EINVAL = 1,      /* bad argument: n < 1, p < 1, unknown enum, NULL pointer, non-finite or
                          non-symmetric A, or tol < 0                                                       */
-  PR_ENOTSPD = 2,     /* A has a non-positive diagonal entry, so it cannot be positive definite          */
+  PR_ENOTSPD = 2,     /* A is not positive definite: a non-positive diagonal entry, or a failed Cholesky
+                         factorisation of one of its diagonal blocks of order 64 (principal submatrices of
+                         an SPD matrix are SPD)                                                            */
   PR_ENOMEM = 3,      /* device allocation failed                                                        */
   PR_ECUDA = 4,       /* a CUDA runtime call or kernel launch failed                                     */
   PR_EDIVERGED = 5,   /* the residual became NaN or Inf                                                  */
   PR_ESTAGNATED = 6,  /* residual below stag_below stopped halving: the precision floor was reached      */
   PR_EMAXITER = 7,    /* the step budget of this call (or the handle's max_iter) ran out                 */
   PR_ETIMEOUT = 8,    /* a bounded device wait expired; the kernel returned without finishing            */
-  PR_EGATE = 9,       /* reserved for initial guesses that fail the Eq. 2 check                          */
+  PR_EGATE = 9,       /* a PR_C0_POLY guess failed its gate (Eq. 2 or positivity) and pr_options.gate_fallback
+                         is 0                                                                              */
   PR_ESTATE = 10,     /* call out of order (e.g. pr_result before any pr_init)                           */
-  PR_EUNSUPPORTED = 11 /* precision or form not available for this n / p                                 */
+  PR_EUNSUPPORTED = 11, /* precision or form not available for this n / p                                */
+  PR_EINACCURATE = 12  /* coupled form: the carried residual ||I - M_k||_F met tol, but the true residual
+                          ||I - X_k^p A||_F evaluated at the stop (pr_stats.true_residual) did not. Rounding
+                          errors carried in M since M_0 let X drift from the root (Eq. 3's M_0 spans
+                          kappa^(p+1)); iterating further does not help. A stop reason: the handle stays valid */
 } pr_status;
 
 /* Arithmetic of the matrix products. */
@@ -83,7 +90,8 @@ typedef enum {
                           A gate checks it: if q <= 0 somewhere on [0, 1.05 rho] (rho: a power-iteration
                           estimate of ||A||_2 / ||A||_1, so C_0 might not be positive definite) or a
                           power-iteration estimate of ||I - C_0^p A||_2 (Eq. 2) is not below gate_max, the
-                          handle falls back to Eq. 3 (pr_stats.c0 reports the guess used)                  */
+                          handle falls back to Eq. 3 (pr_stats.c0 reports the guess used), or the call
+                          returns PR_EGATE when pr_options.gate_fallback is 0                            */
 } pr_c0_kind;
 
 /* Options fixed at pr_init. */
@@ -102,6 +110,13 @@ typedef struct {
   double c0_coef[4];   /* PR_C0_POLY coefficients c_0 .. c_3, default (1, 0, 0, 0) (the scaled identity)  */
   double gate_max;     /* PR_C0_POLY gate on ||I - C_0^p A||_2, default 0.9                                */
   int gate_iters;      /* power iterations of the gate, default 30                                         */
+  int verify;          /* coupled form: whenever pr_iterate stops on tol, stagnation or its budget, evaluate
+                          the true residual ||I - X^p A||_F (p - 1 symmetric products and one full product
+                          at the phase's precision) into pr_stats.true_residual, and turn a stop on
+                          ||I - M||_F <= tol into PR_EINACCURATE if the true residual exceeds tol; default 1 */
+  int gate_fallback;   /* PR_C0_POLY guess failing its gate: 1 (default) use Eq. 3 instead; 0 return PR_EGATE
+                          (pr_init then creates no handle; pr_load and pr_set_initial_guess leave Eq. 3's
+                          C_0 in the handle)                                                              */
 } pr_options;
 
 /* Counters of one handle. */
@@ -131,6 +146,10 @@ typedef struct {
   double gemm_ms_by_precision[4];
   double gemm_flops_by_precision[4];
   double c0_gate;                   /* PR_C0_POLY: the gate's estimate of ||I - C_0^p A||_2, else 0         */
+  double true_residual;     /* ||I - C^p A||_F of the iterate at the last stop of pr_iterate: the verified
+                               value of the coupled form (pr_options.verify), the tested residual of the
+                               Newton-Schulz and literal forms; -1 before the first stop                  */
+  int prescale_log2;        /* k: the handle iterates on 2^k A (see pr_load), 0 when A is taken as given   */
 } pr_stats_t;
 
 /* Fills *opt with the defaults listed above. */
@@ -144,8 +163,14 @@ void pr_default_options(pr_options* opt);
  *   opt     options (NULL = defaults)
  *   stream  cudaStream_t to issue all work on (NULL = default stream)
  * Computes ||A||_1 and ||A||_inf (Eq. 3), checks A (finite, symmetric within opt->sym_tol, positive
- * diagonal), forms C_0 and, for the coupled form, M_0 = C_0^p A with its residual. Synchronises the stream.
- * Errors: PR_EINVAL, PR_ENOTSPD, PR_ENOMEM, PR_ECUDA. */
+ * diagonal, Cholesky of every diagonal block of order 64), and forms C_0. Synchronises the stream.
+ * Eq. 2 for Eq. 3's C_0: the eigenvalues of C_0^p A are lambda^(p+1) / (||A||_1 ||A||_inf)^p <= ||A||_1^(1-p),
+ * so for p > 1 a matrix with ||A||_1 ||A||_inf < 1 can violate Eq. 2 (A = 0.1 I, p = 2 gives
+ * ||I - C_0^2 A||_2 = 9) and the iteration diverges. Such an A (p > 1 only) is scaled by an exact power of
+ * two, A <- 2^k A with ||2^k A||_1 in [1, 2); the handle iterates on 2^k A (its pr_stats norms are those of
+ * 2^k A, prescale_log2 = k), pr_result returns 2^(k/p) C = A^{-1/p}, and every residual ||I - C^p (2^k A)||
+ * equals the residual of the returned root for A in exact arithmetic.
+ * Errors: PR_EINVAL, PR_ENOTSPD, PR_ENOMEM, PR_ECUDA, PR_EGATE (see pr_options.gate_fallback). */
 pr_status pr_init(pr_handle* h, const double* A, int64_t n, int p, const pr_options* opt, void* stream);
 
 /* Loads a new A of the same order into an existing handle without reallocating: repeats the checks,
@@ -161,6 +186,10 @@ pr_status pr_load(pr_handle h, const double* A);
  * returns PR_EMAXITER. *steps_done (may be NULL) receives the number of updates applied in this call.
  * When a PR_BF16 run stops because r_k >= r_{k-1}, the last update is undone (the iterate, its residual
  * and the counters return to step k-1), so that a following precise phase starts from the better iterate.
+ * The residual tested is ||I - C_k^p A||_F for the Newton-Schulz and literal forms and the carried
+ * ||I - M_k||_F for the coupled form (equal in exact arithmetic). With pr_options.verify the coupled form
+ * then evaluates the true residual of the iterate it stops at (pr_stats.true_residual), and a PR_OK whose
+ * true residual exceeds tol becomes PR_EINACCURATE.
  * Synchronises the stream once per update to read r_k. */
 pr_status pr_iterate(pr_handle h, int max_steps, int precision, double tol, int* steps_done);
 
@@ -177,7 +206,9 @@ int pr_stop_rule(const double* hist, const int* prec, int len, double tol, const
 
 /* The precision ladder in one call: up to bulk_steps updates at bulk_precision (stopping early on its
  * floor, i.e. stagnation, or on tol), then updates at final_precision until tol, stagnation or
- * max_iter. bulk_steps = 0 skips the bulk phase. Returns the stop status of the final phase. */
+ * max_iter. bulk_steps = 0 skips the bulk phase; a bulk phase that ends with PR_OK returns at once, one
+ * that ends with PR_ESTAGNATED, PR_EMAXITER or PR_EINACCURATE hands over to the final phase. Returns the
+ * stop status of the last phase run. */
 pr_status pr_solve(pr_handle h, int bulk_precision, int bulk_steps, int final_precision, double tol,
                    int* steps_done);
 
@@ -186,8 +217,9 @@ pr_status pr_solve(pr_handle h, int bulk_precision, int bulk_steps, int final_pr
  * Synchronises the stream. */
 pr_status pr_residual(pr_handle h, int precision, double* res_fro);
 
-/* Copies the current iterate C_k (n*n FP64, row-major) to C_out (device or host memory, caller-owned).
- * Synchronises the stream when C_out is host memory. */
+/* Copies the current iterate C_k (n*n FP64, row-major) to C_out (device or host memory, caller-owned),
+ * multiplied by 2^(k/p) when pr_load scaled A by 2^k (pr_stats.prescale_log2), so that C_out approximates the
+ * root of the A the caller gave. Synchronises the stream when C_out is host memory. */
 pr_status pr_result(pr_handle h, double* C_out);
 
 /* Copies the handle's counters to *out. */
@@ -276,7 +308,8 @@ pr_status pr_set_timing(pr_handle h, int on);
 typedef struct pr_batch_s* pr_batch;
 
 /* Creates a batch. n[i] in [1, 16384], p[i] in [1, 64], A[i]: n[i]*n[i] FP64 row-major, device or host,
- * copied. opt: form must be PR_FORM_AUTO (NULL = defaults). Checks every matrix as pr_init does.
+ * copied. opt: form must be PR_FORM_AUTO (NULL = defaults). Checks every matrix as pr_init does and, where
+ * Eq. 2 needs it (p > 1, ||A||_1 ||A||_inf < 1), scales it by a power of two as pr_load does.
  * Errors: PR_EINVAL, PR_ENOTSPD, PR_ENOMEM, PR_ECUDA. */
 pr_status pr_batch_init(pr_batch* b, int count, const int64_t* n, const int* p, const double* const* A,
                         const pr_options* opt, void* stream);
@@ -288,17 +321,39 @@ pr_status pr_batch_load(pr_batch b, const double* const* A);
 
 /* Iterates every active matrix until its stop rule fires (tol, stagnation, max_iter, divergence), with
  * PR_EMU64 products. iterations[i] and status[i] (a pr_status stop code; may be NULL) receive the outcome
- * per matrix. The first call captures the solve graph (on a private stream); every call launches it once
+ * per matrix. With pr_options.verify (default) the graph then evaluates, as pr_iterate does, the true
+ * residual ||I - X^p A||_F of every coupled-form matrix that stopped on tol, stagnation or max_iter, and a
+ * PR_OK whose true residual exceeds tol becomes PR_EINACCURATE (pr_batch_matrix gives the value).
+ * The first call captures the solve graph (on a private stream); every call launches it once
  * on the batch's stream and synchronises that stream once, at the end. A call after every matrix has
  * stopped changes nothing. Errors: PR_ESTATE, PR_EINVAL (tol < 0), PR_EUNSUPPORTED (precision other than
  * PR_EMU64), PR_ECUDA, PR_ETIMEOUT (a bounded device wait expired). */
 pr_status pr_batch_solve(pr_batch b, int precision, double tol, int* iterations, int* status);
 
-/* Copies the result of matrix i (n[i]*n[i] FP64, row-major) to C_out (device or host). */
+/* Copies the result of matrix i (n[i]*n[i] FP64, row-major) to C_out (device or host), multiplied by
+ * 2^(k/p) for a matrix the batch iterated as 2^k A (pr_batch_matrix_t.prescale_log2). */
 pr_status pr_batch_result(pr_batch b, int i, double* C_out);
 
 /* Residual history r_0 .. r_k of matrix i (host memory), as pr_history. */
 pr_status pr_batch_history(pr_batch b, int i, double* out, int cap, int* len);
+
+/* What the batch knows about matrix i after the last pr_batch_solve. */
+typedef struct {
+  int64_t n;
+  int p;
+  int form;              /* PR_FORM_NS (p = 1) or PR_FORM_COUPLED                                          */
+  int status;            /* its pr_status stop code, -1 before a solve                                    */
+  int iterations;
+  double norm_1;         /* ||A||_1 and ||A||_inf of the matrix iterated on (2^k A, see prescale_log2)     */
+  double norm_inf;
+  int prescale_log2;     /* k: as pr_load, a matrix with p > 1 and ||A||_1 ||A||_inf < 1 is iterated as 2^k A
+                            with ||2^k A||_1 in [1, 2) (Eq. 2 for Eq. 3's C_0); pr_batch_result scales back    */
+  double true_residual;  /* ||I - C^p A||_F at the stop: for the coupled form the verification after the solve
+                            loop (pr_options.verify), for p = 1 the tested residual; -1 if not evaluated        */
+} pr_batch_matrix_t;
+
+/* Fills *out for matrix i. Errors: PR_ESTATE (b NULL), PR_EINVAL (bad index, out NULL). */
+pr_status pr_batch_matrix(pr_batch b, int i, pr_batch_matrix_t* out);
 
 /* Kernels launched by the batch so far. */
 int64_t pr_batch_launches(pr_batch b);
@@ -334,7 +389,8 @@ pr_status pr_batch_destroy(pr_batch b);
 
 /* ---- The learned initial guess ---------------------------------------------------------------------------
  * Spectral features of the handle's A for predicting a polynomial initial guess:
- * out[k-1] = tr(Ahat^k) / n for k = 1..6 with Ahat = A / ||A||_1, out[6] = ||A||_1, out[7] = ||A||_inf.
+ * out[k-1] = tr(Ahat^k) / n for k = 1..6 with Ahat = A / ||A||_1, out[6] = ||A||_1, out[7] = ||A||_inf
+ * (the norms of the A the caller gave, before any power-of-two scaling of pr_load).
  * The traces come from Ahat, Ahat^2, Ahat^3 (two PR_EMU64 symmetric products) as Frobenius inner products.
  * out: 8 doubles, host memory. Synchronises the stream. */
 pr_status pr_features(pr_handle h, double* out);
@@ -370,7 +426,7 @@ pr_status pr_mlp_destroy(pr_mlp m);
  * cudaFree, e.g. work issued while a CUDA graph is being captured (allocation calls are not part of a
  * capture), latency-critical paths that cannot afford the synchronisation cudaFree implies, or programs
  * whose device memory is already reserved in full by their own allocator.
- *   A       n*n FP64, row-major, device memory, read only
+ *   A       n*n FP64, row-major, device memory, read only; a NaN entry makes both norms NaN
  *   n       1 <= n <= PR_NORMS_NOALLOC_MAX_N, else PR_EINVAL (nothing is launched)
  *   out     device memory, 2 doubles: out[0] = ||A||_1 (largest absolute column sum),
  *           out[1] = ||A||_inf (largest absolute row sum); written asynchronously on stream
@@ -378,8 +434,10 @@ pr_status pr_mlp_destroy(pr_mlp m);
  * Scratch: a fixed 1 MiB array in the library's device memory (2 * PR_NORMS_NOALLOC_MAX_N doubles) that
  * every device which loads the library keeps until the process exits. The first call on a device looks up
  * that array's device address (cudaGetSymbolAddress); make that first call before any stream capture
- * begins. All calls on a device share the array and each call overwrites what it uses, so calls that
- * overlap on the GPU (on different streams, or from different threads) race and must be serialised.
+ * begins. The address is kept for the life of the process: after cudaDeviceReset the library must not be
+ * called on that device again. All calls on a device share the array and each call overwrites what it
+ * uses, so calls that overlap on the GPU (on different streams, or from different threads) race and must
+ * be serialised.
  * Allocates nothing: no cudaMalloc, cudaFree or allocating library routine. Errors: PR_EINVAL, PR_ECUDA. */
 pr_status pr_norms_noalloc(const double* A, int64_t n, double* out, void* stream);
 

@@ -437,6 +437,29 @@ pr_status literal_update(pr_handle h, int prec) {
   return PR_OK;
 }
 
+// True residual ||I - C^p A||_F of the current iterate: C^p by symmetric products (powers of a symmetric
+// matrix are symmetric), then the full product with A, with products at the given precision.
+pr_status true_residual(pr_handle h, int precision, double* res_fro) {
+  if (lowp(precision)) {
+    pr_status s = refresh_lowp(h);
+    if (s != PR_OK) return s;
+  }
+  Mat* P = &h->X;
+  for (int j = 2; j <= h->p; ++j) {
+    Out o;
+    o.out = (j & 1) ? &h->T1 : &h->T0;
+    o.out_master = false;
+    pr_status s = product(h, precision, h->X, *P, Mode::Sym, o);
+    if (s != PR_OK) return s;
+    P = o.out;
+  }
+  Out o;
+  o.partial = true;
+  pr_status s = product(h, precision, *P, h->A, Mode::Full, o);
+  if (s != PR_OK) return s;
+  return read_residual(h, tiles_for(h, precision, Mode::Full), res_fro);
+}
+
 }  // namespace
 
 // The stop rule (see pr_stop_rule): returns a pr_status to stop with, or -1 to apply one more update.
@@ -572,6 +595,14 @@ pr_status poly_initial_guess(pr_handle h) {
   h->st.c0 = ok ? PR_C0_POLY : PR_C0_EQ3;
   if (!ok) PR_CK(h, pr::init_c0_eq3(h->A.f, n, 1.0 / (h->st.norm_1 * h->st.norm_inf), h->X.f, h->stream));
   h->X.sl_valid = false;
+  if (!ok && !h->opt.gate_fallback) {
+    char buf[200];
+    snprintf(buf, sizeof buf,
+             "the polynomial initial guess failed its gate (estimate of ||I - C_0^p A||_2 = %.3g, limit %.3g, or q not "
+             "positive on the spectrum); the handle holds Eq. 3's C_0",
+             gate, h->opt.gate_max);
+    return fail(h, PR_EGATE, buf);
+  }
   return PR_OK;
 }
 
@@ -588,6 +619,7 @@ void reset_iteration(pr_handle h) {
   h->st.switch_iteration = -1;
   h->st.last_precision = -1;
   h->st.last_residual = 0.0;
+  h->st.true_residual = -1.0;
 }
 
 // C_0 of the loaded A (Eq. 3, the scaled identity, or the gated polynomial) into X.
@@ -601,6 +633,10 @@ pr_status form_initial_guess(pr_handle h) {
     PR_CK(h, pr::set_scaled_identity(h->X.f, n, pow(h->st.norm_1, -1.0 / h->p), h->stream));
   } else {
     pr_status st = poly_initial_guess(h);
+    if (st == PR_EGATE) {
+      const pr_status s2 = sync(h);
+      return s2 == PR_OK ? PR_EGATE : s2;
+    }
     if (st != PR_OK) return st;
   }
   h->X.sl_valid = false;
@@ -716,6 +752,8 @@ void pr_default_options(pr_options* o) {
   o->c0_coef[1] = o->c0_coef[2] = o->c0_coef[3] = 0.0;
   o->gate_max = 0.9;
   o->gate_iters = 30;
+  o->verify = 1;
+  o->gate_fallback = 1;
 }
 
 const char* pr_last_error(pr_handle h) { return h ? h->err.c_str() : g_init_error.c_str(); }
@@ -778,6 +816,7 @@ pr_status pr_init(pr_handle* out, const double* A, int64_t n, int p, const pr_op
   h->st.c0 = o.c0;
   h->st.switch_iteration = -1;
   h->st.last_precision = -1;
+  h->st.true_residual = -1.0;
   cudaGetDevice(&h->device);
 
   auto bail = [&](pr_status code) {
@@ -856,9 +895,27 @@ pr_status pr_load(pr_handle h, const double* A) {
              h->opt.sym_tol);
     return fail(h, PR_EINVAL, buf);
   }
-  if (nonpos > 0) return fail(h, PR_ENOTSPD, "pr_load: A has a non-positive diagonal entry");
+  if (nonpos > 0)
+    return fail(h, PR_ENOTSPD,
+                "pr_load: A is not positive definite (a non-positive diagonal entry, or a diagonal block of order 64 "
+                "without a Cholesky factorisation)");
   h->st.norm_1 = h->hpin[4];
   h->st.norm_inf = h->hpin[5];
+  h->st.prescale_log2 = 0;
+  if (h->p > 1 && h->st.norm_1 * h->st.norm_inf < 1.0) {
+    // Eq. 2 for Eq. 3's C_0 needs ||A||_1 >= 1 when p > 1 (eigenvalues of C_0^p A up to ||A||_1^(1-p)):
+    // iterate on 2^k A with ||2^k A||_1 = 2 f in [1, 2) (||A||_1 = f 2^e, f in [0.5, 1)). A power of two
+    // scales exactly; pr_result multiplies the root by 2^(k/p).
+    int e = 0;
+    frexp(h->st.norm_1, &e);
+    const int k = 1 - e;
+    const double c = ldexp(1.0, k);
+    PR_CK(h, pr::lincomb(h->A.f, h->A.f, (int64_t)n * n, c, 0.0, h->A.f, h->stream));
+    h->st.launches += 1;
+    h->st.norm_1 *= c;
+    h->st.norm_inf *= c;
+    h->st.prescale_log2 = k;
+  }
   return form_initial_guess(h);
 }
 
@@ -1081,6 +1138,26 @@ pr_status pr_iterate(pr_handle h, int max_steps, int precision, double tol, int*
     ++steps;
   }
   if (steps_done) *steps_done = steps;
+  if (stop != PR_EDIVERGED) {
+    if (h->form != PR_FORM_COUPLED) {
+      h->st.true_residual = h->hist.back();  // the tested residual is the true one
+    } else if (h->opt.verify) {
+      // The coupled form tested ||I - M||_F; the true residual of the iterate can be far larger when
+      // rounding errors carried in M let X drift (Eq. 3's M_0 spans kappa^(p+1)).
+      double r = 0.0;
+      s = true_residual(h, precision, &r);
+      if (s != PR_OK) return s;
+      h->st.true_residual = r;
+      if (stop == PR_OK && !(r <= tol)) {
+        char buf[200];
+        snprintf(buf, sizeof buf,
+                 "pr_iterate: ||I - M||_F = %.3e met tol = %.3e, but the true residual ||I - X^p A||_F = %.3e does not",
+                 h->hist.back(), tol, r);
+        h->err = buf;
+        stop = PR_EINACCURATE;
+      }
+    }
+  }
   h->st.last_stop = stop;
   if (stop == PR_EDIVERGED) h->err = "pr_iterate: the residual is not finite";
   return (pr_status)stop;
@@ -1101,7 +1178,7 @@ pr_status pr_solve(pr_handle h, int bulk_precision, int bulk_steps, int final_pr
   if (bulk_steps > 0) {
     pr_status s = pr_iterate(h, bulk_steps, bulk_precision, tol, &d1);
     if (steps_done) *steps_done = d1;
-    if (s != PR_ESTAGNATED && s != PR_EMAXITER) return s;
+    if (s != PR_ESTAGNATED && s != PR_EMAXITER && s != PR_EINACCURATE) return s;
   }
   pr_status s = pr_iterate(h, 1 << 30, final_precision, tol, &d2);
   if (steps_done) *steps_done = d1 + d2;
@@ -1113,25 +1190,7 @@ pr_status pr_residual(pr_handle h, int precision, double* res_fro) {
   if (!res_fro) return fail(h, PR_EINVAL, "pr_residual: res_fro is NULL");
   if (!precision_known(precision)) return fail(h, PR_EINVAL, "pr_residual: unknown precision");
   cudaSetDevice(h->device);
-  if (lowp(precision)) {
-    pr_status s = refresh_lowp(h);
-    if (s != PR_OK) return s;
-  }
-  // C^p by symmetric products (powers of a symmetric matrix are symmetric), then the full product with A.
-  Mat* P = &h->X;
-  for (int j = 2; j <= h->p; ++j) {
-    Out o;
-    o.out = (j & 1) ? &h->T1 : &h->T0;
-    o.out_master = false;
-    pr_status s = product(h, precision, h->X, *P, Mode::Sym, o);
-    if (s != PR_OK) return s;
-    P = o.out;
-  }
-  Out o;
-  o.partial = true;
-  pr_status s = product(h, precision, *P, h->A, Mode::Full, o);
-  if (s != PR_OK) return s;
-  return read_residual(h, tiles_for(h, precision, Mode::Full), res_fro);
+  return true_residual(h, precision, res_fro);
 }
 
 pr_status pr_result(pr_handle h, double* C_out) {
@@ -1139,7 +1198,17 @@ pr_status pr_result(pr_handle h, double* C_out) {
   if (!C_out) return fail(h, PR_EINVAL, "pr_result: C_out is NULL");
   cudaSetDevice(h->device);
   const size_t bytes = (size_t)h->n * (size_t)h->n * sizeof(double);
-  PR_CK(h, cudaMemcpyAsync(C_out, h->X.f, bytes, cudaMemcpyDefault, h->stream));
+  const double* src = h->X.f;
+  if (h->st.prescale_log2 != 0) {
+    // The handle iterates on 2^k A: A^{-1/p} = 2^(k/p) (2^k A)^{-1/p}, scaled into the scratch product T1.
+    PR_CK(h, pr::lincomb(h->X.f, h->X.f, h->n * h->n, exp2((double)h->st.prescale_log2 / h->p), 0.0, h->T1.f,
+                         h->stream));
+    h->st.launches += 1;
+    h->T1.sl_valid = false;
+    h->powers_valid = false;
+    src = h->T1.f;
+  }
+  PR_CK(h, cudaMemcpyAsync(C_out, src, bytes, cudaMemcpyDefault, h->stream));
   return sync(h);
 }
 
@@ -1181,8 +1250,8 @@ pr_status pr_features(pr_handle h, double* out) {
     sk *= s1;
     out[k] = t[k] / sk / n;  // tr(A^{k+1}) / s^{k+1} / n
   }
-  out[6] = h->st.norm_1;
-  out[7] = h->st.norm_inf;
+  out[6] = ldexp(h->st.norm_1, -h->st.prescale_log2);  // the norms of the caller's A
+  out[7] = ldexp(h->st.norm_inf, -h->st.prescale_log2);
   return PR_OK;
 }
 

@@ -9,7 +9,8 @@
 //
 // The whole solve is one CUDA graph, launched once per pr_batch_solve: a prologue (the coupled start
 // M_0 = X_0^p A), then a device-side while loop whose body is two iterations (the FP64 buffers alternate,
-// so two iterations bring them back), then the timing harvest. Every decision between launches (which
+// so two iterations bring them back), then the verification (the true residual ||I - X^p A||_F of every
+// coupled-form matrix that stopped, as pr_iterate evaluates it) and the timing harvest. Every decision between launches (which
 // matrices take part in a stage, their residuals, their stop rules, the loop condition) is taken by the
 // control kernels of k_batch.cu from state kept on the device, so the host neither waits nor builds work
 // lists during the solve. The graph is captured on the first pr_batch_solve and reused.
@@ -58,10 +59,16 @@ struct pr_batch_s {
   int device = 0;
   pr_options opt{};
   std::vector<int> n, p, row0, form;
+  std::vector<int> pre;                    // per matrix: the batch iterates on 2^pre A (Eq. 2 scaling)
+  std::vector<double> norm1, norminf;      // per matrix: norms of the matrix iterated on
+  std::vector<double> true_res;            // per matrix: true residual at the stop (-1: none)
   Buf A, X, Xn, M, Mn, N, Nn, T0, T1;
   double* result = nullptr;  // packed results
   int* row_n = nullptr;      // order of the matrix owning each packed row (-1 once it stopped)
   int* row_n_p3 = nullptr;   // the same for rows of p = 3 matrices, -1 on every other row
+  int* row_v = nullptr;      // the same for rows of matrices being verified after the loop
+  const int* slice_rows = nullptr;  // the per-row orders the digit slicing follows (row_n, or row_v)
+  double* truer = nullptr;   // per matrix: true residual from the verification (-1: not verified)
   double* partial = nullptr;
   int4* items = nullptr;     // the current stage's work list
   int* err = nullptr;
@@ -119,7 +126,7 @@ pr_status bfail(pr_batch b, pr_status code, const std::string& msg) {
 
 pr_status ensure_slices(pr_batch b, Buf& x) {
   if (x.sl_valid) return PR_OK;
-  PB_CK(b, pr::slice_rows(x.f, b->R, b->K, b->ld, pr::emu_ld(b->K), b->S, b->row_n, x.sl, x.ex, b->stream));
+  PB_CK(b, pr::slice_rows(x.f, b->R, b->K, b->ld, pr::emu_ld(b->K), b->S, b->slice_rows, x.sl, x.ex, b->stream));
   b->cnt += 1;
   x.sl_valid = true;
   return PR_OK;
@@ -162,7 +169,7 @@ pr_status stage(pr_batch b, Buf& Xb, Buf& Yb, const BatchStage& sp, const StageO
                                 b->scratch, b->err, b->tstamp + 2 * st.slot, b->stream));
   b->cnt += 2;
   if (so.partial) {
-    PB_CK(b, pr::batch_residuals(b->ctl, b->partial, b->stream));
+    PB_CK(b, pr::batch_residuals(b->ctl, b->partial, sp.verify, b->stream));
     b->cnt += 1;
   }
   if (so.out) so.out->sl_valid = false;
@@ -264,6 +271,44 @@ void invalidate_slices(pr_batch b) {
   for (Buf* x : {&b->A, &b->X, &b->Xn, &b->M, &b->Mn, &b->N, &b->Nn, &b->T0, &b->T1}) x->sl_valid = false;
 }
 
+// After the solve loop: ||I - X^p A||_F of every coupled-form matrix that stopped on tol, stagnation or
+// max_iter, in the order of pr_residual (P_j = X P_{j-1} symmetric for j = 2..p, then the full product
+// P_p A), with X the stopped iterate in the results. Members of stage j are the verified matrices with
+// p >= j; P_j lands in T0 (j even) or T1 (j odd), rows of different matrices never overlap, so P_p of a
+// matrix with p = j survives later stages and its final product runs right after. The loop's state
+// buffers are free by now: the results' digit planes go into Mn's.
+pr_status verify(pr_batch b) {
+  PB_CK(b, pr::batch_verify_rows(b->ctl, b->stream));
+  b->cnt += 1;
+  invalidate_slices(b);
+  b->A.sl_valid = true;  // sliced on every row by the prologue and not changed since
+  b->slice_rows = b->row_v;
+  Buf R;
+  R.f = b->result;
+  R.sl = b->Mn.sl;
+  R.ex = b->Mn.ex;
+  Buf* P = &R;
+  pr_status s = PR_OK;
+  for (int j = 2; j <= b->pmax && s == PR_OK; ++j) {
+    Buf& out = (j & 1) ? b->T1 : b->T0;
+    StageOut o;
+    o.out = &out;
+    BatchStage st = spec(0, PR_FORM_COUPLED, 2, j - 1, 0);
+    st.verify = 1;
+    s = stage(b, R, *P, st, o);
+    if (s != PR_OK) break;
+    P = &out;
+    StageOut f;
+    f.partial = true;
+    BatchStage sf = spec(1, PR_FORM_COUPLED, 1, j, 0);
+    sf.verify = 1;
+    s = stage(b, out, b->A, sf, f);
+  }
+  b->slice_rows = b->row_n;
+  invalidate_slices(b);
+  return s;
+}
+
 // Captures the solve graph (prologue, while loop of two iterations, harvest) on a private stream.
 pr_status build_graph(pr_batch b) {
   PB_CK(b, pr::emu_prepare());
@@ -331,6 +376,10 @@ pr_status build_graph(pr_batch b) {
   }
   if (s == PR_OK) {
     s = capture(b->graph, &loop, 1, [&]() -> pr_status {
+      if (b->pmax >= 2 && b->opt.verify) {
+        pr_status r = verify(b);
+        if (r != PR_OK) return r;
+      }
       PB_CK(b, pr::batch_harvest(b->ctl, b->nslots, b->stream));
       b->cnt += 1;
       return PR_OK;
@@ -377,6 +426,7 @@ pr_status load(pr_batch b, const double* const* A, const char* who) {
     b->status[m] = -1;
     b->iterations[m] = 0;
     b->hist[m].clear();
+    b->true_res[m] = -1.0;
   }
   // Per matrix: checks and the norms of Eq. 3 (all matrices queued, one read-back), then C_0; staged
   // through an n x n work area on the batch's stream, without waiting between matrices.
@@ -401,7 +451,32 @@ pr_status load(pr_batch b, const double* const* A, const char* who) {
     if (h[2] > 0 || h[1] > b->opt.sym_tol * h[0])
       return bfail(b, PR_EINVAL, std::string(who) + ": matrix " + std::to_string(m) + " is not finite and symmetric");
     if (h[3] > 0)
-      return bfail(b, PR_ENOTSPD, std::string(who) + ": matrix " + std::to_string(m) + " has a non-positive diagonal");
+      return bfail(b, PR_ENOTSPD, std::string(who) + ": matrix " + std::to_string(m) +
+                                      " is not positive definite (a non-positive diagonal entry, or a diagonal block "
+                                      "of order 64 without a Cholesky factorisation)");
+  }
+  // Eq. 2 for Eq. 3's C_0 with p > 1 needs ||A||_1 >= 1: such matrices are scaled by an exact power of two
+  // into ||2^k A||_1 in [1, 2), as pr_load does; pr_batch_result scales the root back by 2^(k/p).
+  for (int m = 0; m < count && e == cudaSuccess; ++m) {
+    double* h = b->hs + 8 * m;
+    b->pre[m] = 0;
+    if (b->p[m] > 1 && h[4] * h[5] < 1.0) {
+      const int nm = b->n[m];
+      const size_t pitch = (size_t)b->ld * sizeof(double), w = (size_t)nm * sizeof(double);
+      int ex = 0;
+      frexp(h[4], &ex);
+      const double c = ldexp(1.0, 1 - ex);
+      double* rows = b->A.f + (size_t)b->row0[m] * b->ld;
+      e = cudaMemcpy2DAsync(b->tA, w, rows, pitch, w, nm, cudaMemcpyDeviceToDevice, b->stream);
+      if (e == cudaSuccess) e = pr::lincomb(b->tA, b->tA, (int64_t)nm * nm, c, 0.0, b->tA, b->stream);
+      if (e == cudaSuccess) e = cudaMemcpy2DAsync(rows, pitch, b->tA, w, w, nm, cudaMemcpyDeviceToDevice, b->stream);
+      b->launches += 1;
+      h[4] *= c;
+      h[5] *= c;
+      b->pre[m] = 1 - ex;
+    }
+    b->norm1[m] = h[4];
+    b->norminf[m] = h[5];
   }
   for (int m = 0; m < count && e == cudaSuccess; ++m) {
     const int nm = b->n[m];
@@ -440,7 +515,8 @@ pr_status pr_batch_destroy(pr_batch b) {
     if (x->sl) cudaFree(x->sl);
     if (x->ex) cudaFree(x->ex);
   }
-  for (void* q : {(void*)b->result, (void*)b->row_n, (void*)b->row_n_p3, (void*)b->partial, (void*)b->items, (void*)b->err,
+  for (void* q : {(void*)b->result, (void*)b->row_n, (void*)b->row_n_p3, (void*)b->row_v, (void*)b->truer,
+                  (void*)b->partial, (void*)b->items, (void*)b->err,
                   (void*)b->scratch, (void*)b->d_static, (void*)b->d_items_all, (void*)b->d_state, (void*)b->d_dstate,
                   (void*)b->d_stage, (void*)b->mats, (void*)b->tstamp, (void*)b->flops_pending, (void*)b->tA,
                   (void*)b->tC, (void*)b->scal, (void*)b->work})
@@ -487,6 +563,10 @@ pr_status pr_batch_init(pr_batch* out, int count, const int64_t* n, const int* p
   b->row0.resize(count);
   b->form.resize(count);
   b->hist.resize(count);
+  b->pre.assign(count, 0);
+  b->norm1.assign(count, 0.0);
+  b->norminf.assign(count, 0.0);
+  b->true_res.assign(count, -1.0);
   b->status.assign(count, -1);
   b->iterations.assign(count, 0);
   b->hcap = o.max_iter + 2;
@@ -524,6 +604,9 @@ pr_status pr_batch_init(pr_batch* out, int count, const int64_t* n, const int* p
   PB_INIT_CK(cudaMalloc((void**)&b->result, fbytes));
   PB_INIT_CK(cudaMalloc((void**)&b->row_n, (size_t)b->R * sizeof(int)));
   PB_INIT_CK(cudaMalloc((void**)&b->row_n_p3, (size_t)b->R * sizeof(int)));
+  PB_INIT_CK(cudaMalloc((void**)&b->row_v, (size_t)b->R * sizeof(int)));
+  PB_INIT_CK(cudaMalloc((void**)&b->truer, (size_t)count * sizeof(double)));
+  b->slice_rows = b->row_n;
   // Every matrix's work items (symmetric and full) and the device-side control state.
   std::vector<int4> isym, ifull;
   std::vector<int> stat(9 * (size_t)count);
@@ -616,6 +699,8 @@ pr_status pr_batch_init(pr_batch* out, int count, const int64_t* n, const int* p
     c.row_n = b->row_n;
     c.row_n2 = b->row_n_p3;
     c.err = b->err;
+    c.truer = b->truer;
+    c.row_v = b->row_v;
   }
   PB_INIT_CK(cudaMalloc((void**)&b->tA, (size_t)K * K * sizeof(double)));
   PB_INIT_CK(cudaMalloc((void**)&b->tC, (size_t)K * K * sizeof(double)));
@@ -658,6 +743,10 @@ pr_status pr_batch_solve(pr_batch b, int precision, double tol, int* iterations,
   PB_CK(b, cudaMemcpyAsync(b->h_dstate, b->d_dstate, (hist_len + 8) * sizeof(double), cudaMemcpyDeviceToHost,
                            b->stream));
   PB_CK(b, cudaMemcpyAsync(&b->h_err, b->err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  const bool verified = b->pmax >= 2 && b->opt.verify;
+  if (verified)
+    PB_CK(b, cudaMemcpyAsync(b->true_res.data(), b->truer, (size_t)count * sizeof(double), cudaMemcpyDeviceToHost,
+                             b->stream));
   PB_CK(b, cudaStreamSynchronize(b->stream));
   // Launches: the prologue and the harvest once, the loop body once per pass.
   const int loops = b->h_state[4 * count];
@@ -677,6 +766,13 @@ pr_status pr_batch_solve(pr_batch b, int precision, double tol, int* iterations,
     b->iterations[m] = b->h_state[2 * count + m];
     const int len = b->h_state[3 * count + m];
     b->hist[m].assign(b->h_dstate + (size_t)m * b->hcap, b->h_dstate + (size_t)m * b->hcap + len);
+    if (b->form[m] != PR_FORM_COUPLED) {
+      b->true_res[m] = (b->status[m] >= 0 && b->status[m] != PR_EDIVERGED && len > 0) ? b->hist[m].back() : -1.0;
+    } else if (!verified) {
+      b->true_res[m] = -1.0;
+    } else if (b->status[m] == PR_OK && !(b->true_res[m] <= tol)) {
+      b->status[m] = PR_EINACCURATE;  // ||I - M||_F met tol, the true residual did not (see pr_iterate)
+    }
     if (iterations) iterations[m] = b->iterations[m];
     if (status) status[m] = b->status[m];
   }
@@ -697,9 +793,35 @@ pr_status pr_batch_result(pr_batch b, int i, double* C_out) {
   if (b->status[i] < 0) return bfail(b, PR_ESTATE, "pr_batch_result: matrix not solved yet");
   cudaSetDevice(b->device);
   const size_t w = (size_t)b->n[i] * sizeof(double);
-  PB_CK(b, cudaMemcpy2DAsync(C_out, w, b->result + (size_t)b->row0[i] * b->ld, (size_t)b->ld * sizeof(double), w,
-                             b->n[i], cudaMemcpyDefault, b->stream));
+  const double* rows = b->result + (size_t)b->row0[i] * b->ld;
+  if (b->pre[i] != 0) {
+    // The batch iterated on 2^k A: the root of A is 2^(k/p) times the result.
+    const int64_t nn = (int64_t)b->n[i] * b->n[i];
+    PB_CK(b, cudaMemcpy2DAsync(b->tA, w, rows, (size_t)b->ld * sizeof(double), w, b->n[i], cudaMemcpyDeviceToDevice,
+                               b->stream));
+    PB_CK(b, pr::lincomb(b->tA, b->tA, nn, exp2((double)b->pre[i] / b->p[i]), 0.0, b->tA, b->stream));
+    b->launches += 1;
+    PB_CK(b, cudaMemcpyAsync(C_out, b->tA, (size_t)nn * sizeof(double), cudaMemcpyDefault, b->stream));
+  } else {
+    PB_CK(b, cudaMemcpy2DAsync(C_out, w, rows, (size_t)b->ld * sizeof(double), w, b->n[i], cudaMemcpyDefault,
+                               b->stream));
+  }
   PB_CK(b, cudaStreamSynchronize(b->stream));
+  return PR_OK;
+}
+
+pr_status pr_batch_matrix(pr_batch b, int i, pr_batch_matrix_t* out) {
+  if (!b) return bfail(nullptr, PR_ESTATE, "pr_batch_matrix: NULL batch");
+  if (i < 0 || i >= b->count || !out) return bfail(b, PR_EINVAL, "pr_batch_matrix: bad index or NULL output");
+  out->n = b->n[i];
+  out->p = b->p[i];
+  out->form = b->form[i];
+  out->status = b->status[i];
+  out->iterations = b->iterations[i];
+  out->norm_1 = b->norm1[i];
+  out->norm_inf = b->norminf[i];
+  out->prescale_log2 = b->pre[i];
+  out->true_residual = b->true_res[i];
   return PR_OK;
 }
 

@@ -7,6 +7,8 @@
 //  * k_batch_decide: the stop rule of every iterating matrix (the rule of pr_iterate); a matrix that stops
 //    has its iterate copied to the results and its rows dropped from the digit slicing;
 //  * k_batch_advance: one more update counted per iterating matrix, and the loop condition;
+//  * k_batch_verify_rows: after the loop, the coupled-form matrices whose true residual ||I - X^p A||_F the
+//    verification stages evaluate (their partials go to a per-matrix true residual, not the history);
 //  * timing: each product launch folds its first start and last end time into a slot (%globaltimer); the
 //    next list build for the same slot, or k_batch_harvest, adds that span to the tally.
 #include "pr_internal.h"
@@ -18,11 +20,23 @@ namespace {
 
 constexpr int kCtlThreads = 1024;  // one block builds a stage's list
 
+// A matrix stopped on tol, stagnation or max_iter (not diverged) whose true residual the verification
+// after the solve loop evaluates: the coupled form tests ||I - M||_F, which rounding can separate from it.
+__device__ __forceinline__ bool to_verify(const BatchCtl& c, int m) {
+  const int s = c.status[m];
+  return !c.active[m] && c.form[m] == PR_FORM_COUPLED && (s == PR_OK || s == PR_ESTAGNATED || s == PR_EMAXITER);
+}
+
 __device__ __forceinline__ bool stage_member(const BatchCtl& c, const BatchStage& st, int m) {
-  if (!c.active[m] || c.form[m] != st.form) return false;
+  if (st.verify) {
+    if (!to_verify(c, m)) return false;
+  } else if (!c.active[m] || c.form[m] != st.form) {
+    return false;
+  }
   const int p = c.p[m];
   if (st.pcmp == 1 && p != st.pj) return false;
   if (st.pcmp == 2 && p <= st.pj) return false;
+  if (st.verify) return true;
   if (st.fresh_only && c.hlen[m] != 0) return false;
   if (st.pskip != 0 && p == st.pskip) return false;
   return true;
@@ -135,12 +149,14 @@ __global__ void __launch_bounds__(kCtlThreads) k_batch_stage(BatchCtl c, BatchSt
   }
 }
 
-__global__ void k_batch_residuals(BatchCtl c, const double* __restrict__ partial) {
+__global__ void k_batch_residuals(BatchCtl c, const double* __restrict__ partial, int to_true) {
   __shared__ double sh[kReduceThreads];
   const int m = blockIdx.x;
   if (!c.member[m]) return;  // uniform over the block
   const double r = block_sum_sqrt(partial + c.seg_b[m], c.seg_e[m] - c.seg_b[m], sh);
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && to_true) {
+    c.truer[m] = r;
+  } else if (threadIdx.x == 0) {
     const int len = c.hlen[m];
     if (len < c.hcap) {
       c.hist[(size_t)m * c.hcap + len] = r;
@@ -215,6 +231,14 @@ __global__ void __launch_bounds__(256) k_batch_lincomb(BatchCtl c, int pj, const
     }
 }
 
+// Block m: the rows of matrix m get its order if it is verified, else -1; its true residual is reset.
+__global__ void k_batch_verify_rows(BatchCtl c) {
+  const int m = blockIdx.x;
+  const int v = to_verify(c, m) ? c.n[m] : -1, r0 = c.row0[m];
+  for (int r = threadIdx.x; r < c.n[m]; r += blockDim.x) c.row_v[r0 + r] = v;
+  if (threadIdx.x == 0) c.truer[m] = -1.0;
+}
+
 __global__ void k_batch_harvest(BatchCtl c, int nslots) {
   if (threadIdx.x == 0)
     for (int k = 0; k < nslots; ++k) harvest_slot(c, k);
@@ -227,8 +251,13 @@ cudaError_t batch_stage_list(const BatchCtl& c, const BatchStage& st, cudaStream
   return cudaGetLastError();
 }
 
-cudaError_t batch_residuals(const BatchCtl& c, const double* partial, cudaStream_t s) {
-  k_batch_residuals<<<c.count, kReduceThreads, 0, s>>>(c, partial);
+cudaError_t batch_residuals(const BatchCtl& c, const double* partial, int to_true, cudaStream_t s) {
+  k_batch_residuals<<<c.count, kReduceThreads, 0, s>>>(c, partial, to_true);
+  return cudaGetLastError();
+}
+
+cudaError_t batch_verify_rows(const BatchCtl& c, cudaStream_t s) {
+  k_batch_verify_rows<<<c.count, 256, 0, s>>>(c);
   return cudaGetLastError();
 }
 

@@ -13,8 +13,11 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+// The larger of a and b, NaN if either is NaN (fmax would drop a NaN and hide a non-finite input).
+__device__ __forceinline__ double nan_max(double a, double b) { return (a > b || a != a) ? a : b; }
+
 __device__ __forceinline__ double warp_max(double v) {
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) v = nan_max(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
 
@@ -78,20 +81,52 @@ __global__ void k_abs_colsum(const double* __restrict__ A, int n, double* __rest
   }
 }
 
-// out[0] = max(cols), out[1] = max(rows); one block.
+// out[0] = max(cols), out[1] = max(rows); one block. A NaN sum (from a NaN entry of A) gives a NaN maximum.
 __global__ void k_max2(const double* __restrict__ cols, const double* __restrict__ rows, int n, double* __restrict__ out) {
   __shared__ double sc[kThreads / 32], sr[kThreads / 32];
   double mc = 0.0, mr = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) { mc = fmax(mc, cols[i]); mr = fmax(mr, rows[i]); }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) { mc = nan_max(mc, cols[i]); mr = nan_max(mr, rows[i]); }
   mc = warp_max(mc);
   mr = warp_max(mr);
   if ((threadIdx.x & 31) == 0) { sc[threadIdx.x >> 5] = mc; sr[threadIdx.x >> 5] = mr; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int w = 1; w < kThreads / 32; ++w) { mc = fmax(mc, sc[w]); mr = fmax(mr, sr[w]); }
-    out[0] = fmax(mc, sc[0]);
-    out[1] = fmax(mr, sr[0]);
+    for (int w = 1; w < kThreads / 32; ++w) { mc = nan_max(mc, sc[w]); mr = nan_max(mr, sr[w]); }
+    out[0] = nan_max(mc, sc[0]);
+    out[1] = nan_max(mr, sr[0]);
   }
+}
+
+// Cholesky factorisation of every diagonal block of order 64 (the last one smaller), one block of 64
+// threads each, in shared memory: a principal submatrix of an SPD matrix is SPD, so a pivot that is not
+// positive shows that A is not. Right-looking, thread t owns row t of the lower triangle. Adds the number
+// of failing blocks to *bad.
+constexpr int kCholB = 64;
+__global__ void __launch_bounds__(kCholB) k_diag_cholesky(const double* __restrict__ A, int n, double* __restrict__ bad) {
+  __shared__ double L[kCholB][kCholB + 1];
+  __shared__ int fail;
+  const int b0 = blockIdx.x * kCholB, m = min(kCholB, n - b0), t = threadIdx.x;
+  for (int i = 0; i < m; ++i)
+    if (t < m) L[i][t] = A[(int64_t)(b0 + i) * n + b0 + t];
+  if (t == 0) fail = 0;
+  __syncthreads();
+  for (int j = 0; j < m; ++j) {
+    if (t == 0) {
+      const double d = L[j][j];
+      if (d > 0.0) L[j][j] = sqrt(d);
+      else fail = 1;
+    }
+    __syncthreads();
+    if (fail) break;  // uniform: read after the barrier
+    if (t > j && t < m) L[t][j] /= L[j][j];
+    __syncthreads();
+    if (t > j && t < m) {
+      const double lt = L[t][j];
+      for (int k = j + 1; k <= t; ++k) L[t][k] -= lt * L[k][j];
+    }
+    __syncthreads();
+  }
+  if (t == 0 && fail) atomicAdd(bad, 1.0);
 }
 
 // X = A^T * inv_s through a 32 x 32 shared-memory transpose (coalesced on both sides).
@@ -177,6 +212,7 @@ cudaError_t validate(const double* A, int n, double* scal4, cudaStream_t s) {
   cudaError_t err = cudaMemsetAsync(scal4, 0, 4 * sizeof(double), s);
   if (err != cudaSuccess) return err;
   k_validate<<<grid_for((int64_t)n * n), kThreads, 0, s>>>(A, n, scal4);
+  k_diag_cholesky<<<(n + kCholB - 1) / kCholB, kCholB, 0, s>>>(A, n, scal4 + 3);
   return cudaGetLastError();
 }
 

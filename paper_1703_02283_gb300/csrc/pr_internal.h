@@ -133,6 +133,7 @@ cudaError_t gemm_emu_batched(const __half* DX, const int* ex, const __half* DY, 
 
 // ---- elementwise and reductions (k_elementwise.cu)
 // scal[0] = max |a_ij|, scal[1] = max |a_ij - a_ji|, scal[2] = #non-finite, scal[3] = #non-positive diagonal
+// entries + #diagonal blocks of order 64 without a Cholesky factorisation (A not positive definite if > 0)
 cudaError_t validate(const double* A, int n, double* scal4, cudaStream_t s);
 // out[0] = ||A||_1 (max column abs-sum), out[1] = ||A||_inf (max row abs-sum); work: 2n doubles
 cudaError_t abs_norms(const double* A, int n, double* work, double* out2, cudaStream_t s);
@@ -239,6 +240,10 @@ struct BatchCtl {
   int* row_n;
   int* row_n2;     // if set: a second per-row order array (-1 for rows not sliced) that stops also clear
   const int* err;
+  // verification after the solve loop: the true residual ||I - X^p A||_F of every coupled-form matrix that
+  // stopped on tol, stagnation or max_iter (-1 for the others), and the per-row orders of those matrices
+  double* truer;
+  int* row_v;
 };
 // Membership of a product stage: matrices of one form that are still iterating, optionally with p == pj
 // (pcmp 1) or p > pj (pcmp 2), optionally only those without a residual yet (fresh_only), and never those
@@ -251,10 +256,15 @@ struct BatchStage {
   int pskip;
   int slot;         // timing slot of the product launch
   double a, b, c;   // epilogue coefficients of the members
+  int verify;       // 1: members are the stopped matrices being verified (batch_verify_rows), not iterating ones
 };
 cudaError_t batch_stage_list(const BatchCtl& c, const BatchStage& st, cudaStream_t s);
-// Residual of every member of the last stage from its partials, appended to its history.
-cudaError_t batch_residuals(const BatchCtl& c, const double* partial, cudaStream_t s);
+// Residual of every member of the last stage from its partials, appended to its history (to_true: stored
+// as the member's true residual instead).
+cudaError_t batch_residuals(const BatchCtl& c, const double* partial, int to_true, cudaStream_t s);
+// Marks the matrices to verify after the solve loop (coupled form, stopped on tol, stagnation or max_iter):
+// their rows get their order in row_v (-1 elsewhere); truer is reset to -1.
+cudaError_t batch_verify_rows(const BatchCtl& c, cudaStream_t s);
 // The stop rule for every iterating matrix; a stopping matrix's rows of X go to the results and leave
 // the digit slicing (row order -1).
 cudaError_t batch_decide(const BatchCtl& c, const double* X, const pr_options& o, cudaStream_t s);

@@ -15,10 +15,10 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libpthroot.so")
 
 # enums (values fixed by include/pthroot.h)
 PR_OK, PR_EINVAL, PR_ENOTSPD, PR_ENOMEM, PR_ECUDA, PR_EDIVERGED, PR_ESTAGNATED = 0, 1, 2, 3, 4, 5, 6
-PR_EMAXITER, PR_ETIMEOUT, PR_EGATE, PR_ESTATE, PR_EUNSUPPORTED = 7, 8, 9, 10, 11
+PR_EMAXITER, PR_ETIMEOUT, PR_EGATE, PR_ESTATE, PR_EUNSUPPORTED, PR_EINACCURATE = 7, 8, 9, 10, 11, 12
 STATUS_NAMES = {0: "PR_OK", 1: "PR_EINVAL", 2: "PR_ENOTSPD", 3: "PR_ENOMEM", 4: "PR_ECUDA",
                 5: "PR_EDIVERGED", 6: "PR_ESTAGNATED", 7: "PR_EMAXITER", 8: "PR_ETIMEOUT",
-                9: "PR_EGATE", 10: "PR_ESTATE", 11: "PR_EUNSUPPORTED"}
+                9: "PR_EGATE", 10: "PR_ESTATE", 11: "PR_EUNSUPPORTED", 12: "PR_EINACCURATE"}
 PR_FP64, PR_EMU64, PR_BF16 = 0, 1, 3
 PR_FORM_AUTO, PR_FORM_COUPLED, PR_FORM_NS, PR_FORM_LITERAL = 0, 1, 2, 3
 PR_C0_EQ3, PR_C0_SCALED_I, PR_C0_POLY = 0, 1, 2
@@ -30,7 +30,7 @@ class pr_options(ctypes.Structure):
                 ("stag_below", ctypes.c_double), ("stag_ratio", ctypes.c_double),
                 ("sym_tol", ctypes.c_double), ("reanchor", ctypes.c_int), ("emu_slices", ctypes.c_int),
                 ("stag_below_lowp", ctypes.c_double), ("c0_coef", ctypes.c_double * 4), ("gate_max", ctypes.c_double),
-                ("gate_iters", ctypes.c_int)]
+                ("gate_iters", ctypes.c_int), ("verify", ctypes.c_int), ("gate_fallback", ctypes.c_int)]
 
 
 class pr_stats_t(ctypes.Structure):
@@ -42,7 +42,8 @@ class pr_stats_t(ctypes.Structure):
                 ("launches", ctypes.c_int64), ("gemms_timed", ctypes.c_int64), ("gemm_ms", ctypes.c_double),
                 ("gemm_flops_timed", ctypes.c_double), ("emu_slices", ctypes.c_int),
                 ("gemms_timed_by_precision", ctypes.c_int64 * 4), ("gemm_ms_by_precision", ctypes.c_double * 4),
-                ("gemm_flops_by_precision", ctypes.c_double * 4), ("c0_gate", ctypes.c_double)]
+                ("gemm_flops_by_precision", ctypes.c_double * 4), ("c0_gate", ctypes.c_double),
+                ("true_residual", ctypes.c_double), ("prescale_log2", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -60,6 +61,15 @@ class pr_state_header(ctypes.Structure):
                 ("iterations_by_precision", ctypes.c_int32 * 4), ("switch_iteration", ctypes.c_int32),
                 ("last_precision", ctypes.c_int32), ("hist_len", ctypes.c_int32), ("n_mats", ctypes.c_int32),
                 ("ldl", ctypes.c_int32), ("reserved", ctypes.c_int32), ("last_residual", ctypes.c_double)]
+
+
+class pr_batch_matrix_t(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("p", ctypes.c_int), ("form", ctypes.c_int), ("status", ctypes.c_int),
+                ("iterations", ctypes.c_int), ("norm_1", ctypes.c_double), ("norm_inf", ctypes.c_double),
+                ("prescale_log2", ctypes.c_int), ("true_residual", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class pr_batch_stats_t(ctypes.Structure):
@@ -105,6 +115,7 @@ def _load() -> ctypes.CDLL:
         "pr_batch_history": (ctypes.c_int, [_handle_t, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                             ctypes.POINTER(ctypes.c_int)]),
         "pr_batch_launches": (ctypes.c_int64, [_handle_t]),
+        "pr_batch_matrix": (ctypes.c_int, [_handle_t, ctypes.c_int, ctypes.POINTER(pr_batch_matrix_t)]),
         "pr_batch_stats": (ctypes.c_int, [_handle_t, ctypes.POINTER(pr_batch_stats_t)]),
         "pr_batch_set_timing": (ctypes.c_int, [_handle_t, ctypes.c_int]),
         "pr_batch_last_error": (ctypes.c_char_p, [_handle_t]),
@@ -193,11 +204,12 @@ def pr_set_timing(h: int, on: bool) -> None:
     _check(_lib.pr_set_timing(h, 1 if on else 0), h)
 
 
-STOPS = (PR_OK, PR_ESTAGNATED, PR_EMAXITER)
+STOPS = (PR_OK, PR_ESTAGNATED, PR_EMAXITER, PR_EINACCURATE)
 
 
 def pr_iterate(h: int, max_steps: int, precision: int, tol: float) -> tuple[int, int]:
-    """Returns (status, steps_done); stop statuses (PR_OK, PR_ESTAGNATED, PR_EMAXITER) do not raise."""
+    """Returns (status, steps_done); stop statuses (PR_OK, PR_ESTAGNATED, PR_EMAXITER, PR_EINACCURATE) do not
+    raise."""
     d = ctypes.c_int(0)
     st = _lib.pr_iterate(h, int(max_steps), int(precision), float(tol), ctypes.byref(d))
     _check(st, h, STOPS)
@@ -368,6 +380,12 @@ def pr_batch_history(b: int, i: int) -> list[float]:
     buf = (ctypes.c_double * max(ln.value, 1))()
     _bcheck(_lib.pr_batch_history(b, int(i), buf, ln.value, ctypes.byref(ln)), b)
     return list(buf[: ln.value])
+
+
+def pr_batch_matrix(b: int, i: int) -> dict:
+    s = pr_batch_matrix_t()
+    _bcheck(_lib.pr_batch_matrix(b, int(i), ctypes.byref(s)), b)
+    return s.as_dict()
 
 
 def pr_batch_launches(b: int) -> int:

@@ -36,15 +36,16 @@ def single_emu(case, p, c0=P.PR_C0_EQ3, max_iter=None):
     A = torch.from_numpy(case.A).to(DEV)
     h = P.pr_init(A, case.n, p, o, torch.cuda.current_stream(DEV).cuda_stream)
     try:
-        P.pr_iterate(h, 100, P.PR_EMU64, 1e-12)
+        st, _ = P.pr_iterate(h, 100, P.PR_EMU64, 1e-12)
         C = torch.empty_like(A)
         P.pr_result(h, C)
+        single_emu.last = (st, P.pr_stats(h))
         return C.cpu().numpy(), P.pr_history(h)
     finally:
         P.pr_destroy(h)
 
 
-def run_batch(cases, ps, host=False, c0=P.PR_C0_EQ3, max_iter=None, repeat=False):
+def run_batch(cases, ps, host=False, c0=P.PR_C0_EQ3, max_iter=None, repeat=False, info=None):
     o = P.pr_default_options()
     o.c0 = c0
     if max_iter is not None:
@@ -63,6 +64,8 @@ def run_batch(cases, ps, host=False, c0=P.PR_C0_EQ3, max_iter=None, repeat=False
             return out
 
         out = results()
+        if info is not None:
+            info.extend(P.pr_batch_matrix(b, i) for i in range(len(cases)))
         if repeat:
             # A second solve after every matrix stopped runs the graph once more and changes nothing.
             launches = P.pr_batch_launches(b)
@@ -77,7 +80,8 @@ def run_batch(cases, ps, host=False, c0=P.PR_C0_EQ3, max_iter=None, repeat=False
 
 def test_batch_matches_oracle_and_single_path():
     cases, ps = make_batch(10, 5, 300, 1e3, 7)
-    out, its, sts, launches = run_batch(cases, ps)
+    minfo = []
+    out, its, sts, launches = run_batch(cases, ps, info=minfo)
     assert launches > 0
     for i, (case, p) in enumerate(zip(cases, ps)):
         C, hist = out[i]
@@ -87,10 +91,44 @@ def test_batch_matches_oracle_and_single_path():
         assert O.forward_error(C, Z) <= bound, (i, case.n, p)
         assert O.forward_error(C, Co) <= bound, (i, case.n, p)
         assert abs(its[i] - info.iterations) <= 1
-        assert sts[i] in (P.PR_OK, P.PR_ESTAGNATED)
+        assert sts[i] in (P.PR_OK, P.PR_ESTAGNATED, P.PR_EINACCURATE)
         Cs, hs = single_emu(case, p)
         assert np.array_equal(C, Cs), (i, case.n, p)
         assert hist == hs
+        # The verification after the solve loop reproduces pr_iterate's: same status, same true residual.
+        st1, s1 = single_emu.last
+        assert sts[i] == st1 and minfo[i]["status"] == st1
+        assert minfo[i]["true_residual"] == s1["true_residual"], (i, p)
+        if sts[i] == P.PR_EINACCURATE:
+            assert minfo[i]["true_residual"] > 1e-12 >= hist[-1]
+
+
+def test_batch_prescale_and_verification():
+    # Matrices with ||A||_1 < 1: those with p > 1 are iterated as 2^k A (Eq. 2 for Eq. 3's C_0) and scaled
+    # back, as the single-matrix path does; every result meets the oracle's bar for the shrunk matrix
+    # (the oracle solving 2^k A by its eq2_prescale reading). p = 1 matrices are not scaled.
+    cases, ps = make_batch(6, 40, 200, 1e2, 19)
+    shrunk = [np.ascontiguousarray(0.01 * c.A) for c in cases]
+    minfo = []
+    o = P.pr_default_options()
+    b = P.pr_batch_init([torch.from_numpy(A).to(DEV) for A in shrunk], ps, o,
+                        torch.cuda.current_stream(DEV).cuda_stream)
+    try:
+        its, sts = P.pr_batch_solve(b, len(cases), P.PR_EMU64, 1e-12)
+        for i, (case, p) in enumerate(zip(cases, ps)):
+            C = np.empty((case.n, case.n))
+            P.pr_batch_result(b, i, C)
+            m = P.pr_batch_matrix(b, i)
+            As, k = O.eq2_prescale(shrunk[i], p)
+            assert m["prescale_log2"] == k and (k > 0) == (p > 1)
+            assert m["norm_1"] == pytest.approx(O.norm_1(As), rel=1e-14)
+            Co, info = O.solve(As, p, tol=1e-12)
+            Z = O.closed_form_root(case.Q, 0.01 * case.lam, p)
+            bound = max(1e-12, 10 * O.forward_error(2.0 ** (k / p) * Co, Z))
+            assert O.forward_error(C, Z) <= bound, (i, case.n, p)
+            assert m["true_residual"] > 0 and sts[i] != P.PR_EDIVERGED
+    finally:
+        P.pr_batch_destroy(b)
 
 
 def test_batch_scaled_identity_host_inputs():
@@ -120,7 +158,7 @@ def test_batch_more_matrices_than_one_control_block():
     # results equal the single-matrix path bit for bit, and a repeated solve changes nothing.
     cases, ps = make_batch(1100, 1, 24, 1e2, 5)
     out, its, sts, _ = run_batch(cases, ps, repeat=True)
-    assert all(s in (P.PR_OK, P.PR_ESTAGNATED) for s in sts)
+    assert all(s in (P.PR_OK, P.PR_ESTAGNATED, P.PR_EINACCURATE) for s in sts)
     for i in list(range(0, 1100, 97)) + [1099]:
         Cs, hs = single_emu(cases[i], ps[i])
         assert np.array_equal(out[i][0], Cs), (i, cases[i].n, ps[i])
@@ -196,7 +234,8 @@ def test_batch_full_size_sampled():
 def test_batch_stats_count_every_product():
     # Per matrix of order n and k iterations: Newton-Schulz (p = 1) runs k + 1 residual products A X (full,
     # 2 n^3 flops) and k updates X T (symmetric, n^2 (n + 1)); the coupled form runs p products for M_0 and
-    # p + 1 per iteration (3 for p = 3: X N, M^2, L R), all symmetric.
+    # p + 1 per iteration (3 for p = 3: X N, M^2, L R), all symmetric, and the verification of its stop:
+    # X^p by p - 1 symmetric products, then the full product with A.
     cases, ps = make_batch(6, 64, 300, 1e3, 77)
     mats = [torch.from_numpy(c.A).to(DEV) for c in cases]
     b = P.pr_batch_init(mats, ps, P.pr_default_options(), torch.cuda.current_stream(DEV).cuda_stream)
@@ -215,8 +254,8 @@ def test_batch_stats_count_every_product():
             flops += (k + 1) * full + k * sym
         else:
             per = 3 if p == 3 else p + 1
-            products += p + k * per
-            flops += (p + k * per) * sym
+            products += p + k * per + p
+            flops += (p + k * per + p - 1) * sym + full
     assert st["products"] == products
     assert st["product_flops"] == pytest.approx(flops, rel=1e-12)
     assert st["stages_timed"] == st["stages"] and st["stage_flops_timed"] == st["product_flops"]

@@ -155,11 +155,14 @@ def test_resume_and_stats():
         P.pr_destroy(h)
     Co, info = O.solve(case.A, 2, tol=1e-12)
     assert st1 == P.PR_EMAXITER and d1 == 7
-    assert st2 == P.PR_OK and abs(d1 + d2 - info.iterations) <= 1
+    # The oracle's verified stop decides between PR_OK and PR_EINACCURATE (Eq. 3's C_0 at kappa = 1e2).
+    assert st2 == {"tol": P.PR_OK, "inaccurate": P.PR_EINACCURATE}[info.stop]
+    assert abs(d1 + d2 - info.iterations) <= 1
     assert s["iterations"] == d1 + d2 and s["iterations_by_precision"][P.PR_FP64] == d1 + d2
     assert s["norm_1"] == pytest.approx(O.norm_1(case.A), rel=1e-14)
     assert s["norm_inf"] == pytest.approx(O.norm_inf(case.A), rel=1e-14)
-    assert s["gemms"] == 2 + 3 * s["iterations"]
+    # M_0 (2 products), 3 per update, and the verification at each of the two stops (X X, then X^2 A).
+    assert s["gemms"] == 2 + 3 * s["iterations"] + 2 * 2
 
 
 def test_input_errors():
@@ -182,6 +185,74 @@ def test_input_errors():
     assert e.value.status == P.PR_ENOTSPD
 
 
+@pytest.mark.parametrize("where", [(2, 3, 100), (70, 71, 100), (100, 98, 100)])
+def test_indefinite_with_positive_diagonal(where):
+    # I + 2 (e_i e_j^T + e_j e_i^T) has the eigenvalue -1 and a unit diagonal: the Cholesky factorisation of
+    # the diagonal block of order 64 that holds rows i and j fails (in the first, the second and the last,
+    # ragged block of an order-100 matrix).
+    i, j, n = where
+    A = np.eye(n)
+    A[i, j] = A[j, i] = 2.0
+    with pytest.raises(P.PthrootError) as e:
+        P.pr_init(torch.from_numpy(A).to(DEV), n, 2, None, torch.cuda.current_stream(DEV).cuda_stream)
+    assert e.value.status == P.PR_ENOTSPD and "Cholesky" in str(e.value)
+
+
+def test_coupled_stop_is_verified():
+    # The oracle's verified stop (Eq. 3's M_0 spans kappa^(p+1); at kappa = 1e3, p = 3 the carried
+    # ||I - M||_F meets 1e-12 while the true residual stays far above it) is what the library reports:
+    # PR_EINACCURATE, with the true residual of its result in the stats. Without verification: PR_OK and
+    # no true residual.
+    case = W.spd_from_spectrum(128, 1e-3, 5)
+    Co, info = O.solve(case.A, 3, tol=1e-12)
+    assert info.stop == "inaccurate"
+    C, st, steps, hist, stats, h = gpu_solve(case.A, 3)
+    P.pr_destroy(h)
+    assert st == P.PR_EINACCURATE and hist[-1] <= 1e-12
+    want = O.residual_fro(C, case.A, 3)
+    assert stats["true_residual"] == pytest.approx(want, rel=1e-6) and want > 1e-9
+    o = P.pr_default_options()
+    o.verify = 0
+    h = P.pr_init(torch.from_numpy(case.A).to(DEV), 128, 3, o, torch.cuda.current_stream(DEV).cuda_stream)
+    try:
+        st2, _ = P.pr_iterate(h, 100, P.PR_FP64, 1e-12)
+        s2 = P.pr_stats(h)
+    finally:
+        P.pr_destroy(h)
+    assert st2 == P.PR_OK and s2["true_residual"] == -1.0
+    # The scaled identity (M_0 spans kappa) meets the tolerance for real at kappa = 10.
+    case = W.spd_from_spectrum(64, 0.1, 5)
+    C, st, steps, hist, stats, h = gpu_solve(case.A, 3, c0="scaled_identity")
+    P.pr_destroy(h)
+    assert st == P.PR_OK and 0 < stats["true_residual"] <= 1e-12
+    assert stats["true_residual"] == pytest.approx(O.residual_fro(C, case.A, 3), rel=1e-2, abs=1e-14)
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_prescale_for_eq2(p):
+    # ||A||_1 < 1 with p > 1: Eq. 3's C_0 would violate Eq. 2 (the oracle diverges on A itself); the library
+    # iterates on 2^k A (the oracle's eq2_prescale reading) and returns 2^(k/p) times that root. Compared with
+    # the oracle's solve of the scaled problem and with the closed form of the shrunk matrix.
+    case = W.spd_from_spectrum(150, 0.05, 30 + p)
+    A = 0.01 * case.A
+    As, k = O.eq2_prescale(A, p)
+    Co, info = O.solve(As, p, tol=1e-12)
+    Co = 2.0 ** (k / p) * Co
+    Z = O.closed_form_root(case.Q, 0.01 * case.lam, p)
+    bound = max(1e-12, 10 * O.forward_error(Co, Z))
+    C, st, steps, hist, stats, h = gpu_solve(A, p)
+    P.pr_destroy(h)
+    assert stats["prescale_log2"] == k > 0
+    assert stats["norm_1"] == pytest.approx(O.norm_1(As), rel=1e-14)
+    assert O.forward_error(C, Z) <= bound and O.forward_error(C, Co) <= bound
+    assert abs(steps - info.iterations) <= 1
+    # p = 1 needs no scaling (Eq. 3 is scale-invariant there).
+    C1, st1, _, _, stats1, h = gpu_solve(A, 1)
+    P.pr_destroy(h)
+    assert stats1["prescale_log2"] == 0
+    assert O.forward_error(C1, O.closed_form_root(case.Q, 0.01 * case.lam, 1)) <= 1e-12
+
+
 def test_p4_chain_uses_squares():
     # p = 4: M' = N^4 M is formed as (N^2)^2 M, three products per update (plus X N); M_0 = X^4 A keeps the
     # plain chain of four. Same iterates as the oracle's N (N (N (N M))) up to rounding.
@@ -195,7 +266,7 @@ def test_p4_chain_uses_squares():
         P.pr_result(h, C)
     finally:
         P.pr_destroy(h)
-    assert s["gemms"] == 4 + 4 * s["iterations"]
+    assert s["gemms"] == 4 + 4 * s["iterations"] + 4  # + the verification at the stop: X^4 by 3, then A
     Co, info = O.solve(case.A, 4, tol=1e-12)
     Z = O.closed_form_root(case.Q, case.lam, 4)
     bound = max(1e-12, 10 * O.forward_error(Co, Z))
@@ -217,7 +288,7 @@ def test_p3_update_takes_two_products(prec):
         P.pr_result(h, C)
     finally:
         P.pr_destroy(h)
-    assert s["gemms"] == 3 + 3 * s["iterations"]
+    assert s["gemms"] == 3 + 3 * s["iterations"] + 3  # + the verification at the stop: X^3 by 2, then A
     Co, info = O.solve(case.A, 3, tol=1e-12)
     Z = O.closed_form_root(case.Q, case.lam, 3)
     bound = max(1e-12, 10 * O.forward_error(Co, Z))

@@ -212,3 +212,28 @@ def test_trained_network_cuts_iterations():
             gained += t.iterations - its
             assert its < t.iterations
     assert gained > 0
+
+
+def test_gate_without_fallback_reports_egate():
+    # gate_fallback = 0: a guess that fails the gate is an error (PR_EGATE) instead of a silent fallback.
+    # pr_init creates no handle; pr_set_initial_guess leaves Eq. 3's C_0 in the handle, which still solves.
+    c = W.spd_from_spectrum(128, 1e-2, 40)
+    bad = [40.0, 0.0, 0.0, 0.0]  # positive, but ||I - C_0^2 A||_2 far above 1
+    with pytest.raises(P.PthrootError) as e:
+        handle(c.A, 2, c0=P.PR_C0_POLY, c0_coef=bad, gate_fallback=0)
+    assert e.value.status == P.PR_EGATE
+    h = handle(c.A, 2, gate_fallback=0)
+    try:
+        with pytest.raises(P.PthrootError) as e:
+            P.pr_set_initial_guess(h, P.PR_C0_POLY, bad)
+        assert e.value.status == P.PR_EGATE and "gate" in str(e.value)
+        st = P.pr_stats(h)
+        assert st["c0"] == P.PR_C0_EQ3 and st["c0_gate"] > 0.9
+        P.pr_iterate(h, 100, P.PR_EMU64, 1e-12)
+        C = torch.empty((128, 128), dtype=torch.float64, device=DEV)
+        P.pr_result(h, C)
+    finally:
+        P.pr_destroy(h)
+    Z = O.closed_form_root(c.Q, c.lam, 2)
+    Co, _ = O.solve(c.A, 2, tol=1e-12)
+    assert O.forward_error(C.cpu().numpy(), Z) <= max(1e-12, 10 * O.forward_error(Co, Z))
