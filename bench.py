@@ -4,18 +4,24 @@ Workload: the n = 4096, kappa = 1e3 SPD matrix (Q diag(lam) Q^T, lam log-uniform
 roots p = 1, 2, 3, 4, initial guess of Eq. 3, tolerance 1e-12 on the iteration's residual.
 
 One step = the whole hot path for every p in --p: load A (checks, ||A||_1, ||A||_inf, C_0), iterate Eq. 1
-to the tolerance or the precision floor, the true residual ||I - C^p A||_F and the result copy. The value is
-milliseconds per step (lower is better) for --mode:
+to the tolerance or the precision floor (the coupled form's stop verified against the true residual), the
+true residual ||I - C^p A||_F and the result copy. The value is milliseconds per step (lower is better) for
+--mode:
   fast   FP64-accurate products from exact FP16 digit slices (PR_EMU64) for every p; for p = 1, whose
          Newton-Schulz form corrects earlier errors, BF16 iterations first, then PR_EMU64 ones (default);
   emu64  PR_EMU64 for every iteration;
   fp64   native FP64 products (the plain FP64 GPU iteration).
-Unless --no-compare, the plain FP64 GPU iteration is also run once per p in the same process and its time
-and accuracy are reported beside the value. Inputs are resident in HBM before the timed region; the
-working set (about 1.5 GiB per handle) exceeds the 129 MB L2.
+Beside the value the line reports the same solves from the scaled identity C_0 = ||A||_1^{-1/p} I (Sec. 2's
+"other choices" of C_0; FP64-accurate for every p, where Eq. 3's C_0 loses u kappa^(p+1)), timed the same
+way, and, unless --no-compare, the plain FP64 GPU iteration of both (--compare-warmup + --compare-steps
+steps each). Unless --no-extra it also runs the batched workload (512 matrices) and the learned-guess
+workload with --sub-warmup / --sub-steps steps and reports them under "batched" and "learned". Inputs are
+resident in HBM before the timed regions; the working sets exceed the 129 MB L2.
 
-`--impl reference` times the CPU oracle (numpy FP64) on the host cores instead, on a bounded sample scaled
-to the same unit.
+`--impl reference` times the CPU oracle (numpy FP64) on the host cores instead: each step times one oracle
+update of one root (the roots in turn); the value is the oracle's time to the same solves, the measured
+setup plus the measured update time times the iteration count, and one full p = 1 oracle solve checks that
+model. ms_per_step is the measured time of a step.
 """
 from __future__ import annotations
 
@@ -38,11 +44,13 @@ from paper_1703_02283_gb300 import workloads as W  # noqa: E402
 METRIC = "time to FP64-accurate A^(-1/p) vs plain FP64 GPU; GEMM TFLOP/s, % of peak"
 NOMINAL_BF16_TFLOPS = 2250.0
 NOMINAL_FP64_TFLOPS = 1.25
-PREC_NAMES = {0: "fp64", 1: "emu64", 3: "bf16"}
+PREC_NAMES = {0: "fp64", 1: "emu64", 2: "fp32x", 3: "bf16", 4: "fp8"}
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one symmetric product, by n. Taken before the kernel
 # gained its split-tile variant; the unsplit code path that n = 4096 runs is unchanged (same registers and
 # spills), but until it is captured again the roofline reports it as traffic_last_capture, not traffic.
 EMU_TRAFFIC_BYTES = {4096: 2.371166e9 + 0.200156e9}
+# The same figure from a capture of the kernel as it is now (filled in once one exists).
+EMU_TRAFFIC_CURRENT: dict = {}
 
 
 # ----------------------------------------------------------------------------- replicas (N > 1 under torchrun)
@@ -92,7 +100,14 @@ def parse():
     ap.add_argument("--learned-n", type=int, default=2048, help="learned: matrix order")
     ap.add_argument("--train-seqs", type=int, default=40, help="learned: training sequences (ids 0..)")
     ap.add_argument("--test-seqs", type=int, default=10, help="learned: held-out sequences (ids 40..)")
-    ap.add_argument("--every", type=int, default=50, help="learned: sample every this many of 200 steps")
+    ap.add_argument("--every", type=int, default=10, help="learned: sample every this many of 200 steps")
+    ap.add_argument("--compare-steps", type=int, default=2, help="timed steps of each plain FP64 comparison")
+    ap.add_argument("--compare-warmup", type=int, default=1, help="warm-up steps of each plain FP64 comparison")
+    ap.add_argument("--no-scaled-identity", action="store_true", help="skip the scaled-identity arm")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched and learned summaries")
+    ap.add_argument("--sub-steps", type=int, default=5, help="timed steps of the batched / learned summaries")
+    ap.add_argument("--sub-warmup", type=int, default=3, help="warm-up steps of the batched / learned summaries")
+    ap.add_argument("--e2e-steps", type=int, default=5, help="steps of the end-to-end measurement")
     return ap.parse_args()
 
 
@@ -165,18 +180,49 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- CPU oracle timing
 
+class OracleModel:
+    """Time of the oracle's solve of (A, p) from measurements: its setup (norms, C_0 and, for the coupled
+    form, M_0 = C_0^p A) once, and the time of single updates, measured on the oracle's own iterates."""
+
+    def __init__(self, A: np.ndarray, p: int, c0: str = "eq3"):
+        from oracle import pthroot_oracle as O
+        self.O, self.A, self.p, self.c0 = O, A, p, c0
+        self.form = O.default_form(p)
+        t0 = time.perf_counter()
+        C = O.initial_guess_eq3(A) if c0 == "eq3" else O.initial_guess_scaled_identity(A, p)
+        if self.form == "coupled":
+            self.X, self.M = O.coupled_start(C, A, p)
+            np.linalg.norm(np.eye(A.shape[0]) - self.M)
+        else:
+            self.C = C
+        self.setup_s = time.perf_counter() - t0
+        self.updates = []
+
+    def time_update(self) -> float:
+        """One update of the oracle's form, with the residual it tests (seconds)."""
+        O, A, n = self.O, self.A, self.A.shape[0]
+        t0 = time.perf_counter()
+        if self.form == "coupled":
+            self.X, self.M = O.step_coupled(self.X, self.M, self.p)
+            np.linalg.norm(np.eye(n) - self.M)
+        else:
+            T = A @ self.C
+            np.linalg.norm(np.eye(n) - T)
+            self.C = O.symmetrize(2.0 * self.C - self.C @ T)
+        dt = time.perf_counter() - t0
+        self.updates.append(dt)
+        return dt
+
+    def solve_ms(self, iterations: int) -> float:
+        return (self.setup_s + float(np.median(self.updates)) * iterations) * 1e3
+
+
 def oracle_sample(A: np.ndarray, p: int, iterations: int) -> tuple[float, str]:
-    """Times the oracle's setup plus one and two updates and extrapolates to `iterations` updates."""
-    from oracle import pthroot_oracle as O
-    t0 = time.perf_counter()
-    O.solve(A, p, tol=0.0, max_iter=1, stag_below=0.0)
-    t1 = time.perf_counter()
-    O.solve(A, p, tol=0.0, max_iter=2, stag_below=0.0)
-    t2 = time.perf_counter()
-    per_update = max((t2 - t1) - (t1 - t0), 1e-9)
-    setup = max((t1 - t0) - per_update, 0.0)
-    return (setup + per_update * iterations) * 1e3, (f"n={A.shape[0]} p={p}: oracle setup + 1 and + 2 updates, "
-                                                     f"extrapolated to {iterations} updates")
+    """The oracle's time to a solve of `iterations` updates: measured setup + iterations x a measured update."""
+    m = OracleModel(A, p)
+    m.time_update()
+    return m.solve_ms(iterations), (f"n={A.shape[0]} p={p}: oracle setup + one update measured, times "
+                                    f"{iterations} updates")
 
 
 def predicted_iterations(case, p: int, tol: float) -> int:
@@ -211,24 +257,47 @@ def config_dict(args, ps):
 
 
 def run_reference(args, ps):
+    """The oracle timed on the host cores. Each step times one update of one root (the roots in turn, on the
+    oracle's own iterates); the value is the modelled time of the oracle's solves of every root (measured
+    setup + median measured update x the iterations the exact-arithmetic recurrence predicts). Before the
+    steps, one full p = 1 oracle solve is timed and compared with the model (model_check)."""
     if int(os.environ.get("RANK", "0")) != 0:
         return
+    from oracle import pthroot_oracle as O
     case = W.spd_from_spectrum(args.n, args.lam_min, args.seed)
-    totals, samples = [], []
-    for _ in range(args.warmup + args.steps):
-        ms = 0.0
-        for p in ps:
-            est, what = oracle_sample(case.A, p, predicted_iterations(case, p, args.tol))
-            ms += est
-            samples.append(what)
-        totals.append(ms)
-    value = float(np.mean(totals[args.warmup:]))
+    its = {p: predicted_iterations(case, p, args.tol) for p in ps}
+    check = None
+    if 1 in ps:
+        _, info = O.solve(case.A, 1, tol=args.tol)
+        m1 = OracleModel(case.A, 1)
+        for _ in range(2):
+            m1.time_update()
+        check = {"p": 1, "full_solve_ms": info.seconds * 1e3, "iterations": info.iterations,
+                 "model_ms": m1.solve_ms(info.iterations)}
+        check["model_over_full"] = check["model_ms"] / check["full_solve_ms"]
+    models = {p: OracleModel(case.A, p) for p in ps}
+    step_ms = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        models[ps[k % len(ps)]].time_update()
+        step_ms.append((time.perf_counter() - t0) * 1e3)
+    for p in ps:  # a root whose update fell only into the warm-up steps still gets a measured update
+        if not models[p].updates:
+            models[p].time_update()
+    value = sum(models[p].solve_ms(its[p]) for p in ps)
+    ms = float(np.mean(step_ms[args.warmup:])) if args.steps else 0.0
+    sample = (f"n={args.n}, p={','.join(map(str, ps))}: oracle setup of every root and single updates measured "
+              f"(one per step, roots in turn), value = setup + median update x predicted iterations "
+              f"({', '.join(f'p={p}: {its[p]}' for p in ps)})")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(args, ps),
+            "value_model": "value = modelled oracle time to the solves of one step; ms_per_step = measured time of "
+                           "one benchmark step (one oracle update)",
+            "model_check": check,
             "cpu_baseline": {"value": value, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": "; ".join(samples[:len(ps)]) + " (every step)"},
+                             "sample": sample},
             "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -282,13 +351,18 @@ def run_batched(args):
             return
         cases, ps = batched_cases(args.count)
         its = [predicted_iterations(c, p, args.tol) for c, p in zip(cases, ps)]
-        vals = []
+        vals, step_ms = [], []
         for _ in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
             v, what = oracle_batched_sample(cases, ps, its)
+            step_ms.append((time.perf_counter() - t0) * 1e3)
             vals.append(v)
         value = float(np.mean(vals[args.warmup:]))
+        ms = float(np.mean(step_ms[args.warmup:])) if args.steps else 0.0
         print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
-                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": value,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                          "value_model": "value = modelled oracle time to every solve of the batch; ms_per_step = "
+                                         "measured time of one benchmark step (the sampled oracle updates)",
                           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                           "data": "synthetic", "config": batched_config(args),
                           "cpu_baseline": {"value": value, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
@@ -300,6 +374,19 @@ def run_batched(args):
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
+    line = measure_batched(args, world, rank, local, dist, args.steps, args.warmup, not args.no_e2e,
+                           rank == 0 and world == 1 and not args.no_cpu_baseline)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def measure_batched(args, world, rank, local, dist, steps, warmup, e2e_on, cpu_on):
+    """The batched workload's JSON fields on this rank (timed over `steps` steps after `warmup`)."""
+    import torch
+
+    from paper_1703_02283_gb300 import pthroot as P
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
     cases, ps = batched_cases(args.count, rank)
@@ -329,16 +416,16 @@ def run_batched(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         one(mats)
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         ev0.record(stream)
-        runs = [one(mats) for _ in range(args.steps)]
+        runs = [one(mats) for _ in range(steps)]
         ev1.record(stream)
         barrier()
-    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, dev)
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / steps, dist, dev)
     its, sts, outs, bst = runs[-1]
     launches = sum(r[3]["launches"] for r in runs)
     # Roofline of the product kernel over the timed steps (CUDA events around every product launch).
@@ -356,14 +443,15 @@ def run_batched(args):
                 "fp64_equivalent_tflops": stage_fl / (stage_ms * 1e-3) / 1e12,
                 "peak_source": f"{peak_src} bf16 sustained x nominal fp16/bf16 ratio 1 (kernel timed inside a long step)",
                 "launches_timed": stages, "avg_launch_ms": stage_ms / stages if stages else None,
-                "product_kernel_share": stage_ms / (ms * args.steps)}
+                "product_kernel_share": stage_ms / (ms * steps)}
     roofline["frac"] = roofline["achieved"] / roofline["peak"]
     errs = []
     for i, c in enumerate(cases):
         Z = (c.Q * c.lam ** (-1.0 / ps[i])) @ c.Q.T
         errs.append(float(np.linalg.norm(outs[i].cpu().numpy() - Z) / np.linalg.norm(Z)))
+    tres = [P.pr_batch_matrix(b, i)["true_residual"] for i in range(len(cases))]
     e2e = None
-    if not args.no_e2e:
+    if e2e_on:
         host = [c.A.copy() for c in cases]
         host = [torch.from_numpy(h).pin_memory() for h in host]
         barrier()
@@ -374,24 +462,22 @@ def run_batched(args):
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
     P.pr_batch_destroy(b)
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if cpu_on:
         v, what = oracle_batched_sample(cases, ps, its)
         cpu = {"value": v, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle", "sample": what}
     stat = {}
     for s_ in sts:
         stat[P.STATUS_NAMES[s_]] = stat.get(P.STATUS_NAMES[s_], 0) + 1
-    line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+    line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "emu64(fp16 slices)", "data": "synthetic", "config": batched_config(args),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(),
             "batch": {"statuses": stat, "iterations_max": max(its), "iterations_mean": float(np.mean(its)),
                       "rel_error_median": float(np.median(errs)), "rel_error_max": float(np.max(errs)),
+                      "true_residual_median": float(np.median(tres)), "true_residual_max": float(np.max(tres)),
                       "matrices_per_second": world * len(cases) / (ms * 1e-3)}}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    return line
 
 
 # ----------------------------------------------------------------------------- learned initial guess
@@ -408,9 +494,10 @@ def learned_config(args):
 
 
 def learned_sets(args):
+    """(training matrices as a generator, one sequence at a time; held-out test matrices as a list)."""
     from paper_1703_02283_gb300 import learned as L
     n = args.learned_n
-    train = [S for q in range(args.train_seqs) for S in L.overlap_sequence(q, 200, n, every=args.every)]
+    train = (S for q in range(args.train_seqs) for S in L.overlap_sequence(q, 200, n, every=args.every))
     test = [S for q in range(40, 40 + args.test_seqs) for S in L.overlap_sequence(q, 200, n, every=args.every)]
     return train, test
 
@@ -423,30 +510,28 @@ def run_learned(args):
             return
         from oracle import pthroot_oracle as O
         _, test = learned_sets(args)
-        vals, what = [], ""
+        # The plain method on every test matrix: the iterations the scalar recurrence of Eq. 1 predicts for
+        # each matrix's spectrum, at the oracle's measured setup and update times on the first one.
+        predicted = []
+        for S in test:
+            lam = np.linalg.eigvalsh(S)
+            r = O.scalar_residuals(lam, lam / (O.norm_1(S) * O.norm_inf(S)), p, 200)
+            hit = np.nonzero(r <= max(args.tol, 1e-13))[0]
+            predicted.append(int(hit[0]) if len(hit) else 200)
+        model = OracleModel(test[0], p)
+        step_ms = []
         for _ in range(args.warmup + args.steps):
-            # The plain method on every test matrix: oracle setup + 1, 2 updates on one, extrapolated to the
-            # iterations the scalar recurrence of Eq. 1 predicts for each matrix's spectrum.
-            S0 = test[0]
             t0 = time.perf_counter()
-            O.solve(S0, p, tol=0.0, max_iter=1, stag_below=0.0)
-            t1 = time.perf_counter()
-            O.solve(S0, p, tol=0.0, max_iter=2, stag_below=0.0)
-            t2 = time.perf_counter()
-            per = max((t2 - t1) - (t1 - t0), 1e-9)
-            setup = max((t1 - t0) - per, 0.0)
-            tot = 0.0
-            for S in test:
-                lam = np.linalg.eigvalsh(S)
-                r = O.scalar_residuals(lam, lam / (O.norm_1(S) * O.norm_inf(S)), p, 200)
-                hit = np.nonzero(r <= max(args.tol, 1e-13))[0]
-                tot += setup + per * (int(hit[0]) if len(hit) else 200)
-            vals.append(tot * 1e3)
-            what = (f"oracle (plain method, Eq.3 C_0) setup + 1 and + 2 updates on one n={args.learned_n} matrix, "
-                    f"extrapolated to the predicted iterations of each of the {len(test)} test matrices")
-        value = float(np.mean(vals[args.warmup:]))
+            model.time_update()
+            step_ms.append((time.perf_counter() - t0) * 1e3)
+        value = sum(model.solve_ms(k) for k in predicted)
+        ms = float(np.mean(step_ms[args.warmup:])) if args.steps else 0.0
+        what = (f"oracle (plain method, Eq.3 C_0): setup and one update per step measured on one n={args.learned_n} "
+                f"matrix, times the predicted iterations of each of the {len(test)} test matrices")
         print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
-                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": value,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                          "value_model": "value = modelled oracle time to every test solve; ms_per_step = measured "
+                                         "time of one benchmark step (one oracle update)",
                           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                           "data": "synthetic", "config": learned_config(args),
                           "cpu_baseline": {"value": value, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
@@ -455,14 +540,26 @@ def run_learned(args):
         return
 
     import torch
-
-    from paper_1703_02283_gb300 import learned as L
-    from paper_1703_02283_gb300 import pthroot as P
     import torch.distributed as dist
     world, rank, local = replica_env()
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
+    line = measure_learned(args, world, rank, local, dist, args.steps, args.warmup, not args.no_e2e,
+                           rank == 0 and world == 1 and not args.no_cpu_baseline)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def measure_learned(args, world, rank, local, dist, steps, warmup, e2e_on, cpu_on):
+    """The learned-guess workload's JSON fields on this rank (timed over `steps` steps after `warmup`)."""
+    import torch
+
+    from paper_1703_02283_gb300 import learned as L
+    from paper_1703_02283_gb300 import pthroot as P
+    p = 2
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
     sptr = stream.cuda_stream
@@ -501,20 +598,20 @@ def run_learned(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         learned_step(Ad, Cd)
     barrier()
     s0 = P.pr_stats(h)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         ev0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             info = learned_step(Ad, Cd)
         ev1.record(stream)
         barrier()
-    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, dev)
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / steps, dist, dev)
     s1 = P.pr_stats(h)
-    launches = (s1["launches"] - s0["launches"]) + args.steps * len(test)  # + one MLP forward per matrix
+    launches = (s1["launches"] - s0["launches"]) + steps * len(test)  # + one MLP forward per matrix
     dms = s1["gemm_ms_by_precision"][P.PR_EMU64] - s0["gemm_ms_by_precision"][P.PR_EMU64]
     dfl = s1["gemm_flops_by_precision"][P.PR_EMU64] - s0["gemm_flops_by_precision"][P.PR_EMU64]
     dn = s1["gemms_timed_by_precision"][P.PR_EMU64] - s0["gemms_timed_by_precision"][P.PR_EMU64]
@@ -528,7 +625,7 @@ def run_learned(args):
                 "fp64_equivalent_tflops": dfl / (dms * 1e-3) / 1e12,
                 "peak_source": f"{peak_src} bf16 sustained x nominal fp16/bf16 ratio 1 (kernel timed inside a long step)",
                 "launches_timed": dn, "avg_launch_ms": dms / dn if dn else None,
-                "product_kernel_share": dms / (ms * args.steps)}
+                "product_kernel_share": dms / (ms * steps)}
     roofline["frac"] = roofline["achieved"] / roofline["peak"]
     learned_out = [C.cpu().numpy() for C in Cd]
 
@@ -551,7 +648,7 @@ def run_learned(args):
         errs_p.append(float(np.linalg.norm(plain_out[i] - Z) / np.linalg.norm(Z)))
 
     e2e = None
-    if not args.no_e2e:
+    if e2e_on:
         Ah = [torch.from_numpy(S).pin_memory() for S in test]
         Ch = [torch.empty((n, n), dtype=torch.float64).pin_memory() for _ in test]
         learned_step(Ah, Ch)
@@ -563,7 +660,7 @@ def run_learned(args):
         e2e = {"value": max_over_ranks((time.perf_counter() - t0) * 1e3, dist, dev), "unit": "ms",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if cpu_on:
         its_plain = [x[1] for x in pinfo]
         est, what = oracle_sample(test[0], p, int(np.mean(its_plain)))
         cpu = {"value": est * len(test), "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
@@ -573,8 +670,8 @@ def run_learned(args):
     its_l = [x[1] for x in info]
     its_p = [x[1] for x in pinfo]
     used = sum(1 for x in info if x[2] == P.PR_C0_POLY)
-    line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+    line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "emu64(fp16 slices)", "data": "synthetic", "config": learned_config(args),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(),
@@ -587,10 +684,7 @@ def run_learned(args):
             "plain_eq3": {"ms_per_step": pms, "speedup_of_value": pms / ms, "iterations_mean": float(np.mean(its_p)),
                           "iterations": its_p, "statuses": [P.STATUS_NAMES[x[0]] for x in pinfo],
                           "rel_error_vs_eigh": errs_p}}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    return line
 
 
 def main():
@@ -620,9 +714,16 @@ def main():
     case = W.spd_from_spectrum(args.n, args.lam_min, replica_seed(args.seed, rank))
     A = torch.from_numpy(case.A).to(dev)
     C = torch.empty_like(A)
-    opts = P.pr_default_options()
-    opts.emu_slices = args.emu_slices
-    handles = {p: P.pr_init(A, args.n, p, opts, sptr) for p in ps}
+
+    def make_handles(c0):
+        opts = P.pr_default_options()
+        opts.emu_slices = args.emu_slices
+        opts.c0 = c0
+        return {p: P.pr_init(A, args.n, p, opts, sptr) for p in ps}
+
+    arms = {"eq3": make_handles(P.PR_C0_EQ3)}
+    if not args.no_scaled_identity:
+        arms["scaled_identity"] = make_handles(P.PR_C0_SCALED_I)
 
     def plan(p, mode):
         """(bulk precision, bulk steps, final precision) of one solve."""
@@ -632,7 +733,7 @@ def main():
             return P.PR_EMU64, 0, P.PR_EMU64
         return P.PR_BF16, 100, P.PR_EMU64
 
-    def solve_all(mode, Ain, Cout):
+    def solve_all(handles, mode, Ain, Cout):
         info = {}
         for p, h in handles.items():
             bulk, nb, fin = plan(p, mode)
@@ -642,8 +743,9 @@ def main():
             P.pr_result(h, Cout)
             s = P.pr_stats(h)
             info[p] = {"status": P.STATUS_NAMES[st], "iterations": steps, "true_residual": res,
-                       "iterations_by_precision": {PREC_NAMES[k]: s["iterations_by_precision"][k] for k in (0, 1, 3)
-                                                   if s["iterations_by_precision"][k]},
+                       "tol_met": bool(res <= args.tol),
+                       "iterations_by_precision": {PREC_NAMES[k]: s["iterations_by_precision"][k]
+                                                   for k in range(P.PR_NPREC) if s["iterations_by_precision"][k]},
                        "switch_iteration": s["switch_iteration"]}
         return info
 
@@ -656,28 +758,39 @@ def main():
         Z = (case.Q * case.lam ** (-1.0 / p)) @ case.Q.T
         return float(np.linalg.norm(Ct.cpu().numpy() - Z) / np.linalg.norm(Z))
 
-    for _ in range(args.warmup):
-        solve_all(args.mode, A, C)
-    barrier()
-    s0 = {p: P.pr_stats(h) for p, h in handles.items()}
-    for h in handles.values():
-        P.pr_set_timing(h, True)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
+    def timed(handles, mode, steps, warmup, sample_clocks=False):
+        """(ms per step, the last step's solve records with forward errors, stats before and after)."""
+        for _ in range(warmup):
+            solve_all(handles, mode, A, C)
         barrier()
-        ev0.record(stream)
-        infos = [solve_all(args.mode, A, C) for _ in range(args.steps)]
-        ev1.record(stream)
-        barrier()
-    for h in handles.values():
-        P.pr_set_timing(h, False)
-    ms = ev0.elapsed_time(ev1) / args.steps
-    s1 = {p: P.pr_stats(h) for p, h in handles.items()}
-    ms = max_over_ranks(ms, dist, dev)
-    last = infos[-1]
-    for p, h in handles.items():
-        P.pr_result(h, C)
-        last[p]["rel_error_vs_closed_form"] = rel_err(C, p)
+        s0 = {p: P.pr_stats(h) for p, h in handles.items()}
+        for h in handles.values():
+            P.pr_set_timing(h, True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clk = ClockSampler(local) if sample_clocks else None
+        if clk:
+            clk.__enter__()
+        try:
+            barrier()
+            ev0.record(stream)
+            infos = [solve_all(handles, mode, A, C) for _ in range(steps)]
+            ev1.record(stream)
+            barrier()
+        finally:
+            if clk:
+                clk.__exit__(None, None, None)
+        for h in handles.values():
+            P.pr_set_timing(h, False)
+        ms = max_over_ranks(ev0.elapsed_time(ev1) / steps, dist, dev)
+        s1 = {p: P.pr_stats(h) for p, h in handles.items()}
+        last = infos[-1]
+        for p, h in handles.items():
+            P.pr_result(h, C)
+            last[p]["rel_error_vs_closed_form"] = rel_err(C, p)
+        return ms, last, s0, s1, clk
+
+    # ---- the headline: Eq. 3's C_0 (the plain method's start)
+    ms, last, s0, s1, clk = timed(arms["eq3"], args.mode, args.steps, args.warmup, sample_clocks=True)
     launches = sum(s1[p]["launches"] - s0[p]["launches"] for p in ps)
 
     # Roofline of the dominant product kernel over the timed region (CUDA events around every launch).
@@ -685,7 +798,7 @@ def main():
         return sum(s1[p][key][k] - s0[p][key][k] for p in ps)
 
     by_prec = {k: (delta("gemm_ms_by_precision", k), delta("gemm_flops_by_precision", k),
-                   delta("gemms_timed_by_precision", k)) for k in (0, 1, 3)}
+                   delta("gemms_timed_by_precision", k)) for k in range(P.PR_NPREC)}
     dom = max(by_prec, key=lambda k: by_prec[k][0])
     dms, dfl, dn = by_prec[dom]
     peaks, peak_src = load_peaks()
@@ -693,20 +806,20 @@ def main():
     if dom == P.PR_EMU64:
         pairs = S * (S + 1) // 2
         exec_fl = dfl * pairs
-        # DRAM bytes (read + write) per symmetric n = 4096 product from one ncu capture; other sizes were not
-        # captured.
         traffic_seen = EMU_TRAFFIC_BYTES.get(args.n) if S == 8 else None
         roofline = {"bound": "tensor", "kernel": "k_gemm_emu (tcgen05 FP16 digit-slice products)",
                     "achieved": exec_fl / (dms * 1e-3) / 1e12, "peak": peaks["bf16_tflops_sustained"],
-                    "unit": "TFLOP/s", "traffic": None, "traffic_last_capture": traffic_seen,
+                    "unit": "TFLOP/s", "traffic": EMU_TRAFFIC_CURRENT.get(args.n) if S == 8 else None,
+                    "traffic_last_capture": traffic_seen,
                     "note": f"algorithmic = the {pairs} FP16 digit-pair products per emulated FP64 product "
                             f"(S={S}), upper-triangle tiles; fp64_equivalent_tflops = FP64 flops / time",
                     "fp64_equivalent_tflops": dfl / (dms * 1e-3) / 1e12,
                     "peak_source": f"{peak_src} bf16 sustained x nominal fp16/bf16 ratio 1 (kernel timed inside a long step)"}
-    elif dom == P.PR_BF16:
-        roofline = {"bound": "tensor", "kernel": "k_gemm_bf16_tc", "achieved": dfl / (dms * 1e-3) / 1e12,
-                    "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s", "traffic": None,
-                    "peak_source": f"{peak_src} bf16 sustained"}
+    elif dom in (P.PR_BF16, P.PR_FP8):
+        nominal = 2.0 if dom == P.PR_FP8 else 1.0
+        roofline = {"bound": "tensor", "kernel": "k_gemm_lowp_tc", "achieved": dfl / (dms * 1e-3) / 1e12,
+                    "peak": peaks["bf16_tflops_sustained"] * nominal, "unit": "TFLOP/s", "traffic": None,
+                    "peak_source": f"{peak_src} bf16 sustained x nominal ratio {nominal:g}"}
     else:
         peak = peaks["bf16_tflops_sustained"] * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS
         roofline = {"bound": "tensor", "kernel": "k_gemm_f64 (DMMA)", "achieved": dfl / (dms * 1e-3) / 1e12,
@@ -723,30 +836,48 @@ def main():
     if not args.no_e2e:
         Ah = torch.from_numpy(case.A).pin_memory()
         Ch = torch.empty_like(Ah).pin_memory()
-        solve_all(args.mode, Ah, Ch)
+        solve_all(arms["eq3"], args.mode, Ah, Ch)
         barrier()
+        k = max(1, min(args.steps, args.e2e_steps))
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            solve_all(args.mode, Ah, Ch)
+        for _ in range(k):
+            solve_all(arms["eq3"], args.mode, Ah, Ch)
         barrier()
         nbytes = args.n * args.n * 8 * len(ps)
-        e2e = {"value": max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, dist, dev), "unit": "ms",
-               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+        e2e = {"value": max_over_ranks((time.perf_counter() - t0) * 1e3 / k, dist, dev), "unit": "ms",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": k}
 
-    # The plain FP64 GPU iteration on the same matrices, once per p (the speed comparison).
-    plain = None
-    if not args.no_compare and args.mode != "fp64":
+    def plain_fp64(handles, ref_ms):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(args.compare_warmup):
+            solve_all(handles, "fp64", A, C)
         barrier()
         e0.record(stream)
-        pinfo = solve_all("fp64", A, C)
+        pinfo = None
+        for _ in range(args.compare_steps):
+            pinfo = solve_all(handles, "fp64", A, C)
         e1.record(stream)
         barrier()
         for p, h in handles.items():
             P.pr_result(h, C)
             pinfo[p]["rel_error_vs_closed_form"] = rel_err(C, p)
-        pms = e0.elapsed_time(e1)
-        plain = {"ms_per_step": pms, "speedup_of_value": pms / ms, "solves": {str(p): v for p, v in pinfo.items()}}
+        pms = e0.elapsed_time(e1) / args.compare_steps
+        return {"ms_per_step": pms, "speedup_of_value": pms / ref_ms, "steps": args.compare_steps,
+                "warmup": args.compare_warmup, "solves": {str(p): v for p, v in pinfo.items()}}
+
+    # ---- the scaled identity C_0 = ||A||_1^{-1/p} I: same solves, FP64-accurate for every p
+    si = None
+    if "scaled_identity" in arms:
+        si_ms, si_last, _, _, _ = timed(arms["scaled_identity"], args.mode, args.steps, args.warmup)
+        si = {"ms_per_step": si_ms, "steps": args.steps, "warmup": args.warmup,
+              "solves": {str(p): v for p, v in si_last.items()}}
+
+    # ---- the plain FP64 GPU iteration of both starts (the speed comparison)
+    plain, plain_si = None, None
+    if not args.no_compare and args.mode != "fp64":
+        plain = plain_fp64(arms["eq3"], ms)
+        if si:
+            plain_si = plain_fp64(arms["scaled_identity"], si["ms_per_step"])
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -757,8 +888,25 @@ def main():
             what.append(w)
         cpu = {"value": tot, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle", "sample": "; ".join(what)}
 
-    for h in handles.values():
-        P.pr_destroy(h)
+    for handles in arms.values():
+        for h in handles.values():
+            P.pr_destroy(h)
+    del A, C
+    torch.cuda.empty_cache()
+
+    # ---- the other workloads, summarised (their own JSON lines: --workload batched / learned)
+    extra = {}
+    if not args.no_extra:
+        for name, fn in (("batched", measure_batched), ("learned", measure_learned)):
+            try:
+                sub = fn(args, world, rank, local, dist, args.sub_steps, args.sub_warmup, False, False)
+                keep = ("value", "unit", "steps", "warmup", "config", "roofline", "batch", "learned", "plain_eq3",
+                        "gpu_launches", "clocks")
+                extra[name] = {k: sub[k] for k in keep if k in sub}
+            except Exception as exc:  # a failing summary must not hide the headline
+                extra[name] = {"error": f"{type(exc).__name__}: {exc}"}
+            torch.cuda.empty_cache()
+
     if rank == 0:
         line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
@@ -766,7 +914,10 @@ def main():
                                                "fp64": "f64"}[args.mode],
                 "data": "synthetic", "config": config_dict(args, ps), "roofline": roofline,
                 "kernel_time_share": kernel_share, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk.summary(), "solves": {str(p): v for p, v in last.items()}, "plain_fp64_gpu": plain}
+                "clocks": clk.summary(), "solves": {str(p): v for p, v in last.items()}, "plain_fp64_gpu": plain,
+                "scaled_identity": si, "plain_fp64_gpu_scaled_identity": plain_si,
+                "ms_per_step_scaled_identity": si["ms_per_step"] if si else None}
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -69,8 +69,18 @@ typedef enum {
                     row exponent; the digit pairs with s + t <= S + 1 are exact FP16 tensor-core
                     products, summed per level s + t exactly in FP32 (drained every 128 terms) and then
                     in 128-bit integers, rounded once to FP64                                          */
-  PR_BF16 = 3    /* BF16 operands, FP32 accumulation in TMEM (tcgen05 kind::f16); FP64 master copies     */
+  PR_FP32X = 2,  /* split-FP32 products: the first 3 of PR_EMU64's base-256 digit planes (24 bits per row,
+                    the significand width of FP32), the 6 exact digit-pair products with s + t <= 4 summed
+                    exactly, rounded once to FP64; about FP32 accuracy (2^-25 per term relative to the row and
+                    column scales) at 1/6 of PR_EMU64's tensor work                                         */
+  PR_BF16 = 3,   /* BF16 operands, FP32 accumulation in TMEM (tcgen05 kind::f16); FP64 master copies     */
+  PR_FP8 = 4     /* E4M3 operands with a power-of-two FP32 scale per row (per column of the B operand,
+                    the same for symmetric iterates; the largest |x| of a row maps into [128, 256)),
+                    round to nearest even from FP64, FP32 accumulation in TMEM (tcgen05 kind::f8f6f4);
+                    FP64 master copies, re-quantised before each FP8 product                              */
 } pr_precision;
+
+#define PR_NPREC 5 /* number of pr_precision values: arrays indexed by precision have this length */
 
 /* Evaluation order of Eq. 1 (identical iterates in exact arithmetic). */
 typedef enum {
@@ -105,8 +115,9 @@ typedef struct {
   int reanchor;        /* coupled form: on a switch to higher precision recompute M = X^p A, default 1  */
   int emu_slices;      /* PR_EMU64 digit planes per operand, 1..8 (0 = the default, 8): S planes keep
                           8S bits per row and cost S (S + 1) / 2 FP16 products per FP64 product         */
-  double stag_below_lowp; /* stag_below for low-precision (PR_BF16) residuals, whose floor is higher,
-                             default 0.5 (below 0.5 every eigencomponent is in the quadratic phase)      */
+  double stag_below_lowp; /* stag_below for the rungs below FP64 accuracy (PR_FP8, PR_BF16, PR_FP32X),
+                             whose floor is higher, default 0.5 (below 0.5 every eigencomponent is in the
+                             quadratic phase)                                                          */
   double c0_coef[4];   /* PR_C0_POLY coefficients c_0 .. c_3, default (1, 0, 0, 0) (the scaled identity)  */
   double gate_max;     /* PR_C0_POLY gate on ||I - C_0^p A||_2, default 0.9                                */
   int gate_iters;      /* power iterations of the gate, default 30                                         */
@@ -126,7 +137,7 @@ typedef struct {
   int form;                 /* the form actually run (never PR_FORM_AUTO)                               */
   int c0;
   int iterations;           /* updates applied so far                                                    */
-  int iterations_by_precision[4]; /* indexed by pr_precision                                             */
+  int iterations_by_precision[PR_NPREC]; /* indexed by pr_precision                                      */
   int switch_iteration;     /* iteration index at which the precision last changed, -1 if never          */
   int last_precision;       /* precision of the last update, -1 before the first                          */
   int last_stop;            /* pr_status of the last pr_iterate / pr_solve                                */
@@ -142,9 +153,9 @@ typedef struct {
   double gemm_flops_timed;  /* algorithmic flops of the timed products                                     */
   int emu_slices;           /* digit planes per operand used by PR_EMU64 (S; S (S + 1) / 2 FP16 products
                                per emulated product)                                                     */
-  int64_t gemms_timed_by_precision[4];  /* the timed counters above, split by pr_precision            */
-  double gemm_ms_by_precision[4];
-  double gemm_flops_by_precision[4];
+  int64_t gemms_timed_by_precision[PR_NPREC];  /* the timed counters above, split by pr_precision     */
+  double gemm_ms_by_precision[PR_NPREC];
+  double gemm_flops_by_precision[PR_NPREC];
   double c0_gate;                   /* PR_C0_POLY: the gate's estimate of ||I - C_0^p A||_2, else 0         */
   double true_residual;     /* ||I - C^p A||_F of the iterate at the last stop of pr_iterate: the verified
                                value of the coupled form (pr_options.verify), the tested residual of the
@@ -184,8 +195,9 @@ pr_status pr_load(pr_handle h, const double* A);
  * iterate is tested: r_k <= tol returns PR_OK; a non-finite r_k returns PR_EDIVERGED; r_{k-1} < stag_below
  * and r_k > stag_ratio * r_{k-1} (both computed in this call) returns PR_ESTAGNATED; an exhausted budget
  * returns PR_EMAXITER. *steps_done (may be NULL) receives the number of updates applied in this call.
- * When a PR_BF16 run stops because r_k >= r_{k-1}, the last update is undone (the iterate, its residual
- * and the counters return to step k-1), so that a following precise phase starts from the better iterate.
+ * When a run below FP64 accuracy (PR_FP8, PR_BF16, PR_FP32X) stops because r_k >= r_{k-1} or r_k is not finite,
+ * the last update is undone (the iterate, its residual and the counters return to step k-1) and the stop is
+ * PR_ESTAGNATED, so that a following precise phase starts from the better iterate.
  * The residual tested is ||I - C_k^p A||_F for the Newton-Schulz and literal forms and the carried
  * ||I - M_k||_F for the coupled form (equal in exact arithmetic). With pr_options.verify the coupled form
  * then evaluates the true residual of the iterate it stops at (pr_stats.true_residual), and a PR_OK whose
@@ -198,9 +210,9 @@ pr_status pr_iterate(pr_handle h, int max_steps, int precision, double tol, int*
  * was computed at; opt NULL = defaults. Returns PR_EDIVERGED if r_k is not finite, PR_OK if r_k <= tol,
  * PR_ESTAGNATED if r_{k-1} and r_k were computed at the same precision and either
  *   (a) r_{k-1} < arm and r_k > stag_ratio * r_{k-1}, arm = stag_below (PR_FP64, PR_EMU64) or
- *       stag_below_lowp (PR_BF16), or
- *   (b) PR_BF16 only: r_k >= r_{k-1} (a low-precision floor, or the iteration leaving its region of
- *       convergence because the rounding of the iterate is too coarse for the conditioning of A),
+ *       stag_below_lowp (PR_FP8, PR_BF16, PR_FP32X), or
+ *   (b) PR_FP8, PR_BF16, PR_FP32X only: r_k >= r_{k-1} (a low-precision floor, or the iteration leaving its
+ *       region of convergence because the rounding of the iterate is too coarse for the conditioning of A),
  * and -1 otherwise (continue). The step budget and max_iter are checked by pr_iterate itself. */
 int pr_stop_rule(const double* hist, const int* prec, int len, double tol, const pr_options* opt);
 
@@ -211,6 +223,17 @@ int pr_stop_rule(const double* hist, const int* prec, int len, double tol, const
  * stop status of the last phase run. */
 pr_status pr_solve(pr_handle h, int bulk_precision, int bulk_steps, int final_precision, double tol,
                    int* steps_done);
+
+/* A precision ladder of `count` rungs in one call: rung r runs pr_iterate at precisions[r] with at most
+ * max_steps[r] updates (max_steps NULL: no per-rung limit beyond max_iter). A rung that ends with PR_OK
+ * returns at once; one that ends with PR_ESTAGNATED (its precision floor), PR_EMAXITER or PR_EINACCURATE
+ * hands over to the next rung; any other status is returned. The coupled form re-forms M = X^p A at the
+ * higher precision when the level rises (pr_options.reanchor): PR_FP8 < PR_BF16 < PR_FP32X < PR_FP64 =
+ * PR_EMU64. Returns the status of the last rung run; *steps_done (may be NULL) receives the updates of all
+ * rungs together. pr_stats.iterations_by_precision and switch_iteration record where each rung ended.
+ * Errors: as pr_iterate, and PR_EINVAL for count < 1 or a NULL precisions array. */
+pr_status pr_solve_ladder(pr_handle h, int count, const int* precisions, const int* max_steps, double tol,
+                          int* steps_done);
 
 /* True residual ||I - C^p A||_F of the current iterate (Eq. 2 in the Frobenius norm), evaluated with
  * products at the given precision: C^p by symmetric products, then the full product with A.
@@ -233,9 +256,11 @@ pr_status pr_history(pr_handle h, double* out, int cap, int* len);
  * P = X Y for symmetric n x n FP64 X and Y (device or host memory) that commute, so that X Y is symmetric.
  * sym != 0 computes only the upper-triangle tiles and mirrors them (the iteration's symmetric products);
  * sym == 0 computes every tile. precision PR_FP64 uses FP64 DMMA; PR_BF16 rounds X and Y to BF16 and
- * accumulates in FP32 on the tcgen05 tensor cores; PR_EMU64 forms the product from 8 balanced base-256
- * digit planes per operand, exact in FP16, and the 36 digit-plane pairs that reach FP64 accuracy (see
- * PR_EMU64). P: n*n FP64 output (device or host), caller-owned.
+ * accumulates in FP32 on the tcgen05 tensor cores; PR_FP8 rounds X 2^-sx_i and Y 2^-sy_j to E4M3 row by
+ * row (see PR_FP8) and accumulates in FP32; PR_EMU64 forms the product from 8 balanced base-256 digit
+ * planes per operand, exact in FP16, and the 36 digit-plane pairs that reach FP64 accuracy (see PR_EMU64);
+ * PR_FP32X uses the first 3 of those planes and their 6 pairs. P: n*n FP64 output (device or host),
+ * caller-owned.
  * Allocates and frees temporary device buffers. Synchronises the stream. */
 pr_status pr_matmul(int precision, const double* X, const double* Y, int64_t n, int sym, double* P, void* stream);
 
@@ -253,10 +278,11 @@ pr_status pr_matmul_emu(int slices, const double* X, const double* Y, int64_t n,
  * Layout: pr_state_header; hist_len doubles (r_0 ..); hist_len int32 precisions, padded to a multiple of
  * 8 bytes; n_mats FP64 matrices n x n (X, then M, N); n_mats BF16 matrices n x ldl (same order). */
 #define PR_STATE_MAGIC 0x5052535441544531ull /* "PRSTATE1" */
+#define PR_STATE_VERSION 2                   /* 2: per-precision counters for PR_NPREC precisions */
 typedef struct {
   uint64_t magic;
   int64_t n;
-  int32_t version;         /* 1 */
+  int32_t version;         /* PR_STATE_VERSION */
   int32_t p;
   int32_t form;
   int32_t c0;
@@ -266,13 +292,14 @@ typedef struct {
   int32_t state_level;     /* precision level at which M was formed */
   int32_t lp_stale;        /* the BF16 copies are out of date */
   int32_t iterations;
-  int32_t iterations_by_precision[4];
+  int32_t iterations_by_precision[PR_NPREC];
   int32_t switch_iteration;
   int32_t last_precision;
   int32_t hist_len;
   int32_t n_mats;          /* 1 (X) or 3 (X, M, N) */
   int32_t ldl;             /* leading dimension of the BF16 copies */
   int32_t reserved;
+  int32_t reserved2;
   double last_residual;
 } pr_state_header;
 
@@ -394,6 +421,13 @@ pr_status pr_batch_destroy(pr_batch b);
  * The traces come from Ahat, Ahat^2, Ahat^3 (two PR_EMU64 symmetric products) as Frobenius inner products.
  * out: 8 doubles, host memory. Synchronises the stream. */
 pr_status pr_features(pr_handle h, double* out);
+
+/* Estimates of the extreme eigenvalues of the caller's A, by `iters` power iterations on the device (each from
+ * below): *lam_max = ||A||_2, and *lam_min = ||C||_2^(-p) with C the current iterate (the root the handle
+ * returns), which is lambda_min(A) once C has converged to A^{-1/p}. Used to build training labels for the
+ * learned guess (the spectral interval of A / ||A||_1). Synchronises the stream.
+ * Errors: PR_ESTATE (NULL handle, no matrix), PR_EINVAL (iters < 1, NULL output), PR_ECUDA. */
+pr_status pr_spectral_bounds(pr_handle h, int iters, double* lam_min, double* lam_max);
 
 /* Re-forms C_0 from the loaded A with `kind` (PR_C0_EQ3, PR_C0_SCALED_I or PR_C0_POLY; coef: the 4 cubic
  * coefficients for PR_C0_POLY, host memory, else may be NULL) and restarts the iteration from it (history

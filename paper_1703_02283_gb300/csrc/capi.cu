@@ -18,7 +18,18 @@ namespace {
 thread_local std::string g_init_error;  // text of the last failing pr_init (no handle to hold it)
 
 // Precision levels: a switch to a higher level re-forms the coupled product M at that level.
-int precision_level(int prec) { return prec == PR_BF16 ? 1 : 2; }
+int precision_level(int prec) {
+  switch (prec) {
+    case PR_FP8: return 0;
+    case PR_BF16: return 1;
+    case PR_FP32X: return 2;
+    default: return 3;  // PR_FP64, PR_EMU64
+  }
+}
+
+// Digit planes a PR_FP32X product uses: 3 of the 8 base-256 digits (24 bits per row, the significand width
+// of FP32), 6 exact digit-pair products.
+constexpr int kFp32xSlices = 3;
 
 // One matrix in the two representations the products use: FP64 (leading dimension n) and BF16
 // (leading dimension ldl, the operand of the tensor-core products).
@@ -28,6 +39,10 @@ struct Mat {
   __half* sl = nullptr;         // PR_EMU64: S FP16 digit planes of f (allocated on first use)
   int* ex = nullptr;            // PR_EMU64: row exponents of the digit planes
   bool sl_valid = false;        // the digit planes describe the current f
+  uint8_t* q = nullptr;         // PR_FP8: E4M3 copy of f / 2^qe (row by row), allocated on first use
+  int* qe = nullptr;            // PR_FP8: row scales (exponents)
+  bool q_valid = false;         // the E4M3 copy describes the current f
+  void changed() { sl_valid = q_valid = false; }  // f was written
 };
 
 void swap(Mat& a, Mat& b) { std::swap(a, b); }
@@ -53,6 +68,7 @@ struct pr_handle_s {
   cudaStream_t stream = nullptr;
   int device = 0;
   int ldl = 0;  // leading dimension of the BF16 copies
+  int ldq = 0;  // leading dimension (bytes) of the E4M3 copies
   int eld = 0;  // K extent of a PR_EMU64 digit-plane row (n rounded up to 16)
   int S = 8;    // digit planes per operand for PR_EMU64
   int4* emu_items[2] = {nullptr, nullptr};  // PR_EMU64 work lists: symmetric, full products
@@ -150,9 +166,26 @@ pr_status sync(pr_handle h) {
   return PR_OK;
 }
 
-bool lowp(int prec) { return prec == PR_BF16; }
+// The rungs below FP64 accuracy: their own stagnation threshold (stag_below_lowp), a stop at the first
+// residual that does not fall, and the roll-back of that last step.
+bool lowp(int prec) { return prec == PR_BF16 || prec == PR_FP8 || prec == PR_FP32X; }
 
 // Digit planes of m for PR_EMU64 products (allocated on first use, recomputed when m changed).
+// The E4M3 copy of m for PR_FP8 products (allocated on first use, recomputed when m changed).
+pr_status ensure_fp8(pr_handle h, Mat& m) {
+  const int n = (int)h->n;
+  if (!m.q) {
+    PR_CK(h, cudaMalloc((void**)&m.q, (size_t)n * (size_t)h->ldq));
+    PR_CK(h, cudaMalloc((void**)&m.qe, (size_t)n * sizeof(int)));
+    m.q_valid = false;
+  }
+  if (m.q_valid) return PR_OK;
+  PR_CK(h, pr::to_fp8(m.f, n, h->ldq, m.q, m.qe, h->stream));
+  h->st.launches += 1;
+  m.q_valid = true;
+  return PR_OK;
+}
+
 pr_status ensure_slices(pr_handle h, Mat& m) {
   const int n = (int)h->n;
   if (!m.sl) {
@@ -170,9 +203,12 @@ pr_status ensure_slices(pr_handle h, Mat& m) {
 // One matrix product P = X Y (X, Y symmetric, or Y given transposed in its BF16 copy) at the requested
 // precision, with the fused epilogue described by o.
 pr_status product(pr_handle h, int prec, Mat& X, Mat& Y, Mode mode, const Out& o) {
-  const pr::NvtxRange trace(prec == PR_EMU64 ? (mode == Mode::Sym ? "product EMU64 sym" : "product EMU64 full")
-                            : prec == PR_BF16 ? (mode == Mode::Sym ? "product BF16 sym" : "product BF16 full")
-                                              : (mode == Mode::Sym ? "product FP64 sym" : "product FP64 full"));
+  const bool sym = mode == Mode::Sym;
+  const pr::NvtxRange trace(prec == PR_EMU64    ? (sym ? "product EMU64 sym" : "product EMU64 full")
+                            : prec == PR_FP32X ? (sym ? "product FP32X sym" : "product FP32X full")
+                            : prec == PR_BF16  ? (sym ? "product BF16 sym" : "product BF16 full")
+                            : prec == PR_FP8   ? (sym ? "product FP8 sym" : "product FP8 full")
+                                               : (sym ? "product FP64 sym" : "product FP64 full"));
   const int n = (int)h->n;
   const double flops = mode == Mode::Sym ? sym_flops(n) : full_flops(n);
   Epilogue e;
@@ -181,13 +217,19 @@ pr_status product(pr_handle h, int prec, Mat& X, Mat& Y, Mode mode, const Out& o
   e.b = o.b;
   e.c = o.c;
   e.partial = o.partial ? h->partial : nullptr;
-  if (prec == PR_EMU64) {
+  if (prec == PR_EMU64 || prec == PR_FP32X) {
     pr_status s = ensure_slices(h, X);
     if (s == PR_OK) s = ensure_slices(h, Y);
     if (s != PR_OK) return s;
     if (o.out) e.out = o.out->f;
     if (o.out2) e.out2 = o.out2->f;
-  } else if (lowp(prec)) {
+  } else if (prec == PR_FP8) {
+    pr_status s = ensure_fp8(h, X);
+    if (s == PR_OK) s = ensure_fp8(h, Y);
+    if (s != PR_OK) return s;
+    if (o.out) e.out = o.out->f;  // FP8 results keep their FP64 copies: the next product re-quantises them
+    if (o.out2) e.out2 = o.out2->f;
+  } else if (prec == PR_BF16) {
     if (o.out) {
       e.out_lp = o.out->b;
       if (o.out_master) e.out = o.out->f;
@@ -220,18 +262,24 @@ pr_status product(pr_handle h, int prec, Mat& X, Mat& Y, Mode mode, const Out& o
       PR_CK(h, pr::gemm_bf16_tc(X.b, Y.b, n, h->ldl, mode, o.transpose, e, h->err_word(), h->stream));
       break;
     case PR_EMU64:
-      PR_CK(h, pr::gemm_emu(X.sl, X.ex, Y.sl, Y.ex, n, h->eld, h->S, mode, o.transpose,
-                            h->emu_items[mode == Mode::Sym ? 0 : 1], h->emu_nitems[mode == Mode::Sym ? 0 : 1], e,
-                            h->emu_scratch, h->emu_nsplit[mode == Mode::Sym ? 0 : 1] ? h->emu_split : nullptr,
-                            h->emu_split_cnt, h->err_word(), h->stream));
+    case PR_FP32X:
+      PR_CK(h, pr::gemm_emu(X.sl, X.ex, Y.sl, Y.ex, n, h->eld, prec == PR_FP32X ? std::min(h->S, kFp32xSlices) : h->S,
+                            mode, o.transpose, h->emu_items[mode == Mode::Sym ? 0 : 1],
+                            h->emu_nitems[mode == Mode::Sym ? 0 : 1], e, h->emu_scratch,
+                            h->emu_nsplit[mode == Mode::Sym ? 0 : 1] ? h->emu_split : nullptr, h->emu_split_cnt,
+                            h->err_word(), h->stream));
+      h->lp_stale = true;
+      break;
+    case PR_FP8:
+      PR_CK(h, pr::gemm_fp8_tc(X.q, X.qe, Y.q, Y.qe, n, h->ldq, mode, o.transpose, e, h->err_word(), h->stream));
       h->lp_stale = true;
       break;
     default:
       return fail(h, PR_EUNSUPPORTED, "precision not available in this build");
   }
   h->st.launches += 1;
-  if (o.out) o.out->sl_valid = false;
-  if (o.out2) o.out2->sl_valid = false;
+  if (o.out) o.out->changed();
+  if (o.out2) o.out2->changed();
   if (h->timing) {
     PR_CK(h, cudaEventRecord(h->ev[2 * h->ev_pending + 1], h->stream));
     h->ev_flops[h->ev_pending] = flops;
@@ -242,7 +290,7 @@ pr_status product(pr_handle h, int prec, Mat& X, Mat& Y, Mode mode, const Out& o
 }
 
 int tiles_for(pr_handle h, int prec, Mode mode) {
-  if (prec == PR_EMU64) return pr::emu_tiles((int)h->n, mode);
+  if (prec == PR_EMU64 || prec == PR_FP32X) return pr::emu_tiles((int)h->n, mode);
   return lowp(prec) ? pr::gemm_tc_tiles((int)h->n, mode) : pr::gemm_f64_tiles((int)h->n, mode);
 }
 
@@ -324,8 +372,8 @@ pr_status coupled_update(pr_handle h, int prec) {
   last.partial = true;
   // At low precision the FP64 copies of M and N are only needed if a later switch to higher precision
   // carries them over instead of re-forming M from X.
-  last.out_master = last.out2_master = !(lowp(prec) && h->opt.reanchor);
-  if (p == 3 && !lowp(prec)) {
+  last.out_master = last.out2_master = !(prec == PR_BF16 && h->opt.reanchor);
+  if (p == 3 && prec != PR_BF16) {
     // N^3 M = M (4I - M)^3 / 27 = L R with L = 4M - M^2 and R = (16I - 8M + M^2) / 27: two products
     // instead of three (every factor is a polynomial in M, hence in A). The first product gives M^2 and, in
     // its epilogue, R; L follows element by element. (Low precision keeps the plain chain: its FP64 copy of
@@ -341,7 +389,7 @@ pr_status coupled_update(pr_handle h, int prec) {
     if (s != PR_OK) return s;
     PR_CK(h, pr::lincomb(h->M.f, h->T0.f, h->n * h->n, 4.0, -1.0, h->T0.f, h->stream));
     h->st.launches += 1;
-    h->T0.sl_valid = false;
+    h->T0.changed();
     s = product(h, prec, h->T0, h->T1, Mode::Sym, last);
     if (s != PR_OK) return s;
   } else if (p == 4) {
@@ -432,7 +480,7 @@ pr_status literal_update(pr_handle h, int prec) {
   if (s != PR_OK) return s;
   PR_CK(h, pr::symmetrize(h->Mn.f, (int)h->n, h->Xn.f, h->stream));
   h->st.launches += 1;
-  h->Xn.sl_valid = false;
+  h->Xn.changed();
   swap(h->X, h->Xn);
   return PR_OK;
 }
@@ -440,7 +488,7 @@ pr_status literal_update(pr_handle h, int prec) {
 // True residual ||I - C^p A||_F of the current iterate: C^p by symmetric products (powers of a symmetric
 // matrix are symmetric), then the full product with A, with products at the given precision.
 pr_status true_residual(pr_handle h, int precision, double* res_fro) {
-  if (lowp(precision)) {
+  if (precision == PR_BF16) {
     pr_status s = refresh_lowp(h);
     if (s != PR_OK) return s;
   }
@@ -478,7 +526,7 @@ int decide(pr_handle h, double tol, int steps_this_call, int max_steps) {
   return -1;
 }
 
-bool precision_known(int prec) { return prec == PR_FP64 || prec == PR_EMU64 || prec == PR_BF16; }
+bool precision_known(int prec) { return prec >= PR_FP64 && prec <= PR_FP8; }
 
 pr_status check_precision(pr_handle h, int prec) {
   if (!precision_known(prec)) return fail(h, PR_EINVAL, "unknown precision");
@@ -488,7 +536,7 @@ pr_status check_precision(pr_handle h, int prec) {
 }
 
 pr_status ensure_state(pr_handle h, int prec) {
-  if (lowp(prec)) {
+  if (prec == PR_BF16) {
     pr_status s = refresh_lowp(h);
     if (s != PR_OK) return s;
   }
@@ -528,6 +576,23 @@ pr_status powers_of_A(pr_handle h) {
   s = product(h, PR_EMU64, h->A, h->T0, Mode::Sym, o3);
   h->powers_valid = s == PR_OK;
   return s;
+}
+
+// Power iteration for ||M||_2 of a symmetric n x n M (from below), `iters` steps.
+pr_status power_norm(pr_handle h, const double* M, int iters, double* out) {
+  const int n = (int)h->n;
+  double *v = h->vec, *u = v + n, *zero = u + n, *w = zero + n, *work = w + n, *sc2 = work + kVecBlocks;
+  PR_CK(h, cudaMemsetAsync(zero, 0, sizeof(double) * n, h->stream));
+  PR_CK(h, pr::power_start(n, v, h->stream));
+  for (int it = 0; it < iters; ++it) {
+    PR_CK(h, pr::gemv(M, n, v, u, h->stream));
+    PR_CK(h, pr::power_finish_step(zero, u, n, w, work, sc2, v, sc2 + 1, h->stream));  // v = -M v / |M v|
+    h->st.launches += 4;
+  }
+  PR_CK(h, cudaMemcpyAsync(h->hpin + 6, sc2 + 1, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  pr_status st = sync(h);
+  if (st == PR_OK) *out = h->hpin[6];
+  return st;
 }
 
 // Power iteration for ||A||_2 (from below): the spectrum of A / ||A||_1 lies in (0, ||A||_2 / ||A||_1].
@@ -594,7 +659,7 @@ pr_status poly_initial_guess(pr_handle h) {
   h->st.c0_gate = gate;
   h->st.c0 = ok ? PR_C0_POLY : PR_C0_EQ3;
   if (!ok) PR_CK(h, pr::init_c0_eq3(h->A.f, n, 1.0 / (h->st.norm_1 * h->st.norm_inf), h->X.f, h->stream));
-  h->X.sl_valid = false;
+  h->X.changed();
   if (!ok && !h->opt.gate_fallback) {
     char buf[200];
     snprintf(buf, sizeof buf,
@@ -611,7 +676,7 @@ void reset_iteration(pr_handle h) {
   h->state_ready = false;
   h->state_level = 0;
   h->lp_stale = true;
-  for (Mat* m : {&h->X, &h->Xn, &h->M, &h->Mn, &h->N, &h->Nn, &h->T0, &h->T1}) m->sl_valid = false;
+  for (Mat* m : {&h->X, &h->Xn, &h->M, &h->Mn, &h->N, &h->Nn, &h->T0, &h->T1}) m->changed();
   h->hist.clear();
   h->hist_prec.clear();
   h->st.iterations = 0;
@@ -639,7 +704,7 @@ pr_status form_initial_guess(pr_handle h) {
     }
     if (st != PR_OK) return st;
   }
-  h->X.sl_valid = false;
+  h->X.changed();
   h->st.launches += 1;
   return sync(h);
 }
@@ -656,13 +721,14 @@ pr_status matmul(int precision, int S, const double* X, const double* Y, int64_t
                  void* stream) {
   if (!X || !Y || !P) return fail(nullptr, PR_EINVAL, "pr_matmul: NULL matrix");
   if (n < 1 || n > (int64_t)1 << 17) return fail(nullptr, PR_EINVAL, "pr_matmul: n must be in [1, 131072]");
-  if (precision != PR_FP64 && precision != PR_BF16 && precision != PR_EMU64)
-    return fail(nullptr, PR_EINVAL, "pr_matmul: unknown precision");
+  if (!precision_known(precision)) return fail(nullptr, PR_EINVAL, "pr_matmul: unknown precision");
+  const bool emu = precision == PR_EMU64 || precision == PR_FP32X;
   cudaStream_t s = (cudaStream_t)stream;
   const int ni = (int)n, ldl = pr::bf16_ld(ni);
   const size_t bytes = (size_t)n * (size_t)n * sizeof(double);
-  const int eld = pr::emu_ld(ni);
-  const size_t lbytes = precision == PR_EMU64 ? (size_t)8 * (size_t)n * (size_t)eld * sizeof(__half)
+  const int eld = pr::emu_ld(ni), ldq = pr::fp8_ld(ni);
+  const size_t lbytes = emu                     ? (size_t)8 * (size_t)n * (size_t)eld * sizeof(__half)
+                        : precision == PR_FP8 ? (size_t)n * (size_t)ldq
                                               : (size_t)n * (size_t)ldl * sizeof(__nv_bfloat16);
   const Mode mode = sym ? Mode::Sym : Mode::Full;
   double *dX = nullptr, *dY = nullptr, *dP = nullptr;
@@ -700,6 +766,11 @@ pr_status matmul(int precision, int S, const double* X, const double* Y, int64_t
       step(pr::to_bf16(dX, ni, ldl, bX, s));
       step(pr::to_bf16(dY, ni, ldl, bY, s));
       step(pr::gemm_bf16_tc(bX, bY, ni, ldl, mode, false, ep, err, s));
+    } else if (precision == PR_FP8) {
+      uint8_t *qX = reinterpret_cast<uint8_t*>(bX), *qY = reinterpret_cast<uint8_t*>(bY);
+      step(pr::to_fp8(dX, ni, ldq, qX, eX, s));
+      step(pr::to_fp8(dY, ni, ldq, qY, eY, s));
+      step(pr::gemm_fp8_tc(qX, eX, qY, eY, ni, ldq, mode, false, ep, err, s));
     } else {
       __half *hX = reinterpret_cast<__half*>(bX), *hY = reinterpret_cast<__half*>(bY);
       pr::emu_launch_list(ni, mode, hitems);
@@ -714,8 +785,8 @@ pr_status matmul(int precision, int S, const double* X, const double* Y, int64_t
       step(cudaMemcpyAsync(items, hitems.data(), hitems.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
       step(pr::slice(dX, ni, eld, S, hX, eX, s));
       step(pr::slice(dY, ni, eld, S, hY, eY, s));
-      step(pr::gemm_emu(hX, eX, hY, eY, ni, eld, S, mode, false, items, (int)hitems.size(), ep, scratch, split,
-                        split_cnt, err, s));
+      step(pr::gemm_emu(hX, eX, hY, eY, ni, eld, precision == PR_FP32X ? std::min(S, kFp32xSlices) : S, mode, false,
+                        items, (int)hitems.size(), ep, scratch, split, split_cnt, err, s));
     }
     step(cudaMemcpyAsync(P, dP, bytes, cudaMemcpyDefault, s));
     step(cudaMemcpyAsync(&word, err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -767,6 +838,8 @@ pr_status pr_destroy(pr_handle h) {
     if (m->b) cudaFree(m->b);
     if (m->sl) cudaFree(m->sl);
     if (m->ex) cudaFree(m->ex);
+    if (m->q) cudaFree(m->q);
+    if (m->qe) cudaFree(m->qe);
   }
   for (double* b : {h->partial, h->work, h->scal, h->vec})
     if (b) cudaFree(b);
@@ -807,6 +880,7 @@ pr_status pr_init(pr_handle* out, const double* A, int64_t n, int p, const pr_op
   h->form = o.form == PR_FORM_AUTO ? (p == 1 ? PR_FORM_NS : PR_FORM_COUPLED) : o.form;
   h->stream = (cudaStream_t)stream;
   h->ldl = pr::bf16_ld((int)n);
+  h->ldq = pr::fp8_ld((int)n);
   h->eld = pr::emu_ld((int)n);
   h->S = o.emu_slices > 0 ? o.emu_slices : pr::emu_max_slices();
   h->st.emu_slices = h->S;
@@ -878,7 +952,7 @@ pr_status pr_load(pr_handle h, const double* A) {
   const size_t bytes = (size_t)n * (size_t)n * sizeof(double);
   reset_iteration(h);
   h->powers_valid = false;
-  h->A.sl_valid = false;
+  h->A.changed();
   h->st.norm_1 = 0.0;
   PR_CK(h, cudaMemcpyAsync(h->A.f, A, bytes, cudaMemcpyDefault, h->stream));
   PR_CK(h, pr::validate(h->A.f, n, h->scal, h->stream));
@@ -957,7 +1031,7 @@ pr_status pr_export_state(pr_handle h, void* buf, size_t bytes) {
   cudaSetDevice(h->device);
   pr_state_header hd{};
   hd.magic = PR_STATE_MAGIC;
-  hd.version = 1;
+  hd.version = PR_STATE_VERSION;
   hd.n = h->n;
   hd.p = h->p;
   hd.form = h->form;
@@ -968,7 +1042,7 @@ pr_status pr_export_state(pr_handle h, void* buf, size_t bytes) {
   hd.state_level = h->state_level;
   hd.lp_stale = h->lp_stale ? 1 : 0;
   hd.iterations = h->st.iterations;
-  for (int k = 0; k < 4; ++k) hd.iterations_by_precision[k] = h->st.iterations_by_precision[k];
+  for (int k = 0; k < PR_NPREC; ++k) hd.iterations_by_precision[k] = h->st.iterations_by_precision[k];
   hd.switch_iteration = h->st.switch_iteration;
   hd.last_precision = h->st.last_precision;
   hd.hist_len = (int32_t)h->hist.size();
@@ -1000,7 +1074,7 @@ pr_status pr_import_state(pr_handle h, const void* buf, size_t bytes) {
   if (!buf || bytes < sizeof(pr_state_header)) return fail(h, PR_EINVAL, "pr_import_state: buffer NULL or too small");
   pr_state_header hd;
   memcpy(&hd, buf, sizeof hd);
-  if (hd.magic != PR_STATE_MAGIC || hd.version != 1) return fail(h, PR_EINVAL, "pr_import_state: not a state buffer");
+  if (hd.magic != PR_STATE_MAGIC || hd.version != PR_STATE_VERSION) return fail(h, PR_EINVAL, "pr_import_state: not a state buffer");
   if (hd.n != h->n || hd.p != h->p || hd.form != h->form || hd.ldl != h->ldl)
     return fail(h, PR_EINVAL, "pr_import_state: the state belongs to another order, root or form");
   if (hd.norm_1 != h->st.norm_1 || hd.norm_inf != h->st.norm_inf)
@@ -1032,7 +1106,7 @@ pr_status pr_import_state(pr_handle h, const void* buf, size_t bytes) {
   h->lp_stale = hd.lp_stale != 0;
   h->st.c0 = hd.c0;
   h->st.iterations = hd.iterations;
-  for (int k = 0; k < 4; ++k) h->st.iterations_by_precision[k] = hd.iterations_by_precision[k];
+  for (int k = 0; k < PR_NPREC; ++k) h->st.iterations_by_precision[k] = hd.iterations_by_precision[k];
   h->st.switch_iteration = hd.switch_iteration;
   h->st.last_precision = hd.last_precision;
   h->st.last_residual = hd.last_residual;
@@ -1110,10 +1184,13 @@ pr_status pr_iterate(pr_handle h, int max_steps, int precision, double tol, int*
       push_residual(h, r, precision, same_iterate);
     }
     stop = decide(h, tol, steps, max_steps);
-    if (stop == PR_ESTAGNATED && lowp(precision) && steps > 0 && h->hist.size() >= 2 &&
-        h->hist.back() >= h->hist[h->hist.size() - 2] && h->form != PR_FORM_LITERAL) {
-      // The last low-precision update made things worse: return to the previous iterate, which the
-      // double-buffered state still holds, so that a precise phase starts from the better one.
+    const bool worse = h->hist.size() >= 2 && !(h->hist.back() < h->hist[h->hist.size() - 2]);  // or not finite
+    if ((stop == PR_ESTAGNATED || stop == PR_EDIVERGED) && lowp(precision) && steps > 0 && worse &&
+        h->form != PR_FORM_LITERAL) {
+      // The last low-precision update made things worse (or overflowed): return to the previous iterate,
+      // which the double-buffered state still holds, so that a more precise phase starts from the better
+      // one. A low-precision rung that overflows has reached its floor, not diverged.
+      stop = PR_ESTAGNATED;
       swap(h->X, h->Xn);
       if (h->form == PR_FORM_COUPLED) {
         swap(h->M, h->Mn);
@@ -1185,6 +1262,23 @@ pr_status pr_solve(pr_handle h, int bulk_precision, int bulk_steps, int final_pr
   return s;
 }
 
+pr_status pr_solve_ladder(pr_handle h, int count, const int* precisions, const int* max_steps, double tol,
+                          int* steps_done) {
+  if (steps_done) *steps_done = 0;
+  if (!h) return fail(nullptr, PR_ESTATE, "pr_solve_ladder: NULL handle");
+  if (count < 1 || !precisions) return fail(h, PR_EINVAL, "pr_solve_ladder: count < 1 or precisions NULL");
+  int total = 0;
+  pr_status s = PR_EINVAL;
+  for (int r = 0; r < count; ++r) {
+    int d = 0;
+    s = pr_iterate(h, max_steps ? max_steps[r] : (1 << 30), precisions[r], tol, &d);
+    total += d;
+    if (steps_done) *steps_done = total;
+    if (s != PR_ESTAGNATED && s != PR_EMAXITER && s != PR_EINACCURATE) return s;
+  }
+  return s;
+}
+
 pr_status pr_residual(pr_handle h, int precision, double* res_fro) {
   if (!h) return fail(nullptr, PR_ESTATE, "pr_residual: NULL handle");
   if (!res_fro) return fail(h, PR_EINVAL, "pr_residual: res_fro is NULL");
@@ -1204,7 +1298,7 @@ pr_status pr_result(pr_handle h, double* C_out) {
     PR_CK(h, pr::lincomb(h->X.f, h->X.f, h->n * h->n, exp2((double)h->st.prescale_log2 / h->p), 0.0, h->T1.f,
                          h->stream));
     h->st.launches += 1;
-    h->T1.sl_valid = false;
+    h->T1.changed();
     h->powers_valid = false;
     src = h->T1.f;
   }
@@ -1252,6 +1346,23 @@ pr_status pr_features(pr_handle h, double* out) {
   }
   out[6] = ldexp(h->st.norm_1, -h->st.prescale_log2);  // the norms of the caller's A
   out[7] = ldexp(h->st.norm_inf, -h->st.prescale_log2);
+  return PR_OK;
+}
+
+pr_status pr_spectral_bounds(pr_handle h, int iters, double* lam_min, double* lam_max) {
+  if (!h) return fail(nullptr, PR_ESTATE, "pr_spectral_bounds: NULL handle");
+  if (iters < 1 || !lam_min || !lam_max) return fail(h, PR_EINVAL, "pr_spectral_bounds: iters < 1 or NULL output");
+  if (h->st.norm_1 <= 0.0) return fail(h, PR_ESTATE, "pr_spectral_bounds: no matrix loaded");
+  cudaSetDevice(h->device);
+  pr_status s = ensure_vec(h);
+  double na = 0.0, nc = 0.0;
+  if (s == PR_OK) s = power_norm(h, h->A.f, iters, &na);
+  if (s == PR_OK) s = power_norm(h, h->X.f, iters, &nc);
+  if (s != PR_OK) return s;
+  // The handle holds 2^k A and its root: lambda_max(A) = ||2^k A||_2 2^-k; the root of A is 2^(k/p) X, so
+  // lambda_min(A) = ||2^(k/p) X||_2^(-p) = ||X||_2^(-p) 2^-k.
+  *lam_max = ldexp(na, -h->st.prescale_log2);
+  *lam_min = ldexp(pow(nc, -(double)h->p), -h->st.prescale_log2);
   return PR_OK;
 }
 

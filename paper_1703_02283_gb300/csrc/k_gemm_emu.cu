@@ -307,8 +307,9 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
   __syncthreads();
   ptx::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  // Planes used by a pass: levels 2..5 need digits 1..4 only (one plane group), levels 6..9 all 8.
-  const int groups1 = S > 4 ? 2 : 1;
+  // Planes used by a pass: levels 2..5 need digits 1..4 only (one plane group), levels 6..9 all 8. With at
+  // most 4 digits (S <= 4) every level is at most 5: the second pass has no work and is skipped.
+  const int groups1 = S > 4 ? 2 : 1, npass = S > 4 ? 2 : 1;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -319,7 +320,7 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
         int bi, bj, kpart, j0, j1;
         const EmuMat& mt = item_of<SPLIT>(args, t, bi, bj, kpart, j0, j1);
         const int ya = mt.row0 + bi * EBM, yb = mt.row0 + bj * EBN;
-        for (int pass = 0; pass < 2 && !stop; ++pass) {
+        for (int pass = 0; pass < npass && !stop; ++pass) {
           const int ng = pass == 0 ? 1 : groups1;
           for (int j = j0; j < j1; ++j, ++it) {
             const int st = it % NSTAGE;
@@ -351,7 +352,7 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
       for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
         int bi, bj, kpart, j0, j1;
         item_of<SPLIT>(args, t, bi, bj, kpart, j0, j1);
-        for (int pass = 0; pass < 2 && !stop; ++pass) {
+        for (int pass = 0; pass < npass && !stop; ++pass) {
           const int np = pass == 0 ? min(S, 4) : S;
           for (int j = j0; j < j1; ++j, ++it) {
             const int st = it % NSTAGE, b = it & 1;
@@ -385,7 +386,7 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
         int bi, bj, kpart, j0, j1;
         item_of<SPLIT>(args, t, bi, bj, kpart, j0, j1);
         const int KS = j1 - j0;
-        for (int pass = 0; pass < 2 && !stop; ++pass) {
+        for (int pass = 0; pass < npass && !stop; ++pass) {
           for (int j = 0; j < KS && !stop; ++j, ++it) {
             const int st = it % NSTAGE, b = it & 1;
             if (*s_abort || !ptx::mbar_wait(full0 + 8 * st, (it / NSTAGE) & 1, args.err, 14) ||
@@ -459,7 +460,7 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
       long long acc[EPI_COLS];
 #pragma unroll
       for (int c = 0; c < EPI_COLS; ++c) acc[c] = 0;
-      for (int pass = 0; pass < 2 && !stop; ++pass) {
+      for (int pass = 0; pass < npass && !stop; ++pass) {
         for (int j = 0; j < KS && !stop; ++j) {
           const bool lastj = j == KS - 1;
           for (int a = 0; a < NACC; ++a) {

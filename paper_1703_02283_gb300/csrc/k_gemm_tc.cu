@@ -1,11 +1,20 @@
-// BF16 tensor-core products for the low-precision iterations of Eq. 1 (Sec. 3, approximate arithmetic).
+// BF16 and FP8 tensor-core products for the low-precision iterations of Eq. 1 (Sec. 3, approximate
+// arithmetic).
 //
-// P[i][j] = sum_k X[i][k] Y[j][k] for BF16 operands stored row-major (K contiguous), i.e. P = X Y^T; for the
-// symmetric iterates of Sec. 2 Y^T = Y, so this is X Y. Persistent kernel, one CTA per SM, 128 x 256
-// output tiles (symmetric mode: only tiles that reach the upper triangle), 192 threads:
-//   warp 0 (one lane)  TMA producer: 128 x 64 boxes of X and 256 x 64 boxes of Y, 128-byte swizzled, into a
-//                      4-stage ring (48 KB per stage), completing on the stage's "full" mbarrier;
-//   warp 1 (one lane)  MMA issuer: 4 x tcgen05.mma (M = 128, N = 256, K = 16) per stage into one of two
+// P[i][j] = sum_k X[i][k] Y[j][k] for operands stored row-major (K contiguous), i.e. P = X Y^T; for the
+// symmetric iterates of Sec. 2 Y^T = Y, so this is X Y. Two operand types share one kernel:
+//   BF16  kind::f16 MMAs, K = 16 per instruction, 64 elements per 128-byte row of a stage;
+//   FP8   E4M3 with a power-of-two scale per row (X_ik = 2^sx_i q_ik, Y_jk = 2^sy_j r_jk), kind::f8f6f4 MMAs,
+//         K = 32 per instruction, 128 elements per 128-byte row; the epilogue multiplies the FP32 sum by
+//         2^(sx_i + sy_j). Row scales of a symmetric iterate are its column scales, so the tile (i, j) of P
+//         gets the scale of its row block times that of its column block, element by element.
+// Both move the same bytes per stage and advance 32 bytes along K per instruction, so the ring, the
+// descriptors and the epilogue are shared. Persistent kernel, one CTA per SM, 128 x 256 output tiles
+// (symmetric mode: only tiles that reach the upper triangle), 192 threads:
+//   warp 0 (one lane)  TMA producer: 128 x 128-byte boxes of X and 256 x 128-byte boxes of Y, 128-byte
+//                      swizzled, into a 4-stage ring (48 KB per stage), completing on the stage's "full"
+//                      mbarrier;
+//   warp 1 (one lane)  MMA issuer: 4 x tcgen05.mma (M = 128, N = 256) per stage into one of two
 //                      256-column FP32 accumulators in TMEM; tcgen05.commit frees the ring stage and, after
 //                      the last K block, hands the accumulator to the epilogue ("tfull");
 //   warps 2-5          epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile rows) with tcgen05.ld,
@@ -23,19 +32,24 @@
 namespace pr {
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int BM = 128, BN = 256, ROW_BYTES = 128, STAGES = 4;
 constexpr int EPI_WARPS = 4, THREADS = 64 + 32 * EPI_WARPS;
-constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int A_BYTES = BM * ROW_BYTES, B_BYTES = BN * ROW_BYTES, STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int STG_FLOATS = 32 * 33;
 constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + EPI_WARPS * STG_FLOATS * 4 + 256;
 constexpr int TMEM_COLS = 2 * BN;
-constexpr uint32_t kIdesc = ptx::idesc_bf16_f32(BM, BN);
+
+// Elements of one 128-byte row of a stage (the K block) for 2-byte (BF16) and 1-byte (E4M3) operands.
+template <bool F8>
+constexpr int block_k() { return F8 ? 128 : 64; }
 
 struct TcArgs {
   int n, ldl;
   int Tm, Tn, ntiles;
   int transpose;  // full mode: store P^T
   Epilogue e;
+  const int* sx;  // FP8: row scales (exponents) of X and Y
+  const int* sy;
   int* err;
 };
 
@@ -79,9 +93,11 @@ struct Emit {
   }
 };
 
-template <bool SYM>
+template <bool SYM, bool F8>
 __global__ void __launch_bounds__(THREADS, 1)
-    k_gemm_bf16_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, TcArgs args) {
+    k_gemm_lowp_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, TcArgs args) {
+  constexpr int BK = block_k<F8>();
+  constexpr uint32_t kIdesc = F8 ? ptx::idesc_e4m3_f32(BM, BN) : ptx::idesc_bf16_f32(BM, BN);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* ring = smem;
@@ -167,8 +183,10 @@ __global__ void __launch_bounds__(THREADS, 1)
           const uint32_t sa = ptx::smem_u32(ring + s * STAGE_BYTES);
           const uint64_t da = ptx::desc_sw128_kmajor(sa), db = ptx::desc_sw128_kmajor(sa + A_BYTES);
 #pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk)  // +32 bytes along K: +2 in the encoded start address
-            ptx::mma_f16(d, da + 2 * kk, db + 2 * kk, kIdesc, (kb | kk) != 0);
+          for (int kk = 0; kk < 4; ++kk) {  // +32 bytes along K: +2 in the encoded start address
+            if constexpr (F8) ptx::mma_f8(d, da + 2 * kk, db + 2 * kk, kIdesc, (kb | kk) != 0);
+            else ptx::mma_f16(d, da + 2 * kk, db + 2 * kk, kIdesc, (kb | kk) != 0);
+          }
           ptx::mma_commit(empty0 + 8 * s);
         }
         if (!ok) break;
@@ -198,12 +216,21 @@ __global__ void __launch_bounds__(THREADS, 1)
       tile_coords(t, args.Tm, args.Tn, SYM, bi, bj);
       const int i0 = bi * BM, j0 = bj * BN;
       const int i = i0 + 32 * q + lane;
+      int sxi = 0;
+      if constexpr (F8) sxi = i < n ? args.sx[i] : 0;
       float part = 0.0f;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
         uint32_t v[32];
         ptx::tmem_ld_32x32b_x32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + c0), v);
         ptx::tmem_ld_wait();
+        if constexpr (F8) {
+          // P_ij = 2^(sx_i + sy_j) x the FP32 sum of the E4M3 products (lane = row i; column c0 + c).
+          const int jl = j0 + c0 + lane, syl = jl < n ? args.sy[jl] : 0;
+#pragma unroll
+          for (int c = 0; c < 32; ++c)
+            v[c] = __float_as_uint(ldexpf(__uint_as_float(v[c]), sxi + __shfl_sync(0xffffffffu, syl, c)));
+        }
         // Register layout: lane = row i. Residual partials, and the stores that land at (j, i).
         const bool colset = SYM || args.transpose;
 #pragma unroll
@@ -261,16 +288,18 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // Tensor map of an n x n BF16 matrix with leading dimension ldl: boxes of 64 (K) x box_rows, 128B swizzle.
-cudaError_t make_map(CUtensorMap* map, const __nv_bfloat16* ptr, int n, int ldl, int box_rows) {
+// Tensor map of an n x n matrix of `esize`-byte elements with leading dimension ld (elements): boxes of one
+// 128-byte row (K) x box_rows, 128B swizzle.
+cudaError_t make_map(CUtensorMap* map, const void* ptr, int n, int ld, int esize, int box_rows) {
   auto fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
   cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)n};
-  cuuint64_t strides[1] = {(cuuint64_t)ldl * 2};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * esize};
+  cuuint32_t box[2] = {(cuuint32_t)(ROW_BYTES / esize), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(ptr), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = fn(map, esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                  const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
@@ -295,6 +324,108 @@ void tile_grid(int n, Mode mode, int& Tm, int& Tn, int& ntiles) {
   }
 }
 
+
+cudaError_t set_attributes() {
+  static bool attr_set = false;
+  if (attr_set) return cudaSuccess;
+  for (auto k : {k_gemm_lowp_tc<true, false>, k_gemm_lowp_tc<false, false>, k_gemm_lowp_tc<true, true>,
+                 k_gemm_lowp_tc<false, true>}) {
+    cudaError_t a = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (a != cudaSuccess) return a;
+  }
+  attr_set = true;
+  return cudaSuccess;
+}
+
+template <bool F8>
+cudaError_t launch(const void* X, const void* Y, const int* sx, const int* sy, int n, int ld, Mode mode,
+                   bool transpose, const Epilogue& e, int* err, cudaStream_t s) {
+  const int esize = F8 ? 1 : 2;
+  if ((ld * esize) % 16 != 0 || ld < n) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) & 15) return cudaErrorMisalignedAddress;
+  if (F8 && (!sx || !sy)) return cudaErrorInvalidValue;
+  cudaError_t r = set_attributes();
+  if (r != cudaSuccess) return r;
+  CUtensorMap mx, my;
+  r = make_map(&mx, X, n, ld, esize, BM);
+  if (r != cudaSuccess) return r;
+  r = make_map(&my, Y, n, ld, esize, BN);
+  if (r != cudaSuccess) return r;
+  TcArgs args;
+  args.n = n;
+  args.ldl = ld;
+  tile_grid(n, mode, args.Tm, args.Tn, args.ntiles);
+  args.transpose = transpose ? 1 : 0;
+  args.e = e;
+  args.sx = sx;
+  args.sy = sy;
+  args.err = err;
+  const int grid = args.ntiles < sm_count() ? args.ntiles : sm_count();
+  if (mode == Mode::Sym) {
+    k_gemm_lowp_tc<true, F8><<<grid, THREADS, SMEM_BYTES, s>>>(mx, my, args);
+  } else {
+    k_gemm_lowp_tc<false, F8><<<grid, THREADS, SMEM_BYTES, s>>>(mx, my, args);
+  }
+  return cudaGetLastError();
+}
+
+// Exponent of the row's largest |x| (FP64 bits; 0 for a zero row) minus 7: the row, divided by 2^s, has its
+// largest magnitude in [128, 256), below E4M3's largest finite 448.
+__device__ __forceinline__ int fp8_row_scale(unsigned long long max_bits) {
+  const int E = (int)(max_bits >> 52);
+  return E == 0 ? 0 : E - 1023 - 7;
+}
+
+// Rounds the finite y to E4M3 (1 sign, 4 exponent bits of bias 7, 3 mantissa bits; subnormals m 2^-9; no
+// infinities; largest finite 448, larger magnitudes saturate to it) to nearest, ties to even, in one
+// rounding from FP64 (integer arithmetic on the bit pattern).
+__device__ __forceinline__ uint8_t e4m3_rne(double y) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(y);
+  const unsigned sign = (unsigned)(b >> 63) << 7;
+  const int E = (int)((b >> 52) & 0x7ff);
+  if (E == 0) return (uint8_t)sign;  // zero, or an FP64 subnormal: far below 2^-10
+  const int e = E - 1023;
+  const unsigned long long M = (b & 0xfffffffffffffull) | (1ull << 52);  // |y| = M 2^(e - 52)
+  const int emin = e < -6 ? -6 : e;           // binade of the result's last bit: 2^(emin - 3)
+  const int sh = 49 + (emin - e);             // bits of M below that last bit
+  unsigned q = 0;
+  if (sh < 54) {
+    q = (unsigned)(M >> sh);
+    const unsigned long long rest = M & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    if (rest > half || (rest == half && (q & 1u))) ++q;
+  }
+  int ee = emin;
+  if (q >= 16u) {  // rounded up into the next binade
+    q >>= 1;
+    ++ee;
+  }
+  if (q < 8u) return (uint8_t)(sign | q);  // subnormal (ee = -6), or zero
+  if (ee > 8 || (ee == 8 && q > 14u)) return (uint8_t)(sign | 0x7e);  // saturate at 448
+  return (uint8_t)(sign | ((unsigned)(ee + 7) << 3) | (q - 8u));
+}
+
+// One warp per row: s_i from the row maximum, then q_ij = E4M3(x_ij 2^-s_i) (exact scaling, one rounding).
+// Columns n .. ld - 1 get 0.
+__global__ void k_to_fp8(const double* __restrict__ X, int n, int ld, uint8_t* __restrict__ Q, int* __restrict__ sx) {
+  const int lane = threadIdx.x & 31;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += (gridDim.x * blockDim.x) >> 5) {
+    const unsigned long long* row = reinterpret_cast<const unsigned long long*>(X + (int64_t)i * n);
+    unsigned long long mb = 0;
+    for (int k = lane; k < n; k += 32) {
+      const unsigned long long u = row[k] & 0x7fffffffffffffffull;
+      mb = u > mb ? u : mb;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long w = __shfl_xor_sync(0xffffffffu, mb, o);
+      mb = w > mb ? w : mb;
+    }
+    const int si = fp8_row_scale(mb);
+    if (lane == 0) sx[i] = si;
+    for (int k = lane; k < ld; k += 32)
+      Q[(int64_t)i * ld + k] = k < n ? e4m3_rne(ldexp(__longlong_as_double((long long)row[k]), -si)) : (uint8_t)0;
+  }
+}
+
 }  // namespace
 
 int gemm_tc_tiles(int n, Mode mode) {
@@ -307,34 +438,22 @@ int bf16_ld(int n) { return (n + 7) / 8 * 8; }
 
 cudaError_t gemm_bf16_tc(const __nv_bfloat16* X, const __nv_bfloat16* Y, int n, int ldl, Mode mode, bool transpose,
                          const Epilogue& e, int* err, cudaStream_t s) {
-  if (ldl % 8 != 0 || ldl < n) return cudaErrorInvalidValue;
-  if ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) & 15) return cudaErrorMisalignedAddress;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t a = cudaFuncSetAttribute(k_gemm_bf16_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (a != cudaSuccess) return a;
-    a = cudaFuncSetAttribute(k_gemm_bf16_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (a != cudaSuccess) return a;
-    attr_set = true;
-  }
-  CUtensorMap mx, my;
-  cudaError_t r = make_map(&mx, X, n, ldl, BM);
-  if (r != cudaSuccess) return r;
-  r = make_map(&my, Y, n, ldl, BN);
-  if (r != cudaSuccess) return r;
-  TcArgs args;
-  args.n = n;
-  args.ldl = ldl;
-  tile_grid(n, mode, args.Tm, args.Tn, args.ntiles);
-  args.transpose = transpose ? 1 : 0;
-  args.e = e;
-  args.err = err;
-  const int grid = args.ntiles < sm_count() ? args.ntiles : sm_count();
-  if (mode == Mode::Sym) {
-    k_gemm_bf16_tc<true><<<grid, THREADS, SMEM_BYTES, s>>>(mx, my, args);
-  } else {
-    k_gemm_bf16_tc<false><<<grid, THREADS, SMEM_BYTES, s>>>(mx, my, args);
-  }
+  return launch<false>(X, Y, nullptr, nullptr, n, ldl, mode, transpose, e, err, s);
+}
+
+cudaError_t gemm_fp8_tc(const uint8_t* X, const int* sx, const uint8_t* Y, const int* sy, int n, int ldq, Mode mode,
+                        bool transpose, const Epilogue& e, int* err, cudaStream_t s) {
+  if (e.out_lp || e.out2_lp) return cudaErrorInvalidValue;  // FP8 products write FP64 results only
+  return launch<true>(X, Y, sx, sy, n, ldq, mode, transpose, e, err, s);
+}
+
+int fp8_ld(int n) { return (n + 15) / 16 * 16; }
+
+cudaError_t to_fp8(const double* X, int n, int ldq, uint8_t* Q, int* sx, cudaStream_t s) {
+  if (ldq < n || ldq % 16 != 0) return cudaErrorInvalidValue;
+  int blocks = (n + 7) / 8;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_to_fp8<<<blocks, 256, 0, s>>>(X, n, ldq, Q, sx);
   return cudaGetLastError();
 }
 

@@ -84,6 +84,14 @@ int gemm_tc_tiles(int n, Mode mode);
 int bf16_ld(int n);
 cudaError_t gemm_bf16_tc(const __nv_bfloat16* X, const __nv_bfloat16* Y, int n, int ldl, Mode mode, bool transpose,
                          const Epilogue& e, int* err, cudaStream_t s);
+// ---- FP8 (E4M3) tensor-core products (k_gemm_tc.cu): X = 2^sx_i Q_X, Y = 2^sy_j Q_Y row by row, Q n x n bytes
+// with leading dimension ldq = fp8_ld(n) (a multiple of 16); P = X Y^T with FP32 accumulation, FP64 outputs
+// only (the epilogue's out / out2 / partial; out_lp / out2_lp must be null). to_fp8: Q and sx of an FP64
+// matrix (per row: s_i = exponent of its largest |x| - 7, then E4M3 round-to-nearest-even of x 2^-s_i).
+int fp8_ld(int n);
+cudaError_t to_fp8(const double* X, int n, int ldq, uint8_t* Q, int* sx, cudaStream_t s);
+cudaError_t gemm_fp8_tc(const uint8_t* X, const int* sx, const uint8_t* Y, const int* sy, int n, int ldq, Mode mode,
+                        bool transpose, const Epilogue& e, int* err, cudaStream_t s);
 
 // ---- FP64-accurate products from exact FP16 digit slices (k_gemm_emu.cu).
 // slice(): X (n x n FP64) -> 8 digit planes D (layout [row][k / 16][plane][k % 16], n x 8 ldl FP16 with
@@ -190,8 +198,9 @@ cudaError_t segmented_reduce_sqrt(const double* partial, const int* begin, const
                                   cudaStream_t s);
 
 // The stop rule of pr_iterate on the newest residual r of a history: prev says that the residual before it,
-// q, was taken at the same precision; low that the precision is a low one (PR_BF16). Returns a pr_status
-// to stop with, or -1 to apply one more update. (Host and device: the batched solver decides on the GPU.)
+// q, was taken at the same precision; low that the precision is below FP64 accuracy (PR_FP8, PR_BF16,
+// PR_FP32X). Returns a pr_status to stop with, or -1 to apply one more update. (Host and device: the batched
+// solver decides on the GPU.)
 __host__ __device__ inline int stop_rule_last(double r, bool prev, double q, bool low, double tol,
                                               const pr_options& o) {
   if (!isfinite(r)) return PR_EDIVERGED;

@@ -9,8 +9,10 @@ is the cubic that makes q(x)^p x closest to 1 in least squares over that interva
 basis), i.e. C_0^p A close to I. The library gates every predicted guess against Eq. 2 and falls back to
 Eq. 3, so a poor prediction costs iterations, not correctness.
 
-Everything numerical in the solve runs in the library; this module prepares data (seeded positions,
-labels from converged roots) and drives training.
+Everything numerical in the solve runs in the library, and so do the label's spectral estimates
+(pr_spectral_bounds: power iterations on A and on the converged root, on the device). This module prepares
+data (seeded positions) and drives training; the one host computation is the label's least-squares fit of
+4 coefficients on 400 points of the spectral interval (training-data tooling, not part of a solve).
 """
 from __future__ import annotations
 
@@ -41,25 +43,11 @@ def overlap_sequence(seq: int, steps: int, n: int, every: int = 1, sigma: float 
     return out
 
 
-def _power_norm(apply, n: int, iters: int = 60) -> float:
-    v = 1.0 + 0.5 * np.sin(1.0 + np.arange(n))
-    v /= np.linalg.norm(v)
-    lam = 0.0
-    for _ in range(iters):
-        w = apply(v)
-        lam = float(np.linalg.norm(w))
-        v = w / lam
-    return lam
-
-
-def target_coefficients(A: np.ndarray, C: np.ndarray, p: int, points: int = 400) -> np.ndarray:
+def target_coefficients(s1: float, lam_min: float, lam_max: float, p: int, points: int = 400) -> np.ndarray:
     """Label: the cubic minimising sum_x (1 - q(x) x^{1/p})^2 over log-spaced x on the spectral interval of
-    A/||A||_1, the interval read from the converged root C of the plain method. The top end is widened by
-    10 % so that q stays positive across the margin the library checks above its estimate of ||A||_2."""
-    n = A.shape[0]
-    s1 = float(np.abs(A).sum(axis=0).max())
-    lam_max = _power_norm(lambda v: A @ v, n)
-    lam_min = _power_norm(lambda v: C @ v, n) ** (-p)
+    A/||A||_1 (s1 = ||A||_1; lam_min, lam_max from pr_spectral_bounds on the plain method's converged root).
+    The top end is widened by 10 % so that q stays positive across the margin the library checks above its
+    estimate of ||A||_2."""
     lo, hi = lam_min / s1, min(1.1 * lam_max / s1, 1.0)
     x = np.exp(np.linspace(math.log(lo), math.log(hi), points))
     B = np.stack([x ** (i + 1.0 / p) for i in range(4)], axis=1)
@@ -85,11 +73,10 @@ def make_samples(torch, mats, p: int, stream: int = 0, tol: float = 1e-12):
         try:
             f = np.array(P.pr_features(h))
             _, its = P.pr_iterate(h, 100, P.PR_EMU64, tol)
-            C = torch.empty_like(A)
-            P.pr_result(h, C)
+            lam_min, lam_max = P.pr_spectral_bounds(h, 60)
         finally:
             P.pr_destroy(h)
-        out.append(Sample(f, target_coefficients(S, C.cpu().numpy(), p), its))
+        out.append(Sample(f, target_coefficients(float(f[6]), lam_min, lam_max, p), its))
     return out
 
 

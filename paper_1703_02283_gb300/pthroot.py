@@ -19,7 +19,9 @@ PR_EMAXITER, PR_ETIMEOUT, PR_EGATE, PR_ESTATE, PR_EUNSUPPORTED, PR_EINACCURATE =
 STATUS_NAMES = {0: "PR_OK", 1: "PR_EINVAL", 2: "PR_ENOTSPD", 3: "PR_ENOMEM", 4: "PR_ECUDA",
                 5: "PR_EDIVERGED", 6: "PR_ESTAGNATED", 7: "PR_EMAXITER", 8: "PR_ETIMEOUT",
                 9: "PR_EGATE", 10: "PR_ESTATE", 11: "PR_EUNSUPPORTED", 12: "PR_EINACCURATE"}
-PR_FP64, PR_EMU64, PR_BF16 = 0, 1, 3
+PR_FP64, PR_EMU64, PR_FP32X, PR_BF16, PR_FP8 = 0, 1, 2, 3, 4
+PR_NPREC = 5
+PREC_NAMES = {PR_FP64: "fp64", PR_EMU64: "emu64", PR_FP32X: "fp32x", PR_BF16: "bf16", PR_FP8: "fp8"}
 PR_FORM_AUTO, PR_FORM_COUPLED, PR_FORM_NS, PR_FORM_LITERAL = 0, 1, 2, 3
 PR_C0_EQ3, PR_C0_SCALED_I, PR_C0_POLY = 0, 1, 2
 PR_MLP_PARAMS = 4996
@@ -35,14 +37,15 @@ class pr_options(ctypes.Structure):
 
 class pr_stats_t(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("p", ctypes.c_int), ("form", ctypes.c_int), ("c0", ctypes.c_int),
-                ("iterations", ctypes.c_int), ("iterations_by_precision", ctypes.c_int * 4),
+                ("iterations", ctypes.c_int), ("iterations_by_precision", ctypes.c_int * PR_NPREC),
                 ("switch_iteration", ctypes.c_int), ("last_precision", ctypes.c_int),
                 ("last_stop", ctypes.c_int), ("norm_1", ctypes.c_double), ("norm_inf", ctypes.c_double),
                 ("last_residual", ctypes.c_double), ("gemms", ctypes.c_int64), ("gemm_flops", ctypes.c_double),
                 ("launches", ctypes.c_int64), ("gemms_timed", ctypes.c_int64), ("gemm_ms", ctypes.c_double),
                 ("gemm_flops_timed", ctypes.c_double), ("emu_slices", ctypes.c_int),
-                ("gemms_timed_by_precision", ctypes.c_int64 * 4), ("gemm_ms_by_precision", ctypes.c_double * 4),
-                ("gemm_flops_by_precision", ctypes.c_double * 4), ("c0_gate", ctypes.c_double),
+                ("gemms_timed_by_precision", ctypes.c_int64 * PR_NPREC),
+                ("gemm_ms_by_precision", ctypes.c_double * PR_NPREC),
+                ("gemm_flops_by_precision", ctypes.c_double * PR_NPREC), ("c0_gate", ctypes.c_double),
                 ("true_residual", ctypes.c_double), ("prescale_log2", ctypes.c_int)]
 
     def as_dict(self) -> dict:
@@ -58,9 +61,10 @@ class pr_state_header(ctypes.Structure):
                 ("p", ctypes.c_int32), ("form", ctypes.c_int32), ("c0", ctypes.c_int32),
                 ("norm_1", ctypes.c_double), ("norm_inf", ctypes.c_double), ("state_ready", ctypes.c_int32),
                 ("state_level", ctypes.c_int32), ("lp_stale", ctypes.c_int32), ("iterations", ctypes.c_int32),
-                ("iterations_by_precision", ctypes.c_int32 * 4), ("switch_iteration", ctypes.c_int32),
+                ("iterations_by_precision", ctypes.c_int32 * PR_NPREC), ("switch_iteration", ctypes.c_int32),
                 ("last_precision", ctypes.c_int32), ("hist_len", ctypes.c_int32), ("n_mats", ctypes.c_int32),
-                ("ldl", ctypes.c_int32), ("reserved", ctypes.c_int32), ("last_residual", ctypes.c_double)]
+                ("ldl", ctypes.c_int32), ("reserved", ctypes.c_int32), ("reserved2", ctypes.c_int32),
+                ("last_residual", ctypes.c_double)]
 
 
 class pr_batch_matrix_t(ctypes.Structure):
@@ -101,6 +105,8 @@ def _load() -> ctypes.CDLL:
                                       ctypes.POINTER(ctypes.c_int)]),
         "pr_solve": (ctypes.c_int, [_handle_t, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                     ctypes.POINTER(ctypes.c_int)]),
+        "pr_solve_ladder": (ctypes.c_int, [_handle_t, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.POINTER(ctypes.c_int)]),
         "pr_residual": (ctypes.c_int, [_handle_t, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
         "pr_result": (ctypes.c_int, [_handle_t, _dptr]),
         "pr_stop_rule": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), ctypes.c_int,
@@ -121,6 +127,8 @@ def _load() -> ctypes.CDLL:
         "pr_batch_last_error": (ctypes.c_char_p, [_handle_t]),
         "pr_batch_destroy": (ctypes.c_int, [_handle_t]),
         "pr_features": (ctypes.c_int, [_handle_t, ctypes.POINTER(ctypes.c_double)]),
+        "pr_spectral_bounds": (ctypes.c_int, [_handle_t, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_double)]),
         "pr_set_initial_guess": (ctypes.c_int, [_handle_t, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
         "pr_mlp_create": (ctypes.c_int, [ctypes.POINTER(_handle_t), _dptr, ctypes.c_int, ctypes.c_void_p]),
         "pr_mlp_forward": (ctypes.c_int, [_handle_t, _dptr, ctypes.c_int, _dptr]),
@@ -223,6 +231,17 @@ def pr_solve(h: int, bulk_precision: int, bulk_steps: int, final_precision: int,
     return st, d.value
 
 
+def pr_solve_ladder(h: int, precisions, max_steps, tol: float) -> tuple[int, int]:
+    """precisions: the rungs in order; max_steps: per-rung update limits (None: none). Returns (status, steps)."""
+    k = len(precisions)
+    pr_ = (ctypes.c_int * k)(*[int(x) for x in precisions])
+    ms = None if max_steps is None else (ctypes.c_int * k)(*[int(x) for x in max_steps])
+    d = ctypes.c_int(0)
+    st = _lib.pr_solve_ladder(h, k, pr_, ms, float(tol), ctypes.byref(d))
+    _check(st, h, STOPS)
+    return st, d.value
+
+
 def pr_residual(h: int, precision: int = PR_FP64) -> float:
     r = ctypes.c_double(0.0)
     _check(_lib.pr_residual(h, int(precision), ctypes.byref(r)), h)
@@ -244,6 +263,13 @@ def pr_features(h: int) -> list[float]:
     out = (ctypes.c_double * 8)()
     _check(_lib.pr_features(h, out), h)
     return list(out)
+
+
+def pr_spectral_bounds(h: int, iters: int = 60) -> tuple[float, float]:
+    """(lambda_min estimate from the current iterate, lambda_max estimate) of the loaded A."""
+    lo, hi = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(_lib.pr_spectral_bounds(h, int(iters), ctypes.byref(lo), ctypes.byref(hi)), h)
+    return lo.value, hi.value
 
 
 def pr_set_initial_guess(h: int, kind: int, coef=None) -> None:

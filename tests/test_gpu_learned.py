@@ -237,3 +237,19 @@ def test_gate_without_fallback_reports_egate():
     Z = O.closed_form_root(c.Q, c.lam, 2)
     Co, _ = O.solve(c.A, 2, tol=1e-12)
     assert O.forward_error(C.cpu().numpy(), Z) <= max(1e-12, 10 * O.forward_error(Co, Z))
+
+
+def test_spectral_bounds_from_the_device():
+    # pr_spectral_bounds: power iterations on A (||A||_2 = lambda_max = 1 for this recipe) and on the
+    # converged root (||C||_2^(-p) = lambda_min), both from below / above as power iteration gives them; a
+    # scaled A (p > 1, ||A||_1 < 1, iterated as 2^k A) reports the caller's eigenvalues.
+    c = W.spd_from_spectrum(200, 1e-2, 41)
+    for scale, p in ((1.0, 2), (0.01, 2), (1.0, 1)):
+        h = handle(scale * c.A, p)
+        try:
+            P.pr_iterate(h, 100, P.PR_EMU64, 1e-12)
+            lo, hi = P.pr_spectral_bounds(h, 80)
+        finally:
+            P.pr_destroy(h)
+        assert 0.95 * scale <= hi <= scale * (1 + 1e-12), (scale, p, hi)
+        assert scale * 1e-2 * (1 - 1e-9) <= lo <= 1.05 * scale * 1e-2, (scale, p, lo)
