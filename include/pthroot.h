@@ -128,6 +128,14 @@ typedef struct {
   int gate_fallback;   /* PR_C0_POLY guess failing its gate: 1 (default) use Eq. 3 instead; 0 return PR_EGATE
                           (pr_init then creates no handle; pr_load and pr_set_initial_guess leave Eq. 3's
                           C_0 in the handle)                                                              */
+  int emu_tile;        /* digit-slice products (PR_EMU64, PR_FP32X): output tile width. 0 (default) tunes:
+                          the first product of each kind (symmetric / full, per precision) times every work-list
+                          variant of this order (tiles 128 x 96 or 128 x 48, whole or split over K into two
+                          halves when the tiles fill fewer than 4 waves of the SMs) and keeps the fastest; the
+                          choice is remembered for the process per (order, kind, digit planes). 96 or 48 fix
+                          the width (tiles split by the wave rule). Products are exact integer sums rounded
+                          once, the same for every variant; residuals, which add per-tile partial sums, differ
+                          in their last bits between widths                                             */
 } pr_options;
 
 /* Counters of one handle. */
@@ -161,6 +169,9 @@ typedef struct {
                                value of the coupled form (pr_options.verify), the tested residual of the
                                Newton-Schulz and literal forms; -1 before the first stop                  */
   int prescale_log2;        /* k: the handle iterates on 2^k A (see pr_load), 0 when A is taken as given   */
+  int emu_tile_n[2];        /* PR_EMU64 products, symmetric [0] and full [1]: tile width in use (0: none yet) */
+  int emu_tile_split[2];    /* ... and whether their tiles are split over K                               */
+  double emu_tune_ms;       /* time the tuner of pr_options.emu_tile spent on trial launches in this handle */
 } pr_stats_t;
 
 /* Fills *opt with the defaults listed above. */
@@ -268,6 +279,14 @@ pr_status pr_matmul(int precision, const double* X, const double* Y, int64_t n, 
  * testing every slice count the options allow (pr_options.emu_slices). Errors: as pr_matmul, and
  * PR_EINVAL for slices outside [1, 8]. */
 pr_status pr_matmul_emu(int slices, const double* X, const double* Y, int64_t n, int sym, double* P, void* stream);
+
+/* pr_matmul_emu with a chosen work-list variant of the digit-slice kernel (the variants pr_options.emu_tile
+ * tunes between): tile_n = 96 or 48 output columns per 128-row tile; split = 1 splits every tile over K into
+ * two halves run by different CTAs (orders above 16), 0 never, -1 when the tiles fill fewer of the SMs'
+ * waves than the halves would. Every variant gives the same product (exact digit-pair sums, rounded once).
+ * Errors: as pr_matmul_emu, and PR_EINVAL for another tile_n or split. */
+pr_status pr_matmul_emu_tiled(int slices, int tile_n, int split, const double* X, const double* Y, int64_t n, int sym,
+                              double* P, void* stream);
 
 /* ---- Checkpoint and resume ----------------------------------------------------------------------------
  * The state of an iteration as one host byte buffer: the iterate X and, for the coupled form with its
@@ -398,6 +417,10 @@ typedef struct {
   double stage_ms;           /* summed time of the timed launches: first CTA start to last CTA end */
   double stage_flops_timed;  /* FP64-equivalent algorithmic flops of the timed launches */
   int emu_slices;            /* digit planes per operand */
+  int tile_n;                /* output columns per tile of the batch's products: pr_options.emu_tile, or the
+                                width the tuner at pr_batch_init found faster on the symmetric product A A of
+                                every matrix (one launch per width, best of two)                            */
+  double tune_ms;            /* time of those trial launches                                               */
 } pr_batch_stats_t;
 
 /* Fills *out. Errors: PR_ESTATE (b NULL), PR_EINVAL (out NULL). */

@@ -61,7 +61,7 @@ __all__ = [
     "sym_product", "power_times", "residual_fro", "step_literal", "step_newton_schulz",
     "coupled_start", "step_coupled", "solve", "SolveInfo", "closed_form_root", "eig_root",
     "scalar_recurrence", "scalar_residuals", "forward_error", "default_form", "closed_form_block",
-    "residual_rows", "eq2_prescale",
+    "residual_rows", "eq2_prescale", "round_mantissa", "matmul_rounded", "quantized_iterates",
 ]
 
 
@@ -332,6 +332,54 @@ def scalar_residuals(lam: np.ndarray, c0: np.ndarray, p: int, k_max: int) -> np.
 def forward_error(C: np.ndarray, Z: np.ndarray) -> float:
     """||C - Z||_F / ||Z||_F, the Frobenius error of Sec. 4.3 made relative."""
     return float(np.linalg.norm(C - Z) / np.linalg.norm(Z))
+
+
+# ---------------------------------------------------------------- custom-precision simulation (Sec. 4.2, 4.3)
+#
+# The paper's experiment: the iteration with floating-point numbers of m stored mantissa bits, either for all
+# involved calculations ("arithmetic") or only for the input and the stored intermediate results ("storage",
+# approximate storage or data exchange), against the exact root (Fig. 2). Readings: the exponent range stays
+# that of FP64 (only the mantissa is shortened); rounding is to nearest, ties to even; an operation in the
+# custom type is the FP64 operation followed by that rounding; a product of matrices sums its terms in the
+# order k = 0, 1, ..., n - 1, rounding every product and every partial sum; the iteration is Eq. 1 as printed
+# (C^{p+1} A right to left, the new iterate symmetrised), from Eq. 3's C_0 computed in FP64 from the rounded
+# input and then rounded; storage keeps A and each iterate rounded and computes in FP64.
+
+def round_mantissa(x, m: int):
+    """x rounded to m stored mantissa bits (m + 1 significant bits), ties to even: x = f 2^e with
+    0.5 <= |f| < 1 becomes rint(f 2^(m+1)) 2^(e - m - 1)."""
+    f, e = np.frexp(np.asarray(x, dtype=np.float64))
+    return np.ldexp(np.rint(np.ldexp(f, m + 1)), e - m - 1)
+
+
+def matmul_rounded(X: np.ndarray, Y: np.ndarray, m: int) -> np.ndarray:
+    """X Y in the m-bit arithmetic: P_ij = (((x_i0 y_0j) + x_i1 y_1j) + ...), every product and every partial
+    sum rounded to m bits."""
+    P = np.zeros((X.shape[0], Y.shape[1]))
+    for k in range(X.shape[1]):
+        P = round_mantissa(P + round_mantissa(np.outer(X[:, k], Y[k, :]), m), m)
+    return P
+
+
+def quantized_iterates(A: np.ndarray, p: int, m: int, mode: str, iterations: int):
+    """The literal iteration of Eq. 1 in the custom precision (mode "storage" or "arithmetic"); returns the
+    iterates C_0 .. C_iterations. Arithmetic: every product term and sum (matmul_rounded), and the update
+    ((p + 1) C - C^{p+1} A) / p and the symmetrisation (Y + Y^T) / 2 one rounded operation at a time."""
+    rnd = lambda Y: round_mantissa(Y, m)  # noqa: E731
+    Aq = rnd(A)
+    C = rnd(initial_guess_eq3(Aq))
+    out = [C]
+    for _ in range(iterations):
+        T = Aq
+        for _ in range(p + 1):
+            T = C @ T if mode == "storage" else matmul_rounded(C, T, m)
+        if mode == "storage":
+            C = rnd(symmetrize(((p + 1) * C - T) / p))
+        else:
+            W = rnd(rnd(rnd((p + 1) * C) - T) / p)
+            C = rnd(W + W.T) * 0.5
+        out.append(C)
+    return out
 
 
 # ---------------------------------------------------------------- learned polynomial initial guess

@@ -7,7 +7,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -71,12 +74,15 @@ struct pr_handle_s {
   int ldq = 0;  // leading dimension (bytes) of the E4M3 copies
   int eld = 0;  // K extent of a PR_EMU64 digit-plane row (n rounded up to 16)
   int S = 8;    // digit planes per operand for PR_EMU64
-  int4* emu_items[2] = {nullptr, nullptr};  // PR_EMU64 work lists: symmetric, full products
-  int emu_nitems[2] = {0, 0};
+  // PR_EMU64 / PR_FP32X work lists per product mode (symmetric, full) and variant (kEmuVariants: tile width
+  // 96 or 48, whole tiles or tiles split over K); a variant that does not apply has no list.
+  int4* emu_items[2][4] = {};
+  int emu_nitems[2][4] = {};
+  int emu_nsplit[2][4] = {};                 // split tiles of each list (0: whole tiles)
+  int emu_plan[2][2] = {{-1, -1}, {-1, -1}}; // [mode][0: PR_EMU64, 1: PR_FP32X] chosen variant, -1 not yet
   long long* emu_scratch = nullptr;          // PR_EMU64 first-pass totals (pr::emu_scratch_bytes())
   long long* emu_split = nullptr;            // PR_EMU64 half totals of tiles split over K (pr::emu_launch_list)
   int* emu_split_cnt = nullptr;
-  int emu_nsplit[2] = {0, 0};                // split tiles of the symmetric and the full work list
 
   // The input, the iterate X, the carried product M and operand N of the coupled form, their next
   // values, and two scratch products.
@@ -166,6 +172,21 @@ pr_status sync(pr_handle h) {
   return PR_OK;
 }
 
+// The work-list variants of the digit-slice products: tile width (output columns per tile) and whether every
+// tile is split over K into two halves run by neighbouring CTAs.
+struct EmuVariant {
+  int bn, split;
+};
+constexpr EmuVariant kEmuVariants[4] = {{96, 0}, {96, 1}, {48, 0}, {48, 1}};
+
+// Process-wide record of the variant the tuner chose per (order, mode, digit planes), so that later handles of
+// the same order (and repeated pr_load) do not tune again.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int>& tune_cache() {
+  static std::map<std::tuple<int, int, int>, int> cache;
+  return cache;
+}
+
 // The rungs below FP64 accuracy: their own stagnation threshold (stag_below_lowp), a stop at the first
 // residual that does not fall, and the roll-back of that last step.
 bool lowp(int prec) { return prec == PR_BF16 || prec == PR_FP8 || prec == PR_FP32X; }
@@ -197,6 +218,66 @@ pr_status ensure_slices(pr_handle h, Mat& m) {
   PR_CK(h, pr::slice(m.f, n, h->eld, h->S, m.sl, m.ex, h->stream));
   h->st.launches += 1;
   m.sl_valid = true;
+  return PR_OK;
+}
+
+// The work-list variant of the digit-slice products of mode m (0 symmetric, 1 full) at precision class pc
+// (0 PR_EMU64, 1 PR_FP32X): fixed by pr_options.emu_tile (96 or 48, tiles split by the wave rule), taken from
+// the process-wide record, or tuned: every applicable variant runs the product about to be computed twice
+// (its results are exact integer totals rounded once, the same for every variant; the last run, with the
+// chosen variant, writes the residual partials), timed with CUDA events, and the fastest is kept.
+template <class Launch>
+pr_status choose_emu_variant(pr_handle h, int m, int pc, int S, Launch&& launch) {
+  const int n = (int)h->n;
+  const Mode mode = m == 0 ? Mode::Sym : Mode::Full;
+  if (h->opt.emu_tile != 0) {
+    const int base = h->opt.emu_tile == 96 ? 0 : 2;
+    h->emu_plan[m][pc] = base + (pr::emu_split_slots(n, mode, kEmuVariants[base].bn, -1) > 0 ? 1 : 0);
+  } else {
+    const auto key = std::make_tuple(n, m, S);
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      auto it = tune_cache().find(key);
+      if (it != tune_cache().end()) h->emu_plan[m][pc] = it->second;
+    }
+    if (h->emu_plan[m][pc] < 0) {
+      cudaEvent_t e0, e1;
+      PR_CK(h, cudaEventCreate(&e0));
+      PR_CK(h, cudaEventCreate(&e1));
+      float best = 1e30f;
+      int pick = 0;
+      for (int v = 0; v < 4; ++v) {
+        if (!h->emu_items[m][v]) continue;
+        float t = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+          PR_CK(h, cudaEventRecord(e0, h->stream));
+          PR_CK(h, launch(v));
+          PR_CK(h, cudaEventRecord(e1, h->stream));
+          PR_CK(h, cudaEventSynchronize(e1));
+          float ms = 0.f;
+          PR_CK(h, cudaEventElapsedTime(&ms, e0, e1));
+          t = std::min(t, ms);
+          h->st.launches += 1;
+        }
+        h->st.emu_tune_ms += t * 2;
+        if (t < best) {
+          best = t;
+          pick = v;
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      pr_status s = sync(h);  // a bounded wait that expired during a trial shows here
+      if (s != PR_OK) return s;
+      h->emu_plan[m][pc] = pick;
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      tune_cache()[key] = pick;
+    }
+  }
+  if (pc == 0) {
+    h->st.emu_tile_n[m] = kEmuVariants[h->emu_plan[m][pc]].bn;
+    h->st.emu_tile_split[m] = kEmuVariants[h->emu_plan[m][pc]].split;
+  }
   return PR_OK;
 }
 
@@ -262,14 +343,22 @@ pr_status product(pr_handle h, int prec, Mat& X, Mat& Y, Mode mode, const Out& o
       PR_CK(h, pr::gemm_bf16_tc(X.b, Y.b, n, h->ldl, mode, o.transpose, e, h->err_word(), h->stream));
       break;
     case PR_EMU64:
-    case PR_FP32X:
-      PR_CK(h, pr::gemm_emu(X.sl, X.ex, Y.sl, Y.ex, n, h->eld, prec == PR_FP32X ? std::min(h->S, kFp32xSlices) : h->S,
-                            mode, o.transpose, h->emu_items[mode == Mode::Sym ? 0 : 1],
-                            h->emu_nitems[mode == Mode::Sym ? 0 : 1], e, h->emu_scratch,
-                            h->emu_nsplit[mode == Mode::Sym ? 0 : 1] ? h->emu_split : nullptr, h->emu_split_cnt,
-                            h->err_word(), h->stream));
+    case PR_FP32X: {
+      const int m = mode == Mode::Sym ? 0 : 1, pc = prec == PR_FP32X ? 1 : 0;
+      const int S = prec == PR_FP32X ? std::min(h->S, kFp32xSlices) : h->S;
+      auto launch = [&](int v) {
+        return pr::gemm_emu(X.sl, X.ex, Y.sl, Y.ex, n, h->eld, S, mode, o.transpose, h->emu_items[m][v],
+                            h->emu_nitems[m][v], e, h->emu_scratch, h->emu_nsplit[m][v] ? h->emu_split : nullptr,
+                            h->emu_split_cnt, h->err_word(), h->stream, kEmuVariants[v].bn);
+      };
+      if (h->emu_plan[m][pc] < 0) {
+        pr_status ps = choose_emu_variant(h, m, pc, S, launch);
+        if (ps != PR_OK) return ps;
+      }
+      PR_CK(h, launch(h->emu_plan[m][pc]));
       h->lp_stale = true;
       break;
+    }
     case PR_FP8:
       PR_CK(h, pr::gemm_fp8_tc(X.q, X.qe, Y.q, Y.qe, n, h->ldq, mode, o.transpose, e, h->err_word(), h->stream));
       h->lp_stale = true;
@@ -290,7 +379,10 @@ pr_status product(pr_handle h, int prec, Mat& X, Mat& Y, Mode mode, const Out& o
 }
 
 int tiles_for(pr_handle h, int prec, Mode mode) {
-  if (prec == PR_EMU64 || prec == PR_FP32X) return pr::emu_tiles((int)h->n, mode);
+  if (prec == PR_EMU64 || prec == PR_FP32X) {
+    const int v = h->emu_plan[mode == Mode::Sym ? 0 : 1][prec == PR_FP32X ? 1 : 0];
+    return pr::emu_tiles((int)h->n, mode, kEmuVariants[v < 0 ? 0 : v].bn);
+  }
   return lowp(prec) ? pr::gemm_tc_tiles((int)h->n, mode) : pr::gemm_f64_tiles((int)h->n, mode);
 }
 
@@ -718,7 +810,7 @@ void set_handleless_error(const char* msg) { g_init_error = msg; }
 namespace {
 
 pr_status matmul(int precision, int S, const double* X, const double* Y, int64_t n, int sym, double* P,
-                 void* stream) {
+                 void* stream, int bn = 96, int split_mode = -1) {
   if (!X || !Y || !P) return fail(nullptr, PR_EINVAL, "pr_matmul: NULL matrix");
   if (n < 1 || n > (int64_t)1 << 17) return fail(nullptr, PR_EINVAL, "pr_matmul: n must be in [1, 131072]");
   if (!precision_known(precision)) return fail(nullptr, PR_EINVAL, "pr_matmul: unknown precision");
@@ -773,8 +865,8 @@ pr_status matmul(int precision, int S, const double* X, const double* Y, int64_t
       step(pr::gemm_fp8_tc(qX, eX, qY, eY, ni, ldq, mode, false, ep, err, s));
     } else {
       __half *hX = reinterpret_cast<__half*>(bX), *hY = reinterpret_cast<__half*>(bY);
-      pr::emu_launch_list(ni, mode, hitems);
-      const int slots = pr::emu_split_slots(ni, mode);
+      pr::emu_launch_list(ni, mode, hitems, bn, split_mode);
+      const int slots = pr::emu_split_slots(ni, mode, bn, split_mode);
       step(cudaMalloc((void**)&items, hitems.size() * sizeof(int4)));
       step(cudaMalloc((void**)&scratch, pr::emu_scratch_bytes()));
       if (slots > 0) {
@@ -786,7 +878,7 @@ pr_status matmul(int precision, int S, const double* X, const double* Y, int64_t
       step(pr::slice(dX, ni, eld, S, hX, eX, s));
       step(pr::slice(dY, ni, eld, S, hY, eY, s));
       step(pr::gemm_emu(hX, eX, hY, eY, ni, eld, precision == PR_FP32X ? std::min(S, kFp32xSlices) : S, mode, false,
-                        items, (int)hitems.size(), ep, scratch, split, split_cnt, err, s));
+                        items, (int)hitems.size(), ep, scratch, split, split_cnt, err, s, bn));
     }
     step(cudaMemcpyAsync(P, dP, bytes, cudaMemcpyDefault, s));
     step(cudaMemcpyAsync(&word, err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -825,6 +917,7 @@ void pr_default_options(pr_options* o) {
   o->gate_iters = 30;
   o->verify = 1;
   o->gate_fallback = 1;
+  o->emu_tile = 0;
 }
 
 const char* pr_last_error(pr_handle h) { return h ? h->err.c_str() : g_init_error.c_str(); }
@@ -843,8 +936,9 @@ pr_status pr_destroy(pr_handle h) {
   }
   for (double* b : {h->partial, h->work, h->scal, h->vec})
     if (b) cudaFree(b);
-  for (int4* it : h->emu_items)
-    if (it) cudaFree(it);
+  for (auto& lists : h->emu_items)
+    for (int4* it : lists)
+      if (it) cudaFree(it);
   if (h->emu_scratch) cudaFree(h->emu_scratch);
   if (h->emu_split) cudaFree(h->emu_split);
   if (h->emu_split_cnt) cudaFree(h->emu_split_cnt);
@@ -870,7 +964,7 @@ pr_status pr_init(pr_handle* out, const double* A, int64_t n, int p, const pr_op
     return fail(nullptr, PR_EINVAL, "pr_init: bad gate options");
   if (o.form == PR_FORM_NS && p != 1) return fail(nullptr, PR_EINVAL, "pr_init: the Newton-Schulz form needs p = 1");
   if (o.max_iter < 0 || !(o.stag_ratio > 0) || !(o.sym_tol >= 0) || !(o.stag_below_lowp >= 0) ||
-      o.emu_slices < 0 || o.emu_slices > pr::emu_max_slices())
+      o.emu_slices < 0 || o.emu_slices > pr::emu_max_slices() || (o.emu_tile != 0 && !pr::emu_tile_width_ok(o.emu_tile)))
     return fail(nullptr, PR_EINVAL, "pr_init: bad option value");
 
   pr_handle h = new pr_handle_s();
@@ -913,7 +1007,7 @@ pr_status pr_init(pr_handle* out, const double* A, int64_t n, int p, const pr_op
   const int T64 = (int)((n + 63) / 64);
   size_t nparts = (size_t)T64 * T64;
   const size_t tc_parts = (size_t)pr::gemm_tc_tiles((int)n, Mode::Full);
-  const size_t emu_parts = (size_t)pr::emu_tiles((int)n, Mode::Full);
+  const size_t emu_parts = (size_t)pr::emu_tiles((int)n, Mode::Full, 48);  // the narrower tile has more
   if (tc_parts > nparts) nparts = tc_parts;
   if (emu_parts > nparts) nparts = emu_parts;
   PR_INIT_CK(cudaMalloc((void**)&h->partial, sizeof(double) * nparts));
@@ -921,15 +1015,26 @@ pr_status pr_init(pr_handle* out, const double* A, int64_t n, int p, const pr_op
   PR_INIT_CK(cudaMalloc((void**)&h->scal, sizeof(double) * 8));
   PR_INIT_CK(cudaMemset(h->scal, 0, sizeof(double) * 8));
   PR_INIT_CK(cudaMallocHost((void**)&h->hpin, sizeof(double) * 8));
+  // The digit-slice products' work lists of this order (symmetric, full) for every variant that applies:
+  // whole tiles always; tiles split over K only for short launches (fewer than 4 waves of tiles) with at
+  // least two K steps, and only for the width chosen by emu_tile if it is fixed.
   int slots = 0;
-  for (int k = 0; k < 2; ++k) {  // the PR_EMU64 work lists of this order (symmetric, full)
-    std::vector<int4> items;
-    pr::emu_launch_list((int)n, k == 0 ? Mode::Sym : Mode::Full, items);
-    h->emu_nsplit[k] = pr::emu_split_slots((int)n, k == 0 ? Mode::Sym : Mode::Full);
-    slots = std::max(slots, h->emu_nsplit[k]);
-    h->emu_nitems[k] = (int)items.size();
-    PR_INIT_CK(cudaMalloc((void**)&h->emu_items[k], items.size() * sizeof(int4)));
-    PR_INIT_CK(cudaMemcpy(h->emu_items[k], items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  for (int k = 0; k < 2; ++k) {
+    const Mode mode = k == 0 ? Mode::Sym : Mode::Full;
+    for (int v = 0; v < 4; ++v) {
+      const EmuVariant var = kEmuVariants[v];
+      if (o.emu_tile != 0 && var.bn != o.emu_tile) continue;
+      if (var.split && !(o.emu_tile == 0 ? pr::emu_split_useful((int)n, mode, var.bn)
+                                         : pr::emu_split_slots((int)n, mode, var.bn, -1) > 0))
+        continue;
+      std::vector<int4> items;
+      pr::emu_launch_list((int)n, mode, items, var.bn, var.split);
+      h->emu_nsplit[k][v] = pr::emu_split_slots((int)n, mode, var.bn, var.split);
+      slots = std::max(slots, h->emu_nsplit[k][v]);
+      h->emu_nitems[k][v] = (int)items.size();
+      PR_INIT_CK(cudaMalloc((void**)&h->emu_items[k][v], items.size() * sizeof(int4)));
+      PR_INIT_CK(cudaMemcpy(h->emu_items[k][v], items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    }
   }
   PR_INIT_CK(cudaMalloc((void**)&h->emu_scratch, pr::emu_scratch_bytes()));
   if (slots > 0) {
@@ -1310,6 +1415,15 @@ pr_status pr_matmul_emu(int slices, const double* X, const double* Y, int64_t n,
   if (slices < 1 || slices > pr::emu_max_slices())
     return fail(nullptr, PR_EINVAL, "pr_matmul_emu: slices must be in [1, 8]");
   return matmul(PR_EMU64, slices, X, Y, n, sym, P, stream);
+}
+
+pr_status pr_matmul_emu_tiled(int slices, int tile_n, int split, const double* X, const double* Y, int64_t n, int sym,
+                              double* P, void* stream) {
+  if (slices < 1 || slices > pr::emu_max_slices())
+    return fail(nullptr, PR_EINVAL, "pr_matmul_emu_tiled: slices must be in [1, 8]");
+  if (!pr::emu_tile_width_ok(tile_n) || split < -1 || split > 1)
+    return fail(nullptr, PR_EINVAL, "pr_matmul_emu_tiled: tile_n must be 96 or 48 and split -1, 0 or 1");
+  return matmul(PR_EMU64, slices, X, Y, n, sym, P, stream, tile_n, split);
 }
 
 pr_status pr_matmul(int precision, const double* X, const double* Y, int64_t n, int sym, double* P, void* stream) {

@@ -55,6 +55,8 @@ struct pr_batch_s {
   int pmax = 0;  // largest root of a coupled-form matrix
   bool has_p3 = false;  // some matrix has p = 3 (its update takes two products, update_p3)
   int hcap = 0;  // history entries per matrix (max_iter + 2)
+  int bn = 96;   // tile width of the digit-slice products (pr_options.emu_tile, or tuned at init)
+  double tune_ms = 0.0;
   cudaStream_t stream = nullptr;
   int device = 0;
   pr_options opt{};
@@ -166,7 +168,7 @@ pr_status stage(pr_batch b, Buf& Xb, Buf& Yb, const BatchStage& sp, const StageO
   e.partial = so.partial ? b->partial : nullptr;
   PB_CK(b, pr::gemm_emu_batched(Xb.sl, Xb.ex, Yb.sl, Yb.ex, b->R, b->K, pr::emu_ld(b->K), b->ld, b->S,
                                 st.full ? Mode::Full : Mode::Sym, so.transpose, b->items, 0, b->ctl.nitems, b->mats, e,
-                                b->scratch, b->err, b->tstamp + 2 * st.slot, b->stream));
+                                b->scratch, b->err, b->tstamp + 2 * st.slot, b->stream, b->bn));
   b->cnt += 2;
   if (so.partial) {
     PB_CK(b, pr::batch_residuals(b->ctl, b->partial, sp.verify, b->stream));
@@ -499,6 +501,66 @@ pr_status load(pr_batch b, const double* const* A, const char* who) {
   return PR_OK;
 }
 
+// The tile width of the batch's products (pr_options.emu_tile = 0): the symmetric product A A of every
+// matrix, as one launch over all their tiles, timed (best of two) with 128 x 96 and with 128 x 48 tiles on
+// the batch's stream; the faster width is kept for every stage. (Small orders waste less of a narrower tile;
+// large ones issue fewer, larger MMAs with the wider one.)
+pr_status tune_batch(pr_batch b) {
+  pr_status s = ensure_slices(b, b->A);
+  if (s != PR_OK) return s;
+  std::vector<EmuBatchMat> mats(b->count);
+  for (int m = 0; m < b->count; ++m) mats[m] = EmuBatchMat{b->n[m], b->row0[m], 0.0, 0.0, 0.0};
+  EmuBatchMat* dmats = nullptr;
+  int4* ditems = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float best = 1e30f;
+  int pick = 96;
+  cudaError_t e = cudaMalloc((void**)&dmats, mats.size() * sizeof(EmuBatchMat));
+  if (e == cudaSuccess) e = cudaMemcpy(dmats, mats.data(), mats.size() * sizeof(EmuBatchMat), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  for (int bn : {96, 48}) {
+    if (e != cudaSuccess) break;
+    std::vector<int4> items;
+    for (int m = 0; m < b->count; ++m) pr::emu_tile_list(m, b->n[m], Mode::Sym, items, bn);
+    if (ditems) cudaFree(ditems);
+    ditems = nullptr;
+    e = cudaMalloc((void**)&ditems, items.size() * sizeof(int4));
+    if (e == cudaSuccess) e = cudaMemcpy(ditems, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    Epilogue ep;
+    ep.out = b->T0.f;
+    float t = 1e30f;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+      e = cudaEventRecord(e0, b->stream);
+      if (e == cudaSuccess)
+        e = pr::gemm_emu_batched(b->A.sl, b->A.ex, b->A.sl, b->A.ex, b->R, b->K, pr::emu_ld(b->K), b->ld, b->S,
+                                 Mode::Sym, false, ditems, (int)items.size(), nullptr, dmats, ep, b->scratch, b->err,
+                                 nullptr, b->stream, bn);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      t = std::min(t, ms);
+      b->launches += 1;
+    }
+    b->tune_ms += 2 * t;
+    if (t < best) {
+      best = t;
+      pick = bn;
+    }
+  }
+  if (ditems) cudaFree(ditems);
+  if (dmats) cudaFree(dmats);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return bfail(b, PR_ECUDA, std::string("pr_batch_init: tile tuning: ") + cudaGetErrorName(e));
+  int word = 0;
+  PB_CK(b, cudaMemcpy(&word, b->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (word != 0) return bfail(b, PR_ETIMEOUT, "pr_batch_init: a bounded device wait expired while tuning");
+  b->bn = pick;
+  return PR_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -538,7 +600,8 @@ pr_status pr_batch_init(pr_batch* out, int count, const int64_t* n, const int* p
   else pr_default_options(&o);
   if (o.form != PR_FORM_AUTO) return bfail(nullptr, PR_EINVAL, "pr_batch_init: batches run the automatic forms");
   if (o.c0 != PR_C0_EQ3 && o.c0 != PR_C0_SCALED_I) return bfail(nullptr, PR_EINVAL, "pr_batch_init: unknown c0");
-  if (o.emu_slices < 0 || o.emu_slices > pr::emu_max_slices() || o.max_iter < 0)
+  if (o.emu_slices < 0 || o.emu_slices > pr::emu_max_slices() || o.max_iter < 0 ||
+      (o.emu_tile != 0 && !pr::emu_tile_width_ok(o.emu_tile)))
     return bfail(nullptr, PR_EINVAL, "pr_batch_init: bad option value");
   int64_t R = 0, K = 0;
   for (int m = 0; m < count; ++m) {
@@ -570,6 +633,7 @@ pr_status pr_batch_init(pr_batch* out, int count, const int64_t* n, const int* p
   b->status.assign(count, -1);
   b->iterations.assign(count, 0);
   b->hcap = o.max_iter + 2;
+  b->bn = o.emu_tile != 0 ? o.emu_tile : 96;
   int row = 0;
   for (int m = 0; m < count; ++m) {
     b->n[m] = (int)n[m];
@@ -607,34 +671,12 @@ pr_status pr_batch_init(pr_batch* out, int count, const int64_t* n, const int* p
   PB_INIT_CK(cudaMalloc((void**)&b->row_v, (size_t)b->R * sizeof(int)));
   PB_INIT_CK(cudaMalloc((void**)&b->truer, (size_t)count * sizeof(double)));
   b->slice_rows = b->row_n;
-  // Every matrix's work items (symmetric and full) and the device-side control state.
-  std::vector<int4> isym, ifull;
-  std::vector<int> stat(9 * (size_t)count);
-  int* s_order = stat.data();
-  std::iota(s_order, s_order + count, 0);
-  std::stable_sort(s_order, s_order + count, [&](int x, int y) { return b->n[x] > b->n[y]; });
-  for (int m = 0; m < count; ++m) {
-    stat[count + m] = b->n[m];
-    stat[2 * count + m] = b->p[m];
-    stat[3 * count + m] = b->form[m];
-    stat[4 * count + m] = b->row0[m];
-    stat[5 * count + m] = (int)isym.size();
-    pr::emu_tile_list(m, b->n[m], Mode::Sym, isym);
-    stat[6 * count + m] = (int)isym.size() - stat[5 * count + m];
-    stat[7 * count + m] = (int)ifull.size();
-    pr::emu_tile_list(m, b->n[m], Mode::Full, ifull);
-    stat[8 * count + m] = (int)ifull.size() - stat[7 * count + m];
-  }
-  const size_t items = ifull.size();  // no stage has more items than every matrix's full product
+  // Device-side control state (independent of the tile width) and the loading work areas.
   const size_t hist_len = (size_t)count * b->hcap;
-  PB_INIT_CK(cudaMalloc((void**)&b->items, items * sizeof(int4)));
-  PB_INIT_CK(cudaMalloc((void**)&b->partial, items * pr::emu_partials_per_item() * sizeof(double)));
   PB_INIT_CK(cudaMalloc((void**)&b->mats, (size_t)count * sizeof(EmuBatchMat)));
   PB_INIT_CK(cudaMalloc((void**)&b->err, sizeof(int)));
   PB_INIT_CK(cudaMalloc((void**)&b->scratch, pr::emu_scratch_bytes()));
   PB_INIT_CK(cudaMemsetAsync(b->err, 0, sizeof(int), b->stream));
-  PB_INIT_CK(cudaMalloc((void**)&b->d_static, stat.size() * sizeof(int)));
-  PB_INIT_CK(cudaMalloc((void**)&b->d_items_all, (isym.size() + ifull.size()) * sizeof(int4)));
   PB_INIT_CK(cudaMalloc((void**)&b->d_state, (4 * (size_t)count + 1) * sizeof(int)));
   PB_INIT_CK(cudaMalloc((void**)&b->d_dstate, (hist_len + 16) * sizeof(double)));
   PB_INIT_CK(cudaMalloc((void**)&b->d_stage, (1 + 4 * (size_t)count) * sizeof(int)));
@@ -651,15 +693,46 @@ pr_status pr_batch_init(pr_batch* out, int count, const int64_t* n, const int* p
       ts[2 * k] = ULLONG_MAX;
       ts[2 * k + 1] = 0ull;
     }
-    PB_INIT_CK(cudaMemcpy(b->d_static, stat.data(), stat.size() * sizeof(int), cudaMemcpyHostToDevice));
-    PB_INIT_CK(cudaMemcpy(b->d_items_all, isym.data(), isym.size() * sizeof(int4), cudaMemcpyHostToDevice));
-    PB_INIT_CK(cudaMemcpy(b->d_items_all + isym.size(), ifull.data(), ifull.size() * sizeof(int4),
-                          cudaMemcpyHostToDevice));
     PB_INIT_CK(cudaMemcpy(b->d_state, st0.data(), st0.size() * sizeof(int), cudaMemcpyHostToDevice));
     PB_INIT_CK(cudaMemset(b->d_dstate, 0, (hist_len + 16) * sizeof(double)));
     PB_INIT_CK(cudaMemcpy(b->tstamp, ts.data(), ts.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice));
     PB_INIT_CK(cudaMemset(b->flops_pending, 0, kMaxSlots * sizeof(double)));
   }
+  PB_INIT_CK(cudaMalloc((void**)&b->tA, (size_t)K * K * sizeof(double)));
+  PB_INIT_CK(cudaMalloc((void**)&b->tC, (size_t)K * K * sizeof(double)));
+  PB_INIT_CK(cudaMalloc((void**)&b->scal, 8 * (size_t)count * sizeof(double)));
+  PB_INIT_CK(cudaMalloc((void**)&b->work, 2 * (size_t)K * sizeof(double)));
+  PB_INIT_CK(cudaMallocHost((void**)&b->hs, 8 * (size_t)count * sizeof(double)));
+  pr_status st = load(b, A, "pr_batch_init");
+  if (st == PR_OK && o.emu_tile == 0) st = tune_batch(b);
+  if (st != PR_OK) return bail(st);
+  // Every matrix's work items (symmetric and full) for the tile width in use, and the static description.
+  std::vector<int4> isym, ifull;
+  std::vector<int> stat(9 * (size_t)count);
+  int* s_order = stat.data();
+  std::iota(s_order, s_order + count, 0);
+  std::stable_sort(s_order, s_order + count, [&](int x, int y) { return b->n[x] > b->n[y]; });
+  for (int m = 0; m < count; ++m) {
+    stat[count + m] = b->n[m];
+    stat[2 * count + m] = b->p[m];
+    stat[3 * count + m] = b->form[m];
+    stat[4 * count + m] = b->row0[m];
+    stat[5 * count + m] = (int)isym.size();
+    pr::emu_tile_list(m, b->n[m], Mode::Sym, isym, b->bn);
+    stat[6 * count + m] = (int)isym.size() - stat[5 * count + m];
+    stat[7 * count + m] = (int)ifull.size();
+    pr::emu_tile_list(m, b->n[m], Mode::Full, ifull, b->bn);
+    stat[8 * count + m] = (int)ifull.size() - stat[7 * count + m];
+  }
+  const size_t items = ifull.size();  // no stage has more items than every matrix's full product
+  PB_INIT_CK(cudaMalloc((void**)&b->items, items * sizeof(int4)));
+  PB_INIT_CK(cudaMalloc((void**)&b->partial, items * pr::emu_partials_per_item() * sizeof(double)));
+  PB_INIT_CK(cudaMalloc((void**)&b->d_static, stat.size() * sizeof(int)));
+  PB_INIT_CK(cudaMalloc((void**)&b->d_items_all, (isym.size() + ifull.size()) * sizeof(int4)));
+  PB_INIT_CK(cudaMemcpy(b->d_static, stat.data(), stat.size() * sizeof(int), cudaMemcpyHostToDevice));
+  PB_INIT_CK(cudaMemcpy(b->d_items_all, isym.data(), isym.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  PB_INIT_CK(cudaMemcpy(b->d_items_all + isym.size(), ifull.data(), ifull.size() * sizeof(int4),
+                        cudaMemcpyHostToDevice));
   {
     BatchCtl& c = b->ctl;
     const int* d = b->d_static;
@@ -702,14 +775,7 @@ pr_status pr_batch_init(pr_batch* out, int count, const int64_t* n, const int* p
     c.truer = b->truer;
     c.row_v = b->row_v;
   }
-  PB_INIT_CK(cudaMalloc((void**)&b->tA, (size_t)K * K * sizeof(double)));
-  PB_INIT_CK(cudaMalloc((void**)&b->tC, (size_t)K * K * sizeof(double)));
-  PB_INIT_CK(cudaMalloc((void**)&b->scal, 8 * (size_t)count * sizeof(double)));
-  PB_INIT_CK(cudaMalloc((void**)&b->work, 2 * (size_t)K * sizeof(double)));
-  PB_INIT_CK(cudaMallocHost((void**)&b->hs, 8 * (size_t)count * sizeof(double)));
-  const pr_status st = load(b, A, "pr_batch_init");
 #undef PB_INIT_CK
-  if (st != PR_OK) return bail(st);
   *out = b;
   return PR_OK;
 }
@@ -842,6 +908,8 @@ pr_status pr_batch_stats(pr_batch b, pr_batch_stats_t* out) {
   *out = b->st;
   out->launches = b->launches;
   out->emu_slices = b->S;
+  out->tile_n = b->bn;
+  out->tune_ms = b->tune_ms;
   return PR_OK;
 }
 

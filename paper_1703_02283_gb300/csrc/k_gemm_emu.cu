@@ -55,20 +55,31 @@
 namespace pr {
 namespace {
 
-constexpr int EBM = 128, EBN = 96, EBK = 16, SMAX = 8, BAND = 8, NSTAGE = 4;
+constexpr int EBM = 128, EBK = 16, SMAX = 8, BAND = 8, NSTAGE = 4;
 constexpr int NACC = 4;                  // level accumulators in TMEM: levels 2..5 (pass 0), 6..9 (pass 1)
 constexpr int MMA_WARPS = 2, EPI_WARPS = 16, THREADS = 32 * (2 + MMA_WARPS + EPI_WARPS);
-constexpr int EPI_COLS = EBN / 4;        // columns per epilogue warp (four warps per TMEM lane quadrant)
-constexpr int A_GROUP = EBM * 128, B_GROUP = EBN * 128;  // bytes of 4 planes (one 128-byte row per row)
-constexpr int A_BYTES = 2 * A_GROUP, STAGE_BYTES = A_BYTES + 2 * B_GROUP;
+constexpr int A_GROUP = EBM * 128;       // bytes of 4 planes of the X tile (one 128-byte row per row)
+constexpr int A_BYTES = 2 * A_GROUP;
 constexpr int NBARS = 2 * NSTAGE + 2 * NACC + 2 + 1;
-constexpr int SMEM_BYTES = 1024 + NSTAGE * STAGE_BYTES + 8 * NBARS + 16;
-constexpr int ACOL = NACC * EBN;         // TMEM column of the first X-plane buffer (after the accumulators)
-constexpr int SCRATCH_PER_CTA = 2 * EPI_WARPS * 32 * EPI_COLS;  // int64 totals: first pass (hi), then lo
-constexpr int SPLIT_PER_PART = 2 * EPI_WARPS * 32 * EPI_COLS;  // int64: (hi, lo) per element of a tile
-constexpr uint32_t kIdesc = ptx::idesc_f16_f32(EBM, EBN);
-static_assert(ACOL + 2 * SMAX * 8 <= 512, "tensor memory budget");
-static_assert(STAGE_BYTES % 1024 == 0 && SMEM_BYTES <= 232448, "shared memory");
+constexpr int BN_WIDE = 96, BN_NARROW = 48;  // the two tile widths (output columns per tile)
+
+// What depends on the tile width BN (the N of every MMA and the rows of Y per stage).
+template <int BN>
+struct EmuTile {
+  static constexpr int EPI_COLS = BN / 4;     // columns per epilogue warp (four warps per TMEM lane quadrant)
+  static constexpr int B_GROUP = BN * 128;    // bytes of 4 planes of the Y tile
+  static constexpr int STAGE_BYTES = A_BYTES + 2 * B_GROUP;
+  static constexpr int SMEM_BYTES = 1024 + NSTAGE * STAGE_BYTES + 8 * NBARS + 16;
+  static constexpr int ACOL = NACC * BN;      // TMEM column of the first X-plane buffer (after the accumulators)
+  static constexpr int SCRATCH_PER_CTA = 2 * EPI_WARPS * 32 * EPI_COLS;  // int64 totals: first pass, then lo
+  static constexpr int SPLIT_PER_PART = 2 * EPI_WARPS * 32 * EPI_COLS;   // int64: (hi, lo) per tile element
+  static constexpr uint32_t kIdesc = ptx::idesc_f16_f32(EBM, BN);
+  static_assert(BN % 16 == 0 && BN <= 256, "MMA N for M = 128");
+  static_assert(ACOL + 2 * SMAX * 8 <= 512, "tensor memory budget");
+  static_assert(STAGE_BYTES % 1024 == 0 && B_GROUP % 1024 == 0, "1024-byte aligned swizzle atoms");
+  static_assert(SMEM_BYTES <= 232448, "shared memory");
+  static_assert(EPI_COLS == 24 || EPI_COLS == 12, "epilogue column split");
+};
 
 // ------------------------------------------------------------------------------------------ slicing
 
@@ -174,7 +185,7 @@ struct EmuArgs {
   Epilogue e;            // output pointers are the bases of the (packed) FP64 buffers
   const int* ex;         // row exponents of X (indexed by packed row)
   const int* ey;         // row exponents of Y
-  long long* scratch;    // SCRATCH_PER_CTA int64 per CTA: the first pass's exact totals
+  long long* scratch;    // EmuTile::SCRATCH_PER_CTA int64 per CTA: the first pass's exact totals
   int* err;
   unsigned long long* tstamp;  // if set: [0] min over CTAs of the start time, [1] max of the end time (ns)
   long long* split;      // split tiles: per slot, 2 parts x SPLIT_PER_PART exact totals (hi, lo pairs)
@@ -239,26 +250,28 @@ __device__ __noinline__ double wide_to_double(long long H, unsigned long long Lw
 
 // The MMAs of one level L for S = 8 (pairs s = 1 .. L - 1, t = L - s), unrolled: X plane s - 1 from TMEM
 // buffer aT, Y plane t - 1 from the shared-memory stage whose first plane group has descriptor bdesc.
-template <int L>
+template <int BN, int L>
 __device__ __forceinline__ void mma_level(uint32_t d, uint32_t aT, uint64_t bdesc, bool fresh) {
+  using T = EmuTile<BN>;
 #pragma unroll
   for (int s = 1; s <= L - 1; ++s) {
     const int t = L - s - 1;
-    ptx::mma_f16_ts(d, aT + 8 * (s - 1), bdesc + (uint64_t)(((t >> 2) * B_GROUP + (t & 3) * 32) >> 4), kIdesc,
+    ptx::mma_f16_ts(d, aT + 8 * (s - 1), bdesc + (uint64_t)(((t >> 2) * T::B_GROUP + (t & 3) * 32) >> 4), T::kIdesc,
                     (fresh && s == 1) ? 0u : 1u);
   }
 }
 
+template <int BN>
 __device__ __forceinline__ void mma_level_s8(int L, uint32_t d, uint32_t aT, uint64_t bdesc, bool fresh) {
   switch (L) {
-    case 2: mma_level<2>(d, aT, bdesc, fresh); break;
-    case 3: mma_level<3>(d, aT, bdesc, fresh); break;
-    case 4: mma_level<4>(d, aT, bdesc, fresh); break;
-    case 5: mma_level<5>(d, aT, bdesc, fresh); break;
-    case 6: mma_level<6>(d, aT, bdesc, fresh); break;
-    case 7: mma_level<7>(d, aT, bdesc, fresh); break;
-    case 8: mma_level<8>(d, aT, bdesc, fresh); break;
-    default: mma_level<9>(d, aT, bdesc, fresh); break;
+    case 2: mma_level<BN, 2>(d, aT, bdesc, fresh); break;
+    case 3: mma_level<BN, 3>(d, aT, bdesc, fresh); break;
+    case 4: mma_level<BN, 4>(d, aT, bdesc, fresh); break;
+    case 5: mma_level<BN, 5>(d, aT, bdesc, fresh); break;
+    case 6: mma_level<BN, 6>(d, aT, bdesc, fresh); break;
+    case 7: mma_level<BN, 7>(d, aT, bdesc, fresh); break;
+    case 8: mma_level<BN, 8>(d, aT, bdesc, fresh); break;
+    default: mma_level<BN, 9>(d, aT, bdesc, fresh); break;
   }
 }
 
@@ -266,9 +279,13 @@ __device__ __forceinline__ void mma_level_s8(int L, uint32_t d, uint32_t aT, uin
 // second step; 8 pairs x 8 steps x 16 x 2^14 = 2^24 keeps every level exact) and after the pass's last step.
 __device__ __forceinline__ bool drains_after(int a, int j) { return ((j + 2 * a) & 7) == 7; }
 
-template <bool SYM, bool SPLIT>
+template <int BN, bool SYM, bool SPLIT>
 __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (5 warps per sub-partition)
     k_gemm_emu(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, EmuArgs args) {
+  using T = EmuTile<BN>;
+  constexpr int EPI_COLS = T::EPI_COLS, B_GROUP = T::B_GROUP, STAGE_BYTES = T::STAGE_BYTES, ACOL = T::ACOL;
+  constexpr int SCRATCH_PER_CTA = T::SCRATCH_PER_CTA, SPLIT_PER_PART = T::SPLIT_PER_PART;
+  constexpr uint32_t kIdesc = T::kIdesc;
   const int ntiles = args.ntiles_dev ? *args.ntiles_dev : args.ntiles;
   if ((int)blockIdx.x >= ntiles) return;  // no work for this CTA (uniform over the block)
   if (args.tstamp && threadIdx.x == 0) atomicMin(&args.tstamp[0], (unsigned long long)ptx::globaltimer());
@@ -319,7 +336,7 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
       for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
         int bi, bj, kpart, j0, j1;
         const EmuMat& mt = item_of<SPLIT>(args, t, bi, bj, kpart, j0, j1);
-        const int ya = mt.row0 + bi * EBM, yb = mt.row0 + bj * EBN;
+        const int ya = mt.row0 + bi * EBM, yb = mt.row0 + bj * BN;
         for (int pass = 0; pass < npass && !stop; ++pass) {
           const int ng = pass == 0 ? 1 : groups1;
           for (int j = j0; j < j1; ++j, ++it) {
@@ -416,9 +433,9 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
                 }
                 ptx::tc_fence_after();
               }
-              const uint32_t d = tmem + (uint32_t)(EBN * a);
+              const uint32_t d = tmem + (uint32_t)(BN * a);
               if (S == SMAX) {
-                mma_level_s8(L, d, aT, bdesc, fr);
+                mma_level_s8<BN>(L, d, aT, bdesc, fr);
               } else {
                 const int s0 = max(1, L - S), s1 = min(S, L - 1);
                 for (int s = s0; s <= s1; ++s) {
@@ -477,16 +494,27 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
             }
             ptx::tc_fence_after();
             const int sh = 8 * (3 - a);  // 8 (5 - L) in the first pass, 8 (9 - L) in the second
-            const uint32_t ta = tmem + lane_off + (uint32_t)(EBN * a + EPI_COLS * h);
-            // 24 columns as 16 + 8 (h even) or 8 + 16 (h odd): every load starts on a multiple of its width.
-            // Both loads, one wait, and the accumulator is released before any integer work.
+            const uint32_t ta = tmem + lane_off + (uint32_t)(BN * a + EPI_COLS * h);
+            // 24 columns as 16 + 8 (h even) or 8 + 16 (h odd), 12 as 8 + 4 or 4 + 8: every load starts on a
+            // multiple of its width. Both loads, one wait, and the accumulator is released before any
+            // integer work.
             uint32_t v[EPI_COLS];
-            if ((h & 1) == 0) {
-              ptx::tmem_ld_32x32b_x16(ta, v);
-              ptx::tmem_ld_32x32b_x8(ta + 16, v + 16);
+            if constexpr (EPI_COLS == 24) {
+              if ((h & 1) == 0) {
+                ptx::tmem_ld_32x32b_x16(ta, v);
+                ptx::tmem_ld_32x32b_x8(ta + 16, v + 16);
+              } else {
+                ptx::tmem_ld_32x32b_x8(ta, v);
+                ptx::tmem_ld_32x32b_x16(ta + 8, v + 8);
+              }
             } else {
-              ptx::tmem_ld_32x32b_x8(ta, v);
-              ptx::tmem_ld_32x32b_x16(ta + 8, v + 8);
+              if ((h & 1) == 0) {
+                ptx::tmem_ld_32x32b_x8(ta, v);
+                ptx::tmem_ld_32x32b_x4(ta + 8, v + 8);
+              } else {
+                ptx::tmem_ld_32x32b_x4(ta, v);
+                ptx::tmem_ld_32x32b_x8(ta + 4, v + 4);
+              }
             }
             ptx::tmem_ld_wait();
             ptx::tc_fence_before();
@@ -549,7 +577,7 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
       float part = 0.0f;
 #pragma unroll
       for (int c = 0; c < EPI_COLS; ++c) {
-        const int jc = bj * EBN + EPI_COLS * h + c;
+        const int jc = bj * BN + EPI_COLS * h + c;
         const long long hi = scr[(size_t)c * (EPI_WARPS * 32)];
         const long long lo = SPLIT ? scr_lo[(size_t)c * (EPI_WARPS * 32)] : acc[c];
         if (i >= n || jc >= n || (SYM && i > jc)) continue;
@@ -628,16 +656,22 @@ int sm_count_emu() {
   return count;
 }
 
+template <int BN>
+cudaError_t set_emu_attributes() {
+  const int bytes = EmuTile<BN>::SMEM_BYTES;
+  for (auto k : {k_gemm_emu<BN, true, false>, k_gemm_emu<BN, false, false>, k_gemm_emu<BN, true, true>,
+                 k_gemm_emu<BN, false, true>}) {
+    cudaError_t r = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (r != cudaSuccess) return r;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t prepare_emu() {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t r = cudaFuncSetAttribute(k_gemm_emu<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (r != cudaSuccess) return r;
-    r = cudaFuncSetAttribute(k_gemm_emu<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (r != cudaSuccess) return r;
-    r = cudaFuncSetAttribute(k_gemm_emu<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (r != cudaSuccess) return r;
-    r = cudaFuncSetAttribute(k_gemm_emu<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaError_t r = set_emu_attributes<BN_WIDE>();
+    if (r == cudaSuccess) r = set_emu_attributes<BN_NARROW>();
     if (r != cudaSuccess) return r;
     attr_set = true;
   }
@@ -646,8 +680,23 @@ cudaError_t prepare_emu() {
   return cudaSuccess;
 }
 
-cudaError_t launch_emu(const __half* DX, const __half* DY, int R, int K, int ldl, Mode mode, EmuArgs& a,
+template <int BN>
+cudaError_t launch_emu_bn(const CUtensorMap& mx, const CUtensorMap& my, int grid, Mode mode, const EmuArgs& a,
+                          cudaStream_t s) {
+  const int bytes = EmuTile<BN>::SMEM_BYTES;
+  if (mode == Mode::Sym) {
+    if (a.split) k_gemm_emu<BN, true, true><<<grid, THREADS, bytes, s>>>(mx, my, a);
+    else k_gemm_emu<BN, true, false><<<grid, THREADS, bytes, s>>>(mx, my, a);
+  } else {
+    if (a.split) k_gemm_emu<BN, false, true><<<grid, THREADS, bytes, s>>>(mx, my, a);
+    else k_gemm_emu<BN, false, false><<<grid, THREADS, bytes, s>>>(mx, my, a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_emu(const __half* DX, const __half* DY, int R, int K, int ldl, Mode mode, int bn, EmuArgs& a,
                        cudaStream_t s) {
+  if (bn != BN_WIDE && bn != BN_NARROW) return cudaErrorInvalidValue;
   if (a.S < 1 || a.S > SMAX || ldl % 16 != 0 || ldl < K || K < 1 || !a.items || !a.scratch) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(DX) | reinterpret_cast<uintptr_t>(DY)) & 15) return cudaErrorMisalignedAddress;
   cudaError_t pr_ = prepare_emu();
@@ -656,42 +705,41 @@ cudaError_t launch_emu(const __half* DX, const __half* DY, int R, int K, int ldl
   CUtensorMap mx, my;
   cudaError_t r = make_plane_map(&mx, DX, R, ldl, EBM);
   if (r != cudaSuccess) return r;
-  r = make_plane_map(&my, DY, R, ldl, EBN);
+  r = make_plane_map(&my, DY, R, ldl, bn);
   if (r != cudaSuccess) return r;
   const int grid = a.ntiles_dev || a.ntiles >= sm_count_emu() ? sm_count_emu() : a.ntiles;
-  if (mode == Mode::Sym) {
-    if (a.split) k_gemm_emu<true, true><<<grid, THREADS, SMEM_BYTES, s>>>(mx, my, a);
-    else k_gemm_emu<true, false><<<grid, THREADS, SMEM_BYTES, s>>>(mx, my, a);
-  } else {
-    if (a.split) k_gemm_emu<false, true><<<grid, THREADS, SMEM_BYTES, s>>>(mx, my, a);
-    else k_gemm_emu<false, false><<<grid, THREADS, SMEM_BYTES, s>>>(mx, my, a);
-  }
-  return cudaGetLastError();
+  return bn == BN_WIDE ? launch_emu_bn<BN_WIDE>(mx, my, grid, mode, a, s)
+                       : launch_emu_bn<BN_NARROW>(mx, my, grid, mode, a, s);
 }
 
 }  // namespace
 
-void emu_tile_list(int m, int n, Mode mode, std::vector<int4>& out) {
-  const int TM = (n + EBM - 1) / EBM, TN = (n + EBN - 1) / EBN;
+void emu_tile_list(int m, int n, Mode mode, std::vector<int4>& out, int bn) {
+  const int TM = (n + EBM - 1) / EBM, TN = (n + bn - 1) / bn;
   for (int g = 0; g < TM; g += BAND)
     for (int bj = 0; bj < TN; ++bj)
       for (int bi = g; bi < std::min(g + BAND, TM); ++bi)
-        if (mode != Mode::Sym || EBN * bj + EBN - 1 >= EBM * bi) out.push_back(make_int4(m, bi, bj, 0));
+        if (mode != Mode::Sym || bn * bj + bn - 1 >= EBM * bi) out.push_back(make_int4(m, bi, bj, 0));
 }
 
 // One product of a single matrix: its tiles, each split over K into two halves when that shortens the
 // launch. A launch of T tiles on G CTAs lasts ceil(T / G) tile times; split, ceil(2T / G) half-tile times.
 // Halves of tile k are items (0, bi, bj, 1 + 2k) and (0, bi, bj, 2 + 2k), next to each other.
-int emu_split_slots(int n, Mode mode) {
-  const int T = emu_tile_count(n, mode), G = sm_count_emu(), KS = (n + EBK - 1) / EBK;
-  const bool split = KS >= 2 && T < 4 * G && (2 * T + G - 1) / G < 2 * ((T + G - 1) / G);
-  return split ? T : 0;
+int emu_split_slots(int n, Mode mode, int bn, int split) {
+  const int T = emu_tile_count(n, mode, bn), G = sm_count_emu(), KS = (n + EBK - 1) / EBK;
+  if (KS < 2 || split == 0) return 0;
+  if (split > 0) return T;
+  return T < 4 * G && (2 * T + G - 1) / G < 2 * ((T + G - 1) / G) ? T : 0;
 }
 
-void emu_launch_list(int n, Mode mode, std::vector<int4>& out) {
+bool emu_split_useful(int n, Mode mode, int bn) {
+  return (n + EBK - 1) / EBK >= 2 && emu_tile_count(n, mode, bn) < 4 * sm_count_emu();
+}
+
+void emu_launch_list(int n, Mode mode, std::vector<int4>& out, int bn, int split) {
   std::vector<int4> tiles;
-  emu_tile_list(0, n, mode, tiles);
-  if (emu_split_slots(n, mode) == 0) {
+  emu_tile_list(0, n, mode, tiles, bn);
+  if (emu_split_slots(n, mode, bn, split) == 0) {
     out.insert(out.end(), tiles.begin(), tiles.end());
     return;
   }
@@ -702,19 +750,24 @@ void emu_launch_list(int n, Mode mode, std::vector<int4>& out) {
   }
 }
 
-size_t emu_split_bytes(int slots) { return (size_t)slots * 2 * SPLIT_PER_PART * sizeof(long long); }
+// Sized for the wider tile, so that one buffer serves either width.
+size_t emu_split_bytes(int slots) {
+  return (size_t)slots * 2 * EmuTile<BN_WIDE>::SPLIT_PER_PART * sizeof(long long);
+}
 
 size_t emu_split_counters(int slots) { return (size_t)slots * EPI_WARPS; }
 
-int emu_tile_count(int n, Mode mode) {
+int emu_tile_count(int n, Mode mode, int bn) {
   std::vector<int4> v;
-  emu_tile_list(0, n, mode, v);
+  emu_tile_list(0, n, mode, v, bn);
   return (int)v.size();
 }
 
-int emu_tiles(int n, Mode mode) { return emu_tile_count(n, mode) * EPI_WARPS; }
+int emu_tiles(int n, Mode mode, int bn) { return emu_tile_count(n, mode, bn) * EPI_WARPS; }
 
 int emu_partials_per_item() { return EPI_WARPS; }
+
+bool emu_tile_width_ok(int bn) { return bn == BN_WIDE || bn == BN_NARROW; }
 
 int emu_max_slices() { return SMAX; }
 
@@ -736,11 +789,13 @@ cudaError_t slice_rows(const double* X, int R, int n, int ldx, int ldl, int S, c
 
 cudaError_t emu_prepare() { return prepare_emu(); }
 
-size_t emu_scratch_bytes() { return (size_t)sm_count_emu() * SCRATCH_PER_CTA * sizeof(long long); }
+size_t emu_scratch_bytes() {
+  return (size_t)sm_count_emu() * EmuTile<BN_WIDE>::SCRATCH_PER_CTA * sizeof(long long);  // the wider tile's
+}
 
 cudaError_t gemm_emu(const __half* DX, const int* ex, const __half* DY, const int* ey, int n, int ldl, int S, Mode mode,
                      bool transpose, const int4* items, int nitems, const Epilogue& e, long long* scratch,
-                     long long* split, int* split_cnt, int* err, cudaStream_t s) {
+                     long long* split, int* split_cnt, int* err, cudaStream_t s, int bn) {
   EmuArgs a{};
   a.scratch = scratch;
   a.split = split;
@@ -756,13 +811,13 @@ cudaError_t gemm_emu(const __half* DX, const int* ex, const __half* DY, const in
   a.ex = ex;
   a.ey = ey;
   a.err = err;
-  return launch_emu(DX, DY, n, n, ldl, mode, a, s);
+  return launch_emu(DX, DY, n, n, ldl, mode, bn, a, s);
 }
 
 cudaError_t gemm_emu_batched(const __half* DX, const int* ex, const __half* DY, const int* ey, int R, int K, int ldl,
                              int ld, int S, Mode mode, bool transpose, const int4* items, int nitems,
                              const int* nitems_dev, const EmuBatchMat* mats, const Epilogue& e, long long* scratch,
-                             int* err, unsigned long long* tstamp, cudaStream_t s) {
+                             int* err, unsigned long long* tstamp, cudaStream_t s, int bn) {
   static_assert(sizeof(EmuBatchMat) == sizeof(EmuMat), "batch matrix record");
   EmuArgs a{};
   a.scratch = scratch;
@@ -778,7 +833,7 @@ cudaError_t gemm_emu_batched(const __half* DX, const int* ex, const __half* DY, 
   a.ex = ex;
   a.ey = ey;
   a.err = err;
-  return launch_emu(DX, DY, R, K, ldl, mode, a, s);
+  return launch_emu(DX, DY, R, K, ldl, mode, bn, a, s);
 }
 
 }  // namespace pr

@@ -99,19 +99,24 @@ cudaError_t gemm_fp8_tc(const uint8_t* X, const int* sx, const uint8_t* Y, const
 // gemm_emu(): P = X Y^T from the slices of X and Y over the work items (emu_launch_list), FP64 epilogue
 // (out / out2 / partial; no BF16 copies). One residual partial per epilogue warp and tile
 // (emu_partials_per_item() per tile, in tile order, also when tiles are split).
+// Tiles are 128 rows x bn columns, bn = 96 (the default) or 48 (emu_tile_width_ok); the work items of a
+// launch must be built for the bn it runs with.
 // emu_tile_list(): appends the work items (m, tile row, tile column, 0) of matrix m (order n) in the
-// kernel's order; tiles are 128 rows x 96 columns, symmetric mode keeps those reaching the upper triangle.
-void emu_tile_list(int m, int n, Mode mode, std::vector<int4>& out);
-int emu_tile_count(int n, Mode mode);
+// kernel's order; symmetric mode keeps the tiles reaching the upper triangle.
+bool emu_tile_width_ok(int bn);
+void emu_tile_list(int m, int n, Mode mode, std::vector<int4>& out, int bn = 96);
+int emu_tile_count(int n, Mode mode, int bn = 96);
 // The work list of one single-matrix product: emu_tile_list, with every tile split over K into two items
-// when that shortens the launch (emu_split_slots tiles; 0: not split). A split launch needs
+// (emu_split_slots tiles; 0: not split) when split > 0, never when split == 0, and when that shortens the
+// launch (ceil(2T / G) < 2 ceil(T / G) on G SMs) when split < 0. A split launch needs
 // emu_split_bytes(slots) bytes of exact half totals and emu_split_counters(slots) ints, zero before the
 // first launch (the kernel leaves them zero).
-void emu_launch_list(int n, Mode mode, std::vector<int4>& out);
-int emu_split_slots(int n, Mode mode);
+void emu_launch_list(int n, Mode mode, std::vector<int4>& out, int bn = 96, int split = -1);
+int emu_split_slots(int n, Mode mode, int bn = 96, int split = -1);
+bool emu_split_useful(int n, Mode mode, int bn);  // at least 2 K steps and fewer than 4 waves of tiles
 size_t emu_split_bytes(int slots);
 size_t emu_split_counters(int slots);
-int emu_tiles(int n, Mode mode);  // residual partials of one product: emu_tile_count * emu_partials_per_item
+int emu_tiles(int n, Mode mode, int bn = 96);  // residual partials of one product: tiles * emu_partials_per_item
 int emu_partials_per_item();
 int emu_max_slices();
 int emu_ld(int K);  // the K extent of a digit-plane row: K rounded up to 16
@@ -123,7 +128,7 @@ cudaError_t slice_rows(const double* X, int R, int n, int ldx, int ldl, int S, c
                        cudaStream_t s);
 cudaError_t gemm_emu(const __half* DX, const int* ex, const __half* DY, const int* ey, int n, int ldl, int S, Mode mode,
                      bool transpose, const int4* items, int nitems, const Epilogue& e, long long* scratch,
-                     long long* split, int* split_cnt, int* err, cudaStream_t s);
+                     long long* split, int* split_cnt, int* err, cudaStream_t s, int bn = 96);
 
 // A batch of matrices packed row-wise in shared buffers (leading dimension ld for FP64, ldl for digit
 // planes; R packed rows per plane; K the largest order). Work items from emu_tile_list per matrix;
@@ -137,7 +142,7 @@ struct EmuBatchMat {
 cudaError_t gemm_emu_batched(const __half* DX, const int* ex, const __half* DY, const int* ey, int R, int K, int ldl,
                              int ld, int S, Mode mode, bool transpose, const int4* items, int nitems,
                              const int* nitems_dev, const EmuBatchMat* mats, const Epilogue& e, long long* scratch,
-                             int* err, unsigned long long* tstamp, cudaStream_t s);
+                             int* err, unsigned long long* tstamp, cudaStream_t s, int bn = 96);
 
 // ---- elementwise and reductions (k_elementwise.cu)
 // scal[0] = max |a_ij|, scal[1] = max |a_ij - a_ji|, scal[2] = #non-finite, scal[3] = #non-positive diagonal

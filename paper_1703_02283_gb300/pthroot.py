@@ -32,7 +32,8 @@ class pr_options(ctypes.Structure):
                 ("stag_below", ctypes.c_double), ("stag_ratio", ctypes.c_double),
                 ("sym_tol", ctypes.c_double), ("reanchor", ctypes.c_int), ("emu_slices", ctypes.c_int),
                 ("stag_below_lowp", ctypes.c_double), ("c0_coef", ctypes.c_double * 4), ("gate_max", ctypes.c_double),
-                ("gate_iters", ctypes.c_int), ("verify", ctypes.c_int), ("gate_fallback", ctypes.c_int)]
+                ("gate_iters", ctypes.c_int), ("verify", ctypes.c_int), ("gate_fallback", ctypes.c_int),
+                ("emu_tile", ctypes.c_int)]
 
 
 class pr_stats_t(ctypes.Structure):
@@ -46,12 +47,13 @@ class pr_stats_t(ctypes.Structure):
                 ("gemms_timed_by_precision", ctypes.c_int64 * PR_NPREC),
                 ("gemm_ms_by_precision", ctypes.c_double * PR_NPREC),
                 ("gemm_flops_by_precision", ctypes.c_double * PR_NPREC), ("c0_gate", ctypes.c_double),
-                ("true_residual", ctypes.c_double), ("prescale_log2", ctypes.c_int)]
+                ("true_residual", ctypes.c_double), ("prescale_log2", ctypes.c_int),
+                ("emu_tile_n", ctypes.c_int * 2), ("emu_tile_split", ctypes.c_int * 2), ("emu_tune_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
         for k in ("iterations_by_precision", "gemms_timed_by_precision", "gemm_ms_by_precision",
-                  "gemm_flops_by_precision"):
+                  "gemm_flops_by_precision", "emu_tile_n", "emu_tile_split"):
             d[k] = list(getattr(self, k))
         return d
 
@@ -79,7 +81,8 @@ class pr_batch_matrix_t(ctypes.Structure):
 class pr_batch_stats_t(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("stages", ctypes.c_int64), ("products", ctypes.c_int64),
                 ("product_flops", ctypes.c_double), ("stages_timed", ctypes.c_int64), ("stage_ms", ctypes.c_double),
-                ("stage_flops_timed", ctypes.c_double), ("emu_slices", ctypes.c_int)]
+                ("stage_flops_timed", ctypes.c_double), ("emu_slices", ctypes.c_int), ("tile_n", ctypes.c_int),
+                ("tune_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -143,6 +146,8 @@ def _load() -> ctypes.CDLL:
                                      ctypes.c_void_p]),
         "pr_matmul_emu": (ctypes.c_int, [ctypes.c_int, _dptr, _dptr, ctypes.c_int64, ctypes.c_int, _dptr,
                                      ctypes.c_void_p]),
+        "pr_matmul_emu_tiled": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dptr, _dptr, ctypes.c_int64,
+                                               ctypes.c_int, _dptr, ctypes.c_void_p]),
         "pr_state_size": (ctypes.c_int, [_handle_t, ctypes.POINTER(ctypes.c_size_t)]),
         "pr_export_state": (ctypes.c_int, [_handle_t, ctypes.c_void_p, ctypes.c_size_t]),
         "pr_import_state": (ctypes.c_int, [_handle_t, ctypes.c_void_p, ctypes.c_size_t]),
@@ -345,6 +350,11 @@ def pr_selftest_wait(stream: int = 0) -> tuple[int, float]:
 def pr_matmul_emu(slices: int, X, Y, n: int, sym: bool, P, stream: int = 0) -> None:
     _check(_lib.pr_matmul_emu(int(slices), _ptr(X), _ptr(Y), int(n), 1 if sym else 0, _ptr(P),
                               ctypes.c_void_p(stream)), None)
+
+
+def pr_matmul_emu_tiled(slices: int, tile_n: int, split: int, X, Y, n: int, sym: bool, P, stream: int = 0) -> None:
+    _check(_lib.pr_matmul_emu_tiled(int(slices), int(tile_n), int(split), _ptr(X), _ptr(Y), int(n), 1 if sym else 0,
+                                    _ptr(P), ctypes.c_void_p(stream)), None)
 
 
 def pr_stats(h: int) -> dict:

@@ -3,7 +3,9 @@
 Each matrix of a batch must meet the single-matrix bar against the CPU oracle, and its result must equal,
 bit for bit, the single-matrix PR_EMU64 solve of the same matrix (same digit planes, same tiles, same
 stop rule): the batch's work lists, residuals and stop decisions, taken on the device inside one graph,
-must reproduce what the single-matrix path decides on the host.
+must reproduce what the single-matrix path decides on the host. Bit-equality needs the same tile width on
+both sides (residuals add per-tile partial sums), so those tests fix pr_options.emu_tile = 96; a separate
+test lets the tuner choose.
 """
 import numpy as np
 import pytest
@@ -28,9 +30,10 @@ def make_batch(count, n_lo, n_hi, kappa_hi, seed):
     return cases, [int(x) for x in spec.p]
 
 
-def single_emu(case, p, c0=P.PR_C0_EQ3, max_iter=None):
+def single_emu(case, p, c0=P.PR_C0_EQ3, max_iter=None, tile=96):
     o = P.pr_default_options()
     o.c0 = c0
+    o.emu_tile = tile
     if max_iter is not None:
         o.max_iter = max_iter
     A = torch.from_numpy(case.A).to(DEV)
@@ -45,9 +48,10 @@ def single_emu(case, p, c0=P.PR_C0_EQ3, max_iter=None):
         P.pr_destroy(h)
 
 
-def run_batch(cases, ps, host=False, c0=P.PR_C0_EQ3, max_iter=None, repeat=False, info=None):
+def run_batch(cases, ps, host=False, c0=P.PR_C0_EQ3, max_iter=None, repeat=False, info=None, tile=96):
     o = P.pr_default_options()
     o.c0 = c0
+    o.emu_tile = tile
     if max_iter is not None:
         o.max_iter = max_iter
     mats = [np.ascontiguousarray(c.A) if host else torch.from_numpy(c.A).to(DEV) for c in cases]
@@ -171,7 +175,9 @@ def test_batch_load_reuses_the_batch():
     # bit (same captured graph, state reset on the device).
     cases, ps = make_batch(7, 30, 260, 1e3, 41)
     other = [W.spd_from_spectrum(c.n, 1e-2, 5000 + i) for i, c in enumerate(cases)]
-    b = P.pr_batch_init([torch.from_numpy(c.A).to(DEV) for c in cases], ps, P.pr_default_options(),
+    o = P.pr_default_options()
+    o.emu_tile = 96
+    b = P.pr_batch_init([torch.from_numpy(c.A).to(DEV) for c in cases], ps, o,
                         torch.cuda.current_stream(DEV).cuda_stream)
     try:
         P.pr_batch_solve(b, len(cases), P.PR_EMU64, 1e-12)
@@ -260,3 +266,30 @@ def test_batch_stats_count_every_product():
     assert st["product_flops"] == pytest.approx(flops, rel=1e-12)
     assert st["stages_timed"] == st["stages"] and st["stage_flops_timed"] == st["product_flops"]
     assert st["stage_ms"] > 0 and st["emu_slices"] == 8 and st["launches"] > st["stages"]
+
+
+def test_batch_tile_tuner_and_narrow_tiles():
+    # Default options: pr_batch_init times the batch's symmetric product with 128 x 96 and 128 x 48 tiles and
+    # keeps the faster; the choice is reported. Every result meets the oracle bar whichever width runs, and a
+    # batch fixed at 48 gives the same products as one fixed at 96 (exact digit-pair sums): results equal
+    # bit for bit wherever the two made the same stop decisions.
+    cases, ps = make_batch(8, 20, 400, 1e3, 61)
+    mats = [torch.from_numpy(c.A).to(DEV) for c in cases]
+    b = P.pr_batch_init(mats, ps, P.pr_default_options(), torch.cuda.current_stream(DEV).cuda_stream)
+    try:
+        st = P.pr_batch_stats(b)
+        assert st["tile_n"] in (96, 48) and st["tune_ms"] > 0
+        its, sts = P.pr_batch_solve(b, len(cases), P.PR_EMU64, 1e-12)
+        for i, (case, p) in enumerate(zip(cases, ps)):
+            C = np.empty((case.n, case.n))
+            P.pr_batch_result(b, i, C)
+            Co, _ = O.solve(case.A, p, tol=1e-12)
+            Z = O.closed_form_root(case.Q, case.lam, p)
+            assert O.forward_error(C, Z) <= max(1e-12, 10 * O.forward_error(Co, Z)), (i, case.n, p)
+    finally:
+        P.pr_batch_destroy(b)
+    out48, its48, _, _ = run_batch(cases, ps, tile=48)
+    out96, its96, _, _ = run_batch(cases, ps, tile=96)
+    for i in range(len(cases)):
+        if its48[i] == its96[i]:
+            assert np.array_equal(out48[i][0], out96[i][0]), i

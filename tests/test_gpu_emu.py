@@ -88,6 +88,48 @@ def test_emu_product_every_slice_count(slices, n, sym):
     assert np.all(err[sel] <= bound[sel]), (slices, float(np.max(err[sel] / bound[sel])))
 
 
+@pytest.mark.parametrize("tile_n", [96, 48])
+@pytest.mark.parametrize("split", [-1, 0, 1])
+@pytest.mark.parametrize("n,sym", [(17, True), (129, True), (300, False), (700, True)])
+def test_emu_product_every_variant(tile_n, split, n, sym):
+    # Every work-list variant the tuner chooses between (tile width, whole or K-split tiles) gives the same
+    # product: element-wise within the truncation bound, and bit-equal to the default variant.
+    X, Y = sym_pair(n, 110 + n)
+    ref = X.astype(np.longdouble) @ Y.T.astype(np.longdouble)
+    Xd, Yd = torch.from_numpy(X).to(DEV), torch.from_numpy(Y).to(DEV)
+    Pd = torch.empty_like(Xd)
+    P.pr_matmul_emu_tiled(8, tile_n, split, Xd, Yd, n, sym, Pd, torch.cuda.current_stream(DEV).cuda_stream)
+    Pg = Pd.cpu().numpy()
+    err = np.abs(Pg.astype(np.longdouble) - ref).astype(np.float64)
+    bound = emu_bound(X, Y, ref.astype(np.float64))
+    sel = np.triu_indices(n) if sym else np.indices((n, n)).reshape(2, -1)
+    assert np.all(err[sel] <= bound[sel])
+    assert np.array_equal(Pg, gpu_matmul(P.PR_EMU64, X, Y, sym))
+
+
+@pytest.mark.parametrize("tile", [0, 48])
+def test_emu_solve_with_tuned_or_narrow_tiles(tile):
+    # The tuner (tile 0) picks a variant per product kind; the narrow tiles can be fixed. Either way the solve
+    # meets the oracle bar, and the stats report the width in use.
+    case = W.spd_from_spectrum(300, 1e-2, 7)
+    o = P.pr_default_options()
+    o.emu_tile = tile
+    A = torch.from_numpy(case.A).to(DEV)
+    h = P.pr_init(A, 300, 2, o, torch.cuda.current_stream(DEV).cuda_stream)
+    try:
+        P.pr_iterate(h, 100, P.PR_EMU64, 1e-12)
+        C = torch.empty_like(A)
+        P.pr_result(h, C)
+        st = P.pr_stats(h)
+    finally:
+        P.pr_destroy(h)
+    assert st["emu_tile_n"][0] in ((96, 48) if tile == 0 else (48,))
+    Co, info = O.solve(case.A, 2, tol=1e-12)
+    Z = O.closed_form_root(case.Q, case.lam, 2)
+    bound = max(1e-12, 10 * O.forward_error(Co, Z))
+    assert O.forward_error(C.cpu().numpy(), Z) <= bound
+
+
 def test_emu_product_full_size_sampled():
     n = 4096
     c = W.spd_from_spectrum(n, 1e-3, 1)

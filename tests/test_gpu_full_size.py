@@ -167,10 +167,11 @@ def test_single_recipe_n4096_scaled_identity(single_case, p, prec):
     assert np.max(np.abs(blk - want)) <= bar * np.max(np.abs(want))
     assert np.linalg.norm(blk - want) <= bar * np.linalg.norm(want)
     assert abs(info["steps"] - g["iterations"]) <= 1
-    # The true residual sits at the FP64 floor for both; most of it is the rounding of evaluating I - C^p A,
-    # which EMU64 products (one rounding per element) do with less error than the oracle's FP64 products.
+    # The true residual sits at the FP64 floor for both; most of it is the rounding of evaluating I - C^p A
+    # itself: EMU64 products (one rounding per element) report less than the oracle's blocked FP64 products,
+    # native FP64 products (4096-term sequential sums per element in the DMMA kernel) up to a few times more.
     tr = info["stats"]["true_residual"]
-    assert 0 < tr <= 3 * g["true_residual"], (tr, g["true_residual"])
+    assert 0 < tr <= (3 if prec == P.PR_EMU64 else 10) * g["true_residual"], (tr, g["true_residual"])
 
 
 @pytest.mark.slow
