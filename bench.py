@@ -94,7 +94,7 @@ def parse():
     ap.add_argument("--emu-slices", type=int, default=0, help="PR_EMU64 digit planes per operand (0: the default, 8)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "learned"],
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "learned", "f1"],
                     help="single: the n=4096 matrix for every p; batched: 512 matrices, n in [64, 1024]")
     ap.add_argument("--count", type=int, default=512, help="batched: number of matrices")
     ap.add_argument("--learned-n", type=int, default=2048, help="learned: matrix order")
@@ -108,6 +108,10 @@ def parse():
     ap.add_argument("--sub-steps", type=int, default=5, help="timed steps of the batched / learned summaries")
     ap.add_argument("--sub-warmup", type=int, default=3, help="warm-up steps of the batched / learned summaries")
     ap.add_argument("--e2e-steps", type=int, default=5, help="steps of the end-to-end measurement")
+    ap.add_argument("--f1-n", type=int, default=768, help="f1: order of the overlap stand-in")
+    ap.add_argument("--f1-iters", type=int, default=40, help="f1: iterations per mantissa width")
+    ap.add_argument("--f1-storage-bits", default="2,3,4,6,8,10,12,16,20,24")
+    ap.add_argument("--f1-arith-bits", default="6,8,9,10,11,12,14,16,18,20,24")
     return ap.parse_args()
 
 
@@ -687,6 +691,111 @@ def measure_learned(args, world, rank, local, dist, steps, warmup, e2e_on, cpu_o
     return line
 
 
+# ----------------------------------------------------------------------------- the paper's precision experiment
+
+def f1_matrix(n: int):
+    """The overlap stand-in of the experiment (Sec. 4.3: N = 768, p = 2): n points of the 2048-point density,
+    seeded 7000 + n, and its exact inverse square root from a LAPACK eigendecomposition (host)."""
+    S = W.overlap_matrix(W.overlap_points(n, 20.0 * (n / 2048) ** (1 / 3), 7000 + n))
+    lam, V = np.linalg.eigh(S)
+    return S, (V * lam ** -0.5) @ V.T
+
+
+def f1_config(args):
+    return {"workload": f"custom-precision experiment: overlap stand-in n={args.f1_n}, p=2, literal Eq. 1 from Eq. 3, "
+                        f"{args.f1_iters} iterations per mantissa width, storage widths {args.f1_storage_bits}, "
+                        f"arithmetic widths {args.f1_arith_bits}", "n": args.f1_n, "p": 2,
+            "l2": l2_note(9 * 8.0 * args.f1_n ** 2) + " per handle"}
+
+
+def measure_f1(args, local):
+    """Per mode and mantissa width: the error ||C_k - S^{-1/2}||_F (absolute, as Fig. 2 plots it) of every
+    iterate; reported are its smallest value, the iteration where it occurs and the final error. A width
+    'converges' when the smallest error is below 1e-2 of the starting error."""
+    import torch
+
+    from paper_1703_02283_gb300 import pthroot as P
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    S, Z = f1_matrix(args.f1_n)
+    A = torch.from_numpy(S).to(dev)
+    C = torch.empty_like(A)
+    zn = float(np.linalg.norm(Z))
+    table = {}
+    t0 = time.perf_counter()
+    for mode, name, bits in ((P.PR_QUANT_STORAGE, "storage", args.f1_storage_bits),
+                             (P.PR_QUANT_ARITH, "arithmetic", args.f1_arith_bits)):
+        rows = []
+        for m in [int(x) for x in bits.split(",")]:
+            o = P.pr_default_options()
+            o.form = P.PR_FORM_LITERAL
+            o.quant_bits = m
+            o.quant_mode = mode
+            o.stag_below = 0.0
+            h = P.pr_init(A, args.f1_n, 2, o, stream.cuda_stream)
+            errs = []
+            Zd = torch.from_numpy(Z).to(dev)
+            try:
+                for k in range(args.f1_iters + 1):
+                    if k:
+                        try:
+                            P.pr_iterate(h, 1, P.PR_FP64, 0.0)
+                        except P.PthrootError as exc:  # the iterate overflowed: the width diverged
+                            if exc.status != P.PR_EDIVERGED:
+                                raise
+                            errs += [float("inf")] * (args.f1_iters + 1 - k)
+                            break
+                    P.pr_result(h, C)
+                    e = float(torch.linalg.norm(C - Zd).item())
+                    errs.append(e if np.isfinite(e) else float("inf"))
+            finally:
+                P.pr_destroy(h)
+            k_min = int(np.argmin(errs))
+            rows.append({"bits": m, "min_error": errs[k_min], "min_rel_error": errs[k_min] / zn, "at_iteration": k_min,
+                         "final_error": errs[-1] if np.isfinite(errs[-1]) else "inf",
+                         "converges": bool(errs[k_min] < 1e-2 * errs[0]),
+                         "errors": [float(f"{e:.3g}") if np.isfinite(e) else "inf" for e in errs]})
+        table[name] = rows
+    torch.cuda.synchronize(dev)
+    return {"value": (time.perf_counter() - t0) * 1e3, "table": table, "reference_norm": zn}
+
+
+def run_f1(args):
+    if args.impl == "reference":
+        if int(os.environ.get("RANK", "0")) != 0:
+            return
+        from oracle import pthroot_oracle as O
+        S, Z = f1_matrix(args.f1_n)
+        step_ms = []
+        for _ in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            O.quantized_iterates(S, 2, 10, "storage", 1)
+            step_ms.append((time.perf_counter() - t0) * 1e3)
+        per = float(np.median(step_ms))
+        widths = len(args.f1_storage_bits.split(",")) + len(args.f1_arith_bits.split(","))
+        value = per * args.f1_iters * widths
+        ms = float(np.mean(step_ms[args.warmup:])) if args.steps else 0.0
+        print(json.dumps({"impl": "reference", "metric": "time of the custom-precision sweep", "value": value,
+                          "unit": "ms", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+                          "dtype": "f64", "data": "synthetic", "config": f1_config(args),
+                          "value_model": "value = one oracle storage-mode iteration (measured per step) x iterations x "
+                                         "widths; the arithmetic mode's per-operation rounding is slower still",
+                          "cpu_baseline": {"value": value, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+                                           "sample": f"one storage-mode iteration at n={args.f1_n}, m=10"},
+                          "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return
+    import torch
+    world, rank, local = replica_env()
+    torch.cuda.set_device(local)
+    r = measure_f1(args, local)
+    if rank == 0:
+        print(json.dumps({"metric": "time of the custom-precision sweep", "value": r["value"], "unit": "ms",
+                          "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": r["value"],
+                          "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "custom-m-bit",
+                          "data": "synthetic", "config": f1_config(args), "f1": r["table"]}), flush=True)
+
+
 def main():
     args = parse()
     ps = [int(x) for x in args.p.split(",")]
@@ -694,6 +803,8 @@ def main():
         return run_batched(args)
     if args.workload == "learned":
         return run_learned(args)
+    if args.workload == "f1":
+        return run_f1(args)
     if args.impl == "reference":
         return run_reference(args, ps)
 
@@ -746,7 +857,9 @@ def main():
                        "tol_met": bool(res <= args.tol),
                        "iterations_by_precision": {PREC_NAMES[k]: s["iterations_by_precision"][k]
                                                    for k in range(P.PR_NPREC) if s["iterations_by_precision"][k]},
-                       "switch_iteration": s["switch_iteration"]}
+                       "switch_iteration": s["switch_iteration"],
+                       "emu_tiles": {"sym": [s["emu_tile_n"][0], s["emu_tile_split"][0]],
+                                     "full": [s["emu_tile_n"][1], s["emu_tile_split"][1]]}}
         return info
 
     def barrier():
@@ -906,6 +1019,11 @@ def main():
             except Exception as exc:  # a failing summary must not hide the headline
                 extra[name] = {"error": f"{type(exc).__name__}: {exc}"}
             torch.cuda.empty_cache()
+        try:
+            r1 = measure_f1(args, local)
+            extra["f1"] = {"ms": r1["value"], "reference_norm": r1["reference_norm"], **r1["table"]}
+        except Exception as exc:
+            extra["f1"] = {"error": f"{type(exc).__name__}: {exc}"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,

@@ -104,6 +104,15 @@ typedef enum {
                           returns PR_EGATE when pr_options.gate_fallback is 0                            */
 } pr_c0_kind;
 
+/* The custom-precision experiment of Sec. 4.2-4.3 (Fig. 2): numbers with m stored mantissa bits (m + 1
+ * significant bits) and FP64's exponent range, rounded to nearest with ties to even. */
+typedef enum {
+  PR_QUANT_STORAGE = 1,  /* the input A and every stored iterate (C_0 included) are rounded; arithmetic in FP64  */
+  PR_QUANT_ARITH = 2     /* A, C_0 and every operation of the iteration: each product term and partial sum of
+                            the matrix products (summed in the order k = 0, 1, ..., n - 1), each operation of
+                            ((p + 1) C - C^{p+1} A) / p and of the symmetrisation rnd(C + C^T) / 2             */
+} pr_quant_mode;
+
 /* Options fixed at pr_init. */
 typedef struct {
   int form;            /* pr_form, default PR_FORM_AUTO                                                  */
@@ -136,6 +145,10 @@ typedef struct {
                           the width (tiles split by the wave rule). Products are exact integer sums rounded
                           once, the same for every variant; residuals, which add per-tile partial sums, differ
                           in their last bits between widths                                             */
+  int quant_bits;      /* 0 (default): off. 1..52: run the custom-precision experiment with this many stored
+                          mantissa bits (PR_FORM_LITERAL from Eq. 3's C_0 with PR_FP64 iterations only, else
+                          pr_init returns PR_EUNSUPPORTED). The stop test's residual is evaluated in FP64  */
+  int quant_mode;      /* pr_quant_mode, default PR_QUANT_STORAGE                                          */
 } pr_options;
 
 /* Counters of one handle. */

@@ -547,7 +547,28 @@ pr_status ns_update(pr_handle h, int prec) {
 }
 
 // Literal Eq. 1 (FP64 only): T_j = C T_{j-1}, T_0 = A (full products); the residual from T_p = C^p A.
+// The custom-precision experiment (pr_options.quant_bits with quant_mode PR_QUANT_ARITH): every operation
+// of the literal iteration in m-bit arithmetic (k_quant.cu).
+bool quant_arith(pr_handle h) { return h->opt.quant_bits > 0 && h->opt.quant_mode == PR_QUANT_ARITH; }
+
 pr_status literal_residual(pr_handle h, int prec, double* r) {
+  if (quant_arith(h)) {
+    // T_j = C T_{j-1} in the m-bit arithmetic; the residual ||I - T_p||_F (the stop test) in FP64.
+    const int n = (int)h->n, m = h->opt.quant_bits;
+    Mat* src = &h->A;
+    for (int j = 1; j <= h->p; ++j) {
+      Mat* dst = (j & 1) ? &h->T0 : &h->T1;
+      PR_CK(h, pr::gemm_round(h->X.f, src->f, n, m, dst->f, h->stream));
+      dst->changed();
+      h->powers_valid = false;
+      h->st.gemms += 1;
+      h->st.gemm_flops += full_flops(n);
+      src = dst;
+    }
+    PR_CK(h, pr::resid_rows(src->f, n, h->partial, h->stream));
+    h->st.launches += h->p + 1;
+    return read_residual(h, pr::resid_row_partials(n), r);
+  }
   Mat* src = &h->A;
   for (int j = 1; j <= h->p; ++j) {
     Out o;
@@ -560,9 +581,23 @@ pr_status literal_residual(pr_handle h, int prec, double* r) {
   return read_residual(h, tiles_for(h, prec, Mode::Full), r);
 }
 
-// C' = sym(((p+1) C - C T_p) / p).
+// C' = sym(((p+1) C - C T_p) / p); with pr_options.quant_bits the stored iterate is rounded (storage) or
+// every operation is (arithmetic).
 pr_status literal_update(pr_handle h, int prec) {
   Mat& Tp = (h->p & 1) ? h->T0 : h->T1;
+  const int n = (int)h->n, m = h->opt.quant_bits;
+  if (quant_arith(h)) {
+    PR_CK(h, pr::gemm_round(h->X.f, Tp.f, n, m, h->Mn.f, h->stream));
+    PR_CK(h, pr::quant_update(h->X.f, h->Mn.f, n, h->p, m, h->Mn.f, h->stream));
+    PR_CK(h, pr::quant_sym(h->Mn.f, n, m, h->Xn.f, h->stream));
+    h->st.gemms += 1;
+    h->st.gemm_flops += full_flops(n);
+    h->st.launches += 3;
+    h->Xn.changed();
+    h->Mn.changed();
+    swap(h->X, h->Xn);
+    return PR_OK;
+  }
   Out o;
   o.out2 = &h->Mn;
   o.b = -1.0 / h->p;
@@ -572,6 +607,10 @@ pr_status literal_update(pr_handle h, int prec) {
   if (s != PR_OK) return s;
   PR_CK(h, pr::symmetrize(h->Mn.f, (int)h->n, h->Xn.f, h->stream));
   h->st.launches += 1;
+  if (m > 0) {  // storage: the new iterate is stored with m mantissa bits
+    PR_CK(h, pr::round_values(h->Xn.f, (int64_t)n * n, m, h->Xn.f, h->stream));
+    h->st.launches += 1;
+  }
   h->Xn.changed();
   swap(h->X, h->Xn);
   return PR_OK;
@@ -788,7 +827,7 @@ pr_status form_initial_guess(pr_handle h) {
     PR_CK(h, pr::init_c0_eq3(h->A.f, n, 1.0 / (h->st.norm_1 * h->st.norm_inf), h->X.f, h->stream));
   } else if (h->opt.c0 == PR_C0_SCALED_I) {
     PR_CK(h, pr::set_scaled_identity(h->X.f, n, pow(h->st.norm_1, -1.0 / h->p), h->stream));
-  } else {
+  } else if (h->opt.c0 == PR_C0_POLY) {
     pr_status st = poly_initial_guess(h);
     if (st == PR_EGATE) {
       const pr_status s2 = sync(h);
@@ -796,6 +835,8 @@ pr_status form_initial_guess(pr_handle h) {
     }
     if (st != PR_OK) return st;
   }
+  if (h->opt.quant_bits > 0)  // C_0, computed in FP64, is stored with m mantissa bits
+    PR_CK(h, pr::round_values(h->X.f, (int64_t)n * n, h->opt.quant_bits, h->X.f, h->stream));
   h->X.changed();
   h->st.launches += 1;
   return sync(h);
@@ -918,6 +959,8 @@ void pr_default_options(pr_options* o) {
   o->verify = 1;
   o->gate_fallback = 1;
   o->emu_tile = 0;
+  o->quant_bits = 0;
+  o->quant_mode = PR_QUANT_STORAGE;
 }
 
 const char* pr_last_error(pr_handle h) { return h ? h->err.c_str() : g_init_error.c_str(); }
@@ -963,6 +1006,11 @@ pr_status pr_init(pr_handle* out, const double* A, int64_t n, int p, const pr_op
   if (o.c0 == PR_C0_POLY && (!(o.gate_max > 0) || o.gate_iters < 1))
     return fail(nullptr, PR_EINVAL, "pr_init: bad gate options");
   if (o.form == PR_FORM_NS && p != 1) return fail(nullptr, PR_EINVAL, "pr_init: the Newton-Schulz form needs p = 1");
+  if (o.quant_bits != 0 &&
+      (o.quant_bits < 1 || o.quant_bits > 52 || (o.quant_mode != PR_QUANT_STORAGE && o.quant_mode != PR_QUANT_ARITH)))
+    return fail(nullptr, PR_EINVAL, "pr_init: quant_bits must be in [1, 52] and quant_mode storage or arithmetic");
+  if (o.quant_bits != 0 && (o.form != PR_FORM_LITERAL || o.c0 != PR_C0_EQ3))
+    return fail(nullptr, PR_EUNSUPPORTED, "pr_init: the custom-precision experiment runs the literal form from Eq. 3");
   if (o.max_iter < 0 || !(o.stag_ratio > 0) || !(o.sym_tol >= 0) || !(o.stag_below_lowp >= 0) ||
       o.emu_slices < 0 || o.emu_slices > pr::emu_max_slices() || (o.emu_tile != 0 && !pr::emu_tile_width_ok(o.emu_tile)))
     return fail(nullptr, PR_EINVAL, "pr_init: bad option value");
@@ -1060,6 +1108,10 @@ pr_status pr_load(pr_handle h, const double* A) {
   h->A.changed();
   h->st.norm_1 = 0.0;
   PR_CK(h, cudaMemcpyAsync(h->A.f, A, bytes, cudaMemcpyDefault, h->stream));
+  if (h->opt.quant_bits > 0) {  // the custom-precision experiment: the input is stored with m mantissa bits
+    PR_CK(h, pr::round_values(h->A.f, (int64_t)n * n, h->opt.quant_bits, h->A.f, h->stream));
+    h->st.launches += 1;
+  }
   PR_CK(h, pr::validate(h->A.f, n, h->scal, h->stream));
   PR_CK(h, pr::abs_norms(h->A.f, n, h->work, h->scal + 4, h->stream));
   h->st.launches += 4;

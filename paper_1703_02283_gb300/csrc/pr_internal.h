@@ -144,6 +144,18 @@ cudaError_t gemm_emu_batched(const __half* DX, const int* ex, const __half* DY, 
                              const int* nitems_dev, const EmuBatchMat* mats, const Epilogue& e, long long* scratch,
                              int* err, unsigned long long* tstamp, cudaStream_t s, int bn = 96);
 
+// ---- the custom-precision experiment (k_quant.cu): m stored mantissa bits, round to nearest even
+// gemm_round: P = X Y with every product and partial sum rounded (order k = 0, 1, ...); quant_update:
+// out = (((p + 1) C - T) / p) one rounded operation at a time (out may be T); quant_sym: out = rnd(W + W^T) / 2;
+// round_values: out = rnd(x) (out may be x); resid_rows: per 8 rows the FP64 sum of (delta_ij - T_ij)^2
+// (resid_row_partials(n) values).
+cudaError_t gemm_round(const double* X, const double* Y, int n, int m, double* P, cudaStream_t s);
+cudaError_t quant_update(const double* C, const double* T, int n, int p, int m, double* out, cudaStream_t s);
+cudaError_t quant_sym(const double* W, int n, int m, double* out, cudaStream_t s);
+cudaError_t round_values(const double* x, int64_t total, int m, double* out, cudaStream_t s);
+int resid_row_partials(int n);
+cudaError_t resid_rows(const double* T, int n, double* partial, cudaStream_t s);
+
 // ---- elementwise and reductions (k_elementwise.cu)
 // scal[0] = max |a_ij|, scal[1] = max |a_ij - a_ji|, scal[2] = #non-finite, scal[3] = #non-positive diagonal
 // entries + #diagonal blocks of order 64 without a Cholesky factorisation (A not positive definite if > 0)

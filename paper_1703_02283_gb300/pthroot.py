@@ -24,6 +24,7 @@ PR_NPREC = 5
 PREC_NAMES = {PR_FP64: "fp64", PR_EMU64: "emu64", PR_FP32X: "fp32x", PR_BF16: "bf16", PR_FP8: "fp8"}
 PR_FORM_AUTO, PR_FORM_COUPLED, PR_FORM_NS, PR_FORM_LITERAL = 0, 1, 2, 3
 PR_C0_EQ3, PR_C0_SCALED_I, PR_C0_POLY = 0, 1, 2
+PR_QUANT_STORAGE, PR_QUANT_ARITH = 1, 2
 PR_MLP_PARAMS = 4996
 
 
@@ -33,7 +34,7 @@ class pr_options(ctypes.Structure):
                 ("sym_tol", ctypes.c_double), ("reanchor", ctypes.c_int), ("emu_slices", ctypes.c_int),
                 ("stag_below_lowp", ctypes.c_double), ("c0_coef", ctypes.c_double * 4), ("gate_max", ctypes.c_double),
                 ("gate_iters", ctypes.c_int), ("verify", ctypes.c_int), ("gate_fallback", ctypes.c_int),
-                ("emu_tile", ctypes.c_int)]
+                ("emu_tile", ctypes.c_int), ("quant_bits", ctypes.c_int), ("quant_mode", ctypes.c_int)]
 
 
 class pr_stats_t(ctypes.Structure):

@@ -25,6 +25,7 @@ def run_bench(*args):
     ("--n", "256", "--lam-min", "1e-2", "--p", "1,2"),
     ("--workload", "batched", "--count", "3"),
     ("--workload", "learned", "--learned-n", "200", "--train-seqs", "1", "--test-seqs", "1", "--every", "100"),
+    ("--workload", "f1", "--f1-n", "64", "--f1-iters", "3"),
 ])
 def test_reference_line_has_the_contract_keys(args):
     d = run_bench(*args, "--steps", "2", "--warmup", "3")
