@@ -694,9 +694,10 @@ def measure_learned(args, world, rank, local, dist, steps, warmup, e2e_on, cpu_o
 # ----------------------------------------------------------------------------- the paper's precision experiment
 
 def f1_matrix(n: int):
-    """The overlap stand-in of the experiment (Sec. 4.3: N = 768, p = 2): n points of the 2048-point density,
-    seeded 7000 + n, and its exact inverse square root from a LAPACK eigendecomposition (host)."""
-    S = W.overlap_matrix(W.overlap_points(n, 20.0 * (n / 2048) ** (1 / 3), 7000 + n))
+    """The overlap stand-in of the experiment (Sec. 4.3: N = 768, p = 2): n points uniform in a cube of side 20
+    (kappa about 20 at n = 768, the recipe the survey probed), seeded 7000 + n, and its exact inverse square
+    root from a LAPACK eigendecomposition (host)."""
+    S = W.overlap_matrix(W.overlap_points(n, 20.0, 7000 + n))
     lam, V = np.linalg.eigh(S)
     return S, (V * lam ** -0.5) @ V.T
 
@@ -758,6 +759,56 @@ def measure_f1(args, local):
         table[name] = rows
     torch.cuda.synchronize(dev)
     return {"value": (time.perf_counter() - t0) * 1e3, "table": table, "reference_norm": zn}
+
+
+def measure_large(args, local):
+    """The large recipe (n = 16384, kappa = 1e4, p = 2, the matrix built on the device, scaled-identity start):
+    the FP8 -> BF16 -> split-FP32 ladder, and the all-EMU64 solve, each timed once after a short untimed pass
+    that tunes and allocates. Errors: relative Frobenius error on a sampled 64 x 64 block of the closed form
+    Q diag(lam^-1/2) Q^T (rows I, columns I) and the true residual of the library's own evaluation."""
+    import torch
+
+    from oracle import pthroot_oracle as O
+    from paper_1703_02283_gb300 import pthroot as P
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    n, p = W.LARGE_CASE["n"], W.LARGE_CASE["p"]
+    case = W.spd_from_spectrum_device(n, W.LARGE_CASE["lam_min"], W.LARGE_CASE["seed"], dev)
+    rng = np.random.default_rng(16384)
+    I = np.sort(rng.choice(n, 64, replace=False))
+    QI = case.Q[I].cpu().numpy()
+    Zb = O.closed_form_block(QI, QI, case.lam, p)
+    del case.Q
+    torch.cuda.empty_cache()
+    out = {"workload": f"SPD n={n}, kappa=1e4, p={p}, scaled-identity C_0, tol {args.tol:g}"}
+    for name, rungs in (("ladder_fp8_bf16_fp32x", [P.PR_FP8, P.PR_BF16, P.PR_FP32X]), ("emu64", [P.PR_EMU64])):
+        o = P.pr_default_options()
+        o.c0 = P.PR_C0_SCALED_I
+        h = P.pr_init(case.A, n, p, o, stream.cuda_stream)
+        try:
+            for prec in rungs:  # tune and allocate outside the timed solve
+                P.pr_iterate(h, 1, prec, args.tol)
+            P.pr_load(h, case.A)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, steps = P.pr_solve_ladder(h, rungs, None, args.tol)
+            e1.record(stream)
+            e1.synchronize()
+            s = P.pr_stats(h)
+            C = torch.empty((n, n), dtype=torch.float64, device=dev)
+            P.pr_result(h, C)
+            Cb = C[I][:, I].cpu().numpy()
+            del C
+        finally:
+            P.pr_destroy(h)
+        out[name] = {"ms": e0.elapsed_time(e1), "status": P.STATUS_NAMES[st], "iterations": steps,
+                     "iterations_by_precision": {PREC_NAMES[k]: s["iterations_by_precision"][k]
+                                                 for k in range(P.PR_NPREC) if s["iterations_by_precision"][k]},
+                     "true_residual": s["true_residual"],
+                     "rel_error_sampled_block": float(np.linalg.norm(Cb - Zb) / np.linalg.norm(Zb))}
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_f1(args):
@@ -858,8 +909,8 @@ def main():
                        "iterations_by_precision": {PREC_NAMES[k]: s["iterations_by_precision"][k]
                                                    for k in range(P.PR_NPREC) if s["iterations_by_precision"][k]},
                        "switch_iteration": s["switch_iteration"],
-                       "emu_tiles": {"sym": [s["emu_tile_n"][0], s["emu_tile_split"][0]],
-                                     "full": [s["emu_tile_n"][1], s["emu_tile_split"][1]]}}
+                       "emu_variant": {"sym": {"tile_n": s["emu_tile_n"][0], "split": s["emu_tile_split"][0]},
+                                       "full": {"tile_n": s["emu_tile_n"][1], "split": s["emu_tile_split"][1]}}}
         return info
 
     def barrier():
@@ -1019,6 +1070,11 @@ def main():
             except Exception as exc:  # a failing summary must not hide the headline
                 extra[name] = {"error": f"{type(exc).__name__}: {exc}"}
             torch.cuda.empty_cache()
+        try:
+            extra["large"] = measure_large(args, local)
+        except Exception as exc:
+            extra["large"] = {"error": f"{type(exc).__name__}: {exc}"}
+        torch.cuda.empty_cache()
         try:
             r1 = measure_f1(args, local)
             extra["f1"] = {"ms": r1["value"], "reference_norm": r1["reference_norm"], **r1["table"]}

@@ -138,7 +138,7 @@ typedef struct {
                           (pr_init then creates no handle; pr_load and pr_set_initial_guess leave Eq. 3's
                           C_0 in the handle)                                                              */
   int emu_tile;        /* digit-slice products (PR_EMU64, PR_FP32X): output tile width. 0 (default) tunes:
-                          the first product of each kind (symmetric / full, per precision) times every work-list
+                          the first product of each kind (symmetric / full, per precision) times every kernel
                           variant of this order (tiles 128 x 96 or 128 x 48, whole or split over K into two
                           halves when the tiles fill fewer than 4 waves of the SMs) and keeps the fastest; the
                           choice is remembered for the process per (order, kind, digit planes). 96 or 48 fix
@@ -185,6 +185,9 @@ typedef struct {
   int emu_tile_n[2];        /* PR_EMU64 products, symmetric [0] and full [1]: tile width in use (0: none yet) */
   int emu_tile_split[2];    /* ... and whether their tiles are split over K                               */
   double emu_tune_ms;       /* time the tuner of pr_options.emu_tile spent on trial launches in this handle */
+  double emu_variant_ms[2][4]; /* PR_EMU64 products tuned in this handle, symmetric [0] and full [1]: the best
+                                  trial time (ms) of each variant, index (width 48 ? 2 : 0) + (split ? 1 : 0),
+                                  0 where not tried (the variant does not apply, or the choice was known) */
 } pr_stats_t;
 
 /* Fills *opt with the defaults listed above. */

@@ -173,7 +173,8 @@ pr_status sync(pr_handle h) {
 }
 
 // The work-list variants of the digit-slice products: tile width (output columns per tile) and whether every
-// tile is split over K into two halves run by neighbouring CTAs.
+// tile is split over K into two halves run by neighbouring CTAs. All give bit-identical products, and the
+// same residual partials for one tile width.
 struct EmuVariant {
   int bn, split;
 };
@@ -260,6 +261,7 @@ pr_status choose_emu_variant(pr_handle h, int m, int pc, int S, Launch&& launch)
           h->st.launches += 1;
         }
         h->st.emu_tune_ms += t * 2;
+        if (pc == 0) h->st.emu_variant_ms[m][v] = t;
         if (t < best) {
           best = t;
           pick = v;

@@ -49,10 +49,12 @@ class pr_stats_t(ctypes.Structure):
                 ("gemm_ms_by_precision", ctypes.c_double * PR_NPREC),
                 ("gemm_flops_by_precision", ctypes.c_double * PR_NPREC), ("c0_gate", ctypes.c_double),
                 ("true_residual", ctypes.c_double), ("prescale_log2", ctypes.c_int),
-                ("emu_tile_n", ctypes.c_int * 2), ("emu_tile_split", ctypes.c_int * 2), ("emu_tune_ms", ctypes.c_double)]
+                ("emu_tile_n", ctypes.c_int * 2), ("emu_tile_split", ctypes.c_int * 2),
+                ("emu_tune_ms", ctypes.c_double), ("emu_variant_ms", (ctypes.c_double * 4) * 2)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["emu_variant_ms"] = [list(r) for r in self.emu_variant_ms]
         for k in ("iterations_by_precision", "gemms_timed_by_precision", "gemm_ms_by_precision",
                   "gemm_flops_by_precision", "emu_tile_n", "emu_tile_split"):
             d[k] = list(getattr(self, k))
