@@ -12,8 +12,8 @@
 //    The digits are small integers, exact in FP16. Integer arithmetic only.
 //  * products (k_gemm_emu): P_ij = 2^(e_i + f_j) sum_{L=2..S+1} 2^(-8L) V_L with the level sums
 //    V_L = sum_{s + t = L} sum_k dX_s,ik dY_t,jk. Each digit product is at most 2^14 in magnitude, so a
-//    level (at most 8 pairs) summed over 128 values of k stays within 2^24 and the FP32 accumulation of
-//    the tensor cores is exact. Dropping the pairs with s + t > S + 1 and the digits beyond S leaves an
+//    level of m pairs summed over 16 P values of k with m P <= 64 stays within 2^24 and the FP32
+//    accumulation of the tensor cores is exact (P = 8 steps for the 8-pair level, up to 64 for one pair). Dropping the pairs with s + t > S + 1 and the digits beyond S leaves an
 //    error of about (S + 2) 2^(-8S - 2) in units of 2^(e_i + f_j) per product term: S = 8 (the default)
 //    gives 2^-63. F must fit in 64-bit integers, which limits S to 8.
 //
@@ -30,9 +30,10 @@
 // (matrix, tile row, tile column). Tensor memory holds four FP32 level accumulators of 96 columns and two
 // 64-column buffers of X planes, so a tile takes two passes over k: levels 2..5 (digits 1..4 only) and
 // levels 6..9. 640 threads: warp 0 TMA producer (4-stage ring), warp 1 copies the X planes into TMEM,
-// warps 2-3 issue the MMAs (warp w owns accumulators 3 - w and w: 5 and 13 pairs per step), warps 4-19
-// epilogue (four warps per TMEM lane quadrant, 24 columns each). An accumulator is drained every 8
-// steps, staggered one every second step: the epilogue warps load its columns, release it, convert the
+// warps 2-3 issue the MMAs (warp w owns accumulators 3 - w and w: 5 and 13 pairs per step; all 32 lanes
+// run the loop on warp-uniform values and one elected lane issues each instruction), warps 4-19 epilogue
+// (four warps per TMEM lane quadrant, 24 columns each). An accumulator is drained every P steps (8 to 64,
+// by its level's pair count), staggered: the epilogue warps load its columns, release it, convert the
 // exact FP32 values to integers and add them, shifted, into an exact int64 total per element. The
 // first pass's totals wait in a scratch buffer; at the tile's end the 128-bit total hi 2^32 + lo is
 // rounded once to FP64 (integer arithmetic), scaled by 2^(e_i + f_j) and the fused epilogue applied.
@@ -251,33 +252,26 @@ __device__ __noinline__ double wide_to_double(long long H, unsigned long long Lw
 // The MMAs of one level L for S = 8 (pairs s = 1 .. L - 1, t = L - s), unrolled: X plane s - 1 from TMEM
 // buffer aT, Y plane t - 1 from the shared-memory stage whose first plane group has descriptor bdesc.
 template <int BN, int L>
-__device__ __forceinline__ void mma_level(uint32_t d, uint32_t aT, uint64_t bdesc, bool fresh) {
-  using T = EmuTile<BN>;
+struct MmaLevel {
+  __device__ __forceinline__ void operator()(uint32_t d, uint32_t aT, uint64_t bdesc, bool fresh) const {
+    using T = EmuTile<BN>;
 #pragma unroll
-  for (int s = 1; s <= L - 1; ++s) {
-    const int t = L - s - 1;
-    ptx::mma_f16_ts(d, aT + 8 * (s - 1), bdesc + (uint64_t)(((t >> 2) * T::B_GROUP + (t & 3) * 32) >> 4), T::kIdesc,
-                    (fresh && s == 1) ? 0u : 1u);
+    for (int s = 1; s <= L - 1; ++s) {
+      const int t = L - s - 1;
+      ptx::mma_f16_ts_w(d, aT + 8 * (s - 1), bdesc + (uint64_t)(((t >> 2) * T::B_GROUP + (t & 3) * 32) >> 4),
+                        T::kIdesc, (fresh && s == 1) ? 0u : 1u);
+    }
   }
-}
+};
 
-template <int BN>
-__device__ __forceinline__ void mma_level_s8(int L, uint32_t d, uint32_t aT, uint64_t bdesc, bool fresh) {
-  switch (L) {
-    case 2: mma_level<BN, 2>(d, aT, bdesc, fresh); break;
-    case 3: mma_level<BN, 3>(d, aT, bdesc, fresh); break;
-    case 4: mma_level<BN, 4>(d, aT, bdesc, fresh); break;
-    case 5: mma_level<BN, 5>(d, aT, bdesc, fresh); break;
-    case 6: mma_level<BN, 6>(d, aT, bdesc, fresh); break;
-    case 7: mma_level<BN, 7>(d, aT, bdesc, fresh); break;
-    case 8: mma_level<BN, 8>(d, aT, bdesc, fresh); break;
-    default: mma_level<BN, 9>(d, aT, bdesc, fresh); break;
-  }
+// Drain period of level L: the largest power of two P <= 64 with m P <= 64 for the level's m digit pairs
+// (m pairs x P steps x 16 values of k x 2^14 <= 2^24 keeps the level's FP32 sum exact). Accumulator a of a
+// pass is drained after step j when (j + 2a) % P == P - 1 (the offsets stagger the drains) and after the
+// pass's last step.
+__device__ __forceinline__ int drain_period(int L, int S) {
+  const int m = min(S, L - 1) - max(1, L - S) + 1;
+  return m <= 1 ? 64 : m <= 2 ? 32 : m <= 4 ? 16 : 8;
 }
-
-// Accumulator a of a pass is drained after step j when (j + 2a) % 8 == 7 (staggered: one drain every
-// second step; 8 pairs x 8 steps x 16 x 2^14 = 2^24 keeps every level exact) and after the pass's last step.
-__device__ __forceinline__ bool drains_after(int a, int j) { return ((j + 2 * a) & 7) == 7; }
 
 template <int BN, bool SYM, bool SPLIT>
 __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (5 warps per sub-partition)
@@ -392,74 +386,111 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
       ptx::mbar_wait(drain, 0, nullptr, 0);
     }
   } else if (warp < 2 + MMA_WARPS) {
-    if (lane == 0) {
-      // ---------------- MMA warp w: accumulators a = 3 - w and w of each pass (levels 5 - w, 2 + w in the first
-      // pass, 9 - w, 6 + w in the second: 5 and 13 pairs per step for S = 8, the same for both warps).
-      const int w = warp - 2;
-      uint32_t fresh = 3u, drained = 0u, par = 0u;  // per own accumulator k (a = k == 0 ? 3 - w : w)
-      int it = 0;
-      bool stop = false;
-      for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
-        int bi, bj, kpart, j0, j1;
-        item_of<SPLIT>(args, t, bi, bj, kpart, j0, j1);
-        const int KS = j1 - j0;
-        for (int pass = 0; pass < npass && !stop; ++pass) {
-          for (int j = 0; j < KS && !stop; ++j, ++it) {
-            const int st = it % NSTAGE, b = it & 1;
-            if (*s_abort || !ptx::mbar_wait(full0 + 8 * st, (it / NSTAGE) & 1, args.err, 14) ||
-                !ptx::mbar_wait(aready0 + 8 * b, (it >> 1) & 1, args.err, 15)) {
-              *s_abort = 1;
-              stop = true;
-              break;
-            }
+    // ---------------- MMA warp w: accumulators aH = 3 - w and aL = w of each pass (levels 5 - w, 2 + w in the
+    // first pass, 9 - w, 6 + w in the second: 5 and 13 pairs per step for S = 8, the same for both warps).
+    // All 32 lanes run the loop on warp-uniform values; one elected lane issues each tcgen05 instruction.
+    const int w = warp - 2;
+    uint32_t drained = 0u, par = 0u;  // per own accumulator (bit 0: aH, bit 1: aL): drained once / drain parity
+    int it = 0;
+    bool stop = false;
+    const uint64_t bdesc0 = ptx::desc_sw128_kmajor(ptx::smem_u32(ring) + A_BYTES);
+    const uint32_t aT0 = tmem + (uint32_t)ACOL;
+    auto wait_all = [&](uint32_t bar, uint32_t parity, int code) {
+      return __all_sync(0xffffffffu, ptx::mbar_wait(bar, parity, args.err, code));
+    };
+    // One pass over KS steps with the level issuers iH, iL (iX(d, aT, bdesc, fresh) issues the level's MMAs).
+    auto run_pass = [&](auto iH, auto iL, bool useH, bool useL, int pass, int KS) -> bool {
+      const int aH = 3 - w, aL = w, LH = 2 + 4 * pass + aH, LL = 2 + 4 * pass + aL;
+      const uint32_t dH = tmem + (uint32_t)(BN * aH), dL = tmem + (uint32_t)(BN * aL);
+      const int pmH = drain_period(LH, S) - 1, pmL = drain_period(LL, S) - 1;
+      bool fH = true, fL = true;  // the next MMA into the accumulator starts it afresh
+      for (int j = 0; j < KS; ++j, ++it) {
+        const int st = it % NSTAGE, b = it & 1;
+        if (!wait_all(full0 + 8 * st, (it / NSTAGE) & 1, 14) || !wait_all(aready0 + 8 * b, (it >> 1) & 1, 15))
+          return false;
+        ptx::tc_fence_after();
+        const uint64_t bdesc = bdesc0 + (uint64_t)((st * STAGE_BYTES) >> 4);
+        const uint32_t aT = aT0 + (uint32_t)(64 * b);
+        const bool last = j == KS - 1;
+        // A level restarting after a drain waits for the epilogue's release; it goes second.
+        const bool waitH = useH && fH && (drained & 1u), waitL = useL && fL && (drained & 2u);
+        auto doH = [&]() -> bool {
+          if (!useH) return true;
+          if (waitH) {
+            if (!wait_all(lempty0 + 8 * aH, (par & 1u) ^ 1u, 16)) return false;
             ptx::tc_fence_after();
-            const uint64_t bdesc = ptx::desc_sw128_kmajor(ptx::smem_u32(ring + st * STAGE_BYTES) + A_BYTES);
-            const uint32_t aT = tmem + (uint32_t)(ACOL + 64 * b);
-            const bool last = j == KS - 1;
-            // An accumulator being drained (fresh after a drain) goes second.
-            const int first = ((fresh & 1u) && (drained & 1u)) ? 1 : 0;
-            for (int q = 0; q < 2; ++q) {
-              const int k = q == 0 ? first : 1 - first;
-              const int a = k == 0 ? 3 - w : w;
-              const int L = 2 + 4 * pass + a;
-              if (L > S + 1) continue;
-              const uint32_t bit = 1u << k;
-              const bool fr = (fresh & bit) != 0;
-              if (fr && (drained & bit)) {
-                if (*s_abort || !ptx::mbar_wait(lempty0 + 8 * a, ((par >> k) & 1u) ^ 1u, args.err, 16)) {
-                  *s_abort = 1;
-                  stop = true;
-                  break;
-                }
-                ptx::tc_fence_after();
-              }
-              const uint32_t d = tmem + (uint32_t)(BN * a);
-              if (S == SMAX) {
-                mma_level_s8<BN>(L, d, aT, bdesc, fr);
-              } else {
-                const int s0 = max(1, L - S), s1 = min(S, L - 1);
-                for (int s = s0; s <= s1; ++s) {
-                  const int tt = L - s - 1;
-                  ptx::mma_f16_ts(d, aT + 8 * (s - 1), bdesc + (uint64_t)(((tt >> 2) * B_GROUP + (tt & 3) * 32) >> 4),
-                                  kIdesc, (fr && s == s0) ? 0u : 1u);
-                }
-              }
-              fresh &= ~bit;
-              if (drains_after(a, j) || last) {
-                ptx::mma_commit(lfull0 + 8 * a);
-                par ^= bit;
-                drained |= bit;
-                fresh |= bit;
-              }
-            }
-            if (stop) break;
-            ptx::mma_commit(empty0 + 8 * st);
+          }
+          iH(dH, aT, bdesc, fH);
+          fH = false;
+          if (last || ((j + 2 * aH) & pmH) == pmH) {
+            ptx::mma_commit_w(lfull0 + 8 * aH);
+            par ^= 1u;
+            drained |= 1u;
+            fH = true;
+          }
+          return true;
+        };
+        auto doL = [&]() -> bool {
+          if (!useL) return true;
+          if (waitL) {
+            if (!wait_all(lempty0 + 8 * aL, ((par >> 1) & 1u) ^ 1u, 16)) return false;
+            ptx::tc_fence_after();
+          }
+          iL(dL, aT, bdesc, fL);
+          fL = false;
+          if (last || ((j + 2 * aL) & pmL) == pmL) {
+            ptx::mma_commit_w(lfull0 + 8 * aL);
+            par ^= 2u;
+            drained |= 2u;
+            fL = true;
+          }
+          return true;
+        };
+        if (waitH ? !(doL() && doH()) : !(doH() && doL())) return false;
+        ptx::mma_commit_w(empty0 + 8 * st);
+      }
+      return true;
+    };
+    // Any S: the level's pairs s = max(1, L - S) .. min(S, L - 1), t = L - s, in a loop.
+    auto level_loop = [&](int L) {
+      return [=](uint32_t d, uint32_t aT, uint64_t bdesc, bool fr) {
+        const int s0 = max(1, L - S), s1 = min(S, L - 1);
+        for (int s = s0; s <= s1; ++s) {
+          const int tt = L - s - 1;
+          ptx::mma_f16_ts_w(d, aT + 8 * (s - 1), bdesc + (uint64_t)(((tt >> 2) * B_GROUP + (tt & 3) * 32) >> 4),
+                            kIdesc, (fr && s == s0) ? 0u : 1u);
+        }
+      };
+    };
+    for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+      int bi, bj, kpart, j0, j1;
+      item_of<SPLIT>(args, t, bi, bj, kpart, j0, j1);
+      const int KS = j1 - j0;
+      for (int pass = 0; pass < npass && !stop; ++pass) {
+        if (__any_sync(0xffffffffu, *s_abort != 0)) {
+          stop = true;
+          break;
+        }
+        bool ok;
+        // S = 8: the four (warp, pass) level pairs with every MMA unrolled at compile time.
+        switch (S == SMAX ? 2 * pass + w : -1) {
+          case 0: ok = run_pass(MmaLevel<BN, 5>{}, MmaLevel<BN, 2>{}, true, true, pass, KS); break;
+          case 1: ok = run_pass(MmaLevel<BN, 4>{}, MmaLevel<BN, 3>{}, true, true, pass, KS); break;
+          case 2: ok = run_pass(MmaLevel<BN, 9>{}, MmaLevel<BN, 6>{}, true, true, pass, KS); break;
+          case 3: ok = run_pass(MmaLevel<BN, 8>{}, MmaLevel<BN, 7>{}, true, true, pass, KS); break;
+          default: {
+            const int LH = 5 - w + 4 * pass, LL = 2 + w + 4 * pass;
+            ok = run_pass(level_loop(LH), level_loop(LL), LH <= S + 1, LL <= S + 1, pass, KS);
           }
         }
+        if (!ok) {
+          *s_abort = 1;
+          stop = true;
+        }
       }
-      ptx::mma_commit(drain);
-      ptx::mbar_wait(drain, 0, nullptr, 0);
     }
+    ptx::mma_commit_w(drain);
+    ptx::mbar_wait(drain, 0, nullptr, 0);
   } else {
     // ---------------- epilogue warps: quadrant q (TMEM lanes 32q..), column quarter h (24 columns)
     const int ew = warp - 2 - MMA_WARPS, q = warp & 3, h = ew >> 2;
@@ -478,11 +509,17 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
 #pragma unroll
       for (int c = 0; c < EPI_COLS; ++c) acc[c] = 0;
       for (int pass = 0; pass < npass && !stop; ++pass) {
+        int pm[NACC];  // drain period - 1 of each accumulator's level; -1: the level is empty
+#pragma unroll
+        for (int a = 0; a < NACC; ++a) {
+          const int L = 2 + 4 * pass + a;
+          pm[a] = L > S + 1 ? -1 : drain_period(L, S) - 1;
+        }
         for (int j = 0; j < KS && !stop; ++j) {
           const bool lastj = j == KS - 1;
+#pragma unroll
           for (int a = 0; a < NACC; ++a) {
-            const int L = 2 + 4 * pass + a;
-            if (L > S + 1 || !(lastj || drains_after(a, j))) continue;
+            if (pm[a] < 0 || !(lastj || ((j + 2 * a) & pm[a]) == pm[a])) continue;
             if (__shfl_sync(0xffffffffu, *s_abort, 0)) {
               stop = true;
               break;
