@@ -355,36 +355,66 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
-      // ---------------- copy thread: per step, the X planes of the pass into TMEM buffer (step & 1), once
-      // the MMAs of two steps back (the last readers of that buffer) have finished.
-      int it = 0;
-      bool stop = false;
-      for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
-        int bi, bj, kpart, j0, j1;
-        item_of<SPLIT>(args, t, bi, bj, kpart, j0, j1);
-        for (int pass = 0; pass < npass && !stop; ++pass) {
-          const int np = pass == 0 ? min(S, 4) : S;
-          for (int j = j0; j < j1; ++j, ++it) {
-            const int st = it % NSTAGE, b = it & 1;
-            if (*s_abort || !ptx::mbar_wait(full0 + 8 * st, (it / NSTAGE) & 1, args.err, 12) ||
-                (it >= 2 && !ptx::mbar_wait(empty0 + 8 * ((it - 2) % NSTAGE), ((it - 2) / NSTAGE) & 1, args.err, 13))) {
-              *s_abort = 1;
-              stop = true;
-              break;
-            }
-            ptx::tc_fence_after();
-            const uint32_t sa = ptx::smem_u32(ring + st * STAGE_BYTES), aT = tmem + (uint32_t)(ACOL + 64 * b);
-            for (int s = 0; s < np; ++s)
-              ptx::tmem_cp_128x256b(aT + 8 * s, ptx::desc_sw128_kmajor(sa + (s >> 2) * A_GROUP + (s & 3) * 32));
-            ptx::mma_commit(aready0 + 8 * b);
-            ptx::mma_commit(empty0 + 8 * st);
-          }
+    // ---------------- copy warp: per step, the X planes of the pass into TMEM buffer (step & 1), once the MMAs
+    // of two steps back (the last readers of that buffer) have finished. All 32 lanes run the loop; one
+    // elected lane issues.
+    int it = 0;
+    bool stop = false;
+    const uint64_t xdesc0 = ptx::desc_sw128_kmajor(ptx::smem_u32(ring));
+    const uint32_t aT0 = tmem + (uint32_t)ACOL;
+    auto wait_all = [&](uint32_t bar, uint32_t parity, int code) {
+      return __all_sync(0xffffffffu, ptx::mbar_wait(bar, parity, args.err, code));
+    };
+    // One pass over KS steps; copy(aT, xdesc) copies the pass's planes of the stage with descriptor xdesc.
+    auto run_pass = [&](auto copy, int KS) -> bool {
+      for (int j = 0; j < KS; ++j, ++it) {
+        const int st = it % NSTAGE, b = it & 1;
+        if (!wait_all(full0 + 8 * st, (it / NSTAGE) & 1, 12) ||
+            (it >= 2 && !wait_all(empty0 + 8 * ((it - 2) % NSTAGE), ((it - 2) / NSTAGE) & 1, 13)))
+          return false;
+        ptx::tc_fence_after();
+        copy(aT0 + (uint32_t)(64 * b), xdesc0 + (uint64_t)((st * STAGE_BYTES) >> 4));
+        ptx::mma_commit_w(aready0 + 8 * b);
+        ptx::mma_commit_w(empty0 + 8 * st);
+      }
+      return true;
+    };
+    auto planes = [](uint32_t aT, uint64_t xd, int s) {
+      ptx::tmem_cp_128x256b_w(aT + 8 * s, xd + (uint64_t)(((s >> 2) * A_GROUP + (s & 3) * 32) >> 4));
+    };
+    for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+      int bi, bj, kpart, j0, j1;
+      item_of<SPLIT>(args, t, bi, bj, kpart, j0, j1);
+      for (int pass = 0; pass < npass && !stop; ++pass) {
+        if (__any_sync(0xffffffffu, *s_abort != 0)) {
+          stop = true;
+          break;
+        }
+        const int np = pass == 0 ? min(S, 4) : S;
+        bool ok;
+        if (np == 4) {
+          ok = run_pass([&](uint32_t aT, uint64_t xd) {
+#pragma unroll
+            for (int s = 0; s < 4; ++s) planes(aT, xd, s);
+          }, j1 - j0);
+        } else if (np == 8) {
+          ok = run_pass([&](uint32_t aT, uint64_t xd) {
+#pragma unroll
+            for (int s = 0; s < 8; ++s) planes(aT, xd, s);
+          }, j1 - j0);
+        } else {
+          ok = run_pass([&](uint32_t aT, uint64_t xd) {
+            for (int s = 0; s < np; ++s) planes(aT, xd, s);
+          }, j1 - j0);
+        }
+        if (!ok) {
+          *s_abort = 1;
+          stop = true;
         }
       }
-      ptx::mma_commit(drain);
-      ptx::mbar_wait(drain, 0, nullptr, 0);
     }
+    ptx::mma_commit_w(drain);
+    ptx::mbar_wait(drain, 0, nullptr, 0);
   } else if (warp < 2 + MMA_WARPS) {
     // ---------------- MMA warp w: accumulators aH = 3 - w and aL = w of each pass (levels 5 - w, 2 + w in the
     // first pass, 9 - w, 6 + w in the second: 5 and 13 pairs per step for S = 8, the same for both warps).

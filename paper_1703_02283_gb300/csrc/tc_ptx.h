@@ -134,10 +134,15 @@ __device__ __forceinline__ void mma_commit_w(uint32_t bar) {
       : "memory");
 }
 
-// Copies a 128-row x 256-bit matrix from shared memory (matrix descriptor) into TMEM: row r to lane r,
-// 8 consecutive columns from taddr. Ordered before later tcgen05.mma of the same thread.
-__device__ __forceinline__ void tmem_cp_128x256b(uint32_t taddr, uint64_t sdesc) {
-  asm volatile("tcgen05.cp.cta_group::1.128x256b [%0], %1;" ::"r"(taddr), "l"(sdesc) : "memory");
+// Warp-collective: one elected lane copies a 128-row x 256-bit matrix from shared memory (matrix descriptor)
+// into TMEM: row r to lane r, 8 consecutive columns from taddr. Ordered before later tcgen05.mma of the same
+// thread.
+__device__ __forceinline__ void tmem_cp_128x256b_w(uint32_t taddr, uint64_t sdesc) {
+  asm volatile(
+      "{\n\t.reg .pred e;\n\t"
+      "elect.sync _|e, 0xffffffff;\n\t"
+      "@e tcgen05.cp.cta_group::1.128x256b [%0], %1;\n\t}\n" ::"r"(taddr), "l"(sdesc)
+      : "memory");
 }
 
 // Arrives once on bar when every tcgen05.mma issued so far by this thread has completed.
