@@ -45,12 +45,9 @@ METRIC = "time to FP64-accurate A^(-1/p) vs plain FP64 GPU; GEMM TFLOP/s, % of p
 NOMINAL_BF16_TFLOPS = 2250.0
 NOMINAL_FP64_TFLOPS = 1.25
 PREC_NAMES = {0: "fp64", 1: "emu64", 2: "fp32x", 3: "bf16", 4: "fp8"}
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of one symmetric product, by n. Taken before the kernel
-# gained its split-tile variant; the unsplit code path that n = 4096 runs is unchanged (same registers and
-# spills), but until it is captured again the roofline reports it as traffic_last_capture, not traffic.
-EMU_TRAFFIC_BYTES = {4096: 2.371166e9 + 0.200156e9}
-# The same figure from a capture of the kernel as it is now (filled in once one exists).
-EMU_TRAFFIC_CURRENT: dict = {}
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one symmetric product of the kernel as it is now, by n
+# (profiles/k_gemm_emu_n4096.md). A change to the kernel empties this until it is captured again.
+EMU_TRAFFIC_CURRENT: dict = {4096: 2.416207e9 + 0.358885e9}
 
 
 # ----------------------------------------------------------------------------- replicas (N > 1 under torchrun)
@@ -970,11 +967,9 @@ def main():
     if dom == P.PR_EMU64:
         pairs = S * (S + 1) // 2
         exec_fl = dfl * pairs
-        traffic_seen = EMU_TRAFFIC_BYTES.get(args.n) if S == 8 else None
         roofline = {"bound": "tensor", "kernel": "k_gemm_emu (tcgen05 FP16 digit-slice products)",
                     "achieved": exec_fl / (dms * 1e-3) / 1e12, "peak": peaks["bf16_tflops_sustained"],
                     "unit": "TFLOP/s", "traffic": EMU_TRAFFIC_CURRENT.get(args.n) if S == 8 else None,
-                    "traffic_last_capture": traffic_seen,
                     "note": f"algorithmic = the {pairs} FP16 digit-pair products per emulated FP64 product "
                             f"(S={S}), upper-triangle tiles; fp64_equivalent_tflops = FP64 flops / time",
                     "fp64_equivalent_tflops": dfl / (dms * 1e-3) / 1e12,
