@@ -436,8 +436,9 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
       bool fH = true, fL = true;  // the next MMA into the accumulator starts it afresh
       for (int j = 0; j < KS; ++j, ++it) {
         const int st = it % NSTAGE, b = it & 1;
-        if (!wait_all(full0 + 8 * st, (it / NSTAGE) & 1, 14) || !wait_all(aready0 + 8 * b, (it >> 1) & 1, 15))
-          return false;
+        // One wait per step: the copy warp waited for this stage's TMA load before it copied the X planes, so
+        // the completion of its copy (aready) also orders the stage's Y planes before these MMAs.
+        if (!wait_all(aready0 + 8 * b, (it >> 1) & 1, 15)) return false;
         ptx::tc_fence_after();
         const uint64_t bdesc = bdesc0 + (uint64_t)((st * STAGE_BYTES) >> 4);
         const uint32_t aT = aT0 + (uint32_t)(64 * b);
