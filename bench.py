@@ -47,7 +47,7 @@ NOMINAL_FP64_TFLOPS = 1.25
 PREC_NAMES = {0: "fp64", 1: "emu64", 2: "fp32x", 3: "bf16", 4: "fp8"}
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one symmetric product of the kernel as it is now, by n
 # (profiles/k_gemm_emu_n4096.md). A change to the kernel empties this until it is captured again.
-EMU_TRAFFIC_CURRENT: dict = {4096: 2.416207e9 + 0.358885e9}
+EMU_TRAFFIC_CURRENT: dict = {}
 
 
 # ----------------------------------------------------------------------------- replicas (N > 1 under torchrun)
@@ -760,7 +760,8 @@ def measure_f1(args, local):
 
 def measure_large(args, local):
     """The large recipe (n = 16384, kappa = 1e4, p = 2, the matrix built on the device, scaled-identity start):
-    the FP8 -> BF16 -> split-FP32 ladder, and the all-EMU64 solve, each timed once after a short untimed pass
+    the FP8 -> BF16 -> split-FP32 ladder, the same ladder ending in EMU64, and the all-EMU64 solve, each timed
+    once after a short untimed pass
     that tunes and allocates. Errors: relative Frobenius error on a sampled 64 x 64 block of the closed form
     Q diag(lam^-1/2) Q^T (rows I, columns I) and the true residual of the library's own evaluation."""
     import torch
@@ -778,7 +779,9 @@ def measure_large(args, local):
     del case.Q
     torch.cuda.empty_cache()
     out = {"workload": f"SPD n={n}, kappa=1e4, p={p}, scaled-identity C_0, tol {args.tol:g}"}
-    for name, rungs in (("ladder_fp8_bf16_fp32x", [P.PR_FP8, P.PR_BF16, P.PR_FP32X]), ("emu64", [P.PR_EMU64])):
+    for name, rungs in (("ladder_fp8_bf16_fp32x", [P.PR_FP8, P.PR_BF16, P.PR_FP32X]),
+                        ("ladder_fp8_bf16_fp32x_emu64", [P.PR_FP8, P.PR_BF16, P.PR_FP32X, P.PR_EMU64]),
+                        ("emu64", [P.PR_EMU64])):
         o = P.pr_default_options()
         o.c0 = P.PR_C0_SCALED_I
         h = P.pr_init(case.A, n, p, o, stream.cuda_stream)
@@ -802,7 +805,7 @@ def measure_large(args, local):
         out[name] = {"ms": e0.elapsed_time(e1), "status": P.STATUS_NAMES[st], "iterations": steps,
                      "iterations_by_precision": {PREC_NAMES[k]: s["iterations_by_precision"][k]
                                                  for k in range(P.PR_NPREC) if s["iterations_by_precision"][k]},
-                     "true_residual": s["true_residual"],
+                     "true_residual": s["true_residual"], "rungs_discarded": s["ladder_restores"],
                      "rel_error_sampled_block": float(np.linalg.norm(Cb - Zb) / np.linalg.norm(Zb))}
         torch.cuda.empty_cache()
     return out

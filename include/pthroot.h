@@ -188,6 +188,7 @@ typedef struct {
   double emu_variant_ms[2][4]; /* PR_EMU64 products tuned in this handle, symmetric [0] and full [1]: the best
                                   trial time (ms) of each variant, index (width 48 ? 2 : 0) + (split ? 1 : 0),
                                   0 where not tried (the variant does not apply, or the choice was known) */
+  int ladder_restores;      /* pr_solve_ladder: rungs whose result was discarded (see pr_solve_ladder)       */
 } pr_stats_t;
 
 /* Fills *opt with the defaults listed above. */
@@ -258,7 +259,16 @@ pr_status pr_solve(pr_handle h, int bulk_precision, int bulk_steps, int final_pr
  * higher precision when the level rises (pr_options.reanchor): PR_FP8 < PR_BF16 < PR_FP32X < PR_FP64 =
  * PR_EMU64. Returns the status of the last rung run; *steps_done (may be NULL) receives the updates of all
  * rungs together. pr_stats.iterations_by_precision and switch_iteration record where each rung ended.
- * Errors: as pr_iterate, and PR_EINVAL for count < 1 or a NULL precisions array. */
+ * Rung guard: a low-precision rung (PR_FP8, PR_BF16, PR_FP32X) followed by a higher level, or last in a
+ * ladder of several, tests the carried ||I - M||_F, which can keep falling while rounding errors let X drift
+ * from M. Before the first such rung and after each, the library evaluates ||I - X^p A||_F with the next
+ * rung's products (PR_EMU64 products after the last rung); a rung that leaves
+ * it above the best value seen so far is discarded (X returns to that best iterate and M is re-formed from
+ * it). A rung after the first that diverges from the iterate the earlier rungs left (a low-precision rung can
+ * leave X^p A indefinite while its Frobenius residual fell) runs once more from the starting iterate.
+ * pr_stats.ladder_restores counts both kinds. This costs p products per guarded boundary and two n*n FP64
+ * buffers, allocated on first use and kept until pr_destroy (PR_ENOMEM if they cannot be).
+ * Errors: as pr_iterate, and PR_EINVAL for count < 1, a NULL precisions array or an unknown precision. */
 pr_status pr_solve_ladder(pr_handle h, int count, const int* precisions, const int* max_steps, double tol,
                           int* steps_done);
 

@@ -93,6 +93,8 @@ struct pr_handle_s {
   double* scal = nullptr;     // device scalars: [0..3] checks, [4..5] norms, [6] residual, [7] error word
   double* hpin = nullptr;     // pinned host mirror of scal
   double* vec = nullptr;      // PR_C0_POLY gate and features: 4n vectors + reduction partials + scalars
+  double* xbest = nullptr;    // pr_solve_ladder: the iterate with the lowest true residual at a rung boundary
+  double* xstart = nullptr;   // pr_solve_ladder: the starting iterate, for a rung that diverges
   bool powers_valid = false;  // T0 = A^2 and T1 = A^3 of the loaded A (features, polynomial guess)
 
   // CUDA-event timing of the product kernels (pr_set_timing).
@@ -818,6 +820,7 @@ void reset_iteration(pr_handle h) {
   h->st.last_precision = -1;
   h->st.last_residual = 0.0;
   h->st.true_residual = -1.0;
+  h->st.ladder_restores = 0;
 }
 
 // C_0 of the loaded A (Eq. 3, the scaled identity, or the gated polynomial) into X.
@@ -979,7 +982,7 @@ pr_status pr_destroy(pr_handle h) {
     if (m->q) cudaFree(m->q);
     if (m->qe) cudaFree(m->qe);
   }
-  for (double* b : {h->partial, h->work, h->scal, h->vec})
+  for (double* b : {h->partial, h->work, h->scal, h->vec, h->xbest, h->xstart})
     if (b) cudaFree(b);
   for (auto& lists : h->emu_items)
     for (int4* it : lists)
@@ -1426,14 +1429,72 @@ pr_status pr_solve_ladder(pr_handle h, int count, const int* precisions, const i
   if (steps_done) *steps_done = 0;
   if (!h) return fail(nullptr, PR_ESTATE, "pr_solve_ladder: NULL handle");
   if (count < 1 || !precisions) return fail(h, PR_EINVAL, "pr_solve_ladder: count < 1 or precisions NULL");
+  for (int r = 0; r < count; ++r) {
+    pr_status s = check_precision(h, precisions[r]);
+    if (s != PR_OK) return s;
+  }
+  cudaSetDevice(h->device);
+  const size_t bytes = (size_t)h->n * (size_t)h->n * sizeof(double);
+  // Rung guard. In the coupled form a low-precision rung tests the carried ||I - M||_F, which can keep
+  // falling while rounding errors let X drift from M. At each boundary after a rung below FP64 accuracy
+  // that hands over to a higher level, the true residual ||I - X^p A||_F is evaluated with the next rung's
+  // products; an iterate worse than the best one seen at such a boundary is replaced by that one, and the
+  // next rung starts from it (M re-formed from X).
+  double best = INFINITY;
+  auto restore = [&](const double* from) -> pr_status {
+    PR_CK(h, cudaMemcpyAsync(h->X.f, from, bytes, cudaMemcpyDeviceToDevice, h->stream));
+    h->X.changed();
+    h->lp_stale = true;
+    h->state_ready = false;
+    h->st.ladder_restores += 1;
+    return sync(h);
+  };
+  auto guard = [&](int next_prec) -> pr_status {
+    double r = 0.0;
+    pr_status s = true_residual(h, next_prec, &r);
+    if (s != PR_OK) return s;
+    if (!h->xbest) PR_CK(h, cudaMalloc((void**)&h->xbest, bytes));
+    if (r <= best) {  // NaN compares false: never kept
+      best = r;
+      PR_CK(h, cudaMemcpyAsync(h->xbest, h->X.f, bytes, cudaMemcpyDeviceToDevice, h->stream));
+      return sync(h);
+    }
+    return restore(h->xbest);
+  };
+  // A rung after the first that diverges from the iterate the earlier rungs left (a low-precision rung can
+  // leave X^p A indefinite while its Frobenius residual fell) runs once more from the starting iterate.
+  bool any_lowp = false;
+  for (int r = 0; r + 1 < count; ++r) any_lowp = any_lowp || lowp(precisions[r]);
+  if (any_lowp) {
+    if (!h->xstart) PR_CK(h, cudaMalloc((void**)&h->xstart, bytes));
+    PR_CK(h, cudaMemcpyAsync(h->xstart, h->X.f, bytes, cudaMemcpyDeviceToDevice, h->stream));
+  }
   int total = 0;
   pr_status s = PR_EINVAL;
   for (int r = 0; r < count; ++r) {
+    // The last rung of a ladder of several is judged with FP64-accurate products.
+    const int next = r + 1 < count ? precisions[r + 1] : PR_EMU64;
+    const bool guarded = count > 1 && lowp(precisions[r]) && precision_level(next) > precision_level(precisions[r]);
+    if (guarded && best == INFINITY) {
+      s = guard(next);  // the starting iterate is the first candidate
+      if (s != PR_OK) return s;
+    }
     int d = 0;
     s = pr_iterate(h, max_steps ? max_steps[r] : (1 << 30), precisions[r], tol, &d);
     total += d;
+    if (s == PR_EDIVERGED && r > 0 && any_lowp) {
+      s = restore(h->xstart);
+      if (s != PR_OK) return s;
+      d = 0;
+      s = pr_iterate(h, max_steps ? max_steps[r] : (1 << 30), precisions[r], tol, &d);
+      total += d;
+    }
     if (steps_done) *steps_done = total;
     if (s != PR_ESTAGNATED && s != PR_EMAXITER && s != PR_EINACCURATE) return s;
+    if (guarded) {
+      pr_status g = guard(next);
+      if (g != PR_OK) return g;
+    }
   }
   return s;
 }

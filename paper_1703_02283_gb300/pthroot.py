@@ -50,7 +50,8 @@ class pr_stats_t(ctypes.Structure):
                 ("gemm_flops_by_precision", ctypes.c_double * PR_NPREC), ("c0_gate", ctypes.c_double),
                 ("true_residual", ctypes.c_double), ("prescale_log2", ctypes.c_int),
                 ("emu_tile_n", ctypes.c_int * 2), ("emu_tile_split", ctypes.c_int * 2),
-                ("emu_tune_ms", ctypes.c_double), ("emu_variant_ms", (ctypes.c_double * 4) * 2)]
+                ("emu_tune_ms", ctypes.c_double), ("emu_variant_ms", (ctypes.c_double * 4) * 2),
+                ("ladder_restores", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}

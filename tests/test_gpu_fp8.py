@@ -231,3 +231,47 @@ def test_large_recipe_ladder_reports_its_error():
     fe = O.forward_error(C, Z)
     print("large-recipe ladder at n = 1024:", by, P.STATUS_NAMES[st], "forward error", fe)
     assert fe < 1.0
+
+
+@pytest.mark.parametrize("n, seed", [(1024, 22), (2048, 23)])
+def test_ladder_guard_keeps_the_best_iterate(n, seed):
+    # The rung guard of pr_solve_ladder: after the ladder of the large recipe (FP8, BF16, split-FP32) from the
+    # scaled identity at kappa = 1e4, p = 2, the true residual of the result (FP64-accurate products) is no
+    # larger than the starting iterate's, whatever the carried ||I - M||_F of a low-precision rung said; the
+    # counts of every rung still add up.
+    case = W.spd_from_spectrum(n, 1e-4, seed)
+    A = torch.from_numpy(case.A).to(DEV)
+    o = P.pr_default_options()
+    o.c0 = P.PR_C0_SCALED_I
+    h = P.pr_init(A, n, 2, o, torch.cuda.current_stream(DEV).cuda_stream)
+    try:
+        r0 = P.pr_residual(h, P.PR_EMU64)
+        st, steps = P.pr_solve_ladder(h, [P.PR_FP8, P.PR_BF16, P.PR_FP32X], None, 1e-12)
+        stats = P.pr_stats(h)
+        r1 = P.pr_residual(h, P.PR_EMU64)
+    finally:
+        P.pr_destroy(h)
+    by = stats["iterations_by_precision"]
+    print(f"n = {n}: start {r0:.3e}, ladder end {r1:.3e}, restores {stats['ladder_restores']}, {by}")
+    assert st != P.PR_EDIVERGED
+    assert np.isfinite(r1) and r1 <= r0 * (1 + 1e-3)
+    assert 0 <= stats["ladder_restores"] <= 3
+    assert steps == by[P.PR_FP8] + by[P.PR_BF16] + by[P.PR_FP32X]
+
+
+def test_ladder_ending_in_emu64_reaches_fp64_accuracy():
+    # The large recipe's ladder with an FP64-accurate last rung (kappa = 1e4, p = 2, order 1024, scaled
+    # identity start): whatever the low-precision rungs leave, the last rung ends at the FP64 oracle's
+    # accuracy (a rung that diverges from their iterate restarts from the starting one).
+    case = W.spd_from_spectrum(1024, 1e-4, 22)
+    Z = O.closed_form_root(case.Q, case.lam, 2)
+    C, st, steps, stats, hist = solve(case, 2, [P.PR_FP8, P.PR_BF16, P.PR_FP32X, P.PR_EMU64],
+                                      c0=P.PR_C0_SCALED_I)
+    Co, info = O.solve(case.A, 2, tol=1e-12, c0="scaled_identity")
+    by = stats["iterations_by_precision"]
+    fe, feo = O.forward_error(C, Z), O.forward_error(Co, Z)
+    print("ladder ending in EMU64:", by, P.STATUS_NAMES[st], "restores", stats["ladder_restores"], "forward error",
+          fe, "oracle", feo)
+    assert st in (P.PR_OK, P.PR_ESTAGNATED, P.PR_EINACCURATE)
+    assert by[P.PR_EMU64] > 0 and steps == sum(by)
+    assert fe <= max(1e-12, 10 * feo)
