@@ -104,64 +104,114 @@ __device__ __forceinline__ long long fixed_point(unsigned long long u, int e, in
   return (u >> 63) ? -F : F;
 }
 
-// One warp per row r of an R-row FP64 array (leading dimension ldx): exponent e_r, then 8 digit planes in
-// the layout D[r][k / 16][s][k % 16] (row length 8 ldl halves, ldl a multiple of 16; s = 0 is the most
-// significant digit, planes s >= S are zero). Row r has row_n[r] valid columns (all rows n when row_n is
-// null); columns from there up to the next multiple of 16 (the last step the products read for that
+// One 128-thread block per row r of an R-row FP64 array (leading dimension ldx): exponent e_r, then 8
+// digit planes in the layout D[r][k / 16][s][k % 16] (row length 8 ldl halves, ldl a multiple of 16; s = 0
+// is the most significant digit, planes s >= S are zero). Row r has row_n[r] valid columns (all rows n when
+// row_n is null); columns from there up to the next multiple of 16 (the last step the products read for that
 // row's matrix) get digit 0, later columns are left as they are; rows with row_n[r] < 0 are skipped.
-// Each lane handles two adjacent columns, so loads are 16 bytes and stores half2.
-__global__ void k_slice(const double* __restrict__ X, int R, int n, int ldx, int ldl, int S,
-                        const int* __restrict__ row_n, __half* __restrict__ D, int* __restrict__ ex) {
-  const int lane = threadIdx.x & 31;
-  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < R; i += (gridDim.x * blockDim.x) >> 5) {
-    const int nr = row_n ? row_n[i] : n;
+// Each thread takes 8 consecutive columns at a time: two 16-byte loads per pair of columns when the row is
+// 16-byte aligned, and one 16-byte store per digit plane (half a step's plane).
+constexpr int SLICE_THREADS = 128;
+
+__device__ __forceinline__ void balanced_digits(long long F, int S, int (&d)[SMAX]) {
+  if (S == SMAX) {
+    // Balanced base-256 digits in 32-bit arithmetic: digit k (least significant first) is
+    // v = byte_k(F) + c minus 256 c' with carry c' = (v >= 128); the top digit is (F >> 56) + c.
+    // (The same digits as the 64-bit recurrence F <- (F - d) >> 8 below.)
+    const unsigned lo = (unsigned)F, hu = (unsigned)(F >> 32);
+    int c = 0;
+#pragma unroll
+    for (int k = 0; k < SMAX - 1; ++k) {
+      const int v = (int)(((k < 4 ? lo >> (8 * k) : hu >> (8 * (k - 4)))) & 255u) + c;
+      c = v >= 128 ? 1 : 0;
+      d[SMAX - 1 - k] = v - 256 * c;
+    }
+    d[0] = ((int)hu >> 24) + c;
+  } else {
+    // Balanced base-256 digits, least significant first (digit S - 1 down to 1); the most significant one
+    // takes the remainder (|.| <= 128); planes S .. 7 are zero.
+#pragma unroll
+    for (int s = SMAX - 1; s >= 1; --s) {
+      if (s < S) {
+        const int r = (int)(F & 255);
+        const int dd = r >= 128 ? r - 256 : r;
+        F = (F - dd) >> 8;
+        d[s] = dd;
+      } else {
+        d[s] = 0;
+      }
+    }
+    d[0] = (int)F;
+  }
+}
+
+__global__ void __launch_bounds__(SLICE_THREADS) k_slice(const double* __restrict__ X, int R, int n, int ldx, int ldl,
+                                                         int S, const int* __restrict__ row_n, __half* __restrict__ D,
+                                                         int* __restrict__ ex) {
+  __shared__ unsigned long long red[SLICE_THREADS / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = blockIdx.x; i < R; i += gridDim.x) {
+    const int nr = row_n ? row_n[i] : n;  // uniform over the block
     if (nr < 0) continue;
-    const unsigned long long* row = reinterpret_cast<const unsigned long long*>(X + (int64_t)i * ldx);
+    const double* rowd = X + (int64_t)i * ldx;
+    const unsigned long long* row = reinterpret_cast<const unsigned long long*>(rowd);
+    const bool vec = (reinterpret_cast<uintptr_t>(rowd) & 15) == 0;
     unsigned long long mb = 0;  // largest |x| as a bit pattern (non-negative doubles order like integers)
-    for (int k = lane; k < nr; k += 32) {
-      const unsigned long long u = row[k] & 0x7fffffffffffffffull;
-      mb = u > mb ? u : mb;
+    for (int k = 8 * threadIdx.x; k < nr; k += 8 * SLICE_THREADS) {
+      if (vec && k + 8 <= nr) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const ulonglong2 u = *reinterpret_cast<const ulonglong2*>(row + k + 2 * q);
+          const unsigned long long a = u.x & 0x7fffffffffffffffull, b = u.y & 0x7fffffffffffffffull;
+          mb = a > mb ? a : mb;
+          mb = b > mb ? b : mb;
+        }
+      } else {
+        for (int q = 0; q < 8 && k + q < nr; ++q) {
+          const unsigned long long a = row[k + q] & 0x7fffffffffffffffull;
+          mb = a > mb ? a : mb;
+        }
+      }
     }
     mb = warp_max_u64(mb);
+    if (lane == 0) red[warp] = mb;
+    __syncthreads();
+    mb = red[0];
+#pragma unroll
+    for (int w = 1; w < SLICE_THREADS / 32; ++w) mb = red[w] > mb ? red[w] : mb;
+    __syncthreads();  // red is reused by the next row
     const int emax = (int)(mb >> 52);               // biased exponent of the row maximum
     const int e = emax == 0 ? 0 : emax - 1023 + 2;  // zero (or subnormal-only) rows get digits 0
-    if (lane == 0) ex[i] = e;
+    if (threadIdx.x == 0) ex[i] = e;
     const int kend = min(ldl, (nr + 15) & ~15);
-    for (int k = 2 * lane; k < kend; k += 64) {
-      long long F0 = 0, F1 = 0;
-      if (emax != 0) {
-        if (k < nr) F0 = fixed_point(row[k], e, S);
-        if (k + 1 < nr) F1 = fixed_point(row[k + 1], e, S);
-      }
-      __half2* dst = reinterpret_cast<__half2*>(D + (int64_t)i * 8 * ldl + (k >> 4) * 128 + (k & 15));
-      if (S == SMAX) {
-        // Balanced base-256 digits in 32-bit arithmetic: digit k (least significant first) is
-        // v = byte_k(F) + c minus 256 c' with carry c' = (v >= 128); the top digit is (F >> 56) + c.
-        // (The same digits as the 64-bit recurrence F <- (F - d) >> 8 below.)
-        const unsigned lo0 = (unsigned)F0, lo1 = (unsigned)F1;
-        const unsigned hu0 = (unsigned)(F0 >> 32), hu1 = (unsigned)(F1 >> 32);
-        int c0 = 0, c1 = 0;
+    for (int k = 8 * threadIdx.x; k < kend; k += 8 * SLICE_THREADS) {
+      unsigned long long u[8];
+      if (vec && k + 8 <= nr) {
 #pragma unroll
-        for (int k = 0; k < SMAX - 1; ++k) {
-          const int v0 = (int)(((k < 4 ? lo0 >> (8 * k) : hu0 >> (8 * (k - 4)))) & 255u) + c0;
-          const int v1 = (int)(((k < 4 ? lo1 >> (8 * k) : hu1 >> (8 * (k - 4)))) & 255u) + c1;
-          c0 = v0 >= 128 ? 1 : 0;
-          c1 = v1 >= 128 ? 1 : 0;
-          dst[8 * (SMAX - 1 - k)] = __floats2half2_rn((float)(v0 - 256 * c0), (float)(v1 - 256 * c1));
+        for (int q = 0; q < 4; ++q) {
+          const ulonglong2 w2 = *reinterpret_cast<const ulonglong2*>(row + k + 2 * q);
+          u[2 * q] = w2.x;
+          u[2 * q + 1] = w2.y;
         }
-        dst[0] = __floats2half2_rn((float)(((int)hu0 >> 24) + c0), (float)(((int)hu1 >> 24) + c1));
       } else {
-        for (int s = S; s < SMAX; ++s) dst[8 * s] = __floats2half2_rn(0.0f, 0.0f);
-        // Balanced base-256 digits, least significant first; the last one takes the remainder (|.| <= 128).
-        for (int s = S - 1; s >= 1; --s) {
-          const int r0 = (int)(F0 & 255), r1 = (int)(F1 & 255);
-          const int d0 = r0 >= 128 ? r0 - 256 : r0, d1 = r1 >= 128 ? r1 - 256 : r1;
-          F0 = (F0 - d0) >> 8;
-          F1 = (F1 - d1) >> 8;
-          dst[8 * s] = __floats2half2_rn((float)d0, (float)d1);
-        }
-        dst[0] = __floats2half2_rn((float)F0, (float)F1);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) u[q] = k + q < nr ? row[k + q] : 0ull;
       }
+      uint32_t h2[SMAX][4];  // plane s, column pair c: two halves
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        int d0[SMAX], d1[SMAX];
+        balanced_digits(emax != 0 && k + 2 * c < nr ? fixed_point(u[2 * c], e, S) : 0ll, S, d0);
+        balanced_digits(emax != 0 && k + 2 * c + 1 < nr ? fixed_point(u[2 * c + 1], e, S) : 0ll, S, d1);
+#pragma unroll
+        for (int s = 0; s < SMAX; ++s) {
+          const __half2 v = __floats2half2_rn((float)d0[s], (float)d1[s]);
+          h2[s][c] = *reinterpret_cast<const uint32_t*>(&v);
+        }
+      }
+      uint4* dst = reinterpret_cast<uint4*>(D + (int64_t)i * 8 * ldl + (k >> 4) * 128 + (k & 15));
+#pragma unroll
+      for (int s = 0; s < SMAX; ++s) dst[2 * s] = make_uint4(h2[s][0], h2[s][1], h2[s][2], h2[s][3]);
     }
   }
 }
@@ -848,10 +898,10 @@ cudaError_t slice(const double* X, int n, int ldl, int S, __half* D, int* ex, cu
 cudaError_t slice_rows(const double* X, int R, int n, int ldx, int ldl, int S, const int* row_n, __half* D, int* ex,
                        cudaStream_t s) {
   if (S < 1 || S > SMAX || ldl % 16 != 0) return cudaErrorInvalidValue;
-  int blocks = (R + 7) / 8;  // 8 warps (rows) per block
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  int blocks = R;  // one block per row, up to 16 resident blocks per SM
+  if (blocks > sm_count_emu() * 16) blocks = sm_count_emu() * 16;
   if (blocks < 1) return cudaSuccess;
-  k_slice<<<blocks, 256, 0, s>>>(X, R, n, ldx, ldl, S, row_n, D, ex);
+  k_slice<<<blocks, SLICE_THREADS, 0, s>>>(X, R, n, ldx, ldl, S, row_n, D, ex);
   return cudaGetLastError();
 }
 
