@@ -692,7 +692,7 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
       // Tile end: P = 2^(e_i + f_j - 72) (hi 2^32 + lo), then the fused epilogue (FP64 values, FP32 partials).
       const int i = bi * EBM + 32 * q + lane;
       const int ei = i < n ? args.ex[row0 + i] : 0;
-      float part = 0.0f;
+      double part = 0.0;  // the tile's share of ||I - P||_F^2, accumulated in FP64
 #pragma unroll
       for (int c = 0; c < EPI_COLS; ++c) {
         const int jc = bj * BN + EPI_COLS * h + c;
@@ -703,8 +703,8 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
         const long long H = (hi >> 32) + (lo >> 63) + (lw < lw0 ? 1 : 0);
         const double P = wide_to_double(H, lw, ei + args.ey[row0 + jc] - 72);
         if (e.partial) {
-          const float dd = i == jc ? (float)(1.0 - P) : -__double2float_rn(P);
-          part = fmaf((SYM && i != jc) ? 2.0f * dd : dd, dd, part);
+          const double dd = (i == jc ? 1.0 : 0.0) - P;
+          part = fma((SYM && i != jc) ? 2.0 * dd : dd, dd, part);
         }
         const int64_t ij = (int64_t)(row0 + i) * args.ld + jc, ji = (int64_t)(row0 + jc) * args.ld + i;
         double w2 = 0.0;
@@ -724,7 +724,7 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
       }
       if (e.partial) {
         for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        if (lane == 0) e.partial[(int64_t)tile * EPI_WARPS + ew] = (double)part;
+        if (lane == 0) e.partial[(int64_t)tile * EPI_WARPS + ew] = part;
       }
     }
   }

@@ -30,10 +30,11 @@ if not torch.cuda.is_available():
 from paper_1703_02283_gb300 import pthroot as P  # noqa: E402
 
 DEV = torch.device("cuda:0")
-# The library's residuals come from FP32 partial sums of the squared FP64 residual entries (per lane 24
-# terms, then a 32-lane tree per partial; the partials are added in FP64): relative error below
-# (24 + 5) 2^-24 / 2 < 2e-6 in r.
-RES_RTOL = 2e-6
+# The library's EMU64 residuals accumulate the squared FP64 residual entries in FP64 (per lane, then a
+# 32-lane tree, then the partials in a fixed order). While a residual is far above rounding, its histories
+# and the oracle's differ only by the rounding of differently ordered FP64 arithmetic carried through the
+# iterations: far below 1e-8 relative.
+RES_RTOL = 1e-8
 with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_n4096.json")) as _f:
     GOLD = json.load(_f)
 
@@ -124,7 +125,11 @@ def test_single_recipe_n4096_against_oracle(single_case, p):
         hg = np.asarray(g["residuals"])
         k = np.nonzero(hg > 0.5 * np.sqrt(4096))[0]
         assert len(k) >= 3
-        np.testing.assert_allclose(np.asarray(info["history"])[k], hg[k], rtol=RES_RTOL)
+        # At p = 4, M_0 spans kappa^5 = 1e15: its smallest eigenvalues carry relative errors up to
+        # u kappa^5 ~ 0.2 from the first products on, in either arithmetic, and the two histories move apart
+        # by about 1e-6 relative (measured 1.0e-6) before the residual falls below 0.5 sqrt(n).
+        rtol = RES_RTOL if p <= 3 else 1e-5
+        np.testing.assert_allclose(np.asarray(info["history"])[k], hg[k], rtol=rtol)
     # The true residual of the result, with EMU64 products: at most what the oracle's result has.
     assert info["residual"] <= max(GOLD["tol"], 10 * g["true_residual"])
 
