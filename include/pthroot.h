@@ -180,7 +180,8 @@ typedef struct {
   double c0_gate;                   /* PR_C0_POLY: the gate's estimate of ||I - C_0^p A||_2, else 0         */
   double true_residual;     /* ||I - C^p A||_F of the iterate at the last stop of pr_iterate: the verified
                                value of the coupled form (pr_options.verify), the tested residual of the
-                               Newton-Schulz and literal forms; -1 before the first stop                  */
+                               Newton-Schulz and literal forms; -1 before the first stop. After a
+                               pr_solve_ladder rung guard restored an earlier iterate: that iterate's value */
   int prescale_log2;        /* k: the handle iterates on 2^k A (see pr_load), 0 when A is taken as given   */
   int emu_tile_n[2];        /* PR_EMU64 products, symmetric [0] and full [1]: tile width in use (0: none yet) */
   int emu_tile_split[2];    /* ... and whether their tiles are split over K                               */

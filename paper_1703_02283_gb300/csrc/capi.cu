@@ -1459,6 +1459,7 @@ pr_status pr_solve_ladder(pr_handle h, int count, const int* precisions, const i
       PR_CK(h, cudaMemcpyAsync(h->xbest, h->X.f, bytes, cudaMemcpyDeviceToDevice, h->stream));
       return sync(h);
     }
+    h->st.true_residual = best;  // the restored iterate's, evaluated when it was kept
     return restore(h->xbest);
   };
   // A rung after the first that diverges from the iterate the earlier rungs left (a low-precision rung can
