@@ -318,6 +318,10 @@ struct MmaLevel {
 // (m pairs x P steps x 16 values of k x 2^14 <= 2^24 keeps the level's FP32 sum exact). Accumulator a of a
 // pass is drained after step j when (j + 2a) % P == P - 1 (the offsets stagger the drains) and after the
 // pass's last step.
+// 16-wide K chunks per pipeline step. The first pass moves one plane group per chunk, so a stage (and an
+// X-plane buffer in TMEM) holds two chunks: chunk c's planes take the slots of the second pass's group c.
+__device__ __forceinline__ int chunks_per_step(int pass) { return pass == 0 ? 2 : 1; }
+
 __device__ __forceinline__ int drain_period(int L, int S) {
   const int m = min(S, L - 1) - max(1, L - S) + 1;
   return m <= 1 ? 64 : m <= 2 ? 32 : m <= 4 ? 16 : 8;
@@ -382,19 +386,23 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
         const EmuMat& mt = item_of<SPLIT>(args, t, bi, bj, kpart, j0, j1);
         const int ya = mt.row0 + bi * EBM, yb = mt.row0 + bj * BN;
         for (int pass = 0; pass < npass && !stop; ++pass) {
-          const int ng = pass == 0 ? 1 : groups1;
-          for (int j = j0; j < j1; ++j, ++it) {
-            const int st = it % NSTAGE;
+          const int ng = pass == 0 ? 1 : groups1, kc = chunks_per_step(pass);
+          for (int j = j0; j < j1; j += kc, ++it) {
+            const int st = it % NSTAGE, nc = min(kc, j1 - j);
             if (*s_abort || !ptx::mbar_wait(empty0 + 8 * st, ((it / NSTAGE) & 1) ^ 1, args.err, 11)) {
               *s_abort = 1;
               stop = true;
               break;
             }
             uint8_t* sp = ring + st * STAGE_BYTES;
-            ptx::mbar_expect_tx(full0 + 8 * st, (uint32_t)ng * (A_GROUP + B_GROUP));
-            for (int g = 0; g < ng; ++g) {
-              ptx::tma_load_3d(ptx::smem_u32(sp + g * A_GROUP), &tmX, full0 + 8 * st, 0, 2 * j + g, ya);
-              ptx::tma_load_3d(ptx::smem_u32(sp + A_BYTES + g * B_GROUP), &tmY, full0 + 8 * st, 0, 2 * j + g, yb);
+            ptx::mbar_expect_tx(full0 + 8 * st, (uint32_t)(nc * ng) * (A_GROUP + B_GROUP));
+            for (int c = 0; c < nc; ++c) {
+              for (int g = 0; g < ng; ++g) {
+                const int slot = c * ng + g;
+                ptx::tma_load_3d(ptx::smem_u32(sp + slot * A_GROUP), &tmX, full0 + 8 * st, 0, 2 * (j + c) + g, ya);
+                ptx::tma_load_3d(ptx::smem_u32(sp + A_BYTES + slot * B_GROUP), &tmY, full0 + 8 * st, 0,
+                                 2 * (j + c) + g, yb);
+              }
             }
           }
         }
@@ -416,8 +424,8 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
       return __all_sync(0xffffffffu, ptx::mbar_wait(bar, parity, args.err, code));
     };
     // One pass over KS steps; copy(aT, xdesc) copies the pass's planes of the stage with descriptor xdesc.
-    auto run_pass = [&](auto copy, int KS) -> bool {
-      for (int j = 0; j < KS; ++j, ++it) {
+    auto run_pass = [&](auto copy, int nsteps) -> bool {
+      for (int q = 0; q < nsteps; ++q, ++it) {
         const int st = it % NSTAGE, b = it & 1;
         if (!wait_all(full0 + 8 * st, (it / NSTAGE) & 1, 12) ||
             (it >= 2 && !wait_all(empty0 + 8 * ((it - 2) % NSTAGE), ((it - 2) / NSTAGE) & 1, 13)))
@@ -440,22 +448,19 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
           stop = true;
           break;
         }
-        const int np = pass == 0 ? min(S, 4) : S;
+        // Buffer plane v: the second pass's digit plane v, or in the first pass plane v % 4 of chunk v / 4.
+        const int kc = chunks_per_step(pass), np = pass == 0 ? min(S, 4) : S, nsteps = (j1 - j0 + kc - 1) / kc;
         bool ok;
-        if (np == 4) {
+        if (np == 8 || (pass == 0 && np == 4)) {
           ok = run_pass([&](uint32_t aT, uint64_t xd) {
 #pragma unroll
-            for (int s = 0; s < 4; ++s) planes(aT, xd, s);
-          }, j1 - j0);
-        } else if (np == 8) {
-          ok = run_pass([&](uint32_t aT, uint64_t xd) {
-#pragma unroll
-            for (int s = 0; s < 8; ++s) planes(aT, xd, s);
-          }, j1 - j0);
+            for (int v = 0; v < 8; ++v) planes(aT, xd, v);
+          }, nsteps);
         } else {
           ok = run_pass([&](uint32_t aT, uint64_t xd) {
-            for (int s = 0; s < np; ++s) planes(aT, xd, s);
-          }, j1 - j0);
+            for (int c = 0; c < kc; ++c)
+              for (int s = 0; s < np; ++s) planes(aT, xd, 4 * c + s);
+          }, nsteps);
         }
         if (!ok) {
           *s_abort = 1;
@@ -482,9 +487,10 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
     auto run_pass = [&](auto iH, auto iL, bool useH, bool useL, int pass, int KS) -> bool {
       const int aH = 3 - w, aL = w, LH = 2 + 4 * pass + aH, LL = 2 + 4 * pass + aL;
       const uint32_t dH = tmem + (uint32_t)(BN * aH), dL = tmem + (uint32_t)(BN * aL);
-      const int pmH = drain_period(LH, S) - 1, pmL = drain_period(LL, S) - 1;
+      const int kc = chunks_per_step(pass), nsteps = (KS + kc - 1) / kc;
+      const int pmH = drain_period(LH, S) / kc - 1, pmL = drain_period(LL, S) / kc - 1;
       bool fH = true, fL = true;  // the next MMA into the accumulator starts it afresh
-      for (int j = 0; j < KS; ++j, ++it) {
+      for (int j = 0; j < nsteps; ++j, ++it) {
         const int st = it % NSTAGE, b = it & 1;
         // One wait per step: the copy warp waited for this stage's TMA load before it copied the X planes, so
         // the completion of its copy (aready) also orders the stage's Y planes before these MMAs.
@@ -492,7 +498,7 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
         ptx::tc_fence_after();
         const uint64_t bdesc = bdesc0 + (uint64_t)((st * STAGE_BYTES) >> 4);
         const uint32_t aT = aT0 + (uint32_t)(64 * b);
-        const bool last = j == KS - 1;
+        const bool last = j == nsteps - 1, two = kc == 2 && kc * j + 1 < KS;  // two chunks in this step
         // A level restarting after a drain waits for the epilogue's release; it goes second.
         const bool waitH = useH && fH && (drained & 1u), waitL = useL && fL && (drained & 2u);
         auto doH = [&]() -> bool {
@@ -502,6 +508,7 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
             ptx::tc_fence_after();
           }
           iH(dH, aT, bdesc, fH);
+          if (two) iH(dH, aT + 32, bdesc + (uint64_t)(B_GROUP >> 4), false);  // chunk 1: planes 4 columns on
           fH = false;
           if (last || ((j + 2 * aH) & pmH) == pmH) {
             ptx::mma_commit_w(lfull0 + 8 * aH);
@@ -518,6 +525,7 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
             ptx::tc_fence_after();
           }
           iL(dL, aT, bdesc, fL);
+          if (two) iL(dL, aT + 32, bdesc + (uint64_t)(B_GROUP >> 4), false);
           fL = false;
           if (last || ((j + 2 * aL) & pmL) == pmL) {
             ptx::mma_commit_w(lfull0 + 8 * aL);
@@ -590,14 +598,15 @@ __global__ void __launch_bounds__(THREADS, 1)  // 20 warps: up to 96 registers (
 #pragma unroll
       for (int c = 0; c < EPI_COLS; ++c) acc[c] = 0;
       for (int pass = 0; pass < npass && !stop; ++pass) {
-        int pm[NACC];  // drain period - 1 of each accumulator's level; -1: the level is empty
+        const int kc = chunks_per_step(pass), nsteps = (KS + kc - 1) / kc;
+        int pm[NACC];  // drain period (in steps) - 1 of each accumulator's level; -1: the level is empty
 #pragma unroll
         for (int a = 0; a < NACC; ++a) {
           const int L = 2 + 4 * pass + a;
-          pm[a] = L > S + 1 ? -1 : drain_period(L, S) - 1;
+          pm[a] = L > S + 1 ? -1 : drain_period(L, S) / kc - 1;
         }
-        for (int j = 0; j < KS && !stop; ++j) {
-          const bool lastj = j == KS - 1;
+        for (int j = 0; j < nsteps && !stop; ++j) {
+          const bool lastj = j == nsteps - 1;
 #pragma unroll
           for (int a = 0; a < NACC; ++a) {
             if (pm[a] < 0 || !(lastj || ((j + 2 * a) & pm[a]) == pm[a])) continue;
