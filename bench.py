@@ -47,7 +47,7 @@ NOMINAL_FP64_TFLOPS = 1.25
 PREC_NAMES = {0: "fp64", 1: "emu64", 2: "fp32x", 3: "bf16", 4: "fp8"}
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one symmetric product of the kernel as it is now, by n
 # (profiles/k_gemm_emu_n4096.md). A change to the kernel empties this until it is captured again.
-EMU_TRAFFIC_CURRENT: dict = {}
+EMU_TRAFFIC_CURRENT: dict = {4096: 2.434416e9 + 0.352206e9}
 
 
 # ----------------------------------------------------------------------------- replicas (N > 1 under torchrun)
