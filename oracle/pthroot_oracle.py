@@ -48,6 +48,14 @@ network's forward pass, mean-squared loss and gradient written out layer by laye
 eigenvalues, Eq. 3 and the scaled identity as special coefficient vectors, the gate against the scalar
 model of Eq. 2, the fit on a vanishing interval, a hand-computed network case and central differences of
 the loss.
+
+Refinement (``refine_newton``, the section before the custom-precision functions): Newton's method on the
+balanced residual ``I - sym(X^m A X^m')`` (m = floor(p/2), m' = p - m) with a conjugate-gradient solve of the
+linearised equation, which corrects perturbations of any structure, the step Sec. 3 and Sec. 5 rely on to turn
+an approximate result into a precise one. Its pins (tests/test_oracle_refine.py): on diagonal matrices every
+entry follows the scalar Newton step for x^p a = 1; one correction equals the entry-wise solution in the
+eigenbasis of a commuting X; a perturbed root converges quadratically to the closed form while the coupled
+form started from it does not; planted mistakes in the linearised operator fail.
 """
 from __future__ import annotations
 
@@ -62,6 +70,7 @@ __all__ = [
     "coupled_start", "step_coupled", "solve", "SolveInfo", "closed_form_root", "eig_root",
     "scalar_recurrence", "scalar_residuals", "forward_error", "default_form", "closed_form_block",
     "residual_rows", "eq2_prescale", "round_mantissa", "matmul_rounded", "quantized_iterates",
+    "refine_operator", "refine_residual", "refine_correction", "refine_newton", "RefineInfo",
 ]
 
 
@@ -332,6 +341,142 @@ def scalar_residuals(lam: np.ndarray, c0: np.ndarray, p: int, k_max: int) -> np.
 def forward_error(C: np.ndarray, Z: np.ndarray) -> float:
     """||C - Z||_F / ||Z||_F, the Frobenius error of Sec. 4.3 made relative."""
     return float(np.linalg.norm(C - Z) / np.linalg.norm(Z))
+
+
+# ---------------------------------------------------------------- refinement of an approximate root (Sec. 3, Sec. 5)
+#
+# Sec. 3 and Sec. 5: an approximation computed with imprecise arithmetic is refined into a precise root in a
+# few additional precise iterations. For p = 1 Eq. 1's own step (Newton-Schulz) does that: it removes any
+# perturbation of C to first order. For p >= 2 it does not: the coupled form keeps X_k M_k^{-1/p} fixed, so a
+# perturbation that does not commute with A stays in the limit, amplified by up to about kappa / p.
+# The refinement below is Newton's method on the balanced residual
+#
+#     G(X) = I - sym(X^m A X^m'),   m = floor(p / 2),  m' = p - m,
+#
+# whose solution near A^{-1/p} is A^{-1/p} (in the eigenbasis of a commuting X the residual is
+# 1 - x^p lam). A step solves the linearised equation L_X(D) = G(X) for a symmetric correction D with
+# L_X(D) = sym(dP_m(D) A X^m' + X^m A dP_m'(D)), where dP_k(D) = sum_{j<k} X^j D X^(k-1-j) is the first-order
+# change of X^k, by conjugate gradients preconditioned with D = sym(X R) / p (the inverse of L_X on the
+# diagonal of X's eigenbasis, where L_X multiplies by p x^(p-1) lam = p / x at the root), and sets
+# X <- sym(X + D). Splitting X^p into two halves around A makes L_X a symmetric positive definite operator
+# near the root with a spread of only about kappa^(1/2) between its eigenvalues (for p = 2 it is the Lyapunov
+# operator D -> D A^(1/2) + A^(1/2) D).
+
+def refine_operator(X: np.ndarray, A: np.ndarray, p: int, D: np.ndarray) -> np.ndarray:
+    """L_X(D) = sym(dP_m(D) A X^m' + X^m A dP_m'(D)): the first-order change of sym(X^m A X^m') when X moves
+    by D (m = floor(p / 2), m' = p - m, dP_k(D) = sum_{j<k} X^j D X^(k-1-j))."""
+    m, mq = p // 2, p - p // 2
+
+    def power(k):
+        return np.linalg.matrix_power(X, k)
+
+    def dpow(k):
+        out = np.zeros_like(X)
+        for j in range(k):
+            out = out + power(j) @ D @ power(k - 1 - j)
+        return out
+
+    return symmetrize(dpow(m) @ A @ power(mq) + power(m) @ A @ dpow(mq))
+
+
+def refine_residual(X: np.ndarray, A: np.ndarray, p: int) -> np.ndarray:
+    """G(X) = I - sym(X^m A X^m'), m = floor(p / 2), m' = p - m."""
+    m, mq = p // 2, p - p // 2
+    F = np.linalg.matrix_power(X, m) @ A @ np.linalg.matrix_power(X, mq)
+    return np.eye(A.shape[0]) - symmetrize(F)
+
+
+def refine_correction(X: np.ndarray, A: np.ndarray, p: int, G: np.ndarray, cg_max: int = 50,
+                      cg_tol: float = 1e-12):
+    """The Newton correction: D with L_X(D) = G by conjugate gradients in the Frobenius inner product,
+    preconditioned with R -> sym(X R) / p, from D = 0, until ||G - L_X(D)||_F <= cg_tol ||G||_F or cg_max
+    iterations. Returns (D, iterations)."""
+    def precondition(R):
+        return symmetrize(X @ R) / p
+
+    D = np.zeros_like(X)
+    R = np.array(G, dtype=np.float64, copy=True)
+    g0 = float(np.linalg.norm(G))
+    if g0 == 0.0:
+        return D, 0
+    Zr = precondition(R)
+    S = Zr.copy()
+    rz = float(np.sum(R * Zr))
+    it = 0
+    while it < cg_max:
+        LS = refine_operator(X, A, p, S)
+        alpha = rz / float(np.sum(S * LS))
+        D = D + alpha * S
+        R = R - alpha * LS
+        it += 1
+        if float(np.linalg.norm(R)) <= cg_tol * g0:
+            break
+        Zr = precondition(R)
+        rz_new = float(np.sum(R * Zr))
+        S = Zr + (rz_new / rz) * S
+        rz = rz_new
+    return D, it
+
+
+@dataclass
+class RefineInfo:
+    p: int
+    steps: int = 0                                      # Newton corrections kept
+    residuals: list = field(default_factory=list)       # ||G(X_k)||_F for k = 0 .. steps (last: returned X)
+    cg_iterations: list = field(default_factory=list)   # CG iterations of each kept correction
+    stop: str = ""        # "tol", "stagnation", "max_steps", "diverged" or "inaccurate"
+    true_residual: float = -1.0                         # ||I - X^p A||_F of the returned X
+
+
+def refine_newton(A: np.ndarray, X0: np.ndarray, p: int, max_steps: int = 8, tol: float = 1e-12,
+                  cg_max: int = 50, cg_tol: float = 1e-12, stag_below: float = 1e-3, stag_ratio: float = 0.5):
+    """Newton refinement of an approximate root X0 of A^{-1/p} (see the section comment).
+
+    Before each step the residual g_k = ||G(X_k)||_F is recorded and tested: "tol" if g_k <= tol; if g_k is
+    not finite or (k >= 1) g_k >= g_{k-1}, the last correction is undone (X and the record return to step
+    k - 1) and the stop is "diverged" (not finite) or "stagnation"; "stagnation" also if g_{k-1} < stag_below
+    and g_k > stag_ratio g_{k-1} (X_k kept); "max_steps" if k == max_steps. Otherwise one correction is
+    applied. Afterwards the true residual ||I - X^p A||_F of the returned X is evaluated, and a "tol" stop
+    whose true residual exceeds tol becomes "inaccurate". Returns (X, RefineInfo).
+    """
+    A = np.asarray(A, dtype=np.float64)
+    X = symmetrize(np.asarray(X0, dtype=np.float64))
+    info = RefineInfo(p=p)
+    prev = None
+    k = 0
+    while True:
+        G = refine_residual(X, A, p)
+        g = float(np.linalg.norm(G))
+        info.residuals.append(g)
+        if not np.isfinite(g) or (k >= 1 and g >= info.residuals[-2]):
+            stop = "diverged" if not np.isfinite(g) else "stagnation"
+            if prev is not None:
+                X = prev
+                info.residuals.pop()
+                info.cg_iterations.pop()
+                k -= 1
+            break
+        if g <= tol:
+            stop = "tol"
+            break
+        if k >= 1 and info.residuals[-2] < stag_below and g > stag_ratio * info.residuals[-2]:
+            stop = "stagnation"
+            break
+        if k >= max_steps:
+            stop = "max_steps"
+            break
+        D, its = refine_correction(X, A, p, G, cg_max, cg_tol)
+        info.cg_iterations.append(its)
+        prev = X
+        X = symmetrize(X + D)
+        k += 1
+    info.steps = k
+    if stop != "diverged":
+        info.true_residual = residual_fro(X, A, p)
+        if stop == "tol" and not info.true_residual <= tol:
+            stop = "inaccurate"
+    info.stop = stop
+    return X, info
 
 
 # ---------------------------------------------------------------- custom-precision simulation (Sec. 4.2, 4.3)

@@ -17,6 +17,8 @@ Recipes (all seeded with ``numpy.random.default_rng``):
   entries in (0, 1], decaying with distance), which are not available.
 * ``spd_from_spectrum_device``: the same recipe built on the GPU by torch, for the order-16384 case.
 * ``batched_specs``: sizes, condition numbers and roots of a batch of independent problems.
+* ``symmetric_perturbation(n, seed)``: a symmetric N(0, 1) matrix scaled to unit Frobenius norm, the
+  direction of the error planted in an approximate root that the refinement tests start from.
 """
 from __future__ import annotations
 
@@ -104,6 +106,14 @@ def spd_from_spectrum_device(n: int, lam_min: float, seed: int, device) -> Devic
     A.add_(At).mul_(0.5)
     del At
     return DeviceSpdCase(A=A, Q=Q, lam=lam, seed=seed)
+
+
+def symmetric_perturbation(n: int, seed: int) -> np.ndarray:
+    """(G + G^T) / 2 for an n x n N(0, 1) matrix G, scaled to unit Frobenius norm (a perturbation direction
+    with no relation to any matrix's eigenvectors)."""
+    G = np.random.default_rng(seed).standard_normal((n, n))
+    E = 0.5 * (G + G.T)
+    return np.ascontiguousarray(E / np.linalg.norm(E))
 
 
 # The fixed workloads. Sizes and spectra follow the benchmark recipes: a small plain-FP64 case that the
