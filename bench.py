@@ -8,7 +8,9 @@ to the tolerance or the precision floor (the coupled form's stop verified agains
 true residual ||I - C^p A||_F and the result copy. The value is milliseconds per step (lower is better) for
 --mode:
   fast   FP64-accurate products from exact FP16 digit slices (PR_EMU64) for every p; for p = 1, whose
-         Newton-Schulz form corrects earlier errors, BF16 iterations first, then PR_EMU64 ones (default);
+         Newton-Schulz form corrects earlier errors, BF16 iterations first, then PR_EMU64 ones; for p >= 2,
+         whose coupled form keeps the error of its iterates, Newton refinement afterwards (pr_refine: EMU64
+         residuals, BF16 conjugate-gradient solves) (default);
   emu64  PR_EMU64 for every iteration;
   fp64   native FP64 products (the plain FP64 GPU iteration).
 Beside the value the line reports the same solves from the scaled identity C_0 = ||A||_1^{-1/p} I (Sec. 2's
@@ -48,6 +50,9 @@ PREC_NAMES = {0: "fp64", 1: "emu64", 2: "fp32x", 3: "bf16", 4: "fp8"}
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one symmetric product of the kernel as it is now, by n
 # (profiles/k_gemm_emu_n4096.md). A change to the kernel empties this until it is captured again.
 EMU_TRAFFIC_CURRENT: dict = {4096: 2.434416e9 + 0.352206e9}
+# Mode fast, p >= 2: Newton refinement after the EMU64 iterations (pr_refine: EMU64 residuals, BF16 conjugate-
+# gradient solves, each correction about a hundredfold).
+REFINE = dict(max_steps=12, cg_max=40, cg_tol=1e-2)
 
 
 # ----------------------------------------------------------------------------- replicas (N > 1 under torchrun)
@@ -101,6 +106,8 @@ def parse():
     ap.add_argument("--compare-steps", type=int, default=2, help="timed steps of each plain FP64 comparison")
     ap.add_argument("--compare-warmup", type=int, default=1, help="warm-up steps of each plain FP64 comparison")
     ap.add_argument("--no-scaled-identity", action="store_true", help="skip the scaled-identity arm")
+    ap.add_argument("--no-refine", action="store_true",
+                    help="mode fast: skip the Newton refinement (pr_refine) of the p >= 2 solves")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and learned summaries")
     ap.add_argument("--sub-steps", type=int, default=5, help="timed steps of the batched / learned summaries")
     ap.add_argument("--sub-warmup", type=int, default=3, help="warm-up steps of the batched / learned summaries")
@@ -254,6 +261,8 @@ def config_dict(args, ps):
     return {"workload": f"SPD n={args.n} (Q diag(lam) Q^T), kappa={1 / args.lam_min:g}, p={','.join(map(str, ps))}, "
                         f"Eq.3 C_0, tol {args.tol:g}", "n": args.n, "kappa": 1 / args.lam_min, "p": ps,
             "seed": args.seed, "mode": args.mode,
+            "refine": None if args.mode != "fast" or args.no_refine else
+            {"p": ">= 2", "residual": "emu64", "solve": "bf16", **REFINE},
             "l2": l2_note(handle_bytes(args.n)) + " per handle"}
 
 
@@ -901,9 +910,18 @@ def main():
             bulk, nb, fin = plan(p, mode)
             P.pr_load(h, Ain)
             st, steps = P.pr_solve(h, bulk, nb, fin, args.tol)
-            res = P.pr_residual(h, fin)
-            P.pr_result(h, Cout)
+            refine = None
+            if mode == "fast" and p >= 2 and not args.no_refine:
+                # The coupled form keeps the error its iterates picked up (Eq. 3's M_0 spans kappa^(p+1));
+                # Newton corrections with BF16 solves remove it.
+                st, k = P.pr_refine(h, P.PR_EMU64, P.PR_BF16, REFINE["max_steps"], args.tol, REFINE["cg_max"],
+                                    REFINE["cg_tol"])
+                refine = k
             s = P.pr_stats(h)
+            # The true residual ||I - C^p A||_F of the result: evaluated by the library at the stop (the verified
+            # coupled stop, the tested Newton-Schulz residual, or the end of the refinement).
+            res = s["true_residual"]
+            P.pr_result(h, Cout)
             info[p] = {"status": P.STATUS_NAMES[st], "iterations": steps, "true_residual": res,
                        "tol_met": bool(res <= args.tol),
                        "iterations_by_precision": {PREC_NAMES[k]: s["iterations_by_precision"][k]
@@ -911,6 +929,9 @@ def main():
                        "switch_iteration": s["switch_iteration"],
                        "emu_variant": {"sym": {"tile_n": s["emu_tile_n"][0], "split": s["emu_tile_split"][0]},
                                        "full": {"tile_n": s["emu_tile_n"][1], "split": s["emu_tile_split"][1]}}}
+            if refine is not None:
+                info[p]["refine"] = {"steps": refine, "residuals": s["refine_residuals"],
+                                     "cg_iterations": s["refine_cg"]}
         return info
 
     def barrier():
@@ -1082,7 +1103,8 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-                "vs_baseline": None, "dtype": {"fast": "bf16+emu64(fp16 slices)", "emu64": "emu64(fp16 slices)",
+                "vs_baseline": None, "dtype": {"fast": "bf16+emu64(fp16 slices)+bf16 refinement solves",
+                                               "emu64": "emu64(fp16 slices)",
                                                "fp64": "f64"}[args.mode],
                 "data": "synthetic", "config": config_dict(args, ps), "roofline": roofline,
                 "kernel_time_share": kernel_share, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

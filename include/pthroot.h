@@ -151,6 +151,9 @@ typedef struct {
   int quant_mode;      /* pr_quant_mode, default PR_QUANT_STORAGE                                          */
 } pr_options;
 
+/* Most Newton corrections one pr_refine call applies. */
+#define PR_REFINE_MAX_STEPS 16
+
 /* Counters of one handle. */
 typedef struct {
   int64_t n;
@@ -190,6 +193,12 @@ typedef struct {
                                   trial time (ms) of each variant, index (width 48 ? 2 : 0) + (split ? 1 : 0),
                                   0 where not tried (the variant does not apply, or the choice was known) */
   int ladder_restores;      /* pr_solve_ladder: rungs whose result was discarded (see pr_solve_ladder)       */
+  int refine_steps;         /* Newton corrections kept by pr_refine over the handle's life                     */
+  int64_t refine_cg_iterations; /* their conjugate-gradient iterations                                        */
+  int refine_len;           /* residuals recorded by the last pr_refine (its corrections kept + 1), 0 before   */
+  double refine_residuals[PR_REFINE_MAX_STEPS + 1]; /* ||G(X_k)||_F of the last pr_refine, k = 0 .. refine_len - 1,
+                                                       the last one of the iterate it returned (see pr_refine) */
+  int refine_cg[PR_REFINE_MAX_STEPS]; /* conjugate-gradient iterations of each correction of the last pr_refine */
 } pr_stats_t;
 
 /* Fills *opt with the defaults listed above. */
@@ -272,6 +281,57 @@ pr_status pr_solve(pr_handle h, int bulk_precision, int bulk_steps, int final_pr
  * Errors: as pr_iterate, and PR_EINVAL for count < 1, a NULL precisions array or an unknown precision. */
 pr_status pr_solve_ladder(pr_handle h, int count, const int* precisions, const int* max_steps, double tol,
                           int* steps_done);
+
+/* ---- Refinement of an approximate root (Sec. 3 and Sec. 5) ------------------------------------------------
+ * Sec. 3 and Sec. 5: a result computed with imprecise arithmetic is refined into a precise root in a few
+ * additional precise iterations. Eq. 1's own step does that for p = 1 (Newton-Schulz removes any perturbation
+ * to first order) but not for p >= 2: the coupled form keeps X_k M_k^{-1/p} fixed and so converges to
+ * X_0 (X_0^p A)^{-1/p}, which differs from A^{-1/p} whenever X_0 carries an error that does not commute with A
+ * (the rounding errors of a low-precision phase, or those of M_0 = C_0^p A from Eq. 3's C_0, whose eigenvalues
+ * span kappa^(p+1)). pr_refine applies Newton's method to the balanced residual
+ *     G(X) = I - sym(X^m A X^m'),   m = floor(p/2), m' = p - m,   sym(Y) = (Y + Y^T) / 2,
+ * which vanishes at A^{-1/p}. A step solves the linearised equation
+ *     sym(dP_m(D) A X^m' + X^m A dP_m'(D)) = G(X),   dP_k(D) = sum_{j<k} X^j D X^(k-1-j),
+ * for a symmetric correction D by conjugate gradients (Frobenius inner product, preconditioner R -> sym(X R) / p)
+ * and sets X <- X + D. Each step squares the error of X up to a constant, whatever its structure; the
+ * solve needs only the accuracy the step is to gain, so its products may be low precision while G(X) is
+ * evaluated with FP64-accurate products.
+ *   precision        products of G(X) (and of the true residual at the end): PR_EMU64 or PR_FP64 for an
+ *                    FP64-accurate root; any pr_precision is accepted
+ *   inner_precision  products of the conjugate-gradient solve, any pr_precision (PR_FP32X: about 1e-6 per
+ *                    correction; PR_BF16: about 1e-2, more steps but each far cheaper)
+ *   max_steps        at most this many corrections, 0 .. PR_REFINE_MAX_STEPS
+ *   tol              stop when ||G(X)||_F <= tol
+ *   cg_max, cg_tol   the solve stops when ||G - L(D)||_F <= cg_tol ||G||_F or after cg_max >= 1 iterations
+ *   steps_done       (may be NULL) corrections kept in this call
+ * Before each step ||G(X_k)||_F is evaluated and tested: PR_OK if <= tol; if it is not finite, or not below
+ * the previous step's value, the last correction is undone (X returns to the previous iterate) and the stop is
+ * PR_EDIVERGED or PR_ESTAGNATED; PR_ESTAGNATED also when the previous value was below stag_below and this one
+ * above stag_ratio times it (the precision floor; the iterate is kept); PR_EMAXITER after max_steps
+ * corrections. Then the true residual ||I - X^p A||_F of the returned iterate is evaluated with `precision`
+ * products into pr_stats.true_residual, and a PR_OK whose true residual exceeds tol becomes PR_EINACCURATE.
+ * pr_stats records each step's residual and solve length (refine_residuals, refine_cg). The iteration counters
+ * and history of Eq. 1 are not changed; a following pr_iterate re-forms the coupled form's M from the refined X.
+ * Works on every form and on the iterate pr_iterate, pr_solve, pr_solve_ladder or pr_set_iterate left.
+ * Products per step: 1 (p = 1), 2 (p = 2), 3 (p = 4) or 4 (p = 3) with `precision`; per solve iteration
+ * 2, 2, 3 or 4 with `inner_precision`. Uses three n*n FP64 matrices (with their BF16 copies, and digit planes
+ * where the products need them) and a copy of X beyond pr_init's, allocated on the first call and kept until
+ * pr_destroy (PR_ENOMEM if they cannot be). Synchronises the stream twice per solve iteration.
+ * Errors: PR_ESTATE (NULL handle, no matrix), PR_EINVAL (unknown precision, max_steps outside
+ * [0, PR_REFINE_MAX_STEPS], tol, cg_tol < 0 or NaN, cg_max < 1), PR_EUNSUPPORTED (the custom-precision
+ * experiment, pr_options.quant_bits), PR_ECUDA, PR_ETIMEOUT, PR_ENOMEM. */
+pr_status pr_refine(pr_handle h, int precision, int inner_precision, int max_steps, double tol, int cg_max,
+                    double cg_tol, int* steps_done);
+
+/* Replaces the handle's iterate by X: n*n FP64 row-major, an approximation of A^{-1/p} for the A the caller
+ * gave (device or host memory; copied). For pr_refine of a root known to low precision, e.g. one computed
+ * elsewhere or the root of a nearby matrix of a sequence, or to restart Eq. 1 from a chosen C_0. Checks X as
+ * pr_init checks A (finite, symmetric within sym_tol, positive diagonal, Cholesky of the diagonal blocks of
+ * order 64) and multiplies it by 2^(-k/p) when the handle iterates on 2^k A (pr_stats.prescale_log2).
+ * Clears the iteration state, history and counters as pr_set_initial_guess does. Synchronises the stream.
+ * Errors: PR_ESTATE (NULL handle, no matrix), PR_EINVAL (X NULL, non-finite or not symmetric), PR_ENOTSPD,
+ * PR_ECUDA. */
+pr_status pr_set_iterate(pr_handle h, const double* X);
 
 /* True residual ||I - C^p A||_F of the current iterate (Eq. 2 in the Frobenius norm), evaluated with
  * products at the given precision: C^p by symmetric products, then the full product with A.

@@ -45,7 +45,8 @@ struct Mat {
   uint8_t* q = nullptr;         // PR_FP8: E4M3 copy of f / 2^qe (row by row), allocated on first use
   int* qe = nullptr;            // PR_FP8: row scales (exponents)
   bool q_valid = false;         // the E4M3 copy describes the current f
-  void changed() { sl_valid = q_valid = false; }  // f was written
+  bool b_valid = false;         // pr_refine: the BF16 copy describes the current f (read by lp_operand only)
+  void changed() { sl_valid = q_valid = b_valid = false; }  // f was written
 };
 
 void swap(Mat& a, Mat& b) { std::swap(a, b); }
@@ -95,6 +96,9 @@ struct pr_handle_s {
   double* vec = nullptr;      // PR_C0_POLY gate and features: 4n vectors + reduction partials + scalars
   double* xbest = nullptr;    // pr_solve_ladder: the iterate with the lowest true residual at a rung boundary
   double* xstart = nullptr;   // pr_solve_ladder: the starting iterate, for a rung that diverges
+  Mat Ra, Rb, Rc;             // pr_refine: three more matrices, allocated on its first call
+  double* rdev = nullptr;     // pr_refine: reduction work area and device scalars
+  double* rpin = nullptr;     // pr_refine: pinned host mirror of its scalars
   bool powers_valid = false;  // T0 = A^2 and T1 = A^3 of the loaded A (features, polynomial guess)
 
   // CUDA-event timing of the product kernels (pr_set_timing).
@@ -941,6 +945,236 @@ pr_status matmul(int precision, int S, const double* X, const double* Y, int64_t
 
 }  // namespace
 
+namespace {
+
+// ---- Newton refinement of an approximate root (pr_refine)
+//
+// Newton's method on the balanced residual G(X) = I - sym(X^m A X^m'), m = floor(p/2), m' = p - m: each step
+// solves sym(dP_m(D) A X^m' + X^m A dP_m'(D)) = G(X) for a symmetric D by preconditioned conjugate gradients
+// and sets X <- X + D (see pr_refine in the header). With U = X^m, V = X^m', Y = V A and W = U A:
+//   G(X) = I - sym(W V),   L(S) = sym(Y dP_m(S) + W dP_m'(S))   (the transpose of the first term of the
+//   definition, D_m A V, is V A D_m = Y dP_m(S); sym() does not see the difference),
+//   dP_1(S) = S, dP_2(S) = X S + S X = 2 sym(X S); for m = m' both terms are equal, L(S) = 2 sym(Y dP_m(S)).
+// Every product below has a symmetric second operand, so X Y and X Y^T coincide and the product kernels of
+// every precision apply. Buffers (the coupled form's state and the scratch products are free while a
+// refinement runs; the next pr_iterate re-forms M and N from X): T0 = X^2, T1 = Y, Nn = W (p = 3; W = Y when
+// m = m', W = A when p = 1), M = R (the solve's residual, first G), Mn = D (the correction), N = S (the search
+// direction), Ra = Z (the preconditioned residual), Rb = L(S), Rc = dP_2(S), Xn = a product before its
+// symmetrisation.
+
+constexpr int kRefScalars = 8;
+
+pr_status ensure_refine(pr_handle h) {
+  const size_t nn = (size_t)h->n * (size_t)h->n;
+  for (Mat* m : {&h->Ra, &h->Rb, &h->Rc}) {
+    if (!m->f) PR_CK(h, cudaMalloc((void**)&m->f, nn * sizeof(double)));
+    if (!m->b) PR_CK(h, cudaMalloc((void**)&m->b, (size_t)h->n * (size_t)h->ldl * sizeof(__nv_bfloat16)));
+  }
+  if (!h->xbest) PR_CK(h, cudaMalloc((void**)&h->xbest, nn * sizeof(double)));
+  if (!h->rdev) PR_CK(h, cudaMalloc((void**)&h->rdev, sizeof(double) * (kVecBlocks + kRefScalars)));
+  if (!h->rpin) PR_CK(h, cudaMallocHost((void**)&h->rpin, sizeof(double) * kRefScalars));
+  return PR_OK;
+}
+
+// BF16 products read their operands' BF16 copies; refresh them from the FP64 values. (Digit planes and E4M3
+// copies are refreshed by product() itself when the matrix changed.)
+pr_status lp_operand(pr_handle h, int prec, Mat& m) {
+  if (prec != PR_BF16 || m.b_valid) return PR_OK;
+  PR_CK(h, pr::to_bf16(m.f, (int)h->n, h->ldl, m.b, h->stream));
+  h->st.launches += 1;
+  m.b_valid = true;
+  return PR_OK;
+}
+
+// out = P = Xop Yop (Yop symmetric) in the given mode.
+pr_status plain_product(pr_handle h, int prec, Mat& Xop, Mat& Yop, Mode mode, Mat& out) {
+  pr_status s = lp_operand(h, prec, Xop);
+  if (s == PR_OK) s = lp_operand(h, prec, Yop);
+  if (s != PR_OK) return s;
+  Out o;
+  o.out = &out;
+  return product(h, prec, Xop, Yop, mode, o);
+}
+
+// out = scale sym(Xop Yop) (Yop symmetric), the full product going through Xn.
+pr_status sym_of_product(pr_handle h, int prec, Mat& Xop, Mat& Yop, double scale, Mat& out) {
+  pr_status s = lp_operand(h, prec, Xop);
+  if (s == PR_OK) s = lp_operand(h, prec, Yop);
+  if (s != PR_OK) return s;
+  Out o;
+  o.out2 = &h->Xn;
+  o.b = scale;
+  s = product(h, prec, Xop, Yop, Mode::Full, o);
+  if (s != PR_OK) return s;
+  PR_CK(h, pr::symmetrize(h->Xn.f, (int)h->n, out.f, h->stream));
+  h->st.launches += 1;
+  out.changed();
+  return PR_OK;
+}
+
+// Frobenius inner product <x, y> into device scalar k.
+pr_status fdot(pr_handle h, const Mat& x, const Mat& y, int k) {
+  PR_CK(h, pr::frobenius_dot(x.f, y.f, h->n * h->n, h->rdev, h->rdev + kVecBlocks + k, h->stream));
+  h->st.launches += 2;
+  return PR_OK;
+}
+
+// Device scalars 0 .. count-1 -> h->rpin (synchronises; a bounded wait that expired shows here).
+pr_status read_scalars(pr_handle h, int count) {
+  PR_CK(h, cudaMemcpyAsync(h->rpin, h->rdev + kVecBlocks, count * sizeof(double), cudaMemcpyDeviceToHost,
+                           h->stream));
+  return sync(h);
+}
+
+struct RefineOps {
+  int m = 0, mq = 0;
+  Mat *U = nullptr, *V = nullptr, *Y = nullptr, *W = nullptr;  // U = X^m (null: I), V = X^m', Y = V A, W = U A
+};
+
+// The products of one step that do not depend on the correction, at the residual's precision.
+pr_status refine_setup(pr_handle h, int prec, RefineOps& o) {
+  o.m = h->p / 2;
+  o.mq = h->p - o.m;
+  pr_status s = PR_OK;
+  Mat* X2 = nullptr;
+  if (o.mq == 2) {
+    s = plain_product(h, prec, h->X, h->X, Mode::Sym, h->T0);
+    if (s != PR_OK) return s;
+    X2 = &h->T0;
+  }
+  o.V = o.mq == 1 ? &h->X : X2;
+  o.U = o.m == 0 ? nullptr : (o.m == 1 ? &h->X : X2);
+  if (o.m >= 1) {
+    s = plain_product(h, prec, *o.V, h->A, Mode::Full, h->T1);
+    if (s != PR_OK) return s;
+    o.Y = &h->T1;
+  }
+  if (o.m == 0) {
+    o.W = &h->A;
+  } else if (o.m == o.mq) {
+    o.W = o.Y;
+  } else {
+    s = plain_product(h, prec, *o.U, h->A, Mode::Full, h->Nn);
+    if (s != PR_OK) return s;
+    o.W = &h->Nn;
+  }
+  return PR_OK;
+}
+
+// R = G(X) = I - sym(W V); *g = ||G(X)||_F.
+pr_status refine_residual(pr_handle h, int prec, const RefineOps& o, double* g) {
+  pr_status s = lp_operand(h, prec, *o.W);
+  if (s == PR_OK) s = lp_operand(h, prec, *o.V);
+  if (s != PR_OK) return s;
+  Out oo;
+  oo.a = 1.0;
+  oo.b = -1.0;
+  if (o.m == o.mq) {  // W V = X^m A X^m is symmetric: upper tiles, mirrored
+    oo.out2 = &h->M;
+    s = product(h, prec, *o.W, *o.V, Mode::Sym, oo);
+    if (s != PR_OK) return s;
+  } else {
+    oo.out2 = &h->Xn;
+    s = product(h, prec, *o.W, *o.V, Mode::Full, oo);
+    if (s != PR_OK) return s;
+    PR_CK(h, pr::symmetrize(h->Xn.f, (int)h->n, h->M.f, h->stream));
+    h->st.launches += 1;
+  }
+  h->M.changed();
+  s = fdot(h, h->M, h->M, 0);
+  if (s == PR_OK) s = read_scalars(h, 1);
+  if (s != PR_OK) return s;
+  *g = sqrt(h->rpin[0]);
+  return PR_OK;
+}
+
+// LS = L(S) at prec.
+pr_status refine_apply(pr_handle h, int prec, const RefineOps& o, Mat& S, Mat& LS) {
+  pr_status s = PR_OK;
+  Mat* D2 = nullptr;
+  if (o.m == 2 || o.mq == 2) {
+    s = sym_of_product(h, prec, h->X, S, 2.0, h->Rc);  // dP_2(S) = X S + S X
+    if (s != PR_OK) return s;
+    D2 = &h->Rc;
+  }
+  Mat* Dm = o.m == 1 ? &S : D2;
+  Mat* Dmq = o.mq == 1 ? &S : D2;
+  if (o.m == o.mq) return sym_of_product(h, prec, *o.Y, *Dm, 2.0, LS);
+  if (o.m == 0) return sym_of_product(h, prec, *o.W, *Dmq, 1.0, LS);
+  // p = 3: sym(Y S + W dP_2(S)), the first product kept in LS until the second adds it in its epilogue
+  s = plain_product(h, prec, *o.Y, *Dm, Mode::Full, LS);
+  if (s == PR_OK) s = lp_operand(h, prec, *o.W);
+  if (s == PR_OK) s = lp_operand(h, prec, *Dmq);
+  if (s != PR_OK) return s;
+  Out oo;
+  oo.out2 = &h->Xn;
+  oo.b = 1.0;
+  oo.c = 1.0;
+  oo.cin = LS.f;
+  s = product(h, prec, *o.W, *Dmq, Mode::Full, oo);
+  if (s != PR_OK) return s;
+  PR_CK(h, pr::symmetrize(h->Xn.f, (int)h->n, LS.f, h->stream));
+  h->st.launches += 1;
+  LS.changed();
+  return PR_OK;
+}
+
+// D with L(D) = R (R = G on entry, overwritten) by conjugate gradients preconditioned with Z = sym(X R) / p,
+// from D = 0, until ||R||_F <= cg_tol g0 or cg_max iterations, or a breakdown (a non-positive curvature
+// <S, L(S)> or <R, Z>, possible only far from the root); *its: the iterations taken.
+pr_status refine_solve(pr_handle h, int prec, const RefineOps& o, double g0, int cg_max, double cg_tol, int* its) {
+  Mat &R = h->M, &D = h->Mn, &S = h->N, &Z = h->Ra, &LS = h->Rb;
+  const int64_t total = h->n * h->n;
+  const double inv_p = 1.0 / h->p;
+  *its = 0;
+  PR_CK(h, cudaMemsetAsync(D.f, 0, (size_t)total * sizeof(double), h->stream));
+  D.changed();
+  pr_status s = sym_of_product(h, prec, h->X, R, inv_p, Z);
+  if (s != PR_OK) return s;
+  PR_CK(h, cudaMemcpyAsync(S.f, Z.f, (size_t)total * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  S.changed();
+  s = fdot(h, R, Z, 0);
+  if (s == PR_OK) s = read_scalars(h, 1);
+  if (s != PR_OK) return s;
+  double rz = h->rpin[0];
+  int it = 0;
+  while (it < cg_max && rz > 0.0 && std::isfinite(rz)) {
+    const pr::NvtxRange trace("refine solve iteration");
+    s = refine_apply(h, prec, o, S, LS);
+    if (s == PR_OK) s = fdot(h, S, LS, 0);
+    if (s == PR_OK) s = read_scalars(h, 1);
+    if (s != PR_OK) return s;
+    const double curv = h->rpin[0];
+    if (!(curv > 0.0) || !std::isfinite(curv)) break;
+    const double alpha = rz / curv;
+    PR_CK(h, pr::lincomb(D.f, S.f, total, 1.0, alpha, D.f, h->stream));
+    PR_CK(h, pr::lincomb(R.f, LS.f, total, 1.0, -alpha, R.f, h->stream));
+    h->st.launches += 2;
+    D.changed();
+    R.changed();
+    ++it;
+    s = fdot(h, R, R, 0);
+    if (s != PR_OK) return s;
+    if (it < cg_max) {  // the next preconditioned residual, read back with ||R||^2 in one synchronisation
+      s = sym_of_product(h, prec, h->X, R, inv_p, Z);
+      if (s == PR_OK) s = fdot(h, R, Z, 1);
+      if (s != PR_OK) return s;
+    }
+    s = read_scalars(h, it < cg_max ? 2 : 1);
+    if (s != PR_OK) return s;
+    if (sqrt(h->rpin[0]) <= cg_tol * g0 || it >= cg_max) break;
+    const double rz_new = h->rpin[1];
+    PR_CK(h, pr::lincomb(Z.f, S.f, total, 1.0, rz_new / rz, S.f, h->stream));
+    h->st.launches += 1;
+    S.changed();
+    rz = rz_new;
+  }
+  *its = it;
+  return PR_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int pr_version(void) { return 100; }
@@ -974,7 +1208,7 @@ pr_status pr_destroy(pr_handle h) {
   if (!h) return PR_OK;
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
-  for (Mat* m : {&h->A, &h->X, &h->Xn, &h->M, &h->Mn, &h->N, &h->Nn, &h->T0, &h->T1}) {
+  for (Mat* m : {&h->A, &h->X, &h->Xn, &h->M, &h->Mn, &h->N, &h->Nn, &h->T0, &h->T1, &h->Ra, &h->Rb, &h->Rc}) {
     if (m->f) cudaFree(m->f);
     if (m->b) cudaFree(m->b);
     if (m->sl) cudaFree(m->sl);
@@ -982,8 +1216,9 @@ pr_status pr_destroy(pr_handle h) {
     if (m->q) cudaFree(m->q);
     if (m->qe) cudaFree(m->qe);
   }
-  for (double* b : {h->partial, h->work, h->scal, h->vec, h->xbest, h->xstart})
+  for (double* b : {h->partial, h->work, h->scal, h->vec, h->xbest, h->xstart, h->rdev})
     if (b) cudaFree(b);
+  if (h->rpin) cudaFreeHost(h->rpin);
   for (auto& lists : h->emu_items)
     for (int4* it : lists)
       if (it) cudaFree(it);
@@ -1601,6 +1836,129 @@ pr_status pr_stats(pr_handle h, pr_stats_t* out) {
   if (!out) return fail(h, PR_EINVAL, "pr_stats: out is NULL");
   *out = h->st;
   return PR_OK;
+}
+
+pr_status pr_refine(pr_handle h, int precision, int inner_precision, int max_steps, double tol, int cg_max,
+                    double cg_tol, int* steps_done) {
+  if (steps_done) *steps_done = 0;
+  if (!h) return fail(nullptr, PR_ESTATE, "pr_refine: NULL handle");
+  if (!precision_known(precision) || !precision_known(inner_precision))
+    return fail(h, PR_EINVAL, "pr_refine: unknown precision");
+  if (max_steps < 0 || max_steps > PR_REFINE_MAX_STEPS || !(tol >= 0) || cg_max < 1 || !(cg_tol >= 0))
+    return fail(h, PR_EINVAL, "pr_refine: max_steps outside [0, PR_REFINE_MAX_STEPS], tol or cg_tol < 0, or cg_max < 1");
+  if (h->st.norm_1 <= 0.0) return fail(h, PR_ESTATE, "pr_refine: no matrix loaded");
+  if (h->opt.quant_bits > 0) return fail(h, PR_EUNSUPPORTED, "pr_refine: not part of the custom-precision experiment");
+  if (h->p > 4) return fail(h, PR_EUNSUPPORTED, "pr_refine: p > 4");
+  cudaSetDevice(h->device);
+  pr_status s = ensure_refine(h);
+  if (s != PR_OK) return s;
+  const pr::NvtxRange trace("pr_refine");
+  const size_t bytes = (size_t)h->n * (size_t)h->n * sizeof(double);
+  // From here on the coupled form's M and N, the scratch products and the BF16 copies are overwritten.
+  h->state_ready = false;
+  h->lp_stale = true;
+  h->powers_valid = false;
+  // Only this call's own conversions vouch for a BF16 copy (other paths keep theirs by lp_stale).
+  for (Mat* m : {&h->A, &h->X, &h->Xn, &h->M, &h->Mn, &h->N, &h->Nn, &h->T0, &h->T1, &h->Ra, &h->Rb, &h->Rc})
+    m->b_valid = false;
+  h->st.refine_len = 0;
+  int k = 0;
+  double gprev = 0.0;
+  pr_status stop = PR_OK;
+  while (true) {
+    const pr::NvtxRange trace_step("refine step");
+    RefineOps o;
+    double g = 0.0;
+    s = refine_setup(h, precision, o);
+    if (s == PR_OK) s = refine_residual(h, precision, o, &g);
+    if (s != PR_OK) return s;
+    h->st.refine_residuals[h->st.refine_len++] = g;
+    if (!std::isfinite(g) || (k >= 1 && !(g < gprev))) {
+      // The last correction did not help (the precision floor) or overflowed: return to the previous iterate.
+      stop = std::isfinite(g) ? PR_ESTAGNATED : PR_EDIVERGED;
+      if (k >= 1) {
+        PR_CK(h, cudaMemcpyAsync(h->X.f, h->xbest, bytes, cudaMemcpyDeviceToDevice, h->stream));
+        h->X.changed();
+        h->st.refine_len -= 1;
+        k -= 1;
+        h->st.refine_steps -= 1;
+        h->st.refine_cg_iterations -= h->st.refine_cg[k];
+        h->st.refine_cg[k] = 0;
+      }
+      break;
+    }
+    if (g <= tol) {
+      stop = PR_OK;
+      break;
+    }
+    if (k >= 1 && gprev < h->opt.stag_below && g > h->opt.stag_ratio * gprev) {
+      stop = PR_ESTAGNATED;
+      break;
+    }
+    if (k >= max_steps) {
+      stop = PR_EMAXITER;
+      break;
+    }
+    int its = 0;
+    s = refine_solve(h, inner_precision, o, g, cg_max, cg_tol, &its);
+    if (s != PR_OK) return s;
+    PR_CK(h, cudaMemcpyAsync(h->xbest, h->X.f, bytes, cudaMemcpyDeviceToDevice, h->stream));
+    PR_CK(h, pr::lincomb(h->X.f, h->Mn.f, h->n * h->n, 1.0, 1.0, h->X.f, h->stream));
+    h->st.launches += 1;
+    h->X.changed();
+    h->st.refine_cg[k] = its;
+    h->st.refine_steps += 1;
+    h->st.refine_cg_iterations += its;
+    gprev = g;
+    ++k;
+  }
+  if (steps_done) *steps_done = k;
+  for (Mat* m : {&h->X, &h->Xn, &h->M, &h->Mn, &h->N, &h->Nn, &h->T0, &h->T1}) m->changed();
+  if (stop != PR_EDIVERGED) {
+    double r = 0.0;
+    s = true_residual(h, precision, &r);
+    if (s != PR_OK) return s;
+    h->st.true_residual = r;
+    if (stop == PR_OK && !(r <= tol)) {
+      char buf[200];
+      snprintf(buf, sizeof buf,
+               "pr_refine: ||G(X)||_F = %.3e met tol = %.3e, but the true residual ||I - X^p A||_F = %.3e does not",
+               h->st.refine_residuals[h->st.refine_len - 1], tol, r);
+      h->err = buf;
+      stop = PR_EINACCURATE;
+    }
+  } else {
+    h->err = "pr_refine: the residual is not finite";
+  }
+  h->st.last_stop = stop;
+  return stop;
+}
+
+pr_status pr_set_iterate(pr_handle h, const double* X) {
+  if (!h) return fail(nullptr, PR_ESTATE, "pr_set_iterate: NULL handle");
+  if (!X) return fail(h, PR_EINVAL, "pr_set_iterate: X is NULL");
+  if (h->st.norm_1 <= 0.0) return fail(h, PR_ESTATE, "pr_set_iterate: no matrix loaded");
+  cudaSetDevice(h->device);
+  const int n = (int)h->n;
+  const size_t bytes = (size_t)n * (size_t)n * sizeof(double);
+  PR_CK(h, cudaMemcpyAsync(h->Xn.f, X, bytes, cudaMemcpyDefault, h->stream));
+  PR_CK(h, pr::validate(h->Xn.f, n, h->scal, h->stream));
+  h->st.launches += 1;
+  PR_CK(h, cudaMemcpyAsync(h->hpin, h->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  pr_status s = sync(h);
+  if (s != PR_OK) return s;
+  const double amax = h->hpin[0], asym = h->hpin[1], nonfinite = h->hpin[2], nonpos = h->hpin[3];
+  if (nonfinite > 0) return fail(h, PR_EINVAL, "pr_set_iterate: X has non-finite entries");
+  if (asym > h->opt.sym_tol * amax) return fail(h, PR_EINVAL, "pr_set_iterate: X is not symmetric");
+  if (nonpos > 0) return fail(h, PR_ENOTSPD, "pr_set_iterate: X is not positive definite");
+  reset_iteration(h);
+  // The handle iterates on 2^k A, whose root is 2^(-k/p) times the root of the caller's A.
+  const double c = exp2(-(double)h->st.prescale_log2 / h->p);
+  PR_CK(h, pr::lincomb(h->Xn.f, h->Xn.f, (int64_t)n * n, c, 0.0, h->X.f, h->stream));
+  h->st.launches += 1;
+  h->X.changed();
+  h->Xn.changed();
+  return sync(h);
 }
 
 pr_status pr_history(pr_handle h, double* out, int cap, int* len) {

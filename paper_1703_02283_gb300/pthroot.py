@@ -26,6 +26,7 @@ PR_FORM_AUTO, PR_FORM_COUPLED, PR_FORM_NS, PR_FORM_LITERAL = 0, 1, 2, 3
 PR_C0_EQ3, PR_C0_SCALED_I, PR_C0_POLY = 0, 1, 2
 PR_QUANT_STORAGE, PR_QUANT_ARITH = 1, 2
 PR_MLP_PARAMS = 4996
+PR_REFINE_MAX_STEPS = 16
 
 
 class pr_options(ctypes.Structure):
@@ -51,7 +52,10 @@ class pr_stats_t(ctypes.Structure):
                 ("true_residual", ctypes.c_double), ("prescale_log2", ctypes.c_int),
                 ("emu_tile_n", ctypes.c_int * 2), ("emu_tile_split", ctypes.c_int * 2),
                 ("emu_tune_ms", ctypes.c_double), ("emu_variant_ms", (ctypes.c_double * 4) * 2),
-                ("ladder_restores", ctypes.c_int)]
+                ("ladder_restores", ctypes.c_int), ("refine_steps", ctypes.c_int),
+                ("refine_cg_iterations", ctypes.c_int64), ("refine_len", ctypes.c_int),
+                ("refine_residuals", ctypes.c_double * (PR_REFINE_MAX_STEPS + 1)),
+                ("refine_cg", ctypes.c_int * PR_REFINE_MAX_STEPS)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -59,6 +63,8 @@ class pr_stats_t(ctypes.Structure):
         for k in ("iterations_by_precision", "gemms_timed_by_precision", "gemm_ms_by_precision",
                   "gemm_flops_by_precision", "emu_tile_n", "emu_tile_split"):
             d[k] = list(getattr(self, k))
+        d["refine_residuals"] = list(self.refine_residuals)[: self.refine_len]
+        d["refine_cg"] = list(self.refine_cg)[: max(self.refine_len - 1, 0)]
         return d
 
 
@@ -115,6 +121,9 @@ def _load() -> ctypes.CDLL:
         "pr_solve_ladder": (ctypes.c_int, [_handle_t, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                            ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.POINTER(ctypes.c_int)]),
         "pr_residual": (ctypes.c_int, [_handle_t, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+        "pr_refine": (ctypes.c_int, [_handle_t, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                     ctypes.c_double, ctypes.POINTER(ctypes.c_int)]),
+        "pr_set_iterate": (ctypes.c_int, [_handle_t, _dptr]),
         "pr_result": (ctypes.c_int, [_handle_t, _dptr]),
         "pr_stop_rule": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                         ctypes.c_double, ctypes.POINTER(pr_options)]),
@@ -255,6 +264,21 @@ def pr_residual(h: int, precision: int = PR_FP64) -> float:
     r = ctypes.c_double(0.0)
     _check(_lib.pr_residual(h, int(precision), ctypes.byref(r)), h)
     return r.value
+
+
+def pr_refine(h: int, precision: int, inner_precision: int, max_steps: int, tol: float, cg_max: int,
+              cg_tol: float) -> tuple[int, int]:
+    """Returns (status, corrections kept); stop statuses (PR_OK, PR_ESTAGNATED, PR_EMAXITER, PR_EINACCURATE) do
+    not raise."""
+    d = ctypes.c_int(0)
+    st = _lib.pr_refine(h, int(precision), int(inner_precision), int(max_steps), float(tol), int(cg_max),
+                        float(cg_tol), ctypes.byref(d))
+    _check(st, h, STOPS)
+    return st, d.value
+
+
+def pr_set_iterate(h: int, X) -> None:
+    _check(_lib.pr_set_iterate(h, _ptr(X)), h)
 
 
 def pr_result(h: int, C_out) -> None:

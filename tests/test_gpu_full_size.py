@@ -6,6 +6,8 @@
   EMU64 and native FP64 products.
 * Order-4096 instances of the large recipe (kappa = 1e4, p = 2) from the scaled identity.
 * The order-16384 large case itself, built on the device.
+* The benchmark's refinement (pr_refine) of the order-4096 Eq. 3 solves for p = 2..4, held to the
+  scaled-identity bar.
 
 The order-4096 results are compared with the oracle's own solves of the same recipes
 (tests/golden/oracle_n4096.json, written by tests/golden/make_oracle_n4096.py from oracle/ only) and with
@@ -132,6 +134,37 @@ def test_single_recipe_n4096_against_oracle(single_case, p):
         np.testing.assert_allclose(np.asarray(info["history"])[k], hg[k], rtol=rtol)
     # The true residual of the result, with EMU64 products: at most what the oracle's result has.
     assert info["residual"] <= max(GOLD["tol"], 10 * g["true_residual"])
+
+
+# The benchmark's refinement of the p >= 2 solves (Newton corrections with BF16 solves), and the same with
+# split-FP32 solves.
+REFINE = {"bf16": dict(inner=P.PR_BF16, max_steps=12, cg_max=40, cg_tol=1e-2),
+          "fp32x": dict(inner=P.PR_FP32X, max_steps=8, cg_max=80, cg_tol=1e-6)}
+
+
+@pytest.mark.parametrize("solve", ["bf16", "fp32x"])
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_single_recipe_n4096_refined_to_fp64_accuracy(single_case, p, solve):
+    # The benchmark's launch configuration for p >= 2: EMU64 iterations from Eq. 3's C_0 (which end at
+    # u kappa^(p+1)), then pr_refine with EMU64 residuals and BF16 solves. The result meets the bar of the
+    # oracle's FP64-accurate solve of the same matrix from the scaled identity: on the whole result against
+    # the closed form, and on its stored 64 x 64 block.
+    c, A = single_case
+    g = gold(1e-3, 1, p, "scaled_identity")
+    r = REFINE[solve]
+    h = P.pr_init(A, 4096, p, None, stream())
+    try:
+        P.pr_iterate(h, 100, P.PR_EMU64, GOLD["tol"])
+        st, k = P.pr_refine(h, P.PR_EMU64, r["inner"], r["max_steps"], GOLD["tol"], r["cg_max"], r["cg_tol"])
+        C = torch.empty((4096, 4096), dtype=torch.float64, device=DEV)
+        P.pr_result(h, C)
+        stats = P.pr_stats(h)
+    finally:
+        P.pr_destroy(h)
+    fe = check_against_gold(C.cpu().numpy(), None, g, O.closed_form_root(c.Q, c.lam, p))
+    assert fe <= 1e-12
+    assert st in (P.PR_ESTAGNATED, P.PR_EINACCURATE) and 1 <= k <= r["max_steps"]
+    assert stats["true_residual"] <= max(GOLD["tol"], 10 * g["true_residual"])
 
 
 @pytest.mark.parametrize("seed", [20, 21])
