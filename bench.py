@@ -769,8 +769,8 @@ def measure_f1(args, local):
 
 def measure_large(args, local):
     """The large recipe (n = 16384, kappa = 1e4, p = 2, the matrix built on the device, scaled-identity start):
-    the FP8 -> BF16 -> split-FP32 ladder, the same ladder ending in EMU64, and the all-EMU64 solve, each timed
-    once after a short untimed pass
+    the FP8 -> BF16 -> split-FP32 ladder, the same ladder ending in EMU64, the split-FP32 rung refined by Newton
+    corrections (pr_refine), and the all-EMU64 solve, each timed once after a short untimed pass
     that tunes and allocates. Errors: relative Frobenius error on a sampled 64 x 64 block of the closed form
     Q diag(lam^-1/2) Q^T (rows I, columns I) and the true residual of the library's own evaluation."""
     import torch
@@ -788,20 +788,26 @@ def measure_large(args, local):
     del case.Q
     torch.cuda.empty_cache()
     out = {"workload": f"SPD n={n}, kappa=1e4, p={p}, scaled-identity C_0, tol {args.tol:g}"}
-    for name, rungs in (("ladder_fp8_bf16_fp32x", [P.PR_FP8, P.PR_BF16, P.PR_FP32X]),
-                        ("ladder_fp8_bf16_fp32x_emu64", [P.PR_FP8, P.PR_BF16, P.PR_FP32X, P.PR_EMU64]),
-                        ("emu64", [P.PR_EMU64])):
+    for name, rungs, refine in (("ladder_fp8_bf16_fp32x", [P.PR_FP8, P.PR_BF16, P.PR_FP32X], False),
+                                ("ladder_fp8_bf16_fp32x_emu64", [P.PR_FP8, P.PR_BF16, P.PR_FP32X, P.PR_EMU64], False),
+                                ("ladder_fp32x_refined", [P.PR_FP32X], True),
+                                ("emu64", [P.PR_EMU64], False)):
         o = P.pr_default_options()
         o.c0 = P.PR_C0_SCALED_I
         h = P.pr_init(case.A, n, p, o, stream.cuda_stream)
         try:
             for prec in rungs:  # tune and allocate outside the timed solve
                 P.pr_iterate(h, 1, prec, args.tol)
+            if refine:
+                P.pr_refine(h, P.PR_EMU64, P.PR_BF16, 1, 0.0, REFINE["cg_max"], REFINE["cg_tol"])
             P.pr_load(h, case.A)
             torch.cuda.synchronize(dev)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             st, steps = P.pr_solve_ladder(h, rungs, None, args.tol)
+            if refine:  # the split-FP32 rung's end, refined: Newton corrections (EMU64 residuals, BF16 solves)
+                st, _ = P.pr_refine(h, P.PR_EMU64, P.PR_BF16, REFINE["max_steps"], args.tol, REFINE["cg_max"],
+                                    REFINE["cg_tol"])
             e1.record(stream)
             e1.synchronize()
             s = P.pr_stats(h)
@@ -816,6 +822,9 @@ def measure_large(args, local):
                                                  for k in range(P.PR_NPREC) if s["iterations_by_precision"][k]},
                      "true_residual": s["true_residual"], "rungs_discarded": s["ladder_restores"],
                      "rel_error_sampled_block": float(np.linalg.norm(Cb - Zb) / np.linalg.norm(Zb))}
+        if refine:
+            out[name]["refine"] = {"steps": len(s["refine_residuals"]) - 1, "residuals": s["refine_residuals"],
+                                   "cg_iterations": s["refine_cg"]}
         torch.cuda.empty_cache()
     return out
 

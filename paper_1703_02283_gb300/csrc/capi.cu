@@ -61,6 +61,7 @@ struct Out {
   double a = 0.0, b = 0.0, c = 0.0;
   bool partial = false;      // per-tile sums of the residual ||I - P||_F^2
   bool transpose = false;    // full-mode products whose result is the B operand of a later product
+  bool lp_copy = true;       // BF16: also write the BF16 copies of out / out2 (operands of later BF16 products)
 };
 }  // namespace
 
@@ -320,12 +321,12 @@ pr_status product(pr_handle h, int prec, Mat& X, Mat& Y, Mode mode, const Out& o
     if (o.out2) e.out2 = o.out2->f;
   } else if (prec == PR_BF16) {
     if (o.out) {
-      e.out_lp = o.out->b;
-      if (o.out_master) e.out = o.out->f;
+      if (o.lp_copy) e.out_lp = o.out->b;
+      if (o.out_master || !o.lp_copy) e.out = o.out->f;
     }
     if (o.out2) {
-      e.out2_lp = o.out2->b;
-      if (o.out2_master) e.out2 = o.out2->f;
+      if (o.lp_copy) e.out2_lp = o.out2->b;
+      if (o.out2_master || !o.lp_copy) e.out2 = o.out2->f;
     }
   } else {
     if (o.out) e.out = o.out->f;
@@ -993,6 +994,7 @@ pr_status plain_product(pr_handle h, int prec, Mat& Xop, Mat& Yop, Mode mode, Ma
   if (s != PR_OK) return s;
   Out o;
   o.out = &out;
+  o.lp_copy = false;
   return product(h, prec, Xop, Yop, mode, o);
 }
 
@@ -1004,6 +1006,7 @@ pr_status sym_of_product(pr_handle h, int prec, Mat& Xop, Mat& Yop, double scale
   Out o;
   o.out2 = &h->Xn;
   o.b = scale;
+  o.lp_copy = false;
   s = product(h, prec, Xop, Yop, Mode::Full, o);
   if (s != PR_OK) return s;
   PR_CK(h, pr::symmetrize(h->Xn.f, (int)h->n, out.f, h->stream));
@@ -1069,6 +1072,7 @@ pr_status refine_residual(pr_handle h, int prec, const RefineOps& o, double* g) 
   Out oo;
   oo.a = 1.0;
   oo.b = -1.0;
+  oo.lp_copy = false;
   if (o.m == o.mq) {  // W V = X^m A X^m is symmetric: upper tiles, mirrored
     oo.out2 = &h->M;
     s = product(h, prec, *o.W, *o.V, Mode::Sym, oo);
@@ -1111,6 +1115,7 @@ pr_status refine_apply(pr_handle h, int prec, const RefineOps& o, Mat& S, Mat& L
   oo.b = 1.0;
   oo.c = 1.0;
   oo.cin = LS.f;
+  oo.lp_copy = false;
   s = product(h, prec, *o.W, *Dmq, Mode::Full, oo);
   if (s != PR_OK) return s;
   PR_CK(h, pr::symmetrize(h->Xn.f, (int)h->n, LS.f, h->stream));
