@@ -96,7 +96,7 @@ def parse():
     ap.add_argument("--emu-slices", type=int, default=0, help="PR_EMU64 digit planes per operand (0: the default, 8)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "learned", "f1"],
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "learned", "f1", "f3"],
                     help="single: the n=4096 matrix for every p; batched: 512 matrices, n in [64, 1024]")
     ap.add_argument("--count", type=int, default=512, help="batched: number of matrices")
     ap.add_argument("--learned-n", type=int, default=2048, help="learned: matrix order")
@@ -829,6 +829,69 @@ def measure_large(args, local):
     return out
 
 
+def measure_f3(args, local):
+    """The sparse overlap stand-in of Sec. 4.1 at the paper's densities (6.2 % non-zeros at N = 3072, 3.1 % at
+    6144): S^-1 (p = 1: BF16 then EMU64 Newton-Schulz) and S^-1/2 (p = 2: EMU64 coupled form from Eq. 3, then the
+    refinement), each with block-sparse products with S (pr_options.block_sparse) and dense ones, one timed solve
+    after an untimed one on the same handle. The two give bit-identical results; forward errors against a LAPACK
+    root at N = 3072."""
+    import torch
+
+    from oracle import pthroot_oracle as O
+    from paper_1703_02283_gb300 import pthroot as P
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    out = {}
+    for n in (3072, 6144):
+        S, cut = W.sparse_overlap(n, W.PAPER_OVERLAP_DENSITY[n], n)
+        Sd = torch.from_numpy(S).to(dev)
+        rec = {"density": float(np.count_nonzero(S) / S.size), "cutoff": cut}
+        for p in (1, 2):
+            Z = O.eig_root(S, p) if n <= 3072 else None
+            res = {}
+            for bs in (1, 0):
+                o = P.pr_default_options()
+                o.block_sparse = bs
+                h = P.pr_init(Sd, n, p, o, stream.cuda_stream)
+                try:
+                    def solve():
+                        P.pr_load(h, Sd)
+                        if p == 1:
+                            st, its = P.pr_solve(h, P.PR_BF16, 100, P.PR_EMU64, args.tol)
+                        else:
+                            st, its = P.pr_iterate(h, 100, P.PR_EMU64, args.tol)
+                            st, _ = P.pr_refine(h, P.PR_EMU64, P.PR_BF16, REFINE["max_steps"], args.tol,
+                                                REFINE["cg_max"], REFINE["cg_tol"])
+                        return st, its
+                    solve()
+                    torch.cuda.synchronize(dev)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    st, its = solve()
+                    e1.record(stream)
+                    e1.synchronize()
+                    s = P.pr_stats(h)
+                    C = torch.empty((n, n), dtype=torch.float64, device=dev)
+                    P.pr_result(h, C)
+                finally:
+                    P.pr_destroy(h)
+                r = {"ms": e0.elapsed_time(e1), "status": P.STATUS_NAMES[st], "iterations": its,
+                     "true_residual": s["true_residual"], "sparse_keep": s["sparse_keep"],
+                     "sparse_products": s["sparse_products"]}
+                if Z is not None:
+                    r["rel_error_vs_lapack"] = O.forward_error(C.cpu().numpy(), Z)
+                res["block_sparse" if bs else "dense"] = (r, C)
+            (rs, Cs), (rd, Cd) = res["block_sparse"], res["dense"]
+            rs["bit_identical_to_dense"] = bool(torch.equal(Cs, Cd))
+            rs["speedup_over_dense"] = rd["ms"] / rs["ms"]
+            rec[f"p{p}"] = {"block_sparse": rs, "dense": rd}
+            del Cs, Cd
+        out[str(n)] = rec
+        del Sd
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_f1(args):
     if args.impl == "reference":
         if int(os.environ.get("RANK", "0")) != 0:
@@ -874,6 +937,16 @@ def main():
         return run_learned(args)
     if args.workload == "f1":
         return run_f1(args)
+    if args.workload == "f3":  # the sparse overlap summary on its own (one GPU, rank 0 prints)
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the sparse overlap summary has no oracle timing"}))
+            return None
+        import torch
+        torch.cuda.set_device(replica_env()[2])
+        out = measure_f3(args, replica_env()[2])
+        if replica_env()[1] == 0:
+            print(json.dumps({"workload": "f3", **out}), flush=True)
+        return None
     if args.impl == "reference":
         return run_reference(args, ps)
 
@@ -1108,6 +1181,11 @@ def main():
             extra["f1"] = {"ms": r1["value"], "reference_norm": r1["reference_norm"], **r1["table"]}
         except Exception as exc:
             extra["f1"] = {"error": f"{type(exc).__name__}: {exc}"}
+        torch.cuda.empty_cache()
+        try:
+            extra["f3"] = measure_f3(args, local)
+        except Exception as exc:
+            extra["f3"] = {"error": f"{type(exc).__name__}: {exc}"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,

@@ -149,6 +149,10 @@ typedef struct {
                           mantissa bits (PR_FORM_LITERAL from Eq. 3's C_0 with PR_FP64 iterations only, else
                           pr_init returns PR_EUNSUPPORTED). The stop test's residual is evaluated in FP64  */
   int quant_mode;      /* pr_quant_mode, default PR_QUANT_STORAGE                                          */
+  int block_sparse;    /* 1 (default): products with A at PR_EMU64 / PR_FP32X skip the K steps where the rows
+                          of A that a tile reads are zero, when that leaves out at least 1/8 of the steps
+                          (A's zero pattern is read at pr_init / pr_load). The steps skipped hold zero digits,
+                          so every product is bit-identical to the dense one. 0: never skip              */
 } pr_options;
 
 /* Most Newton corrections one pr_refine call applies. */
@@ -199,6 +203,9 @@ typedef struct {
   double refine_residuals[PR_REFINE_MAX_STEPS + 1]; /* ||G(X_k)||_F of the last pr_refine, k = 0 .. refine_len - 1,
                                                        the last one of the iterate it returned (see pr_refine) */
   int refine_cg[PR_REFINE_MAX_STEPS]; /* conjugate-gradient iterations of each correction of the last pr_refine */
+  double sparse_keep;       /* block sparsity of the loaded A (pr_options.block_sparse): the fraction of K steps a
+                               full product A X keeps, 1 when products with A run dense                       */
+  int64_t sparse_products;  /* products with A that skipped K steps                                            */
 } pr_stats_t;
 
 /* Fills *opt with the defaults listed above. */

@@ -85,6 +85,14 @@ struct pr_handle_s {
   long long* emu_scratch = nullptr;          // PR_EMU64 first-pass totals (pr::emu_scratch_bytes())
   long long* emu_split = nullptr;            // PR_EMU64 half totals of tiles split over K (pr::emu_launch_list)
   int* emu_split_cnt = nullptr;
+  // Block-sparse A (pr_options.block_sparse): per row of the loaded A the first and last non-zero column, and
+  // work lists of the unsplit variants restricted to the K steps the rows of A in a tile can reach,
+  // [mode][width 96 / 48][A the first operand, the second, both], rebuilt after each pr_load.
+  int* span_dev = nullptr;                   // 2n ints
+  std::vector<int> a_first, a_last;
+  bool sp_on = false;
+  int4* sp_items[2][2][3] = {};
+  bool sp_built[2][2][3] = {};
 
   // The input, the iterate X, the carried product M and operand N of the coupled form, their next
   // values, and two scratch products.
@@ -364,7 +372,18 @@ pr_status product(pr_handle h, int prec, Mat& X, Mat& Y, Mode mode, const Out& o
         pr_status ps = choose_emu_variant(h, m, pc, S, launch);
         if (ps != PR_OK) return ps;
       }
-      PR_CK(h, launch(h->emu_plan[m][pc]));
+      const bool xa = &X == &h->A, ya = &Y == &h->A;
+      if (h->sp_on && (xa || ya)) {
+        // Block-sparse A: the unsplit list of the chosen width, each tile restricted to the K steps where the
+        // rows of A it reads are non-zero (the other steps add exact zeros).
+        const int wi = kEmuVariants[h->emu_plan[m][pc]].bn == 96 ? 0 : 1, side = xa && ya ? 2 : (xa ? 0 : 1);
+        PR_CK(h, pr::gemm_emu(X.sl, X.ex, Y.sl, Y.ex, n, h->eld, S, mode, o.transpose, h->sp_items[m][wi][side],
+                              h->emu_nitems[m][2 * wi], e, h->emu_scratch, nullptr, h->emu_split_cnt, h->err_word(),
+                              h->stream, kEmuVariants[2 * wi].bn));
+        h->st.sparse_products += 1;
+      } else {
+        PR_CK(h, launch(h->emu_plan[m][pc]));
+      }
       h->lp_stale = true;
       break;
     }
@@ -948,6 +967,61 @@ pr_status matmul(int precision, int S, const double* X, const double* Y, int64_t
 
 namespace {
 
+// ---- Block-sparse A (pr_options.block_sparse)
+//
+// From the first and last non-zero column of every row of A: the unsplit work lists of every product mode and
+// tile width with each tile restricted to the K steps [j0, j1) that can hold non-zero digits of the rows of A
+// the tile reads (A the first operand: the tile's 128 rows; the second: its bn columns, i.e. rows of A; both:
+// the intersection). A tile whose rows of A are zero keeps one step (its digits are zero). Used when the full
+// product A X keeps at most 7/8 of the steps; the lists are rebuilt at every pr_load.
+pr_status build_sparse_lists(pr_handle h) {
+  const int n = (int)h->n, KS = (n + 15) / 16;
+  auto envelope = [&](int r0, int rows, int& lo, int& hi) {
+    for (int r = r0; r < std::min(n, r0 + rows); ++r) {
+      lo = std::min(lo, h->a_first[r]);
+      hi = std::max(hi, h->a_last[r]);
+    }
+  };
+  std::vector<int4> lists[2][2][3];
+  double kept = 0.0, total = 0.0;
+  for (int m = 0; m < 2; ++m)
+    for (int wi = 0; wi < 2; ++wi) {
+      if (!h->emu_items[m][2 * wi]) continue;  // width not in use (pr_options.emu_tile)
+      const int bn = kEmuVariants[2 * wi].bn;
+      std::vector<int4> base;
+      pr::emu_launch_list(n, m == 0 ? Mode::Sym : Mode::Full, base, bn, 0);
+      for (int side = 0; side < 3; ++side) {
+        std::vector<int4>& out = lists[m][wi][side];
+        out.reserve(base.size());
+        for (const int4& it : base) {
+          int lo1 = n, hi1 = -1, lo2 = n, hi2 = -1;
+          if (side != 1) envelope(128 * it.y, 128, lo1, hi1);
+          if (side != 0) envelope(bn * it.z, bn, lo2, hi2);
+          const int lo = side == 0 ? lo1 : side == 1 ? lo2 : std::max(lo1, lo2);
+          const int hi = side == 0 ? hi1 : side == 1 ? hi2 : std::min(hi1, hi2);
+          const int j0 = hi < lo ? 0 : lo / 16, j1 = hi < lo ? 1 : hi / 16 + 1;
+          out.push_back(j0 == 0 && j1 == KS ? it : pr::emu_range_item(it, j0, j1));
+          if (m == 1 && wi == 0 && side == 0) {
+            kept += j1 - j0;
+            total += KS;
+          }
+        }
+      }
+    }
+  h->st.sparse_keep = total > 0 ? kept / total : 1.0;
+  h->sp_on = h->st.sparse_keep <= 0.875;
+  if (!h->sp_on) return PR_OK;
+  for (int m = 0; m < 2; ++m)
+    for (int wi = 0; wi < 2; ++wi)
+      for (int side = 0; side < 3; ++side) {
+        const std::vector<int4>& v = lists[m][wi][side];
+        if (v.empty()) continue;
+        if (!h->sp_items[m][wi][side]) PR_CK(h, cudaMalloc((void**)&h->sp_items[m][wi][side], v.size() * sizeof(int4)));
+        PR_CK(h, cudaMemcpy(h->sp_items[m][wi][side], v.data(), v.size() * sizeof(int4), cudaMemcpyHostToDevice));
+      }
+  return PR_OK;
+}
+
 // ---- Newton refinement of an approximate root (pr_refine)
 //
 // Newton's method on the balanced residual G(X) = I - sym(X^m A X^m'), m = floor(p/2), m' = p - m: each step
@@ -1205,6 +1279,7 @@ void pr_default_options(pr_options* o) {
   o->emu_tile = 0;
   o->quant_bits = 0;
   o->quant_mode = PR_QUANT_STORAGE;
+  o->block_sparse = 1;
 }
 
 const char* pr_last_error(pr_handle h) { return h ? h->err.c_str() : g_init_error.c_str(); }
@@ -1230,6 +1305,11 @@ pr_status pr_destroy(pr_handle h) {
   if (h->emu_scratch) cudaFree(h->emu_scratch);
   if (h->emu_split) cudaFree(h->emu_split);
   if (h->emu_split_cnt) cudaFree(h->emu_split_cnt);
+  if (h->span_dev) cudaFree(h->span_dev);
+  for (auto& a : h->sp_items)
+    for (auto& b : a)
+      for (int4* it : b)
+        if (it) cudaFree(it);
   if (h->hpin) cudaFreeHost(h->hpin);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   delete h;
@@ -1330,6 +1410,7 @@ pr_status pr_init(pr_handle* out, const double* A, int64_t n, int p, const pr_op
     }
   }
   PR_INIT_CK(cudaMalloc((void**)&h->emu_scratch, pr::emu_scratch_bytes()));
+  PR_INIT_CK(cudaMalloc((void**)&h->span_dev, 2 * (size_t)n * sizeof(int)));
   if (slots > 0) {
     PR_INIT_CK(cudaMalloc((void**)&h->emu_split, pr::emu_split_bytes(slots)));
     PR_INIT_CK(cudaMalloc((void**)&h->emu_split_cnt, pr::emu_split_counters(slots) * sizeof(int)));
@@ -1361,6 +1442,16 @@ pr_status pr_load(pr_handle h, const double* A) {
   PR_CK(h, pr::abs_norms(h->A.f, n, h->work, h->scal + 4, h->stream));
   h->st.launches += 4;
   PR_CK(h, cudaMemcpyAsync(h->hpin, h->scal, 6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  h->sp_on = false;
+  h->st.sparse_keep = 1.0;
+  if (h->opt.block_sparse) {
+    PR_CK(h, pr::row_spans(h->A.f, n, h->span_dev, h->span_dev + n, h->stream));
+    h->st.launches += 1;
+    h->a_first.resize(n);
+    h->a_last.resize(n);
+    PR_CK(h, cudaMemcpyAsync(h->a_first.data(), h->span_dev, n * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    PR_CK(h, cudaMemcpyAsync(h->a_last.data(), h->span_dev + n, n * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  }
   pr_status s = sync(h);
   if (s != PR_OK) return s;
   const double amax = h->hpin[0], asym = h->hpin[1], nonfinite = h->hpin[2], nonpos = h->hpin[3];
@@ -1377,6 +1468,10 @@ pr_status pr_load(pr_handle h, const double* A) {
                 "without a Cholesky factorisation)");
   h->st.norm_1 = h->hpin[4];
   h->st.norm_inf = h->hpin[5];
+  if (h->opt.block_sparse) {
+    s = build_sparse_lists(h);
+    if (s != PR_OK) return s;
+  }
   h->st.prescale_log2 = 0;
   if (h->p > 1 && h->st.norm_1 * h->st.norm_inf < 1.0) {
     // Eq. 2 for Eq. 3's C_0 needs ||A||_1 >= 1 when p > 1 (eigenvalues of C_0^p A up to ||A||_1^(1-p)):

@@ -163,6 +163,26 @@ __global__ void k_lincomb(const double* x, const double* y, int64_t total, doubl
     out[e] = fma(a, x[e], b * y[e]);
 }
 
+// One warp per row: the first and last column with a non-zero entry (n and -1 for a zero row).
+__global__ void k_row_spans(const double* __restrict__ A, int n, int* __restrict__ first, int* __restrict__ last) {
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (i >= n) return;
+  int lo = n, hi = -1;
+  for (int j = lane; j < n; j += 32)
+    if (A[(int64_t)i * n + j] != 0.0) {
+      lo = min(lo, j);
+      hi = max(hi, j);
+    }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  if (lane == 0) {
+    first[i] = lo;
+    last[i] = hi;
+  }
+}
+
 __global__ void k_symmetrize(const double* __restrict__ in, int n, double* __restrict__ out) {
   __shared__ double tile[32][33];
   const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
@@ -243,6 +263,11 @@ cudaError_t axpby_identity(const double* in, int n, double a, double b, double* 
 
 cudaError_t lincomb(const double* x, const double* y, int64_t total, double a, double b, double* out, cudaStream_t s) {
   k_lincomb<<<grid_for(total), kThreads, 0, s>>>(x, y, total, a, b, out);
+  return cudaGetLastError();
+}
+
+cudaError_t row_spans(const double* A, int n, int* first, int* last, cudaStream_t s) {
+  k_row_spans<<<(n + 7) / 8, 256, 0, s>>>(A, n, first, last);
   return cudaGetLastError();
 }
 

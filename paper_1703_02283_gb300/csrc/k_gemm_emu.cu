@@ -245,6 +245,8 @@ struct EmuArgs {
 
 // Item t: its matrix, tile, and the K steps [j0, j1) it covers. kpart = 0 is the whole tile; a tile split in
 // two has items with kpart = 1 + 2 slot + half, half 0 taking the first KS / 2 steps and half 1 the rest.
+// Unsplit items with w > 0 cover only the steps [w >> 16, w & 0xffff) (block-sparse operands: the digits of
+// every other step are zero for the rows of the tile, so those steps add exact zeros; emu_range_item).
 template <bool SPLIT>
 __device__ __forceinline__ const EmuMat& item_of(const EmuArgs& a, int t, int& bi, int& bj, int& kpart, int& j0,
                                                  int& j1) {
@@ -260,8 +262,8 @@ __device__ __forceinline__ const EmuMat& item_of(const EmuArgs& a, int t, int& b
     j1 = kpart == 0 || ((kpart - 1) & 1) == 1 ? KS : h;
   } else {
     kpart = 0;
-    j0 = 0;
-    j1 = KS;
+    j0 = it.w > 0 ? (it.w >> 16) : 0;
+    j1 = it.w > 0 ? (it.w & 0xffff) : KS;
   }
   return mt;
 }
@@ -861,6 +863,11 @@ int emu_split_slots(int n, Mode mode, int bn, int split) {
 
 bool emu_split_useful(int n, Mode mode, int bn) {
   return (n + EBK - 1) / EBK >= 2 && emu_tile_count(n, mode, bn) < 4 * sm_count_emu();
+}
+
+int4 emu_range_item(int4 item, int j0, int j1) {
+  item.w = (j0 << 16) | j1;
+  return item;
 }
 
 void emu_launch_list(int n, Mode mode, std::vector<int4>& out, int bn, int split) {

@@ -114,6 +114,9 @@ int emu_tile_count(int n, Mode mode, int bn = 96);
 void emu_launch_list(int n, Mode mode, std::vector<int4>& out, int bn = 96, int split = -1);
 int emu_split_slots(int n, Mode mode, int bn = 96, int split = -1);
 bool emu_split_useful(int n, Mode mode, int bn);  // at least 2 K steps and fewer than 4 waves of tiles
+// An unsplit item (from emu_tile_list) restricted to the K steps [j0, j1), 0 <= j0 < j1 <= KS < 65536: the
+// steps left out must hold zero digits in the operand rows of the tile (a block-sparse operand).
+int4 emu_range_item(int4 item, int j0, int j1);
 size_t emu_split_bytes(int slots);
 size_t emu_split_counters(int slots);
 int emu_tiles(int n, Mode mode, int bn = 96);  // residual partials of one product: tiles * emu_partials_per_item
@@ -170,6 +173,8 @@ cudaError_t set_scaled_identity(double* X, int n, double c, cudaStream_t s);
 cudaError_t axpby_identity(const double* in, int n, double a, double b, double* out, cudaStream_t s);
 // out[e] = fma(a, x[e], b y[e]) for e < total (out may alias x or y)
 cudaError_t lincomb(const double* x, const double* y, int64_t total, double a, double b, double* out, cudaStream_t s);
+// first[i] / last[i] = the smallest / largest j with A_ij != 0 (n and -1 for a zero row)
+cudaError_t row_spans(const double* A, int n, int* first, int* last, cudaStream_t s);
 // out = (in + in^T) / 2 (out != in)
 cudaError_t symmetrize(const double* in, int n, double* out, cudaStream_t s);
 // *result = sqrt(sum of partial[0..count)) in a fixed order

@@ -35,7 +35,8 @@ class pr_options(ctypes.Structure):
                 ("sym_tol", ctypes.c_double), ("reanchor", ctypes.c_int), ("emu_slices", ctypes.c_int),
                 ("stag_below_lowp", ctypes.c_double), ("c0_coef", ctypes.c_double * 4), ("gate_max", ctypes.c_double),
                 ("gate_iters", ctypes.c_int), ("verify", ctypes.c_int), ("gate_fallback", ctypes.c_int),
-                ("emu_tile", ctypes.c_int), ("quant_bits", ctypes.c_int), ("quant_mode", ctypes.c_int)]
+                ("emu_tile", ctypes.c_int), ("quant_bits", ctypes.c_int), ("quant_mode", ctypes.c_int),
+                ("block_sparse", ctypes.c_int)]
 
 
 class pr_stats_t(ctypes.Structure):
@@ -55,7 +56,8 @@ class pr_stats_t(ctypes.Structure):
                 ("ladder_restores", ctypes.c_int), ("refine_steps", ctypes.c_int),
                 ("refine_cg_iterations", ctypes.c_int64), ("refine_len", ctypes.c_int),
                 ("refine_residuals", ctypes.c_double * (PR_REFINE_MAX_STEPS + 1)),
-                ("refine_cg", ctypes.c_int * PR_REFINE_MAX_STEPS)]
+                ("refine_cg", ctypes.c_int * PR_REFINE_MAX_STEPS), ("sparse_keep", ctypes.c_double),
+                ("sparse_products", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -183,6 +183,31 @@ def test_large_recipe_n4096_instances_against_oracle(seed):
     np.testing.assert_allclose(np.asarray(info["history"])[k], hg[k], rtol=RES_RTOL)
 
 
+@pytest.mark.parametrize("seed", [20, 21])
+def test_large_recipe_n4096_split_fp32_rung_refined(seed):
+    # The large recipe's split-FP32 rung ends far from the root at kappa = 1e4 (a few percent); Newton
+    # corrections with EMU64 residuals and BF16 solves (the benchmark's arm) take it to the oracle's bar.
+    c = W.spd_from_spectrum(4096, 1e-4, seed)
+    g = gold(1e-4, seed, 2, "scaled_identity")
+    o = P.pr_default_options()
+    o.c0 = P.PR_C0_SCALED_I
+    h = P.pr_init(torch.from_numpy(c.A).to(DEV), 4096, 2, o, stream())
+    try:
+        st, _ = P.pr_solve_ladder(h, [P.PR_FP32X], None, GOLD["tol"])
+        Cl = torch.empty((4096, 4096), dtype=torch.float64, device=DEV)
+        P.pr_result(h, Cl)
+        r = REFINE["bf16"]
+        st, k = P.pr_refine(h, P.PR_EMU64, r["inner"], r["max_steps"], GOLD["tol"], r["cg_max"], r["cg_tol"])
+        C = torch.empty((4096, 4096), dtype=torch.float64, device=DEV)
+        P.pr_result(h, C)
+    finally:
+        P.pr_destroy(h)
+    Z = O.closed_form_root(c.Q, c.lam, 2)
+    assert O.forward_error(Cl.cpu().numpy(), Z) > 1e-6
+    fe = check_against_gold(C.cpu().numpy(), None, g, Z)
+    assert fe <= 1e-10 and k >= 1
+
+
 @pytest.mark.parametrize("prec", [P.PR_EMU64, P.PR_FP64])
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
 def test_single_recipe_n4096_scaled_identity(single_case, p, prec):

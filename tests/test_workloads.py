@@ -35,3 +35,22 @@ def test_batched_specs():
     assert set(np.unique(b.p)) <= {1, 2, 3}
     assert np.all(b.lam_min <= 0.1 + 1e-12) and np.all(b.lam_min >= 1e-4 - 1e-18)
     assert b.seeds[0] == 1000 and b.seeds[-1] == 1511
+
+
+def test_sparse_overlap_recipe():
+    # The densities of Sec. 4.1's overlap matrices, symmetric positive definite, unit diagonal, entries in
+    # [0, 1], non-zeros in a band of columns for every block of 128 rows (points ordered by x).
+    S, c = W.sparse_overlap(768, W.PAPER_OVERLAP_DENSITY[768], 3)
+    assert S.shape == (768, 768) and S.flags.c_contiguous and np.array_equal(S, S.T)
+    assert abs(np.count_nonzero(S) / S.size - 0.25) < 1e-3
+    assert np.all(np.diag(S) == 1.0) and S.min() >= 0.0 and S.max() <= 1.0
+    w = np.linalg.eigvalsh(S)
+    assert w.min() > 0 and w.max() / w.min() < 1e3
+    S2, c2 = W.sparse_overlap(768, W.PAPER_OVERLAP_DENSITY[768], 3)
+    assert np.array_equal(S, S2) and c == c2
+    S3, c3 = W.sparse_overlap(1536, W.PAPER_OVERLAP_DENSITY[1536], 3)
+    assert abs(np.count_nonzero(S3) / S3.size - 0.124) < 1e-3 and c3 < c + 1.0
+    for M, n in ((S, 768), (S3, 1536)):
+        nz = M != 0
+        spans = [np.ptp(np.nonzero(nz[b:b + 128].any(axis=0))[0]) + 1 for b in range(0, n, 128)]
+        assert np.mean(spans) < (0.85 if n == 768 else 0.7) * n
