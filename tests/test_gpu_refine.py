@@ -76,6 +76,36 @@ def test_refinement_follows_the_oracle(n, p):
     assert stats["true_residual"] == pytest.approx(O.residual_fro(C, c.A, p), rel=1e-2, abs=1e-12)
 
 
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_native_fp64_products_follow_the_oracle(p):
+    # The residual and the solve with native FP64 (DMMA) products, whose kernel computes X Y (not X Y^T): the
+    # p = 3 residual takes the W V form there.
+    c, Z, X0 = perturbed_root(200, 1e-2, 150 + p, p)
+    C, st, k, stats = refine_on_gpu(c.A, X0, p, P.PR_FP64, P.PR_FP64, 3, 0.0, 60, 1e-10)
+    Xo, info = O.refine_newton(c.A, X0, p, max_steps=3, tol=0.0, cg_max=60, cg_tol=1e-10)
+    hg, ho = np.asarray(stats["refine_residuals"]), np.asarray(info.residuals)
+    assert hg[0] == pytest.approx(ho[0], rel=1e-10)
+    m = min(len(hg), len(ho))
+    far = [i for i in range(1, m) if ho[i] > 1e-9]
+    np.testing.assert_allclose(hg[far], ho[far], rtol=1e-3)
+    assert O.forward_error(C, Z) <= max(1e-12, 10 * O.forward_error(Xo, Z))
+
+
+def test_start_outside_the_region_of_convergence_is_left_unchanged():
+    # Eq. 3's C_0 is far from the root for p = 2 at kappa = 1e2: a correction that does not lower the residual
+    # is undone, and the handle keeps the iterate it was given.
+    n, p = 160, 2
+    c = W.spd_from_spectrum(n, 1e-2, 61)
+    X0 = np.ascontiguousarray(O.initial_guess_eq3(c.A))
+    Xo, info = O.refine_newton(c.A, X0, p, max_steps=4, tol=0.0)
+    C, st, k, stats = refine_on_gpu(c.A, X0, p, P.PR_EMU64, P.PR_EMU64, 4, 0.0, 50, 1e-12)
+    assert st in (P.PR_ESTAGNATED, P.PR_EMAXITER, P.PR_EDIVERGED)
+    r = stats["refine_residuals"]
+    assert all(b < a for a, b in zip(r, r[1:]))  # every kept step lowered the residual
+    if info.steps == 0:  # the oracle keeps the start too: so must the library
+        assert k == 0 and np.array_equal(C, X0)
+
+
 @pytest.mark.parametrize("p", [2, 3, 4])
 @pytest.mark.parametrize("inner,cg_tol,steps", [(P.PR_FP32X, 1e-6, 6), (P.PR_BF16, 1e-2, 12)])
 def test_low_precision_solves_reach_the_bar(p, inner, cg_tol, steps):
