@@ -320,9 +320,8 @@ pr_status pr_solve_ladder(pr_handle h, int count, const int* precisions, const i
  * pr_stats records each step's residual and solve length (refine_residuals, refine_cg). The iteration counters
  * and history of Eq. 1 are not changed; a following pr_iterate re-forms the coupled form's M from the refined X.
  * Works on every form and on the iterate pr_iterate, pr_solve, pr_solve_ladder or pr_set_iterate left.
- * Products per step: 1 (p = 1), 2 (p = 2) or 3 (p = 3, 4) with `precision` (p = 3 adds one with
- * `inner_precision`, or with PR_FP64 when `precision` is PR_FP64); per solve iteration 2, 2, 3 or 4 with
- * `inner_precision`. Uses three n*n FP64 matrices (with their BF16 copies, and digit planes
+ * Products per step: 1 (p = 1), 2 (p = 2), 3 (p = 4) or 4 (p = 3) with `precision`; per solve iteration
+ * 2, 2, 3 or 4 with `inner_precision`. Uses three n*n FP64 matrices (with their BF16 copies, and digit planes
  * where the products need them) and a copy of X beyond pr_init's, allocated on the first call and kept until
  * pr_destroy (PR_ENOMEM if they cannot be). Synchronises the stream twice per solve iteration.
  * Errors: PR_ESTATE (NULL handle, no matrix), PR_EINVAL (unknown precision, max_steps outside

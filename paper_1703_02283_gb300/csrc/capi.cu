@@ -1031,8 +1031,7 @@ pr_status build_sparse_lists(pr_handle h) {
 //   definition, D_m A V, is V A D_m = Y dP_m(S); sym() does not see the difference),
 //   dP_1(S) = S, dP_2(S) = X S + S X = 2 sym(X S); for m = m' both terms are equal, L(S) = 2 sym(Y dP_m(S)).
 // Every product below has a symmetric second operand, so X Y and X Y^T coincide and the product kernels of
-// every precision apply; the one exception, p = 3's residual X Y^T = X A X^2, is used with the kernels that
-// compute X Y^T (all but native FP64, which forms W V). Buffers (the coupled form's state and the scratch products are free while a
+// every precision apply. Buffers (the coupled form's state and the scratch products are free while a
 // refinement runs; the next pr_iterate re-forms M and N from X): T0 = X^2, T1 = Y, Nn = W (p = 3; W = Y when
 // m = m', W = A when p = 1), M = R (the solve's residual, first G), Mn = D (the correction), N = S (the search
 // direction), Ra = Z (the preconditioned residual), Rb = L(S), Rc = dP_2(S), Xn = a product before its
@@ -1109,10 +1108,8 @@ struct RefineOps {
   Mat *U = nullptr, *V = nullptr, *Y = nullptr, *W = nullptr;  // U = X^m (null: I), V = X^m', Y = V A, W = U A
 };
 
-// The products of one step that do not depend on the correction: at the residual's precision, except W for
-// p = 3, which only the solve reads (at the solve's precision; refine_residual then forms X Y^T = X A X^2 instead
-// of W V, with the kernels that compute X Y^T, i.e. all but native FP64).
-pr_status refine_setup(pr_handle h, int prec, int inner, RefineOps& o) {
+// The products of one step that do not depend on the correction, at the residual's precision.
+pr_status refine_setup(pr_handle h, int prec, RefineOps& o) {
   o.m = h->p / 2;
   o.mq = h->p - o.m;
   pr_status s = PR_OK;
@@ -1134,7 +1131,7 @@ pr_status refine_setup(pr_handle h, int prec, int inner, RefineOps& o) {
   } else if (o.m == o.mq) {
     o.W = o.Y;
   } else {
-    s = plain_product(h, prec == PR_FP64 ? prec : inner, *o.U, h->A, Mode::Full, h->Nn);
+    s = plain_product(h, prec, *o.U, h->A, Mode::Full, h->Nn);
     if (s != PR_OK) return s;
     o.W = &h->Nn;
   }
@@ -1143,13 +1140,8 @@ pr_status refine_setup(pr_handle h, int prec, int inner, RefineOps& o) {
 
 // R = G(X) = I - sym(W V); *g = ||G(X)||_F.
 pr_status refine_residual(pr_handle h, int prec, const RefineOps& o, double* g) {
-  // p = 3 (m = 1, m' = 2): X Y^T = X A X^2, since W is at the solve's precision (all kernels but native FP64
-  // compute X Y^T); otherwise W V.
-  const bool xy = o.m >= 1 && o.m != o.mq && prec != PR_FP64;
-  Mat& F1 = xy ? h->X : *o.W;
-  Mat& F2 = xy ? *o.Y : *o.V;
-  pr_status s = lp_operand(h, prec, F1);
-  if (s == PR_OK) s = lp_operand(h, prec, F2);
+  pr_status s = lp_operand(h, prec, *o.W);
+  if (s == PR_OK) s = lp_operand(h, prec, *o.V);
   if (s != PR_OK) return s;
   Out oo;
   oo.a = 1.0;
@@ -1157,11 +1149,11 @@ pr_status refine_residual(pr_handle h, int prec, const RefineOps& o, double* g) 
   oo.lp_copy = false;
   if (o.m == o.mq) {  // W V = X^m A X^m is symmetric: upper tiles, mirrored
     oo.out2 = &h->M;
-    s = product(h, prec, F1, F2, Mode::Sym, oo);
+    s = product(h, prec, *o.W, *o.V, Mode::Sym, oo);
     if (s != PR_OK) return s;
   } else {
     oo.out2 = &h->Xn;
-    s = product(h, prec, F1, F2, Mode::Full, oo);
+    s = product(h, prec, *o.W, *o.V, Mode::Full, oo);
     if (s != PR_OK) return s;
     PR_CK(h, pr::symmetrize(h->Xn.f, (int)h->n, h->M.f, h->stream));
     h->st.launches += 1;
@@ -1977,7 +1969,7 @@ pr_status pr_refine(pr_handle h, int precision, int inner_precision, int max_ste
     const pr::NvtxRange trace_step("refine step");
     RefineOps o;
     double g = 0.0;
-    s = refine_setup(h, precision, inner_precision, o);
+    s = refine_setup(h, precision, o);
     if (s == PR_OK) s = refine_residual(h, precision, o, &g);
     if (s != PR_OK) return s;
     h->st.refine_residuals[h->st.refine_len++] = g;
