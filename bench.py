@@ -298,7 +298,8 @@ def run_reference(args, ps):
     ms = float(np.mean(step_ms[args.warmup:])) if args.steps else 0.0
     sample = (f"n={args.n}, p={','.join(map(str, ps))}: oracle setup of every root and single updates measured "
               f"(one per step, roots in turn), value = setup + median update x predicted iterations "
-              f"({', '.join(f'p={p}: {its[p]}' for p in ps)})")
+              f"({', '.join(f'p={p}: {its[p]}' for p in ps)}); the iteration of Eq. 1 only: the GPU arm's "
+              f"refinement of the p >= 2 roots (Newton steps with conjugate-gradient solves) has no oracle time here")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -1191,6 +1192,7 @@ def main():
             est, w = oracle_sample(case.A, p, last[p]["iterations"])
             tot += est
             what.append(w)
+        what.append("the iteration of Eq. 1 only (the refinement of the p >= 2 roots has no oracle time here)")
         cpu = {"value": tot, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle", "sample": "; ".join(what)}
 
     for handles in arms.values():
